@@ -173,3 +173,16 @@ def test_polar_diffusion_closed_form():
     B = 1 + 4 * nu * t
     ex = np.exp(-r ** 2 / B) / B + 0.5 * r ** 2 * np.exp(-r ** 2 / B) / B ** 3 * np.cos(2 * phi) + 0 * z
     assert O.weighted_l2(g, O.backward(g, s) - ex, ex) < 1e-7
+
+
+def test_norm_ratio_matches_log_form():
+    # The exact ratio agrees with the paper's exp(ln N_j - ln N_n) form to the
+    # accuracy of the rounded logs.
+    from oracle.operators import norm_ratio
+    for m in (0, 3, 50):
+        for n in range(m, m + 120, 7):
+            for j in (n - 2, n - 1, n + 1, n + 2):
+                if j < m:
+                    continue
+                lg = math.exp(O.ln_norm(j, m) - O.ln_norm(n, m))
+                assert abs(norm_ratio(j, n, m) / lg - 1) < 1e-12
