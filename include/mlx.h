@@ -1,0 +1,164 @@
+/*
+ * mlx.h -- C-ABI of the B300 (sm_103a) mapped Legendre / Fourier spectral hot path.
+ *
+ * The method (Lee & Wang, "MLegS: a modern mapped Legendre spectral method solver
+ * for unbounded domains"):
+ *   - algebraic map r = ell sqrt((1+x)/(1-x)) onto Gauss-Legendre nodes x_i   (Eq. (1))
+ *   - truncated expansion in normalised associated Legendre functions times
+ *     Fourier modes in phi and z, triangular n >= m, only m >= 0 stored       (Eq. (2), Eq. (7))
+ *   - pentadiagonal horizontal Laplacian D_m, full Laplacian D_m - kappa^2 I   (Eqs. (4)-(5))
+ *   - split form ds/dt = A(s) + L s, L = nu lap - nu_h (-lap)^{p/2}           (Eqs. (10)-(11))
+ *   - FE-BE and AB-CN with a Richardson start from FE-BE substeps              (Eq. (12), Sec. 3.3)
+ *   - Fisher-KPP reaction gamma u (1 - u)                                      (Eq. (17))
+ *
+ * Conventions shared by every entry point
+ *   - Every function returns int: MLX_OK (0) or a negative MLX_E* code; no C++
+ *     exception crosses this boundary.  mlx_strerror() names a code.
+ *   - The library owns its context (basis tables, operator factors, workspace,
+ *     CUDA graphs).  The caller owns every field buffer: device pointers that it
+ *     allocated, 16-byte aligned, passed with the CUDA stream to run on.
+ *     Nothing is freed or retained by the library after a call returns, except
+ *     cached CUDA graphs keyed on the caller's pointers (released by mlx_destroy).
+ *   - Physical fields: real, layout [Nz][Nphi][Nr] (r fastest), node (i, j, l) at
+ *     r_i, phi_j = 2 pi j / Nphi, z_l = Lz l / Nz.  Element type double for
+ *     MLX_FP64 and float for MLX_FP32 / MLX_BF16X3.
+ *   - Spectral fields: complex128 (interleaved re, im doubles) in the flat ragged
+ *     layout  index(m, k, n) = K * sum_{m' < m} (Nc - m') + k * (Nc - m) + (n - m),
+ *     m = 0..M-1, k = 0..K-1 in FFT order (wavenumber k for k < Kz, k - K above),
+ *     n = m..Nc-1.  K = 2 Kz - 1.  Basis functions carry no Condon-Shortley phase.
+ *     The m = 0 block of a real field is Hermitian in k.
+ *   - Calls on one context are not thread-safe; use one context per host thread.
+ *   - Errors: MLX_EINVAL for bad sizes, chops, ell <= 0, Lz <= 0, NULL or
+ *     misaligned pointers; MLX_ECUDA for a failed CUDA call (the message is kept
+ *     per context, see mlx_last_cuda_error); MLX_ESTATE for a call out of order
+ *     (solve before setup); MLX_ENOMEM when device allocation fails.
+ */
+#ifndef MLX_H
+#define MLX_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+struct CUstream_st;                       /* cudaStream_t without the CUDA headers */
+typedef struct CUstream_st* mlx_stream;   /* NULL = the legacy default stream      */
+
+typedef struct mlx_ctx mlx_ctx;
+
+enum {
+  MLX_OK = 0,
+  MLX_EINVAL = -1,
+  MLX_ECUDA = -2,
+  MLX_ENUMERIC = -3,
+  MLX_ETIMEOUT = -4,
+  MLX_ESTATE = -5,
+  MLX_ENOMEM = -6
+};
+
+/* Arithmetic of the transforms.  The implicit solve and the spectral state are
+ * always FP64; basis values, nodes and weights are generated in FP64. */
+enum { MLX_FP64 = 0, MLX_FP32 = 1, MLX_BF16X3 = 2 };
+
+/* Chop policy used when the corresponding chop in mlx_params is 0.
+ * LINEAR: M = Nphi/2, Kz = max(1, Nz/2) (Nyquist dropped).
+ * TWOTHIRDS: M = (Nphi-1)/3 + 1, Kz = (Nz-1)/3 + 1 -- the two-thirds mask of
+ * Sec. 3.3 realised as storage truncation.  Nc = Nr unless nr_c is given. */
+enum { MLX_CHOP_LINEAR = 0, MLX_CHOP_TWOTHIRDS = 1 };
+
+/* Nonlinear term kinds for mlx_nonlinear / mlx_advance. */
+enum { MLX_NONLIN_NONE = 0, MLX_NONLIN_FKPP = 1 };
+
+/* Implicit step kinds for mlx_implicit_solve. */
+enum { MLX_STEP_FEBE_HALF = 0, MLX_STEP_FEBE_FULL = 1, MLX_STEP_ABCN = 2 };
+
+typedef struct {
+  int nr, nphi, nz;          /* collocation counts: 2 <= Nr <= 1024; Nphi a power of
+                                two in [4, 1024]; Nz 1 or a power of two <= 1024     */
+  int nr_c, nphi_c, nz_c;    /* chops Nc, M, Kz (0 = from chop_policy); bounds of
+                                Sec. 3.1: Nc <= Nr, M <= Nphi/2, Kz <= Nz/2 (1 if Nz=1),
+                                and M <= Nc                                           */
+  double ell;                /* map scale ell > 0, Eq. (1)                            */
+  double lz;                 /* axial period Lz > 0 (kappa_k = 2 pi k / Lz)           */
+  int precision;             /* MLX_FP64 | MLX_FP32 | MLX_BF16X3                      */
+  int chop_policy;           /* MLX_CHOP_LINEAR | MLX_CHOP_TWOTHIRDS                  */
+} mlx_params;
+
+typedef struct {
+  int nr, nphi, nz;
+  int nc, M, Kz, K;          /* chops in effect and K = 2 Kz - 1                      */
+  long long n_phys;          /* Nz * Nphi * Nr real values                            */
+  long long n_spec;          /* K * sum_m (Nc - m) complex values                     */
+  int precision;
+  double ell, lz;
+} mlx_info;
+
+const char* mlx_strerror(int code);
+
+/* Text of the last CUDA error seen by this context ("" if none). */
+const char* mlx_last_cuda_error(const mlx_ctx* ctx);
+
+/* Build a context: Gauss-Legendre nodes and weights by Newton iteration in FP64
+ * on the GPU, the mapped radii (Eq. (1)), the normalised associated Legendre
+ * tables Pbar_n^m(x_i) by the normalised three-term recurrence (Eq. (7), no
+ * factorial is formed), the quadrature table w_i Pbar_n^m(x_i), the pentadiagonal
+ * Laplacian bands (Eq. (5), rescaled to the orthonormal basis), Fourier twiddles,
+ * and the workspace.  Runs on `stream` and synchronises it before returning.
+ * On error *out is set to NULL and nothing stays allocated. */
+int mlx_create(const mlx_params* params, mlx_stream stream, mlx_ctx** out);
+int mlx_destroy(mlx_ctx* ctx);
+int mlx_query(const mlx_ctx* ctx, mlx_info* info);
+
+/* Copy the FP64 nodes x_i (ascending), weights w_i and radii r_i, each Nr
+ * doubles, to host buffers (any may be NULL).  Synchronous. */
+int mlx_get_nodes(const mlx_ctx* ctx, double* x, double* w, double* r);
+
+/* Forward transform (physical -> spectral), Eq. (2) inverted by the phi and z
+ * DFTs (scaled 1/Nphi, 1/Nz) and the Gauss quadrature
+ * shat_nmk = sum_i w_i Pbar_n^m(x_i) f_mk(r_i).  Modes beyond the chops are
+ * dropped.  phys: device, n_phys reals (double or float, see above); spec:
+ * device, n_spec complex128.  Asynchronous on `stream`. */
+int mlx_forward(mlx_ctx* ctx, const void* phys, void* spec, mlx_stream stream);
+
+/* Backward transform (spectral -> physical): Eq. (2) summed at the nodes,
+ * s = Re sum_k f_0k e^{i kappa z} + 2 Re sum_{m>=1,k} f_mk e^{i(m phi + kappa z)}. */
+int mlx_backward(mlx_ctx* ctx, const void* spec, void* phys, mlx_stream stream);
+
+/* Nonlinear term A(s) of Eq. (10) in spectral space (one backward and one
+ * forward transform with the pointwise product between them, Sec. 3.3):
+ *   MLX_NONLIN_FKPP: A = gamma u (1 - u), Eq. (17); coeffs[0] = gamma.
+ * spec_in, spec_out: device complex128 ragged (may not alias). */
+int mlx_nonlinear(mlx_ctx* ctx, int kind, const double* coeffs, int ncoeffs,
+                  const void* spec_in, void* spec_out, mlx_stream stream);
+
+/* Set up the implicit operators for time step dt: per harmonic (m, |k|) the
+ * band matrix of L = nu (D_m - kappa^2) - nu_h (-(D_m - kappa^2))^{p/2}
+ * (Eq. (11); the power composes truncated band matrices), the band of
+ * I + dt/2 L, and banded LU factors with partial pivoting of I - dt/2 L and
+ * I - dt L, all in FP64 on the GPU.  p in {4, 6, 8} when nu_h > 0.
+ * Synchronises `stream`. */
+int mlx_implicit_setup(mlx_ctx* ctx, double nu, double nu_h, int p, double dt,
+                       mlx_stream stream);
+
+/* One implicit step per harmonic, FP64 (Eq. (12) and the FE-BE scheme):
+ *   MLX_STEP_FEBE_HALF: (I - dt/2 L) out = s + dt/2 A
+ *   MLX_STEP_FEBE_FULL: (I - dt   L) out = s + dt   A
+ *   MLX_STEP_ABCN:      (I - dt/2 L) out = (I + dt/2 L) s + dt/2 (3 A - A_prev)
+ * A may be NULL (A = 0); A_prev is read only by MLX_STEP_ABCN (NULL = 0).
+ * out must not alias s, A or A_prev.  MLX_ESTATE before mlx_implicit_setup. */
+int mlx_implicit_solve(mlx_ctx* ctx, int step, const void* s, const void* A,
+                       const void* A_prev, void* out, mlx_stream stream);
+
+/* Advance `nsteps` time steps of AB-CN (Eq. (12)) with the nonlinear term
+ * `kind`, in place on `state` (device complex128 ragged).  prev_A (device,
+ * n_spec complex128) holds A^{j-1} between calls.  If start != 0 the first step
+ * is the Richardson start s^1 = 2 FEBE_{dt/2}(FEBE_{dt/2}(s^0)) - FEBE_dt(s^0)
+ * and prev_A is overwritten with A(s^0); otherwise prev_A must hold A^{j-1}.
+ * One step is captured once per (state, prev_A) pair into a CUDA graph and
+ * replayed; the graph is launched on `stream`. */
+int mlx_advance(mlx_ctx* ctx, int kind, const double* coeffs, int ncoeffs,
+                void* state, void* prev_A, int nsteps, int start, mlx_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MLX_H */

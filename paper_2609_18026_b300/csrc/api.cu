@@ -1,0 +1,310 @@
+// C-ABI entry points of libmlx (declared in include/mlx.h).
+#include "mlx_internal.cuh"
+
+#include <stdlib.h>
+#include <string.h>
+
+int mlx_legendre_tiles(mlx_ctx* c, std::vector<LegTile>& fwd, std::vector<LegTile>& bwd);
+int mlx_fft_prepare(mlx_ctx* c);
+
+namespace {
+
+bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+bool aligned16(const void* p) { return (((uintptr_t)p) & 15u) == 0; }
+
+void free_ctx(mlx_ctx* c) {
+  if (!c) return;
+  for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
+  c->graphs.clear();
+  void* ptrs[] = {c->d_soff, c->d_boff, c->d_x, c->d_w, c->d_r, c->d_P64, c->d_W64, c->d_P32,
+                  c->d_W32, c->d_lap, c->d_twphi64, c->d_twz64, c->d_twphi32, c->d_twz32,
+                  c->d_tiles_fwd, c->d_tiles_bwd, c->d_mixed, c->d_zm, c->d_phys, c->d_specA,
+                  c->d_spec1, c->d_spec2, c->d_spec3, c->d_band_off, c->d_Bplus,
+                  c->lu_half.U, c->lu_half.L, c->lu_half.piv, c->lu_half.invd,
+                  c->lu_full.U, c->lu_full.L, c->lu_full.piv, c->lu_full.invd};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  delete c;
+}
+
+template <typename P>
+int dalloc(mlx_ctx* c, P** p, size_t bytes) {
+  cudaError_t e = cudaMalloc((void**)p, bytes ? bytes : 16);
+  if (e != cudaSuccess) {
+    c->last_err = std::string("cudaMalloc: ") + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? MLX_ENOMEM : MLX_ECUDA;
+  }
+  return MLX_OK;
+}
+
+// One AB-CN step: A^j = A(s) into Anew, then (I - dt/2 L) out = (I + dt/2 L) s
+// + dt/2 (3 A^j - A^{j-1}).
+int nonlinear_into(mlx_ctx* c, int kind, double c0, const double2* s, double2* A, cudaStream_t st) {
+  if (kind == MLX_NONLIN_NONE) {
+    MLX_CUDA_TRY(c, cudaMemsetAsync(A, 0, sizeof(double2) * c->n_spec, st));
+    return MLX_OK;
+  }
+  int rc = mlx_legendre_backward(c, s, st);
+  if (rc) return rc;
+  rc = mlx_fft_fkpp(c, c0, st);
+  if (rc) return rc;
+  return mlx_legendre_forward(c, A, st);
+}
+
+int abcn_step(mlx_ctx* c, int kind, double c0, const double2* s, double2* Anew,
+              const double2* Aprev, double2* out, cudaStream_t st) {
+  int rc = nonlinear_into(c, kind, c0, s, Anew, st);
+  if (rc) return rc;
+  return mlx_band_solve(c, MLX_STEP_ABCN, s, Anew, Aprev, out, st);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* mlx_strerror(int code) {
+  switch (code) {
+    case MLX_OK: return "ok";
+    case MLX_EINVAL: return "invalid argument";
+    case MLX_ECUDA: return "CUDA error";
+    case MLX_ENUMERIC: return "non-finite value detected";
+    case MLX_ETIMEOUT: return "bounded device wait expired";
+    case MLX_ESTATE: return "call out of order";
+    case MLX_ENOMEM: return "device allocation failed";
+    default: return "unknown error";
+  }
+}
+
+const char* mlx_last_cuda_error(const mlx_ctx* ctx) { return ctx ? ctx->last_err.c_str() : ""; }
+
+int mlx_create(const mlx_params* p, mlx_stream stream, mlx_ctx** out) {
+  if (!out) return MLX_EINVAL;
+  *out = nullptr;
+  if (!p) return MLX_EINVAL;
+  if (p->nr < 2 || p->nr > 1024) return MLX_EINVAL;
+  if (!is_pow2(p->nphi) || p->nphi < 4 || p->nphi > 1024) return MLX_EINVAL;
+  if (!(p->nz == 1 || (is_pow2(p->nz) && p->nz <= 1024))) return MLX_EINVAL;
+  if (!(p->ell > 0.0) || !(p->lz > 0.0)) return MLX_EINVAL;
+  if (p->precision != MLX_FP64 && p->precision != MLX_FP32) return MLX_EINVAL;
+  if (p->chop_policy != MLX_CHOP_LINEAR && p->chop_policy != MLX_CHOP_TWOTHIRDS) return MLX_EINVAL;
+  if (p->nr_c < 0 || p->nphi_c < 0 || p->nz_c < 0) return MLX_EINVAL;
+  int nc = p->nr_c ? p->nr_c : p->nr;
+  int M, Kz;
+  if (p->chop_policy == MLX_CHOP_LINEAR) {
+    M = p->nphi / 2;
+    Kz = p->nz > 1 ? p->nz / 2 : 1;
+  } else {
+    M = (p->nphi - 1) / 3 + 1;
+    Kz = (p->nz - 1) / 3 + 1;
+  }
+  if (p->nphi_c) M = p->nphi_c;
+  if (p->nz_c) Kz = p->nz_c;
+  if (nc > p->nr || M > p->nphi / 2 || M > nc || M < 1) return MLX_EINVAL;
+  if (Kz < 1 || (p->nz == 1 && Kz != 1) || (p->nz > 1 && Kz > p->nz / 2)) return MLX_EINVAL;
+
+  mlx_ctx* c = new mlx_ctx();
+  c->nr = p->nr; c->nphi = p->nphi; c->nz = p->nz;
+  c->nc = nc; c->M = M; c->Kz = Kz; c->K = 2 * Kz - 1;
+  c->precision = p->precision;
+  c->ell = p->ell; c->lz = p->lz;
+  c->n_phys = (long long)c->nz * c->nphi * c->nr;
+  c->soff.assign(M + 1, 0);
+  c->boff.assign(M + 1, 0);
+  c->band_off.assign(M + 1, 0);
+  long long tri = 0;
+  for (int m = 0; m < M; ++m) {
+    c->soff[m] = (long long)c->K * tri;
+    c->boff[m] = tri * c->nr;
+    c->band_off[m] = (long long)Kz * tri;
+    tri += nc - m;
+  }
+  c->soff[M] = (long long)c->K * tri;
+  c->boff[M] = tri * c->nr;
+  c->band_off[M] = (long long)Kz * tri;
+  c->tri = tri;
+  c->n_spec = (long long)c->K * tri;
+  c->band_rows = (long long)Kz * tri;
+
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t es = elem_size(c->precision);
+  int rc = MLX_OK;
+#define ALLOC(ptr, bytes) do { rc = dalloc(c, &(ptr), (bytes)); if (rc) { free_ctx(c); return rc; } } while (0)
+  ALLOC(c->d_soff, sizeof(long long) * (M + 1));
+  ALLOC(c->d_boff, sizeof(long long) * (M + 1));
+  ALLOC(c->d_band_off, sizeof(long long) * (M + 1));
+  ALLOC(c->d_x, sizeof(double) * c->nr);
+  ALLOC(c->d_w, sizeof(double) * c->nr);
+  ALLOC(c->d_r, sizeof(double) * c->nr);
+  ALLOC(c->d_P64, sizeof(double) * tri * c->nr);
+  ALLOC(c->d_W64, sizeof(double) * tri * c->nr);
+  ALLOC(c->d_P32, sizeof(float) * tri * c->nr);
+  ALLOC(c->d_W32, sizeof(float) * tri * c->nr);
+  ALLOC(c->d_lap, sizeof(double) * tri * 5);
+  ALLOC(c->d_twphi64, sizeof(double2) * (c->nphi / 2));
+  ALLOC(c->d_twphi32, sizeof(float2) * (c->nphi / 2));
+  ALLOC(c->d_twz64, sizeof(double2) * (c->nz / 2 + 1));
+  ALLOC(c->d_twz32, sizeof(float2) * (c->nz / 2 + 1));
+  ALLOC(c->d_mixed, es * 2 * c->K * c->M * c->nr);
+  if (c->nz > 1) ALLOC(c->d_zm, es * 2 * c->nz * c->M * c->nr);
+  ALLOC(c->d_phys, es * c->n_phys);
+  ALLOC(c->d_specA, sizeof(double2) * c->n_spec);
+  ALLOC(c->d_spec1, sizeof(double2) * c->n_spec);
+  ALLOC(c->d_spec2, sizeof(double2) * c->n_spec);
+  ALLOC(c->d_spec3, sizeof(double2) * c->n_spec);
+  std::vector<LegTile> tf, tb;
+  mlx_legendre_tiles(c, tf, tb);
+  c->ntiles_fwd = (int)tf.size();
+  c->ntiles_bwd = (int)tb.size();
+  ALLOC(c->d_tiles_fwd, sizeof(LegTile) * tf.size());
+  ALLOC(c->d_tiles_bwd, sizeof(LegTile) * tb.size());
+#undef ALLOC
+#define TRY(call) do { cudaError_t _e = (call); if (_e != cudaSuccess) { c->last_err = cudaGetErrorString(_e); free_ctx(c); return MLX_ECUDA; } } while (0)
+  TRY(cudaMemcpyAsync(c->d_soff, c->soff.data(), sizeof(long long) * (M + 1), cudaMemcpyHostToDevice, st));
+  TRY(cudaMemcpyAsync(c->d_boff, c->boff.data(), sizeof(long long) * (M + 1), cudaMemcpyHostToDevice, st));
+  TRY(cudaMemcpyAsync(c->d_band_off, c->band_off.data(), sizeof(long long) * (M + 1), cudaMemcpyHostToDevice, st));
+  TRY(cudaMemcpyAsync(c->d_tiles_fwd, tf.data(), sizeof(LegTile) * tf.size(), cudaMemcpyHostToDevice, st));
+  TRY(cudaMemcpyAsync(c->d_tiles_bwd, tb.data(), sizeof(LegTile) * tb.size(), cudaMemcpyHostToDevice, st));
+  TRY(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+#undef TRY
+  rc = mlx_fft_prepare(c);
+  if (!rc) rc = mlx_basis_build(c, st);
+  if (!rc) {
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) { c->last_err = cudaGetErrorString(e); rc = MLX_ECUDA; }
+  }
+  if (rc) { free_ctx(c); return rc; }
+  *out = c;
+  return MLX_OK;
+}
+
+int mlx_destroy(mlx_ctx* ctx) {
+  if (!ctx) return MLX_EINVAL;
+  free_ctx(ctx);
+  return MLX_OK;
+}
+
+int mlx_query(const mlx_ctx* c, mlx_info* info) {
+  if (!c || !info) return MLX_EINVAL;
+  info->nr = c->nr; info->nphi = c->nphi; info->nz = c->nz;
+  info->nc = c->nc; info->M = c->M; info->Kz = c->Kz; info->K = c->K;
+  info->n_phys = c->n_phys; info->n_spec = c->n_spec;
+  info->precision = c->precision;
+  info->ell = c->ell; info->lz = c->lz;
+  return MLX_OK;
+}
+
+int mlx_get_nodes(const mlx_ctx* cc, double* x, double* w, double* r) {
+  mlx_ctx* c = const_cast<mlx_ctx*>(cc);
+  if (!c) return MLX_EINVAL;
+  if (x) MLX_CUDA_TRY(c, cudaMemcpy(x, c->d_x, sizeof(double) * c->nr, cudaMemcpyDeviceToHost));
+  if (w) MLX_CUDA_TRY(c, cudaMemcpy(w, c->d_w, sizeof(double) * c->nr, cudaMemcpyDeviceToHost));
+  if (r) MLX_CUDA_TRY(c, cudaMemcpy(r, c->d_r, sizeof(double) * c->nr, cudaMemcpyDeviceToHost));
+  return MLX_OK;
+}
+
+int mlx_forward(mlx_ctx* c, const void* phys, void* spec, mlx_stream stream) {
+  if (!c || !phys || !spec || !aligned16(phys) || !aligned16(spec)) return MLX_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  int rc = mlx_fft_forward(c, phys, st);
+  if (rc) return rc;
+  return mlx_legendre_forward(c, (double2*)spec, st);
+}
+
+int mlx_backward(mlx_ctx* c, const void* spec, void* phys, mlx_stream stream) {
+  if (!c || !phys || !spec || !aligned16(phys) || !aligned16(spec)) return MLX_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  int rc = mlx_legendre_backward(c, (const double2*)spec, st);
+  if (rc) return rc;
+  return mlx_fft_backward(c, phys, st);
+}
+
+int mlx_nonlinear(mlx_ctx* c, int kind, const double* coeffs, int ncoeffs, const void* spec_in,
+                  void* spec_out, mlx_stream stream) {
+  if (!c || !spec_in || !spec_out || spec_in == spec_out) return MLX_EINVAL;
+  if (!aligned16(spec_in) || !aligned16(spec_out)) return MLX_EINVAL;
+  if (kind == MLX_NONLIN_FKPP && (!coeffs || ncoeffs < 1)) return MLX_EINVAL;
+  if (kind != MLX_NONLIN_FKPP && kind != MLX_NONLIN_NONE) return MLX_EINVAL;
+  return nonlinear_into(c, kind, coeffs ? coeffs[0] : 0.0, (const double2*)spec_in,
+                        (double2*)spec_out, (cudaStream_t)stream);
+}
+
+int mlx_implicit_setup(mlx_ctx* c, double nu, double nu_h, int p, double dt, mlx_stream stream) {
+  if (!c || !(dt > 0.0) || nu < 0.0 || nu_h < 0.0) return MLX_EINVAL;
+  if (nu_h > 0.0 && p != 4 && p != 6 && p != 8) return MLX_EINVAL;
+  for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
+  c->graphs.clear();
+  c->nu = nu; c->nu_h = nu_h; c->p = p; c->dt = dt;
+  c->kl = (nu_h > 0.0) ? p : 2;
+  c->implicit_ready = false;
+  int rc = mlx_band_setup(c, (cudaStream_t)stream);
+  if (rc) return rc;
+  c->implicit_ready = true;
+  return MLX_OK;
+}
+
+int mlx_implicit_solve(mlx_ctx* c, int step, const void* s, const void* A, const void* A_prev,
+                       void* out, mlx_stream stream) {
+  if (!c || !s || !out) return MLX_EINVAL;
+  if (!c->implicit_ready) return MLX_ESTATE;
+  if (step != MLX_STEP_FEBE_HALF && step != MLX_STEP_FEBE_FULL && step != MLX_STEP_ABCN) return MLX_EINVAL;
+  if (out == s || out == A || out == A_prev) return MLX_EINVAL;
+  return mlx_band_solve(c, step, (const double2*)s, (const double2*)A, (const double2*)A_prev,
+                        (double2*)out, (cudaStream_t)stream);
+}
+
+int mlx_advance(mlx_ctx* c, int kind, const double* coeffs, int ncoeffs, void* state, void* prev_A,
+                int nsteps, int start, mlx_stream stream) {
+  if (!c || !state || !prev_A || nsteps < 0 || state == prev_A) return MLX_EINVAL;
+  if (!aligned16(state) || !aligned16(prev_A)) return MLX_EINVAL;
+  if (kind != MLX_NONLIN_NONE && kind != MLX_NONLIN_FKPP) return MLX_EINVAL;
+  if (kind == MLX_NONLIN_FKPP && (!coeffs || ncoeffs < 1)) return MLX_EINVAL;
+  if (!c->implicit_ready) return MLX_ESTATE;
+  if (nsteps == 0) return MLX_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  const double c0 = coeffs ? coeffs[0] : 0.0;
+  double2* s = (double2*)state;
+  double2* Ap = (double2*)prev_A;
+  int rc;
+  if (start) {
+    // Richardson start: s1 = 2 FEBE_{dt/2}(FEBE_{dt/2}(s0)) - FEBE_dt(s0); A^0 kept.
+    if ((rc = nonlinear_into(c, kind, c0, s, Ap, st))) return rc;
+    if ((rc = mlx_band_solve(c, MLX_STEP_FEBE_HALF, s, Ap, nullptr, c->d_spec1, st))) return rc;
+    if ((rc = nonlinear_into(c, kind, c0, c->d_spec1, c->d_specA, st))) return rc;
+    if ((rc = mlx_band_solve(c, MLX_STEP_FEBE_HALF, c->d_spec1, c->d_specA, nullptr, c->d_spec2, st))) return rc;
+    if ((rc = mlx_band_solve(c, MLX_STEP_FEBE_FULL, s, Ap, nullptr, c->d_spec3, st))) return rc;
+    if ((rc = mlx_spec_axpby(c, 2.0, c->d_spec2, -1.0, c->d_spec3, s, st))) return rc;
+    --nsteps;
+  }
+  const int pairs = nsteps / 2;
+  if (pairs > 0) {
+    // two steps per graph: (s, A_prev) -> (spec1, specA) -> (s, A_prev), no copies
+    mlx_ctx::GraphKey key{state, prev_A, kind, c0};
+    auto it = c->graphs.find(key);
+    cudaGraphExec_t exec = nullptr;
+    if (it == c->graphs.end()) {
+      cudaGraph_t g = nullptr;
+      MLX_CUDA_TRY(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+      rc = abcn_step(c, kind, c0, s, c->d_specA, Ap, c->d_spec1, c->cap_stream);
+      if (!rc) rc = abcn_step(c, kind, c0, c->d_spec1, Ap, c->d_specA, s, c->cap_stream);
+      cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
+      if (rc) { if (g) cudaGraphDestroy(g); return rc; }
+      if (e != cudaSuccess) { c->last_err = cudaGetErrorString(e); return MLX_ECUDA; }
+      e = cudaGraphInstantiate(&exec, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) { c->last_err = cudaGetErrorString(e); return MLX_ECUDA; }
+      c->graphs[key] = exec;
+    } else {
+      exec = it->second;
+    }
+    for (int i = 0; i < pairs; ++i) MLX_CUDA_TRY(c, cudaGraphLaunch(exec, st));
+  }
+  if (nsteps % 2) {
+    if ((rc = abcn_step(c, kind, c0, s, c->d_specA, Ap, c->d_spec1, st))) return rc;
+    MLX_CUDA_TRY(c, cudaMemcpyAsync(s, c->d_spec1, sizeof(double2) * c->n_spec, cudaMemcpyDeviceToDevice, st));
+    MLX_CUDA_TRY(c, cudaMemcpyAsync(Ap, c->d_specA, sizeof(double2) * c->n_spec, cudaMemcpyDeviceToDevice, st));
+  }
+  return MLX_OK;
+}
+
+}  // extern "C"

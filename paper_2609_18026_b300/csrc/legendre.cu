@@ -1,0 +1,148 @@
+// K4 (SIMT form): the ragged per-m Gauss-quadrature contraction of the transform
+// pair (Eq. (2) and its quadrature inverse, Sec. 3.1).
+//
+// Forward, per m:  spec[m][k][n] = sum_i W_m[n][i] X[k][m][i]   (W = w_i Pbar_n^m(x_i))
+// Backward, per m: X[k][m][i]    = sum_n P_m[n][i] spec[m][k][n]
+// The real basis times complex data is one real GEMM with 2K columns
+// (column c < K: Re of wavenumber slot c; c >= K: Im of slot c - K).
+// Work is a host-built list of 64 x 64 output tiles over (m, row tile, col tile),
+// so the triangle's shrinking row count (Nc - m) wastes no whole tiles.
+// T is the storage and accumulation type (double: FP64 parity form; float: FP32).
+#include "mlx_internal.cuh"
+
+namespace {
+
+constexpr int BM = 64, BN = 64, BK = 16, NT = 256;
+
+template <typename T, bool FWD>
+__global__ void __launch_bounds__(NT) k_legendre(const LegTile* __restrict__ tiles, int nc, int nr,
+                                                 int M, int K, const long long* __restrict__ boff,
+                                                 const long long* __restrict__ soff,
+                                                 const T* __restrict__ table,  // W (fwd) or P (bwd)
+                                                 T* __restrict__ mixed,        // planar [2][K][M][Nr]
+                                                 double2* __restrict__ spec) {
+  __shared__ T As[BK][BM + 1];
+  __shared__ T Bs[BK][BN + 1];
+  const LegTile tile = tiles[blockIdx.x];
+  const int m = tile.m;
+  const int Nm = nc - m;
+  const int rows = FWD ? Nm : nr;         // output rows
+  const int kdim = FWD ? nr : Nm;         // contraction length
+  const int row0 = tile.row0, col0 = tile.col0;
+  const int ncol = 2 * K;
+  const long long plane = (long long)K * M * nr;
+  const T* tab = table + boff[m];
+  const long long so = soff[m];
+  const int tid = threadIdx.x;
+  const int tr = tid & 15, tc = tid >> 4;
+
+  T acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = (T)0;
+
+  for (int k0 = 0; k0 < kdim; k0 += BK) {
+    // A tile: A(row, kk)
+    for (int t = tid; t < BM * BK; t += NT) {
+      int row, kk;
+      if (FWD) { kk = t % BK; row = t / BK; }   // W_m[row][kk] contiguous in kk
+      else     { row = t % BM; kk = t / BM; }   // P_m[kk][row] contiguous in row (= i)
+      const int gr = row0 + row, gk = k0 + kk;
+      T v = (T)0;
+      if (gr < rows && gk < kdim)
+        v = FWD ? tab[(long long)gr * nr + gk] : tab[(long long)gk * nr + gr];
+      As[kk][row] = v;
+    }
+    // B tile: B(kk, col)
+    for (int t = tid; t < BK * BN; t += NT) {
+      const int kk = t % BK, col = t / BK;
+      const int gk = k0 + kk, gc = col0 + col;
+      T v = (T)0;
+      if (gk < kdim && gc < ncol) {
+        const int p = gc >= K;
+        const int kidx = gc - p * K;
+        if (FWD) {
+          v = mixed[p * plane + ((long long)kidx * M + m) * nr + gk];
+        } else {
+          const double2 s = spec[so + (long long)kidx * Nm + gk];
+          v = (T)(p ? s.y : s.x);
+        }
+      }
+      Bs[kk][col] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      T a[4], b[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) { a[q] = As[kk][tr + 16 * q]; b[q] = Bs[kk][tc + 16 * q]; }
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) acc[x][y] += a[x] * b[y];
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int x = 0; x < 4; ++x) {
+    const int gr = row0 + tr + 16 * x;
+    if (gr >= rows) continue;
+#pragma unroll
+    for (int y = 0; y < 4; ++y) {
+      const int gc = col0 + tc + 16 * y;
+      if (gc >= ncol) continue;
+      const int p = gc >= K;
+      const int kidx = gc - p * K;
+      if (FWD) {
+        double* dst = reinterpret_cast<double*>(&spec[so + (long long)kidx * Nm + gr]);
+        dst[p] = (double)acc[x][y];
+      } else {
+        mixed[p * plane + ((long long)kidx * M + m) * nr + gr] = acc[x][y];
+      }
+    }
+  }
+}
+
+}  // namespace
+
+int mlx_legendre_forward(mlx_ctx* c, double2* spec, cudaStream_t st) {
+  if (c->precision == MLX_FP64)
+    k_legendre<double, true><<<c->ntiles_fwd, NT, 0, st>>>(c->d_tiles_fwd, c->nc, c->nr, c->M, c->K,
+                                                          c->d_boff, c->d_soff, c->d_W64,
+                                                          (double*)c->d_mixed, spec);
+  else
+    k_legendre<float, true><<<c->ntiles_fwd, NT, 0, st>>>(c->d_tiles_fwd, c->nc, c->nr, c->M, c->K,
+                                                         c->d_boff, c->d_soff, c->d_W32,
+                                                         (float*)c->d_mixed, spec);
+  MLX_LAUNCH_CHECK(c);
+  return MLX_OK;
+}
+
+int mlx_legendre_backward(mlx_ctx* c, const double2* spec, cudaStream_t st) {
+  if (c->precision == MLX_FP64)
+    k_legendre<double, false><<<c->ntiles_bwd, NT, 0, st>>>(c->d_tiles_bwd, c->nc, c->nr, c->M, c->K,
+                                                           c->d_boff, c->d_soff, c->d_P64,
+                                                           (double*)c->d_mixed, (double2*)spec);
+  else
+    k_legendre<float, false><<<c->ntiles_bwd, NT, 0, st>>>(c->d_tiles_bwd, c->nc, c->nr, c->M, c->K,
+                                                          c->d_boff, c->d_soff, c->d_P32,
+                                                          (float*)c->d_mixed, (double2*)spec);
+  MLX_LAUNCH_CHECK(c);
+  return MLX_OK;
+}
+
+// Host: tile lists for both directions.
+int mlx_legendre_tiles(mlx_ctx* c, std::vector<LegTile>& fwd, std::vector<LegTile>& bwd) {
+  fwd.clear();
+  bwd.clear();
+  const int ncol = 2 * c->K;
+  for (int m = 0; m < c->M; ++m) {
+    const int Nm = c->nc - m;
+    for (int r0 = 0; r0 < Nm; r0 += BM)
+      for (int c0 = 0; c0 < ncol; c0 += BN) fwd.push_back(LegTile{m, r0, c0, 0});
+    for (int r0 = 0; r0 < c->nr; r0 += BM)
+      for (int c0 = 0; c0 < ncol; c0 += BN) bwd.push_back(LegTile{m, r0, c0, 0});
+  }
+  return MLX_OK;
+}

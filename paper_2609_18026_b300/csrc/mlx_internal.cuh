@@ -1,0 +1,126 @@
+// Internal definitions shared by the CUDA translation units of libmlx.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+#include <vector>
+#include <map>
+#include <utility>
+
+#include "../../include/mlx.h"
+
+#define MLX_CUDA_TRY(ctx, call)                                              \
+  do {                                                                       \
+    cudaError_t _e = (call);                                                 \
+    if (_e != cudaSuccess) {                                                 \
+      if (ctx) (ctx)->last_err = std::string(#call) + ": " + cudaGetErrorString(_e); \
+      return MLX_ECUDA;                                                      \
+    }                                                                        \
+  } while (0)
+
+#define MLX_LAUNCH_CHECK(ctx) MLX_CUDA_TRY(ctx, cudaGetLastError())
+
+// One GEMM work tile of the ragged per-m Legendre contraction.
+struct LegTile {
+  int m;     // azimuthal order
+  int row0;  // first output row of the tile (n - m for forward, i for backward)
+  int col0;  // first output column (0..2K-1; column c < K is Re of k = c, else Im)
+  int pad;
+};
+
+// Banded implicit operator storage for one matrix family, per (m, |k|):
+// rows i = 0..N_m-1 (N_m = Nc - m).  U row i holds columns i..i+kl+ku
+// (ku_f = kl + ku entries after the diagonal), L holds kl multipliers per
+// column, piv the pivot row of each column, invd 1/U[i][i].
+struct BandLU {
+  double* U = nullptr;     // [rows][W_u] with W_u = 1 + kl + ku
+  double* L = nullptr;     // [rows][kl]
+  int* piv = nullptr;      // [rows]
+  double* invd = nullptr;  // [rows]
+};
+
+struct mlx_ctx {
+  // sizes
+  int nr, nphi, nz, nc, M, Kz, K;
+  int precision;
+  double ell, lz;
+  long long n_phys, n_spec;
+  long long tri;                       // T = sum_m (Nc - m)
+  std::vector<long long> soff;         // spectral offset of m (complex units), size M+1
+  std::vector<long long> boff;         // basis-table offset of m (elements), size M+1
+  long long* d_soff = nullptr;
+  long long* d_boff = nullptr;
+
+  // nodes and basis (FP64 generated on the GPU)
+  double* d_x = nullptr;
+  double* d_w = nullptr;
+  double* d_r = nullptr;
+  double* d_P64 = nullptr;             // Pbar_n^m(x_i), [m][n-m][i]
+  double* d_W64 = nullptr;             // w_i Pbar_n^m(x_i), same layout
+  float* d_P32 = nullptr;
+  float* d_W32 = nullptr;
+  double* d_lap = nullptr;             // Laplacian band, [tri][5] (offsets -2..+2)
+
+  // Fourier twiddles exp(-2 pi i t / N), t < N/2, as (cos, sin) pairs
+  double2* d_twphi64 = nullptr;
+  double2* d_twz64 = nullptr;
+  float2* d_twphi32 = nullptr;
+  float2* d_twz32 = nullptr;
+
+  // Legendre GEMM tiles
+  LegTile* d_tiles_fwd = nullptr;
+  LegTile* d_tiles_bwd = nullptr;
+  int ntiles_fwd = 0, ntiles_bwd = 0;
+
+  // workspace (element type follows precision)
+  void* d_mixed = nullptr;             // planar complex [2][K][M][Nr]
+  void* d_zm = nullptr;                // planar complex [2][Nz][M][Nr]
+  void* d_phys = nullptr;              // physical scratch [Nz][Nphi][Nr]
+  double2* d_specA = nullptr;          // A^j
+  double2* d_spec1 = nullptr;          // Richardson temporaries
+  double2* d_spec2 = nullptr;
+  double2* d_spec3 = nullptr;
+
+  // implicit operators
+  bool implicit_ready = false;
+  double nu = 0, nu_h = 0, dt = 0;
+  int p = 8;
+  int kl = 2;                          // half bandwidth of L (2, or p with nu_h > 0)
+  long long band_rows = 0;             // sum_m (Nc - m) * Kz
+  std::vector<long long> band_off;     // row offset of (m, kabs=0), size M+1 (rows of m = Kz * N_m)
+  long long* d_band_off = nullptr;
+  double* d_Bplus = nullptr;           // band of I + dt/2 L, [rows][2kl+1]
+  BandLU lu_half, lu_full;
+  double* d_setup_scratch = nullptr;
+
+  // graphs cached per (state, prev_A, kind, gamma)
+  struct GraphKey {
+    void* s; void* a; int kind; double c0;
+    bool operator<(const GraphKey& o) const {
+      if (s != o.s) return s < o.s;
+      if (a != o.a) return a < o.a;
+      if (kind != o.kind) return kind < o.kind;
+      return c0 < o.c0;
+    }
+  };
+  std::map<GraphKey, cudaGraphExec_t> graphs;
+  cudaStream_t cap_stream = nullptr;
+
+  std::string last_err;
+};
+
+static inline size_t elem_size(int precision) { return precision == MLX_FP64 ? 8 : 4; }
+
+// ---- kernel-launch entry points (one per translation unit) ----
+int mlx_basis_build(mlx_ctx* c, cudaStream_t st);
+int mlx_fft_forward(mlx_ctx* c, const void* phys, cudaStream_t st);    // phys -> d_mixed
+int mlx_fft_backward(mlx_ctx* c, void* phys, cudaStream_t st);         // d_mixed -> phys
+int mlx_fft_fkpp(mlx_ctx* c, double gamma, cudaStream_t st);           // d_mixed -> A(mixed)
+int mlx_legendre_forward(mlx_ctx* c, double2* spec, cudaStream_t st);  // d_mixed -> spec
+int mlx_legendre_backward(mlx_ctx* c, const double2* spec, cudaStream_t st); // spec -> d_mixed
+int mlx_band_setup(mlx_ctx* c, cudaStream_t st);
+int mlx_band_solve(mlx_ctx* c, int step, const double2* s, const double2* A,
+                   const double2* Ap, double2* out, cudaStream_t st);
+int mlx_spec_axpby(mlx_ctx* c, double a, const double2* x, double b, const double2* y,
+                   double2* out, cudaStream_t st);

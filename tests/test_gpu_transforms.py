@@ -1,0 +1,98 @@
+"""GPU parity of nodes, transforms and the nonlinear term against the oracle.
+
+Bars: FP64 form within 1e-12 relative (spectral l2 with multiplicity 2 for
+m >= 1, or l2 over the nodes); FP32 form within 1e-6 relative.
+"""
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2609_18026_b300 import binding as B
+
+from gpu_common import pair, to_gpu_phys, to_gpu_spec, spec_from_gpu, rand_phys, rand_spec, rel
+
+pytestmark = pytest.mark.gpu
+
+GRIDS = [
+    # nr, nphi, nz, ell, policy       (tiny, ragged, several tiles, Nz = 1 and > 1)
+    (4, 4, 1, 1.0, "linear"),
+    (5, 8, 4, 0.8, "linear"),
+    (33, 16, 8, 1.7, "twothirds"),
+    (70, 32, 16, 2.0, "linear"),
+    (100, 64, 1, 4.0, "twothirds"),
+    (128, 128, 64, 4.0, "twothirds"),
+]
+TOL = {B.FP64: 1e-12, B.FP32: 1e-6}
+
+
+@pytest.mark.parametrize("nr", [2, 24, 96, 256, 1024])
+def test_nodes_weights_radii(nr):
+    g, ctx = pair(nr, 4, 1, 1.3)
+    x, w, r = ctx.nodes()
+    assert np.max(np.abs(x - g.x)) <= 4e-16
+    assert np.max(np.abs(w - g.w) / g.w) <= 1e-12
+    assert np.max(np.abs(r - g.r) / g.r) <= 1e-12
+
+
+@pytest.mark.parametrize("prec", [B.FP64, B.FP32])
+@pytest.mark.parametrize("grid", GRIDS)
+def test_forward_parity(grid, prec):
+    nr, nphi, nz, ell, pol = grid
+    g, ctx = pair(nr, nphi, nz, ell, lz=3.7, policy=pol, precision=prec)
+    f = rand_phys(g, 11)
+    if prec == B.FP32:
+        f = f.astype(np.float32).astype(np.float64)   # both sides see the same input
+    spec = ctx.forward(to_gpu_phys(ctx, f), ctx.new_spec())
+    got = spec_from_gpu(g, spec)
+    ref = O.forward(g, f)
+    assert O.spec_rel_err(g, got, ref) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", [B.FP64, B.FP32])
+@pytest.mark.parametrize("grid", GRIDS)
+def test_backward_parity(grid, prec):
+    nr, nphi, nz, ell, pol = grid
+    g, ctx = pair(nr, nphi, nz, ell, lz=3.7, policy=pol, precision=prec)
+    flat = rand_spec(g, 5)
+    phys = ctx.backward(to_gpu_spec(flat), ctx.new_phys())
+    got = phys.double().cpu().numpy()
+    ref = O.backward(g, O.from_flat(g, flat))
+    assert rel(got, ref) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", [B.FP64, B.FP32])
+def test_roundtrip_identity(prec):
+    g, ctx = pair(64, 32, 16, 1.0, policy="twothirds", precision=prec)
+    flat = rand_spec(g, 9)
+    s = to_gpu_spec(flat)
+    back = ctx.forward(ctx.backward(s, ctx.new_phys()), ctx.new_spec())
+    assert O.spec_rel_err(g, spec_from_gpu(g, back), O.from_flat(g, flat)) <= TOL[prec]
+
+
+def test_azimuthal_purity_exact():
+    # Sec. 5.1: odd harmonics of a cos(2 phi) field are identically zero.  The
+    # input is made bitwise periodic under phi -> phi + pi; the FFT's first
+    # butterfly then cancels exactly.
+    g, ctx = pair(48, 16, 1, 1.0)
+    r, phi, z = g.nodes3()
+    j = np.arange(g.nphi)
+    c2 = np.cos(2 * np.pi * ((2 * j) % g.nphi) / g.nphi)
+    f = (r ** 2 * np.exp(-r ** 2 / 2)) * c2[None, :, None] + 0 * z
+    spec = spec_from_gpu(g, ctx.forward(to_gpu_phys(ctx, f), ctx.new_spec()))
+    for m in range(1, g.M, 2):
+        assert np.all(spec[m] == 0.0)
+    assert np.max(np.abs(spec[0])) < 1e-16
+
+
+@pytest.mark.parametrize("prec", [B.FP64, B.FP32])
+@pytest.mark.parametrize("grid", [(5, 8, 4, 0.8), (40, 16, 8, 2.0), (128, 128, 64, 4.0)])
+def test_fkpp_nonlinear_parity(grid, prec):
+    nr, nphi, nz, ell = grid
+    g, ctx = pair(nr, nphi, nz, ell, lz=2 * np.pi * 8, policy="twothirds", precision=prec)
+    r, phi, z = g.nodes3()
+    from paper_2609_18026_b300 import workloads as W
+    s0 = O.forward(g, W.fkpp_seed(r, phi, z))
+    out = ctx.nonlinear(B.NONLIN_FKPP, [1.0], to_gpu_spec(O.to_flat(g, s0)), ctx.new_spec())
+    ref = O.fkpp_nonlinear(g, 1.0)(s0)
+    assert O.spec_rel_err(g, spec_from_gpu(g, out), ref) <= TOL[prec]
