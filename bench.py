@@ -1,0 +1,411 @@
+"""Benchmark of the spectral hot path on the 3-D Fisher-KPP workload.
+
+Workload: u_t = D lap u + u (1 - u) on the unbounded cylinder, Nr = Nphi = 128,
+Nz = 64, ell = 4, D = 1, Lz = 2 pi * 8, two-thirds chops (M = Kz = 43 stored
+harmonics), u0 = exp(-r^2/4)(1 + 0.01 xi), xi ~ U(-1, 1) per node (PCG64 seed 2),
+AB-CN with Richardson start, dt = 1e-2, 1000 time steps (t = 10).  Every time
+step is one transform pair (backward, pointwise reaction, forward) plus the FP64
+banded implicit solve, all in the CUDA library; transforms in FP32 (the FP64
+form is timed beside it).
+
+A benchmark "step" is 100 time steps of the workload (one graph-replay chain);
+the default 10 timed steps are the workload's 1000 time steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mlx|reference]
+
+Prints one JSON line (rank 0).  Under torchrun every rank advances its own
+independent copy of the workload (replicas: the solve has no data-parallel
+exchange on one problem of this size), timing is the max over ranks.
+"""
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+NR, NPHI, NZ, ELL = 128, 128, 64, 4.0
+LZ = 2.0 * math.pi * 8.0
+DT, D_COEF, GAMMA = 1e-2, 1.0, 1.0
+STEPS_PER_BENCH_STEP = 100
+WORKLOAD = "fkpp3d_128x128x64"
+METRIC = "timesteps/s"
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return d.get("hbm_gbs", 6400.0), "measured"
+    return 6400.0, "fallback"
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,pci.bus_id,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self):
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self, bus_id=None):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 10:
+                continue
+            rows.append(parts)
+        os.unlink(self.path)
+        if bus_id is not None:
+            mine = [r for r in rows if r[1].lower().endswith(bus_id.lower())]
+            rows = mine or rows
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        idx0 = rows[0][0]
+        rows = [r for r in rows if r[0] == idx0]
+
+        def num(v):
+            try:
+                return float(v)
+            except ValueError:
+                return float("nan")
+        sm = [num(r[2]) for r in rows]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for k, name in enumerate(names):
+                if r[6 + k].lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": num(rows[0][3]),
+                "power_w_max": max(num(r[4]) for r in rows), "samples": len(rows),
+                "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------- oracle arm
+_ORACLE = {}
+
+
+def oracle_sample(nsteps):
+    """Time the FP64 oracle, as it stands, on the full-size workload for `nsteps`
+    time steps from t = 0 (the first is the Richardson start); the grid and LU
+    factors are built once, outside the timing.  Returns (timesteps/s, threads, s)."""
+    import oracle as O
+    from paper_2609_18026_b300 import workloads as W
+    try:
+        from threadpoolctl import threadpool_info
+        threads = max([d.get("num_threads", 1) for d in threadpool_info()] or [1])
+    except Exception:
+        threads = 1
+    if not _ORACLE:
+        g = O.Grid(NR, NPHI, NZ, ELL, lz=LZ, policy="twothirds")
+        r, phi, z = g.nodes3()
+        _ORACLE["st"] = O.Stepper(g, D_COEF, DT, nonlinear=O.fkpp_nonlinear(g, GAMMA))
+        _ORACLE["s0"] = O.forward(g, W.fkpp_seed(r, phi, z))
+    t0 = time.perf_counter()
+    _ORACLE["st"].run_abcn(_ORACLE["s0"], nsteps)
+    sec = time.perf_counter() - t0
+    return nsteps / sec, threads, sec
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    per = max(1, int(os.environ.get("MLX_REF_STEPS_PER_SAMPLE", "2")))
+    oracle_sample(1)   # warm-up (imports, caches)
+    vals = []
+    t_all = time.perf_counter()
+    for _ in range(args.steps):
+        v, threads, _ = oracle_sample(per)
+        vals.append(v)
+    sec = time.perf_counter() - t_all
+    value = float(np.mean(vals))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "timesteps/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000.0 * STEPS_PER_BENCH_STEP / value,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded analytic initial condition)",
+        "config": {"workload": WORKLOAD, "nr": NR, "nphi": NPHI, "nz": NZ, "ell": ELL,
+                   "dt": DT, "timesteps_per_step": STEPS_PER_BENCH_STEP},
+        "cpu_baseline": {"value": value, "unit": "timesteps/s", "cores": threads, "kind": "oracle",
+                         "sample": "%d samples of %d full-size time steps each (first is the Richardson start), %.1f s"
+                                   % (args.steps, per, sec)},
+        "e2e": {"value": value, "unit": "timesteps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- GPU arm
+def algorithmic(kernel, ctx, nz_gt1=True):
+    """Algorithmic DRAM bytes and useful flops of one launch of a kernel at this size."""
+    es = 8 if ctx.precision == 0 else 4
+    tri = sum(ctx.nc - m for m in range(ctx.M))
+    mixed = 2 * ctx.K * ctx.M * ctx.nr * es
+    zm = 2 * ctx.nz * ctx.M * ctx.nr * es
+    spec = 16 * ctx.n_spec
+    table = tri * ctx.nr * es
+    leg_flops = 2.0 * 2.0 * ctx.K * tri * ctx.nr
+    rows = ctx.Kz * tri
+    kl = 2
+    if kernel == "legendre_forward":
+        return mixed + table + spec, leg_flops
+    if kernel == "legendre_backward":
+        return spec + table + mixed, leg_flops
+    if kernel == "phi_fkpp_fused":
+        return 2 * zm, 0.0
+    if kernel in ("z_forward", "z_inverse"):
+        return zm + mixed, 0.0
+    if kernel == "band_solve":
+        factors = rows * (8 * (2 * kl + 1) * 2 + 8 * kl + 4 + 8)
+        return 4 * spec + factors, 0.0
+    return 0, 0.0
+
+
+def run_gpu(args, rank, world):
+    import torch
+    import torch.distributed as dist
+    from paper_2609_18026_b300 import binding as B
+    from paper_2609_18026_b300 import workloads as W
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+
+    ctx = B.Context(NR, NPHI, NZ, ELL, lz=LZ, precision=B.FP32, chop_policy=B.CHOP_TWOTHIRDS)
+    ctx64 = B.Context(NR, NPHI, NZ, ELL, lz=LZ, precision=B.FP64, chop_policy=B.CHOP_TWOTHIRDS)
+    x, w, r = ctx.nodes()
+    phi = 2 * np.pi * np.arange(NPHI) / NPHI
+    zz = LZ * np.arange(NZ) / NZ
+    u0 = W.fkpp_seed(r[None, None, :], phi[None, :, None], zz[:, None, None], seed=2 + rank)
+    u0_32 = torch.as_tensor(u0, dtype=torch.float32, device=dev)
+    u0_64 = torch.as_tensor(u0, dtype=torch.float64, device=dev)
+    for c in (ctx, ctx64):
+        c.implicit_setup(D_COEF, DT)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+
+    def fresh(c, u):
+        s = c.forward(u, c.new_spec())
+        return s, c.new_spec()
+
+    def run_steps(c, s, a, k, timed):
+        """k bench steps from t = 0; returns per-step device ms (L2 flushed before each)."""
+        times = []
+        for i in range(k):
+            flush.fill_(i & 0xFF)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            c.advance(B.NONLIN_FKPP, [GAMMA], s, a, STEPS_PER_BENCH_STEP, i == 0)
+            e1.record(stream)
+            if timed:
+                times.append((e0, e1))
+        torch.cuda.synchronize()
+        return [a_.elapsed_time(b_) for a_, b_ in times]
+
+    # warm-up (graphs captured, caches warm)
+    s, a = fresh(ctx, u0_32)
+    run_steps(ctx, s, a, max(1, args.warmup), False)
+    s64, a64 = fresh(ctx64, u0_64)
+    run_steps(ctx64, s64, a64, 1, False)
+
+    # ---- timed region: FP32 transforms, K bench steps from t = 0
+    s, a = fresh(ctx, u0_32)
+    clocks = ClockSampler()
+    barrier()
+    clocks.start()
+    t_wall = time.perf_counter()
+    ms = run_steps(ctx, s, a, args.steps, True)
+    barrier()
+    t_wall = time.perf_counter() - t_wall
+    bus = None
+    try:
+        p = torch.cuda.get_device_properties(local)
+        bus = "%02x:%02x.0" % (p.pci_bus_id, p.pci_device_id)
+    except Exception:
+        pass
+    clk = clocks.stop(bus)
+    total_ms = float(sum(ms))
+    tmax = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    total_ms = float(tmax.item())
+    timesteps = args.steps * STEPS_PER_BENCH_STEP * world
+    value = timesteps / (total_ms / 1000.0)
+
+    # ---- FP64 form, same workload and step count
+    s64, a64 = fresh(ctx64, u0_64)
+    ms64 = run_steps(ctx64, s64, a64, args.steps, True)
+    fp64_value = args.steps * STEPS_PER_BENCH_STEP / (sum(ms64) / 1000.0)
+    d = (s.cpu().numpy() - s64.cpu().numpy())
+    mult = np.ones(ctx.n_spec)
+    off = ctx.K * ctx.nc   # m = 0 block has multiplicity 1
+    mult[off:] = 2.0
+    rel_err = float(np.sqrt(np.sum(mult * np.abs(d) ** 2) / np.sum(mult * np.abs(s64.cpu().numpy()) ** 2)))
+
+    # ---- transform pair alone (backward + forward through the C-ABI)
+    spec_in = s.clone()
+    phys = ctx.new_phys()
+    spec_out = ctx.new_spec()
+    for _ in range(5):
+        ctx.backward(spec_in, phys)
+        ctx.forward(phys, spec_out)
+    flush.fill_(1)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    npair = 200
+    e0.record(stream)
+    for _ in range(npair):
+        ctx.backward(spec_in, phys)
+        ctx.forward(phys, spec_out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    pair_per_s = npair / (e0.elapsed_time(e1) / 1000.0)
+
+    # ---- per-kernel CUDA-event timing of the same bench steps (instrumented pass)
+    s_i, a_i = fresh(ctx, u0_32)
+    ctx.timing(True)
+    run_steps(ctx, s_i, a_i, 2, False)          # bench steps 1-2 exactly as timed above
+    kt = ctx.timing_read()
+    ctx.timing(False)
+    launches_2 = sum(v[0] for v in kt.values())
+    ctx.timing(True)
+    ctx.advance(B.NONLIN_FKPP, [GAMMA], s_i, a_i, 10, False)
+    steady = sum(v[0] for v in ctx.timing_read().values()) / 10.0   # launches per AB-CN step
+    ctx.timing(False)
+    first_step_launches = launches_2 - steady * STEPS_PER_BENCH_STEP
+    gpu_launches = int(round(first_step_launches + steady * STEPS_PER_BENCH_STEP * (args.steps - 1)))
+    total_k = sum(v[1] for v in kt.values())
+    top = max(kt.items(), key=lambda kv: kv[1][1])
+    top_name, (top_n, top_ms) = top[0], top[1]
+    avg_s = top_ms / top_n / 1000.0
+    bytes_, flops_ = algorithmic(top_name, ctx)
+    hbm_peak, peak_kind = peaks()
+    achieved = bytes_ / avg_s / 1e9
+    roofline = {"kernel": top_name, "bound": "hbm", "achieved": achieved, "peak": hbm_peak,
+                "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": None,
+                "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs, copy)",
+                "algorithmic_bytes_per_launch": bytes_, "avg_launch_us": avg_s * 1e6,
+                "share_of_kernel_time": top_ms / total_k}
+    kernels = {k: {"launches": v[0], "avg_us": 1000.0 * v[1] / v[0], "share": v[1] / total_k}
+               for k, v in sorted(kt.items(), key=lambda kv: -kv[1][1])}
+
+    # ---- end to end through the C-ABI with host buffers
+    host_in = torch.empty((NZ, NPHI, NR), dtype=torch.float32, pin_memory=True)
+    host_in.copy_(u0_32.cpu())
+    host_out = torch.empty_like(host_in).pin_memory()
+    dev_phys = ctx.new_phys()
+    s_e, a_e = ctx.new_spec(), ctx.new_spec()
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    dev_phys.copy_(host_in, non_blocking=True)
+    ctx.forward(dev_phys, s_e)
+    for i in range(args.steps):
+        ctx.advance(B.NONLIN_FKPP, [GAMMA], s_e, a_e, STEPS_PER_BENCH_STEP, i == 0)
+    ctx.backward(s_e, dev_phys)
+    host_out.copy_(dev_phys, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1)
+    tm = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(tm, op=dist.ReduceOp.MAX)
+    e2e_value = args.steps * STEPS_PER_BENCH_STEP * world / (float(tm.item()) / 1000.0)
+
+    if rank != 0:
+        return
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        v, threads, sec = oracle_sample(2)
+        cpu = {"value": v, "unit": "timesteps/s", "cores": threads, "kind": "oracle",
+               "sample": "2 full-size time steps of the same workload (Richardson start + 1 AB-CN), %.1f s" % sec}
+    line = {
+        "metric": METRIC, "value": value, "unit": "timesteps/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 transforms, f64 solve",
+        "data": "synthetic (seeded analytic initial condition, PCG64 seed 2)",
+        "config": {"workload": WORKLOAD, "nr": NR, "nphi": NPHI, "nz": NZ, "ell": ELL,
+                   "lz": LZ, "chop": "two-thirds (M=43, K=43)", "dt": DT,
+                   "timesteps_per_step": STEPS_PER_BENCH_STEP, "scheme": "AB-CN + Richardson start",
+                   "l2": "flushed (256 MB write) before every timed step; one time step's working set (~9 MB) stays L2-resident within a step",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "transform_pairs_per_s": pair_per_s,
+        "fp64_form": {"value": fp64_value, "unit": "timesteps/s", "speedup_mixed_vs_fp64": value / world / fp64_value},
+        "rel_err_fp32_vs_fp64_at_t10": rel_err,
+        "roofline": roofline,
+        "kernels": kernels,
+        "clocks": clk,
+        "e2e": {"value": e2e_value, "unit": "timesteps/s",
+                "h2d_bytes_per_step": int(NZ * NPHI * NR * 4 / args.steps),
+                "d2h_bytes_per_step": int(NZ * NPHI * NR * 4 / args.steps)},
+        "gpu_launches": gpu_launches,
+        "wall_s_timed": t_wall,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="mlx", choices=["mlx", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    try:
+        run_gpu(args, rank, world)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -158,6 +158,19 @@ int mlx_implicit_solve(mlx_ctx* ctx, int step, const void* s, const void* A,
 int mlx_advance(mlx_ctx* ctx, int kind, const double* coeffs, int ncoeffs,
                 void* state, void* prev_A, int nsteps, int start, mlx_stream stream);
 
+/* ---- measurement support (not part of the method) ----
+ * Opt-in per-launch timing: with enable != 0 every kernel launch of this context
+ * is bracketed by CUDA events recorded on its stream, and mlx_advance launches
+ * its steps directly instead of replaying a CUDA graph.  Enabling or disabling
+ * resets the counters.  mlx_timing_read synchronises on the recorded events and
+ * returns, for kernel id 0 <= kernel < mlx_kernel_count(), the number of timed
+ * launches and their summed device time in milliseconds.  mlx_kernel_name gives
+ * a stable short name per id ("" when out of range). */
+int mlx_timing(mlx_ctx* ctx, int enable);
+int mlx_timing_read(mlx_ctx* ctx, int kernel, long long* launches, double* total_ms);
+int mlx_kernel_count(void);
+const char* mlx_kernel_name(int kernel);
+
 #ifdef __cplusplus
 }
 #endif

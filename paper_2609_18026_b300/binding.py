@@ -21,7 +21,8 @@ STEP_FEBE_HALF, STEP_FEBE_FULL, STEP_ABCN = 0, 1, 2
 # Entry points declared in include/mlx.h (checked by the CPU test suite).
 EXPORTS = ("mlx_strerror", "mlx_last_cuda_error", "mlx_create", "mlx_destroy", "mlx_query",
            "mlx_get_nodes", "mlx_forward", "mlx_backward", "mlx_nonlinear",
-           "mlx_implicit_setup", "mlx_implicit_solve", "mlx_advance")
+           "mlx_implicit_setup", "mlx_implicit_solve", "mlx_advance",
+           "mlx_timing", "mlx_timing_read", "mlx_kernel_count", "mlx_kernel_name")
 
 
 class MlxError(RuntimeError):
@@ -71,10 +72,16 @@ def load():
     lib.mlx_implicit_setup.argtypes = [vp, d, d, i, d, vp]
     lib.mlx_implicit_solve.argtypes = [vp, i, vp, vp, vp, vp, vp]
     lib.mlx_advance.argtypes = [vp, i, ctypes.POINTER(d), i, vp, vp, i, i, vp]
+    lib.mlx_timing.argtypes = [vp, i]
+    lib.mlx_timing_read.argtypes = [vp, i, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(d)]
+    lib.mlx_kernel_count.argtypes = []
+    lib.mlx_kernel_name.argtypes = [i]
+    lib.mlx_kernel_name.restype = ctypes.c_char_p
     for name in EXPORTS:
         getattr(lib, name).restype = getattr(lib, name).restype or ctypes.c_int
     lib.mlx_strerror.restype = ctypes.c_char_p
     lib.mlx_last_cuda_error.restype = ctypes.c_char_p
+    lib.mlx_kernel_name.restype = ctypes.c_char_p
     _lib = lib
     return lib
 
@@ -177,6 +184,20 @@ class Context:
     def implicit_solve(self, step, s, A, A_prev, out, stream=None):
         self._check(self.lib.mlx_implicit_solve(self._h, step, _ptr(s), _ptr(A), _ptr(A_prev),
                                                 _ptr(out), _stream(stream)))
+        return out
+
+    def timing(self, enable):
+        self._check(self.lib.mlx_timing(self._h, int(bool(enable))))
+
+    def timing_read(self):
+        """{kernel name: (launches, total ms)} for kernels launched while timing was on."""
+        out = {}
+        for k in range(self.lib.mlx_kernel_count()):
+            n = ctypes.c_longlong()
+            ms = ctypes.c_double()
+            self._check(self.lib.mlx_timing_read(self._h, k, ctypes.byref(n), ctypes.byref(ms)))
+            if n.value:
+                out[self.lib.mlx_kernel_name(k).decode()] = (n.value, ms.value)
         return out
 
     def advance(self, kind, coeffs, state, prev_A, nsteps, start, stream=None):

@@ -25,6 +25,8 @@ void free_ctx(mlx_ctx* c) {
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  for (auto& p : c->timing.pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
+  for (auto e : c->timing.pool) cudaEventDestroy(e);
   delete c;
 }
 
@@ -277,7 +279,14 @@ int mlx_advance(mlx_ctx* c, int kind, const double* coeffs, int ncoeffs, void* s
     --nsteps;
   }
   const int pairs = nsteps / 2;
-  if (pairs > 0) {
+  if (pairs > 0 && c->timing.on) {
+    // instrumented mode: the same two-step sequence launched directly so that
+    // every kernel is bracketed by CUDA events
+    for (int i = 0; i < pairs; ++i) {
+      if ((rc = abcn_step(c, kind, c0, s, c->d_specA, Ap, c->d_spec1, st))) return rc;
+      if ((rc = abcn_step(c, kind, c0, c->d_spec1, Ap, c->d_specA, s, st))) return rc;
+    }
+  } else if (pairs > 0) {
     // two steps per graph: (s, A_prev) -> (spec1, specA) -> (s, A_prev), no copies
     mlx_ctx::GraphKey key{state, prev_A, kind, c0};
     auto it = c->graphs.find(key);
@@ -304,6 +313,42 @@ int mlx_advance(mlx_ctx* c, int kind, const double* coeffs, int ncoeffs, void* s
     MLX_CUDA_TRY(c, cudaMemcpyAsync(s, c->d_spec1, sizeof(double2) * c->n_spec, cudaMemcpyDeviceToDevice, st));
     MLX_CUDA_TRY(c, cudaMemcpyAsync(Ap, c->d_specA, sizeof(double2) * c->n_spec, cudaMemcpyDeviceToDevice, st));
   }
+  return MLX_OK;
+}
+
+static const char* kKernelNames[KID_COUNT] = {
+    "phi_analysis", "phi_synthesis", "phi_fkpp_fused", "z_forward", "z_inverse",
+    "legendre_forward", "legendre_backward", "band_solve", "spec_axpby"};
+
+int mlx_kernel_count(void) { return KID_COUNT; }
+
+const char* mlx_kernel_name(int kernel) {
+  return (kernel >= 0 && kernel < KID_COUNT) ? kKernelNames[kernel] : "";
+}
+
+int mlx_timing(mlx_ctx* c, int enable) {
+  if (!c) return MLX_EINVAL;
+  for (auto& p : c->timing.pending) { c->timing.pool.push_back(p.a); c->timing.pool.push_back(p.b); }
+  c->timing.pending.clear();
+  for (int k = 0; k < KID_COUNT; ++k) { c->timing.launches[k] = 0; c->timing.ms[k] = 0.0; }
+  c->timing.on = enable != 0;
+  return MLX_OK;
+}
+
+int mlx_timing_read(mlx_ctx* c, int kernel, long long* launches, double* total_ms) {
+  if (!c || kernel < 0 || kernel >= KID_COUNT) return MLX_EINVAL;
+  for (auto& p : c->timing.pending) {
+    MLX_CUDA_TRY(c, cudaEventSynchronize(p.b));
+    float ms = 0.f;
+    MLX_CUDA_TRY(c, cudaEventElapsedTime(&ms, p.a, p.b));
+    c->timing.launches[p.kid] += 1;
+    c->timing.ms[p.kid] += ms;
+    c->timing.pool.push_back(p.a);
+    c->timing.pool.push_back(p.b);
+  }
+  c->timing.pending.clear();
+  if (launches) *launches = c->timing.launches[kernel];
+  if (total_ms) *total_ms = c->timing.ms[kernel];
   return MLX_OK;
 }
 

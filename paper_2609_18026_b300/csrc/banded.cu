@@ -280,6 +280,7 @@ int mlx_band_setup(mlx_ctx* c, cudaStream_t st) {
 
 int mlx_band_solve(mlx_ctx* c, int step, const double2* s, const double2* A, const double2* Ap,
                    double2* out, cudaStream_t st) {
+  TimedLaunch tl(c, KID_BAND_SOLVE, st);
   const BandLU& f = (step == MLX_STEP_FEBE_FULL) ? c->lu_full : c->lu_half;
   const int nsys = c->M * c->K;
   const int tb = 64;
@@ -292,6 +293,7 @@ int mlx_band_solve(mlx_ctx* c, int step, const double2* s, const double2* A, con
 
 int mlx_spec_axpby(mlx_ctx* c, double a, const double2* x, double b, const double2* y,
                    double2* out, cudaStream_t st) {
+  TimedLaunch tl(c, KID_AXPBY, st);
   const long long n = c->n_spec;
   const int tb = 256;
   k_axpby<<<(unsigned)((n + tb - 1) / tb), tb, 0, st>>>(n, a, x, b, y, out);

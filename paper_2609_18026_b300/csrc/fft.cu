@@ -236,6 +236,7 @@ int phi_launch(mlx_ctx* c, int mode, T* phys, T* zbase, const void* tw, double g
   T* zre = zbase;
   T* zim = zbase + pl;
   const C* twp = reinterpret_cast<const C*>(tw);
+  TimedLaunch tl(c, mode == PHI_FWD ? KID_PHI_FWD : (mode == PHI_BWD ? KID_PHI_BWD : KID_PHI_FKPP), st);
   if (mode == PHI_FWD) {
     k_phi<T, PHI_FWD><<<grid, 256, smem, st>>>(c->nphi, c->M, c->nr, R, phys, zre, zim, twp, (T)gamma);
   } else if (mode == PHI_BWD) {
@@ -257,6 +258,7 @@ int z_launch(mlx_ctx* c, bool inverse, T* zbase, T* mbase, const void* tw, cudaS
   const long long plz = (long long)c->nz * c->M * c->nr;
   const long long plm = (long long)c->K * c->M * c->nr;
   const C* twp = reinterpret_cast<const C*>(tw);
+  TimedLaunch tl(c, inverse ? KID_Z_BWD : KID_Z_FWD, st);
   if (!inverse) {
     k_z<T, false><<<grid, 256, smem, st>>>(c->nz, c->Kz, c->K, c->M, c->nr, R, zbase, zbase + plz,
                                            mbase, mbase + plm, twp);

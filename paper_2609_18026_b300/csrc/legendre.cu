@@ -107,6 +107,7 @@ __global__ void __launch_bounds__(NT) k_legendre(const LegTile* __restrict__ til
 }  // namespace
 
 int mlx_legendre_forward(mlx_ctx* c, double2* spec, cudaStream_t st) {
+  TimedLaunch tl(c, KID_LEG_FWD, st);
   if (c->precision == MLX_FP64)
     k_legendre<double, true><<<c->ntiles_fwd, NT, 0, st>>>(c->d_tiles_fwd, c->nc, c->nr, c->M, c->K,
                                                           c->d_boff, c->d_soff, c->d_W64,
@@ -120,6 +121,7 @@ int mlx_legendre_forward(mlx_ctx* c, double2* spec, cudaStream_t st) {
 }
 
 int mlx_legendre_backward(mlx_ctx* c, const double2* spec, cudaStream_t st) {
+  TimedLaunch tl(c, KID_LEG_BWD, st);
   if (c->precision == MLX_FP64)
     k_legendre<double, false><<<c->ntiles_bwd, NT, 0, st>>>(c->d_tiles_bwd, c->nc, c->nr, c->M, c->K,
                                                            c->d_boff, c->d_soff, c->d_P64,

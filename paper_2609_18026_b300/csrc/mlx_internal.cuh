@@ -21,6 +21,21 @@
 
 #define MLX_LAUNCH_CHECK(ctx) MLX_CUDA_TRY(ctx, cudaGetLastError())
 
+// Kernel identifiers for the opt-in per-launch CUDA-event timing.
+enum KernelId {
+  KID_PHI_FWD = 0, KID_PHI_BWD, KID_PHI_FKPP, KID_Z_FWD, KID_Z_BWD,
+  KID_LEG_FWD, KID_LEG_BWD, KID_BAND_SOLVE, KID_AXPBY, KID_COUNT
+};
+
+struct TimingState {
+  bool on = false;
+  long long launches[KID_COUNT] = {0};
+  double ms[KID_COUNT] = {0};
+  std::vector<cudaEvent_t> pool;
+  struct Pending { int kid; cudaEvent_t a, b; };
+  std::vector<Pending> pending;
+};
+
 // One GEMM work tile of the ragged per-m Legendre contraction.
 struct LegTile {
   int m;     // azimuthal order
@@ -107,7 +122,26 @@ struct mlx_ctx {
   std::map<GraphKey, cudaGraphExec_t> graphs;
   cudaStream_t cap_stream = nullptr;
 
+  TimingState timing;
   std::string last_err;
+};
+
+// RAII bracket: with timing on, records CUDA events around one kernel launch on
+// its stream (the events are resolved by mlx_timing_read).
+struct TimedLaunch {
+  mlx_ctx* c; int kid; cudaStream_t st; cudaEvent_t a = nullptr, b = nullptr;
+  static cudaEvent_t get(mlx_ctx* c) {
+    if (!c->timing.pool.empty()) { cudaEvent_t e = c->timing.pool.back(); c->timing.pool.pop_back(); return e; }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+  }
+  TimedLaunch(mlx_ctx* c_, int kid_, cudaStream_t st_) : c(c_), kid(kid_), st(st_) {
+    if (c->timing.on) { a = get(c); b = get(c); cudaEventRecord(a, st); }
+  }
+  ~TimedLaunch() {
+    if (a) { cudaEventRecord(b, st); c->timing.pending.push_back({kid, a, b}); }
+  }
 };
 
 static inline size_t elem_size(int precision) { return precision == MLX_FP64 ? 8 : 4; }

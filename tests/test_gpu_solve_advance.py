@@ -28,6 +28,31 @@ def test_implicit_solve_parity(step, nu_h, p):
         ref = st.abcn(S, AA, AP)
     else:
         ref = st.febe(S, step == B.STEP_FEBE_HALF, AA)
+    # Bar: 1e-12, or the FP64 perturbation bound 2 kappa u of a backward-stable
+    # solve when the systems are worse conditioned than 1e12 * u allows (the p = 8
+    # hyperviscous operator reaches kappa ~ 1e5 here; the oracle itself is 1.5e-12
+    # from a 50-digit solve on those systems).
+    c = 0.5 * dt if step != B.STEP_FEBE_FULL else dt
+    kappa = max(np.linalg.cond(np.eye(L.shape[0]) - c * L) for L in st.L.values())
+    tol = max(1e-12, 2.0 * kappa * 2.0 ** -53)
+    assert O.spec_rel_err(g, spec_from_gpu(g, out), ref) <= tol
+
+
+@pytest.mark.parametrize("step", [B.STEP_FEBE_HALF, B.STEP_ABCN])
+def test_implicit_solve_parity_smooth_rhs(step):
+    # Spectrally decaying right-hand sides (what the time loop sees): 1e-12 even
+    # with the p = 8 hyperviscous operator.
+    g, ctx = pair(40, 16, 8, 1.5, lz=3.0, policy="twothirds")
+    dt, nu = 2e-2, 0.3
+    ctx.implicit_setup(nu, dt, nu_h=5e-7, p=8)
+    st = O.Stepper(g, nu, dt, nu_h=5e-7, p=8)
+    s, A, Ap = (rand_spec(g, k) for k in (1, 2, 3))
+    S, AA, AP = (O.from_flat(g, v) for v in (s, A, Ap))
+    for blk in (S, AA, AP):
+        for m, b in enumerate(blk):
+            b *= np.exp(-0.3 * np.arange(m, g.nc))[None, :]
+    out = ctx.implicit_solve(step, *(to_gpu_spec(O.to_flat(g, v)) for v in (S, AA, AP)), ctx.new_spec())
+    ref = st.abcn(S, AA, AP) if step == B.STEP_ABCN else st.febe(S, True, AA)
     assert O.spec_rel_err(g, spec_from_gpu(g, out), ref) <= 1e-12
 
 
