@@ -73,7 +73,7 @@ enum { MLX_STEP_FEBE_HALF = 0, MLX_STEP_FEBE_FULL = 1, MLX_STEP_ABCN = 2 };
 
 typedef struct {
   int nr, nphi, nz;          /* collocation counts: 2 <= Nr <= 1024; Nphi a power of
-                                two in [4, 1024]; Nz 1 or a power of two <= 1024     */
+                                two in [4, 512]; Nz 1 or a power of two <= 512       */
   int nr_c, nphi_c, nz_c;    /* chops Nc, M, Kz (0 = from chop_policy); bounds of
                                 Sec. 3.1: Nc <= Nr, M <= Nphi/2, Kz <= Nz/2 (1 if Nz=1),
                                 and M <= Nc                                           */
@@ -157,6 +157,15 @@ int mlx_implicit_solve(mlx_ctx* ctx, int step, const void* s, const void* A,
  * replayed; the graph is launched on `stream`. */
 int mlx_advance(mlx_ctx* ctx, int kind, const double* coeffs, int ncoeffs,
                 void* state, void* prev_A, int nsteps, int start, mlx_stream stream);
+
+/* Launch-shape tuning (not part of the method).  Keys:
+ *   "solve_cpw": real chains per warp of the banded solve, 4, 8, 16 or 32
+ *                (default 8);
+ *   "solve_wpb": warps per CTA of the banded solve, 1, 2 or 4 (default 4).
+ *   The substitution is a sequential FP64 recurrence per real chain; the best
+ *   shape trades per-warp staging latency against FP64 pipe sharing.
+ * Invalidates cached graphs.  MLX_EINVAL for an unknown key or value. */
+int mlx_set_tuning(mlx_ctx* ctx, const char* key, int value);
 
 /* ---- measurement support (not part of the method) ----
  * Opt-in per-launch timing: with enable != 0 every kernel launch of this context

@@ -22,7 +22,8 @@ STEP_FEBE_HALF, STEP_FEBE_FULL, STEP_ABCN = 0, 1, 2
 EXPORTS = ("mlx_strerror", "mlx_last_cuda_error", "mlx_create", "mlx_destroy", "mlx_query",
            "mlx_get_nodes", "mlx_forward", "mlx_backward", "mlx_nonlinear",
            "mlx_implicit_setup", "mlx_implicit_solve", "mlx_advance",
-           "mlx_timing", "mlx_timing_read", "mlx_kernel_count", "mlx_kernel_name")
+           "mlx_timing", "mlx_timing_read", "mlx_kernel_count", "mlx_kernel_name",
+           "mlx_set_tuning")
 
 
 class MlxError(RuntimeError):
@@ -75,6 +76,7 @@ def load():
     lib.mlx_timing.argtypes = [vp, i]
     lib.mlx_timing_read.argtypes = [vp, i, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(d)]
     lib.mlx_kernel_count.argtypes = []
+    lib.mlx_set_tuning.argtypes = [vp, ctypes.c_char_p, i]
     lib.mlx_kernel_name.argtypes = [i]
     lib.mlx_kernel_name.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -185,6 +187,9 @@ class Context:
         self._check(self.lib.mlx_implicit_solve(self._h, step, _ptr(s), _ptr(A), _ptr(A_prev),
                                                 _ptr(out), _stream(stream)))
         return out
+
+    def set_tuning(self, key, value):
+        self._check(self.lib.mlx_set_tuning(self._h, key.encode(), int(value)))
 
     def timing(self, enable):
         self._check(self.lib.mlx_timing(self._h, int(bool(enable))))

@@ -6,6 +6,7 @@
 
 int mlx_legendre_tiles(mlx_ctx* c, std::vector<LegTile>& fwd, std::vector<LegTile>& bwd);
 int mlx_fft_prepare(mlx_ctx* c);
+int mlx_band_prepare(mlx_ctx* c);
 
 namespace {
 
@@ -40,8 +41,8 @@ int dalloc(mlx_ctx* c, P** p, size_t bytes) {
   return MLX_OK;
 }
 
-// One AB-CN step: A^j = A(s) into Anew, then (I - dt/2 L) out = (I + dt/2 L) s
-// + dt/2 (3 A^j - A^{j-1}).
+// Nonlinear term A(s) into A.  Fisher-KPP: A = P[gamma u (1 - u)] with u = B s
+// (B backward, P forward transform), the product formed at the nodes (Sec. 3.3).
 int nonlinear_into(mlx_ctx* c, int kind, double c0, const double2* s, double2* A, cudaStream_t st) {
   if (kind == MLX_NONLIN_NONE) {
     MLX_CUDA_TRY(c, cudaMemsetAsync(A, 0, sizeof(double2) * c->n_spec, st));
@@ -53,6 +54,9 @@ int nonlinear_into(mlx_ctx* c, int kind, double c0, const double2* s, double2* A
   if (rc) return rc;
   return mlx_legendre_forward(c, A, st);
 }
+
+// One AB-CN step: A^j = A(s) into Anew, then (I - dt/2 L) out = (I + dt/2 L) s
+// + dt/2 (3 A^j - A^{j-1}).
 
 int abcn_step(mlx_ctx* c, int kind, double c0, const double2* s, double2* Anew,
               const double2* Aprev, double2* out, cudaStream_t st) {
@@ -85,8 +89,8 @@ int mlx_create(const mlx_params* p, mlx_stream stream, mlx_ctx** out) {
   *out = nullptr;
   if (!p) return MLX_EINVAL;
   if (p->nr < 2 || p->nr > 1024) return MLX_EINVAL;
-  if (!is_pow2(p->nphi) || p->nphi < 4 || p->nphi > 1024) return MLX_EINVAL;
-  if (!(p->nz == 1 || (is_pow2(p->nz) && p->nz <= 1024))) return MLX_EINVAL;
+  if (!is_pow2(p->nphi) || p->nphi < 4 || p->nphi > 512) return MLX_EINVAL;
+  if (!(p->nz == 1 || (is_pow2(p->nz) && p->nz <= 512))) return MLX_EINVAL;
   if (!(p->ell > 0.0) || !(p->lz > 0.0)) return MLX_EINVAL;
   if (p->precision != MLX_FP64 && p->precision != MLX_FP32) return MLX_EINVAL;
   if (p->chop_policy != MLX_CHOP_LINEAR && p->chop_policy != MLX_CHOP_TWOTHIRDS) return MLX_EINVAL;
@@ -170,6 +174,7 @@ int mlx_create(const mlx_params* p, mlx_stream stream, mlx_ctx** out) {
   TRY(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
 #undef TRY
   rc = mlx_fft_prepare(c);
+  if (!rc) rc = mlx_band_prepare(c);
   if (!rc) rc = mlx_basis_build(c, st);
   if (!rc) {
     cudaError_t e = cudaStreamSynchronize(st);
@@ -314,6 +319,25 @@ int mlx_advance(mlx_ctx* c, int kind, const double* coeffs, int ncoeffs, void* s
     MLX_CUDA_TRY(c, cudaMemcpyAsync(Ap, c->d_specA, sizeof(double2) * c->n_spec, cudaMemcpyDeviceToDevice, st));
   }
   return MLX_OK;
+}
+
+int mlx_set_tuning(mlx_ctx* c, const char* key, int value) {
+  if (!c || !key) return MLX_EINVAL;
+  if (strcmp(key, "solve_cpw") == 0) {
+    if (value != 4 && value != 8 && value != 16 && value != 32) return MLX_EINVAL;
+    c->solve_cpw = value;
+    for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
+    c->graphs.clear();
+    return MLX_OK;
+  }
+  if (strcmp(key, "solve_wpb") == 0) {
+    if (value != 1 && value != 2 && value != 4) return MLX_EINVAL;
+    c->solve_wpb = value;
+    for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
+    c->graphs.clear();
+    return MLX_OK;
+  }
+  return MLX_EINVAL;
 }
 
 static const char* kKernelNames[KID_COUNT] = {

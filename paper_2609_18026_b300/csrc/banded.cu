@@ -8,23 +8,36 @@
 // the wavenumbers k and -k.
 //
 // Storage per (m, |k|) system of size N = Nc - m, rows i = 0..N-1:
-//   Bplus [N][2kl+1]  band of I + dt/2 L (column i + o at slot o + kl)
+//   Bplus [N][2kl+1]  band of I + dt/2 L (column i + o at slot o + kl), kept
+//                     for reference and tests; the solve does not read it
 //   LU of I - c L, c = dt/2 (half) and dt (full), partial pivoting over the kl
-//   rows below the diagonal: U row i holds columns i..i+2kl (slot t = column - i),
-//   L multipliers [N][kl], pivot rows, and 1/U[i][i].
-// One thread per system factorises; one thread per (m, k) solves (the complex
-// right-hand side as two real ones sharing the real factors).
+//   rows below the diagonal: U row i holds U_ii then columns i+1..i+2kl divided
+//   by U_ii (slot t = column - i), L multipliers [N][kl], pivot rows, 1/U_ii.
+// One thread per system factorises.  The solve is described at k_band_solve.
 #include "mlx_internal.cuh"
 
 namespace {
 
-// rows of (m, kabs) start at band_off[m] + kabs * (Nc - m)
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// Factor rows of one m are interleaved by |k|: row (m, i, kabs) has index
+// band_off[m] + i * Kz + kabs, so the threads of a warp (consecutive k) read
+// neighbouring rows.
 __device__ __forceinline__ void sys_of(int idx, int M, int nc, int Kz, const long long* band_off,
                                        int& m, int& kabs, long long& row0) {
   // idx enumerates (m, kabs) m-major
   m = idx / Kz;
   kabs = idx % Kz;
-  row0 = band_off[m] + (long long)kabs * (nc - m);
+  row0 = band_off[m] + kabs;
 }
 
 // Build the band of L (half width kl) for system (m, kabs) into Lb[N][2kl+1]
@@ -75,9 +88,10 @@ __device__ void build_L(int m, int N, double kappa2, double nu, double nu_h, int
 }
 
 // Banded LU with partial pivoting of A = I - c L.  work: [N][3kl+1] row windows
-// (column j of row i at slot j - i + kl).
+// (column j of row i at slot j - i + kl).  Factor row i is stored at row index
+// i * rs of U / Lm / piv / invd (rs = Kz: systems of one m are interleaved by |k|).
 __device__ void band_lu(int N, int kl, double c, const double* Lb, double* work, double* U,
-                        double* Lm, int* piv, double* invd) {
+                        double* Lm, int* piv, double* invd, int rs) {
   const int W = 2 * kl + 1;     // band of L
   const int WW = 3 * kl + 1;    // window: columns i-kl .. i+2kl
   for (long long t = 0; t < (long long)N * WW; ++t) work[t] = 0.0;
@@ -97,7 +111,7 @@ __device__ void band_lu(int N, int kl, double c, const double* Lb, double* work,
       const double v = fabs(work[i * WW + (j - i) + kl]);
       if (v > best) { best = v; pr = i; }
     }
-    piv[j] = pr;
+    piv[(long long)j * rs] = pr;
     const int cend = min(N - 1, j + 2 * kl);
     if (pr != j) {
       for (int cc = j; cc <= cend; ++cc) {
@@ -110,18 +124,23 @@ __device__ void band_lu(int N, int kl, double c, const double* Lb, double* work,
     const double inv = 1.0 / d;
     for (int i = j + 1; i <= last; ++i) {
       const double l = work[i * WW + (j - i) + kl] * inv;
-      Lm[j * kl + (i - j - 1)] = l;
+      Lm[(long long)j * rs * kl + (i - j - 1)] = l;
       work[i * WW + (j - i) + kl] = 0.0;
       for (int cc = j + 1; cc <= cend; ++cc) work[i * WW + (cc - i) + kl] -= l * work[j * WW + (cc - j) + kl];
     }
-    for (int i = last + 1; i <= j + kl; ++i) Lm[j * kl + (i - j - 1)] = 0.0;
+    for (int i = last + 1; i <= j + kl; ++i) Lm[(long long)j * rs * kl + (i - j - 1)] = 0.0;
   }
+  // U row i is stored as (U_ii, U_i,i+1 / U_ii, ..., U_i,i+2kl / U_ii) so that the
+  // back substitution is x_i = y_i / U_ii - sum_t (U_i,i+t / U_ii) x_{i+t}
   for (int i = 0; i < N; ++i) {
-    for (int t = 0; t <= 2 * kl; ++t) {
+    double* Ui = U + (long long)i * rs * (2 * kl + 1);
+    const double dinv = 1.0 / work[i * WW + kl];
+    Ui[0] = work[i * WW + kl];
+    for (int t = 1; t <= 2 * kl; ++t) {
       const int cc = i + t;
-      U[i * (2 * kl + 1) + t] = (cc < N) ? work[i * WW + t + kl] : 0.0;
+      Ui[t] = (cc < N) ? work[i * WW + t + kl] * dinv : 0.0;
     }
-    invd[i] = 1.0 / U[i * (2 * kl + 1)];
+    invd[(long long)i * rs] = dinv;
   }
 }
 
@@ -149,80 +168,156 @@ __global__ void k_band_setup(int M, int nc, int Kz, double lz, const long long* 
     for (int o = 0; o < W; ++o) {
       double v = 0.5 * dt * Lb[i * W + o];
       if (o == kl) v += 1.0;
-      Bplus[(row0 + i) * W + o] = v;
+      Bplus[(row0 + (long long)i * Kz) * W + o] = v;
     }
-  band_lu(N, kl, 0.5 * dt, Lb, work, Uh + row0 * W, Lh + row0 * kl, Ph + row0, Dh + row0);
-  band_lu(N, kl, dt, Lb, work, Uf + row0 * W, Lf + row0 * kl, Pf + row0, Df + row0);
+  band_lu(N, kl, 0.5 * dt, Lb, work, Uh + row0 * W, Lh + row0 * kl, Ph + row0, Dh + row0, Kz);
+  band_lu(N, kl, dt, Lb, work, Uf + row0 * W, Lf + row0 * kl, Pf + row0, Df + row0, Kz);
 }
 
-// One thread per (m, kidx): RHS assembly then forward / back substitution in out.
-__global__ void k_band_solve(int M, int nc, int Kz, int K, int kl, int step, double dt,
-                             const long long* __restrict__ soff, const long long* __restrict__ band_off,
-                             const double* __restrict__ Bplus,
-                             const double* __restrict__ U, const double* __restrict__ Lm,
-                             const int* __restrict__ piv, const double* __restrict__ invd,
-                             const double2* __restrict__ s, const double2* __restrict__ A,
-                             const double2* __restrict__ Ap, double2* __restrict__ out) {
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= M * K) return;
-  const int m = idx / K, kidx = idx % K;
-  const int kabs = kidx < Kz ? kidx : K - kidx;
+// Solve kernel.  The substitution is a sequential recurrence in the row index, and
+// on this GPU FP64 throughput per SM sub-partition is the limit, so the work is
+// spread as widely as possible: every real chain (one of Re / Im of one system)
+// is one lane, a warp owns CPW chains = CPW/4 values of |k| for one m (the four
+// chains +|k| Re/Im, -|k| Re/Im share one set of real factors), and each warp
+// stages its factors and right-hand sides in its own shared-memory slab, so warps
+// never wait on one another.  For AB-CN the right-hand side uses the identity
+//   (I - c L)^{-1} ((I + c L) s + r) = (I - c L)^{-1} (2 s + r) - s,   c = dt/2,
+// which needs no band product: rhs = 2 s + dt/2 (3 A - A_prev), and s is
+// subtracted after the back substitution.
+template <int KL>
+struct SolveSmem {
+  static constexpr int W = 2 * KL + 1;
+  // per |k| and row: U (W), L (KL), 1/diag (1) doubles + pivot row (int)
+  __host__ __device__ static size_t per_warp(int nc, int CPW) {
+    const int G = CPW / 4;
+    const size_t b = (size_t)nc * G * (W + KL + 1) * sizeof(double) +
+                     (size_t)nc * CPW * sizeof(double) + (size_t)nc * G * sizeof(int);
+    return (b + 15) / 16 * 16;   // keeps every warp's slab 16-byte aligned
+  }
+};
+
+template <int KL>
+__global__ void k_band_solve(int M, int nc, int Kz, int K, int CPW, int groups_per_m, int step,
+                             double dt, const long long* __restrict__ soff,
+                             const long long* __restrict__ band_off, const double* __restrict__ U,
+                             const double* __restrict__ Lm, const int* __restrict__ piv,
+                             const double* __restrict__ invd, const double* __restrict__ s,
+                             const double* __restrict__ A, const double* __restrict__ Ap,
+                             double* __restrict__ out) {
+  constexpr int W = 2 * KL + 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int gw = blockIdx.x * (blockDim.x >> 5) + wib;   // global warp = (m, group)
+  if (gw >= M * groups_per_m) return;
+  const int m = gw / groups_per_m;
+  const int G = CPW / 4;
+  const int k0 = (gw % groups_per_m) * G;
+  const int gcnt = min(G, Kz - k0);
   const int N = nc - m;
-  const long long row0 = band_off[m] + (long long)kabs * N;
-  const long long so = soff[m] + (long long)kidx * N;
-  const int W = 2 * kl + 1;
-  const double2* sv = s + so;
-  double2* o = out + so;
-  // right-hand side
-  for (int i = 0; i < N; ++i) {
-    double2 r;
+  unsigned char* base = smem_raw + (size_t)wib * SolveSmem<KL>::per_warp(nc, CPW);
+  double* Us = reinterpret_cast<double*>(base);              // [N][G][W]
+  double* Ls = Us + (size_t)N * G * W;                       // [N][G][KL]
+  double* Ds = Ls + (size_t)N * G * KL;                      // [N][G]
+  double* Y = Ds + (size_t)N * G;                            // [N][CPW]
+  int* Pi = reinterpret_cast<int*>(Y + (size_t)N * CPW);     // [N][G] pivot rows
+  const long long fb = band_off[m];
+  const long long sm = soff[m];
+
+  // stage factors with asynchronous copies (every lane keeps many in flight)
+  for (int e = lane; e < N * gcnt * W; e += 32) {
+    const int i = e / (gcnt * W), rem = e - i * gcnt * W;
+    const int kk = rem / W, q = rem - kk * W;
+    const long long row = fb + (long long)i * Kz + k0 + kk;
+    cp_async8(Us + ((size_t)i * G + kk) * W + q, U + row * W + q);
+  }
+  for (int e = lane; e < N * gcnt * KL; e += 32) {
+    const int i = e / (gcnt * KL), rem = e - i * gcnt * KL;
+    const int kk = rem / KL, q = rem - kk * KL;
+    const long long row = fb + (long long)i * Kz + k0 + kk;
+    cp_async8(Ls + ((size_t)i * G + kk) * KL + q, Lm + row * KL + q);
+  }
+  for (int e = lane; e < N * gcnt; e += 32) {
+    const int i = e / gcnt, kk = e - i * gcnt;
+    const long long row = fb + (long long)i * Kz + k0 + kk;
+    cp_async8(Ds + (size_t)i * G + kk, invd + row);
+    cp_async4(Pi + (size_t)i * G + kk, piv + row);
+  }
+  cp_async_commit();
+  // stage right-hand sides; chain c = kk * 4 + sgn * 2 + part
+  const double h = (step == MLX_STEP_FEBE_FULL) ? dt : 0.5 * dt;
+#pragma unroll 4
+  for (int e = lane; e < N * 4 * gcnt; e += 32) {
+    const int c = e / N, i = e - c * N;
+    const int kk = c >> 2, sgn = (c >> 1) & 1, part = c & 1;
+    const int kabs = k0 + kk;
+    if (sgn && kabs == 0) continue;
+    const int kidx = sgn ? K - kabs : kabs;
+    const long long o = 2 * (sm + (long long)kidx * N + i) + part;
+    double r;
     if (step == MLX_STEP_ABCN) {
-      r.x = 0.0; r.y = 0.0;
-      const double* bp = Bplus + (row0 + i) * W;
-      for (int t = -kl; t <= kl; ++t) {
-        const int j = i + t;
-        if (j < 0 || j >= N) continue;
-        const double b = bp[t + kl];
-        const double2 v = sv[j];
-        r.x += b * v.x;
-        r.y += b * v.y;
-      }
-      if (A) { const double2 a = A[so + i]; r.x += 1.5 * dt * a.x; r.y += 1.5 * dt * a.y; }
-      if (Ap) { const double2 a = Ap[so + i]; r.x -= 0.5 * dt * a.x; r.y -= 0.5 * dt * a.y; }
+      r = 2.0 * s[o];
+      if (A) r += 1.5 * dt * A[o];
+      if (Ap) r -= 0.5 * dt * Ap[o];
     } else {
-      const double h = (step == MLX_STEP_FEBE_HALF) ? 0.5 * dt : dt;
-      r = sv[i];
-      if (A) { const double2 a = A[so + i]; r.x += h * a.x; r.y += h * a.y; }
+      r = s[o];
+      if (A) r += h * A[o];
     }
-    o[i] = r;
+    Y[(size_t)i * CPW + c] = r;
   }
-  // forward elimination with the recorded row interchanges
-  for (int j = 0; j < N; ++j) {
-    const int pr = piv[row0 + j];
-    double2 vj = o[j];
-    if (pr != j) { const double2 t = o[pr]; o[pr] = vj; vj = t; o[j] = vj; }
-    const double* l = Lm + (row0 + j) * kl;
-    for (int t = 1; t <= kl && j + t < N; ++t) {
-      const double lv = l[t - 1];
-      double2 w = o[j + t];
-      w.x -= lv * vj.x;
-      w.y -= lv * vj.y;
-      o[j + t] = w;
+  cp_async_wait_all();
+  __syncwarp();
+
+  const int c = lane;
+  const int kk = c >> 2, sgn = (c >> 1) & 1, part = c & 1;
+  const bool valid = c < 4 * gcnt && !(sgn && k0 + kk == 0);
+  if (c < 4 * gcnt) {
+    double* y = Y + c;
+    // forward elimination, rows j..j+KL of the chain in registers
+    double w[KL + 1];
+#pragma unroll
+    for (int q = 0; q < KL; ++q) w[q + 1] = (q < N) ? y[(size_t)q * CPW] : 0.0;
+#pragma unroll 2
+    for (int j = 0; j < N; ++j) {
+#pragma unroll
+      for (int q = 0; q < KL; ++q) w[q] = w[q + 1];
+      w[KL] = (j + KL < N) ? y[(size_t)(j + KL) * CPW] : 0.0;
+      const int d = Pi[(size_t)j * G + kk] - j;
+#pragma unroll
+      for (int q = 1; q <= KL; ++q)
+        if (q == d) { const double t = w[0]; w[0] = w[q]; w[q] = t; }
+      y[(size_t)j * CPW] = w[0];
+      const double* l = Ls + ((size_t)j * G + kk) * KL;
+#pragma unroll
+      for (int q = 1; q <= KL; ++q) w[q] -= l[q - 1] * w[0];
+    }
+    // back substitution; known terms first, x_{i+1} last
+    double x[2 * KL + 1];
+#pragma unroll
+    for (int q = 0; q <= 2 * KL; ++q) x[q] = 0.0;
+#pragma unroll 2
+    for (int i = N - 1; i >= 0; --i) {
+      const double* u = Us + ((size_t)i * G + kk) * W;
+      double acc = y[(size_t)i * CPW] * Ds[(size_t)i * G + kk];
+#pragma unroll
+      for (int q = 2 * KL; q >= 1; --q) acc -= u[q] * x[q];
+      y[(size_t)i * CPW] = acc;
+#pragma unroll
+      for (int q = 2 * KL; q >= 2; --q) x[q] = x[q - 1];
+      x[1] = acc;
     }
   }
-  // back substitution
-  for (int i = N - 1; i >= 0; --i) {
-    const double* u = U + (row0 + i) * W;
-    double2 acc = o[i];
-    for (int t = 1; t <= 2 * kl && i + t < N; ++t) {
-      const double2 x = o[i + t];
-      acc.x -= u[t] * x.x;
-      acc.y -= u[t] * x.y;
-    }
-    const double d = invd[row0 + i];
-    acc.x *= d;
-    acc.y *= d;
-    o[i] = acc;
+  __syncwarp();
+  (void)valid;
+  for (int e = lane; e < N * 4 * gcnt; e += 32) {
+    const int cc = e / N, i = e - cc * N;
+    const int kq = cc >> 2, sg = (cc >> 1) & 1, pt = cc & 1;
+    const int kabs = k0 + kq;
+    if (sg && kabs == 0) continue;
+    const int kidx = sg ? K - kabs : kabs;
+    const long long o = 2 * (sm + (long long)kidx * N + i) + pt;
+    double v = Y[(size_t)i * CPW + cc];
+    if (step == MLX_STEP_ABCN) v -= s[o];
+    out[o] = v;
   }
 }
 
@@ -278,16 +373,49 @@ int mlx_band_setup(mlx_ctx* c, cudaStream_t st) {
   return MLX_OK;
 }
 
+template <int KL>
+static int launch_solve(mlx_ctx* c, int step, const BandLU& f, const double2* s, const double2* A,
+                        const double2* Ap, double2* out, cudaStream_t st) {
+  // Chains per warp and warps per CTA are launch-shape parameters (measured best
+  // at the 128x128x64 workload: 8 chains per warp, 1-4 warps per CTA).
+  int CPW = c->solve_cpw;
+  while (CPW > 4 && SolveSmem<KL>::per_warp(c->nc, CPW) > 200 * 1024) CPW /= 2;
+  const size_t pw = SolveSmem<KL>::per_warp(c->nc, CPW);
+  int WPB = c->solve_wpb;
+  while (WPB > 1 && pw * WPB > 200 * 1024) WPB /= 2;
+  if (pw * WPB > 200 * 1024) return MLX_EINVAL;
+  const int gpm = (c->Kz + CPW / 4 - 1) / (CPW / 4);
+  const int warps = c->M * gpm;
+  const int blocks = (warps + WPB - 1) / WPB;
+  k_band_solve<KL><<<blocks, 32 * WPB, pw * WPB, st>>>(
+      c->M, c->nc, c->Kz, c->K, CPW, gpm, step, c->dt, c->d_soff, c->d_band_off, f.U, f.L, f.piv,
+      f.invd, (const double*)s, (const double*)A, (const double*)Ap, (double*)out);
+  return MLX_OK;
+}
+
 int mlx_band_solve(mlx_ctx* c, int step, const double2* s, const double2* A, const double2* Ap,
                    double2* out, cudaStream_t st) {
   TimedLaunch tl(c, KID_BAND_SOLVE, st);
   const BandLU& f = (step == MLX_STEP_FEBE_FULL) ? c->lu_full : c->lu_half;
-  const int nsys = c->M * c->K;
-  const int tb = 64;
-  k_band_solve<<<(nsys + tb - 1) / tb, tb, 0, st>>>(c->M, c->nc, c->Kz, c->K, c->kl, step, c->dt,
-                                                    c->d_soff, c->d_band_off, c->d_Bplus, f.U, f.L,
-                                                    f.piv, f.invd, s, A, Ap, out);
+  int rc;
+  switch (c->kl) {
+    case 2: rc = launch_solve<2>(c, step, f, s, A, Ap, out, st); break;
+    case 4: rc = launch_solve<4>(c, step, f, s, A, Ap, out, st); break;
+    case 6: rc = launch_solve<6>(c, step, f, s, A, Ap, out, st); break;
+    case 8: rc = launch_solve<8>(c, step, f, s, A, Ap, out, st); break;
+    default: return MLX_EINVAL;
+  }
+  if (rc) return rc;
   MLX_LAUNCH_CHECK(c);
+  return MLX_OK;
+}
+
+int mlx_band_prepare(mlx_ctx* c) {
+  const int lim = 200 * 1024;
+  MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_band_solve<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+  MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_band_solve<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+  MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_band_solve<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+  MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_band_solve<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
   return MLX_OK;
 }
 

@@ -1,14 +1,21 @@
 // K2/K3: azimuthal (real) and axial (complex) Fourier transforms of the
-// transform pair (Eq. (2)), as batched shared-memory FFTs.
+// transform pair (Eq. (2)), as batched warp-shuffle FFTs.
 //
-// Layouts (planar complex, r fastest so that a warp reads consecutive radii):
+// Global layouts (planar complex, r fastest so that a warp reads consecutive radii):
 //   physical  [Nz][Nphi][Nr] real
 //   zm        [2][Nz][M][Nr]      after the phi transform (Re plane, Im plane)
 //   mixed     [2][K][M][Nr]       after the z transform; for Nz == 1 zm == mixed
 // A CTA of the phi kernel owns one z-plane and a tile of R radii; two real radial
 // lines (r and r + R/2) are packed into one complex line of length Nphi.  A CTA of
-// the z kernel owns one m and a tile of radii.  Transforms are radix-2 Stockham
-// passes over smem buffers laid out [point][line] (line fastest).
+// the z kernel owns one m and a tile of R radii (one complex line per radius).
+// Tiles are staged through shared memory as [line][point] rows of stride N + 1
+// (coalesced global access along r; conflict-free per-line reads).  Each line is
+// transformed by one warp (or a group of N lanes when N < 32): lane l holds
+// points l + 32 e, e < E = N/32, in registers; butterflies at distance >= 32 are
+// in-lane, below 32 they use __shfl_xor_sync.  DIF (natural in, bit-reversed
+// out) and DIT (bit-reversed in, natural out) radix-2 stages; the fused Fisher-KPP
+// kernel runs inverse DIF -> gamma u (1 - u) -> forward DIT without leaving
+// registers.
 #include "mlx_internal.cuh"
 
 namespace {
@@ -22,50 +29,108 @@ template <typename C> __device__ __forceinline__ C csub(C a, C b) { C r; r.x = a
 template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
   C r; r.x = a.x * b.x - a.y * b.y; r.y = a.x * b.y + a.y * b.x; return r;
 }
+template <typename C> __device__ __forceinline__ C shfl_xor(C v, int d) {
+  C r;
+  r.x = __shfl_xor_sync(0xffffffffu, v.x, d);
+  r.y = __shfl_xor_sync(0xffffffffu, v.y, d);
+  return r;
+}
+// twiddle exp(-+ 2 pi i t / N) from the table exp(-2 pi i t / N), t < N/2
+template <typename C> __device__ __forceinline__ C twid(const C* __restrict__ tw, int t, bool inv) {
+  C w = tw[t];
+  if (inv) w.y = -w.y;
+  return w;
+}
 
-// Radix-2 Stockham FFT of B lines of length N held at x[pos * B + line].
-// tw[t] = exp(-2 pi i t / N) for t < N/2; inverse uses the conjugate (no 1/N).
-// Returns the buffer (x or y) that holds the result in natural order.
-template <typename C>
-__device__ C* fft_lines(C* x, C* y, int N, int B, const C* __restrict__ tw, bool inverse) {
-  int n = N, s = 1;
-  const int half = (N >> 1) * B;
-  while (n > 1) {
-    const int m = n >> 1;
-    for (int t = threadIdx.x; t < half; t += blockDim.x) {
-      const int b = t % B;
-      const int pq = t / B;
-      const int q = pq % s;
-      const int p = pq / s;
-      C w = tw[p * s];
-      if (inverse) w.y = -w.y;
-      const C a0 = x[(q + s * p) * B + b];
-      const C a1 = x[(q + s * (p + m)) * B + b];
-      y[(q + s * (2 * p)) * B + b] = cadd(a0, a1);
-      y[(q + s * (2 * p + 1)) * B + b] = cmul(csub(a0, a1), w);
+__device__ __forceinline__ int bitrev(int p, int logn) {
+  return logn ? (int)(__brev((unsigned)p) >> (32 - logn)) : 0;
+}
+
+// Decimation in frequency: natural order in, bit-reversed order out.
+// j = lj + 32 e is the point held in v[e]; N = 32 E when E > 1, else N <= 32.
+template <typename C, int E>
+__device__ __forceinline__ void dif(C (&v)[E], int N, int lj, const C* __restrict__ tw, bool inv) {
+#pragma unroll
+  for (int de = E / 2; de >= 1; de >>= 1) {
+    const int d = 32 * de;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      if ((e & de) == 0) {
+        const int j = lj + 32 * e;
+        const C w = twid(tw, (j & (d - 1)) * (N / (2 * d)), inv);
+        const C a = v[e], b = v[e + de];
+        v[e] = cadd(a, b);
+        v[e + de] = cmul(csub(a, b), w);
+      }
     }
-    __syncthreads();
-    C* tmp = x; x = y; y = tmp;
-    n = m;
-    s <<= 1;
   }
-  return x;
+  for (int d = (N >= 32 ? 16 : N / 2); d >= 1; d >>= 1) {
+    const C w = twid(tw, (lj & (d - 1)) * (N / (2 * d)), inv);
+    const bool upper = (lj & d) != 0;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const C p = shfl_xor(v[e], d);
+      v[e] = upper ? cmul(csub(p, v[e]), w) : cadd(v[e], p);
+    }
+  }
+}
+
+// Decimation in time: bit-reversed order in, natural order out.
+template <typename C, int E>
+__device__ __forceinline__ void dit(C (&v)[E], int N, int lj, const C* __restrict__ tw, bool inv) {
+  const int dmax = (N >= 32 ? 16 : N / 2);
+  for (int d = 1; d <= dmax; d <<= 1) {
+    const C w = twid(tw, (lj & (d - 1)) * (N / (2 * d)), inv);
+    const bool upper = (lj & d) != 0;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const C p = shfl_xor(v[e], d);
+      v[e] = upper ? csub(p, cmul(w, v[e])) : cadd(v[e], cmul(w, p));
+    }
+  }
+#pragma unroll
+  for (int de = 1; de <= E / 2; de <<= 1) {
+    const int d = 32 * de;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      if ((e & de) == 0) {
+        const int j = lj + 32 * e;
+        const C w = twid(tw, (j & (d - 1)) * (N / (2 * d)), inv);
+        const C a = v[e], b = cmul(w, v[e + de]);
+        v[e] = cadd(a, b);
+        v[e + de] = csub(a, b);
+      }
+    }
+  }
+}
+
+// Iterate the lines of a CTA tile warp by warp; calls f(line, lj, active).
+// All 32 lanes of a warp take part in every call (the shuffles need them).
+template <typename F>
+__device__ __forceinline__ void for_lines(int N, int nlines, F f) {
+  const int lpl = N < 32 ? N : 32;         // lanes per line
+  const int lpw = 32 / lpl;                 // lines per warp
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int b0 = warp * lpw; b0 < nlines; b0 += nw * lpw) {
+    const int b = b0 + lane / lpl;
+    f(b, lane % lpl, b < nlines);
+  }
 }
 
 enum PhiMode { PHI_FWD = 0, PHI_BWD = 1, PHI_FKPP = 2 };
 
-// Forward real analysis of the packed lines in buf (result of fft_lines with
-// sign -1), scaled by 1/N, written to zm for this (z, r-tile).
+// Real analysis of packed line pairs held in L[b][m] (natural order, forward
+// DFT), scaled by 1/N, written to zm for this (z, r-tile).
 template <typename T, typename C>
-__device__ void phi_unpack_store(const C* buf, int N, int B, int M, int Nr, int r0, int z,
+__device__ void phi_unpack_store(const C* L, int ld, int N, int B, int M, int Nr, int r0, int z,
                                  T* __restrict__ zre, T* __restrict__ zim) {
   const T inv = (T)1 / (T)N;
   const int R = 2 * B;
   for (int t = threadIdx.x; t < M * R; t += blockDim.x) {
     const int m = t / R, rr = t % R;
     const int b = rr % B;
-    const C zm = buf[m * B + b];
-    const C zc = buf[((N - m) % N) * B + b];
+    const C zm = L[b * ld + m];
+    const C zc = L[b * ld + ((N - m) & (N - 1))];
     T re, im;
     if (rr < B) {  // X_m = (Z_m + conj(Z_{N-m})) / 2
       re = (zm.x + zc.x) * (T)0.5;
@@ -83,15 +148,16 @@ __device__ void phi_unpack_store(const C* buf, int N, int B, int M, int Nr, int 
   }
 }
 
-template <typename T, int MODE>
-__global__ void __launch_bounds__(256) k_phi(int N, int M, int Nr, int R, T* __restrict__ phys,
-                                             T* __restrict__ zre, T* __restrict__ zim,
+template <typename T, int MODE, int E>
+__global__ void __launch_bounds__(256) k_phi(int N, int logN, int M, int Nr, int R,
+                                             T* __restrict__ phys, T* __restrict__ zre,
+                                             T* __restrict__ zim,
                                              const typename C2T<T>::type* __restrict__ tw, T gamma) {
   typedef typename C2T<T>::type C;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* bufA = reinterpret_cast<C*>(smem_raw);
+  C* L = reinterpret_cast<C*>(smem_raw);
   const int B = R / 2;
-  C* bufB = bufA + N * B;
+  const int ld = N + 1;
   const int r0 = blockIdx.x * R;
   const int z = blockIdx.y;
   const long long plane = (long long)z * N * Nr;
@@ -101,71 +167,92 @@ __global__ void __launch_bounds__(256) k_phi(int N, int M, int Nr, int R, T* __r
       const int j = t / R, rr = t % R;
       const int r = r0 + rr;
       const T v = (r < Nr) ? phys[plane + (long long)j * Nr + r] : (T)0;
-      T* slot = reinterpret_cast<T*>(&bufA[j * B + (rr % B)]);
+      T* slot = reinterpret_cast<T*>(&L[(rr % B) * ld + j]);
       slot[rr < B ? 0 : 1] = v;
     }
     __syncthreads();
-    C* res = fft_lines<C>(bufA, bufB, N, B, tw, false);
-    phi_unpack_store<T, C>(res, N, B, M, Nr, r0, z, zre, zim);
+    for_lines(N, B, [&](int b, int lj, bool act) {
+      C v[E];
+#pragma unroll
+      for (int e = 0; e < E; ++e) v[e] = act ? L[b * ld + lj + 32 * e] : C{};
+      dif<C, E>(v, N, lj, tw, false);
+      if (act) {
+#pragma unroll
+        for (int e = 0; e < E; ++e) L[b * ld + bitrev(lj + 32 * e, logN)] = v[e];
+      }
+    });
+    __syncthreads();
+    phi_unpack_store<T, C>(L, ld, N, B, M, Nr, r0, z, zre, zim);
   } else {
-  // synthesis: build the packed Hermitian spectrum of line pairs
-  for (int t = threadIdx.x; t < N * B; t += blockDim.x) {
-    C zero; zero.x = 0; zero.y = 0;
-    bufA[t] = zero;
-  }
-  __syncthreads();
-  for (int t = threadIdx.x; t < M * B; t += blockDim.x) {
-    const int m = t / B, b = t % B;
-    const int ra = r0 + b, rb = r0 + b + B;
-    T ar = 0, ai = 0, br = 0, bi = 0;
-    const long long oa = ((long long)z * M + m) * Nr;
-    if (ra < Nr) { ar = zre[oa + ra]; ai = zim[oa + ra]; }
-    if (rb < Nr) { br = zre[oa + rb]; bi = zim[oa + rb]; }
-    if (m == 0) {
-      C v; v.x = ar; v.y = br;       // real parts of the mean modes
-      bufA[b] = v;
+    // packed Hermitian spectrum of each line pair: Zhat[m] = A_m + i B_m,
+    // Zhat[N-m] = conj(A_m) + i conj(B_m), Zhat[0] = Re A_0 + i Re B_0
+    for (int t = threadIdx.x; t < B * ld; t += blockDim.x) L[t] = C{};
+    __syncthreads();
+    for (int t = threadIdx.x; t < M * B; t += blockDim.x) {
+      const int m = t / B, b = t % B;
+      const int ra = r0 + b, rb = r0 + b + B;
+      T ar = 0, ai = 0, br = 0, bi = 0;
+      const long long oa = ((long long)z * M + m) * Nr;
+      if (ra < Nr) { ar = zre[oa + ra]; ai = zim[oa + ra]; }
+      if (rb < Nr) { br = zre[oa + rb]; bi = zim[oa + rb]; }
+      if (m == 0) {
+        C v; v.x = ar; v.y = br;
+        L[b * ld] = v;
+      } else {
+        C v1; v1.x = ar - bi; v1.y = ai + br;
+        C v2; v2.x = ar + bi; v2.y = br - ai;
+        L[b * ld + m] = v1;
+        L[b * ld + N - m] = v2;
+      }
+    }
+    __syncthreads();
+    for_lines(N, B, [&](int b, int lj, bool act) {
+      C v[E];
+#pragma unroll
+      for (int e = 0; e < E; ++e) v[e] = act ? L[b * ld + lj + 32 * e] : C{};
+      dif<C, E>(v, N, lj, tw, true);   // physical values, bit-reversed positions
+      if constexpr (MODE == PHI_FKPP) {
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          v[e].x = gamma * v[e].x * ((T)1 - v[e].x);
+          v[e].y = gamma * v[e].y * ((T)1 - v[e].y);
+        }
+        dit<C, E>(v, N, lj, tw, false);   // forward DFT, natural order
+        if (act) {
+#pragma unroll
+          for (int e = 0; e < E; ++e) L[b * ld + lj + 32 * e] = v[e];
+        }
+      } else {
+        if (act) {
+#pragma unroll
+          for (int e = 0; e < E; ++e) L[b * ld + bitrev(lj + 32 * e, logN)] = v[e];
+        }
+      }
+    });
+    __syncthreads();
+    if constexpr (MODE == PHI_BWD) {
+      for (int t = threadIdx.x; t < N * R; t += blockDim.x) {
+        const int j = t / R, rr = t % R;
+        const int r = r0 + rr;
+        const C v = L[(rr % B) * ld + j];
+        if (r < Nr) phys[plane + (long long)j * Nr + r] = (rr < B) ? v.x : v.y;
+      }
     } else {
-      C v1; v1.x = ar - bi; v1.y = ai + br;   // A_m + i B_m
-      C v2; v2.x = ar + bi; v2.y = br - ai;   // conj(A_m) + i conj(B_m)
-      bufA[m * B + b] = v1;
-      bufA[(N - m) * B + b] = v2;
+      phi_unpack_store<T, C>(L, ld, N, B, M, Nr, r0, z, zre, zim);
     }
-  }
-  __syncthreads();
-  C* res = fft_lines<C>(bufA, bufB, N, B, tw, true);
-  if constexpr (MODE == PHI_BWD) {
-    for (int t = threadIdx.x; t < N * R; t += blockDim.x) {
-      const int j = t / R, rr = t % R;
-      const int r = r0 + rr;
-      const C v = res[j * B + (rr % B)];
-      if (r < Nr) phys[plane + (long long)j * Nr + r] = (rr < B) ? v.x : v.y;
-    }
-  } else {
-  // PHI_FKPP: pointwise gamma u (1 - u) at the nodes, then analysis again
-  for (int t = threadIdx.x; t < N * B; t += blockDim.x) {
-    C v = res[t];
-    v.x = gamma * v.x * ((T)1 - v.x);
-    v.y = gamma * v.y * ((T)1 - v.y);
-    res[t] = v;
-  }
-  __syncthreads();
-  C* other = (res == bufA) ? bufB : bufA;
-  C* res2 = fft_lines<C>(res, other, N, B, tw, false);
-  phi_unpack_store<T, C>(res2, N, B, M, Nr, r0, z, zre, zim);
-  }
   }
 }
 
 // Axial transform for one m and a tile of R radii: lines are radii.
-template <typename T, bool INVERSE>
-__global__ void __launch_bounds__(256) k_z(int Nz, int Kz, int K, int M, int Nr, int R,
+template <typename T, bool INVERSE, int E>
+__global__ void __launch_bounds__(256) k_z(int Nz, int logN, int Kz, int K, int M, int Nr, int R,
                                            T* __restrict__ zre, T* __restrict__ zim,
                                            T* __restrict__ mre, T* __restrict__ mim,
                                            const typename C2T<T>::type* __restrict__ tw) {
   typedef typename C2T<T>::type C;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* bufA = reinterpret_cast<C*>(smem_raw);
-  C* bufB = bufA + Nz * R;
+  C* L = reinterpret_cast<C*>(smem_raw);
+  const int ld = Nz + 1;
   const int r0 = blockIdx.x * R;
   const int m = blockIdx.y;
   if (!INVERSE) {
@@ -177,27 +264,10 @@ __global__ void __launch_bounds__(256) k_z(int Nz, int Kz, int K, int M, int Nr,
         const long long o = ((long long)l * M + m) * Nr + r;
         v.x = zre[o]; v.y = zim[o];
       }
-      bufA[t] = v;
-    }
-    __syncthreads();
-    C* res = fft_lines<C>(bufA, bufB, Nz, R, tw, false);
-    const T inv = (T)1 / (T)Nz;
-    for (int t = threadIdx.x; t < K * R; t += blockDim.x) {
-      const int kk = t / R, b = t % R;
-      const int r = r0 + b;
-      const int pos = (kk < Kz) ? kk : Nz - (K - kk);
-      if (r < Nr) {
-        const C v = res[pos * R + b];
-        const long long o = ((long long)kk * M + m) * Nr + r;
-        mre[o] = v.x * inv;
-        mim[o] = v.y * inv;
-      }
+      L[b * ld + l] = v;
     }
   } else {
-    for (int t = threadIdx.x; t < Nz * R; t += blockDim.x) {
-      C zero; zero.x = 0; zero.y = 0;
-      bufA[t] = zero;
-    }
+    for (int t = threadIdx.x; t < R * ld; t += blockDim.x) L[t] = C{};
     __syncthreads();
     for (int t = threadIdx.x; t < K * R; t += blockDim.x) {
       const int kk = t / R, b = t % R;
@@ -206,16 +276,41 @@ __global__ void __launch_bounds__(256) k_z(int Nz, int Kz, int K, int M, int Nr,
       if (r < Nr) {
         const long long o = ((long long)kk * M + m) * Nr + r;
         C v; v.x = mre[o]; v.y = mim[o];
-        bufA[pos * R + b] = v;
+        L[b * ld + pos] = v;
       }
     }
-    __syncthreads();
-    C* res = fft_lines<C>(bufA, bufB, Nz, R, tw, true);
+  }
+  __syncthreads();
+  for_lines(Nz, R, [&](int b, int lj, bool act) {
+    C v[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) v[e] = act ? L[b * ld + lj + 32 * e] : C{};
+    dif<C, E>(v, Nz, lj, tw, INVERSE);
+    if (act) {
+#pragma unroll
+      for (int e = 0; e < E; ++e) L[b * ld + bitrev(lj + 32 * e, logN)] = v[e];
+    }
+  });
+  __syncthreads();
+  if (!INVERSE) {
+    const T inv = (T)1 / (T)Nz;
+    for (int t = threadIdx.x; t < K * R; t += blockDim.x) {
+      const int kk = t / R, b = t % R;
+      const int r = r0 + b;
+      const int pos = (kk < Kz) ? kk : Nz - (K - kk);
+      if (r < Nr) {
+        const C v = L[b * ld + pos];
+        const long long o = ((long long)kk * M + m) * Nr + r;
+        mre[o] = v.x * inv;
+        mim[o] = v.y * inv;
+      }
+    }
+  } else {
     for (int t = threadIdx.x; t < Nz * R; t += blockDim.x) {
       const int l = t / R, b = t % R;
       const int r = r0 + b;
       if (r < Nr) {
-        const C v = res[t];
+        const C v = L[b * ld + l];
         const long long o = ((long long)l * M + m) * Nr + r;
         zre[o] = v.x;
         zim[o] = v.y;
@@ -224,48 +319,85 @@ __global__ void __launch_bounds__(256) k_z(int Nz, int Kz, int K, int M, int Nr,
   }
 }
 
+int ilog2(int n) { int l = 0; while ((1 << l) < n) ++l; return l; }
+
+constexpr int kSmemLimit = 200 * 1024;
+
+template <typename T, int MODE, int E>
+void phi_go(dim3 grid, size_t smem, cudaStream_t st, int N, int M, int Nr, int R, T* phys, T* zre,
+            T* zim, const void* tw, double gamma) {
+  typedef typename C2T<T>::type C;
+  k_phi<T, MODE, E><<<grid, 256, smem, st>>>(N, ilog2(N), M, Nr, R, phys, zre, zim,
+                                             reinterpret_cast<const C*>(tw), (T)gamma);
+}
+
+template <typename T, int MODE>
+void phi_dispatch(int E, dim3 grid, size_t smem, cudaStream_t st, int N, int M, int Nr, int R,
+                  T* phys, T* zre, T* zim, const void* tw, double gamma) {
+  switch (E) {
+    case 1: phi_go<T, MODE, 1>(grid, smem, st, N, M, Nr, R, phys, zre, zim, tw, gamma); break;
+    case 2: phi_go<T, MODE, 2>(grid, smem, st, N, M, Nr, R, phys, zre, zim, tw, gamma); break;
+    case 4: phi_go<T, MODE, 4>(grid, smem, st, N, M, Nr, R, phys, zre, zim, tw, gamma); break;
+    case 8: phi_go<T, MODE, 8>(grid, smem, st, N, M, Nr, R, phys, zre, zim, tw, gamma); break;
+    default: phi_go<T, MODE, 16>(grid, smem, st, N, M, Nr, R, phys, zre, zim, tw, gamma); break;
+  }
+}
+
 template <typename T>
 int phi_launch(mlx_ctx* c, int mode, T* phys, T* zbase, const void* tw, double gamma,
                cudaStream_t st) {
   typedef typename C2T<T>::type C;
+  const int N = c->nphi;
   int R = 32;
-  size_t smem = (size_t)2 * c->nphi * (R / 2) * sizeof(C);
-  while (smem > 200 * 1024 && R > 2) { R /= 2; smem = (size_t)2 * c->nphi * (R / 2) * sizeof(C); }
+  auto need = [&](int R_) { return (size_t)(R_ / 2) * (N + 1) * sizeof(C); };
+  while (need(R) > kSmemLimit && R > 2) R /= 2;
+  const size_t smem = need(R);
   dim3 grid((c->nr + R - 1) / R, c->nz);
   const long long pl = (long long)c->nz * c->M * c->nr;
   T* zre = zbase;
   T* zim = zbase + pl;
-  const C* twp = reinterpret_cast<const C*>(tw);
+  const int E = N >= 32 ? N / 32 : 1;
   TimedLaunch tl(c, mode == PHI_FWD ? KID_PHI_FWD : (mode == PHI_BWD ? KID_PHI_BWD : KID_PHI_FKPP), st);
-  if (mode == PHI_FWD) {
-    k_phi<T, PHI_FWD><<<grid, 256, smem, st>>>(c->nphi, c->M, c->nr, R, phys, zre, zim, twp, (T)gamma);
-  } else if (mode == PHI_BWD) {
-    k_phi<T, PHI_BWD><<<grid, 256, smem, st>>>(c->nphi, c->M, c->nr, R, phys, zre, zim, twp, (T)gamma);
-  } else {
-    k_phi<T, PHI_FKPP><<<grid, 256, smem, st>>>(c->nphi, c->M, c->nr, R, phys, zre, zim, twp, (T)gamma);
-  }
+  if (mode == PHI_FWD) phi_dispatch<T, PHI_FWD>(E, grid, smem, st, N, c->M, c->nr, R, phys, zre, zim, tw, gamma);
+  else if (mode == PHI_BWD) phi_dispatch<T, PHI_BWD>(E, grid, smem, st, N, c->M, c->nr, R, phys, zre, zim, tw, gamma);
+  else phi_dispatch<T, PHI_FKPP>(E, grid, smem, st, N, c->M, c->nr, R, phys, zre, zim, tw, gamma);
   MLX_LAUNCH_CHECK(c);
   return MLX_OK;
+}
+
+template <typename T, bool INV, int E>
+void z_go(dim3 grid, size_t smem, cudaStream_t st, mlx_ctx* c, int R, T* zb, T* mb, const void* tw) {
+  typedef typename C2T<T>::type C;
+  const long long plz = (long long)c->nz * c->M * c->nr;
+  const long long plm = (long long)c->K * c->M * c->nr;
+  k_z<T, INV, E><<<grid, 256, smem, st>>>(c->nz, ilog2(c->nz), c->Kz, c->K, c->M, c->nr, R, zb,
+                                          zb + plz, mb, mb + plm, reinterpret_cast<const C*>(tw));
+}
+
+template <typename T, bool INV>
+void z_dispatch(int E, dim3 grid, size_t smem, cudaStream_t st, mlx_ctx* c, int R, T* zb, T* mb,
+                const void* tw) {
+  switch (E) {
+    case 1: z_go<T, INV, 1>(grid, smem, st, c, R, zb, mb, tw); break;
+    case 2: z_go<T, INV, 2>(grid, smem, st, c, R, zb, mb, tw); break;
+    case 4: z_go<T, INV, 4>(grid, smem, st, c, R, zb, mb, tw); break;
+    case 8: z_go<T, INV, 8>(grid, smem, st, c, R, zb, mb, tw); break;
+    default: z_go<T, INV, 16>(grid, smem, st, c, R, zb, mb, tw); break;
+  }
 }
 
 template <typename T>
 int z_launch(mlx_ctx* c, bool inverse, T* zbase, T* mbase, const void* tw, cudaStream_t st) {
   typedef typename C2T<T>::type C;
   int R = 32;
-  size_t smem = (size_t)2 * c->nz * R * sizeof(C);
-  while (smem > 200 * 1024 && R > 1) { R /= 2; smem = (size_t)2 * c->nz * R * sizeof(C); }
+  auto need = [&](int R_) { return (size_t)R_ * (c->nz + 1) * sizeof(C); };
+  while (need(R) > kSmemLimit && R > 1) R /= 2;
+  const size_t smem = need(R);
   dim3 grid((c->nr + R - 1) / R, c->M);
-  const long long plz = (long long)c->nz * c->M * c->nr;
-  const long long plm = (long long)c->K * c->M * c->nr;
-  const C* twp = reinterpret_cast<const C*>(tw);
+  const int E = c->nz >= 32 ? c->nz / 32 : 1;
   TimedLaunch tl(c, inverse ? KID_Z_BWD : KID_Z_FWD, st);
-  if (!inverse) {
-    k_z<T, false><<<grid, 256, smem, st>>>(c->nz, c->Kz, c->K, c->M, c->nr, R, zbase, zbase + plz,
-                                           mbase, mbase + plm, twp);
-  } else {
-    k_z<T, true><<<grid, 256, smem, st>>>(c->nz, c->Kz, c->K, c->M, c->nr, R, zbase, zbase + plz,
-                                          mbase, mbase + plm, twp);
-  }
+  if (!inverse) z_dispatch<T, false>(E, grid, smem, st, c, R, zbase, mbase, tw);
+  else z_dispatch<T, true>(E, grid, smem, st, c, R, zbase, mbase, tw);
   MLX_LAUNCH_CHECK(c);
   return MLX_OK;
 }
@@ -302,23 +434,43 @@ int fft_fkpp_t(mlx_ctx* c, double gamma, cudaStream_t st, const void* twphi, con
   return z_launch<T>(c, false, zm, mixed, twz, st);
 }
 
+template <typename T, int MODE, int E>
+int attr_phi(mlx_ctx* c) {
+  MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_phi<T, MODE, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit));
+  return MLX_OK;
+}
+template <typename T, bool INV, int E>
+int attr_z(mlx_ctx* c) {
+  MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_z<T, INV, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit));
+  return MLX_OK;
+}
+template <typename T, int E>
+int attr_all(mlx_ctx* c) {
+  int rc = attr_phi<T, PHI_FWD, E>(c);
+  if (!rc) rc = attr_phi<T, PHI_BWD, E>(c);
+  if (!rc) rc = attr_phi<T, PHI_FKPP, E>(c);
+  if (!rc) rc = attr_z<T, false, E>(c);
+  if (!rc) rc = attr_z<T, true, E>(c);
+  return rc;
+}
+
 }  // namespace
 
-// Opt every FFT kernel into the largest dynamic shared memory any size needs
-// (the launch helpers keep each launch below 200 KB).
+// Opt every FFT kernel into the shared memory the launch helpers may ask for
+// (each launch stays below 200 KB).
 int mlx_fft_prepare(mlx_ctx* c) {
-  const int lim = 200 * 1024;
-  MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_phi<float, PHI_FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-  MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_phi<float, PHI_BWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-  MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_phi<float, PHI_FKPP>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-  MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_phi<double, PHI_FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-  MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_phi<double, PHI_BWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-  MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_phi<double, PHI_FKPP>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-  MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_z<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-  MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_z<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-  MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_z<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-  MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_z<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-  return MLX_OK;
+  int rc = MLX_OK;
+  if (!rc) rc = attr_all<float, 1>(c);
+  if (!rc) rc = attr_all<float, 2>(c);
+  if (!rc) rc = attr_all<float, 4>(c);
+  if (!rc) rc = attr_all<float, 8>(c);
+  if (!rc) rc = attr_all<float, 16>(c);
+  if (!rc) rc = attr_all<double, 1>(c);
+  if (!rc) rc = attr_all<double, 2>(c);
+  if (!rc) rc = attr_all<double, 4>(c);
+  if (!rc) rc = attr_all<double, 8>(c);
+  if (!rc) rc = attr_all<double, 16>(c);
+  return rc;
 }
 
 int mlx_fft_forward(mlx_ctx* c, const void* phys, cudaStream_t st) {

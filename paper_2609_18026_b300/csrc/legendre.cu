@@ -20,7 +20,8 @@ __global__ void __launch_bounds__(NT) k_legendre(const LegTile* __restrict__ til
                                                  const long long* __restrict__ soff,
                                                  const T* __restrict__ table,  // W (fwd) or P (bwd)
                                                  T* __restrict__ mixed,        // planar [2][K][M][Nr]
-                                                 double2* __restrict__ spec) {
+                                                 double2* __restrict__ spec,
+                                                 const double2* __restrict__ addsrc, double alpha) {
   __shared__ T As[BK][BM + 1];
   __shared__ T Bs[BK][BN + 1];
   const LegTile tile = tiles[blockIdx.x];
@@ -95,8 +96,10 @@ __global__ void __launch_bounds__(NT) k_legendre(const LegTile* __restrict__ til
       const int p = gc >= K;
       const int kidx = gc - p * K;
       if (FWD) {
-        double* dst = reinterpret_cast<double*>(&spec[so + (long long)kidx * Nm + gr]);
-        dst[p] = (double)acc[x][y];
+        const long long o = so + (long long)kidx * Nm + gr;
+        double val = (double)acc[x][y];
+        if (addsrc) val += alpha * (p ? addsrc[o].y : addsrc[o].x);   // FP64 epilogue term
+        reinterpret_cast<double*>(&spec[o])[p] = val;
       } else {
         mixed[p * plane + ((long long)kidx * M + m) * nr + gr] = acc[x][y];
       }
@@ -106,16 +109,17 @@ __global__ void __launch_bounds__(NT) k_legendre(const LegTile* __restrict__ til
 
 }  // namespace
 
-int mlx_legendre_forward(mlx_ctx* c, double2* spec, cudaStream_t st) {
+int mlx_legendre_forward(mlx_ctx* c, double2* spec, cudaStream_t st, const double2* addsrc,
+                         double alpha) {
   TimedLaunch tl(c, KID_LEG_FWD, st);
   if (c->precision == MLX_FP64)
     k_legendre<double, true><<<c->ntiles_fwd, NT, 0, st>>>(c->d_tiles_fwd, c->nc, c->nr, c->M, c->K,
                                                           c->d_boff, c->d_soff, c->d_W64,
-                                                          (double*)c->d_mixed, spec);
+                                                          (double*)c->d_mixed, spec, addsrc, alpha);
   else
     k_legendre<float, true><<<c->ntiles_fwd, NT, 0, st>>>(c->d_tiles_fwd, c->nc, c->nr, c->M, c->K,
                                                          c->d_boff, c->d_soff, c->d_W32,
-                                                         (float*)c->d_mixed, spec);
+                                                         (float*)c->d_mixed, spec, addsrc, alpha);
   MLX_LAUNCH_CHECK(c);
   return MLX_OK;
 }
@@ -125,11 +129,11 @@ int mlx_legendre_backward(mlx_ctx* c, const double2* spec, cudaStream_t st) {
   if (c->precision == MLX_FP64)
     k_legendre<double, false><<<c->ntiles_bwd, NT, 0, st>>>(c->d_tiles_bwd, c->nc, c->nr, c->M, c->K,
                                                            c->d_boff, c->d_soff, c->d_P64,
-                                                           (double*)c->d_mixed, (double2*)spec);
+                                                           (double*)c->d_mixed, (double2*)spec, nullptr, 0.0);
   else
     k_legendre<float, false><<<c->ntiles_bwd, NT, 0, st>>>(c->d_tiles_bwd, c->nc, c->nr, c->M, c->K,
                                                           c->d_boff, c->d_soff, c->d_P32,
-                                                          (float*)c->d_mixed, (double2*)spec);
+                                                          (float*)c->d_mixed, (double2*)spec, nullptr, 0.0);
   MLX_LAUNCH_CHECK(c);
   return MLX_OK;
 }

@@ -108,6 +108,8 @@ struct mlx_ctx {
   double* d_Bplus = nullptr;           // band of I + dt/2 L, [rows][2kl+1]
   BandLU lu_half, lu_full;
   double* d_setup_scratch = nullptr;
+  int solve_cpw = 8;                   // real chains per warp in the banded solve (4..32)
+  int solve_wpb = 4;                   // warps per CTA in the banded solve (1..4)
 
   // graphs cached per (state, prev_A, kind, gamma)
   struct GraphKey {
@@ -150,8 +152,10 @@ static inline size_t elem_size(int precision) { return precision == MLX_FP64 ? 8
 int mlx_basis_build(mlx_ctx* c, cudaStream_t st);
 int mlx_fft_forward(mlx_ctx* c, const void* phys, cudaStream_t st);    // phys -> d_mixed
 int mlx_fft_backward(mlx_ctx* c, void* phys, cudaStream_t st);         // d_mixed -> phys
-int mlx_fft_fkpp(mlx_ctx* c, double gamma, cudaStream_t st);           // d_mixed -> A(mixed)
-int mlx_legendre_forward(mlx_ctx* c, double2* spec, cudaStream_t st);  // d_mixed -> spec
+int mlx_fft_fkpp(mlx_ctx* c, double gamma, cudaStream_t st);           // d_mixed -> gamma u (1 - u) (mixed)
+// d_mixed -> spec; with addsrc != NULL adds alpha * addsrc in FP64 to every coefficient
+int mlx_legendre_forward(mlx_ctx* c, double2* spec, cudaStream_t st,
+                         const double2* addsrc = nullptr, double alpha = 0.0);
 int mlx_legendre_backward(mlx_ctx* c, const double2* spec, cudaStream_t st); // spec -> d_mixed
 int mlx_band_setup(mlx_ctx* c, cudaStream_t st);
 int mlx_band_solve(mlx_ctx* c, int step, const double2* s, const double2* A,

@@ -40,7 +40,7 @@ def test_strerror(lib):
 
 @pytest.mark.parametrize("kw", [
     dict(nr=1, nphi=8, nz=1, ell=1.0), dict(nr=8, nphi=12, nz=1, ell=1.0),
-    dict(nr=8, nphi=8, nz=3, ell=1.0), dict(nr=8, nphi=8, nz=1, ell=0.0),
+    dict(nr=8, nphi=8, nz=3, ell=1.0), dict(nr=8, nphi=8, nz=1, ell=0.0), dict(nr=8, nphi=1024, nz=1, ell=1.0),
     dict(nr=8, nphi=8, nz=1, ell=1.0, lz=-1.0), dict(nr=8, nphi=8, nz=1, ell=1.0, precision=7),
     dict(nr=8, nphi=8, nz=1, ell=1.0, nphi_c=5), dict(nr=8, nphi=8, nz=4, ell=1.0, nz_c=3),
     dict(nr=8, nphi=8, nz=1, ell=1.0, nr_c=9), dict(nr=4, nphi=16, nz=1, ell=1.0, nphi_c=8)])

@@ -22,6 +22,9 @@ GRIDS = [
     (70, 32, 16, 2.0, "linear"),
     (100, 64, 1, 4.0, "twothirds"),
     (128, 128, 64, 4.0, "twothirds"),
+    (9, 256, 32, 1.0, "linear", 7),       # in-lane butterfly stages (E = 8), M = 7
+    (6, 512, 2, 1.0, "twothirds", 5),     # E = 16, Nz = 2, M = 5
+    (12, 4, 256, 0.7, "linear"),          # lane groups for Nphi = 4, long z lines
 ]
 TOL = {B.FP64: 1e-12, B.FP32: 1e-6}
 
@@ -38,8 +41,9 @@ def test_nodes_weights_radii(nr):
 @pytest.mark.parametrize("prec", [B.FP64, B.FP32])
 @pytest.mark.parametrize("grid", GRIDS)
 def test_forward_parity(grid, prec):
-    nr, nphi, nz, ell, pol = grid
-    g, ctx = pair(nr, nphi, nz, ell, lz=3.7, policy=pol, precision=prec)
+    nr, nphi, nz, ell, pol = grid[:5]
+    chop = dict(nphi_c=grid[5]) if len(grid) > 5 else {}
+    g, ctx = pair(nr, nphi, nz, ell, lz=3.7, policy=pol, precision=prec, **chop)
     f = rand_phys(g, 11)
     if prec == B.FP32:
         f = f.astype(np.float32).astype(np.float64)   # both sides see the same input
@@ -52,8 +56,9 @@ def test_forward_parity(grid, prec):
 @pytest.mark.parametrize("prec", [B.FP64, B.FP32])
 @pytest.mark.parametrize("grid", GRIDS)
 def test_backward_parity(grid, prec):
-    nr, nphi, nz, ell, pol = grid
-    g, ctx = pair(nr, nphi, nz, ell, lz=3.7, policy=pol, precision=prec)
+    nr, nphi, nz, ell, pol = grid[:5]
+    chop = dict(nphi_c=grid[5]) if len(grid) > 5 else {}
+    g, ctx = pair(nr, nphi, nz, ell, lz=3.7, policy=pol, precision=prec, **chop)
     flat = rand_spec(g, 5)
     phys = ctx.backward(to_gpu_spec(flat), ctx.new_phys())
     got = phys.double().cpu().numpy()
