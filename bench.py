@@ -164,6 +164,26 @@ def run_reference(args, rank, world):
 
 
 # ---------------------------------------------------------------- GPU arm
+def tc_executed_flops(ctx, forward):
+    """Tensor-core flops one launch of the BF16x3 contraction executes (6 products,
+    tiles padded to 128 rows x BN columns x 64-wide K chunks)."""
+    ncol = 2 * ctx.K
+    rt = sum(-(-(ctx.nc - m) // 128) for m in range(ctx.M))
+    bn = 256
+    while bn > 32 and rt * (-(-ncol // bn)) < 148:   # same tile choice as the library
+        bn -= 16
+    nct = -(-ncol // bn)
+    bn = -(-(-(-ncol // nct)) // 16) * 16
+    tot = 0
+    for m in range(ctx.M):
+        nm = ctx.nc - m
+        if forward:
+            tot += -(-nm // 128) * nct * (-(-ctx.nr // 64)) * 64
+        else:
+            tot += -(-ctx.nr // 128) * nct * (-(-nm // 64)) * 64
+    return 6.0 * 2.0 * 128 * bn * tot
+
+
 def algorithmic(kernel, ctx, nz_gt1=True):
     """Algorithmic DRAM bytes and useful flops of one launch of a kernel at this size."""
     es = 8 if ctx.precision == 0 else 4
@@ -171,7 +191,7 @@ def algorithmic(kernel, ctx, nz_gt1=True):
     mixed = 2 * ctx.K * ctx.M * ctx.nr * es
     zm = 2 * ctx.nz * ctx.M * ctx.nr * es
     spec = 16 * ctx.n_spec
-    table = tri * ctx.nr * es
+    table = tri * ctx.nr * (6 if ctx.precision == 2 else es)   # BF16x3: three 2-byte parts
     leg_flops = 2.0 * 2.0 * ctx.K * tri * ctx.nr
     rows = ctx.Kz * tri
     kl = 2
@@ -205,16 +225,20 @@ def run_gpu(args, rank, world):
         if world > 1:
             dist.barrier()
 
-    ctx = B.Context(NR, NPHI, NZ, ELL, lz=LZ, precision=B.FP32, chop_policy=B.CHOP_TWOTHIRDS)
+    prec = {"bf16x3": B.BF16X3, "fp32": B.FP32, "fp64": B.FP64}[args.precision]
+    ctx = B.Context(NR, NPHI, NZ, ELL, lz=LZ, precision=prec, chop_policy=B.CHOP_TWOTHIRDS)
     ctx64 = B.Context(NR, NPHI, NZ, ELL, lz=LZ, precision=B.FP64, chop_policy=B.CHOP_TWOTHIRDS)
+    ctx32 = B.Context(NR, NPHI, NZ, ELL, lz=LZ, precision=B.FP32, chop_policy=B.CHOP_TWOTHIRDS) \
+        if prec != B.FP32 else None
     x, w, r = ctx.nodes()
     phi = 2 * np.pi * np.arange(NPHI) / NPHI
     zz = LZ * np.arange(NZ) / NZ
     u0 = W.fkpp_seed(r[None, None, :], phi[None, :, None], zz[:, None, None], seed=2 + rank)
-    u0_32 = torch.as_tensor(u0, dtype=torch.float32, device=dev)
+    u0_32 = torch.as_tensor(u0, dtype=ctx.phys_dtype, device=dev)
     u0_64 = torch.as_tensor(u0, dtype=torch.float64, device=dev)
-    for c in (ctx, ctx64):
-        c.implicit_setup(D_COEF, DT)
+    for c in (ctx, ctx64, ctx32):
+        if c is not None:
+            c.implicit_setup(D_COEF, DT)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
 
     def fresh(c, u):
@@ -270,6 +294,14 @@ def run_gpu(args, rank, world):
     s64, a64 = fresh(ctx64, u0_64)
     ms64 = run_steps(ctx64, s64, a64, args.steps, True)
     fp64_value = args.steps * STEPS_PER_BENCH_STEP / (sum(ms64) / 1000.0)
+    fp32_value = None
+    if ctx32 is not None:
+        u0_f = torch.as_tensor(u0, dtype=torch.float32, device=dev)
+        s_w, a_w = fresh(ctx32, u0_f)
+        run_steps(ctx32, s_w, a_w, 1, False)
+        s_f, a_f = fresh(ctx32, u0_f)
+        ms32 = run_steps(ctx32, s_f, a_f, args.steps, True)
+        fp32_value = args.steps * STEPS_PER_BENCH_STEP / (sum(ms32) / 1000.0)
     d = (s.cpu().numpy() - s64.cpu().numpy())
     mult = np.ones(ctx.n_spec)
     off = ctx.K * ctx.nc   # m = 0 block has multiplicity 1
@@ -335,6 +367,24 @@ def run_gpu(args, rank, world):
                 "share_of_kernel_time": top_ms / total_k}
     kernels = {k: {"launches": v[0], "avg_us": 1000.0 * v[1] / v[0], "share": v[1] / total_k}
                for k, v in sorted(kt.items(), key=lambda kv: -kv[1][1])}
+    roofline_contraction = None
+    if ctx.precision == B.BF16X3:
+        pk = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+            os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+        tpeak = pk.get("bf16_tflops_sustained", 1400.0)
+        roofline_contraction = {}
+        for name, fwd in (("legendre_forward", True), ("legendre_backward", False)):
+            if name not in kt:
+                continue
+            n_, ms_ = kt[name]
+            avg = ms_ / n_ / 1000.0
+            ex = tc_executed_flops(ctx, fwd)
+            _, useful = algorithmic(name, ctx)
+            roofline_contraction[name] = {
+                "bound": "tensor", "achieved": ex / avg / 1e12, "peak": tpeak, "unit": "TFLOP/s",
+                "frac": ex / avg / 1e12 / tpeak, "executed_tflop_per_launch": ex / 1e12,
+                "useful_tflop_per_launch": useful / 1e12, "avg_launch_us": avg * 1e6,
+                "peak_source": "measured bf16_tflops_sustained (MEASURED_PEAKS.json)"}
 
     # ---- end to end through the C-ABI with host buffers
     host_in = torch.empty((NZ, NPHI, NR), dtype=torch.float32, pin_memory=True)
@@ -371,7 +421,9 @@ def run_gpu(args, rank, world):
         "metric": METRIC, "value": value, "unit": "timesteps/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32 transforms, f64 solve",
+        "vs_baseline": None,
+        "dtype": {"bf16x3": "bf16x3 tensor-core contraction (f32 accumulate), f32 FFTs, f64 solve",
+                  "fp32": "f32 transforms, f64 solve", "fp64": "f64"}[args.precision],
         "data": "synthetic (seeded analytic initial condition, PCG64 seed 2)",
         "config": {"workload": WORKLOAD, "nr": NR, "nphi": NPHI, "nz": NZ, "ell": ELL,
                    "lz": LZ, "chop": "two-thirds (M=43, K=43)", "dt": DT,
@@ -380,10 +432,12 @@ def run_gpu(args, rank, world):
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "transform_pairs_per_s": pair_per_s,
         "fp64_form": {"value": fp64_value, "unit": "timesteps/s", "speedup_mixed_vs_fp64": value / world / fp64_value},
+        "fp32_simt_form": None if fp32_value is None else {"value": fp32_value, "unit": "timesteps/s"},
         "rel_err_fp32_vs_fp64": {"per_time_step_state": step_err, "per_time_step_nonlinear_term": nonl_err,
                                  "trajectory_at_t10": rel_err,
                                  "note": "per-step errors are the precision claim; the trajectory deviation is the per-step error amplified ~e^{gamma t} by the linear instability of u = 0 in the reaction term"},
         "roofline": roofline,
+        "roofline_contraction": roofline_contraction,
         "kernels": kernels,
         "clocks": clk,
         "e2e": {"value": e2e_value, "unit": "timesteps/s",
@@ -403,6 +457,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mlx", choices=["mlx", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "fp32", "fp64"],
+                    help="transform arithmetic of the timed form (the FP64 form is always timed beside it)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

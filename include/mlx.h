@@ -56,7 +56,11 @@ enum {
 };
 
 /* Arithmetic of the transforms.  The implicit solve and the spectral state are
- * always FP64; basis values, nodes and weights are generated in FP64. */
+ * always FP64; basis values, nodes and weights are generated in FP64.
+ *   MLX_FP64   : FFTs and Legendre contraction in FP64 (parity form).
+ *   MLX_FP32   : FFTs and contraction in FP32 on the CUDA cores.
+ *   MLX_BF16X3 : FFTs in FP32; contraction on the tensor cores with every operand
+ *                split into three BF16 parts (six products, FP32 accumulation). */
 enum { MLX_FP64 = 0, MLX_FP32 = 1, MLX_BF16X3 = 2 };
 
 /* Chop policy used when the corresponding chop in mlx_params is 0.
@@ -162,6 +166,9 @@ int mlx_advance(mlx_ctx* ctx, int kind, const double* coeffs, int ncoeffs,
  *   "solve_cpw": real chains per warp of the banded solve, 4, 8, 16 or 32
  *                (default 8);
  *   "solve_wpb": warps per CTA of the banded solve, 1, 2 or 4 (default 4).
+ *   "tc_products": BF16 split products per term in the MLX_BF16X3 contraction,
+ *                6 (hi*hi, hi*mid, mid*hi, hi*lo, lo*hi, mid*mid) or 8 (adds
+ *                mid*lo, lo*mid); default 6.
  *   The substitution is a sequential FP64 recurrence per real chain; the best
  *   shape trades per-warp staging latency against FP64 pipe sharing.
  * Invalidates cached graphs.  MLX_EINVAL for an unknown key or value. */
@@ -179,6 +186,12 @@ int mlx_timing(mlx_ctx* ctx, int enable);
 int mlx_timing_read(mlx_ctx* ctx, int kernel, long long* launches, double* total_ms);
 int mlx_kernel_count(void);
 const char* mlx_kernel_name(int kernel);
+
+/* Device status: synchronises the device, returns MLX_ETIMEOUT (and clears the
+ * word) if a kernel of this context gave up a bounded wait since the last call,
+ * else MLX_OK.  Kernels that give up skip their remaining work and release their
+ * resources; their outputs are then undefined. */
+int mlx_device_status(mlx_ctx* ctx);
 
 #ifdef __cplusplus
 }

@@ -23,7 +23,7 @@ EXPORTS = ("mlx_strerror", "mlx_last_cuda_error", "mlx_create", "mlx_destroy", "
            "mlx_get_nodes", "mlx_forward", "mlx_backward", "mlx_nonlinear",
            "mlx_implicit_setup", "mlx_implicit_solve", "mlx_advance",
            "mlx_timing", "mlx_timing_read", "mlx_kernel_count", "mlx_kernel_name",
-           "mlx_set_tuning")
+           "mlx_set_tuning", "mlx_device_status")
 
 
 class MlxError(RuntimeError):
@@ -77,6 +77,7 @@ def load():
     lib.mlx_timing_read.argtypes = [vp, i, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(d)]
     lib.mlx_kernel_count.argtypes = []
     lib.mlx_set_tuning.argtypes = [vp, ctypes.c_char_p, i]
+    lib.mlx_device_status.argtypes = [vp]
     lib.mlx_kernel_name.argtypes = [i]
     lib.mlx_kernel_name.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -187,6 +188,10 @@ class Context:
         self._check(self.lib.mlx_implicit_solve(self._h, step, _ptr(s), _ptr(A), _ptr(A_prev),
                                                 _ptr(out), _stream(stream)))
         return out
+
+    def device_status(self):
+        """Raise MlxError(MLX_ETIMEOUT) if a kernel gave up a bounded wait."""
+        self._check(self.lib.mlx_device_status(self._h))
 
     def set_tuning(self, key, value):
         self._check(self.lib.mlx_set_tuning(self._h, key.encode(), int(value)))

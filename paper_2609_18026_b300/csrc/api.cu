@@ -22,7 +22,8 @@ void free_ctx(mlx_ctx* c) {
                   c->d_tiles_fwd, c->d_tiles_bwd, c->d_mixed, c->d_zm, c->d_phys, c->d_specA,
                   c->d_spec1, c->d_spec2, c->d_spec3, c->d_band_off, c->d_Bplus,
                   c->lu_half.U, c->lu_half.L, c->lu_half.piv, c->lu_half.invd,
-                  c->lu_full.U, c->lu_full.L, c->lu_full.piv, c->lu_full.invd};
+                  c->lu_full.U, c->lu_full.L, c->lu_full.piv, c->lu_full.invd,
+                  c->d_Wb, c->d_Pb, c->d_arowW, c->d_arowP, c->d_tc_fwd, c->d_tc_bwd, c->d_err};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
@@ -92,7 +93,7 @@ int mlx_create(const mlx_params* p, mlx_stream stream, mlx_ctx** out) {
   if (!is_pow2(p->nphi) || p->nphi < 4 || p->nphi > 512) return MLX_EINVAL;
   if (!(p->nz == 1 || (is_pow2(p->nz) && p->nz <= 512))) return MLX_EINVAL;
   if (!(p->ell > 0.0) || !(p->lz > 0.0)) return MLX_EINVAL;
-  if (p->precision != MLX_FP64 && p->precision != MLX_FP32) return MLX_EINVAL;
+  if (p->precision != MLX_FP64 && p->precision != MLX_FP32 && p->precision != MLX_BF16X3) return MLX_EINVAL;
   if (p->chop_policy != MLX_CHOP_LINEAR && p->chop_policy != MLX_CHOP_TWOTHIRDS) return MLX_EINVAL;
   if (p->nr_c < 0 || p->nphi_c < 0 || p->nz_c < 0) return MLX_EINVAL;
   int nc = p->nr_c ? p->nr_c : p->nr;
@@ -164,6 +165,7 @@ int mlx_create(const mlx_params* p, mlx_stream stream, mlx_ctx** out) {
   c->ntiles_bwd = (int)tb.size();
   ALLOC(c->d_tiles_fwd, sizeof(LegTile) * tf.size());
   ALLOC(c->d_tiles_bwd, sizeof(LegTile) * tb.size());
+  ALLOC(c->d_err, sizeof(int));
 #undef ALLOC
 #define TRY(call) do { cudaError_t _e = (call); if (_e != cudaSuccess) { c->last_err = cudaGetErrorString(_e); free_ctx(c); return MLX_ECUDA; } } while (0)
   TRY(cudaMemcpyAsync(c->d_soff, c->soff.data(), sizeof(long long) * (M + 1), cudaMemcpyHostToDevice, st));
@@ -171,11 +173,13 @@ int mlx_create(const mlx_params* p, mlx_stream stream, mlx_ctx** out) {
   TRY(cudaMemcpyAsync(c->d_band_off, c->band_off.data(), sizeof(long long) * (M + 1), cudaMemcpyHostToDevice, st));
   TRY(cudaMemcpyAsync(c->d_tiles_fwd, tf.data(), sizeof(LegTile) * tf.size(), cudaMemcpyHostToDevice, st));
   TRY(cudaMemcpyAsync(c->d_tiles_bwd, tb.data(), sizeof(LegTile) * tb.size(), cudaMemcpyHostToDevice, st));
+  TRY(cudaMemsetAsync(c->d_err, 0, sizeof(int), st));
   TRY(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
 #undef TRY
   rc = mlx_fft_prepare(c);
   if (!rc) rc = mlx_band_prepare(c);
   if (!rc) rc = mlx_basis_build(c, st);
+  if (!rc && c->precision == MLX_BF16X3) rc = mlx_tc_prepare(c, st);
   if (!rc) {
     cudaError_t e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) { c->last_err = cudaGetErrorString(e); rc = MLX_ECUDA; }
@@ -330,6 +334,13 @@ int mlx_set_tuning(mlx_ctx* c, const char* key, int value) {
     c->graphs.clear();
     return MLX_OK;
   }
+  if (strcmp(key, "tc_products") == 0) {
+    if (value != 6 && value != 8) return MLX_EINVAL;
+    c->tc_products = value;
+    for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
+    c->graphs.clear();
+    return MLX_OK;
+  }
   if (strcmp(key, "solve_wpb") == 0) {
     if (value != 1 && value != 2 && value != 4) return MLX_EINVAL;
     c->solve_wpb = value;
@@ -345,6 +356,17 @@ static const char* kKernelNames[KID_COUNT] = {
     "legendre_forward", "legendre_backward", "band_solve", "spec_axpby"};
 
 int mlx_kernel_count(void) { return KID_COUNT; }
+
+int mlx_device_status(mlx_ctx* c) {
+  if (!c) return MLX_EINVAL;
+  int v = 0;
+  MLX_CUDA_TRY(c, cudaMemcpy(&v, c->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (v) {
+    MLX_CUDA_TRY(c, cudaMemset(c->d_err, 0, sizeof(int)));
+    return MLX_ETIMEOUT;
+  }
+  return MLX_OK;
+}
 
 const char* mlx_kernel_name(int kernel) {
   return (kernel >= 0 && kernel < KID_COUNT) ? kKernelNames[kernel] : "";

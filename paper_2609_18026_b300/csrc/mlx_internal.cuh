@@ -1,6 +1,7 @@
 // Internal definitions shared by the CUDA translation units of libmlx.
 #pragma once
 
+#include <cuda.h>            // CUtensorMap (header only; the driver entry point is fetched at run time)
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string>
@@ -88,6 +89,19 @@ struct mlx_ctx {
   LegTile* d_tiles_bwd = nullptr;
   int ntiles_fwd = 0, ntiles_bwd = 0;
 
+  // tensor-core (BF16x3) form of the Legendre contraction
+  void* d_Wb = nullptr;                // BF16 splits of W: [3][T][Kp]
+  void* d_Pb = nullptr;                // BF16 splits of P^T: [3][M*Nr][Kq]
+  CUtensorMap tmapW, tmapP;
+  long long* d_arowW = nullptr;
+  long long* d_arowP = nullptr;
+  LegTile* d_tc_fwd = nullptr;
+  LegTile* d_tc_bwd = nullptr;
+  int ntc_fwd = 0, ntc_bwd = 0, tc_bn = 0, tc_tmem_cols = 0;
+  int tc_products = 6;                 // BF16 split products per term: 6 or 8
+  int tc_stages = 2;                   // shared-memory stages of the K loop
+  int* d_err = nullptr;                // device status word (bounded waits that expired)
+
   // workspace (element type follows precision)
   void* d_mixed = nullptr;             // planar complex [2][K][M][Nr]
   void* d_zm = nullptr;                // planar complex [2][Nz][M][Nr]
@@ -158,6 +172,9 @@ int mlx_legendre_forward(mlx_ctx* c, double2* spec, cudaStream_t st,
                          const double2* addsrc = nullptr, double alpha = 0.0);
 int mlx_legendre_backward(mlx_ctx* c, const double2* spec, cudaStream_t st); // spec -> d_mixed
 int mlx_band_setup(mlx_ctx* c, cudaStream_t st);
+int mlx_tc_prepare(mlx_ctx* c, cudaStream_t st);
+int mlx_legendre_tc_forward(mlx_ctx* c, double2* spec, cudaStream_t st);
+int mlx_legendre_tc_backward(mlx_ctx* c, const double2* spec, cudaStream_t st);
 int mlx_band_solve(mlx_ctx* c, int step, const double2* s, const double2* A,
                    const double2* Ap, double2* out, cudaStream_t st);
 int mlx_spec_axpby(mlx_ctx* c, double a, const double2* x, double b, const double2* y,

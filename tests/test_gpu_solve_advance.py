@@ -78,7 +78,7 @@ def test_polar_diffusion_100_steps():
     assert O.spec_rel_err(g, spec_from_gpu(g, state), ref) <= 1e-12
 
 
-@pytest.mark.parametrize("prec,tol", [(B.FP64, 1e-12), (B.FP32, 1e-6)])
+@pytest.mark.parametrize("prec,tol", [(B.FP64, 1e-12), (B.FP32, 1e-6), (B.BF16X3, 1e-6)])
 def test_fkpp_advance_small(prec, tol):
     g, ctx = pair(24, 16, 8, 4.0, lz=2 * np.pi * 8, policy="twothirds", precision=prec)
     r, phi, z = g.nodes3()
@@ -112,7 +112,7 @@ def test_advance_checkpoint_resume_bitwise():
     assert np.array_equal(a.cpu().numpy(), b2.cpu().numpy())
 
 
-@pytest.mark.parametrize("prec,tol", [(B.FP64, 1e-12), (B.FP32, 1e-6)])
+@pytest.mark.parametrize("prec,tol", [(B.FP64, 1e-12), (B.FP32, 1e-6), (B.BF16X3, 1e-6)])
 def test_fkpp_full_size_sampled(prec, tol):
     # The benchmarked 3-D Fisher-KPP workload at full size (Nr = Nphi = 128,
     # Nz = 64, ell = 4, Lz = 2 pi 8, two-thirds chops, dt = 1e-2), in the launch
@@ -122,7 +122,7 @@ def test_fkpp_full_size_sampled(prec, tol):
     g, ctx = pair(nr, nphi, nz, ell, lz=lz, policy="twothirds", precision=prec)
     r, phi, z = g.nodes3()
     u0 = W.fkpp_seed(r, phi, z)
-    if prec == B.FP32:
+    if prec != B.FP64:
         u0 = u0.astype(np.float32).astype(np.float64)
     import torch
     state = ctx.forward(torch.as_tensor(u0, dtype=ctx.phys_dtype).cuda(), ctx.new_spec())
