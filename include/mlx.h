@@ -123,6 +123,22 @@ int mlx_get_nodes(const mlx_ctx* ctx, double* x, double* w, double* r);
  * device, n_spec complex128.  Asynchronous on `stream`. */
 int mlx_forward(mlx_ctx* ctx, const void* phys, void* spec, mlx_stream stream);
 
+/* Allocation-free forward transform.  The paper has no counterpart: this entry
+ * point exists for callers that cannot call cudaMalloc when they transform (code
+ * running inside another framework's CUDA-graph capture, or hosts that freeze
+ * their device-memory budget after start-up).  Same arguments, layouts and result
+ * as mlx_forward, but the intermediate Fourier planes live in a fixed 16 MiB
+ * device array built into the library (present on every GPU that loads it, until
+ * exit) instead of the context's workspace; no device memory is allocated or
+ * freed.  Grids whose intermediates exceed 16 MiB
+ * (element size x 2 x (K M Nr + Nz M Nr when Nz > 1)) are rejected with
+ * MLX_EINVAL and a message in mlx_last_cuda_error.  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress) with that device
+ * current; make it before any stream capture.  All calls on a device share the
+ * array: calls whose GPU work overlaps (other streams, other contexts) race, so
+ * serialise them. */
+int mlx_forward_noalloc(mlx_ctx* ctx, const void* phys, void* spec, mlx_stream stream);
+
 /* Backward transform (spectral -> physical): Eq. (2) summed at the nodes,
  * s = Re sum_k f_0k e^{i kappa z} + 2 Re sum_{m>=1,k} f_mk e^{i(m phi + kappa z)}. */
 int mlx_backward(mlx_ctx* ctx, const void* spec, void* phys, mlx_stream stream);

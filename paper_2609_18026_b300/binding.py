@@ -23,7 +23,7 @@ EXPORTS = ("mlx_strerror", "mlx_last_cuda_error", "mlx_create", "mlx_destroy", "
            "mlx_get_nodes", "mlx_forward", "mlx_backward", "mlx_nonlinear",
            "mlx_implicit_setup", "mlx_implicit_solve", "mlx_advance",
            "mlx_timing", "mlx_timing_read", "mlx_kernel_count", "mlx_kernel_name",
-           "mlx_set_tuning", "mlx_device_status")
+           "mlx_set_tuning", "mlx_device_status", "mlx_forward_noalloc")
 
 
 class MlxError(RuntimeError):
@@ -78,6 +78,7 @@ def load():
     lib.mlx_kernel_count.argtypes = []
     lib.mlx_set_tuning.argtypes = [vp, ctypes.c_char_p, i]
     lib.mlx_device_status.argtypes = [vp]
+    lib.mlx_forward_noalloc.argtypes = [vp, vp, vp, vp]
     lib.mlx_kernel_name.argtypes = [i]
     lib.mlx_kernel_name.restype = ctypes.c_char_p
     for name in EXPORTS:
