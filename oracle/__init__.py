@@ -35,3 +35,4 @@ from .operators import (del2h_closed, del2h_quadrature, rdr_matrix,  # noqa: F40
                         linear_operator)
 from .integrate import Stepper, fkpp_nonlinear  # noqa: F401
 from .diagnostics import weighted_l2, circulation, second_moment  # noqa: F401
+from .vortex import VortexOps, vortex_nonlinear  # noqa: F401

@@ -60,8 +60,10 @@ class Stepper:
         return self.nonlinear(s)
 
     def _solve(self, lus, rhs):
+        # a state may hold several fields: block j belongs to order m = j mod M
         out = []
-        for m, blk in enumerate(rhs):
+        for j, blk in enumerate(rhs):
+            m = j % self.g.M
             res = np.empty_like(blk)
             for kidx in range(self.g.K):
                 lu = lus[(m, self._kabs(kidx))]
@@ -73,7 +75,8 @@ class Stepper:
 
     def apply_L(self, s):
         out = []
-        for m, blk in enumerate(s):
+        for j, blk in enumerate(s):
+            m = j % self.g.M
             res = np.empty_like(blk)
             for kidx in range(self.g.K):
                 res[kidx] = self.L[(m, self._kabs(kidx))] @ blk[kidx]
