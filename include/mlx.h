@@ -69,8 +69,14 @@ enum { MLX_FP64 = 0, MLX_FP32 = 1, MLX_BF16X3 = 2 };
  * Sec. 3.3 realised as storage truncation.  Nc = Nr unless nr_c is given. */
 enum { MLX_CHOP_LINEAR = 0, MLX_CHOP_TWOTHIRDS = 1 };
 
-/* Nonlinear term kinds for mlx_nonlinear / mlx_advance. */
-enum { MLX_NONLIN_NONE = 0, MLX_NONLIN_FKPP = 1 };
+/* Nonlinear term kinds for mlx_nonlinear / mlx_advance.
+ *   MLX_NONLIN_FKPP:   one scalar, A = gamma u (1 - u) (Eq. (17)); coeffs[0] = gamma.
+ *   MLX_NONLIN_VORTEX: the toroidal-poloidal pair (psi, chi) of Eq. (8), stored as
+ *                      two consecutive spectral fields (2 n_spec complex128),
+ *                      A = P[(U + v) x omega] (Eq. (19)) with the uniform
+ *                      background U = coeffs[0] e_y (moving frame, Sec. 5.3).
+ *                      Needs mlx_vortex_setup. */
+enum { MLX_NONLIN_NONE = 0, MLX_NONLIN_FKPP = 1, MLX_NONLIN_VORTEX = 2 };
 
 /* Implicit step kinds for mlx_implicit_solve. */
 enum { MLX_STEP_FEBE_HALF = 0, MLX_STEP_FEBE_FULL = 1, MLX_STEP_ABCN = 2 };
@@ -143,12 +149,33 @@ int mlx_forward_noalloc(mlx_ctx* ctx, const void* phys, void* spec, mlx_stream s
  * s = Re sum_k f_0k e^{i kappa z} + 2 Re sum_{m>=1,k} f_mk e^{i(m phi + kappa z)}. */
 int mlx_backward(mlx_ctx* ctx, const void* spec, void* phys, mlx_stream stream);
 
-/* Nonlinear term A(s) of Eq. (10) in spectral space (one backward and one
- * forward transform with the pointwise product between them, Sec. 3.3):
+/* Nonlinear term A(s) of Eq. (10) in spectral space (transforms with the
+ * pointwise products between them, Sec. 3.3):
  *   MLX_NONLIN_FKPP: A = gamma u (1 - u), Eq. (17); coeffs[0] = gamma.
- * spec_in, spec_out: device complex128 ragged (may not alias). */
+ *   MLX_NONLIN_VORTEX: (psi_N, chi_N) = P[(U + v) x omega], Eq. (19): velocity
+ *     and vorticity from (psi, chi) with the banded r d/dr and D_m (six backward
+ *     transforms), the cross product at the nodes, three forward transforms,
+ *     r^2 curl_z and r^2 div_h in spectral space (two backward, 1/r^2, two
+ *     forward), then psi_N = -D_m^{-1} (curl N)_z, g = (D_m - kappa^2)^{-1} div N,
+ *     chi_N = -D_m^{-1} (N_z - i kappa g).  At m = 0 the singular row of D_m is
+ *     the far-field decay condition sum_n Pbar_n^0(1) s_n = 0 (zero net
+ *     circulation, log-proxy coefficient 0, Sec. 3.1).  coeffs[0] = U0.
+ * spec_in, spec_out: device complex128 ragged (may not alias); two fields each
+ * for the vortex kind. */
 int mlx_nonlinear(mlx_ctx* ctx, int kind, const double* coeffs, int ncoeffs,
                   const void* spec_in, void* spec_out, mlx_stream stream);
+
+/* Build the horizontal-Laplacian (D_m, decay row at m = 0) and Helmholtz
+ * (D_m - kappa^2) band factors, the r d/dr band and the workspace of the vortex
+ * term (Sec. 3.2).  Required before MLX_NONLIN_VORTEX and mlx_lap_h_solve.
+ * Synchronises `stream`. */
+int mlx_vortex_setup(mlx_ctx* ctx, mlx_stream stream);
+
+/* Solve grad_h^2 x = rhs harmonic by harmonic (Eq. (9)'s inverse Laplacian):
+ * D_m x = rhs with the far-field decay condition in place of the singular first
+ * equation at m = 0 (rhs's m = 0, n = 0 entries are not used).  FP64, device
+ * complex128 ragged buffers (may not alias).  MLX_ESTATE before mlx_vortex_setup. */
+int mlx_lap_h_solve(mlx_ctx* ctx, const void* rhs, void* out, mlx_stream stream);
 
 /* Set up the implicit operators for time step dt: per harmonic (m, |k|) the
  * band matrix of L = nu (D_m - kappa^2) - nu_h (-(D_m - kappa^2))^{p/2}
@@ -169,8 +196,10 @@ int mlx_implicit_solve(mlx_ctx* ctx, int step, const void* s, const void* A,
                        const void* A_prev, void* out, mlx_stream stream);
 
 /* Advance `nsteps` time steps of AB-CN (Eq. (12)) with the nonlinear term
- * `kind`, in place on `state` (device complex128 ragged).  prev_A (device,
- * n_spec complex128) holds A^{j-1} between calls.  If start != 0 the first step
+ * `kind`, in place on `state` (device complex128 ragged; two fields for the
+ * vortex kind, each advanced with the same implicit operator since the
+ * projection commutes with the Laplacian, Sec. 3.2).  prev_A (device, same size
+ * as state) holds A^{j-1} between calls.  If start != 0 the first step
  * is the Richardson start s^1 = 2 FEBE_{dt/2}(FEBE_{dt/2}(s^0)) - FEBE_dt(s^0)
  * and prev_A is overwritten with A(s^0); otherwise prev_A must hold A^{j-1}.
  * One step is captured once per (state, prev_A) pair into a CUDA graph and

@@ -3,9 +3,19 @@
 Sec. 3.2 and Eq. (19): a solenoidal field V = curl(psi e_z) + curl curl(chi e_z)
 (Eq. (8)) evolves as d(psi, chi)/dt = P[(U + v) x omega] + L(psi, chi), with P the
 toroidal-poloidal projection recovered from Eq. (9).  The paper does not spell out
-how the vector components are transformed; the reading taken (identical in the
-oracle and the CUDA path) works harmonic by harmonic, e^{i(m phi + kappa z)}, with
-the banded r d/dr (R) and horizontal Laplacian (D_m) of Sec. 3.1:
+how the vector components are transformed or how P is evaluated; the reading
+taken here (identical in the oracle and the CUDA path) works harmonic by harmonic,
+e^{i(m phi + kappa z)}, with banded coefficient-space operators only and never
+divides by r at the nodes (division by r^2 near the axis would amplify transform
+round-off by 1/r_min^2).
+
+Operators on the orthonormal coefficients of order m (n = m..Nc-1):
+  R  = r d/dr (tridiagonal, Sec. 3.1),  D_m = horizontal Laplacian (Eq. (5)),
+  J  = multiplication by x (the Jacobi matrix: x Pbar_n = a_{n+1} Pbar_{n+1} + a_n Pbar_{n-1},
+       a_n = sqrt((n^2 - m^2)/(4 n^2 - 1))),
+  Q  = r^2 grad_h^2 = (I - J^2) diag(-n(n+1))   (from Eq. (3): r^2 grad_h^2 Pbar_n = -n(n+1)(1-x^2) Pbar_n),
+  and (1 - x) r^2 = ell^2 (1 + x) (Eq. (1)).
+All products of truncated matrices (truncate, then compose).
 
 velocity (from Eq. (8))      r v_r   = i m psi + i kappa R chi
                              r v_phi = -R psi - m kappa chi
@@ -16,27 +26,30 @@ vorticity (curl of Eq. (8):  omega = curl(Psi e_z) + curl curl(psi e_z),
                              r w_phi = -R Psi - m kappa psi
                              w_z     = -D_m psi
 At the nodes (six backward transforms): N = (v + U) x omega with the uniform
-background U = U0 e_y (U_r = U0 sin phi, U_phi = U0 cos phi; Sec. 5.3 moving frame),
+background U = U0 e_y (U_r = U0 sin phi, U_phi = U0 cos phi; Sec. 5.3 moving frame):
     A = r N_phi = v_z (r w_r) - (r v_r + r U_r) w_z
     B = r N_r   = (r v_phi + r U_phi) w_z - v_z (r w_phi)
-    N_z = [(r v_r + r U_r)(r w_phi) - (r v_phi + r U_phi)(r w_r)] / r^2
-Three forward transforms, then in spectral space
-    X1 = R A - i m B   (= r^2 (curl N)_z),     X2 = R B + i m A   (= r^2 div_h N)
-two backward transforms, division by r^2 at the nodes, two forward transforms give
-(curl N)_z and div_h N; div N = div_h N + i kappa N_z.  Projection (Eq. (9) applied
-to the solenoidal part of N = curl(psi_N e_z) + curl curl(chi_N e_z) + grad g):
-    psi_N = -D_m^{-1} (curl N)_z
-    g     = (D_m - kappa^2)^{-1} div N                  (k != 0)
-    chi_N = -D_m^{-1} (N_z - i kappa g)                 (N_z alone when k == 0)
-D_m is singular at m = 0 (the constant has zero Laplacian); there the first row is
-replaced by the far-field decay condition sum_n Pbar_n^0(1) s_n = 0 with right-hand
-side 0 (log-proxy coefficient c = 0, Sec. 3.1 / Eq. (6): exact for the zero-net-
-circulation vortex pair).
+    C = r^2 N_z = (r v_r + r U_r)(r w_phi) - (r v_phi + r U_phi)(r w_r)
+Three forward transforms, then in coefficient space
+    X1 = R A - i m B   (= r^2 (curl N)_z),     X2 = R B + i m A   (= r^2 div_h N).
+Projection N = curl(psi_N e_z) + curl curl(chi_N e_z) + grad g (Eq. (9) for the
+solenoidal part; div N = lap g removes the gradient):
+    Q psi_N = -X1                                                   (lap_h psi_N = -(curl N)_z, times r^2)
+    [(I - J) Q - kappa^2 ell^2 (I + J)] g = (I - J)(X2 + i kappa C)   (k != 0; (lap_h - kappa^2) g = div N, times (1-x) r^2)
+    (I - J) Q chi_N = i kappa ell^2 (I + J) g - (I - J) C           (lap_h chi_N = i kappa g - N_z, times (1-x) r^2)
+(g = 0 at k = 0).  Q and (I - J) Q have a zero first column at m = 0 (the constant
+has zero Laplacian); there the first row is replaced by the far-field decay
+condition sum_n Pbar_n^0(1) s_n = 0 with right-hand side 0 (log-proxy coefficient
+c = 0, Sec. 3.1 / Eq. (6): exact for the zero-net-circulation vortex pair).
 
-Pins (tests/test_oracle_vortex.py): gradient fields project to zero; a solenoidal
-field built from known (psi, chi) projects back to them; an axisymmetric Lamb-Oseen
-vortex has a pure-gradient N so P(N) = 0; curl/divergence identities checked
-against analytic fields.  The full nonlinear evolution is checked against the
+The inverse horizontal Laplacian with the same decay row (lap_h_inv) gives the
+initial stream function psi = -lap_h^{-1} omega_z of a vortex workload.
+
+Pins (tests/test_oracle_vortex.py): J against Gauss quadrature of <Pbar_j, x Pbar_n>;
+Q against quadrature of <Pbar_j, r^2 lap_h Pbar_n>; gradient fields project to
+zero; a solenoidal field built from known (psi, chi) projects back to them; an
+axisymmetric vortex has a pure-gradient N so P(N) = 0; analytic curl fields; the
+decay-row Laplacian inverse.  The full nonlinear evolution is checked against the
 oracle only: parity unpinned beyond these properties.
 """
 
@@ -47,6 +60,19 @@ import scipy.linalg as sla
 
 from .operators import del2h_closed, rdr_matrix
 from .transform import backward, forward
+
+
+def jacobi_matrix(m, nc):
+    """Multiplication by x on the orthonormal order-m coefficients (tridiagonal),
+    from x Pbar_n^m = a_{n+1} Pbar_{n+1}^m + a_n Pbar_{n-1}^m, a_n = sqrt((n^2-m^2)/(4n^2-1))."""
+    N = nc - m
+    J = np.zeros((N, N))
+    for a in range(N - 1):
+        n = m + a + 1
+        v = math.sqrt((n * n - m * m) / (4.0 * n * n - 1.0))
+        J[a, a + 1] = v
+        J[a + 1, a] = v
+    return J
 
 
 def pbar_at_one(m, nc):
@@ -71,11 +97,31 @@ class VortexOps:
             if m == 0:
                 Dm[0, :] = pbar_at_one(0, g.nc)
             self.lu_h.append(sla.lu_factor(Dm))
-        self.lu_helm = {}
+        # banded projection operators
+        self.J, self.Q, self.H = [], [], []
+        self.lu_Q, self.lu_H = [], []
         for m in range(g.M):
+            J = jacobi_matrix(m, g.nc)
+            n = np.arange(m, g.nc, dtype=np.float64)
+            I = np.eye(g.nc - m)
+            Q = (I - J @ J) @ np.diag(-n * (n + 1.0))
+            H = (I - J) @ Q
+            self.J.append(J)
+            self.Q.append(Q)
+            self.H.append(H)
+            Qd, Hd = Q.copy(), H.copy()
+            if m == 0:
+                Qd[0, :] = pbar_at_one(0, g.nc)
+                Hd[0, :] = pbar_at_one(0, g.nc)
+            self.lu_Q.append(sla.lu_factor(Qd))
+            self.lu_H.append(sla.lu_factor(Hd))
+        self.lu_G = {}
+        for m in range(g.M):
+            I = np.eye(g.nc - m)
             for kabs in range(1, g.Kz):
                 kappa = 2.0 * math.pi * kabs / g.lz
-                self.lu_helm[(m, kabs)] = sla.lu_factor(self.D[m] - kappa * kappa * np.eye(g.nc - m))
+                G = self.H[m] - kappa * kappa * g.ell ** 2 * (I + self.J[m])
+                self.lu_G[(m, kabs)] = sla.lu_factor(G)
 
     def kappa(self, kidx):
         return float(self.g.kappa[kidx])
@@ -89,10 +135,15 @@ class VortexOps:
         xi = sla.lu_solve(self.lu_h[m], b.imag)
         return xr + 1j * xi
 
-    def helm_inv(self, m, kidx, rhs):
-        kabs = abs(int(self.g.kz[kidx]))
-        lu = self.lu_helm[(m, kabs)]
+    @staticmethod
+    def _csolve(lu, rhs):
         return sla.lu_solve(lu, rhs.real) + 1j * sla.lu_solve(lu, rhs.imag)
+
+    def _decay_solve(self, lu, m, rhs):
+        b = np.array(rhs, dtype=np.complex128)
+        if m == 0:
+            b[0] = 0.0
+        return self._csolve(lu, b)
 
     def fields(self, psi, chi):
         """Spectral (r v_r, r v_phi, v_z, r w_r, r w_phi, w_z) from (psi, chi)."""
@@ -116,36 +167,37 @@ class VortexOps:
                 out[f][m] = v
         return out
 
-    def project(self, A, Bf, Nz):
-        """P of the field with spectral r N_phi = A, r N_r = B, N_z = Nz."""
+    def project(self, A, Bf, C):
+        """P of the field with spectral r N_phi = A, r N_r = B, r^2 N_z = C."""
         g = self.g
-        X1, X2 = [], []
-        for m in range(g.M):
-            R = self.R[m]
-            X1.append(np.stack([R @ A[m][kk] - 1j * m * Bf[m][kk] for kk in range(g.K)]))
-            X2.append(np.stack([R @ Bf[m][kk] + 1j * m * A[m][kk] for kk in range(g.K)]))
-        inv_r2 = (1.0 / g.r ** 2)[None, None, :]
-        curlz = forward(g, backward(g, X1) * inv_r2)
-        divh = forward(g, backward(g, X2) * inv_r2)
         psiN, chiN = [], []
         for m in range(g.M):
+            R, J = self.R[m], self.J[m]
+            I = np.eye(g.nc - m)
             pb = np.empty((g.K, g.nc - m), dtype=np.complex128)
             cb = np.empty_like(pb)
             for kk in range(g.K):
                 kap = self.kappa(kk)
-                pb[kk] = -self.lap_h_inv(m, curlz[m][kk])
+                X1 = R @ A[m][kk] - 1j * m * Bf[m][kk]
+                X2 = R @ Bf[m][kk] + 1j * m * A[m][kk]
+                pb[kk] = self._decay_solve(self.lu_Q[m], m, -X1)
                 if g.kz[kk] != 0:
-                    divN = divh[m][kk] + 1j * kap * Nz[m][kk]
-                    gg = self.helm_inv(m, kk, divN)
-                    cb[kk] = -self.lap_h_inv(m, Nz[m][kk] - 1j * kap * gg)
+                    kabs = abs(int(g.kz[kk]))
+                    gg = self._csolve(self.lu_G[(m, kabs)], (I - J) @ (X2 + 1j * kap * C[m][kk]))
+                    rhs = 1j * kap * g.ell ** 2 * ((I + J) @ gg) - (I - J) @ C[m][kk]
                 else:
-                    cb[kk] = -self.lap_h_inv(m, Nz[m][kk])
+                    rhs = -((I - J) @ C[m][kk])
+                cb[kk] = self._decay_solve(self.lu_H[m], m, rhs)
             psiN.append(pb)
             chiN.append(cb)
         return psiN, chiN
 
     def nonlinear(self, psi, chi, U0=0.0):
         """P[(U + v) x omega] for the state (psi, chi)."""
+        return self.project(*self.products(psi, chi, U0))
+
+    def products(self, psi, chi, U0=0.0):
+        """Spectral (A, B, C) = (r N_phi, r N_r, r^2 N_z) of N = (U + v) x omega."""
         g = self.g
         sf = self.fields(psi, chi)
         rvr, rvp, vz, rwr, rwp, wz = (backward(g, f) for f in sf)
@@ -157,8 +209,8 @@ class VortexOps:
         ap = rvp + rUp
         A = vz * rwr - ar * wz
         Bn = ap * wz - vz * rwp
-        Nz = (ar * rwp - ap * rwr) / (r * r)
-        return self.project(forward(g, A), forward(g, Bn), forward(g, Nz))
+        C = ar * rwp - ap * rwr
+        return forward(g, A), forward(g, Bn), forward(g, C)
 
 
 def vortex_nonlinear(g, U0=0.0):

@@ -15,7 +15,7 @@ LIB_PATH = os.path.join(HERE, "libmlx.so")
 
 FP64, FP32, BF16X3 = 0, 1, 2
 CHOP_LINEAR, CHOP_TWOTHIRDS = 0, 1
-NONLIN_NONE, NONLIN_FKPP = 0, 1
+NONLIN_NONE, NONLIN_FKPP, NONLIN_VORTEX = 0, 1, 2
 STEP_FEBE_HALF, STEP_FEBE_FULL, STEP_ABCN = 0, 1, 2
 
 # Entry points declared in include/mlx.h (checked by the CPU test suite).
@@ -23,7 +23,8 @@ EXPORTS = ("mlx_strerror", "mlx_last_cuda_error", "mlx_create", "mlx_destroy", "
            "mlx_get_nodes", "mlx_forward", "mlx_backward", "mlx_nonlinear",
            "mlx_implicit_setup", "mlx_implicit_solve", "mlx_advance",
            "mlx_timing", "mlx_timing_read", "mlx_kernel_count", "mlx_kernel_name",
-           "mlx_set_tuning", "mlx_device_status", "mlx_forward_noalloc")
+           "mlx_set_tuning", "mlx_device_status", "mlx_forward_noalloc",
+           "mlx_vortex_setup", "mlx_lap_h_solve")
 
 
 class MlxError(RuntimeError):
@@ -79,6 +80,8 @@ def load():
     lib.mlx_set_tuning.argtypes = [vp, ctypes.c_char_p, i]
     lib.mlx_device_status.argtypes = [vp]
     lib.mlx_forward_noalloc.argtypes = [vp, vp, vp, vp]
+    lib.mlx_vortex_setup.argtypes = [vp, vp]
+    lib.mlx_lap_h_solve.argtypes = [vp, vp, vp, vp]
     lib.mlx_kernel_name.argtypes = [i]
     lib.mlx_kernel_name.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -196,6 +199,13 @@ class Context:
 
     def set_tuning(self, key, value):
         self._check(self.lib.mlx_set_tuning(self._h, key.encode(), int(value)))
+
+    def vortex_setup(self, stream=None):
+        self._check(self.lib.mlx_vortex_setup(self._h, _stream(stream)))
+
+    def lap_h_solve(self, rhs, out, stream=None):
+        self._check(self.lib.mlx_lap_h_solve(self._h, _ptr(rhs), _ptr(out), _stream(stream)))
+        return out
 
     def timing(self, enable):
         self._check(self.lib.mlx_timing(self._h, int(bool(enable))))

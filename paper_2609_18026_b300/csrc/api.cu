@@ -23,7 +23,12 @@ void free_ctx(mlx_ctx* c) {
                   c->d_spec1, c->d_spec2, c->d_spec3, c->d_band_off, c->d_Bplus,
                   c->lu_half.U, c->lu_half.L, c->lu_half.piv, c->lu_half.invd,
                   c->lu_full.U, c->lu_full.L, c->lu_full.piv, c->lu_full.invd,
-                  c->d_Wb, c->d_Pb, c->d_arowW, c->d_arowP, c->d_tc_fwd, c->d_tc_bwd, c->d_err};
+                  c->d_Wb, c->d_Pb, c->d_arowW, c->d_arowP, c->d_tc_fwd, c->d_tc_bwd, c->d_err,
+                  c->lu_lap.U, c->lu_lap.L, c->lu_lap.piv, c->lu_lap.invd,
+                  c->lu_helm.U, c->lu_helm.L, c->lu_helm.piv, c->lu_helm.invd, c->d_lap_off,
+                  c->d_rdr, c->d_vspec, c->d_vphys,
+                  c->lu_Q.U, c->lu_Q.L, c->lu_Q.piv, c->lu_Q.invd, c->lu_H.U, c->lu_H.L, c->lu_H.piv,
+                  c->lu_H.invd, c->lu_G.U, c->lu_G.L, c->lu_G.piv, c->lu_G.invd};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
@@ -49,6 +54,7 @@ int nonlinear_into(mlx_ctx* c, int kind, double c0, const double2* s, double2* A
     MLX_CUDA_TRY(c, cudaMemsetAsync(A, 0, sizeof(double2) * c->n_spec, st));
     return MLX_OK;
   }
+  if (kind == MLX_NONLIN_VORTEX) return mlx_vortex_nonlinear(c, c0, s, A, st);
   int rc = mlx_legendre_backward(c, s, st);
   if (rc) return rc;
   rc = mlx_fft_fkpp(c, c0, st);
@@ -59,11 +65,24 @@ int nonlinear_into(mlx_ctx* c, int kind, double c0, const double2* s, double2* A
 // One AB-CN step: A^j = A(s) into Anew, then (I - dt/2 L) out = (I + dt/2 L) s
 // + dt/2 (3 A^j - A^{j-1}).
 
+int nfields(int kind) { return kind == MLX_NONLIN_VORTEX ? 2 : 1; }
+
+// implicit step applied to every field of the state (fields share the factors)
+int solve_fields(mlx_ctx* c, int kind, int step, const double2* s, const double2* A, const double2* Ap,
+                 double2* out, cudaStream_t st) {
+  for (int f = 0; f < nfields(kind); ++f) {
+    const long long o = (long long)f * c->n_spec;
+    int rc = mlx_band_solve(c, step, s + o, A ? A + o : nullptr, Ap ? Ap + o : nullptr, out + o, st);
+    if (rc) return rc;
+  }
+  return MLX_OK;
+}
+
 int abcn_step(mlx_ctx* c, int kind, double c0, const double2* s, double2* Anew,
               const double2* Aprev, double2* out, cudaStream_t st) {
   int rc = nonlinear_into(c, kind, c0, s, Anew, st);
   if (rc) return rc;
-  return mlx_band_solve(c, MLX_STEP_ABCN, s, Anew, Aprev, out, st);
+  return solve_fields(c, kind, MLX_STEP_ABCN, s, Anew, Aprev, out, st);
 }
 
 }  // namespace
@@ -234,8 +253,9 @@ int mlx_nonlinear(mlx_ctx* c, int kind, const double* coeffs, int ncoeffs, const
                   void* spec_out, mlx_stream stream) {
   if (!c || !spec_in || !spec_out || spec_in == spec_out) return MLX_EINVAL;
   if (!aligned16(spec_in) || !aligned16(spec_out)) return MLX_EINVAL;
-  if (kind == MLX_NONLIN_FKPP && (!coeffs || ncoeffs < 1)) return MLX_EINVAL;
-  if (kind != MLX_NONLIN_FKPP && kind != MLX_NONLIN_NONE) return MLX_EINVAL;
+  if ((kind == MLX_NONLIN_FKPP || kind == MLX_NONLIN_VORTEX) && (!coeffs || ncoeffs < 1)) return MLX_EINVAL;
+  if (kind != MLX_NONLIN_FKPP && kind != MLX_NONLIN_NONE && kind != MLX_NONLIN_VORTEX) return MLX_EINVAL;
+  if (kind == MLX_NONLIN_VORTEX && !c->vortex_ready) return MLX_ESTATE;
   return nonlinear_into(c, kind, coeffs ? coeffs[0] : 0.0, (const double2*)spec_in,
                         (double2*)spec_out, (cudaStream_t)stream);
 }
@@ -268,9 +288,11 @@ int mlx_advance(mlx_ctx* c, int kind, const double* coeffs, int ncoeffs, void* s
                 int nsteps, int start, mlx_stream stream) {
   if (!c || !state || !prev_A || nsteps < 0 || state == prev_A) return MLX_EINVAL;
   if (!aligned16(state) || !aligned16(prev_A)) return MLX_EINVAL;
-  if (kind != MLX_NONLIN_NONE && kind != MLX_NONLIN_FKPP) return MLX_EINVAL;
-  if (kind == MLX_NONLIN_FKPP && (!coeffs || ncoeffs < 1)) return MLX_EINVAL;
+  if (kind != MLX_NONLIN_NONE && kind != MLX_NONLIN_FKPP && kind != MLX_NONLIN_VORTEX) return MLX_EINVAL;
+  if ((kind == MLX_NONLIN_FKPP || kind == MLX_NONLIN_VORTEX) && (!coeffs || ncoeffs < 1)) return MLX_EINVAL;
   if (!c->implicit_ready) return MLX_ESTATE;
+  if (kind == MLX_NONLIN_VORTEX && !c->vortex_ready) return MLX_ESTATE;
+  const long long nst = (long long)nfields(kind) * c->n_spec;
   if (nsteps == 0) return MLX_OK;
   cudaStream_t st = (cudaStream_t)stream;
   const double c0 = coeffs ? coeffs[0] : 0.0;
@@ -280,11 +302,11 @@ int mlx_advance(mlx_ctx* c, int kind, const double* coeffs, int ncoeffs, void* s
   if (start) {
     // Richardson start: s1 = 2 FEBE_{dt/2}(FEBE_{dt/2}(s0)) - FEBE_dt(s0); A^0 kept.
     if ((rc = nonlinear_into(c, kind, c0, s, Ap, st))) return rc;
-    if ((rc = mlx_band_solve(c, MLX_STEP_FEBE_HALF, s, Ap, nullptr, c->d_spec1, st))) return rc;
+    if ((rc = solve_fields(c, kind, MLX_STEP_FEBE_HALF, s, Ap, nullptr, c->d_spec1, st))) return rc;
     if ((rc = nonlinear_into(c, kind, c0, c->d_spec1, c->d_specA, st))) return rc;
-    if ((rc = mlx_band_solve(c, MLX_STEP_FEBE_HALF, c->d_spec1, c->d_specA, nullptr, c->d_spec2, st))) return rc;
-    if ((rc = mlx_band_solve(c, MLX_STEP_FEBE_FULL, s, Ap, nullptr, c->d_spec3, st))) return rc;
-    if ((rc = mlx_spec_axpby(c, 2.0, c->d_spec2, -1.0, c->d_spec3, s, st))) return rc;
+    if ((rc = solve_fields(c, kind, MLX_STEP_FEBE_HALF, c->d_spec1, c->d_specA, nullptr, c->d_spec2, st))) return rc;
+    if ((rc = solve_fields(c, kind, MLX_STEP_FEBE_FULL, s, Ap, nullptr, c->d_spec3, st))) return rc;
+    if ((rc = mlx_spec_axpby(c, 2.0, c->d_spec2, -1.0, c->d_spec3, s, st, nst))) return rc;
     --nsteps;
   }
   const int pairs = nsteps / 2;
@@ -319,10 +341,22 @@ int mlx_advance(mlx_ctx* c, int kind, const double* coeffs, int ncoeffs, void* s
   }
   if (nsteps % 2) {
     if ((rc = abcn_step(c, kind, c0, s, c->d_specA, Ap, c->d_spec1, st))) return rc;
-    MLX_CUDA_TRY(c, cudaMemcpyAsync(s, c->d_spec1, sizeof(double2) * c->n_spec, cudaMemcpyDeviceToDevice, st));
-    MLX_CUDA_TRY(c, cudaMemcpyAsync(Ap, c->d_specA, sizeof(double2) * c->n_spec, cudaMemcpyDeviceToDevice, st));
+    MLX_CUDA_TRY(c, cudaMemcpyAsync(s, c->d_spec1, sizeof(double2) * nst, cudaMemcpyDeviceToDevice, st));
+    MLX_CUDA_TRY(c, cudaMemcpyAsync(Ap, c->d_specA, sizeof(double2) * nst, cudaMemcpyDeviceToDevice, st));
   }
   return MLX_OK;
+}
+
+int mlx_vortex_setup(mlx_ctx* c, mlx_stream stream) {
+  if (!c) return MLX_EINVAL;
+  return mlx_vortex_prepare(c, (cudaStream_t)stream);
+}
+
+int mlx_lap_h_solve(mlx_ctx* c, const void* rhs, void* out, mlx_stream stream) {
+  if (!c || !rhs || !out || rhs == out) return MLX_EINVAL;
+  if (!aligned16(rhs) || !aligned16(out)) return MLX_EINVAL;
+  if (!c->lap_ready) return MLX_ESTATE;
+  return mlx_lap_solve(c, 0, (const double2*)rhs, (double2*)out, (cudaStream_t)stream);
 }
 
 int mlx_set_tuning(mlx_ctx* c, const char* key, int value) {

@@ -87,11 +87,12 @@ __device__ void build_L(int m, int N, double kappa2, double nu, double nu_h, int
   for (long long t = 0; t < (long long)N * W; ++t) Lb[t] -= nu_h * T1[t];
 }
 
-// Banded LU with partial pivoting of A = I - c L.  work: [N][3kl+1] row windows
-// (column j of row i at slot j - i + kl).  Factor row i is stored at row index
-// i * rs of U / Lm / piv / invd (rs = Kz: systems of one m are interleaved by |k|).
-__device__ void band_lu(int N, int kl, double c, const double* Lb, double* work, double* U,
-                        double* Lm, int* piv, double* invd, int rs) {
+// Banded LU with partial pivoting of A = alpha I + beta Lb.  work: [N][3kl+1] row
+// windows (column j of row i at slot j - i + kl).  Factor row i is stored at row
+// index i * rs of U / Lm / piv / invd (rs = Kz: systems of one m are interleaved by
+// |k|; rs = 1 for the kappa-independent Laplacian factors).
+__device__ void band_lu(int N, int kl, double alpha, double beta, const double* Lb, double* work,
+                        double* U, double* Lm, int* piv, double* invd, int rs) {
   const int W = 2 * kl + 1;     // band of L
   const int WW = 3 * kl + 1;    // window: columns i-kl .. i+2kl
   for (long long t = 0; t < (long long)N * WW; ++t) work[t] = 0.0;
@@ -99,8 +100,8 @@ __device__ void band_lu(int N, int kl, double c, const double* Lb, double* work,
     for (int o = -kl; o <= kl; ++o) {
       const int j = i + o;
       if (j < 0 || j >= N) continue;
-      double v = -c * Lb[i * W + o + kl];
-      if (o == 0) v += 1.0;
+      double v = beta * Lb[i * W + o + kl];
+      if (o == 0) v += alpha;
       work[i * WW + o + kl] = v;
     }
   for (int j = 0; j < N; ++j) {
@@ -170,8 +171,111 @@ __global__ void k_band_setup(int M, int nc, int Kz, double lz, const long long* 
       if (o == kl) v += 1.0;
       Bplus[(row0 + (long long)i * Kz) * W + o] = v;
     }
-  band_lu(N, kl, 0.5 * dt, Lb, work, Uh + row0 * W, Lh + row0 * kl, Ph + row0, Dh + row0, Kz);
-  band_lu(N, kl, dt, Lb, work, Uf + row0 * W, Lf + row0 * kl, Pf + row0, Df + row0, Kz);
+  band_lu(N, kl, 1.0, -0.5 * dt, Lb, work, Uh + row0 * W, Lh + row0 * kl, Ph + row0, Dh + row0, Kz);
+  band_lu(N, kl, 1.0, -dt, Lb, work, Uf + row0 * W, Lf + row0 * kl, Pf + row0, Df + row0, Kz);
+}
+
+// Factors of the horizontal Laplacian D_m (family "lap", one system per m) and of
+// the Helmholtz operator D_m - kappa^2 (family "helm", per (m, |k|)), both with
+// half bandwidth 2.  At m = 0 the Laplacian is singular (its column 0 vanishes:
+// the constant has zero Laplacian); its system drops row and column 0 and the
+// solve recovers x_0 from the far-field decay condition.
+__global__ void k_lap_setup(int M, int nc, int Kz, double lz, int helm, const long long* __restrict__ fac_off,
+                            const long long* __restrict__ lap_rows, const double* __restrict__ lap,
+                            double* __restrict__ U, double* __restrict__ Lm, int* __restrict__ piv,
+                            double* __restrict__ invd, double* __restrict__ scratch, long long stride) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  const int per_m = helm ? Kz : 1;
+  if (idx >= M * per_m) return;
+  const int m = idx / per_m, kabs = idx % per_m;
+  const int shift = (!helm && m == 0) ? 1 : 0;
+  const int N = nc - m - shift;
+  const int kl = 2, W = 5;
+  double* Lb = scratch + (long long)idx * stride;
+  double* work = Lb + (long long)nc * W;
+  const double* lm = lap + (lap_rows[m] + shift) * 5;
+  for (int i = 0; i < N; ++i)
+    for (int o = 0; o < W; ++o) {
+      const int j = i + o - kl;
+      Lb[i * W + o] = (j >= 0 && j < N) ? lm[i * 5 + o] : 0.0;
+    }
+  const double kappa = 2.0 * M_PI * kabs / lz;
+  const int rs = helm ? Kz : 1;
+  const long long row0 = fac_off[m] + (helm ? kabs : 0);
+  band_lu(N, kl, helm ? -kappa * kappa : 0.0, 1.0, Lb, work, U + row0 * W, Lm + row0 * kl, piv + row0,
+          invd + row0, rs);
+}
+
+// Projection operators of the vortex term on order-m coefficients, with
+// J = multiplication by x (J_{i,i+1} = J_{i+1,i} = e_i = a_{m+i+1},
+// a_n = sqrt((n^2 - m^2)/(4 n^2 - 1))) and d_i = -n(n+1):
+//   family 0: Q = (I - J^2) diag(d)            = r^2 lap_h        (per m, decay row at m = 0)
+//   family 1: H = (I - J) Q                    = (1 - x) r^2 lap_h (per m, decay row at m = 0)
+//   family 2: G = H - kappa^2 ell^2 (I + J)                        (per (m, |k|), |k| >= 1)
+// built as half-bandwidth-3 bands and factorised with partial pivoting.
+__device__ __forceinline__ double jac_e(int m, int i) {
+  const double n = (double)(m + i + 1), mm = (double)m;
+  return sqrt((n * n - mm * mm) / (4.0 * n * n - 1.0));
+}
+
+__global__ void k_proj_setup(int M, int nc, int Kz, double lz, double ell, int family,
+                             const long long* __restrict__ fac_off, double* __restrict__ U,
+                             double* __restrict__ Lm, int* __restrict__ piv, double* __restrict__ invd,
+                             double* __restrict__ scratch, long long stride) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  const int per_m = (family == 2) ? Kz : 1;
+  if (idx >= M * per_m) return;
+  const int m = idx / per_m, kabs = idx % per_m;
+  const int Nf = nc - m;                       // full system size
+  const int shift = (family < 2 && m == 0) ? 1 : 0;
+  const int N = Nf - shift;
+  constexpr int kl = 3, W = 7;
+  double* Qb = scratch + (long long)idx * stride;   // [Nf][W] full-size bands
+  double* Hb = Qb + (long long)Nf * W;
+  double* work = Hb + (long long)Nf * W;            // [Nf][3 kl + 1]
+  for (long long t = 0; t < (long long)Nf * W; ++t) { Qb[t] = 0.0; Hb[t] = 0.0; }
+  auto e = [&](int i) -> double { return (i >= 0 && i + 1 < Nf) ? jac_e(m, i) : 0.0; };
+  auto d = [&](int j) -> double { const double n = (double)(m + j); return -n * (n + 1.0); };
+  // Q[i][j] = (delta_ij - (J^2)_ij) d_j
+  for (int i = 0; i < Nf; ++i) {
+    const double j2d = e(i - 1) * e(i - 1) + e(i) * e(i);
+    Qb[i * W + kl] = (1.0 - j2d) * d(i);
+    if (i + 2 < Nf) Qb[i * W + kl + 2] = -e(i) * e(i + 1) * d(i + 2);
+    if (i - 2 >= 0) Qb[i * W + kl - 2] = -e(i - 1) * e(i - 2) * d(i - 2);
+  }
+  if (family >= 1) {
+    // H[i][j] = Q[i][j] - e_{i-1} Q[i-1][j] - e_i Q[i+1][j]
+    for (int i = 0; i < Nf; ++i)
+      for (int o = -kl; o <= kl; ++o) {
+        const int j = i + o;
+        if (j < 0 || j >= Nf) continue;
+        double v = (o >= -2 && o <= 2) ? Qb[i * W + kl + o] : 0.0;
+        if (i - 1 >= 0) { const int oo = j - (i - 1); if (oo >= -2 && oo <= 2) v -= e(i - 1) * Qb[(i - 1) * W + kl + oo]; }
+        if (i + 1 < Nf) { const int oo = j - (i + 1); if (oo >= -2 && oo <= 2) v -= e(i) * Qb[(i + 1) * W + kl + oo]; }
+        Hb[i * W + kl + o] = v;
+      }
+  }
+  double* src = (family == 0) ? Qb : Hb;
+  if (family == 2) {
+    const double kappa = 2.0 * M_PI * kabs / lz;
+    const double c = kappa * kappa * ell * ell;
+    for (int i = 0; i < Nf; ++i) {
+      src[i * W + kl] -= c;
+      if (i + 1 < Nf) src[i * W + kl + 1] -= c * e(i);
+      if (i - 1 >= 0) src[i * W + kl - 1] -= c * e(i - 1);
+    }
+    if (kabs == 0) {   // unused slot: keep it well defined (identity)
+      for (long long t = 0; t < (long long)Nf * W; ++t) src[t] = 0.0;
+      for (int i = 0; i < Nf; ++i) src[i * W + kl] = 1.0;
+    }
+  }
+  // drop row and column 0 at m = 0 for the decay-row families (column 0 is zero
+  // there): the band rows start one row later and band_lu skips entries that
+  // would reach column -1
+  const double* band = src + (long long)shift * W;
+  const int rs = (family == 2) ? Kz : 1;
+  const long long row0 = fac_off[m] + ((family == 2) ? kabs : 0);
+  band_lu(N, kl, 0.0, 1.0, band, work, U + row0 * W, Lm + row0 * kl, piv + row0, invd + row0, rs);
 }
 
 // Solve kernel.  The substitution is a sequential recurrence in the row index, and
@@ -199,7 +303,8 @@ struct SolveSmem {
 template <int KL>
 __global__ void k_band_solve(int M, int nc, int Kz, int K, int CPW, int groups_per_m, int step,
                              double dt, const long long* __restrict__ soff,
-                             const long long* __restrict__ band_off, const double* __restrict__ U,
+                             const long long* __restrict__ band_off, int kz_fac, int m0_shift,
+                             const double* __restrict__ U,
                              const double* __restrict__ Lm, const int* __restrict__ piv,
                              const double* __restrict__ invd, const double* __restrict__ s,
                              const double* __restrict__ A, const double* __restrict__ Ap,
@@ -213,7 +318,9 @@ __global__ void k_band_solve(int M, int nc, int Kz, int K, int CPW, int groups_p
   const int G = CPW / 4;
   const int k0 = (gw % groups_per_m) * G;
   const int gcnt = min(G, Kz - k0);
-  const int N = nc - m;
+  const int sh = (m == 0) ? m0_shift : 0;   // Laplacian at m = 0: unknowns n >= 1
+  const int Nm = nc - m;
+  const int N = Nm - sh;
   unsigned char* base = smem_raw + (size_t)wib * SolveSmem<KL>::per_warp(nc, CPW);
   double* Us = reinterpret_cast<double*>(base);              // [N][G][W]
   double* Ls = Us + (size_t)N * G * W;                       // [N][G][KL]
@@ -222,25 +329,26 @@ __global__ void k_band_solve(int M, int nc, int Kz, int K, int CPW, int groups_p
   int* Pi = reinterpret_cast<int*>(Y + (size_t)N * CPW);     // [N][G] pivot rows
   const long long fb = band_off[m];
   const long long sm = soff[m];
+  // factor row of (i, |k| = k0 + kk)
+  auto frow = [&](int i, int kk) -> long long {
+    return fb + (long long)i * kz_fac + (kz_fac == 1 ? 0 : k0 + kk);
+  };
 
   // stage factors with asynchronous copies (every lane keeps many in flight)
   for (int e = lane; e < N * gcnt * W; e += 32) {
     const int i = e / (gcnt * W), rem = e - i * gcnt * W;
     const int kk = rem / W, q = rem - kk * W;
-    const long long row = fb + (long long)i * Kz + k0 + kk;
-    cp_async8(Us + ((size_t)i * G + kk) * W + q, U + row * W + q);
+    cp_async8(Us + ((size_t)i * G + kk) * W + q, U + frow(i, kk) * W + q);
   }
   for (int e = lane; e < N * gcnt * KL; e += 32) {
     const int i = e / (gcnt * KL), rem = e - i * gcnt * KL;
     const int kk = rem / KL, q = rem - kk * KL;
-    const long long row = fb + (long long)i * Kz + k0 + kk;
-    cp_async8(Ls + ((size_t)i * G + kk) * KL + q, Lm + row * KL + q);
+    cp_async8(Ls + ((size_t)i * G + kk) * KL + q, Lm + frow(i, kk) * KL + q);
   }
   for (int e = lane; e < N * gcnt; e += 32) {
     const int i = e / gcnt, kk = e - i * gcnt;
-    const long long row = fb + (long long)i * Kz + k0 + kk;
-    cp_async8(Ds + (size_t)i * G + kk, invd + row);
-    cp_async4(Pi + (size_t)i * G + kk, piv + row);
+    cp_async8(Ds + (size_t)i * G + kk, invd + frow(i, kk));
+    cp_async4(Pi + (size_t)i * G + kk, piv + frow(i, kk));
   }
   cp_async_commit();
   // stage right-hand sides; chain c = kk * 4 + sgn * 2 + part
@@ -252,9 +360,11 @@ __global__ void k_band_solve(int M, int nc, int Kz, int K, int CPW, int groups_p
     const int kabs = k0 + kk;
     if (sgn && kabs == 0) continue;
     const int kidx = sgn ? K - kabs : kabs;
-    const long long o = 2 * (sm + (long long)kidx * N + i) + part;
+    const long long o = 2 * (sm + (long long)kidx * Nm + sh + i) + part;
     double r;
-    if (step == MLX_STEP_ABCN) {
+    if (step == MLX_STEP_PLAIN) {
+      r = s[o];
+    } else if (step == MLX_STEP_ABCN) {
       r = 2.0 * s[o];
       if (A) r += 1.5 * dt * A[o];
       if (Ap) r -= 0.5 * dt * Ap[o];
@@ -308,13 +418,23 @@ __global__ void k_band_solve(int M, int nc, int Kz, int K, int CPW, int groups_p
   }
   __syncwarp();
   (void)valid;
+  if (sh) {
+    // x_0 from the decay condition sum_n Pbar_n^0(1) x_n = 0, Pbar_n^0(1) = sqrt((2n+1)/2)
+    if (c < 4 * gcnt && valid) {
+      double acc = 0.0;
+      for (int i = 0; i < N; ++i) acc += sqrt((2.0 * (i + 1) + 1.0) * 0.5) * Y[(size_t)i * CPW + c];
+      const int kabs = k0 + kk;
+      const int kidx = sgn ? K - kabs : kabs;
+      out[2 * (sm + (long long)kidx * Nm) + part] = -acc / sqrt(0.5);
+    }
+  }
   for (int e = lane; e < N * 4 * gcnt; e += 32) {
     const int cc = e / N, i = e - cc * N;
     const int kq = cc >> 2, sg = (cc >> 1) & 1, pt = cc & 1;
     const int kabs = k0 + kq;
     if (sg && kabs == 0) continue;
     const int kidx = sg ? K - kabs : kabs;
-    const long long o = 2 * (sm + (long long)kidx * N + i) + pt;
+    const long long o = 2 * (sm + (long long)kidx * Nm + sh + i) + pt;
     double v = Y[(size_t)i * CPW + cc];
     if (step == MLX_STEP_ABCN) v -= s[o];
     out[o] = v;
@@ -374,8 +494,9 @@ int mlx_band_setup(mlx_ctx* c, cudaStream_t st) {
 }
 
 template <int KL>
-static int launch_solve(mlx_ctx* c, int step, const BandLU& f, const double2* s, const double2* A,
-                        const double2* Ap, double2* out, cudaStream_t st) {
+static int launch_solve(mlx_ctx* c, int step, const BandLU& f, const long long* fac_off, int kz_fac,
+                        int m0_shift, const double2* s, const double2* A, const double2* Ap, double2* out,
+                        cudaStream_t st) {
   // Chains per warp and warps per CTA are launch-shape parameters (measured best
   // at the 128x128x64 workload: 8 chains per warp, 1-4 warps per CTA).
   int CPW = c->solve_cpw;
@@ -388,8 +509,8 @@ static int launch_solve(mlx_ctx* c, int step, const BandLU& f, const double2* s,
   const int warps = c->M * gpm;
   const int blocks = (warps + WPB - 1) / WPB;
   k_band_solve<KL><<<blocks, 32 * WPB, pw * WPB, st>>>(
-      c->M, c->nc, c->Kz, c->K, CPW, gpm, step, c->dt, c->d_soff, c->d_band_off, f.U, f.L, f.piv,
-      f.invd, (const double*)s, (const double*)A, (const double*)Ap, (double*)out);
+      c->M, c->nc, c->Kz, c->K, CPW, gpm, step, c->dt, c->d_soff, fac_off, kz_fac, m0_shift, f.U, f.L,
+      f.piv, f.invd, (const double*)s, (const double*)A, (const double*)Ap, (double*)out);
   return MLX_OK;
 }
 
@@ -398,13 +519,103 @@ int mlx_band_solve(mlx_ctx* c, int step, const double2* s, const double2* A, con
   TimedLaunch tl(c, KID_BAND_SOLVE, st);
   const BandLU& f = (step == MLX_STEP_FEBE_FULL) ? c->lu_full : c->lu_half;
   int rc;
+  const long long* fo = c->d_band_off;
   switch (c->kl) {
-    case 2: rc = launch_solve<2>(c, step, f, s, A, Ap, out, st); break;
-    case 4: rc = launch_solve<4>(c, step, f, s, A, Ap, out, st); break;
-    case 6: rc = launch_solve<6>(c, step, f, s, A, Ap, out, st); break;
-    case 8: rc = launch_solve<8>(c, step, f, s, A, Ap, out, st); break;
+    case 2: rc = launch_solve<2>(c, step, f, fo, c->Kz, 0, s, A, Ap, out, st); break;
+    case 4: rc = launch_solve<4>(c, step, f, fo, c->Kz, 0, s, A, Ap, out, st); break;
+    case 6: rc = launch_solve<6>(c, step, f, fo, c->Kz, 0, s, A, Ap, out, st); break;
+    case 8: rc = launch_solve<8>(c, step, f, fo, c->Kz, 0, s, A, Ap, out, st); break;
     default: return MLX_EINVAL;
   }
+  if (rc) return rc;
+  MLX_LAUNCH_CHECK(c);
+  return MLX_OK;
+}
+
+// Laplacian-family factors (horizontal Laplacian per m, Helmholtz per (m, |k|)).
+int mlx_lap_setup(mlx_ctx* c, cudaStream_t st) {
+  if (c->lap_ready) return MLX_OK;
+  const long long rows_lap = c->tri, rows_helm = c->band_rows;
+  for (BandLU* f : {&c->lu_lap, &c->lu_helm}) {
+    const long long rows = (f == &c->lu_lap) ? rows_lap : rows_helm;
+    MLX_CUDA_TRY(c, cudaMalloc(&f->U, sizeof(double) * rows * 5));
+    MLX_CUDA_TRY(c, cudaMalloc(&f->L, sizeof(double) * rows * 2));
+    MLX_CUDA_TRY(c, cudaMalloc(&f->piv, sizeof(int) * rows));
+    MLX_CUDA_TRY(c, cudaMalloc(&f->invd, sizeof(double) * rows));
+  }
+  std::vector<long long> lrows(c->M + 1, 0);
+  for (int m = 0; m < c->M; ++m) lrows[m + 1] = lrows[m] + (c->nc - m);
+  MLX_CUDA_TRY(c, cudaMalloc(&c->d_lap_off, sizeof(long long) * (c->M + 1)));
+  MLX_CUDA_TRY(c, cudaMemcpyAsync(c->d_lap_off, lrows.data(), sizeof(long long) * (c->M + 1),
+                                  cudaMemcpyHostToDevice, st));
+  const long long stride = (long long)c->nc * (5 + 7);
+  double* scratch = nullptr;
+  MLX_CUDA_TRY(c, cudaMalloc(&scratch, sizeof(double) * stride * c->M * c->Kz));
+  const int tb = 64;
+  k_lap_setup<<<(c->M + tb - 1) / tb, tb, 0, st>>>(c->M, c->nc, c->Kz, c->lz, 0, c->d_lap_off, c->d_lap_off,
+                                                  c->d_lap, c->lu_lap.U, c->lu_lap.L, c->lu_lap.piv,
+                                                  c->lu_lap.invd, scratch, stride);
+  MLX_LAUNCH_CHECK(c);
+  k_lap_setup<<<(c->M * c->Kz + tb - 1) / tb, tb, 0, st>>>(c->M, c->nc, c->Kz, c->lz, 1, c->d_band_off,
+                                                          c->d_lap_off, c->d_lap, c->lu_helm.U, c->lu_helm.L,
+                                                          c->lu_helm.piv, c->lu_helm.invd, scratch, stride);
+  MLX_LAUNCH_CHECK(c);
+  MLX_CUDA_TRY(c, cudaStreamSynchronize(st));
+  cudaFree(scratch);
+  c->lap_ready = true;
+  return MLX_OK;
+}
+
+// Plain solves with the Laplacian-family factors: family 0 = D_m (decay row at
+// m = 0), 1 = D_m - kappa^2.
+// Projection factors of the vortex term (families Q, H per m; G per (m, |k|)).
+int mlx_proj_setup(mlx_ctx* c, cudaStream_t st) {
+  if (c->proj_ready) return MLX_OK;
+  const int W = 7, kl = 3;
+  BandLU* fams[3] = {&c->lu_Q, &c->lu_H, &c->lu_G};
+  for (int f = 0; f < 3; ++f) {
+    const long long rows = (f == 2) ? c->band_rows : c->tri;
+    MLX_CUDA_TRY(c, cudaMalloc(&fams[f]->U, sizeof(double) * rows * W));
+    MLX_CUDA_TRY(c, cudaMalloc(&fams[f]->L, sizeof(double) * rows * kl));
+    MLX_CUDA_TRY(c, cudaMalloc(&fams[f]->piv, sizeof(int) * rows));
+    MLX_CUDA_TRY(c, cudaMalloc(&fams[f]->invd, sizeof(double) * rows));
+  }
+  const long long stride = (long long)c->nc * (2 * W + 3 * kl + 1);
+  double* scratch = nullptr;
+  MLX_CUDA_TRY(c, cudaMalloc(&scratch, sizeof(double) * stride * c->M * c->Kz));
+  const int tb = 64;
+  for (int f = 0; f < 3; ++f) {
+    const int nsys = (f == 2) ? c->M * c->Kz : c->M;
+    k_proj_setup<<<(nsys + tb - 1) / tb, tb, 0, st>>>(c->M, c->nc, c->Kz, c->lz, c->ell, f,
+                                                      f == 2 ? c->d_band_off : c->d_lap_off, fams[f]->U,
+                                                      fams[f]->L, fams[f]->piv, fams[f]->invd, scratch, stride);
+    MLX_LAUNCH_CHECK(c);
+  }
+  MLX_CUDA_TRY(c, cudaStreamSynchronize(st));
+  cudaFree(scratch);
+  c->proj_ready = true;
+  return MLX_OK;
+}
+
+// Plain solves with the projection factors: family 0 = Q, 1 = H (decay row at
+// m = 0), 2 = G.
+int mlx_proj_solve(mlx_ctx* c, int family, const double2* rhs, double2* out, cudaStream_t st) {
+  TimedLaunch tl(c, KID_BAND_SOLVE, st);
+  int rc;
+  if (family == 0) rc = launch_solve<3>(c, MLX_STEP_PLAIN, c->lu_Q, c->d_lap_off, 1, 1, rhs, nullptr, nullptr, out, st);
+  else if (family == 1) rc = launch_solve<3>(c, MLX_STEP_PLAIN, c->lu_H, c->d_lap_off, 1, 1, rhs, nullptr, nullptr, out, st);
+  else rc = launch_solve<3>(c, MLX_STEP_PLAIN, c->lu_G, c->d_band_off, c->Kz, 0, rhs, nullptr, nullptr, out, st);
+  if (rc) return rc;
+  MLX_LAUNCH_CHECK(c);
+  return MLX_OK;
+}
+
+int mlx_lap_solve(mlx_ctx* c, int family, const double2* rhs, double2* out, cudaStream_t st) {
+  TimedLaunch tl(c, KID_BAND_SOLVE, st);
+  int rc = (family == 0)
+               ? launch_solve<2>(c, MLX_STEP_PLAIN, c->lu_lap, c->d_lap_off, 1, 1, rhs, nullptr, nullptr, out, st)
+               : launch_solve<2>(c, MLX_STEP_PLAIN, c->lu_helm, c->d_band_off, c->Kz, 0, rhs, nullptr, nullptr,
+                                 out, st);
   if (rc) return rc;
   MLX_LAUNCH_CHECK(c);
   return MLX_OK;
@@ -413,6 +624,7 @@ int mlx_band_solve(mlx_ctx* c, int step, const double2* s, const double2* A, con
 int mlx_band_prepare(mlx_ctx* c) {
   const int lim = 200 * 1024;
   MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_band_solve<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+  MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_band_solve<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
   MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_band_solve<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
   MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_band_solve<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
   MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_band_solve<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
@@ -420,9 +632,9 @@ int mlx_band_prepare(mlx_ctx* c) {
 }
 
 int mlx_spec_axpby(mlx_ctx* c, double a, const double2* x, double b, const double2* y,
-                   double2* out, cudaStream_t st) {
+                   double2* out, cudaStream_t st, long long nn) {
   TimedLaunch tl(c, KID_AXPBY, st);
-  const long long n = c->n_spec;
+  const long long n = nn < 0 ? c->n_spec : nn;
   const int tb = 256;
   k_axpby<<<(unsigned)((n + tb - 1) / tb), tb, 0, st>>>(n, a, x, b, y, out);
   MLX_LAUNCH_CHECK(c);

@@ -121,6 +121,18 @@ struct mlx_ctx {
   long long* d_band_off = nullptr;
   double* d_Bplus = nullptr;           // band of I + dt/2 L, [rows][2kl+1]
   BandLU lu_half, lu_full;
+  // Laplacian-family factors (vortex projection): D_m per m, D_m - kappa^2 per (m, |k|)
+  bool lap_ready = false;
+  BandLU lu_lap, lu_helm;
+  long long* d_lap_off = nullptr;      // row offset of m in the D_m factors (sum_{m'<m} (Nc - m'))
+  // vortex projection factors (Q, H per m; G per (m, |k|)), half bandwidth 3
+  bool proj_ready = false;
+  BandLU lu_Q, lu_H, lu_G;
+  // vortex term workspace
+  bool vortex_ready = false;
+  double* d_rdr = nullptr;             // r d/dr band, [tri][2] (offsets -1, +1)
+  double2* d_vspec = nullptr;          // 9 spectral temporaries
+  void* d_vphys = nullptr;             // 6 physical temporaries
   double* d_setup_scratch = nullptr;
   int solve_cpw = 8;                   // real chains per warp in the banded solve (4..32)
   int solve_wpb = 4;                   // warps per CTA in the banded solve (1..4)
@@ -160,6 +172,9 @@ struct TimedLaunch {
   }
 };
 
+// internal solve mode: right-hand side is the input itself
+#define MLX_STEP_PLAIN 3
+
 static inline size_t elem_size(int precision) { return precision == MLX_FP64 ? 8 : 4; }
 
 // ---- kernel-launch entry points (one per translation unit) ----
@@ -172,10 +187,16 @@ int mlx_legendre_forward(mlx_ctx* c, double2* spec, cudaStream_t st,
                          const double2* addsrc = nullptr, double alpha = 0.0);
 int mlx_legendre_backward(mlx_ctx* c, const double2* spec, cudaStream_t st); // spec -> d_mixed
 int mlx_band_setup(mlx_ctx* c, cudaStream_t st);
+int mlx_lap_setup(mlx_ctx* c, cudaStream_t st);
+int mlx_lap_solve(mlx_ctx* c, int family, const double2* rhs, double2* out, cudaStream_t st);
+int mlx_proj_setup(mlx_ctx* c, cudaStream_t st);
+int mlx_proj_solve(mlx_ctx* c, int family, const double2* rhs, double2* out, cudaStream_t st);
+int mlx_vortex_prepare(mlx_ctx* c, cudaStream_t st);
+int mlx_vortex_nonlinear(mlx_ctx* c, double U0, const double2* state, double2* out, cudaStream_t st);
 int mlx_tc_prepare(mlx_ctx* c, cudaStream_t st);
 int mlx_legendre_tc_forward(mlx_ctx* c, double2* spec, cudaStream_t st);
 int mlx_legendre_tc_backward(mlx_ctx* c, const double2* spec, cudaStream_t st);
 int mlx_band_solve(mlx_ctx* c, int step, const double2* s, const double2* A,
                    const double2* Ap, double2* out, cudaStream_t st);
 int mlx_spec_axpby(mlx_ctx* c, double a, const double2* x, double b, const double2* y,
-                   double2* out, cudaStream_t st);
+                   double2* out, cudaStream_t st, long long n = -1);

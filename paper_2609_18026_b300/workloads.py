@@ -14,6 +14,7 @@ Workloads (all analytic, as in the paper's examples; no dataset is involved):
 * heat_mode           -- manufactured heat mode, Eq. (15)
 * field_sA / field_sB -- rational and Gaussian fields of Eq. (13)
 * kpp_linear          -- linearised Fisher-KPP solution, Eq. (18)
+* vortex_pair_omega   -- counter-rotating Lamb-Oseen pair with a seeded axial displacement
 * random_spectral     -- seeded random coefficients in the flat ragged layout
 * batch_instances     -- the uneven batch of independent 2-D/3-D solves
 """
@@ -72,6 +73,26 @@ def kpp_linear(r, phi, z, t, A=1e-6, D=1.0, gamma=0.25, sigma=1.0):
     r, phi, z = _b(r, phi, z)
     s2 = sigma ** 2 + 2.0 * D * t
     return A * sigma ** 2 / s2 * math.exp(gamma * t) * np.exp(-r * r / (2.0 * s2))
+
+
+def vortex_pair_omega(r, phi, z, lz, b=1.0, a=0.2, gamma=2.0 * math.pi, amp=1e-3, incl_deg=48.0, kseed=1):
+    """Axial vorticity of two counter-rotating Lamb-Oseen vortices (circulations
+    +-gamma, core radius a) at (x, y) = (-+b/2, 0), each displaced by
+    amp cos(2 pi kseed z / lz) along a direction inclined incl_deg from the x axis,
+    mirror-symmetric about x = 0."""
+    r, phi, z = _b(r, phi, z)
+    x = r * np.cos(phi)
+    y = r * np.sin(phi)
+    d = amp * np.cos(2.0 * math.pi * kseed * z / lz)
+    th = math.radians(incl_deg)
+    out = np.zeros_like(x)
+    for sgn, xc in ((+1.0, -0.5 * b), (-1.0, 0.5 * b)):
+        # mirror symmetry about x = 0: the x-displacement flips sign
+        dx = d * math.cos(th) * (-1.0 if xc < 0 else 1.0)
+        dy = d * math.sin(th)
+        rr = (x - xc - dx) ** 2 + (y - dy) ** 2
+        out += sgn * gamma / (math.pi * a * a) * np.exp(-rr / (a * a))
+    return out
 
 
 def random_spectral(nc, M, Kz, seed=0, scale_decay=0.0):

@@ -30,8 +30,8 @@ def test_gradient_field_projects_to_zero():
     fp = 2 * r / q ** 3 - 6 * r ** 3 / q ** 4
     A = -2 * f * np.sin(2 * phi) * np.cos(kap * z)          # r N_phi = d_phi g
     Bf = r * fp * np.cos(2 * phi) * np.cos(kap * z)         # r N_r = r d_r g
-    Nz = -kap * f * np.cos(2 * phi) * np.sin(kap * z)       # d_z g
-    psiN, chiN = ops.project(O.forward(g, A), O.forward(g, Bf), O.forward(g, Nz))
+    C = -kap * r ** 2 * f * np.cos(2 * phi) * np.sin(kap * z)   # r^2 N_z = r^2 d_z g
+    psiN, chiN = ops.project(O.forward(g, A), O.forward(g, Bf), O.forward(g, C))
     scale = O.spec_norm(g, O.forward(g, f * np.cos(2 * phi) * np.cos(kap * z)))
     assert O.spec_norm(g, psiN) < 1e-9 * scale
     assert O.spec_norm(g, chiN) < 1e-9 * scale
@@ -48,7 +48,8 @@ def test_solenoidal_field_projects_back():
     psi = O.forward(g, r ** 2 / q ** 2 * np.cos(2 * phi) * np.cos(kap * z))
     chi = O.forward(g, r / q ** 2 * np.cos(phi) * np.sin(kap * z))
     rvr, rvp, vz, _, _, _ = ops.fields(psi, chi)
-    pN, cN = ops.project(rvp, rvr, vz)
+    r2vz = O.forward(g, r ** 2 * O.backward(g, vz))
+    pN, cN = ops.project(rvp, rvr, r2vz)
     assert O.spec_rel_err(g, pN, psi) < 1e-8
     assert O.spec_rel_err(g, cN, chi) < 1e-8
 
@@ -95,3 +96,22 @@ def test_lap_h_inverse_decay_row():
     assert abs(np.sum(x * O.vortex.pbar_at_one(0, g.nc))) < 1e-12
     exact = O.forward(g, q ** -2 + 0 * phi + 0 * z)[0][0]   # lap_h (1+r^2)^-2 = f, decays
     assert np.max(np.abs(x - exact)) < 1e-10
+
+
+def test_jacobi_and_r2_laplacian_by_quadrature():
+    # J = <Pbar_j, x Pbar_n> and Q = <Pbar_j, r^2 lap_h Pbar_n> = -n(n+1) <Pbar_j, (1-x^2) Pbar_n>
+    # by Gauss quadrature (exact with Nc + 2 nodes); interior block (truncation
+    # affects only the last rows of the composed Q)
+    from oracle.vortex import jacobi_matrix
+    for m, nc in ((0, 12), (3, 20)):
+        xq, wq = O.gauss_legendre(nc + 4)
+        P = O.pbar_table(m + 1, nc + 2, xq)[m]
+        Jq = (P * (wq * xq)[None, :]) @ P.T
+        J = jacobi_matrix(m, nc)
+        assert np.max(np.abs(J - Jq[: nc - m, : nc - m])) < 1e-14
+        n = np.arange(m, nc + 2, dtype=float)
+        Qq = ((P * (wq * (1 - xq ** 2))[None, :]) @ P.T) * (-n * (n + 1))[None, :]
+        ops = O.VortexOps(O.Grid(nc, 2 * (m + 1) + 2, 1, 1.0, M=m + 1, nr_c=nc))
+        Q = ops.Q[m]
+        k = nc - m - 2
+        assert np.max(np.abs(Q[:k, :k] - Qq[:k, :k])) < 1e-11 * np.max(np.abs(Qq))
