@@ -211,6 +211,9 @@ int mlx_advance(mlx_ctx* ctx, int kind, const double* coeffs, int ncoeffs,
  *   "solve_cpw": real chains per warp of the banded solve, 4, 8, 16 or 32
  *                (default 8);
  *   "solve_wpb": warps per CTA of the banded solve, 1, 2 or 4 (default 4).
+ *   "tc_bn":     column-tile width of the MLX_BF16X3 contraction (16..256; the
+ *                width actually used is rounded to a multiple of 16 that
+ *                splits the 2K columns evenly);
  *   "tc_products": BF16 split products per term in the MLX_BF16X3 contraction,
  *                6 (hi*hi, hi*mid, mid*hi, hi*lo, lo*hi, mid*mid) or 8 (adds
  *                mid*lo, lo*mid); default 6.
@@ -218,6 +221,36 @@ int mlx_advance(mlx_ctx* ctx, int kind, const double* coeffs, int ncoeffs,
  *   shape trades per-warp staging latency against FP64 pipe sharing.
  * Invalidates cached graphs.  MLX_EINVAL for an unknown key or value. */
 int mlx_set_tuning(mlx_ctx* ctx, const char* key, int value);
+
+/* ---- batched uneven solves and launch-shape autotuning (no counterpart in the
+ * paper, whose runs are single problems) ----
+ * A batch groups n independent contexts (any sizes, precisions and kinds; each
+ * created and set up by the caller, which keeps owning them).  The batch owns
+ * only streams, events and cached CUDA graphs. */
+typedef struct mlx_batch mlx_batch;
+int mlx_batch_create(mlx_ctx* const* ctxs, int n, mlx_batch** out);
+int mlx_batch_destroy(mlx_batch* batch);
+
+/* Advance every instance i of the batch by nsteps AB-CN steps, exactly as
+ * mlx_advance(ctxs[i], kinds[i], &coeffs[i], 1, states[i], prev_As[i], nsteps,
+ * start) would (same arithmetic, bitwise), but with the two-step pairs of all
+ * instances captured into ONE CUDA graph whose branches (one per instance) run
+ * concurrently; one graph launch per pair advances the whole batch.  The graph
+ * is cached per set of (state, prev_A, kind, coefficient).  MLX_ESTATE if an
+ * instance lacks mlx_implicit_setup (or mlx_vortex_setup for the vortex kind). */
+int mlx_batch_advance(mlx_batch* batch, const int* kinds, const double* coeffs, void* const* states,
+                      void* const* prev_As, int nsteps, int start, mlx_stream stream);
+
+/* Choose the launch shapes of ctx for its nonlinear `kind` by timing candidates
+ * with CUDA events on the context's temporaries: the tensor-core column-tile
+ * width (MLX_BF16X3 only) and the banded solve's chains per warp and warps per
+ * CTA.  Results are cached in the text file cache_path (may be NULL), one line
+ * "sizes precision kind band|bn cpw wpb"; a cached entry is applied without
+ * timing.  chosen (may be NULL) receives {bn, cpw, wpb, from_cache}.  The
+ * context's temporaries are overwritten; call it before advancing.
+ * Synchronises `stream`. */
+int mlx_autotune(mlx_ctx* ctx, int kind, const double* coeffs, int ncoeffs, const char* cache_path,
+                 int* chosen, mlx_stream stream);
 
 /* ---- measurement support (not part of the method) ----
  * Opt-in per-launch timing: with enable != 0 every kernel launch of this context

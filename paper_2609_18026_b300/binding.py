@@ -24,7 +24,8 @@ EXPORTS = ("mlx_strerror", "mlx_last_cuda_error", "mlx_create", "mlx_destroy", "
            "mlx_implicit_setup", "mlx_implicit_solve", "mlx_advance",
            "mlx_timing", "mlx_timing_read", "mlx_kernel_count", "mlx_kernel_name",
            "mlx_set_tuning", "mlx_device_status", "mlx_forward_noalloc",
-           "mlx_vortex_setup", "mlx_lap_h_solve")
+           "mlx_vortex_setup", "mlx_lap_h_solve",
+           "mlx_batch_create", "mlx_batch_destroy", "mlx_batch_advance", "mlx_autotune")
 
 
 class MlxError(RuntimeError):
@@ -82,6 +83,11 @@ def load():
     lib.mlx_forward_noalloc.argtypes = [vp, vp, vp, vp]
     lib.mlx_vortex_setup.argtypes = [vp, vp]
     lib.mlx_lap_h_solve.argtypes = [vp, vp, vp, vp]
+    lib.mlx_batch_create.argtypes = [ctypes.POINTER(vp), i, ctypes.POINTER(vp)]
+    lib.mlx_batch_destroy.argtypes = [vp]
+    lib.mlx_batch_advance.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(d), ctypes.POINTER(vp),
+                                      ctypes.POINTER(vp), i, i, vp]
+    lib.mlx_autotune.argtypes = [vp, i, ctypes.POINTER(d), i, ctypes.c_char_p, ctypes.POINTER(i), vp]
     lib.mlx_kernel_name.argtypes = [i]
     lib.mlx_kernel_name.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -221,8 +227,52 @@ class Context:
                 out[self.lib.mlx_kernel_name(k).decode()] = (n.value, ms.value)
         return out
 
+    def autotune(self, kind, coeffs, cache_path=None, stream=None):
+        """Pick launch shapes by timing; returns dict(bn, cpw, wpb, from_cache)."""
+        arr = (ctypes.c_double * max(1, len(coeffs)))(*coeffs)
+        ch = (ctypes.c_int * 4)()
+        self._check(self.lib.mlx_autotune(self._h, kind, arr, len(coeffs),
+                                          cache_path.encode() if cache_path else None, ch, _stream(stream)))
+        return dict(bn=ch[0], cpw=ch[1], wpb=ch[2], from_cache=bool(ch[3]))
+
     def advance(self, kind, coeffs, state, prev_A, nsteps, start, stream=None):
         arr = (ctypes.c_double * max(1, len(coeffs)))(*coeffs)
         self._check(self.lib.mlx_advance(self._h, kind, arr, len(coeffs), _ptr(state), _ptr(prev_A),
                                          int(nsteps), int(bool(start)), _stream(stream)))
         return state
+
+
+class Batch:
+    """Independent contexts advanced together by one CUDA graph per step pair."""
+
+    def __init__(self, contexts):
+        self.lib = load()
+        self.contexts = list(contexts)
+        arr = (ctypes.c_void_p * len(self.contexts))(*[c._h.value for c in self.contexts])
+        h = ctypes.c_void_p()
+        rc = self.lib.mlx_batch_create(arr, len(self.contexts), ctypes.byref(h))
+        if rc != 0:
+            raise MlxError(rc, "libmlx: mlx_batch_create failed (code %d)" % rc)
+        self._h = h
+
+    def advance(self, kinds, coeffs, states, prevs, nsteps, start, stream=None):
+        n = len(self.contexts)
+        k = (ctypes.c_int * n)(*kinds)
+        c = (ctypes.c_double * n)(*coeffs)
+        s = (ctypes.c_void_p * n)(*[t.data_ptr() for t in states])
+        p = (ctypes.c_void_p * n)(*[t.data_ptr() for t in prevs])
+        rc = self.lib.mlx_batch_advance(self._h, k, c, s, p, int(nsteps), int(bool(start)), _stream(stream))
+        if rc != 0:
+            raise MlxError(rc, "libmlx: mlx_batch_advance failed (code %d): %s" % (
+                rc, self.lib.mlx_strerror(rc).decode()))
+
+    def close(self):
+        if self._h is not None:
+            self.lib.mlx_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -87,6 +87,14 @@ int abcn_step(mlx_ctx* c, int kind, double c0, const double2* s, double2* Anew,
 
 }  // namespace
 
+// Two AB-CN steps (s, A_prev) -> (s, A_prev) through the context's temporaries,
+// enqueued on st (the unit that graphs replay).
+int mlx_enqueue_step_pair(mlx_ctx* c, int kind, double c0, double2* s, double2* Ap, cudaStream_t st) {
+  int rc = abcn_step(c, kind, c0, s, c->d_specA, Ap, c->d_spec1, st);
+  if (rc) return rc;
+  return abcn_step(c, kind, c0, c->d_spec1, Ap, c->d_specA, s, st);
+}
+
 extern "C" {
 
 const char* mlx_strerror(int code) {
@@ -371,6 +379,15 @@ int mlx_set_tuning(mlx_ctx* c, const char* key, int value) {
   if (strcmp(key, "tc_products") == 0) {
     if (value != 6 && value != 8) return MLX_EINVAL;
     c->tc_products = value;
+    for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
+    c->graphs.clear();
+    return MLX_OK;
+  }
+  if (strcmp(key, "tc_bn") == 0) {
+    if (c->precision != MLX_BF16X3) return MLX_EINVAL;
+    int rc = mlx_tc_retile(c, value, nullptr);
+    if (rc) return rc;
+    MLX_CUDA_TRY(c, cudaDeviceSynchronize());
     for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
     c->graphs.clear();
     return MLX_OK;

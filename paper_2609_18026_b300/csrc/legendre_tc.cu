@@ -377,14 +377,25 @@ int mlx_tc_prepare(mlx_ctx* c, cudaStream_t st) {
   // columns per tile (interleaved Re/Im pairs, multiple of 16): narrow tiles when
   // the grid would otherwise leave SMs idle
   const int ncol = 2 * c->K;
+  int bn = 256;
   {
     int rt = 0;
     for (int m = 0; m < c->M; ++m) rt += (c->nc - m + TC_BM - 1) / TC_BM;
-    int bn = 256;
     while (bn > 32 && (long long)rt * ((ncol + bn - 1) / bn) < 148) bn -= 16;
-    const int nct = (ncol + bn - 1) / bn;
-    c->tc_bn = ((ncol + nct - 1) / nct + 15) / 16 * 16;
   }
+  return mlx_tc_retile(c, bn, st);
+}
+
+// Tile lists for a requested column-tile width (the autotuner's knob).
+int mlx_tc_retile(mlx_ctx* c, int bn_req, cudaStream_t st) {
+  const int ncol = 2 * c->K;
+  if (bn_req < 16 || bn_req > 256) return MLX_EINVAL;
+  const int nct = (ncol + bn_req - 1) / bn_req;
+  c->tc_bn = ((ncol + nct - 1) / nct + 15) / 16 * 16;
+  if (c->tc_bn > 256) c->tc_bn = 256;
+  cudaFree(c->d_tc_fwd);
+  cudaFree(c->d_tc_bwd);
+  c->d_tc_fwd = c->d_tc_bwd = nullptr;
   std::vector<LegTile> tf, tb;
   for (int m = 0; m < c->M; ++m) {
     for (int r0 = 0; r0 < c->nc - m; r0 += TC_BM)
@@ -402,7 +413,9 @@ int mlx_tc_prepare(mlx_ctx* c, cudaStream_t st) {
   while (cols < 2 * c->tc_bn) cols <<= 1;   // two accumulators of BN columns
   c->tc_tmem_cols = cols;
   c->tc_stages = tc_smem(c->tc_bn, 2) <= 220 * 1024 ? 2 : 1;
-  const int smem = (int)tc_smem(c->tc_bn, c->tc_stages);
+  // the attribute is a per-function ceiling shared by every context: set it to
+  // the largest size any tile width uses
+  const int smem = 220 * 1024 + 1024;
   MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_leg_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_leg_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   return MLX_OK;

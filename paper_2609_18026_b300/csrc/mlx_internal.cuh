@@ -194,6 +194,8 @@ int mlx_proj_solve(mlx_ctx* c, int family, const double2* rhs, double2* out, cud
 int mlx_vortex_prepare(mlx_ctx* c, cudaStream_t st);
 int mlx_vortex_nonlinear(mlx_ctx* c, double U0, const double2* state, double2* out, cudaStream_t st);
 int mlx_tc_prepare(mlx_ctx* c, cudaStream_t st);
+int mlx_tc_retile(mlx_ctx* c, int bn, cudaStream_t st);
+int mlx_enqueue_step_pair(mlx_ctx* c, int kind, double c0, double2* s, double2* Ap, cudaStream_t st);
 int mlx_legendre_tc_forward(mlx_ctx* c, double2* spec, cudaStream_t st);
 int mlx_legendre_tc_backward(mlx_ctx* c, const double2* spec, cudaStream_t st);
 int mlx_band_solve(mlx_ctx* c, int step, const double2* s, const double2* A,

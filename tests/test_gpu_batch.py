@@ -1,0 +1,100 @@
+"""Batched uneven solves (one CUDA graph per step pair) and the autotuner."""
+
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2609_18026_b300 import binding as B
+from paper_2609_18026_b300 import workloads as W
+
+from gpu_common import spec_from_gpu
+
+pytestmark = pytest.mark.gpu
+
+# uneven instances: (nr, nphi, nz, ell, kind, precision)
+INST = [(32, 16, 1, 0.7, B.NONLIN_NONE, B.FP32),
+        (48, 32, 16, 2.0, B.NONLIN_FKPP, B.FP32),
+        (64, 16, 16, 3.1, B.NONLIN_FKPP, B.BF16X3),
+        (40, 64, 1, 1.3, B.NONLIN_NONE, B.BF16X3),
+        (24, 8, 4, 0.9, B.NONLIN_FKPP, B.FP64)]
+
+
+def _make(inst, seed):
+    import torch
+    nr, nphi, nz, ell, kind, prec = inst
+    ctx = B.Context(nr, nphi, nz, ell, lz=2 * math.pi, precision=prec, chop_policy=B.CHOP_LINEAR)
+    ctx.implicit_setup(1e-2 if kind == B.NONLIN_NONE else 1.0, 1e-3)
+    x, w, r = ctx.nodes()
+    phi = 2 * np.pi * np.arange(nphi) / nphi
+    zz = 2 * np.pi * np.arange(nz) / nz
+    par = dict(x0=0.3 * ell, y0=-0.2 * ell, sigma=ell, nz=nz, lz=2 * math.pi)
+    u0 = W.batch_initial(par, r[None, None, :], phi[None, :, None], zz[:, None, None])
+    s = ctx.forward(torch.as_tensor(u0, dtype=ctx.phys_dtype).cuda(), ctx.new_spec())
+    return ctx, s, u0
+
+
+def test_batched_advance_equals_individual():
+    ctxs, s_b, s_i, p_b, p_i = [], [], [], [], []
+    for j, inst in enumerate(INST):
+        ctx, s, _ = _make(inst, j)
+        ctxs.append(ctx)
+        s_b.append(s.clone()); s_i.append(s.clone())
+        p_b.append(ctx.new_spec()); p_i.append(ctx.new_spec())
+    kinds = [inst[4] for inst in INST]
+    coeffs = [1.0] * len(INST)
+    batch = B.Batch(ctxs)
+    batch.advance(kinds, coeffs, s_b, p_b, 7, True)
+    batch.advance(kinds, coeffs, s_b, p_b, 6, False)
+    for j, ctx in enumerate(ctxs):
+        ctx.advance(kinds[j], [1.0], s_i[j], p_i[j], 7, True)
+        ctx.advance(kinds[j], [1.0], s_i[j], p_i[j], 6, False)
+    for j in range(len(INST)):
+        assert np.array_equal(s_b[j].cpu().numpy(), s_i[j].cpu().numpy()), j
+        assert np.array_equal(p_b[j].cpu().numpy(), p_i[j].cpu().numpy()), j
+    batch.close()
+
+
+def test_batched_instance_matches_oracle():
+    inst = INST[1]
+    ctx, s, u0 = _make(inst, 1)
+    batch = B.Batch([ctx])
+    p = ctx.new_spec()
+    batch.advance([inst[4]], [1.0], [s], [p], 5, True)
+    nr, nphi, nz, ell, kind, prec = inst
+    g = O.Grid(nr, nphi, nz, ell, lz=2 * math.pi, policy="linear")
+    u0 = u0.astype(np.float32).astype(np.float64)
+    st = O.Stepper(g, 1.0, 1e-3, nonlinear=O.fkpp_nonlinear(g, 1.0))
+    ref, _ = st.run_abcn(O.forward(g, u0), 5)
+    assert O.spec_rel_err(g, spec_from_gpu(g, s), ref) <= 1e-6
+
+
+def test_autotune_cache_roundtrip(tmp_path):
+    import torch
+    cache = str(tmp_path / "tune.txt")
+    inst = (128, 128, 64, 4.0, B.NONLIN_FKPP, B.BF16X3)
+    ctx = B.Context(128, 128, 64, 4.0, lz=2 * np.pi * 8, precision=B.BF16X3, chop_policy=B.CHOP_TWOTHIRDS)
+    ctx.implicit_setup(1.0, 1e-2)
+    first = ctx.autotune(B.NONLIN_FKPP, [1.0], cache)
+    assert not first["from_cache"]
+    assert first["cpw"] in (4, 8, 16, 32) and first["wpb"] in (1, 2, 4) and 16 <= first["bn"] <= 256
+    assert os.path.exists(cache)
+    ctx2 = B.Context(128, 128, 64, 4.0, lz=2 * np.pi * 8, precision=B.BF16X3, chop_policy=B.CHOP_TWOTHIRDS)
+    ctx2.implicit_setup(1.0, 1e-2)
+    second = ctx2.autotune(B.NONLIN_FKPP, [1.0], cache)
+    assert second["from_cache"] and second == dict(first, from_cache=True)
+    # the tuned shapes change the arithmetic order only: results agree to 1e-6
+    g = O.Grid(128, 128, 64, 4.0, lz=2 * np.pi * 8, policy="twothirds")
+    r, phi, z = g.nodes3()
+    u0 = W.fkpp_seed(r, phi, z).astype(np.float32)
+    ref_ctx = B.Context(128, 128, 64, 4.0, lz=2 * np.pi * 8, precision=B.BF16X3, chop_policy=B.CHOP_TWOTHIRDS)
+    ref_ctx.implicit_setup(1.0, 1e-2)
+    outs = []
+    for c in (ctx2, ref_ctx):
+        s = c.forward(torch.as_tensor(u0).cuda(), c.new_spec())
+        p = c.new_spec()
+        c.advance(B.NONLIN_FKPP, [1.0], s, p, 10, True)
+        outs.append(O.from_flat(g, s.cpu().numpy()))
+    assert O.spec_rel_err(g, outs[0], outs[1]) <= 1e-6
