@@ -209,6 +209,111 @@ def algorithmic(kernel, ctx, nz_gt1=True):
     return 0, 0.0
 
 
+def measure_vortex(B, W, torch, dev, stream, steps=20, prec=None):
+    """256^3 counter-rotating vortex pair (Nr = Nphi = Nz = 256, ell = 1, two-thirds
+    chops, Lz = 8.6, nu = 1e-4, nu_h = 5e-7, p = 8, U0 = 1, dt = 2.5e-4): AB-CN steps
+    of the toroidal-poloidal pair, transforms in BF16x3, FP64 solves.  Inputs are
+    resident; the step loop is graph-replayed."""
+    import math as _m
+    prec = B.BF16X3 if prec is None else prec
+    nr = nphi = nz = 256
+    lz = 8.6
+    t0 = time.perf_counter()
+    ctx = B.Context(nr, nphi, nz, 1.0, lz=lz, precision=prec, chop_policy=B.CHOP_TWOTHIRDS)
+    ctx.vortex_setup()
+    ctx.implicit_setup(1e-4, 2.5e-4, nu_h=5e-7, p=8)
+    x, w, r = ctx.nodes()
+    phi = 2 * _m.pi * np.arange(nphi) / nphi
+    zz = lz * np.arange(nz) / nz
+    wz = W.vortex_pair_omega(r[None, None, :], phi[None, :, None], zz[:, None, None], lz=lz)
+    ws = ctx.forward(torch.as_tensor(wz, dtype=ctx.phys_dtype, device=dev), ctx.new_spec())
+    psi = ctx.lap_h_solve(-ws, ctx.new_spec())
+    state = torch.zeros(2 * ctx.n_spec, dtype=torch.complex128, device=dev)
+    state[:ctx.n_spec] = psi
+    prev = torch.zeros_like(state)
+    setup_s = time.perf_counter() - t0
+    ctx.advance(B.NONLIN_VORTEX, [1.0], state, prev, 3, True)   # start + warm-up (graph captured)
+    ctx.advance(B.NONLIN_VORTEX, [1.0], state, prev, 2, False)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    ctx.advance(B.NONLIN_VORTEX, [1.0], state, prev, steps, False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    ctx.timing(True)
+    ctx.advance(B.NONLIN_VORTEX, [1.0], state, prev, 2, False)
+    kt = ctx.timing_read()
+    ctx.timing(False)
+    ok = bool(torch.isfinite(state.real).all().item())
+    ctx.device_status()
+    tot = sum(v[1] for v in kt.values())
+    out = {"workload": "vortex_pair_256^3", "timesteps_per_s": steps / (ms / 1000.0), "ms_per_timestep": ms / steps,
+           "timed_steps": steps, "setup_s": setup_s, "finite": ok,
+           "precision": {B.BF16X3: "bf16x3", B.FP32: "fp32", B.FP64: "fp64"}[prec],
+           "transforms_per_step": 9, "kernel_share": {k: round(v[1] / tot, 3) for k, v in kt.items()},
+           "kernel_avg_us": {k: 1000.0 * v[1] / v[0] for k, v in kt.items()}}
+    ctx.close()
+    return out
+
+
+def measure_batch(B, W, torch, dev, stream, steps=100, n=64, tune_cache=None):
+    """64 uneven independent 2-D/3-D diffusion and Fisher-KPP instances (seed
+    20261202: Nr in {32..256}, Nphi in {16..256}, Nz in {1, 16, 64}, ell in
+    [0.5, 4]), FP32 transforms (BF16x3 contraction), FP64 solves, dt = 1e-3,
+    advanced together by one CUDA graph per step pair."""
+    import math as _m
+    t0 = time.perf_counter()
+    insts = W.batch_instances(n)
+    ctxs, states, prevs, kinds, coeffs = [], [], [], [], []
+    tuned = 0
+    for inst in insts:
+        pol = B.CHOP_LINEAR if inst["kind"] == "diffusion" else B.CHOP_TWOTHIRDS
+        m_pol = inst["nphi"] // 2 if pol == B.CHOP_LINEAR else (inst["nphi"] - 1) // 3 + 1
+        # the azimuthal chop cannot exceed the radial one (n >= m, Sec. 3.1)
+        ctx = B.Context(inst["nr"], inst["nphi"], inst["nz"], inst["ell"], lz=inst["lz"], precision=B.BF16X3,
+                        chop_policy=pol, nphi_c=min(m_pol, inst["nr"]))
+        kind = B.NONLIN_NONE if inst["kind"] == "diffusion" else B.NONLIN_FKPP
+        ctx.implicit_setup(1e-2 if kind == B.NONLIN_NONE else 1.0, inst["dt"])
+        if tune_cache and os.path.exists(tune_cache):
+            if ctx.autotune(kind, [1.0], tune_cache)["from_cache"]:
+                tuned += 1
+        x, w, r = ctx.nodes()
+        phi = 2 * _m.pi * np.arange(inst["nphi"]) / inst["nphi"]
+        zz = inst["lz"] * np.arange(inst["nz"]) / inst["nz"]
+        u0 = W.batch_initial(inst, r[None, None, :], phi[None, :, None], zz[:, None, None])
+        s = ctx.forward(torch.as_tensor(u0, dtype=torch.float32, device=dev), ctx.new_spec())
+        ctxs.append(ctx); states.append(s); prevs.append(ctx.new_spec()); kinds.append(kind); coeffs.append(1.0)
+    setup_s = time.perf_counter() - t0
+    batch = B.Batch(ctxs)
+    batch.advance(kinds, coeffs, states, prevs, 3, True)
+    batch.advance(kinds, coeffs, states, prevs, 4, False)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    batch.advance(kinds, coeffs, states, prevs, steps, False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    # the same instances one after another (graph per instance), for comparison
+    e0.record(stream)
+    for j, ctx in enumerate(ctxs):
+        ctx.advance(kinds[j], [1.0], states[j], prevs[j], steps, False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_seq = e0.elapsed_time(e1)
+    ok = all(bool(torch.isfinite(s.real).all().item()) for s in states)
+    batch.close()
+    for c in ctxs:
+        c.close()
+    return {"workload": "batch64_uneven", "instances": n, "instance_timesteps_per_s": n * steps / (ms / 1000.0),
+            "batch_step_ms": ms / steps, "sequential_instance_timesteps_per_s": n * steps / (ms_seq / 1000.0),
+            "speedup_vs_sequential": ms_seq / ms, "timed_steps": steps, "setup_s": setup_s,
+            "autotuned_from_cache": tuned, "finite": ok}
+
+
 def run_gpu(args, rank, world):
     import torch
     import torch.distributed as dist
@@ -410,6 +515,17 @@ def run_gpu(args, rank, world):
         dist.all_reduce(tm, op=dist.ReduceOp.MAX)
     e2e_value = args.steps * STEPS_PER_BENCH_STEP * world / (float(tm.item()) / 1000.0)
 
+    others = {}
+    if not args.no_other_workloads:
+        for name, fn in (("vortex", lambda: measure_vortex(B, W, torch, dev, stream)),
+                         ("batch", lambda: measure_batch(B, W, torch, dev, stream,
+                                                         tune_cache=os.path.join(ROOT, "paper_2609_18026_b300",
+                                                                                 "tuning_cache.txt")))):
+            try:
+                others[name] = fn()
+            except Exception as exc:   # reported, never hides the main line
+                others[name] = {"error": repr(exc)}
+
     if rank != 0:
         return
     cpu = None
@@ -446,6 +562,7 @@ def run_gpu(args, rank, world):
         "gpu_launches": gpu_launches,
         "wall_s_timed": t_wall,
         "cpu_baseline": cpu,
+        "other_workloads": others,
     }
     print(json.dumps(line), flush=True)
 
@@ -457,6 +574,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mlx", choices=["mlx", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-other-workloads", action="store_true",
+                    help="skip the 256^3 vortex and 64-instance batch measurements")
     ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "fp32", "fp64"],
                     help="transform arithmetic of the timed form (the FP64 form is always timed beside it)")
     args = ap.parse_args()

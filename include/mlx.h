@@ -211,6 +211,10 @@ int mlx_advance(mlx_ctx* ctx, int kind, const double* coeffs, int ncoeffs,
  *   "solve_cpw": real chains per warp of the banded solve, 4, 8, 16 or 32
  *                (default 8);
  *   "solve_wpb": warps per CTA of the banded solve, 1, 2 or 4 (default 4).
+ *   "solve_direct": 1 = banded-solve variant that reads factor rows from global
+ *                memory and keeps only the solution columns in shared memory
+ *                (32 chains per warp); default 1 for hyperviscous bands
+ *                (half width >= 4, set by mlx_implicit_setup), else 0.
  *   "tc_bn":     column-tile width of the MLX_BF16X3 contraction (16..256; the
  *                width actually used is rounded to a multiple of 16 that
  *                splits the 2K columns evenly);
@@ -246,7 +250,8 @@ int mlx_batch_advance(mlx_batch* batch, const int* kinds, const double* coeffs, 
  * width (MLX_BF16X3 only) and the banded solve's chains per warp and warps per
  * CTA.  Results are cached in the text file cache_path (may be NULL), one line
  * "sizes precision kind band|bn cpw wpb"; a cached entry is applied without
- * timing.  chosen (may be NULL) receives {bn, cpw, wpb, from_cache}.  The
+ * timing.  chosen (may be NULL) receives {bn, cpw, wpb, from_cache}; cpw = wpb = 0
+ * denotes the direct-read solve variant.  The
  * context's temporaries are overwritten; call it before advancing.
  * Synchronises `stream`. */
 int mlx_autotune(mlx_ctx* ctx, int kind, const double* coeffs, int ncoeffs, const char* cache_path,

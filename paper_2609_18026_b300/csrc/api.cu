@@ -275,6 +275,7 @@ int mlx_implicit_setup(mlx_ctx* c, double nu, double nu_h, int p, double dt, mlx
   c->graphs.clear();
   c->nu = nu; c->nu_h = nu_h; c->p = p; c->dt = dt;
   c->kl = (nu_h > 0.0) ? p : 2;
+  c->solve_direct = (c->kl >= 4) ? 1 : 0;   // wide hyperviscous bands: direct-read solve
   c->implicit_ready = false;
   int rc = mlx_band_setup(c, (cudaStream_t)stream);
   if (rc) return rc;
@@ -372,6 +373,13 @@ int mlx_set_tuning(mlx_ctx* c, const char* key, int value) {
   if (strcmp(key, "solve_cpw") == 0) {
     if (value != 4 && value != 8 && value != 16 && value != 32) return MLX_EINVAL;
     c->solve_cpw = value;
+    for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
+    c->graphs.clear();
+    return MLX_OK;
+  }
+  if (strcmp(key, "solve_direct") == 0) {
+    if (value != 0 && value != 1) return MLX_EINVAL;
+    c->solve_direct = value;
     for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
     c->graphs.clear();
     return MLX_OK;

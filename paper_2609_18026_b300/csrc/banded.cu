@@ -493,10 +493,141 @@ int mlx_band_setup(mlx_ctx* c, cudaStream_t st) {
   return MLX_OK;
 }
 
+// Direct-read variant for wide bands (the hyperviscous KL = p operators): only the
+// right-hand side / solution column lives in shared memory (one column per lane,
+// 32 chains per warp), the factor rows are read from global memory (their
+// addresses do not depend on the recurrence, so the loads issue ahead of use),
+// and the back substitution keeps four partial sums so the FP64 pipe sees
+// independent instructions.  Many more warps fit per SM than with staged factors.
+template <int KL>
+__global__ void k_band_solve_direct(int M, int nc, int Kz, int K, int groups_per_m, int step, double dt,
+                                    const long long* __restrict__ soff, const long long* __restrict__ band_off,
+                                    int kz_fac, int m0_shift, const double* __restrict__ U,
+                                    const double* __restrict__ Lm, const int* __restrict__ piv,
+                                    const double* __restrict__ invd, const double* __restrict__ s,
+                                    const double* __restrict__ A, const double* __restrict__ Ap,
+                                    double* __restrict__ out) {
+  constexpr int W = 2 * KL + 1;
+  constexpr int CPW = 32, G = 8;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int gw = blockIdx.x * (blockDim.x >> 5) + wib;
+  if (gw >= M * groups_per_m) return;
+  const int m = gw / groups_per_m;
+  const int k0 = (gw % groups_per_m) * G;
+  const int gcnt = min(G, Kz - k0);
+  const int sh = (m == 0) ? m0_shift : 0;
+  const int Nm = nc - m;
+  const int N = Nm - sh;
+  double* Y = reinterpret_cast<double*>(smem_raw) + (size_t)wib * nc * CPW;   // [N][32]
+  const long long fb = band_off[m];
+  const long long sm = soff[m];
+  const double h = (step == MLX_STEP_FEBE_FULL) ? dt : 0.5 * dt;
+  for (int e = lane; e < N * 4 * gcnt; e += 32) {
+    const int c = e / N, i = e - c * N;
+    const int kk = c >> 2, sgn = (c >> 1) & 1, part = c & 1;
+    const int kabs = k0 + kk;
+    if (sgn && kabs == 0) continue;
+    const int kidx = sgn ? K - kabs : kabs;
+    const long long o = 2 * (sm + (long long)kidx * Nm + sh + i) + part;
+    double r;
+    if (step == MLX_STEP_PLAIN) {
+      r = s[o];
+    } else if (step == MLX_STEP_ABCN) {
+      r = 2.0 * s[o];
+      if (A) r += 1.5 * dt * A[o];
+      if (Ap) r -= 0.5 * dt * Ap[o];
+    } else {
+      r = s[o];
+      if (A) r += h * A[o];
+    }
+    Y[(size_t)i * CPW + c] = r;
+  }
+  __syncwarp();
+  const int c = lane;
+  const int kk = c >> 2, sgn = (c >> 1) & 1, part = c & 1;
+  const bool valid = c < 4 * gcnt && !(sgn && k0 + kk == 0);
+  const long long rbase = fb + (kz_fac == 1 ? 0 : k0 + (kk < gcnt ? kk : 0));
+  if (c < 4 * gcnt) {
+    double* y = Y + c;
+    double w[KL + 1];
+#pragma unroll
+    for (int q = 0; q < KL; ++q) w[q + 1] = (q < N) ? y[(size_t)q * CPW] : 0.0;
+    for (int j = 0; j < N; ++j) {
+      const long long row = rbase + (long long)j * kz_fac;
+      const int d = __ldg(piv + row) - j;
+      double l[KL];
+#pragma unroll
+      for (int q = 0; q < KL; ++q) l[q] = __ldg(Lm + row * KL + q);
+#pragma unroll
+      for (int q = 0; q < KL; ++q) w[q] = w[q + 1];
+      w[KL] = (j + KL < N) ? y[(size_t)(j + KL) * CPW] : 0.0;
+#pragma unroll
+      for (int q = 1; q <= KL; ++q)
+        if (q == d) { const double t = w[0]; w[0] = w[q]; w[q] = t; }
+      y[(size_t)j * CPW] = w[0];
+#pragma unroll
+      for (int q = 1; q <= KL; ++q) w[q] -= l[q - 1] * w[0];
+    }
+    double x[2 * KL + 1];
+#pragma unroll
+    for (int q = 0; q <= 2 * KL; ++q) x[q] = 0.0;
+    for (int i = N - 1; i >= 0; --i) {
+      const long long row = rbase + (long long)i * kz_fac;
+      double u[W];
+#pragma unroll
+      for (int q = 1; q < W; ++q) u[q] = __ldg(U + row * W + q);
+      const double dv = __ldg(invd + row);
+      double p0 = y[(size_t)i * CPW] * dv, p1 = 0.0, p2 = 0.0, p3 = 0.0;
+#pragma unroll
+      for (int q = 2 * KL; q >= 2; --q) {
+        if ((q & 3) == 0) p0 -= u[q] * x[q];
+        else if ((q & 3) == 1) p1 -= u[q] * x[q];
+        else if ((q & 3) == 2) p2 -= u[q] * x[q];
+        else p3 -= u[q] * x[q];
+      }
+      const double acc = ((p0 + p2) + (p1 + p3)) - u[1] * x[1];
+      y[(size_t)i * CPW] = acc;
+#pragma unroll
+      for (int q = 2 * KL; q >= 2; --q) x[q] = x[q - 1];
+      x[1] = acc;
+    }
+  }
+  __syncwarp();
+  if (sh && c < 4 * gcnt && valid) {
+    double acc = 0.0;
+    for (int i = 0; i < N; ++i) acc += sqrt((2.0 * (i + 1) + 1.0) * 0.5) * Y[(size_t)i * CPW + c];
+    const int kidx = sgn ? K - (k0 + kk) : k0 + kk;
+    out[2 * (sm + (long long)kidx * Nm) + part] = -acc / sqrt(0.5);
+  }
+  for (int e = lane; e < N * 4 * gcnt; e += 32) {
+    const int cc = e / N, i = e - cc * N;
+    const int kq = cc >> 2, sg = (cc >> 1) & 1, pt = cc & 1;
+    const int kabs = k0 + kq;
+    if (sg && kabs == 0) continue;
+    const int kidx = sg ? K - kabs : kabs;
+    const long long o = 2 * (sm + (long long)kidx * Nm + sh + i) + pt;
+    double v = Y[(size_t)i * CPW + cc];
+    if (step == MLX_STEP_ABCN) v -= s[o];
+    out[o] = v;
+  }
+}
+
 template <int KL>
 static int launch_solve(mlx_ctx* c, int step, const BandLU& f, const long long* fac_off, int kz_fac,
                         int m0_shift, const double2* s, const double2* A, const double2* Ap, double2* out,
                         cudaStream_t st) {
+  if (c->solve_direct) {
+    const int gpm = (c->Kz + 7) / 8;
+    const int warps = c->M * gpm;
+    int WPB = 4;
+    while (WPB > 1 && (size_t)WPB * c->nc * 32 * sizeof(double) > 200 * 1024) WPB /= 2;
+    const size_t smem = (size_t)WPB * c->nc * 32 * sizeof(double);
+    k_band_solve_direct<KL><<<(warps + WPB - 1) / WPB, 32 * WPB, smem, st>>>(
+        c->M, c->nc, c->Kz, c->K, gpm, step, c->dt, c->d_soff, fac_off, kz_fac, m0_shift, f.U, f.L, f.piv,
+        f.invd, (const double*)s, (const double*)A, (const double*)Ap, (double*)out);
+    return MLX_OK;
+  }
   // Chains per warp and warps per CTA are launch-shape parameters (measured best
   // at the 128x128x64 workload: 8 chains per warp, 1-4 warps per CTA).
   int CPW = c->solve_cpw;
@@ -625,6 +756,11 @@ int mlx_band_prepare(mlx_ctx* c) {
   const int lim = 200 * 1024;
   MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_band_solve<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
   MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_band_solve<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+  MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_band_solve_direct<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+  MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_band_solve_direct<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+  MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_band_solve_direct<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+  MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_band_solve_direct<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+  MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_band_solve_direct<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
   MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_band_solve<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
   MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_band_solve<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
   MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_band_solve<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));

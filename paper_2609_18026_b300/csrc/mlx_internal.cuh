@@ -136,6 +136,7 @@ struct mlx_ctx {
   double* d_setup_scratch = nullptr;
   int solve_cpw = 8;                   // real chains per warp in the banded solve (4..32)
   int solve_wpb = 4;                   // warps per CTA in the banded solve (1..4)
+  int solve_direct = 0;                // 1: direct-read solve variant (wide bands)
 
   // graphs cached per (state, prev_A, kind, gamma)
   struct GraphKey {

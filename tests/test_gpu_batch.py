@@ -79,7 +79,8 @@ def test_autotune_cache_roundtrip(tmp_path):
     ctx.implicit_setup(1.0, 1e-2)
     first = ctx.autotune(B.NONLIN_FKPP, [1.0], cache)
     assert not first["from_cache"]
-    assert first["cpw"] in (4, 8, 16, 32) and first["wpb"] in (1, 2, 4) and 16 <= first["bn"] <= 256
+    # cpw = wpb = 0 denotes the direct-read solve variant
+    assert first["cpw"] in (0, 4, 8, 16, 32) and first["wpb"] in (0, 1, 2, 4) and 16 <= first["bn"] <= 256
     assert os.path.exists(cache)
     ctx2 = B.Context(128, 128, 64, 4.0, lz=2 * np.pi * 8, precision=B.BF16X3, chop_policy=B.CHOP_TWOTHIRDS)
     ctx2.implicit_setup(1.0, 1e-2)

@@ -171,3 +171,21 @@ def test_fkpp_fp32_per_step_error_along_trajectory():
         kappa = np.max(np.abs(1 - 2 * u)) * np.linalg.norm(u) / np.linalg.norm(u * (1 - u))
         assert e_state <= 1e-6, (seg, e_state)
         assert e_nonl <= 1e-6 * max(1.0, kappa), (seg, e_nonl, kappa)
+
+
+@pytest.mark.parametrize("nu_h,p", [(0.0, 8), (5e-7, 8)])
+def test_solve_variants_agree(nu_h, p):
+    # the staged (factor rows in shared memory) and direct-read solve variants
+    # compute the same substitution in a different summation order
+    g, ctx = pair(40, 16, 8, 1.5, lz=3.0, policy="twothirds")
+    ctx.implicit_setup(0.3, 2e-2, nu_h=nu_h, p=p)
+    s, A, Ap = (to_gpu_spec(rand_spec(g, k)) for k in (1, 2, 3))
+    outs = []
+    for direct in (0, 1):
+        ctx.set_tuning("solve_direct", direct)
+        outs.append(ctx.implicit_solve(B.STEP_ABCN, s, A, Ap, ctx.new_spec()).cpu().numpy())
+    # bar: 1e-12, or 2 kappa u for the ill-conditioned hyperviscous systems
+    st = O.Stepper(g, 0.3, 2e-2, nu_h=nu_h, p=p)
+    kappa = max(np.linalg.cond(np.eye(L.shape[0]) - 1e-2 * L) for L in st.L.values())
+    tol = max(1e-12, 2.0 * kappa * 2.0 ** -53)
+    assert np.max(np.abs(outs[0] - outs[1])) <= tol * np.max(np.abs(outs[1]))
