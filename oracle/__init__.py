@@ -18,6 +18,8 @@ for unbounded domains", Lee & Wang):
 * vortex.py      -- toroidal-poloidal velocity/vorticity Eq. (8), projection Eq. (9),
                     nonlinear term of Eq. (19)
 * diagnostics.py -- weighted L2 norm, circulation and second moment Eq. (16)
+* surrogate.py   -- FP64 reference of the learned surrogate's network, its
+                    backward pass and Adam (not in the paper; gradient reference)
 
 Pins (the tests under tests/test_oracle_*.py): library Gauss nodes, discrete
 orthonormality, library associated Legendre values, two independent Laplacian
@@ -36,3 +38,4 @@ from .operators import (del2h_closed, del2h_quadrature, rdr_matrix,  # noqa: F40
 from .integrate import Stepper, fkpp_nonlinear  # noqa: F401
 from .diagnostics import weighted_l2, circulation, second_moment  # noqa: F401
 from .vortex import VortexOps, vortex_nonlinear  # noqa: F401
+from . import surrogate  # noqa: F401
