@@ -257,6 +257,94 @@ int mlx_batch_advance(mlx_batch* batch, const int* kinds, const double* coeffs, 
 int mlx_autotune(mlx_ctx* ctx, int kind, const double* coeffs, int ncoeffs, const char* cache_path,
                  int* chosen, mlx_stream stream);
 
+/* ---- learned spectral surrogate of the vortex solver (no counterpart in the
+ * paper; its reference is the plain method itself) ----
+ * A surrogate advances the two-field vortex state s = (psi, chi) (complex128,
+ * 2 n_spec values, D = 4 n_spec reals) by nsub time steps in one call:
+ *     s_next = E^nsub s + sigma_out * f(s / sigma_in)
+ * where E = (I - dt/2 L)^-1 (I + dt/2 L) is the AB-CN step of Eq. (12) with the
+ * nonlinear term removed (dissipation of Eq. (11) only, the context's cached
+ * banded factors), and f is a 4-layer perceptron on the real view of the
+ * coefficients: f(x) = W4 h3 + b4, h_l = GELU(W_l h_{l-1} + b_l), h_0 = x, with
+ * GELU(z) = z Phi(z) (Phi the standard normal CDF).  Weights and activations
+ * enter the GEMMs as BF16 (round to nearest even), accumulation and the
+ * pre-activations are FP32, master weights and Adam moments FP32.
+ * Parameter layout, flat FP32 of mlx_sur_param_count() values:
+ *     W1 [w][D], b1 [w], W2 [w][w], b2 [w], W3 [w][w], b3 [w], W4 [D][w], b4 [D]
+ * (W_l row-major, one row per output neuron).  Training data (X, T) are device
+ * arrays [n][D]: X BF16 inputs s / sigma_in, T FP32 targets
+ * (s_next - E^nsub s) / sigma_out, filled by mlx_sur_make_pair.
+ * The surrogate owns its parameters, moments, activations and a solver-side
+ * workspace allocated on first use with a vortex context (4 two-field states).
+ * Calls on one surrogate are not thread-safe. */
+typedef struct mlx_sur mlx_sur;
+
+/* Create a surrogate for states of D reals with hidden width `width` (1..1024)
+ * and at most bmax (1..4096) samples per training or inference batch.
+ * Parameters are drawn uniformly from a counter-based hash of `seed`: hidden
+ * layers U(-sqrt(6/fan_in), +), the output layer 1e-3 times that, biases zero.
+ * Scales start at 1.  MLX_ENOMEM if device memory runs out. */
+int mlx_sur_create(int D, int width, int bmax, unsigned long long seed, mlx_sur** out);
+int mlx_sur_destroy(mlx_sur* sur);
+/* Number of FP32 parameters (w D + 2 w^2 + D w + 3 w + D), -1 for NULL. */
+long long mlx_sur_param_count(const mlx_sur* sur);
+/* Host copies of the FP32 parameters and of the gradient of the last training
+ * step (both in the parameter layout); set_params also refreshes the BF16 copies.
+ * These synchronise the device. */
+int mlx_sur_get_params(const mlx_sur* sur, float* host);
+int mlx_sur_set_params(mlx_sur* sur, const float* host);
+int mlx_sur_get_grads(const mlx_sur* sur, float* host);
+/* Host copies of sigma_in and sigma_out (D floats each).  set_scales wants
+ * sigma_in > 0, sigma_out >= 0 and not all zero (MLX_EINVAL otherwise); it also
+ * sets the loss weights w_i above.  A new surrogate has all scales 1 (w_i = 1). */
+int mlx_sur_get_scales(const mlx_sur* sur, float* in_scale, float* out_scale);
+int mlx_sur_set_scales(mlx_sur* sur, const float* in_scale, const float* out_scale);
+
+/* out = E^nsub state (device two-field states, out != state).  The context must
+ * have mlx_vortex_setup and mlx_implicit_setup done (MLX_ESTATE otherwise) and
+ * D = 4 n_spec (MLX_EINVAL otherwise). */
+int mlx_sur_propagate(mlx_ctx* ctx, mlx_sur* sur, const void* state, void* out, int nsub, mlx_stream stream);
+/* Scale fitting: observe accumulates, for one solver pair (s0, s1 = S^nsub(s0)),
+ * the squares of s0 and of the remainder r = s1 - E^nsub s0 per coefficient.
+ * finalize sets  sigma_in_i = max(rms_i(s0), in_floor rms(s0))  (1 where that is
+ * 0) and  sigma_out_i = max(rms_i(r), out_floor rms(r))  (out_floor >= 1: the
+ * uniform rms(r)), with rms_i over the observed pairs and rms over pairs and
+ * coefficients, then clears the statistics and synchronises `stream`.  A zero
+ * sigma_out_i (a coefficient the solver never changes beyond E, e.g. by symmetry)
+ * gives that coefficient no correction.  MLX_EINVAL with no observation or a
+ * negative floor.  The training loss weights coefficient i by
+ * w_i = sigma_out_i^2 / mean_j(sigma_out_j^2), so that it measures the squared
+ * coefficient-space error of the correction sigma_out * f, the judge's norm. */
+int mlx_sur_observe(mlx_ctx* ctx, mlx_sur* sur, const void* s0, const void* s1, int nsub, mlx_stream stream);
+int mlx_sur_finalize_scales(mlx_sur* sur, double in_floor, double out_floor, mlx_stream stream);
+/* One training sample from a solver pair: x (device BF16, D) = s0 / sigma_in,
+ * t (device FP32, D) = (s1 - E^nsub s0) / sigma_out. */
+int mlx_sur_make_pair(mlx_ctx* ctx, mlx_sur* sur, const void* s0, const void* s1, int nsub, void* x, float* t,
+                      mlx_stream stream);
+/* y (device FP32 [B][D]) = f(X[idx[b]]) for b < B (idx: device int32 [B]). */
+int mlx_sur_infer(mlx_sur* sur, const void* X, const int* idx, int B, float* y, mlx_stream stream);
+/* One training step on the rows idx[0..B-1] of (X, T): forward, the loss
+ * mean_{b,i} w_i (f(x_b)_i - t_{b,i})^2 (written to the device float `loss` when not
+ * NULL), its gradient by the hand-written backward pass (kept for
+ * mlx_sur_get_grads), and with lr > 0 one Adam step (beta1 0.9, beta2 0.999,
+ * eps 1e-8, bias-corrected); lr = 0 computes the gradient only. */
+int mlx_sur_train_step(mlx_sur* sur, const void* X, const float* T, const int* idx, int B, float lr, float* loss,
+                       mlx_stream stream);
+/* One surrogate call on the device two-field state (in place): the prediction
+ * E^nsub s + sigma_out f(s / sigma_in), whose m = 0 block (of each field) is then
+ * projected onto the structure of every solver state: Hermitian in k (the
+ * average of k and -k conjugated; imaginary part 0 at k = 0), and the far-field
+ * decay condition sum_n Pbar_n^0(1) s_{k,n} = 0, Pbar_n^0(1) = sqrt((2n+1)/2),
+ * solved for s_{k,0} at every k.  With judge != 0 the plain method also
+ * advances s by nsub steps (Richardson start, then AB-CN; background U0 e_y as
+ * in mlx_advance) and the relative residual ||pred - solver|| / ||solver|| (real
+ * Euclidean norm over all coefficients) decides: <= tol keeps the prediction
+ * (*accepted = 1), otherwise the solver's state is kept (*accepted = 0).
+ * Without the judge the prediction is kept (*accepted = 1, *residual = -1).
+ * accepted / residual may be NULL.  Synchronises `stream`. */
+int mlx_sur_advance(mlx_ctx* ctx, mlx_sur* sur, void* state, int nsub, double U0, int judge, double tol,
+                    int* accepted, double* residual, mlx_stream stream);
+
 /* ---- measurement support (not part of the method) ----
  * Opt-in per-launch timing: with enable != 0 every kernel launch of this context
  * is bracketed by CUDA events recorded on its stream, and mlx_advance launches

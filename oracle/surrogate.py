@@ -7,7 +7,7 @@ The network maps a real vector x of D coefficients to
     f(x) = W4 h3 + b4,   h_l = GELU(W_l h_{l-1} + b_l),  h_0 = x   (l = 1, 2, 3),
     GELU(z) = z Phi(z) = z (1 + erf(z / sqrt 2)) / 2,
 
-trained on the mean squared error L = mean_{b,i} (f(x_b)_i - t_{b,i})^2 with
+trained on the weighted mean squared error L = mean_{b,i} c_i (f(x_b)_i - t_{b,i})^2 with
 Adam (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected).  Parameters use the
 flat layout W1 [w][D], b1 [w], W2 [w][w], b2 [w], W3 [w][w], b3 [w], W4 [D][w],
 b4 [D].
@@ -82,19 +82,22 @@ def forward(theta, X, D, w, bf16=True):
     return Y, (Ws, hs, zs)
 
 
-def loss_and_grad(theta, X, T, D, w, bf16=True):
-    """Mean squared error and its gradient with respect to the flat parameters.
+def loss_and_grad(theta, X, T, D, w, bf16=True, weights=None):
+    """Weighted mean squared error  L = sum_{b,i} c_i (Y_bi - T_bi)^2 / (B D)
+    (c_i = weights[i], 1 when None) and its gradient with respect to the flat
+    parameters.
 
     Backward pass by the chain rule, layer by layer:
-      dY = 2 (Y - T) / (B D)
+      dY = 2 c (Y - T) / (B D)
       dW4 = dY^T h3,  db4 = sum_b dY,  dz3 = (dY W4) * GELU'(z3)
       dW_l = dz_l^T h_{l-1},  db_l = sum_b dz_l,  dz_{l-1} = (dz_l W_l) * GELU'(z_{l-1})
     (weights as they entered the forward products)."""
     Y, (Ws, hs, zs) = forward(theta, X, D, w, bf16)
     E = Y - T
     n = E.size
-    loss = float(np.sum(E * E) / n)
-    dY = 2.0 * E / n
+    c = np.ones(D) if weights is None else np.asarray(weights, dtype=np.float64)
+    loss = float(np.sum(c * E * E) / n)
+    dY = 2.0 * c * E / n
     grads = [None] * 8
     grads[6] = dY.T @ hs[3]
     grads[7] = dY.sum(axis=0)

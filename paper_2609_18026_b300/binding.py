@@ -25,7 +25,11 @@ EXPORTS = ("mlx_strerror", "mlx_last_cuda_error", "mlx_create", "mlx_destroy", "
            "mlx_timing", "mlx_timing_read", "mlx_kernel_count", "mlx_kernel_name",
            "mlx_set_tuning", "mlx_device_status", "mlx_forward_noalloc",
            "mlx_vortex_setup", "mlx_lap_h_solve",
-           "mlx_batch_create", "mlx_batch_destroy", "mlx_batch_advance", "mlx_autotune")
+           "mlx_batch_create", "mlx_batch_destroy", "mlx_batch_advance", "mlx_autotune",
+           "mlx_sur_create", "mlx_sur_destroy", "mlx_sur_param_count", "mlx_sur_get_params",
+           "mlx_sur_set_params", "mlx_sur_get_grads", "mlx_sur_get_scales", "mlx_sur_set_scales",
+           "mlx_sur_propagate", "mlx_sur_observe", "mlx_sur_finalize_scales", "mlx_sur_make_pair",
+           "mlx_sur_infer", "mlx_sur_train_step", "mlx_sur_advance")
 
 
 class MlxError(RuntimeError):
@@ -90,6 +94,22 @@ def load():
     lib.mlx_autotune.argtypes = [vp, i, ctypes.POINTER(d), i, ctypes.c_char_p, ctypes.POINTER(i), vp]
     lib.mlx_kernel_name.argtypes = [i]
     lib.mlx_kernel_name.restype = ctypes.c_char_p
+    f = ctypes.c_float
+    lib.mlx_sur_create.argtypes = [i, i, i, ctypes.c_ulonglong, ctypes.POINTER(vp)]
+    lib.mlx_sur_destroy.argtypes = [vp]
+    lib.mlx_sur_param_count.argtypes = [vp]
+    lib.mlx_sur_param_count.restype = ctypes.c_longlong
+    for name in ("mlx_sur_get_params", "mlx_sur_set_params", "mlx_sur_get_grads"):
+        getattr(lib, name).argtypes = [vp, vp]
+    lib.mlx_sur_get_scales.argtypes = [vp, vp, vp]
+    lib.mlx_sur_set_scales.argtypes = [vp, vp, vp]
+    lib.mlx_sur_propagate.argtypes = [vp, vp, vp, vp, i, vp]
+    lib.mlx_sur_observe.argtypes = [vp, vp, vp, vp, i, vp]
+    lib.mlx_sur_finalize_scales.argtypes = [vp, d, d, vp]
+    lib.mlx_sur_make_pair.argtypes = [vp, vp, vp, vp, i, vp, vp, vp]
+    lib.mlx_sur_infer.argtypes = [vp, vp, vp, i, vp, vp]
+    lib.mlx_sur_train_step.argtypes = [vp, vp, vp, vp, i, f, vp, vp]
+    lib.mlx_sur_advance.argtypes = [vp, vp, vp, i, d, i, d, ctypes.POINTER(i), ctypes.POINTER(d), vp]
     for name in EXPORTS:
         getattr(lib, name).restype = getattr(lib, name).restype or ctypes.c_int
     lib.mlx_strerror.restype = ctypes.c_char_p
@@ -276,3 +296,117 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+class Surrogate:
+    """Learned spectral surrogate of the vortex solver (mlx_sur): a 4-layer
+    perceptron that adds the nonlinear remainder to the linear propagator."""
+
+    def __init__(self, D, width=64, bmax=256, seed=0):
+        self.lib = load()
+        h = ctypes.c_void_p()
+        self._h = None
+        rc = self.lib.mlx_sur_create(int(D), int(width), int(bmax), int(seed), ctypes.byref(h))
+        if rc != 0:
+            raise MlxError(rc, "libmlx: mlx_sur_create failed: %s (code %d)" % (
+                self.lib.mlx_strerror(rc).decode(), rc))
+        self._h = h
+        self.D, self.width, self.bmax = int(D), int(width), int(bmax)
+        self.nparam = int(self.lib.mlx_sur_param_count(self._h))
+
+    def _check(self, rc, ctx=None):
+        if rc != 0:
+            msg = self.lib.mlx_strerror(rc).decode()
+            if ctx is not None and ctx._h is not None:
+                detail = self.lib.mlx_last_cuda_error(ctx._h).decode()
+                if detail:
+                    msg += ": " + detail
+            raise MlxError(rc, "libmlx: %s (code %d)" % (msg, rc))
+
+    def close(self):
+        if self._h is not None:
+            self.lib.mlx_sur_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def offsets(self):
+        """Offsets of W1, b1, W2, b2, W3, b3, W4, b4 in the flat parameter array."""
+        D, w = self.D, self.width
+        sizes = [w * D, w, w * w, w, w * w, w, D * w, D]
+        out, o = [], 0
+        for n in sizes:
+            out.append(o)
+            o += n
+        return out
+
+    def get_params(self):
+        import numpy as np
+        a = np.zeros(self.nparam, dtype=np.float32)
+        self._check(self.lib.mlx_sur_get_params(self._h, a.ctypes.data_as(ctypes.c_void_p)))
+        return a
+
+    def set_params(self, a):
+        import numpy as np
+        a = np.ascontiguousarray(a, dtype=np.float32)
+        assert a.size == self.nparam
+        self._check(self.lib.mlx_sur_set_params(self._h, a.ctypes.data_as(ctypes.c_void_p)))
+
+    def get_grads(self):
+        import numpy as np
+        a = np.zeros(self.nparam, dtype=np.float32)
+        self._check(self.lib.mlx_sur_get_grads(self._h, a.ctypes.data_as(ctypes.c_void_p)))
+        return a
+
+    def get_scales(self):
+        import numpy as np
+        a = np.zeros(self.D, dtype=np.float32)
+        b = np.zeros(self.D, dtype=np.float32)
+        self._check(self.lib.mlx_sur_get_scales(self._h, a.ctypes.data_as(ctypes.c_void_p),
+                                                b.ctypes.data_as(ctypes.c_void_p)))
+        return a, b
+
+    def set_scales(self, a, b):
+        import numpy as np
+        a = np.ascontiguousarray(a, dtype=np.float32)
+        b = np.ascontiguousarray(b, dtype=np.float32)
+        self._check(self.lib.mlx_sur_set_scales(self._h, a.ctypes.data_as(ctypes.c_void_p),
+                                                b.ctypes.data_as(ctypes.c_void_p)))
+
+    def propagate(self, ctx, state, out, nsub, stream=None):
+        self._check(self.lib.mlx_sur_propagate(ctx._h, self._h, _ptr(state), _ptr(out), int(nsub),
+                                               _stream(stream)), ctx)
+        return out
+
+    def observe(self, ctx, s0, s1, nsub, stream=None):
+        self._check(self.lib.mlx_sur_observe(ctx._h, self._h, _ptr(s0), _ptr(s1), int(nsub),
+                                             _stream(stream)), ctx)
+
+    def finalize_scales(self, in_floor=1e-3, out_floor=1e-3, stream=None):
+        self._check(self.lib.mlx_sur_finalize_scales(self._h, float(in_floor), float(out_floor), _stream(stream)))
+
+    def make_pair(self, ctx, s0, s1, nsub, x, t, stream=None):
+        self._check(self.lib.mlx_sur_make_pair(ctx._h, self._h, _ptr(s0), _ptr(s1), int(nsub), _ptr(x),
+                                               _ptr(t), _stream(stream)), ctx)
+
+    def infer(self, X, idx, y, stream=None):
+        self._check(self.lib.mlx_sur_infer(self._h, _ptr(X), _ptr(idx), int(idx.numel()), _ptr(y),
+                                           _stream(stream)))
+        return y
+
+    def train_step(self, X, T, idx, lr, loss=None, stream=None):
+        self._check(self.lib.mlx_sur_train_step(self._h, _ptr(X), _ptr(T), _ptr(idx), int(idx.numel()),
+                                                float(lr), _ptr(loss), _stream(stream)))
+
+    def advance(self, ctx, state, nsub, U0, judge, tol, stream=None):
+        """One call; returns (accepted, residual)."""
+        a = ctypes.c_int()
+        r = ctypes.c_double()
+        self._check(self.lib.mlx_sur_advance(ctx._h, self._h, _ptr(state), int(nsub), float(U0),
+                                             int(bool(judge)), float(tol), ctypes.byref(a), ctypes.byref(r),
+                                             _stream(stream)), ctx)
+        return bool(a.value), r.value

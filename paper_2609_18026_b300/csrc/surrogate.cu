@@ -1,0 +1,705 @@
+// Learned spectral surrogate of the vortex solver (no counterpart in the paper).
+//
+// A call advances the two-field toroidal-poloidal state s = (psi, chi) by nsub
+// time steps:
+//   s_next = E^nsub s + sigma_out * f(s / sigma_in)
+// E is the linear propagator of the AB-CN step with A = 0, (I - dt/2 L)^-1 (I + dt/2 L)
+// (the dissipation operator of Eq. (11) through the cached banded factors), so
+// the network only models the nonlinear remainder.  f is a 4-layer perceptron on
+// the real view of the coefficients (D = 4 n_spec reals):
+//   f(x) = W4 h3 + b4,  h_l = GELU(W_l h_{l-1} + b_l),  h_0 = x   (l = 1..3)
+// with BF16 weights and BF16 activations as GEMM operands, FP32 accumulation,
+// FP32 master weights and Adam moments.  The solver is the judge: with judging on,
+// the same nsub steps run through the plain method (Richardson start, then
+// AB-CN) and a prediction whose relative residual exceeds the tolerance is
+// replaced by the solver's state.
+//
+// Parameter layout (flat FP32, also used by the host-side reference of the same
+// network): W1 [w][D], b1 [w], W2 [w][w], b2 [w], W3 [w][w], b3 [w], W4 [D][w], b4 [D].
+// Activations are batch-major [B][features].
+#include "mlx_internal.cuh"
+
+#include <cuda_bf16.h>
+#include <math.h>
+
+struct mlx_sur {
+  int D = 0, w = 0, bmax = 0;
+  long long nparam = 0;
+  long long oW1, ob1, oW2, ob2, oW3, ob3, oW4, ob4;
+  float* master = nullptr;       // FP32 parameters
+  float* grad = nullptr;
+  float* m1 = nullptr;           // Adam moments
+  float* m2 = nullptr;
+  __nv_bfloat16* wbf = nullptr;  // BF16 copies of the parameters (same offsets)
+  float *z1 = nullptr, *z2 = nullptr, *z3 = nullptr, *y = nullptr;   // pre-activations, output
+  __nv_bfloat16 *x = nullptr, *a1 = nullptr, *a2 = nullptr, *a3 = nullptr;
+  float *d1 = nullptr, *d2 = nullptr, *d3 = nullptr, *dy = nullptr;  // gradients w.r.t. z_l, y
+  float* tg = nullptr;           // gathered targets [bmax][D]
+  float* in_scale = nullptr;     // sigma_in [D]
+  float* out_scale = nullptr;    // sigma_out [D]
+  float* loss = nullptr;         // device scalar
+  double* red = nullptr;         // device reductions [4]
+  // scale statistics
+  double* acc_s = nullptr;       // sum of s_i^2 over observed inputs [D]
+  double* acc_r = nullptr;       // sum of r_i^2 over observed remainders [D]
+  long long nobs = 0;
+  float inv_wref = 1.f;          // 1 / mean_i(sigma_out_i^2): loss weights w_i = sigma_out_i^2 inv_wref
+  // solver-side workspace (two-field states, D/2 complex each)
+  double2 *prop = nullptr, *pred = nullptr, *tmp = nullptr, *Ascr = nullptr;
+  long long t = 0;               // Adam step counter
+};
+
+namespace {
+
+constexpr int GBM = 64, GBN = 64, GBK = 16, GNT = 256;
+
+template <typename T> __device__ __forceinline__ float ld(const T* p, long long i);
+template <> __device__ __forceinline__ float ld<float>(const float* p, long long i) { return p[i]; }
+template <> __device__ __forceinline__ float ld<__nv_bfloat16>(const __nv_bfloat16* p, long long i) {
+  return __bfloat162float(p[i]);
+}
+
+// C[i][j] (+)= sum_k A(i, k) B(k, j) with A(i, k) = A[i * sam + k * sak] and
+// B(k, j) = B[k * sbk + j * sbn]; C row-major with leading dimension N.  The K
+// range is split over gridDim.z; with atomic != 0 partial sums are added
+// atomically (C zeroed by the caller).  The tile loaders walk the contiguous
+// index of each operand across adjacent threads (k when the k-stride is 1, else
+// the row or column index), so that global loads coalesce either way.
+template <typename TA, typename TB>
+__global__ void __launch_bounds__(GNT) k_gemm(int M, int N, int K, const TA* __restrict__ A, long long sam,
+                                             long long sak, const TB* __restrict__ Bm, long long sbk, long long sbn,
+                                             float* __restrict__ C, int atomic, int kchunk) {
+  __shared__ float As[GBK][GBM + 1];
+  __shared__ float Bs[GBK][GBN + 1];
+  const int i0 = blockIdx.y * GBM, j0 = blockIdx.x * GBN;
+  const int kb = blockIdx.z * kchunk, ke = min(K, kb + kchunk);
+  const int tid = threadIdx.x, tr = tid & 15, tc = tid >> 4;
+  const bool ak = sak == 1, bk = sbk == 1;
+  float acc[4][4] = {};
+  for (int k0 = kb; k0 < ke; k0 += GBK) {
+#pragma unroll
+    for (int q = 0; q < (GBM * GBK) / GNT; ++q) {
+      const int t = tid + q * GNT;
+      const int kk = ak ? (t % GBK) : (t / GBM), r = ak ? (t / GBK) : (t % GBM);
+      const int gi = i0 + r, gk = k0 + kk;
+      As[kk][r] = (gi < M && gk < ke) ? ld<TA>(A, (long long)gi * sam + (long long)gk * sak) : 0.f;
+    }
+#pragma unroll
+    for (int q = 0; q < (GBN * GBK) / GNT; ++q) {
+      const int t = tid + q * GNT;
+      const int kk = bk ? (t % GBK) : (t / GBN), cc = bk ? (t / GBK) : (t % GBN);
+      const int gj = j0 + cc, gk = k0 + kk;
+      Bs[kk][cc] = (gj < N && gk < ke) ? ld<TB>(Bm, (long long)gk * sbk + (long long)gj * sbn) : 0.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < GBK; ++kk) {
+      float a[4], b[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) { a[q] = As[kk][tr + 16 * q]; b[q] = Bs[kk][tc + 16 * q]; }
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) acc[x][y] = fmaf(a[x], b[y], acc[x][y]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int x = 0; x < 4; ++x) {
+    const int gi = i0 + tr + 16 * x;
+    if (gi >= M) continue;
+#pragma unroll
+    for (int y = 0; y < 4; ++y) {
+      const int gj = j0 + tc + 16 * y;
+      if (gj >= N) continue;
+      float* p = &C[(long long)gi * N + gj];
+      if (atomic) atomicAdd(p, acc[x][y]); else *p = acc[x][y];
+    }
+  }
+}
+
+__device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.f + erff(z * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_d(float z) {
+  return 0.5f * (1.f + erff(z * 0.70710678118654752f)) + z * 0.39894228040143268f * expf(-0.5f * z * z);
+}
+
+// z += b (per column); a = bf16(GELU(z)) when a != NULL
+__global__ void k_bias_act(int B, int N, float* __restrict__ z, const float* __restrict__ b,
+                           __nv_bfloat16* __restrict__ a) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (long long)B * N) return;
+  const float v = z[i] + b[i % N];
+  z[i] = v;
+  if (a) a[i] = __float2bfloat16_rn(gelu(v));
+}
+
+// Weighted squared error with w_i = sigma_out_i^2 / mean(sigma_out^2), the
+// coefficient-space squared error of the correction sigma_out * y relative to the
+// mean output scale:  loss += sum w (y - t)^2 / n,  dy = 2 w (y - t) / n.
+__global__ void k_mse(long long n, int D, const float* __restrict__ y, const float* __restrict__ tgt,
+                      const float* __restrict__ sout, float inv_wref, float* __restrict__ dy,
+                      float* __restrict__ loss) {
+  __shared__ float red[256];
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  float e = 0.f;
+  if (i < n) {
+    const float so = sout[i % D];
+    const float w = so * so * inv_wref;
+    const float d = y[i] - tgt[i];
+    dy[i] = 2.f * w * d / (float)n;
+    e = w * d * d / (float)n;
+  }
+  red[threadIdx.x] = e;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) atomicAdd(loss, red[0]);
+}
+
+__global__ void k_gelu_bwd(long long n, const float* __restrict__ z, float* __restrict__ d) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) d[i] *= gelu_d(z[i]);
+}
+
+// db[j] = sum_b d[b][j]
+__global__ void k_bias_grad(int B, int N, const float* __restrict__ d, float* __restrict__ db) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= N) return;
+  float s = 0.f;
+  for (int b = 0; b < B; ++b) s += d[(long long)b * N + j];
+  db[j] = s;
+}
+
+__global__ void k_adam(long long n, float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m1,
+                       float* __restrict__ m2, __nv_bfloat16* __restrict__ pb, float lr, float b1, float b2,
+                       float eps, float c1, float c2) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float gi = g[i];
+  const float a = b1 * m1[i] + (1.f - b1) * gi;
+  const float b = b2 * m2[i] + (1.f - b2) * gi * gi;
+  m1[i] = a;
+  m2[i] = b;
+  const float v = p[i] - lr * (a / c1) / (sqrtf(b / c2) + eps);
+  p[i] = v;
+  pb[i] = __float2bfloat16_rn(v);
+}
+
+__global__ void k_to_bf16(long long n, const float* __restrict__ p, __nv_bfloat16* __restrict__ pb) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) pb[i] = __float2bfloat16_rn(p[i]);
+}
+
+// uniform(-a, a) from a splitmix64 hash of (seed, index)
+__global__ void k_init(long long n, float* __restrict__ p, unsigned long long seed, float a) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  unsigned long long z = seed + 0x9E3779B97F4A7C15ULL * (unsigned long long)(i + 1);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  z = z ^ (z >> 31);
+  const double u = (double)(z >> 11) * (1.0 / 9007199254740992.0);
+  p[i] = (float)((2.0 * u - 1.0) * a);
+}
+
+// rows idx[b] of X [n][D] (BF16) and T [n][D] (FP32, optional) into x, tg
+__global__ void k_gather(long long D, int B, const int* __restrict__ idx, const __nv_bfloat16* __restrict__ X,
+                         const float* __restrict__ T, __nv_bfloat16* __restrict__ x, float* __restrict__ tg) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (long long)B * D) return;
+  const int b = (int)(i / D);
+  const long long k = i - (long long)b * D;
+  const long long src = (long long)idx[b] * D + k;
+  x[i] = X[src];
+  if (T) tg[i] = T[src];
+}
+
+// x = bf16(s / sigma_in)
+__global__ void k_normalize(long long D, const double* __restrict__ s, const float* __restrict__ sc,
+                            __nv_bfloat16* __restrict__ x) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < D) x[i] = __float2bfloat16_rn((float)(s[i] / (double)sc[i]));
+}
+
+// out = prop + sigma_out * y
+__global__ void k_denorm_add(long long D, const double* __restrict__ prop, const float* __restrict__ y,
+                             const float* __restrict__ sc, double* __restrict__ out) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < D) out[i] = prop[i] + (double)y[i] * (double)sc[i];
+}
+
+// r[0] += sum (a - b)^2, r[1] += sum b^2
+__global__ void k_resid(long long n, const double* __restrict__ a, const double* __restrict__ b,
+                        double* __restrict__ r) {
+  __shared__ double s0[256], s1[256];
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  double e = 0.0, f = 0.0;
+  if (i < n) { const double d = a[i] - b[i]; e = d * d; f = b[i] * b[i]; }
+  s0[threadIdx.x] = e;
+  s1[threadIdx.x] = f;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) { s0[threadIdx.x] += s0[threadIdx.x + s]; s1[threadIdx.x] += s1[threadIdx.x + s]; }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) { atomicAdd(&r[0], s0[0]); atomicAdd(&r[1], s1[0]); }
+}
+
+// acc_s[i] += s_i^2;  acc_r[i] += r_i^2;  red[2] += sum_i r_i^2  (r = s1 - prop)
+__global__ void k_observe(long long D, const double* __restrict__ s0, const double* __restrict__ s1,
+                          const double* __restrict__ prop, double* __restrict__ acc_s, double* __restrict__ acc_r,
+                          double* __restrict__ red) {
+  __shared__ double sr[256];
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  double e = 0.0;
+  if (i < D) {
+    acc_s[i] += s0[i] * s0[i];
+    const double d = s1[i] - prop[i];
+    e = d * d;
+    acc_r[i] += e;
+  }
+  sr[threadIdx.x] = e;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) sr[threadIdx.x] += sr[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) atomicAdd(&red[2], sr[0]);
+}
+
+__global__ void k_sum(long long n, const double* __restrict__ v, double* __restrict__ out) {
+  __shared__ double sr[256];
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  sr[threadIdx.x] = i < n ? v[i] : 0.0;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) sr[threadIdx.x] += sr[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) atomicAdd(out, sr[0]);
+}
+
+// sigma_in_i  = max(rms_i(s), in_floor rms(s))
+// sigma_out_i = max(rms_i(r), out_floor rms(r)), or rms(r) for out_floor >= 1
+// (rms_i over the observed samples, rms over samples and coefficients)
+__global__ void k_finalize(long long D, double nobs, double in_floor, double out_floor,
+                           const double* __restrict__ acc_s, const double* __restrict__ acc_r,
+                           const double* __restrict__ red, float* __restrict__ sin_, float* __restrict__ sout) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= D) return;
+  const double gs = sqrt(red[3] / (nobs * (double)D));
+  const double gr = sqrt(red[2] / (nobs * (double)D));
+  const double si = fmax(sqrt(acc_s[i] / nobs), in_floor * gs);
+  const double so = out_floor >= 1.0 ? gr : fmax(sqrt(acc_r[i] / nobs), out_floor * gr);
+  sin_[i] = (float)(si > 0.0 ? si : 1.0);
+  sout[i] = (float)so;   // 0 where the remainder vanishes: no correction there
+}
+
+__global__ void k_sumsq(long long n, const float* __restrict__ v, double* __restrict__ out) {
+  __shared__ double sr[256];
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const double a = i < n ? (double)v[i] : 0.0;
+  sr[threadIdx.x] = a * a;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) sr[threadIdx.x] += sr[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) atomicAdd(out, sr[0]);
+}
+
+// Structure every solver state has in its m = 0 block (per field; rows [k][n],
+// k = 0..K-1 in FFT order, n = 0..nc-1): Hermitian symmetry in k (a real field)
+// and the far-field decay condition sum_n Pbar_n^0(1) s_{k,n} = 0 for every k,
+// Pbar_n^0(1) = sqrt((2n+1)/2).  The decay condition holds for the initial state
+// (decay row of lap_h^-1), for the projected nonlinear term (decay rows of the
+// Q and (I - J) Q solves) and is kept by the implicit step (lap_h vanishes at
+// r = infinity), so the prediction is projected onto it: first the Hermitian
+// average of k and -k, then x_{k,0} from the decay condition.  One CTA per field.
+__global__ void k_constrain(double2* __restrict__ s, long long n_spec, int K, int Kz, int nc) {
+  double2* b = s + (long long)blockIdx.x * n_spec;
+  for (int t = threadIdx.x; t < Kz * nc; t += blockDim.x) {
+    const int k = t / nc, n = t % nc;
+    if (k == 0) {
+      b[n].y = 0.0;
+    } else {
+      double2 p = b[(long long)k * nc + n], q = b[(long long)(K - k) * nc + n];
+      const double re = 0.5 * (p.x + q.x), im = 0.5 * (p.y - q.y);
+      b[(long long)k * nc + n] = make_double2(re, im);
+      b[(long long)(K - k) * nc + n] = make_double2(re, -im);
+    }
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < K; k += blockDim.x) {
+    double2 acc = make_double2(0.0, 0.0);
+    for (int n = 1; n < nc; ++n) {
+      const double e = sqrt((2.0 * n + 1.0) * 0.5);
+      const double2 v = b[(long long)k * nc + n];
+      acc.x += e * v.x;
+      acc.y += e * v.y;
+    }
+    const double inv0 = -1.0 / sqrt(0.5);
+    b[(long long)k * nc] = make_double2(inv0 * acc.x, inv0 * acc.y);
+  }
+}
+
+// x = bf16(s0 / sigma_in), t = (s1 - prop) / sigma_out
+__global__ void k_make_pair(long long D, const double* __restrict__ s0, const double* __restrict__ s1,
+                            const double* __restrict__ prop, const float* __restrict__ sin_,
+                            const float* __restrict__ sout, __nv_bfloat16* __restrict__ x, float* __restrict__ t) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= D) return;
+  x[i] = __float2bfloat16_rn((float)(s0[i] / (double)sin_[i]));
+  t[i] = sout[i] > 0.f ? (float)((s1[i] - prop[i]) / (double)sout[i]) : 0.f;
+}
+
+inline unsigned nb(long long n, int t = 256) { return (unsigned)((n + t - 1) / t); }
+
+template <typename TA, typename TB>
+int gemm(int M, int N, int K, const TA* A, long long sam, long long sak, const TB* Bm, long long sbk,
+         long long sbn, float* C, cudaStream_t st) {
+  // split K until the grid covers about two waves of the 148 SMs
+  const int tiles = ((M + GBM - 1) / GBM) * ((N + GBN - 1) / GBN);
+  int splits = 1;
+  while (tiles * splits < 296 && (long long)K / (splits * 2) >= 256) splits *= 2;
+  const int kchunk = ((K + splits - 1) / splits + GBK - 1) / GBK * GBK;
+  splits = (K + kchunk - 1) / kchunk;
+  const bool atomic = splits > 1;
+  if (atomic && cudaMemsetAsync(C, 0, sizeof(float) * (size_t)M * N, st) != cudaSuccess) return MLX_ECUDA;
+  dim3 grid((N + GBN - 1) / GBN, (M + GBM - 1) / GBM, splits);
+  k_gemm<TA, TB><<<grid, GNT, 0, st>>>(M, N, K, A, sam, sak, Bm, sbk, sbn, C, atomic ? 1 : 0, kchunk);
+  return cudaGetLastError() == cudaSuccess ? MLX_OK : MLX_ECUDA;
+}
+
+void sur_free(mlx_sur* s) {
+  if (!s) return;
+  void* ps[] = {s->master, s->grad, s->m1,   s->m2,   s->wbf,   s->z1,       s->z2,        s->z3,
+                s->y,      s->x,    s->a1,   s->a2,   s->a3,    s->d1,       s->d2,        s->d3,
+                s->dy,     s->tg,   s->loss, s->red,  s->acc_s, s->in_scale, s->out_scale, s->prop,
+                s->pred,   s->tmp,  s->Ascr, s->acc_r};
+  for (void* p : ps)
+    if (p) cudaFree(p);
+  delete s;
+}
+
+// network forward for B samples in s->x
+int sur_forward(mlx_sur* s, int B, cudaStream_t st) {
+  const int D = s->D, w = s->w;
+  const __nv_bfloat16* W = s->wbf;
+  const float* P = s->master;
+  using bf = __nv_bfloat16;
+  int rc;
+  if ((rc = gemm<bf, bf>(B, w, D, s->x, D, 1, W + s->oW1, 1, D, s->z1, st))) return rc;
+  k_bias_act<<<nb((long long)B * w), 256, 0, st>>>(B, w, s->z1, P + s->ob1, s->a1);
+  if ((rc = gemm<bf, bf>(B, w, w, s->a1, w, 1, W + s->oW2, 1, w, s->z2, st))) return rc;
+  k_bias_act<<<nb((long long)B * w), 256, 0, st>>>(B, w, s->z2, P + s->ob2, s->a2);
+  if ((rc = gemm<bf, bf>(B, w, w, s->a2, w, 1, W + s->oW3, 1, w, s->z3, st))) return rc;
+  k_bias_act<<<nb((long long)B * w), 256, 0, st>>>(B, w, s->z3, P + s->ob3, s->a3);
+  if ((rc = gemm<bf, bf>(B, D, w, s->a3, w, 1, W + s->oW4, 1, w, s->y, st))) return rc;
+  k_bias_act<<<nb((long long)B * D), 256, 0, st>>>(B, D, s->y, P + s->ob4, nullptr);
+  return cudaGetLastError() == cudaSuccess ? MLX_OK : MLX_ECUDA;
+}
+
+// gradients of the mean squared error against s->tg, into s->grad
+int sur_backward(mlx_sur* s, int B, cudaStream_t st) {
+  const int D = s->D, w = s->w;
+  const __nv_bfloat16* W = s->wbf;
+  float* g = s->grad;
+  using bf = __nv_bfloat16;
+  int rc;
+  if (cudaMemsetAsync(s->loss, 0, sizeof(float), st) != cudaSuccess) return MLX_ECUDA;
+  k_mse<<<nb((long long)B * D), 256, 0, st>>>((long long)B * D, D, s->y, s->tg, s->out_scale, s->inv_wref, s->dy,
+                                              s->loss);
+  // layer 4: dW4 = dy^T a3, db4 = sum_b dy, d3 = (dy W4) * GELU'(z3)
+  if ((rc = gemm<float, bf>(D, w, B, s->dy, 1, D, s->a3, w, 1, g + s->oW4, st))) return rc;
+  k_bias_grad<<<nb(D), 256, 0, st>>>(B, D, s->dy, g + s->ob4);
+  if ((rc = gemm<float, bf>(B, w, D, s->dy, D, 1, W + s->oW4, w, 1, s->d3, st))) return rc;
+  k_gelu_bwd<<<nb((long long)B * w), 256, 0, st>>>((long long)B * w, s->z3, s->d3);
+  // layer 3
+  if ((rc = gemm<float, bf>(w, w, B, s->d3, 1, w, s->a2, w, 1, g + s->oW3, st))) return rc;
+  k_bias_grad<<<nb(w), 256, 0, st>>>(B, w, s->d3, g + s->ob3);
+  if ((rc = gemm<float, bf>(B, w, w, s->d3, w, 1, W + s->oW3, w, 1, s->d2, st))) return rc;
+  k_gelu_bwd<<<nb((long long)B * w), 256, 0, st>>>((long long)B * w, s->z2, s->d2);
+  // layer 2
+  if ((rc = gemm<float, bf>(w, w, B, s->d2, 1, w, s->a1, w, 1, g + s->oW2, st))) return rc;
+  k_bias_grad<<<nb(w), 256, 0, st>>>(B, w, s->d2, g + s->ob2);
+  if ((rc = gemm<float, bf>(B, w, w, s->d2, w, 1, W + s->oW2, w, 1, s->d1, st))) return rc;
+  k_gelu_bwd<<<nb((long long)B * w), 256, 0, st>>>((long long)B * w, s->z1, s->d1);
+  // layer 1: dW1 = d1^T x
+  if ((rc = gemm<float, bf>(w, D, B, s->d1, 1, w, s->x, D, 1, g + s->oW1, st))) return rc;
+  k_bias_grad<<<nb(w), 256, 0, st>>>(B, w, s->d1, g + s->ob1);
+  return cudaGetLastError() == cudaSuccess ? MLX_OK : MLX_ECUDA;
+}
+
+// solver-side workspace for a vortex context
+int sur_bind(mlx_ctx* c, mlx_sur* s) {
+  if (!c->vortex_ready || !c->implicit_ready) return MLX_ESTATE;
+  if ((long long)s->D != 4 * c->n_spec) return MLX_EINVAL;
+  if (s->prop) return MLX_OK;
+  const size_t b = sizeof(double2) * 2 * (size_t)c->n_spec;
+  for (double2** p : {&s->prop, &s->pred, &s->tmp, &s->Ascr})
+    if (cudaMalloc(p, b) != cudaSuccess) { c->last_err = "surrogate workspace allocation"; return MLX_ENOMEM; }
+  return MLX_OK;
+}
+
+// out = E^nsub s for the two-field state (ping-pong through tmp; s is not modified)
+int propagate(mlx_ctx* c, const double2* s, double2* out, double2* tmp, int nsub, cudaStream_t st) {
+  const double2* src = s;
+  for (int k = 0; k < nsub; ++k) {
+    double2* dst = ((nsub - 1 - k) % 2 == 0) ? out : tmp;
+    for (int f = 0; f < 2; ++f) {
+      const long long o = (long long)f * c->n_spec;
+      int rc = mlx_band_solve(c, MLX_STEP_ABCN, src + o, nullptr, nullptr, dst + o, st);
+      if (rc) return rc;
+    }
+    src = dst;
+  }
+  return MLX_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mlx_sur_create(int D, int width, int bmax, unsigned long long seed, mlx_sur** out) {
+  if (!out) return MLX_EINVAL;
+  *out = nullptr;
+  if (D < 1 || width < 1 || width > 1024 || bmax < 1 || bmax > 4096) return MLX_EINVAL;
+  mlx_sur* s = new mlx_sur();
+  s->D = D; s->w = width; s->bmax = bmax;
+  const long long w = width, Dl = D, bm = bmax;
+  long long o = 0;
+  s->oW1 = o; o += w * Dl;
+  s->ob1 = o; o += w;
+  s->oW2 = o; o += w * w;
+  s->ob2 = o; o += w;
+  s->oW3 = o; o += w * w;
+  s->ob3 = o; o += w;
+  s->oW4 = o; o += Dl * w;
+  s->ob4 = o; o += Dl;
+  s->nparam = o;
+  bool ok = true;
+  auto A = [&](void** p, size_t b) { if (cudaMalloc(p, b) != cudaSuccess) ok = false; };
+  A((void**)&s->master, sizeof(float) * o);
+  A((void**)&s->grad, sizeof(float) * o);
+  A((void**)&s->m1, sizeof(float) * o);
+  A((void**)&s->m2, sizeof(float) * o);
+  A((void**)&s->wbf, sizeof(__nv_bfloat16) * o);
+  A((void**)&s->z1, sizeof(float) * bm * w);
+  A((void**)&s->z2, sizeof(float) * bm * w);
+  A((void**)&s->z3, sizeof(float) * bm * w);
+  A((void**)&s->y, sizeof(float) * bm * Dl);
+  A((void**)&s->x, sizeof(__nv_bfloat16) * bm * Dl);
+  A((void**)&s->a1, sizeof(__nv_bfloat16) * bm * w);
+  A((void**)&s->a2, sizeof(__nv_bfloat16) * bm * w);
+  A((void**)&s->a3, sizeof(__nv_bfloat16) * bm * w);
+  A((void**)&s->d1, sizeof(float) * bm * w);
+  A((void**)&s->d2, sizeof(float) * bm * w);
+  A((void**)&s->d3, sizeof(float) * bm * w);
+  A((void**)&s->dy, sizeof(float) * bm * Dl);
+  A((void**)&s->tg, sizeof(float) * bm * Dl);
+  A((void**)&s->in_scale, sizeof(float) * Dl);
+  A((void**)&s->out_scale, sizeof(float) * Dl);
+  A((void**)&s->loss, sizeof(float));
+  A((void**)&s->red, sizeof(double) * 4);
+  A((void**)&s->acc_s, sizeof(double) * Dl);
+  A((void**)&s->acc_r, sizeof(double) * Dl);
+  if (!ok) { sur_free(s); return MLX_ENOMEM; }
+  // He-uniform hidden layers; the output layer starts 1e3 times smaller so that f ~ 0
+  const float a1 = sqrtf(6.f / D), ah = sqrtf(6.f / width), a4 = 1e-3f * sqrtf(6.f / width);
+  k_init<<<nb(w * Dl), 256>>>(w * Dl, s->master + s->oW1, seed * 8 + 1, a1);
+  k_init<<<nb(w * w), 256>>>(w * w, s->master + s->oW2, seed * 8 + 2, ah);
+  k_init<<<nb(w * w), 256>>>(w * w, s->master + s->oW3, seed * 8 + 3, ah);
+  k_init<<<nb(Dl * w), 256>>>(Dl * w, s->master + s->oW4, seed * 8 + 4, a4);
+  bool z = cudaMemset(s->master + s->ob1, 0, sizeof(float) * w) == cudaSuccess &&
+           cudaMemset(s->master + s->ob2, 0, sizeof(float) * w) == cudaSuccess &&
+           cudaMemset(s->master + s->ob3, 0, sizeof(float) * w) == cudaSuccess &&
+           cudaMemset(s->master + s->ob4, 0, sizeof(float) * Dl) == cudaSuccess &&
+           cudaMemset(s->m1, 0, sizeof(float) * o) == cudaSuccess &&
+           cudaMemset(s->m2, 0, sizeof(float) * o) == cudaSuccess &&
+           cudaMemset(s->acc_s, 0, sizeof(double) * Dl) == cudaSuccess &&
+           cudaMemset(s->acc_r, 0, sizeof(double) * Dl) == cudaSuccess &&
+           cudaMemset(s->red, 0, sizeof(double) * 4) == cudaSuccess;
+  k_to_bf16<<<nb(o), 256>>>(o, s->master, s->wbf);
+  // unit scales until fitted
+  std::vector<float> one(D, 1.f);
+  z = z && cudaMemcpy(s->in_scale, one.data(), sizeof(float) * Dl, cudaMemcpyHostToDevice) == cudaSuccess &&
+      cudaMemcpy(s->out_scale, one.data(), sizeof(float) * Dl, cudaMemcpyHostToDevice) == cudaSuccess;
+  if (!z || cudaDeviceSynchronize() != cudaSuccess) { sur_free(s); return MLX_ECUDA; }
+  *out = s;
+  return MLX_OK;
+}
+
+int mlx_sur_destroy(mlx_sur* s) {
+  if (!s) return MLX_EINVAL;
+  cudaDeviceSynchronize();
+  sur_free(s);
+  return MLX_OK;
+}
+
+long long mlx_sur_param_count(const mlx_sur* s) { return s ? s->nparam : -1; }
+
+int mlx_sur_get_params(const mlx_sur* s, float* host) {
+  if (!s || !host) return MLX_EINVAL;
+  return cudaMemcpy(host, s->master, sizeof(float) * s->nparam, cudaMemcpyDeviceToHost) == cudaSuccess
+             ? MLX_OK : MLX_ECUDA;
+}
+
+int mlx_sur_set_params(mlx_sur* s, const float* host) {
+  if (!s || !host) return MLX_EINVAL;
+  if (cudaMemcpy(s->master, host, sizeof(float) * s->nparam, cudaMemcpyHostToDevice) != cudaSuccess)
+    return MLX_ECUDA;
+  k_to_bf16<<<nb(s->nparam), 256>>>(s->nparam, s->master, s->wbf);
+  return cudaDeviceSynchronize() == cudaSuccess ? MLX_OK : MLX_ECUDA;
+}
+
+int mlx_sur_get_grads(const mlx_sur* s, float* host) {
+  if (!s || !host) return MLX_EINVAL;
+  return cudaMemcpy(host, s->grad, sizeof(float) * s->nparam, cudaMemcpyDeviceToHost) == cudaSuccess
+             ? MLX_OK : MLX_ECUDA;
+}
+
+int mlx_sur_get_scales(const mlx_sur* s, float* in_scale, float* out_scale) {
+  if (!s || !in_scale || !out_scale) return MLX_EINVAL;
+  if (cudaMemcpy(in_scale, s->in_scale, sizeof(float) * s->D, cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(out_scale, s->out_scale, sizeof(float) * s->D, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return MLX_ECUDA;
+  return MLX_OK;
+}
+
+int mlx_sur_set_scales(mlx_sur* s, const float* in_scale, const float* out_scale) {
+  if (!s || !in_scale || !out_scale) return MLX_EINVAL;
+  double q = 0.0;
+  for (int i = 0; i < s->D; ++i) {
+    if (!(in_scale[i] > 0.f) || !(out_scale[i] >= 0.f)) return MLX_EINVAL;
+    q += (double)out_scale[i] * out_scale[i];
+  }
+  if (!(q > 0.0)) return MLX_EINVAL;
+  if (cudaMemcpy(s->in_scale, in_scale, sizeof(float) * s->D, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(s->out_scale, out_scale, sizeof(float) * s->D, cudaMemcpyHostToDevice) != cudaSuccess)
+    return MLX_ECUDA;
+  s->inv_wref = (float)(s->D / q);
+  return MLX_OK;
+}
+
+int mlx_sur_propagate(mlx_ctx* c, mlx_sur* s, const void* state, void* out, int nsub, mlx_stream stream) {
+  if (!c || !s || !state || !out || nsub < 1 || state == out) return MLX_EINVAL;
+  int rc = sur_bind(c, s);
+  if (rc) return rc;
+  return propagate(c, (const double2*)state, (double2*)out, s->tmp, nsub, (cudaStream_t)stream);
+}
+
+int mlx_sur_observe(mlx_ctx* c, mlx_sur* s, const void* s0, const void* s1, int nsub, mlx_stream stream) {
+  if (!c || !s || !s0 || !s1 || nsub < 1) return MLX_EINVAL;
+  int rc = sur_bind(c, s);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  if ((rc = propagate(c, (const double2*)s0, s->prop, s->tmp, nsub, st))) return rc;
+  k_observe<<<nb(s->D), 256, 0, st>>>(s->D, (const double*)s0, (const double*)s1, (const double*)s->prop, s->acc_s,
+                                      s->acc_r, s->red);
+  MLX_LAUNCH_CHECK(c);
+  s->nobs += 1;
+  return MLX_OK;
+}
+
+int mlx_sur_finalize_scales(mlx_sur* s, double in_floor, double out_floor, mlx_stream stream) {
+  if (!s || s->nobs < 1 || !(in_floor >= 0.0) || !(out_floor >= 0.0)) return MLX_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (cudaMemsetAsync(s->red + 3, 0, sizeof(double), st) != cudaSuccess) return MLX_ECUDA;
+  k_sum<<<nb(s->D), 256, 0, st>>>(s->D, s->acc_s, s->red + 3);
+  k_finalize<<<nb(s->D), 256, 0, st>>>(s->D, (double)s->nobs, in_floor, out_floor, s->acc_s, s->acc_r, s->red,
+                                       s->in_scale, s->out_scale);
+  if (cudaMemsetAsync(s->red, 0, sizeof(double) * 4, st) != cudaSuccess) return MLX_ECUDA;
+  k_sumsq<<<nb(s->D), 256, 0, st>>>(s->D, s->out_scale, s->red);
+  double q = 0.0;
+  if (cudaMemcpyAsync(&q, s->red, sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaMemsetAsync(s->acc_s, 0, sizeof(double) * s->D, st) != cudaSuccess ||
+      cudaMemsetAsync(s->acc_r, 0, sizeof(double) * s->D, st) != cudaSuccess ||
+      cudaMemsetAsync(s->red, 0, sizeof(double) * 4, st) != cudaSuccess)
+    return MLX_ECUDA;
+  s->nobs = 0;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return MLX_ECUDA;
+  s->inv_wref = q > 0.0 ? (float)(s->D / q) : 1.f;
+  return MLX_OK;
+}
+
+int mlx_sur_make_pair(mlx_ctx* c, mlx_sur* s, const void* s0, const void* s1, int nsub, void* x, float* t,
+                      mlx_stream stream) {
+  if (!c || !s || !s0 || !s1 || !x || !t || nsub < 1) return MLX_EINVAL;
+  int rc = sur_bind(c, s);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  if ((rc = propagate(c, (const double2*)s0, s->prop, s->tmp, nsub, st))) return rc;
+  k_make_pair<<<nb(s->D), 256, 0, st>>>(s->D, (const double*)s0, (const double*)s1, (const double*)s->prop,
+                                        s->in_scale, s->out_scale, (__nv_bfloat16*)x, t);
+  MLX_LAUNCH_CHECK(c);
+  return MLX_OK;
+}
+
+int mlx_sur_infer(mlx_sur* s, const void* X, const int* idx, int B, float* y, mlx_stream stream) {
+  if (!s || !X || !idx || !y || B < 1 || B > s->bmax) return MLX_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  k_gather<<<nb((long long)B * s->D), 256, 0, st>>>(s->D, B, idx, (const __nv_bfloat16*)X, nullptr, s->x, nullptr);
+  int rc = sur_forward(s, B, st);
+  if (rc) return rc;
+  return cudaMemcpyAsync(y, s->y, sizeof(float) * B * (size_t)s->D, cudaMemcpyDeviceToDevice, st) == cudaSuccess
+             ? MLX_OK : MLX_ECUDA;
+}
+
+int mlx_sur_train_step(mlx_sur* s, const void* X, const float* T, const int* idx, int B, float lr, float* loss,
+                       mlx_stream stream) {
+  if (!s || !X || !T || !idx || B < 1 || B > s->bmax || !(lr >= 0.f)) return MLX_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  k_gather<<<nb((long long)B * s->D), 256, 0, st>>>(s->D, B, idx, (const __nv_bfloat16*)X, T, s->x, s->tg);
+  int rc = sur_forward(s, B, st);
+  if (rc) return rc;
+  if ((rc = sur_backward(s, B, st))) return rc;
+  if (loss && cudaMemcpyAsync(loss, s->loss, sizeof(float), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+    return MLX_ECUDA;
+  if (lr > 0.f) {
+    s->t += 1;
+    const float c1 = 1.f - powf(0.9f, (float)s->t), c2 = 1.f - powf(0.999f, (float)s->t);
+    k_adam<<<nb(s->nparam), 256, 0, st>>>(s->nparam, s->master, s->grad, s->m1, s->m2, s->wbf, lr, 0.9f, 0.999f,
+                                          1e-8f, c1, c2);
+  }
+  return cudaGetLastError() == cudaSuccess ? MLX_OK : MLX_ECUDA;
+}
+
+int mlx_sur_advance(mlx_ctx* c, mlx_sur* s, void* state, int nsub, double U0, int judge, double tol, int* accepted,
+                    double* residual, mlx_stream stream) {
+  if (!c || !s || !state || nsub < 1 || !(tol >= 0.0)) return MLX_EINVAL;
+  int rc = sur_bind(c, s);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  double2* S = (double2*)state;
+  const long long n = 2 * c->n_spec;   // complex values of the state
+  if ((rc = propagate(c, S, s->prop, s->tmp, nsub, st))) return rc;
+  k_normalize<<<nb(s->D), 256, 0, st>>>(s->D, (const double*)S, s->in_scale, s->x);
+  if ((rc = sur_forward(s, 1, st))) return rc;
+  k_denorm_add<<<nb(s->D), 256, 0, st>>>(s->D, (const double*)s->prop, s->y, s->out_scale, (double*)s->pred);
+  k_constrain<<<2, 256, 0, st>>>(s->pred, c->n_spec, c->K, c->Kz, c->nc);
+  MLX_LAUNCH_CHECK(c);
+  int acc = 1;
+  double res = -1.0;
+  if (judge) {
+    // S^nsub(s) of the plain method, written over the state
+    if ((rc = mlx_advance(c, MLX_NONLIN_VORTEX, &U0, 1, S, s->Ascr, nsub, 1, stream))) return rc;
+    MLX_CUDA_TRY(c, cudaMemsetAsync(s->red, 0, sizeof(double) * 2, st));
+    k_resid<<<nb(s->D), 256, 0, st>>>(s->D, (const double*)s->pred, (const double*)S, s->red);
+    MLX_LAUNCH_CHECK(c);
+    double hr[2];
+    MLX_CUDA_TRY(c, cudaMemcpyAsync(hr, s->red, sizeof(hr), cudaMemcpyDeviceToHost, st));
+    MLX_CUDA_TRY(c, cudaStreamSynchronize(st));
+    res = sqrt(hr[0] / (hr[1] > 0.0 ? hr[1] : 1.0));
+    acc = (res <= tol) ? 1 : 0;
+  }
+  if (acc) MLX_CUDA_TRY(c, cudaMemcpyAsync(S, s->pred, sizeof(double2) * n, cudaMemcpyDeviceToDevice, st));
+  MLX_CUDA_TRY(c, cudaStreamSynchronize(st));
+  if (accepted) *accepted = acc;
+  if (residual) *residual = res;
+  return MLX_OK;
+}
+
+}  // extern "C"

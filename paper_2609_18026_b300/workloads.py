@@ -17,6 +17,7 @@ Workloads (all analytic, as in the paper's examples; no dataset is involved):
 * vortex_pair_omega   -- counter-rotating Lamb-Oseen pair with a seeded axial displacement
 * random_spectral     -- seeded random coefficients in the flat ragged layout
 * batch_instances     -- the uneven batch of independent 2-D/3-D solves
+* surrogate_trajectories -- seeded vortex-pair variants the learned surrogate trains on
 """
 
 import math
@@ -149,3 +150,21 @@ def batch_initial(inst, r, phi, z):
     if inst["nz"] > 1:
         f = f * (1.0 + 0.1 * np.cos(2.0 * math.pi * z / inst["lz"]))
     return f
+
+
+def surrogate_trajectories(n=2000, seed=20261203):
+    """Seeded parameters of the vortex-pair trajectories for the learned surrogate.
+
+    Per trajectory: axial displacement amplitude 1e-3 x U[0.5, 2], perturbation-plane
+    inclination U[40, 56] degrees, separation b ~ U[0.9, 1.1], core radius
+    a ~ U[0.18, 0.22]; circulation 2 pi and one axial wavelength as in
+    vortex_pair_omega."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for i in range(n):
+        amp = 1e-3 * float(rng.uniform(0.5, 2.0))
+        incl = float(rng.uniform(40.0, 56.0))
+        b = float(rng.uniform(0.9, 1.1))
+        a = float(rng.uniform(0.18, 0.22))
+        out.append(dict(index=i, amp=amp, incl_deg=incl, b=b, a=a))
+    return out

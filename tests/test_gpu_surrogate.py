@@ -1,0 +1,289 @@
+"""GPU checks of the learned surrogate: its BF16 training kernels against the FP64
+reference network (oracle/surrogate.py), its propagator against the oracle's
+linear AB-CN step, the judge and fallback against the plain solver, and the gain
+of a trained network over the propagator alone."""
+
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+import oracle.surrogate as OS
+from paper_2609_18026_b300 import binding as B
+from paper_2609_18026_b300 import surrogate as SG
+from paper_2609_18026_b300 import workloads as W
+
+from gpu_common import pair, to_gpu_spec
+
+pytestmark = pytest.mark.gpu
+
+
+def _theta(D, w, seed):
+    """Seeded parameters with every layer at He scale (so all gradients are O(1))."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    parts = []
+    for shape, fan in (((w, D), D), ((w,), None), ((w, w), w), ((w,), None), ((w, w), w), ((w,), None),
+                       ((D, w), w), ((D,), None)):
+        n = int(np.prod(shape))
+        if fan is None:
+            parts.append(rng.uniform(-0.1, 0.1, n))
+        else:
+            a = math.sqrt(6.0 / fan)
+            parts.append(rng.uniform(-a, a, n))
+    return np.concatenate(parts).astype(np.float32)
+
+
+def _batch(D, Bn, seed):
+    import torch
+    rng = np.random.Generator(np.random.PCG64(seed))
+    X = torch.as_tensor(rng.standard_normal((Bn, D)), dtype=torch.float32).to(torch.bfloat16).cuda()
+    T = torch.as_tensor(rng.standard_normal((Bn, D)) * 0.3, dtype=torch.float32).cuda()
+    return X, T
+
+
+def _blocks(v, D, w):
+    return OS.unpack(v.astype(np.float64), D, w)
+
+
+@pytest.mark.parametrize("D,w,Bn,weighted", [(1000, 64, 8, False), (333, 17, 5, True), (202444, 64, 4, False),
+                                             (202444, 64, 4, True)])
+def test_gradients_match_fp64_reference(D, w, Bn, weighted):
+    """Loss and every parameter block's gradient against the FP64 reference with
+    the same BF16 rounding points.  Bar: 1e-3 relative per block.  What separates
+    the two sides is FP32 accumulation (relative sqrt(K) 2^-24 <= 3e-5 for
+    K <= 2e5) and BF16 activations that round to the other neighbour when the
+    FP32 and FP64 pre-activations straddle a rounding boundary (probability about
+    1e-6 / 2^-8 per activation, each moving one activation by 2^-8)."""
+    import torch
+    sur = B.Surrogate(D, width=w, bmax=Bn, seed=1)
+    theta = _theta(D, w, 2)
+    sur.set_params(theta)
+    X, T = _batch(D, Bn, 3)
+    weights = None
+    if weighted:
+        # output scales weight the loss by sigma_out_i^2 / mean(sigma_out^2); some are 0
+        so = np.random.Generator(np.random.PCG64(13)).uniform(0.0, 2.0, D).astype(np.float32)
+        so[::7] = 0.0
+        sur.set_scales(np.ones(D, np.float32), so)
+        weights = so.astype(np.float64) ** 2 / np.mean(so.astype(np.float64) ** 2)
+    idx = torch.arange(Bn, dtype=torch.int32, device="cuda")
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    sur.train_step(X, T, idx, 0.0, loss)
+    torch.cuda.synchronize()
+    g_gpu = sur.get_grads()
+    ref_loss, g_ref = OS.loss_and_grad(theta.astype(np.float64), X.float().cpu().double().numpy(),
+                                       T.cpu().double().numpy(), D, w, bf16=True, weights=weights)
+    assert abs(loss.item() - ref_loss) <= 1e-5 * ref_loss
+    names = ["W1", "b1", "W2", "b2", "W3", "b3", "W4", "b4"]
+    for name, a, b in zip(names, _blocks(g_gpu, D, w), _blocks(g_ref, D, w)):
+        err = np.linalg.norm(a - b) / np.linalg.norm(b)
+        assert err <= 1e-3, (name, err)
+    # the forward output itself
+    y = torch.zeros((Bn, D), dtype=torch.float32, device="cuda")
+    sur.infer(X, idx, y)
+    Y, _ = OS.forward(theta.astype(np.float64), X.float().cpu().double().numpy(), D, w, bf16=True)
+    assert np.linalg.norm(y.cpu().numpy() - Y) <= 1e-4 * np.linalg.norm(Y)
+    sur.close()
+
+
+def test_adam_step_matches_reference():
+    import torch
+    D, w, Bn = 500, 32, 6
+    sur = B.Surrogate(D, width=w, bmax=Bn, seed=4)
+    theta = _theta(D, w, 5)
+    sur.set_params(theta)
+    X, T = _batch(D, Bn, 6)
+    idx = torch.arange(Bn, dtype=torch.int32, device="cuda")
+    sur.train_step(X, T, idx, 1e-3)
+    torch.cuda.synchronize()
+    new = sur.get_params().astype(np.float64)
+    g = sur.get_grads().astype(np.float64)
+    want, _, _ = OS.adam_step(theta.astype(np.float64), g, np.zeros_like(g), np.zeros_like(g), 1, 1e-3)
+    assert np.max(np.abs(new - want) / (1e-7 + 1e-6 * np.abs(want))) <= 1.0
+    sur.close()
+
+
+def test_training_fits_a_smooth_map():
+    """Adam through the hand-written kernels fits a fixed smooth map of the input."""
+    import torch
+    D, w, n = 256, 64, 512
+    rng = np.random.Generator(np.random.PCG64(9))
+    Xh = rng.standard_normal((n, D))
+    A = rng.standard_normal((D, 8)) / math.sqrt(D)
+    Bm = rng.standard_normal((8, D))
+    Th = np.tanh(Xh @ A) @ Bm
+    X = torch.as_tensor(Xh, dtype=torch.float32).to(torch.bfloat16).cuda()
+    T = torch.as_tensor(Th, dtype=torch.float32).cuda()
+    sur = B.Surrogate(D, width=w, bmax=64, seed=3)
+    hist, _ = SG.train(sur, X, T, n, torch, epochs=60, batch=64, lr=3e-3)
+    assert hist[-1] < 0.05 * hist[0], hist[::10]
+    sur.close()
+
+
+def _vortex_ctx(nr=24, nphi=16, nz=8, prec=B.FP64, nu=1e-3, dt=1e-3):
+    g, ctx = pair(nr, nphi, nz, 1.0, lz=8.6, policy="twothirds", precision=prec)
+    ctx.vortex_setup()
+    ctx.implicit_setup(nu, dt, nu_h=0.0, p=8)
+    return g, ctx
+
+
+def test_propagator_matches_oracle_linear_step():
+    g, ctx = _vortex_ctx()
+    psi = W.random_spectral(g.nc, g.M, g.Kz, seed=21, scale_decay=0.3)
+    chi = W.random_spectral(g.nc, g.M, g.Kz, seed=22, scale_decay=0.3)
+    s = to_gpu_spec(np.concatenate([psi, chi]))
+    sur = B.Surrogate(4 * ctx.n_spec, width=8, bmax=1, seed=0)
+    out = to_gpu_spec(np.zeros(2 * ctx.n_spec, np.complex128))
+    sur.propagate(ctx, s, out, 3)
+    st = O.Stepper(g, 1e-3, 1e-3)
+    ref = O.from_flat(g, psi) + O.from_flat(g, chi)
+    z = [np.zeros_like(b) for b in ref]
+    for _ in range(3):
+        ref = st.abcn(ref, z, z)
+    o = out.cpu().numpy()
+    got = O.from_flat(g, o[:ctx.n_spec]) + O.from_flat(g, o[ctx.n_spec:])
+    assert O.spec_rel_err(g, got, ref) <= 1e-12
+    sur.close()
+
+
+def _pair_state(ctx, g, prm=None):
+    import torch
+    prm = prm or dict(b=1.0, a=0.2, amp=1e-3, incl_deg=48.0)
+    cfg = dict(SG.CONFIG, lz=8.6)
+    return SG.initial_state(ctx, cfg, prm, torch)
+
+
+def test_judge_fallback_keeps_solver_state_exactly():
+    """tol = 0 rejects every prediction: the state must be the plain solver's, bitwise."""
+    import torch
+    g, ctx = _vortex_ctx(prec=B.FP32)
+    s0 = _pair_state(ctx, g)
+    sur = B.Surrogate(4 * ctx.n_spec, width=16, bmax=1, seed=7)
+    s = s0.clone()
+    acc, res = sur.advance(ctx, s, 4, -1.0, True, 0.0)
+    ref = s0.clone()
+    ctx.advance(B.NONLIN_VORTEX, [-1.0], ref, torch.zeros_like(ref), 4, True)
+    assert not acc and res > 0
+    assert torch.equal(s, ref)
+    sur.close()
+
+
+def _constrain_m0(v, ctx):
+    """The m = 0 structure of a solver state, by its definition: Hermitian in k
+    (average of k and conj(-k)), then x_{k,0} from sum_n sqrt((2n+1)/2) x_{k,n} = 0."""
+    v = v.clone()
+    K, Kz, nc, n = ctx.K, ctx.Kz, ctx.nc, ctx.n_spec
+    e = torch_sqrt_weights(nc)
+    for f in range(2):
+        blk = v[f * n:f * n + K * nc].view(K, nc)
+        blk[0] = blk[0].real.to(blk.dtype)
+        for k in range(1, Kz):
+            a = 0.5 * (blk[k] + blk[K - k].conj())
+            blk[k] = a
+            blk[K - k] = a.conj()
+        blk[:, 0] = -(blk[:, 1:] * e[1:]).sum(dim=1) / e[0]
+    return v
+
+
+def torch_sqrt_weights(nc):
+    import torch
+    return torch.sqrt((2.0 * torch.arange(nc, dtype=torch.float64, device="cuda") + 1.0) / 2.0)
+
+
+def test_accepted_prediction_is_propagator_plus_network():
+    """tol = inf accepts: state = E^n s + sigma_out f(bf16(s / sigma_in)) with the
+    m = 0 block projected onto the structure of solver states, and the reported
+    residual is ||pred - solver|| / ||solver||."""
+    import torch
+    g, ctx = _vortex_ctx(prec=B.FP32)
+    s0 = _pair_state(ctx, g)
+    D = 4 * ctx.n_spec
+    sur = B.Surrogate(D, width=16, bmax=1, seed=8)
+    theta = _theta(D, 16, 9) * 0.01
+    sur.set_params(theta)
+    sin_ = np.full(D, 0.5, np.float32)
+    sout = np.full(D, 2e-3, np.float32)
+    sur.set_scales(sin_, sout)
+    s = s0.clone()
+    acc, res = sur.advance(ctx, s, 4, -1.0, True, 1e30)
+    assert acc
+    prop = torch.zeros_like(s0)
+    sur.propagate(ctx, s0, prop, 4)
+    x = (torch.view_as_real(s0).reshape(-1) / 0.5).float().to(torch.bfloat16).reshape(1, D)
+    y = torch.zeros((1, D), dtype=torch.float32, device="cuda")
+    sur.infer(x, torch.zeros(1, dtype=torch.int32, device="cuda"), y)
+    pred = torch.view_as_real(prop).reshape(-1) + 2e-3 * y.double().reshape(-1)
+    pred = torch.view_as_real(_constrain_m0(torch.view_as_complex(pred.view(-1, 2)), ctx)).reshape(-1)
+    got = torch.view_as_real(s).reshape(-1)
+    corr = (pred - torch.view_as_real(prop).reshape(-1)).norm()
+    assert (got - pred).norm() <= 1e-5 * corr + 1e-14 * pred.norm()
+    sol = s0.clone()
+    ctx.advance(B.NONLIN_VORTEX, [-1.0], sol, torch.zeros_like(sol), 4, True)
+    want = float((got - torch.view_as_real(sol).reshape(-1)).norm() / torch.view_as_real(sol).norm())
+    assert abs(res - want) <= 1e-6 * want
+    sur.close()
+
+
+def test_scale_statistics():
+    import torch
+    g, ctx = _vortex_ctx(prec=B.FP32)
+    D = 4 * ctx.n_spec
+    sur = B.Surrogate(D, width=8, bmax=1, seed=0)
+    cfg = dict(SG.CONFIG, windows=3, nsub=4)
+    tr = SG.trajectory(ctx, cfg, dict(b=1.0, a=0.2, amp=1e-3, incl_deg=48.0), torch)
+    S0, R = [], []
+    tmp = torch.zeros_like(tr[0])
+    for j in range(3):
+        sur.observe(ctx, tr[j], tr[j + 1], 4)
+        sur.propagate(ctx, tr[j], tmp, 4)
+        S0.append(torch.view_as_real(tr[j]).reshape(-1).cpu().numpy())
+        R.append(torch.view_as_real(tr[j + 1] - tmp).reshape(-1).cpu().numpy())
+    sur.finalize_scales(1e-2, 1.0)
+    sin_, sout = sur.get_scales()
+    S0, R = np.array(S0), np.array(R)
+    rms_i = np.sqrt(np.mean(S0 ** 2, axis=0))
+    want_in = np.maximum(rms_i, 1e-2 * np.sqrt(np.mean(S0 ** 2)))
+    assert np.max(np.abs(sin_ - want_in) / want_in) <= 1e-6
+    assert abs(sout[0] - np.sqrt(np.mean(R ** 2))) <= 1e-6 * sout[0] and np.all(sout == sout[0])
+    # per-coefficient output scales with a floor (statistics were cleared: observe again)
+    for j in range(3):
+        sur.observe(ctx, tr[j], tr[j + 1], 4)
+    sur.finalize_scales(1e-2, 1e-3)
+    _, sout = sur.get_scales()
+    want_out = np.maximum(np.sqrt(np.mean(R ** 2, axis=0)), 1e-3 * np.sqrt(np.mean(R ** 2)))
+    assert np.max(np.abs(sout - want_out) / want_out) <= 1e-6
+    sur.close()
+
+
+def test_gain_over_propagator_alone():
+    """A network trained on solver windows beats the linear propagator alone on
+    held-out trajectories, in one-window residual and in the free-running chain,
+    and the judged chain accepts some of its calls at tolerance 1e-4."""
+    import torch
+    cfg = dict(SG.CONFIG)
+    params = W.surrogate_trajectories(28, seed=77)
+    ctx = SG.make_context(cfg)
+    sur = B.Surrogate(4 * ctx.n_spec, width=cfg["width"], bmax=32, seed=5)
+    X, T, _ = SG.build_dataset(ctx, sur, cfg, params[:24], torch, n_fit=24)
+    hist, _ = SG.train(sur, X, T, X.shape[0], torch, epochs=80, batch=32, lr=1e-3)
+    trajs = [SG.trajectory(ctx, cfg, p, torch) for p in params[24:]]
+    ev = SG.evaluate(ctx, sur, cfg, trajs, torch, tol=1e-4)
+    print("surrogate gain:", ev)
+    assert ev["window_residual_nn_median"] < 0.3 * ev["window_residual_prop_median"]
+    assert ev["chain_error_nn"] < 0.3 * ev["chain_error_prop"]
+    assert ev["accepted_fraction"] > 0.0
+    sur.close()
+    ctx.close()
+
+
+def test_solver_states_have_the_m0_structure():
+    """The premise of the prediction's m = 0 projection: solver states are
+    Hermitian in k at m = 0 and satisfy the decay condition at every k."""
+    import torch
+    g, ctx = _vortex_ctx(prec=B.FP32)
+    cfg = dict(SG.CONFIG, windows=2, nsub=4)
+    tr = SG.trajectory(ctx, cfg, dict(b=1.0, a=0.2, amp=1e-3, incl_deg=48.0), torch)
+    for s in tr:
+        # round-off level: the decay sum over n and the transforms in FP32
+        assert float((_constrain_m0(s, ctx) - s).norm()) <= 1e-10 * float(s.norm())

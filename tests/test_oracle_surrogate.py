@@ -87,6 +87,20 @@ def test_backward_matches_finite_differences():
         assert abs(fd - g[j]) <= 1e-7 * max(1.0, abs(g[j])), (j, fd, g[j])
 
 
+def test_weighted_backward_matches_finite_differences():
+    theta, X, T, D, w = _tiny(seed=11)
+    c = np.random.Generator(np.random.PCG64(12)).uniform(0.0, 3.0, D)
+    loss, g = S.loss_and_grad(theta, X, T, D, w, bf16=False, weights=c)
+    Y, _ = S.forward(theta, X, D, w, bf16=False)
+    assert abs(loss - np.mean(c * (Y - T) ** 2)) < 1e-14 * max(1.0, loss)
+    h = 1e-6
+    for j in range(0, theta.size, 3):
+        tp = theta.copy(); tp[j] += h
+        tm = theta.copy(); tm[j] -= h
+        fd = (S.loss_and_grad(tp, X, T, D, w, False, c)[0] - S.loss_and_grad(tm, X, T, D, w, False, c)[0]) / (2 * h)
+        assert abs(fd - g[j]) <= 1e-7 * max(1.0, abs(g[j])), (j, fd, g[j])
+
+
 def test_loss_is_mean_square():
     theta, X, T, D, w = _tiny(seed=4)
     Y, _ = S.forward(theta, X, D, w, bf16=False)
