@@ -340,8 +340,9 @@ int mlx_sur_train_step(mlx_sur* sur, const void* X, const float* T, const int* i
  * in mlx_advance) and the relative residual ||pred - solver|| / ||solver|| (real
  * Euclidean norm over all coefficients) decides: <= tol keeps the prediction
  * (*accepted = 1), otherwise the solver's state is kept (*accepted = 0).
- * Without the judge the prediction is kept (*accepted = 1, *residual = -1).
- * accepted / residual may be NULL.  Synchronises `stream`. */
+ * Without the judge the prediction is kept (*accepted = 1, *residual = -1) and
+ * the call is asynchronous on `stream`; with the judge it synchronises `stream`.
+ * accepted / residual may be NULL. */
 int mlx_sur_advance(mlx_ctx* ctx, mlx_sur* sur, void* state, int nsub, double U0, int judge, double tol,
                     int* accepted, double* residual, mlx_stream stream);
 

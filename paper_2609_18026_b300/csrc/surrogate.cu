@@ -46,6 +46,18 @@ struct mlx_sur {
   float inv_wref = 1.f;          // 1 / mean_i(sigma_out_i^2): loss weights w_i = sigma_out_i^2 inv_wref
   // solver-side workspace (two-field states, D/2 complex each)
   double2 *prop = nullptr, *pred = nullptr, *tmp = nullptr, *Ascr = nullptr;
+  // dense propagator blocks: E^nsub per (m, |k|), N_m x N_m, stored transposed
+  // (Et[j][i] = E[i][j]) so that a column sweep reads consecutive rows
+  double* Et = nullptr;
+  long long* d_eoff = nullptr;   // per m: offset of block (m, |k| = 0); (m, kabs) at + kabs N_m^2
+  const mlx_ctx* e_ctx = nullptr;
+  double e_dt = 0, e_nu = 0, e_nuh = 0;
+  int e_p = 0, e_nsub = 0;       // e_nsub = 0: not built
+  // single-sample inference buffers
+  float* part = nullptr;         // layer-1 partial sums [l1_G][w]
+  int l1_G = 0;                  // layer-1 CTAs, each over l1_chunk coefficients
+  long long l1_chunk = 0;
+  float* h3 = nullptr;           // last hidden layer (BF16 values held as float) [w]
   long long t = 0;               // Adam step counter
 };
 
@@ -216,20 +228,6 @@ __global__ void k_gather(long long D, int B, const int* __restrict__ idx, const 
   if (T) tg[i] = T[src];
 }
 
-// x = bf16(s / sigma_in)
-__global__ void k_normalize(long long D, const double* __restrict__ s, const float* __restrict__ sc,
-                            __nv_bfloat16* __restrict__ x) {
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < D) x[i] = __float2bfloat16_rn((float)(s[i] / (double)sc[i]));
-}
-
-// out = prop + sigma_out * y
-__global__ void k_denorm_add(long long D, const double* __restrict__ prop, const float* __restrict__ y,
-                             const float* __restrict__ sc, double* __restrict__ out) {
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < D) out[i] = prop[i] + (double)y[i] * (double)sc[i];
-}
-
 // r[0] += sum (a - b)^2, r[1] += sum b^2
 __global__ void k_resid(long long n, const double* __restrict__ a, const double* __restrict__ b,
                         double* __restrict__ r) {
@@ -355,6 +353,149 @@ __global__ void k_make_pair(long long D, const double* __restrict__ s0, const do
   t[i] = sout[i] > 0.f ? (float)((s1[i] - prop[i]) / (double)sout[i]) : 0.f;
 }
 
+
+// ---- dense propagator blocks ----
+
+// two-field state: zero, except entry a (n - m = a) of every block (m, k) of field 0 with a < N_m set to 1
+__global__ void k_unit(double2* __restrict__ st, int M, int nc, int K, const long long* __restrict__ soff, int a) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= M * K) return;
+  const int m = t / K, k = t % K, N = nc - m;
+  if (a < N) st[soff[m] + (long long)k * N + a] = make_double2(1.0, 0.0);
+}
+
+// column a of E_{m,kabs} (the real image of the unit vector) into the transposed block
+__global__ void k_extract(const double2* __restrict__ out, double* __restrict__ Et, int M, int nc, int Kz,
+                          const long long* __restrict__ soff, const long long* __restrict__ eoff, int a) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int m = blockIdx.y, N = nc - m;
+  if (a >= N || t >= (long long)Kz * N) return;
+  const int kabs = (int)(t / N), i = (int)(t % N);
+  Et[eoff[m] + (long long)kabs * N * N + (long long)a * N + i] = out[soff[m] + (long long)kabs * N + i].x;
+}
+
+// y_{m,k} = E_{m,|k|} x_{m,k} for both fields of a two-field state; one CTA per (|k|, m)
+// handles k = |k| and k = K - |k| of both fields (the blocks that share E)
+__global__ void k_apply_E(const double2* __restrict__ x, double2* __restrict__ y, long long n_spec, int nc, int K,
+                          const long long* __restrict__ soff, const long long* __restrict__ eoff,
+                          const double* __restrict__ Et) {
+  extern __shared__ double2 xcol[];   // [nv][N]
+  const int kabs = blockIdx.x, m = blockIdx.y, N = nc - m;
+  const int nv = kabs ? 4 : 2;
+  const long long b0 = soff[m] + (long long)kabs * N, b1 = soff[m] + (long long)(K - kabs) * N;
+  // vector v: field v & 1, wavenumber index kabs (v < 2) or K - kabs (v >= 2)
+  auto base = [&](int v) { return (long long)(v & 1) * n_spec + ((v >> 1) ? b1 : b0); };
+  for (int t = threadIdx.x; t < nv * N; t += blockDim.x) xcol[t] = x[base(t / N) + t % N];
+  __syncthreads();
+  const double* E = Et + eoff[m] + (long long)kabs * N * N;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    double2 acc[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) acc[v] = make_double2(0.0, 0.0);
+    for (int j = 0; j < N; ++j) {
+      const double e = __ldg(E + (long long)j * N + i);
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        if (v < nv) {
+          const double2 q = xcol[v * N + j];
+          acc[v].x = fma(e, q.x, acc[v].x);
+          acc[v].y = fma(e, q.y, acc[v].y);
+        }
+      }
+    }
+#pragma unroll
+    for (int v = 0; v < 4; ++v)
+      if (v < nv) y[base(v) + i] = acc[v];
+  }
+}
+
+// ---- single-sample inference (the surrogate call) ----
+constexpr int L1_CTAS = 296;       // at least two CTAs per SM of the 148
+constexpr int L1_MAX_CHUNK = 8192; // coefficients staged per CTA (32 KB of shared memory)
+
+// part[b][o] = sum over the CTA's chunk of W1[o][d] x_d with x_d = bf16(s_d / sigma_in_d)
+__global__ void __launch_bounds__(256) k_l1_gemv(long long D, int w, const double* __restrict__ s,
+                                                 const float* __restrict__ sin_,
+                                                 const __nv_bfloat16* __restrict__ W1, float* __restrict__ part,
+                                                 long long chunk) {
+  extern __shared__ float xstage[];
+  const long long d0 = (long long)blockIdx.x * chunk;
+  const long long d1 = d0 + chunk < D ? d0 + chunk : D;
+  const int len = d1 > d0 ? (int)(d1 - d0) : 0;
+  for (int t = threadIdx.x; t < len; t += blockDim.x)
+    xstage[t] = __bfloat162float(__float2bfloat16_rn((float)(s[d0 + t] / (double)sin_[d0 + t])));
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int o = warp; o < w; o += nw) {
+    const __nv_bfloat16* row = W1 + (long long)o * D + d0;
+    float acc = 0.f;
+    for (int t = lane; t < len; t += 32) acc = fmaf(__bfloat162float(row[t]), xstage[t], acc);
+#pragma unroll
+    for (int q = 16; q > 0; q >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, q);
+    if (lane == 0) part[(long long)blockIdx.x * w + o] = acc;
+  }
+}
+
+// layers 1 (finish), 2 and 3 in one CTA of >= w threads: h3 = BF16 activations as float
+__global__ void k_mlp_mid(int G, int w, const float* __restrict__ part, const float* __restrict__ b1,
+                          const __nv_bfloat16* __restrict__ W2, const float* __restrict__ b2,
+                          const __nv_bfloat16* __restrict__ W3, const float* __restrict__ b3,
+                          float* __restrict__ h3) {
+  extern __shared__ float hmid[];   // [2][w]
+  float* ha = hmid;
+  float* hb = hmid + w;
+  const int o = threadIdx.x;
+  if (o < w) {
+    float z = 0.f;
+    for (int g = 0; g < G; ++g) z += part[(long long)g * w + o];
+    z += b1[o];
+    ha[o] = __bfloat162float(__float2bfloat16_rn(gelu(z)));
+  }
+  __syncthreads();
+  if (o < w) {
+    float z = 0.f;
+    for (int i = 0; i < w; ++i) z = fmaf(__bfloat162float(W2[(long long)o * w + i]), ha[i], z);
+    z += b2[o];
+    hb[o] = __bfloat162float(__float2bfloat16_rn(gelu(z)));
+  }
+  __syncthreads();
+  if (o < w) {
+    float z = 0.f;
+    for (int i = 0; i < w; ++i) z = fmaf(__bfloat162float(W3[(long long)o * w + i]), hb[i], z);
+    z += b3[o];
+    h3[o] = __bfloat162float(__float2bfloat16_rn(gelu(z)));
+  }
+}
+
+// pred_d = prop_d + sigma_out_d (sum_o W4[d][o] h3_o + b4_d)
+__global__ void k_l4_out(long long D, int w, const __nv_bfloat16* __restrict__ W4, const float* __restrict__ b4,
+                         const float* __restrict__ h3, const float* __restrict__ sout,
+                         const double* __restrict__ prop, double* __restrict__ pred, int vec) {
+  extern __shared__ float hlast[];
+  for (int t = threadIdx.x; t < w; t += blockDim.x) hlast[t] = h3[t];
+  __syncthreads();
+  const long long d = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (d >= D) return;
+  float acc = 0.f;
+  if (vec) {
+    const uint4* row = reinterpret_cast<const uint4*>(W4 + d * w);
+    for (int q = 0; q < w / 8; ++q) {
+      const uint4 u = __ldg(row + q);
+      const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&u);
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const float2 f = __bfloat1622float2(h[r]);
+        acc = fmaf(f.x, hlast[8 * q + 2 * r], acc);
+        acc = fmaf(f.y, hlast[8 * q + 2 * r + 1], acc);
+      }
+    }
+  } else {
+    for (int o = 0; o < w; ++o) acc = fmaf(__bfloat162float(W4[d * w + o]), hlast[o], acc);
+  }
+  const float yv = acc + b4[d];
+  pred[d] = prop[d] + (double)yv * (double)sout[d];
+}
+
 inline unsigned nb(long long n, int t = 256) { return (unsigned)((n + t - 1) / t); }
 
 template <typename TA, typename TB>
@@ -378,7 +519,7 @@ void sur_free(mlx_sur* s) {
   void* ps[] = {s->master, s->grad, s->m1,   s->m2,   s->wbf,   s->z1,       s->z2,        s->z3,
                 s->y,      s->x,    s->a1,   s->a2,   s->a3,    s->d1,       s->d2,        s->d3,
                 s->dy,     s->tg,   s->loss, s->red,  s->acc_s, s->in_scale, s->out_scale, s->prop,
-                s->pred,   s->tmp,  s->Ascr, s->acc_r};
+                s->pred,   s->tmp,  s->Ascr, s->acc_r, s->Et, s->d_eoff, s->part, s->h3};
   for (void* p : ps)
     if (p) cudaFree(p);
   delete s;
@@ -441,11 +582,24 @@ int sur_bind(mlx_ctx* c, mlx_sur* s) {
   const size_t b = sizeof(double2) * 2 * (size_t)c->n_spec;
   for (double2** p : {&s->prop, &s->pred, &s->tmp, &s->Ascr})
     if (cudaMalloc(p, b) != cudaSuccess) { c->last_err = "surrogate workspace allocation"; return MLX_ENOMEM; }
+  long long G = ((long long)s->D + L1_MAX_CHUNK - 1) / L1_MAX_CHUNK;
+  if (G < L1_CTAS) G = L1_CTAS;
+  s->l1_chunk = ((long long)s->D + G - 1) / G;
+  s->l1_G = (int)(((long long)s->D + s->l1_chunk - 1) / s->l1_chunk);
+  if (cudaMalloc(&s->part, sizeof(float) * s->l1_G * s->w) != cudaSuccess ||
+      cudaMalloc(&s->h3, sizeof(float) * s->w) != cudaSuccess) {
+    c->last_err = "surrogate workspace allocation";
+    return MLX_ENOMEM;
+  }
+  // the column vectors of the E sweep live in shared memory (4 N_0 complex)
+  MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_apply_E, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)(sizeof(double2) * 4 * c->nc)));
   return MLX_OK;
 }
 
-// out = E^nsub s for the two-field state (ping-pong through tmp; s is not modified)
-int propagate(mlx_ctx* c, const double2* s, double2* out, double2* tmp, int nsub, cudaStream_t st) {
+// out = E^nsub s through nsub implicit steps with A = 0 (ping-pong through tmp;
+// s is not modified)
+int propagate_steps(mlx_ctx* c, const double2* s, double2* out, double2* tmp, int nsub, cudaStream_t st) {
   const double2* src = s;
   for (int k = 0; k < nsub; ++k) {
     double2* dst = ((nsub - 1 - k) % 2 == 0) ? out : tmp;
@@ -456,6 +610,71 @@ int propagate(mlx_ctx* c, const double2* s, double2* out, double2* tmp, int nsub
     }
     src = dst;
   }
+  return MLX_OK;
+}
+
+// Dense blocks E^nsub_{m,|k|}, built once per (context, dt, nu, nu_h, p, nsub) by
+// sending the unit vectors e_a (a = 0..Nc-1, in every block at once) through
+// propagate_steps: column a of every block in one sweep.
+int build_E(mlx_ctx* c, mlx_sur* s, int nsub, cudaStream_t st) {
+  if (s->e_nsub == nsub && s->e_ctx == c && s->e_dt == c->dt && s->e_nu == c->nu && s->e_nuh == c->nu_h &&
+      s->e_p == c->p)
+    return MLX_OK;
+  s->e_nsub = 0;
+  if (!s->Et) {
+    std::vector<long long> eoff(c->M + 1, 0);
+    for (int m = 0; m < c->M; ++m) eoff[m + 1] = eoff[m] + (long long)c->Kz * (c->nc - m) * (c->nc - m);
+    if (cudaMalloc(&s->Et, sizeof(double) * eoff[c->M]) != cudaSuccess ||
+        cudaMalloc(&s->d_eoff, sizeof(long long) * (c->M + 1)) != cudaSuccess) {
+      c->last_err = "surrogate propagator allocation";
+      return MLX_ENOMEM;
+    }
+    MLX_CUDA_TRY(c, cudaMemcpyAsync(s->d_eoff, eoff.data(), sizeof(long long) * (c->M + 1),
+                                    cudaMemcpyHostToDevice, st));
+  }
+  const long long n2 = 2 * c->n_spec;
+  for (int a = 0; a < c->nc; ++a) {
+    MLX_CUDA_TRY(c, cudaMemsetAsync(s->prop, 0, sizeof(double2) * n2, st));
+    k_unit<<<nb((long long)c->M * c->K), 256, 0, st>>>(s->prop, c->M, c->nc, c->K, c->d_soff, a);
+    MLX_LAUNCH_CHECK(c);
+    int rc = propagate_steps(c, s->prop, s->pred, s->tmp, nsub, st);
+    if (rc) return rc;
+    dim3 g(nb((long long)c->Kz * c->nc), c->M);
+    k_extract<<<g, 256, 0, st>>>(s->pred, s->Et, c->M, c->nc, c->Kz, c->d_soff, s->d_eoff, a);
+    MLX_LAUNCH_CHECK(c);
+  }
+  s->e_ctx = c; s->e_dt = c->dt; s->e_nu = c->nu; s->e_nuh = c->nu_h; s->e_p = c->p; s->e_nsub = nsub;
+  return MLX_OK;
+}
+
+// out = E^nsub s by the dense blocks (out != s)
+int propagate(mlx_ctx* c, mlx_sur* s, const double2* x, double2* out, int nsub, cudaStream_t st) {
+  int rc = build_E(c, s, nsub, st);
+  if (rc) return rc;
+  const int nt = c->nc >= 128 ? 128 : ((c->nc + 31) / 32) * 32;
+  dim3 g(c->Kz, c->M);
+  k_apply_E<<<g, nt, sizeof(double2) * 4 * c->nc, st>>>(x, out, c->n_spec, c->nc, c->K, c->d_soff, s->d_eoff,
+                                                          s->Et);
+  MLX_LAUNCH_CHECK(c);
+  return MLX_OK;
+}
+
+// pred = E^nsub S + sigma_out f(S / sigma_in), m = 0 block projected
+int predict_one(mlx_ctx* c, mlx_sur* s, const double2* S, int nsub, cudaStream_t st) {
+  int rc = propagate(c, s, S, s->prop, nsub, st);
+  if (rc) return rc;
+  const int G = s->l1_G;
+  k_l1_gemv<<<G, 256, sizeof(float) * s->l1_chunk, st>>>(s->D, s->w, (const double*)S, s->in_scale,
+                                                         s->wbf + s->oW1, s->part, s->l1_chunk);
+  const int tw = ((s->w + 31) / 32) * 32;
+  k_mlp_mid<<<1, tw, sizeof(float) * 2 * s->w, st>>>(G, s->w, s->part, s->master + s->ob1, s->wbf + s->oW2,
+                                                      s->master + s->ob2, s->wbf + s->oW3, s->master + s->ob3,
+                                                      s->h3);
+  const int vec = ((s->w % 8) == 0 && ((s->oW4 * 2) % 16) == 0) ? 1 : 0;
+  k_l4_out<<<nb(s->D), 256, sizeof(float) * s->w, st>>>(s->D, s->w, s->wbf + s->oW4, s->master + s->ob4, s->h3,
+                                                         s->out_scale, (const double*)s->prop, (double*)s->pred, vec);
+  k_constrain<<<2, 256, 0, st>>>(s->pred, c->n_spec, c->K, c->Kz, c->nc);
+  MLX_LAUNCH_CHECK(c);
   return MLX_OK;
 }
 
@@ -588,7 +807,7 @@ int mlx_sur_propagate(mlx_ctx* c, mlx_sur* s, const void* state, void* out, int 
   if (!c || !s || !state || !out || nsub < 1 || state == out) return MLX_EINVAL;
   int rc = sur_bind(c, s);
   if (rc) return rc;
-  return propagate(c, (const double2*)state, (double2*)out, s->tmp, nsub, (cudaStream_t)stream);
+  return propagate(c, s, (const double2*)state, (double2*)out, nsub, (cudaStream_t)stream);
 }
 
 int mlx_sur_observe(mlx_ctx* c, mlx_sur* s, const void* s0, const void* s1, int nsub, mlx_stream stream) {
@@ -596,7 +815,7 @@ int mlx_sur_observe(mlx_ctx* c, mlx_sur* s, const void* s0, const void* s1, int 
   int rc = sur_bind(c, s);
   if (rc) return rc;
   cudaStream_t st = (cudaStream_t)stream;
-  if ((rc = propagate(c, (const double2*)s0, s->prop, s->tmp, nsub, st))) return rc;
+  if ((rc = propagate(c, s, (const double2*)s0, s->prop, nsub, st))) return rc;
   k_observe<<<nb(s->D), 256, 0, st>>>(s->D, (const double*)s0, (const double*)s1, (const double*)s->prop, s->acc_s,
                                       s->acc_r, s->red);
   MLX_LAUNCH_CHECK(c);
@@ -631,7 +850,7 @@ int mlx_sur_make_pair(mlx_ctx* c, mlx_sur* s, const void* s0, const void* s1, in
   int rc = sur_bind(c, s);
   if (rc) return rc;
   cudaStream_t st = (cudaStream_t)stream;
-  if ((rc = propagate(c, (const double2*)s0, s->prop, s->tmp, nsub, st))) return rc;
+  if ((rc = propagate(c, s, (const double2*)s0, s->prop, nsub, st))) return rc;
   k_make_pair<<<nb(s->D), 256, 0, st>>>(s->D, (const double*)s0, (const double*)s1, (const double*)s->prop,
                                         s->in_scale, s->out_scale, (__nv_bfloat16*)x, t);
   MLX_LAUNCH_CHECK(c);
@@ -675,12 +894,7 @@ int mlx_sur_advance(mlx_ctx* c, mlx_sur* s, void* state, int nsub, double U0, in
   cudaStream_t st = (cudaStream_t)stream;
   double2* S = (double2*)state;
   const long long n = 2 * c->n_spec;   // complex values of the state
-  if ((rc = propagate(c, S, s->prop, s->tmp, nsub, st))) return rc;
-  k_normalize<<<nb(s->D), 256, 0, st>>>(s->D, (const double*)S, s->in_scale, s->x);
-  if ((rc = sur_forward(s, 1, st))) return rc;
-  k_denorm_add<<<nb(s->D), 256, 0, st>>>(s->D, (const double*)s->prop, s->y, s->out_scale, (double*)s->pred);
-  k_constrain<<<2, 256, 0, st>>>(s->pred, c->n_spec, c->K, c->Kz, c->nc);
-  MLX_LAUNCH_CHECK(c);
+  if ((rc = predict_one(c, s, S, nsub, st))) return rc;
   int acc = 1;
   double res = -1.0;
   if (judge) {
@@ -696,7 +910,6 @@ int mlx_sur_advance(mlx_ctx* c, mlx_sur* s, void* state, int nsub, double U0, in
     acc = (res <= tol) ? 1 : 0;
   }
   if (acc) MLX_CUDA_TRY(c, cudaMemcpyAsync(S, s->pred, sizeof(double2) * n, cudaMemcpyDeviceToDevice, st));
-  MLX_CUDA_TRY(c, cudaStreamSynchronize(st));
   if (accepted) *accepted = acc;
   if (residual) *residual = res;
   return MLX_OK;
