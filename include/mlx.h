@@ -215,6 +215,18 @@ int mlx_advance(mlx_ctx* ctx, int kind, const double* coeffs, int ncoeffs,
  *                memory and keeps only the solution columns in shared memory
  *                (32 chains per warp); default 1 for hyperviscous bands
  *                (half width >= 4, set by mlx_implicit_setup), else 0.
+ *   "solve_ir":  1 = the implicit step (I - c L) x = b by mixed-precision
+ *                iterative refinement: the band recurrence runs in FP32 with the
+ *                FP32-rounded factors, and FP64 residuals b - (I - c L) x from the
+ *                stored FP64 band correct x until the correction is below 2^-50 |x|
+ *                (FP64 level) or stops contracting (the FP64 residual's rounding
+ *                floor, about kappa u |x|), at most "solve_ir_max" times (1..30,
+ *                default 8).  Default 0 (measured slower than the FP64 recurrence
+ *                at 64^3 to 128^2 x 64).  Grids whose staging exceeds 200 KB of shared memory
+ *                (Nc > 164 at half width 2) use the FP64 recurrence.  A chain
+ *                whose last correction is still above 2^-20 |x| makes
+ *                mlx_device_status return MLX_ENUMERIC.  The projection and
+ *                Laplacian solves always use the FP64 recurrence.
  *   "tc_bn":     column-tile width of the MLX_BF16X3 contraction (16..256; the
  *                width actually used is rounded to a multiple of 16 that
  *                splits the 2K columns evenly);
@@ -251,7 +263,8 @@ int mlx_batch_advance(mlx_batch* batch, const int* kinds, const double* coeffs, 
  * CTA.  Results are cached in the text file cache_path (may be NULL), one line
  * "sizes precision kind band|bn cpw wpb"; a cached entry is applied without
  * timing.  chosen (may be NULL) receives {bn, cpw, wpb, from_cache}; cpw = wpb = 0
- * denotes the direct-read solve variant.  The
+ * denotes the direct-read solve variant, cpw = 1 (wpb = 0) the mixed-precision
+ * refinement variant ("solve_ir").  The
  * context's temporaries are overwritten; call it before advancing.
  * Synchronises `stream`. */
 int mlx_autotune(mlx_ctx* ctx, int kind, const double* coeffs, int ncoeffs, const char* cache_path,
@@ -361,7 +374,8 @@ const char* mlx_kernel_name(int kernel);
 
 /* Device status: synchronises the device, returns MLX_ETIMEOUT (and clears the
  * word) if a kernel of this context gave up a bounded wait since the last call,
- * else MLX_OK.  Kernels that give up skip their remaining work and release their
+ * MLX_ENUMERIC if a refined solve did not reach FP64 level ("solve_ir"), else
+ * MLX_OK.  Kernels that give up skip their remaining work and release their
  * resources; their outputs are then undefined. */
 int mlx_device_status(mlx_ctx* ctx);
 

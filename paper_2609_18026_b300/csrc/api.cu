@@ -23,6 +23,8 @@ void free_ctx(mlx_ctx* c) {
                   c->d_spec1, c->d_spec2, c->d_spec3, c->d_band_off, c->d_Bplus,
                   c->lu_half.U, c->lu_half.L, c->lu_half.piv, c->lu_half.invd,
                   c->lu_full.U, c->lu_full.L, c->lu_full.piv, c->lu_full.invd,
+                  c->lu_half.U32, c->lu_half.L32, c->lu_half.invd32,
+                  c->lu_full.U32, c->lu_full.L32, c->lu_full.invd32,
                   c->d_Wb, c->d_Pb, c->d_arowW, c->d_arowP, c->d_tc_fwd, c->d_tc_bwd, c->d_err,
                   c->lu_lap.U, c->lu_lap.L, c->lu_lap.piv, c->lu_lap.invd,
                   c->lu_helm.U, c->lu_helm.L, c->lu_helm.piv, c->lu_helm.invd, c->d_lap_off,
@@ -276,6 +278,9 @@ int mlx_implicit_setup(mlx_ctx* c, double nu, double nu_h, int p, double dt, mlx
   c->nu = nu; c->nu_h = nu_h; c->p = p; c->dt = dt;
   c->kl = (nu_h > 0.0) ? p : 2;
   c->solve_direct = (c->kl >= 4) ? 1 : 0;   // wide hyperviscous bands: direct-read solve
+  // the refinement variant is opt-in: at the sizes measured it is slower than the
+  // staged FP64 recurrence (one warp of chains per SM leaves its latencies exposed)
+  c->solve_ir = 0;
   c->implicit_ready = false;
   int rc = mlx_band_setup(c, (cudaStream_t)stream);
   if (rc) return rc;
@@ -377,6 +382,20 @@ int mlx_set_tuning(mlx_ctx* c, const char* key, int value) {
     c->graphs.clear();
     return MLX_OK;
   }
+  if (strcmp(key, "solve_ir") == 0) {
+    if (value != 0 && value != 1) return MLX_EINVAL;
+    c->solve_ir = value;
+    for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
+    c->graphs.clear();
+    return MLX_OK;
+  }
+  if (strcmp(key, "solve_ir_max") == 0) {
+    if (value < 1 || value > 30) return MLX_EINVAL;
+    c->solve_ir_max = value;
+    for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
+    c->graphs.clear();
+    return MLX_OK;
+  }
   if (strcmp(key, "solve_direct") == 0) {
     if (value != 0 && value != 1) return MLX_EINVAL;
     c->solve_direct = value;
@@ -422,7 +441,7 @@ int mlx_device_status(mlx_ctx* c) {
   MLX_CUDA_TRY(c, cudaMemcpy(&v, c->d_err, sizeof(int), cudaMemcpyDeviceToHost));
   if (v) {
     MLX_CUDA_TRY(c, cudaMemset(c->d_err, 0, sizeof(int)));
-    return MLX_ETIMEOUT;
+    return (v & 7) ? MLX_ETIMEOUT : MLX_ENUMERIC;
   }
   return MLX_OK;
 }

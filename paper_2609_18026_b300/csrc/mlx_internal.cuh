@@ -54,6 +54,11 @@ struct BandLU {
   double* L = nullptr;     // [rows][kl]
   int* piv = nullptr;      // [rows]
   double* invd = nullptr;  // [rows]
+  // FP32 roundings of U, L, invd (implicit-step families only): the inner solves
+  // of the mixed-precision refinement
+  float* U32 = nullptr;
+  float* L32 = nullptr;
+  float* invd32 = nullptr;
 };
 
 struct mlx_ctx {
@@ -100,7 +105,8 @@ struct mlx_ctx {
   int ntc_fwd = 0, ntc_bwd = 0, tc_bn = 0, tc_tmem_cols = 0;
   int tc_products = 6;                 // BF16 split products per term: 6 or 8
   int tc_stages = 2;                   // shared-memory stages of the K loop
-  int* d_err = nullptr;                // device status word (bounded waits that expired)
+  int* d_err = nullptr;                // device status word: bits 1, 2, 4 bounded waits that
+                                       // expired; bit 8 a refinement that did not converge
 
   // workspace (element type follows precision)
   void* d_mixed = nullptr;             // planar complex [2][K][M][Nr]
@@ -137,6 +143,8 @@ struct mlx_ctx {
   int solve_cpw = 8;                   // real chains per warp in the banded solve (4..32)
   int solve_wpb = 4;                   // warps per CTA in the banded solve (1..4)
   int solve_direct = 0;                // 1: direct-read solve variant (wide bands)
+  int solve_ir = 0;                    // 1: FP32 solves refined to FP64 by FP64 residuals
+  int solve_ir_max = 8;                // refinement steps at most (early exit at FP64 level)
 
   // graphs cached per (state, prev_A, kind, gamma)
   struct GraphKey {

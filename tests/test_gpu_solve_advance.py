@@ -174,18 +174,49 @@ def test_fkpp_fp32_per_step_error_along_trajectory():
 
 
 @pytest.mark.parametrize("nu_h,p", [(0.0, 8), (5e-7, 8)])
-def test_solve_variants_agree(nu_h, p):
-    # the staged (factor rows in shared memory) and direct-read solve variants
-    # compute the same substitution in a different summation order
+@pytest.mark.parametrize("step", [B.STEP_ABCN, B.STEP_FEBE_FULL])
+def test_solve_variants_agree(nu_h, p, step):
+    # the staged (factor rows in shared memory), direct-read and mixed-precision
+    # refinement variants solve the same systems; each is within kappa u of the
+    # exact solution, and the refined one also matches the oracle
     g, ctx = pair(40, 16, 8, 1.5, lz=3.0, policy="twothirds")
     ctx.implicit_setup(0.3, 2e-2, nu_h=nu_h, p=p)
     s, A, Ap = (to_gpu_spec(rand_spec(g, k)) for k in (1, 2, 3))
     outs = []
-    for direct in (0, 1):
+    for ir, direct in ((0, 0), (0, 1), (1, 0)):
+        ctx.set_tuning("solve_ir", ir)
         ctx.set_tuning("solve_direct", direct)
-        outs.append(ctx.implicit_solve(B.STEP_ABCN, s, A, Ap, ctx.new_spec()).cpu().numpy())
+        outs.append(ctx.implicit_solve(step, s, A, Ap, ctx.new_spec()).cpu().numpy())
+    ctx.device_status()   # raises MLX_ENUMERIC if a refinement did not converge
     # bar: 1e-12, or 2 kappa u for the ill-conditioned hyperviscous systems
     st = O.Stepper(g, 0.3, 2e-2, nu_h=nu_h, p=p)
-    kappa = max(np.linalg.cond(np.eye(L.shape[0]) - 1e-2 * L) for L in st.L.values())
+    c = 1e-2 if step == B.STEP_ABCN else 2e-2
+    kappa = max(np.linalg.cond(np.eye(L.shape[0]) - c * L) for L in st.L.values())
     tol = max(1e-12, 2.0 * kappa * 2.0 ** -53)
-    assert np.max(np.abs(outs[0] - outs[1])) <= tol * np.max(np.abs(outs[1]))
+    for o in outs[:2]:
+        assert np.max(np.abs(o - outs[2])) <= tol * np.max(np.abs(outs[2]))
+    S, Af, Apf = (O.from_flat(g, rand_spec(g, k)) for k in (1, 2, 3))
+    if step == B.STEP_ABCN:
+        ref = st.abcn(S, Af, Apf)
+    else:
+        ref = st.febe(S, False, Af)
+    assert O.spec_rel_err(g, O.from_flat(g, outs[2]), ref) <= tol
+
+
+def test_refined_solve_reaches_fp64_level():
+    # FP32 recurrences refined by FP64 residuals give the FP64 solve's result
+    g, ctx = pair(48, 16, 8, 1.0, lz=3.0, policy="twothirds")
+    ctx.implicit_setup(1.0, 1e-2)
+    s, A, Ap = (to_gpu_spec(rand_spec(g, k)) for k in (4, 5, 6))
+    plain = ctx.implicit_solve(B.STEP_ABCN, s, A, Ap, ctx.new_spec()).cpu().numpy()
+    ctx.set_tuning("solve_ir", 1)
+    got = ctx.implicit_solve(B.STEP_ABCN, s, A, Ap, ctx.new_spec()).cpu().numpy()
+    ctx.device_status()
+    assert not np.array_equal(got, plain)      # a different code path ...
+    assert np.max(np.abs(got - plain)) <= 1e-13 * np.max(np.abs(plain))   # ... same FP64 result
+    # one correction stops short of FP64 level but below the 2^-20 |x| failure bar,
+    # so the status word stays clear
+    ctx.set_tuning("solve_ir_max", 1)
+    one = ctx.implicit_solve(B.STEP_ABCN, s, A, Ap, ctx.new_spec()).cpu().numpy()
+    ctx.device_status()
+    assert np.max(np.abs(one - plain)) <= 1e-6 * np.max(np.abs(plain))
