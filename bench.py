@@ -623,12 +623,27 @@ def main():
     ap.add_argument("--impl", default="mlx", choices=["mlx", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-other-workloads", action="store_true",
-                    help="skip the 256^3 vortex and 64-instance batch measurements")
+                    help="skip the 256^3 vortex, 64-instance batch and 64^3 surrogate measurements")
     ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "fp32", "fp64"],
                     help="transform arithmetic of the timed form (the FP64 form is always timed beside it)")
+    ap.add_argument("--profile-workload", default=None, choices=["vortex", "batch", "surrogate"],
+                    help="run only that secondary workload and print its measurement (for profiler captures; "
+                         "not the benchmark line)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.profile_workload:
+        import torch
+        from paper_2609_18026_b300 import binding as B
+        from paper_2609_18026_b300 import workloads as W
+        torch.cuda.init()
+        dev = torch.device("cuda:0")
+        stream = torch.cuda.current_stream()
+        fn = {"vortex": lambda: measure_vortex(B, W, torch, dev, stream),
+              "batch": lambda: measure_batch(B, W, torch, dev, stream),
+              "surrogate": lambda: measure_surrogate(torch)}[args.profile_workload]
+        print(json.dumps(fn()), flush=True)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if args.impl == "reference":

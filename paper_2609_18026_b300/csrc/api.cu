@@ -28,7 +28,7 @@ void free_ctx(mlx_ctx* c) {
                   c->d_Wb, c->d_Pb, c->d_arowW, c->d_arowP, c->d_tc_fwd, c->d_tc_bwd, c->d_err,
                   c->lu_lap.U, c->lu_lap.L, c->lu_lap.piv, c->lu_lap.invd,
                   c->lu_helm.U, c->lu_helm.L, c->lu_helm.piv, c->lu_helm.invd, c->d_lap_off,
-                  c->d_rdr, c->d_vspec, c->d_vphys,
+                  c->d_rdr, c->d_jac, c->d_vspec, c->d_vphys,
                   c->lu_Q.U, c->lu_Q.L, c->lu_Q.piv, c->lu_Q.invd, c->lu_H.U, c->lu_H.L, c->lu_H.piv,
                   c->lu_H.invd, c->lu_G.U, c->lu_G.L, c->lu_G.piv, c->lu_G.invd};
   for (void* p : ptrs)

@@ -27,8 +27,36 @@ __device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
   const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
 }
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+
+// Copy nrows rows of row_bytes bytes (a multiple of 4) from global memory (row stride
+// src_stride bytes) to shared memory (row stride dst_stride bytes) with cp.async,
+// in 16-byte pieces when every address, stride and length allows, else 8 or 4.
+__device__ __forceinline__ void stage_rows(void* dst, int dst_stride, const void* src, long long src_stride,
+                                           int nrows, int row_bytes, int lane) {
+  const unsigned long long a = (unsigned long long)(uintptr_t)src | (unsigned long long)src_stride |
+                               (unsigned long long)row_bytes | (unsigned long long)dst_stride |
+                               (unsigned long long)__cvta_generic_to_shared(dst);
+  const int ch = (a & 15) == 0 ? 16 : ((a & 7) == 0 ? 8 : 4);
+  const int per_row = row_bytes / ch;
+  unsigned char* d0 = reinterpret_cast<unsigned char*>(dst);
+  const unsigned char* s0 = reinterpret_cast<const unsigned char*>(src);
+  for (int e = lane; e < nrows * per_row; e += 32) {
+    const int i = e / per_row, j = e - i * per_row;
+    unsigned char* d = d0 + (size_t)i * dst_stride + (size_t)j * ch;
+    const unsigned char* g = s0 + (long long)i * src_stride + (long long)j * ch;
+    if (ch == 16) cp_async16(d, g);
+    else if (ch == 8) cp_async8(d, g);
+    else cp_async4(d, g);
+  }
+}
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait_group() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
 // Factor rows of one m are interleaved by |k|: row (m, i, kabs) has index
 // band_off[m] + i * Kz + kabs, so the threads of a warp (consecutive k) read
@@ -296,7 +324,7 @@ struct SolveSmem {
   __host__ __device__ static size_t per_warp(int nc, int CPW) {
     const int G = CPW / 4;
     const size_t b = (size_t)nc * G * (W + KL + 1) * sizeof(double) +
-                     (size_t)nc * CPW * sizeof(double) + (size_t)nc * G * sizeof(int);
+                     (size_t)2 * nc * CPW * sizeof(double) + (size_t)nc * G * sizeof(int);
     return (b + 15) / 16 * 16;   // keeps every warp's slab 16-byte aligned
   }
 };
@@ -327,53 +355,57 @@ __global__ void k_band_solve(int M, int nc, int Kz, int K, int CPW, int groups_p
   double* Ls = Us + (size_t)N * G * W;                       // [N][G][KL]
   double* Ds = Ls + (size_t)N * G * KL;                      // [N][G]
   double* Y = Ds + (size_t)N * G;                            // [N][CPW]
-  int* Pi = reinterpret_cast<int*>(Y + (size_t)N * CPW);     // [N][G] pivot rows
+  double* S = Y + (size_t)N * CPW;                           // [N][CPW] s, for the AB-CN "- s"
+  int* Pi = reinterpret_cast<int*>(S + (size_t)N * CPW);     // [N][G] pivot rows
   const long long fb = band_off[m];
   const long long sm = soff[m];
-  // factor row of (i, |k| = k0 + kk)
-  auto frow = [&](int i, int kk) -> long long {
-    return fb + (long long)i * kz_fac + (kz_fac == 1 ? 0 : k0 + kk);
-  };
-
-  // stage factors with asynchronous copies (every lane keeps many in flight)
-  for (int e = lane; e < N * gcnt * W; e += 32) {
-    const int i = e / (gcnt * W), rem = e - i * gcnt * W;
-    const int kk = rem / W, q = rem - kk * W;
-    cp_async8(Us + ((size_t)i * G + kk) * W + q, U + frow(i, kk) * W + q);
-  }
-  for (int e = lane; e < N * gcnt * KL; e += 32) {
-    const int i = e / (gcnt * KL), rem = e - i * gcnt * KL;
-    const int kk = rem / KL, q = rem - kk * KL;
-    cp_async8(Ls + ((size_t)i * G + kk) * KL + q, Lm + frow(i, kk) * KL + q);
-  }
-  for (int e = lane; e < N * gcnt; e += 32) {
-    const int i = e / gcnt, kk = e - i * gcnt;
-    cp_async8(Ds + (size_t)i * G + kk, invd + frow(i, kk));
-    cp_async4(Pi + (size_t)i * G + kk, piv + frow(i, kk));
+  // stage factors with asynchronous copies: the rows of the warp's gcnt values of
+  // |k| are contiguous for every i (interleaved storage), so each i is one span
+  if (kz_fac != 1) {
+    const long long r0 = fb + k0;
+    stage_rows(Us, G * W * 8, U + r0 * W, (long long)kz_fac * W * 8, N, gcnt * W * 8, lane);
+    stage_rows(Ls, G * KL * 8, Lm + r0 * KL, (long long)kz_fac * KL * 8, N, gcnt * KL * 8, lane);
+    stage_rows(Ds, G * 8, invd + r0, (long long)kz_fac * 8, N, gcnt * 8, lane);
+    stage_rows(Pi, G * 4, piv + r0, (long long)kz_fac * 4, N, gcnt * 4, lane);
+  } else {
+    // one factor set per m, shared by every |k|: replicated into each slot
+    for (int kq = 0; kq < gcnt; ++kq) {
+      stage_rows(Us + kq * W, G * W * 8, U + fb * W, (long long)W * 8, N, W * 8, lane);
+      stage_rows(Ls + kq * KL, G * KL * 8, Lm + fb * KL, (long long)KL * 8, N, KL * 8, lane);
+      stage_rows(Ds + kq, G * 8, invd + fb, 8, N, 8, lane);
+      stage_rows(Pi + kq, G * 4, piv + fb, 4, N, 4, lane);
+    }
   }
   cp_async_commit();
-  // stage right-hand sides; chain c = kk * 4 + sgn * 2 + part
+  // stage right-hand sides, one complex value per step (chain c = kk * 4 + sgn * 2 + part)
   const double h = (step == MLX_STEP_FEBE_FULL) ? dt : 0.5 * dt;
+  const double2* s2 = reinterpret_cast<const double2*>(s);
+  const double2* A2 = reinterpret_cast<const double2*>(A);
+  const double2* Ap2 = reinterpret_cast<const double2*>(Ap);
 #pragma unroll 4
-  for (int e = lane; e < N * 4 * gcnt; e += 32) {
-    const int c = e / N, i = e - c * N;
-    const int kk = c >> 2, sgn = (c >> 1) & 1, part = c & 1;
-    const int kabs = k0 + kk;
-    if (sgn && kabs == 0) continue;
-    const int kidx = sgn ? K - kabs : kabs;
-    const long long o = 2 * (sm + (long long)kidx * Nm + sh + i) + part;
-    double r;
+  for (int e = lane; e < N * 2 * gcnt; e += 32) {
+    const int cp = e / N, i = e - cp * N;
+    const int kq = cp >> 1, sg = cp & 1;
+    const int kabs = k0 + kq;
+    if (sg && kabs == 0) continue;
+    const int kidx = sg ? K - kabs : kabs;
+    const long long o = sm + (long long)kidx * Nm + sh + i;
+    const double2 sv = s2[o];
+    double2 r;
     if (step == MLX_STEP_PLAIN) {
-      r = s[o];
+      r = sv;
     } else if (step == MLX_STEP_ABCN) {
-      r = 2.0 * s[o];
-      if (A) r += 1.5 * dt * A[o];
-      if (Ap) r -= 0.5 * dt * Ap[o];
+      r = make_double2(2.0 * sv.x, 2.0 * sv.y);
+      if (A) { const double2 a = A2[o]; r.x += 1.5 * dt * a.x; r.y += 1.5 * dt * a.y; }
+      if (Ap) { const double2 a = Ap2[o]; r.x -= 0.5 * dt * a.x; r.y -= 0.5 * dt * a.y; }
+      S[(size_t)i * CPW + cp * 2] = sv.x;
+      S[(size_t)i * CPW + cp * 2 + 1] = sv.y;
     } else {
-      r = s[o];
-      if (A) r += h * A[o];
+      r = sv;
+      if (A) { const double2 a = A2[o]; r.x += h * a.x; r.y += h * a.y; }
     }
-    Y[(size_t)i * CPW + c] = r;
+    Y[(size_t)i * CPW + cp * 2] = r.x;
+    Y[(size_t)i * CPW + cp * 2 + 1] = r.y;
   }
   cp_async_wait_all();
   __syncwarp();
@@ -401,20 +433,30 @@ __global__ void k_band_solve(int M, int nc, int Kz, int K, int CPW, int groups_p
 #pragma unroll
       for (int q = 1; q <= KL; ++q) w[q] -= l[q - 1] * w[0];
     }
-    // back substitution; known terms first, x_{i+1} last
-    double x[2 * KL + 1];
+    // back substitution x_r = y_r / U_rr - sum_{q=1..2KL} (U_r,r+q / U_rr) x_{r+q},
+    // software-pipelined: acc[t] is the partial sum of row i - t, and at step i
+    // every pending row takes its term with x_{i+1} (row r the term q = i + 1 - r).
+    // The 2KL multiply-adds of a step are independent of one another; only x_i
+    // waits for x_{i+1}.  Each row still adds its terms from q = 2KL down to 1.
+    double acc[2 * KL];
 #pragma unroll
-    for (int q = 0; q <= 2 * KL; ++q) x[q] = 0.0;
+    for (int t = 0; t < 2 * KL; ++t) {
+      const int r = N - 1 - t;
+      acc[t] = (r >= 0) ? y[(size_t)r * CPW] * Ds[(size_t)r * G + kk] : 0.0;
+    }
+    double xn = 0.0;   // x_{i+1}
 #pragma unroll 2
     for (int i = N - 1; i >= 0; --i) {
-      const double* u = Us + ((size_t)i * G + kk) * W;
-      double acc = y[(size_t)i * CPW] * Ds[(size_t)i * G + kk];
+      const double xi = acc[0] - Us[((size_t)i * G + kk) * W + 1] * xn;
 #pragma unroll
-      for (int q = 2 * KL; q >= 1; --q) acc -= u[q] * x[q];
-      y[(size_t)i * CPW] = acc;
+      for (int t = 1; t < 2 * KL; ++t)
+        if (i - t >= 0) acc[t] -= Us[((size_t)(i - t) * G + kk) * W + t + 1] * xn;
+      y[(size_t)i * CPW] = xi;
 #pragma unroll
-      for (int q = 2 * KL; q >= 2; --q) x[q] = x[q - 1];
-      x[1] = acc;
+      for (int t = 0; t < 2 * KL - 1; ++t) acc[t] = acc[t + 1];
+      const int rn = i - 2 * KL;
+      acc[2 * KL - 1] = (rn >= 0) ? y[(size_t)rn * CPW] * Ds[(size_t)rn * G + kk] : 0.0;
+      xn = xi;
     }
   }
   __syncwarp();
@@ -429,16 +471,20 @@ __global__ void k_band_solve(int M, int nc, int Kz, int K, int CPW, int groups_p
       out[2 * (sm + (long long)kidx * Nm) + part] = -acc / sqrt(0.5);
     }
   }
-  for (int e = lane; e < N * 4 * gcnt; e += 32) {
-    const int cc = e / N, i = e - cc * N;
-    const int kq = cc >> 2, sg = (cc >> 1) & 1, pt = cc & 1;
+  double2* out2 = reinterpret_cast<double2*>(out);
+#pragma unroll 4
+  for (int e = lane; e < N * 2 * gcnt; e += 32) {
+    const int cp = e / N, i = e - cp * N;
+    const int kq = cp >> 1, sg = cp & 1;
     const int kabs = k0 + kq;
     if (sg && kabs == 0) continue;
     const int kidx = sg ? K - kabs : kabs;
-    const long long o = 2 * (sm + (long long)kidx * Nm + sh + i) + pt;
-    double v = Y[(size_t)i * CPW + cc];
-    if (step == MLX_STEP_ABCN) v -= s[o];
-    out[o] = v;
+    double2 v = make_double2(Y[(size_t)i * CPW + cp * 2], Y[(size_t)i * CPW + cp * 2 + 1]);
+    if (step == MLX_STEP_ABCN) {
+      v.x -= S[(size_t)i * CPW + cp * 2];
+      v.y -= S[(size_t)i * CPW + cp * 2 + 1];
+    }
+    out2[sm + (long long)kidx * Nm + sh + i] = v;
   }
 }
 
@@ -578,6 +624,7 @@ __global__ void __launch_bounds__(32) k_band_solve_ir(int M, int nc, int Kz, int
   }
   cp_async_commit();
   const double h = (step == MLX_STEP_FEBE_FULL) ? dt : 0.5 * dt;
+#pragma unroll 8
   for (int e = lane; e < N * 4 * gcnt; e += 32) {
     const int c = e / N, i = e - c * N;
     const int kq = c >> 2, sgn = (c >> 1) & 1, part = c & 1;
@@ -651,6 +698,7 @@ __global__ void __launch_bounds__(32) k_band_solve_ir(int M, int nc, int Kz, int
     if (dmax > 0x1p-20f * xmax) atomicOr(err, 8);
   }
   __syncwarp();
+#pragma unroll 8
   for (int e = lane; e < N * 4 * gcnt; e += 32) {
     const int cc = e / N, i = e - cc * N;
     const int kq = cc >> 2, sg = (cc >> 1) & 1, pt = cc & 1;
@@ -726,12 +774,34 @@ int mlx_band_setup(mlx_ctx* c, cudaStream_t st) {
   return MLX_OK;
 }
 
-// Direct-read variant for wide bands (the hyperviscous KL = p operators): only the
-// right-hand side / solution column lives in shared memory (one column per lane,
-// 32 chains per warp), the factor rows are read from global memory (their
-// addresses do not depend on the recurrence, so the loads issue ahead of use),
-// and the back substitution keeps four partial sums so the FP64 pipe sees
-// independent instructions.  Many more warps fit per SM than with staged factors.
+// Ring-staged variant for wide bands (the hyperviscous KL = p operators) and large
+// Nc: only the right-hand side / solution column lives in shared memory for the
+// whole solve (one column per lane, 32 chains per warp); factor rows stream
+// through small per-warp rings, staged by cp.async DIR_AHEAD rows ahead of use
+// (one commit group per row, so the wait before a row covers exactly that row).
+// At 256^3 the factors (hundreds of MB) come from HBM, whose latency a
+// register prefetch of one row could not cover.  The forward ring holds the
+// multipliers and pivots of one row per slot; the back-substitution ring holds
+// the rows of the current window (the pipelined substitution touches rows
+// i - 2KL .. i at step i) plus those in flight.  Same arithmetic, in the same
+// order, as k_band_solve.
+constexpr int DIR_AHEAD = 8;
+
+template <int KL>
+struct DirectSmem {
+  static constexpr int W = 2 * KL + 1;
+  static constexpr int G = 8;
+  static constexpr int RB = 2 * KL + 1 + DIR_AHEAD;   // back-substitution ring rows
+  static constexpr int RF = DIR_AHEAD + 1;            // forward ring rows
+  static constexpr size_t bslot = (size_t)G * (W + 1) * sizeof(double);               // U rows + 1/diag
+  static constexpr size_t fslot = (size_t)G * KL * sizeof(double) + (size_t)G * sizeof(int) + 0;
+  static constexpr size_t fslot16 = (fslot + 15) / 16 * 16;
+  static constexpr size_t ring = (RB * bslot > RF * fslot16) ? RB * bslot : RF * fslot16;
+  __host__ __device__ static size_t per_warp(int nc) {
+    return ((size_t)nc * 32 * sizeof(double) + ring + 15) / 16 * 16;
+  }
+};
+
 template <int KL>
 __global__ void k_band_solve_direct(int M, int nc, int Kz, int K, int groups_per_m, int step, double dt,
                                     const long long* __restrict__ soff, const long long* __restrict__ band_off,
@@ -742,6 +812,8 @@ __global__ void k_band_solve_direct(int M, int nc, int Kz, int K, int groups_per
                                     double* __restrict__ out) {
   constexpr int W = 2 * KL + 1;
   constexpr int CPW = 32, G = 8;
+  using SM = DirectSmem<KL>;
+  constexpr int RB = SM::RB, RF = SM::RF, P = DIR_AHEAD;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int gw = blockIdx.x * (blockDim.x >> 5) + wib;
@@ -752,46 +824,86 @@ __global__ void k_band_solve_direct(int M, int nc, int Kz, int K, int groups_per
   const int sh = (m == 0) ? m0_shift : 0;
   const int Nm = nc - m;
   const int N = Nm - sh;
-  double* Y = reinterpret_cast<double*>(smem_raw) + (size_t)wib * nc * CPW;   // [N][32]
+  unsigned char* wbase = smem_raw + (size_t)wib * SM::per_warp(nc);
+  double* Y = reinterpret_cast<double*>(wbase);                        // [N][32]
+  unsigned char* ring = wbase + (size_t)nc * 32 * sizeof(double);
   const long long fb = band_off[m];
   const long long sm = soff[m];
-  const double h = (step == MLX_STEP_FEBE_FULL) ? dt : 0.5 * dt;
-  for (int e = lane; e < N * 4 * gcnt; e += 32) {
-    const int c = e / N, i = e - c * N;
-    const int kk = c >> 2, sgn = (c >> 1) & 1, part = c & 1;
-    const int kabs = k0 + kk;
-    if (sgn && kabs == 0) continue;
-    const int kidx = sgn ? K - kabs : kabs;
-    const long long o = 2 * (sm + (long long)kidx * Nm + sh + i) + part;
-    double r;
-    if (step == MLX_STEP_PLAIN) {
-      r = s[o];
-    } else if (step == MLX_STEP_ABCN) {
-      r = 2.0 * s[o];
-      if (A) r += 1.5 * dt * A[o];
-      if (Ap) r -= 0.5 * dt * Ap[o];
-    } else {
-      r = s[o];
-      if (A) r += h * A[o];
+  // factor rows of one step: GS consecutive rows (the warp's |k| values), or a
+  // single row shared by every |k| (kz_fac == 1)
+  const int GS = (kz_fac == 1) ? 1 : gcnt;
+  auto rowbase = [&](int r) -> long long { return fb + (long long)r * kz_fac + (kz_fac == 1 ? 0 : k0); };
+  auto stage_f = [&](int r) {   // multipliers and pivots of row r into its forward slot
+    unsigned char* slot = ring + (size_t)(r % RF) * SM::fslot16;
+    const long long rb = rowbase(r);
+    double* ls = reinterpret_cast<double*>(slot);
+    int* ps = reinterpret_cast<int*>(slot + (size_t)G * KL * sizeof(double));
+    for (int e = lane; e < GS * KL + GS; e += 32) {
+      if (e < GS * KL) cp_async8(ls + e, Lm + rb * KL + e);
+      else cp_async4(ps + (e - GS * KL), piv + rb + (e - GS * KL));
     }
-    Y[(size_t)i * CPW + c] = r;
+  };
+  auto stage_b = [&](int r) {   // U rows and 1/diag of row r into its back-substitution slot
+    double* slot = reinterpret_cast<double*>(ring + (size_t)(r % RB) * SM::bslot);
+    const long long rb = rowbase(r);
+    for (int e = lane; e < GS * W + GS; e += 32) {
+      if (e < GS * W) cp_async8(slot + e, U + rb * W + e);
+      else cp_async8(slot + G * W + (e - GS * W), invd + rb + (e - GS * W));
+    }
+  };
+  const double h = (step == MLX_STEP_FEBE_FULL) ? dt : 0.5 * dt;
+  const double2* s2 = reinterpret_cast<const double2*>(s);
+  const double2* A2 = reinterpret_cast<const double2*>(A);
+  const double2* Ap2 = reinterpret_cast<const double2*>(Ap);
+  // forward ring prologue: rows 0 .. P-1 in flight while the right-hand sides load
+  for (int r = 0; r < P; ++r) {
+    if (r < N) stage_f(r);
+    cp_async_commit();
+  }
+  // one complex value per step (chain c = kk * 4 + sgn * 2 + part)
+#pragma unroll 4
+  for (int e = lane; e < N * 2 * gcnt; e += 32) {
+    const int cp = e / N, i = e - cp * N;
+    const int kq = cp >> 1, sg = cp & 1;
+    const int kabs = k0 + kq;
+    if (sg && kabs == 0) continue;
+    const int kidx = sg ? K - kabs : kabs;
+    const long long o = sm + (long long)kidx * Nm + sh + i;
+    const double2 sv = s2[o];
+    double2 r;
+    if (step == MLX_STEP_PLAIN) {
+      r = sv;
+    } else if (step == MLX_STEP_ABCN) {
+      r = make_double2(2.0 * sv.x, 2.0 * sv.y);
+      if (A) { const double2 q = A2[o]; r.x += 1.5 * dt * q.x; r.y += 1.5 * dt * q.y; }
+      if (Ap) { const double2 q = Ap2[o]; r.x -= 0.5 * dt * q.x; r.y -= 0.5 * dt * q.y; }
+    } else {
+      r = sv;
+      if (A) { const double2 q = A2[o]; r.x += h * q.x; r.y += h * q.y; }
+    }
+    Y[(size_t)i * CPW + cp * 2] = r.x;
+    Y[(size_t)i * CPW + cp * 2 + 1] = r.y;
   }
   __syncwarp();
   const int c = lane;
   const int kk = c >> 2, sgn = (c >> 1) & 1, part = c & 1;
   const bool valid = c < 4 * gcnt && !(sgn && k0 + kk == 0);
-  const long long rbase = fb + (kz_fac == 1 ? 0 : k0 + (kk < gcnt ? kk : 0));
-  if (c < 4 * gcnt) {
-    double* y = Y + c;
-    double w[KL + 1];
+  const bool act = c < 4 * gcnt;
+  const int ks = (kz_fac == 1) ? 0 : (kk < gcnt ? kk : 0);   // lane's slot within a staged row
+  double* y = Y + c;
+  // forward elimination
+  double w[KL + 1];
 #pragma unroll
-    for (int q = 0; q < KL; ++q) w[q + 1] = (q < N) ? y[(size_t)q * CPW] : 0.0;
-    for (int j = 0; j < N; ++j) {
-      const long long row = rbase + (long long)j * kz_fac;
-      const int d = __ldg(piv + row) - j;
-      double l[KL];
-#pragma unroll
-      for (int q = 0; q < KL; ++q) l[q] = __ldg(Lm + row * KL + q);
+  for (int q = 0; q < KL; ++q) w[q + 1] = (act && q < N) ? y[(size_t)q * CPW] : 0.0;
+  for (int j = 0; j < N; ++j) {
+    if (j + P < N) stage_f(j + P);
+    cp_async_commit();
+    cp_async_wait_group<P>();
+    __syncwarp();
+    const unsigned char* slot = ring + (size_t)(j % RF) * SM::fslot16;
+    const double* l = reinterpret_cast<const double*>(slot) + ks * KL;
+    const int d = reinterpret_cast<const int*>(slot + (size_t)G * KL * sizeof(double))[ks] - j;
+    if (act) {
 #pragma unroll
       for (int q = 0; q < KL; ++q) w[q] = w[q + 1];
       w[KL] = (j + KL < N) ? y[(size_t)(j + KL) * CPW] : 0.0;
@@ -802,47 +914,76 @@ __global__ void k_band_solve_direct(int M, int nc, int Kz, int K, int groups_per
 #pragma unroll
       for (int q = 1; q <= KL; ++q) w[q] -= l[q - 1] * w[0];
     }
-    double x[2 * KL + 1];
-#pragma unroll
-    for (int q = 0; q <= 2 * KL; ++q) x[q] = 0.0;
-    for (int i = N - 1; i >= 0; --i) {
-      const long long row = rbase + (long long)i * kz_fac;
-      double u[W];
-#pragma unroll
-      for (int q = 1; q < W; ++q) u[q] = __ldg(U + row * W + q);
-      const double dv = __ldg(invd + row);
-      double p0 = y[(size_t)i * CPW] * dv, p1 = 0.0, p2 = 0.0, p3 = 0.0;
-#pragma unroll
-      for (int q = 2 * KL; q >= 2; --q) {
-        if ((q & 3) == 0) p0 -= u[q] * x[q];
-        else if ((q & 3) == 1) p1 -= u[q] * x[q];
-        else if ((q & 3) == 2) p2 -= u[q] * x[q];
-        else p3 -= u[q] * x[q];
-      }
-      const double acc = ((p0 + p2) + (p1 + p3)) - u[1] * x[1];
-      y[(size_t)i * CPW] = acc;
-#pragma unroll
-      for (int q = 2 * KL; q >= 2; --q) x[q] = x[q - 1];
-      x[1] = acc;
-    }
+    __syncwarp();
   }
+  cp_async_wait_all();
   __syncwarp();
-  if (sh && c < 4 * gcnt && valid) {
-    double acc = 0.0;
-    for (int i = 0; i < N; ++i) acc += sqrt((2.0 * (i + 1) + 1.0) * 0.5) * Y[(size_t)i * CPW + c];
-    const int kidx = sgn ? K - (k0 + kk) : k0 + kk;
-    out[2 * (sm + (long long)kidx * Nm) + part] = -acc / sqrt(0.5);
+  // back substitution, software-pipelined as in k_band_solve: acc[t] is the
+  // partial sum of row i - t; at step i every pending row takes its term with
+  // x_{i+1}.  Rows are staged in descending order, P beyond the window.
+  for (int r = N - 1; r >= N - 2 * KL - P; --r) {
+    if (r >= 0) stage_b(r);
+    cp_async_commit();
   }
-  for (int e = lane; e < N * 4 * gcnt; e += 32) {
-    const int cc = e / N, i = e - cc * N;
-    const int kq = cc >> 2, sg = (cc >> 1) & 1, pt = cc & 1;
+  cp_async_wait_group<P>();
+  __syncwarp();
+  auto Urow = [&](int r) -> const double* {
+    return reinterpret_cast<const double*>(ring + (size_t)(r % RB) * SM::bslot) + ks * W;
+  };
+  auto Dval = [&](int r) -> double {
+    return reinterpret_cast<const double*>(ring + (size_t)(r % RB) * SM::bslot)[G * W + ks];
+  };
+  double acc[2 * KL];
+#pragma unroll
+  for (int t = 0; t < 2 * KL; ++t) {
+    const int r = N - 1 - t;
+    acc[t] = (act && r >= 0) ? y[(size_t)r * CPW] * Dval(r) : 0.0;
+  }
+  double xn = 0.0;   // x_{i+1}
+  for (int i = N - 1; i >= 0; --i) {
+    const int rs = i - 2 * KL - P;
+    if (rs >= 0) stage_b(rs);
+    cp_async_commit();
+    cp_async_wait_group<P>();
+    __syncwarp();
+    if (act) {
+      const double xi = acc[0] - Urow(i)[1] * xn;
+#pragma unroll
+      for (int t = 1; t < 2 * KL; ++t)
+        if (i - t >= 0) acc[t] -= Urow(i - t)[t + 1] * xn;
+      y[(size_t)i * CPW] = xi;
+#pragma unroll
+      for (int t = 0; t < 2 * KL - 1; ++t) acc[t] = acc[t + 1];
+      const int rn = i - 2 * KL;
+      acc[2 * KL - 1] = (rn >= 0) ? y[(size_t)rn * CPW] * Dval(rn) : 0.0;
+      xn = xi;
+    }
+    __syncwarp();
+  }
+  cp_async_wait_all();
+  __syncwarp();
+  if (sh && valid) {
+    double dacc = 0.0;
+    for (int i = 0; i < N; ++i) dacc += sqrt((2.0 * (i + 1) + 1.0) * 0.5) * Y[(size_t)i * CPW + c];
+    const int kidx = sgn ? K - (k0 + kk) : k0 + kk;
+    out[2 * (sm + (long long)kidx * Nm) + part] = -dacc / sqrt(0.5);
+  }
+  double2* out2 = reinterpret_cast<double2*>(out);
+#pragma unroll 4
+  for (int e = lane; e < N * 2 * gcnt; e += 32) {
+    const int cp = e / N, i = e - cp * N;
+    const int kq = cp >> 1, sg = cp & 1;
     const int kabs = k0 + kq;
     if (sg && kabs == 0) continue;
     const int kidx = sg ? K - kabs : kabs;
-    const long long o = 2 * (sm + (long long)kidx * Nm + sh + i) + pt;
-    double v = Y[(size_t)i * CPW + cc];
-    if (step == MLX_STEP_ABCN) v -= s[o];
-    out[o] = v;
+    const long long o = sm + (long long)kidx * Nm + sh + i;
+    double2 v = make_double2(Y[(size_t)i * CPW + cp * 2], Y[(size_t)i * CPW + cp * 2 + 1]);
+    if (step == MLX_STEP_ABCN) {
+      const double2 sv = s2[o];
+      v.x -= sv.x;
+      v.y -= sv.y;
+    }
+    out2[o] = v;
   }
 }
 
@@ -853,9 +994,11 @@ static int launch_solve(mlx_ctx* c, int step, const BandLU& f, const long long* 
   if (c->solve_direct) {
     const int gpm = (c->Kz + 7) / 8;
     const int warps = c->M * gpm;
+    const size_t pw = DirectSmem<KL>::per_warp(c->nc);
     int WPB = 4;
-    while (WPB > 1 && (size_t)WPB * c->nc * 32 * sizeof(double) > 200 * 1024) WPB /= 2;
-    const size_t smem = (size_t)WPB * c->nc * 32 * sizeof(double);
+    while (WPB > 1 && (size_t)WPB * pw > 200 * 1024) WPB /= 2;
+    if (pw > 200 * 1024) return MLX_EINVAL;
+    const size_t smem = (size_t)WPB * pw;
     k_band_solve_direct<KL><<<(warps + WPB - 1) / WPB, 32 * WPB, smem, st>>>(
         c->M, c->nc, c->Kz, c->K, gpm, step, c->dt, c->d_soff, fac_off, kz_fac, m0_shift, f.U, f.L, f.piv,
         f.invd, (const double*)s, (const double*)A, (const double*)Ap, (double*)out);

@@ -137,6 +137,7 @@ struct mlx_ctx {
   // vortex term workspace
   bool vortex_ready = false;
   double* d_rdr = nullptr;             // r d/dr band, [tri][2] (offsets -1, +1)
+  double* d_jac = nullptr;             // Jacobi matrix off-diagonal e_{m,i} (x Pbar_{m+i} couples i, i+1), [tri]
   double2* d_vspec = nullptr;          // 9 spectral temporaries
   void* d_vphys = nullptr;             // 6 physical temporaries
   double* d_setup_scratch = nullptr;

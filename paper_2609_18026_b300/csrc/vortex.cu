@@ -53,43 +53,47 @@ __device__ __forceinline__ double2 apply_D(const double* db, const double2* v, i
   return r;
 }
 
-__global__ void k_vortex_fields(long long n_spec, int M, int nc, int Kz, int K, double lz,
-                                const long long* __restrict__ soff, const long long* __restrict__ rows,
-                                const double* __restrict__ rdr, const double* __restrict__ lap,
-                                const double2* __restrict__ psi, const double2* __restrict__ chi,
-                                double2* __restrict__ rvr, double2* __restrict__ rvp, double2* __restrict__ vz,
-                                double2* __restrict__ rwr, double2* __restrict__ rwp, double2* __restrict__ wz) {
-  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= n_spec) return;
-  const int m = m_of(idx, soff, M);
+// One CTA per (m, k) vector: psi and chi are staged in shared memory once, D_m chi
+// and Psi = -(D_m - kappa^2) chi are formed once per entry, and the six fields are
+// read off the staged vectors (no band product is evaluated twice).
+__global__ void k_vortex_fields(int nc, int Kz, int K, double lz, const long long* __restrict__ soff,
+                                const long long* __restrict__ rows, const double* __restrict__ rdr,
+                                const double* __restrict__ lap, const double2* __restrict__ psi,
+                                const double2* __restrict__ chi, double2* __restrict__ rvr,
+                                double2* __restrict__ rvp, double2* __restrict__ vz, double2* __restrict__ rwr,
+                                double2* __restrict__ rwp, double2* __restrict__ wz) {
+  extern __shared__ double2 vsh[];   // [4][nc]: psi, chi, D chi, Psi
+  const int kidx = blockIdx.x, m = blockIdx.y;
   const int Nm = nc - m;
-  const long long loc = idx - soff[m];
-  const int kidx = (int)(loc / Nm), a = (int)(loc - (long long)kidx * Nm);
   const long long base = soff[m] + (long long)kidx * Nm;
+  double2* P = vsh;
+  double2* Ch = vsh + nc;
+  double2* Dc = vsh + 2 * nc;
+  double2* Ps = vsh + 3 * nc;
+  for (int a = threadIdx.x; a < Nm; a += blockDim.x) { P[a] = psi[base + a]; Ch[a] = chi[base + a]; }
+  __syncthreads();
   const double kap = kappa_of(kidx, Kz, K, lz);
   const double* rb = rdr + rows[m] * 2;
   const double* db = lap + rows[m] * 5;
-  const double2* p = psi + base;
-  const double2* c = chi + base;
-  const double2 Rpsi = apply_R(rb, p, a, Nm);
-  const double2 Rchi = apply_R(rb, c, a, Nm);
-  const double2 Dpsi = apply_D(db, p, a, Nm);
-  const double2 Dchi = apply_D(db, c, a, Nm);
-  // Psi = -(D - kappa^2) chi at a - 1, a, a + 1 for R Psi
-  auto Psi_at = [&](int b) -> double2 {
-    return csub(cmulr(kap * kap, c[b]), apply_D(db, c, b, Nm));
-  };
-  const double2 Psi = csub(cmulr(kap * kap, c[a]), Dchi);
-  double2 RPsi = make_double2(0.0, 0.0);
-  if (a - 1 >= 0) RPsi = cadd(RPsi, cmulr(rb[a * 2 + 0], Psi_at(a - 1)));
-  if (a + 1 < Nm) RPsi = cadd(RPsi, cmulr(rb[a * 2 + 1], Psi_at(a + 1)));
+  for (int a = threadIdx.x; a < Nm; a += blockDim.x) {
+    const double2 d = apply_D(db, Ch, a, Nm);
+    Dc[a] = d;
+    Ps[a] = csub(cmulr(kap * kap, Ch[a]), d);
+  }
+  __syncthreads();
   const double mm = (double)m;
-  rvr[idx] = cadd(cimul(mm, p[a]), cimul(kap, Rchi));
-  rvp[idx] = csub(cmulr(-1.0, Rpsi), cmulr(mm * kap, c[a]));
-  vz[idx] = cmulr(-1.0, Dchi);
-  rwr[idx] = cadd(cimul(mm, Psi), cimul(kap, Rpsi));
-  rwp[idx] = csub(cmulr(-1.0, RPsi), cmulr(mm * kap, p[a]));
-  wz[idx] = cmulr(-1.0, Dpsi);
+  for (int a = threadIdx.x; a < Nm; a += blockDim.x) {
+    const long long idx = base + a;
+    const double2 Rpsi = apply_R(rb, P, a, Nm);
+    const double2 Rchi = apply_R(rb, Ch, a, Nm);
+    const double2 RPsi = apply_R(rb, Ps, a, Nm);
+    rvr[idx] = cadd(cimul(mm, P[a]), cimul(kap, Rchi));
+    rvp[idx] = csub(cmulr(-1.0, Rpsi), cmulr(mm * kap, Ch[a]));
+    vz[idx] = cmulr(-1.0, Dc[a]);
+    rwr[idx] = cadd(cimul(mm, Ps[a]), cimul(kap, Rpsi));
+    rwp[idx] = csub(cmulr(-1.0, RPsi), cmulr(mm * kap, P[a]));
+    wz[idx] = cmulr(-1.0, apply_D(db, P, a, Nm));
+  }
 }
 
 template <typename T>
@@ -119,16 +123,26 @@ __global__ void k_vortex_product(long long n_phys, int nphi, int nr, T U0, const
   f2[idx] = ar * rwp - ap * rwr;                 // C = r^2 N_z
 }
 
+// Jacobi matrix entries e_{m,i} = sqrt((n^2 - m^2) / (4 n^2 - 1)), n = m + i + 1, coupling
+// local rows i and i + 1 (multiplication by x, from x Pbar_n = a_{n+1} Pbar_{n+1} + a_n Pbar_{n-1});
+// tabulated once per context (the square root and division are costly in FP64)
 __device__ __forceinline__ double jac_e(int m, int i, int Nm) {
   if (i < 0 || i + 1 >= Nm) return 0.0;
   const double n = (double)(m + i + 1), mm = (double)m;
   return sqrt((n * n - mm * mm) / (4.0 * n * n - 1.0));
 }
-// (J v)_a = e_{a-1} v_{a-1} + e_a v_{a+1}
-__device__ __forceinline__ double2 apply_J(const double2* v, int m, int a, int Nm) {
+__global__ void k_jac_table(int M, int nc, const long long* __restrict__ rows, double* __restrict__ jac) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= rows[M]) return;
+  int lo = 0, hi = M;
+  while (hi - lo > 1) { const int mid = (lo + hi) >> 1; if (rows[mid] <= idx) lo = mid; else hi = mid; }
+  jac[idx] = jac_e(lo, (int)(idx - rows[lo]), nc - lo);
+}
+// (J v)_a = e_{a-1} v_{a-1} + e_a v_{a+1}, e from the table row of m (je = jac + rows[m])
+__device__ __forceinline__ double2 apply_J(const double2* v, const double* je, int a, int Nm) {
   double2 r = make_double2(0.0, 0.0);
-  if (a - 1 >= 0) r = cadd(r, cmulr(jac_e(m, a - 1, Nm), v[a - 1]));
-  if (a + 1 < Nm) r = cadd(r, cmulr(jac_e(m, a, Nm), v[a + 1]));
+  if (a - 1 >= 0) r = cadd(r, cmulr(je[a - 1], v[a - 1]));
+  if (a + 1 < Nm) r = cadd(r, cmulr(je[a], v[a + 1]));
   return r;
 }
 
@@ -154,6 +168,7 @@ __global__ void k_proj_rhs1(long long n_spec, int M, int nc, int Kz, int K, doub
 
 // rhs_g = (I - J) T
 __global__ void k_proj_rhs2(long long n_spec, int M, int nc, const long long* __restrict__ soff,
+                            const long long* __restrict__ rows, const double* __restrict__ jac,
                             const double2* __restrict__ T, double2* __restrict__ rhs_g) {
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= n_spec) return;
@@ -162,12 +177,13 @@ __global__ void k_proj_rhs2(long long n_spec, int M, int nc, const long long* __
   const long long loc = idx - soff[m];
   const int kidx = (int)(loc / Nm), a = (int)(loc - (long long)kidx * Nm);
   const long long base = soff[m] + (long long)kidx * Nm;
-  rhs_g[idx] = csub(T[idx], apply_J(T + base, m, a, Nm));
+  rhs_g[idx] = csub(T[idx], apply_J(T + base, jac + rows[m], a, Nm));
 }
 
 // rhs_chi = i kappa ell^2 (I + J) g - (I - J) C  (first term absent at k = 0)
 __global__ void k_proj_rhs3(long long n_spec, int M, int nc, int Kz, int K, double lz, double ell,
-                            const long long* __restrict__ soff, const double2* __restrict__ gg,
+                            const long long* __restrict__ soff, const long long* __restrict__ rows,
+                            const double* __restrict__ jac, const double2* __restrict__ gg,
                             const double2* __restrict__ C, double2* __restrict__ rhs_chi) {
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= n_spec) return;
@@ -177,8 +193,9 @@ __global__ void k_proj_rhs3(long long n_spec, int M, int nc, int Kz, int K, doub
   const int kidx = (int)(loc / Nm), a = (int)(loc - (long long)kidx * Nm);
   const long long base = soff[m] + (long long)kidx * Nm;
   const double kap = kappa_of(kidx, Kz, K, lz);
-  double2 r = cmulr(-1.0, csub(C[idx], apply_J(C + base, m, a, Nm)));
-  if (kidx != 0) r = cadd(r, cimul(kap * ell * ell, cadd(gg[idx], apply_J(gg + base, m, a, Nm))));
+  const double* je = jac + rows[m];
+  double2 r = cmulr(-1.0, csub(C[idx], apply_J(C + base, je, a, Nm)));
+  if (kidx != 0) r = cadd(r, cimul(kap * ell * ell, cadd(gg[idx], apply_J(gg + base, je, a, Nm))));
   rhs_chi[idx] = r;
 }
 
@@ -213,6 +230,10 @@ int mlx_vortex_prepare(mlx_ctx* c, cudaStream_t st) {
   const size_t es = elem_size(c->precision);
   MLX_CUDA_TRY(c, cudaMalloc(&c->d_rdr, sizeof(double) * c->tri * 2));
   k_rdr_band<<<nblk(c->tri, 256), 256, 0, st>>>(c->M, c->nc, c->d_lap_off, c->d_rdr);
+  MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_vortex_fields, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)(sizeof(double2) * 4 * c->nc)));
+  MLX_CUDA_TRY(c, cudaMalloc(&c->d_jac, sizeof(double) * c->tri));
+  k_jac_table<<<nblk(c->tri, 256), 256, 0, st>>>(c->M, c->nc, c->d_lap_off, c->d_jac);
   MLX_LAUNCH_CHECK(c);
   MLX_CUDA_TRY(c, cudaMalloc(&c->d_vspec, sizeof(double2) * c->n_spec * 9));
   MLX_CUDA_TRY(c, cudaMalloc(&c->d_vphys, es * c->n_phys * 6));
@@ -239,9 +260,12 @@ static int vortex_nonlinear_t(mlx_ctx* c, double U0, const double2* state, doubl
   T* P[6];
   for (int i = 0; i < 6; ++i) P[i] = reinterpret_cast<T*>(c->d_vphys) + np * i;
   const int tb = 256;
-  k_vortex_fields<<<nblk(ns, tb), tb, 0, st>>>(ns, c->M, c->nc, c->Kz, c->K, c->lz, c->d_soff, c->d_lap_off,
-                                               c->d_rdr, c->d_lap, psi, chi, F[0], F[1], F[2], F[3], F[4],
-                                               F[5]);
+  {
+    const int vt = c->nc >= 256 ? 256 : ((c->nc + 31) / 32) * 32;
+    k_vortex_fields<<<dim3(c->K, c->M), vt, sizeof(double2) * 4 * c->nc, st>>>(
+        c->nc, c->Kz, c->K, c->lz, c->d_soff, c->d_lap_off, c->d_rdr, c->d_lap, psi, chi, F[0], F[1], F[2], F[3],
+        F[4], F[5]);
+  }
   MLX_LAUNCH_CHECK(c);
   int rc;
   for (int f = 0; f < 6; ++f) {
@@ -260,12 +284,12 @@ static int vortex_nonlinear_t(mlx_ctx* c, double U0, const double2* state, doubl
   k_proj_rhs1<<<nblk(ns, tb), tb, 0, st>>>(ns, c->M, c->nc, c->Kz, c->K, c->lz, c->d_soff, c->d_lap_off, c->d_rdr,
                                            F[6], F[7], F[8], F[0], F[1]);
   MLX_LAUNCH_CHECK(c);
-  k_proj_rhs2<<<nblk(ns, tb), tb, 0, st>>>(ns, c->M, c->nc, c->d_soff, F[1], F[2]);
+  k_proj_rhs2<<<nblk(ns, tb), tb, 0, st>>>(ns, c->M, c->nc, c->d_soff, c->d_lap_off, c->d_jac, F[1], F[2]);
   MLX_LAUNCH_CHECK(c);
   if ((rc = mlx_proj_solve(c, 0, F[0], out, st))) return rc;         // psi_N
   if ((rc = mlx_proj_solve(c, 2, F[2], F[3], st))) return rc;        // g
-  k_proj_rhs3<<<nblk(ns, tb), tb, 0, st>>>(ns, c->M, c->nc, c->Kz, c->K, c->lz, c->ell, c->d_soff, F[3], F[8],
-                                           F[4]);
+  k_proj_rhs3<<<nblk(ns, tb), tb, 0, st>>>(ns, c->M, c->nc, c->Kz, c->K, c->lz, c->ell, c->d_soff, c->d_lap_off,
+                                           c->d_jac, F[3], F[8], F[4]);
   MLX_LAUNCH_CHECK(c);
   return mlx_proj_solve(c, 1, F[4], out + ns, st);                   // chi_N
 }
