@@ -9,7 +9,9 @@
 // lines (r and r + R/2) are packed into one complex line of length Nphi.  A CTA of
 // the z kernel owns one m and a tile of R radii (one complex line per radius).
 // Tiles are staged through shared memory as [line][point] rows of stride N + 1
-// (coalesced global access along r; conflict-free per-line reads).  Each line is
+// (coalesced global access along r; conflict-free per-line reads; the global-load
+// loops are unrolled so that every thread keeps several loads in flight, which
+// the memory latency needs at these occupancies).  Each line is
 // transformed by one warp (or a group of N lanes when N < 32): lane l holds
 // points l + 32 e, e < E = N/32, in registers; butterflies at distance >= 32 are
 // in-lane, below 32 they use __shfl_xor_sync.  DIF (natural in, bit-reversed
@@ -163,6 +165,7 @@ __global__ void __launch_bounds__(256) k_phi(int N, int logN, int M, int Nr, int
   const long long plane = (long long)z * N * Nr;
 
   if constexpr (MODE == PHI_FWD) {
+#pragma unroll 8
     for (int t = threadIdx.x; t < N * R; t += blockDim.x) {
       const int j = t / R, rr = t % R;
       const int r = r0 + rr;
@@ -188,6 +191,7 @@ __global__ void __launch_bounds__(256) k_phi(int N, int logN, int M, int Nr, int
     // Zhat[N-m] = conj(A_m) + i conj(B_m), Zhat[0] = Re A_0 + i Re B_0
     for (int t = threadIdx.x; t < B * ld; t += blockDim.x) L[t] = C{};
     __syncthreads();
+#pragma unroll 8
     for (int t = threadIdx.x; t < M * B; t += blockDim.x) {
       const int m = t / B, b = t % B;
       const int ra = r0 + b, rb = r0 + b + B;
@@ -256,6 +260,7 @@ __global__ void __launch_bounds__(256) k_z(int Nz, int logN, int Kz, int K, int 
   const int r0 = blockIdx.x * R;
   const int m = blockIdx.y;
   if (!INVERSE) {
+#pragma unroll 8
     for (int t = threadIdx.x; t < Nz * R; t += blockDim.x) {
       const int l = t / R, b = t % R;
       const int r = r0 + b;
@@ -269,6 +274,7 @@ __global__ void __launch_bounds__(256) k_z(int Nz, int logN, int Kz, int K, int 
   } else {
     for (int t = threadIdx.x; t < R * ld; t += blockDim.x) L[t] = C{};
     __syncthreads();
+#pragma unroll 8
     for (int t = threadIdx.x; t < K * R; t += blockDim.x) {
       const int kk = t / R, b = t % R;
       const int r = r0 + b;
