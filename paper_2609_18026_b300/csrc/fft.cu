@@ -123,16 +123,19 @@ enum PhiMode { PHI_FWD = 0, PHI_BWD = 1, PHI_FKPP = 2 };
 
 // Real analysis of packed line pairs held in L[b][m] (natural order, forward
 // DFT), scaled by 1/N, written to zm for this (z, r-tile).
+// With brev the line holds frequency p at position bitrev(p) (DIF output kept in
+// register order), so only the M retained frequencies are looked up scattered.
 template <typename T, typename C>
 __device__ void phi_unpack_store(const C* L, int ld, int N, int B, int M, int Nr, int r0, int z,
-                                 T* __restrict__ zre, T* __restrict__ zim) {
+                                 T* __restrict__ zre, T* __restrict__ zim, bool brev, int logN) {
   const T inv = (T)1 / (T)N;
   const int R = 2 * B;
   for (int t = threadIdx.x; t < M * R; t += blockDim.x) {
     const int m = t / R, rr = t % R;
     const int b = rr % B;
-    const C zm = L[b * ld + m];
-    const C zc = L[b * ld + ((N - m) & (N - 1))];
+    const int pm = m, pc = (N - m) & (N - 1);
+    const C zm = L[b * ld + (brev ? bitrev(pm, logN) : pm)];
+    const C zc = L[b * ld + (brev ? bitrev(pc, logN) : pc)];
     T re, im;
     if (rr < B) {  // X_m = (Z_m + conj(Z_{N-m})) / 2
       re = (zm.x + zc.x) * (T)0.5;
@@ -181,11 +184,11 @@ __global__ void __launch_bounds__(256) k_phi(int N, int logN, int M, int Nr, int
       dif<C, E>(v, N, lj, tw, false);
       if (act) {
 #pragma unroll
-        for (int e = 0; e < E; ++e) L[b * ld + bitrev(lj + 32 * e, logN)] = v[e];
+        for (int e = 0; e < E; ++e) L[b * ld + lj + 32 * e] = v[e];   // bit-reversed order
       }
     });
     __syncthreads();
-    phi_unpack_store<T, C>(L, ld, N, B, M, Nr, r0, z, zre, zim);
+    phi_unpack_store<T, C>(L, ld, N, B, M, Nr, r0, z, zre, zim, true, logN);
   } else {
     // packed Hermitian spectrum of each line pair: Zhat[m] = A_m + i B_m,
     // Zhat[N-m] = conj(A_m) + i conj(B_m), Zhat[0] = Re A_0 + i Re B_0
@@ -199,14 +202,18 @@ __global__ void __launch_bounds__(256) k_phi(int N, int logN, int M, int Nr, int
       const long long oa = ((long long)z * M + m) * Nr;
       if (ra < Nr) { ar = zre[oa + ra]; ai = zim[oa + ra]; }
       if (rb < Nr) { br = zre[oa + rb]; bi = zim[oa + rb]; }
+      // the synthesis-only transform takes its input bit-reversed (DIT), the fused
+      // Fisher-KPP transform in natural order (DIF, product, DIT)
+      const int p1 = (MODE == PHI_BWD) ? bitrev(m, logN) : m;
+      const int p2 = (MODE == PHI_BWD) ? bitrev(N - m, logN) : N - m;
       if (m == 0) {
         C v; v.x = ar; v.y = br;
         L[b * ld] = v;
       } else {
         C v1; v1.x = ar - bi; v1.y = ai + br;
         C v2; v2.x = ar + bi; v2.y = br - ai;
-        L[b * ld + m] = v1;
-        L[b * ld + N - m] = v2;
+        L[b * ld + p1] = v1;
+        L[b * ld + p2] = v2;
       }
     }
     __syncthreads();
@@ -214,6 +221,14 @@ __global__ void __launch_bounds__(256) k_phi(int N, int logN, int M, int Nr, int
       C v[E];
 #pragma unroll
       for (int e = 0; e < E; ++e) v[e] = act ? L[b * ld + lj + 32 * e] : C{};
+      if constexpr (MODE == PHI_BWD) {
+        dit<C, E>(v, N, lj, tw, true);   // bit-reversed spectrum in, physical values in natural order
+        if (act) {
+#pragma unroll
+          for (int e = 0; e < E; ++e) L[b * ld + lj + 32 * e] = v[e];
+        }
+        return;
+      }
       dif<C, E>(v, N, lj, tw, true);   // physical values, bit-reversed positions
       if constexpr (MODE == PHI_FKPP) {
 #pragma unroll
@@ -226,11 +241,6 @@ __global__ void __launch_bounds__(256) k_phi(int N, int logN, int M, int Nr, int
 #pragma unroll
           for (int e = 0; e < E; ++e) L[b * ld + lj + 32 * e] = v[e];
         }
-      } else {
-        if (act) {
-#pragma unroll
-          for (int e = 0; e < E; ++e) L[b * ld + bitrev(lj + 32 * e, logN)] = v[e];
-        }
       }
     });
     __syncthreads();
@@ -242,7 +252,7 @@ __global__ void __launch_bounds__(256) k_phi(int N, int logN, int M, int Nr, int
         if (r < Nr) phys[plane + (long long)j * Nr + r] = (rr < B) ? v.x : v.y;
       }
     } else {
-      phi_unpack_store<T, C>(L, ld, N, B, M, Nr, r0, z, zre, zim);
+      phi_unpack_store<T, C>(L, ld, N, B, M, Nr, r0, z, zre, zim, false, logN);
     }
   }
 }
@@ -282,7 +292,7 @@ __global__ void __launch_bounds__(256) k_z(int Nz, int logN, int Kz, int K, int 
       if (r < Nr) {
         const long long o = ((long long)kk * M + m) * Nr + r;
         C v; v.x = mre[o]; v.y = mim[o];
-        L[b * ld + pos] = v;
+        L[b * ld + bitrev(pos, logN)] = v;   // bit-reversed input of the DIT below
       }
     }
   }
@@ -291,10 +301,15 @@ __global__ void __launch_bounds__(256) k_z(int Nz, int logN, int Kz, int K, int 
     C v[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) v[e] = act ? L[b * ld + lj + 32 * e] : C{};
-    dif<C, E>(v, Nz, lj, tw, INVERSE);
+    // forward: DIF, output kept in register (bit-reversed) order; inverse: DIT
+    // from the bit-reversed input, natural output.  Either way the dense line is
+    // written back in register order, and only the K retained wavenumbers are
+    // addressed through the bit reversal.
+    if (INVERSE) dit<C, E>(v, Nz, lj, tw, true);
+    else dif<C, E>(v, Nz, lj, tw, false);
     if (act) {
 #pragma unroll
-      for (int e = 0; e < E; ++e) L[b * ld + bitrev(lj + 32 * e, logN)] = v[e];
+      for (int e = 0; e < E; ++e) L[b * ld + lj + 32 * e] = v[e];
     }
   });
   __syncthreads();
@@ -305,7 +320,7 @@ __global__ void __launch_bounds__(256) k_z(int Nz, int logN, int Kz, int K, int 
       const int r = r0 + b;
       const int pos = (kk < Kz) ? kk : Nz - (K - kk);
       if (r < Nr) {
-        const C v = L[b * ld + pos];
+        const C v = L[b * ld + bitrev(pos, logN)];
         const long long o = ((long long)kk * M + m) * Nr + r;
         mre[o] = v.x * inv;
         mim[o] = v.y * inv;
