@@ -211,10 +211,14 @@ int mlx_advance(mlx_ctx* ctx, int kind, const double* coeffs, int ncoeffs,
  *   "solve_cpw": real chains per warp of the banded solve, 4, 8, 16 or 32
  *                (default 8);
  *   "solve_wpb": warps per CTA of the banded solve, 1, 2 or 4 (default 4).
- *   "solve_direct": 1 = banded-solve variant that reads factor rows from global
- *                memory and keeps only the solution columns in shared memory
- *                (32 chains per warp); default 1 for hyperviscous bands
- *                (half width >= 4, set by mlx_implicit_setup), else 0.
+ *   "solve_direct": 1 = banded-solve variant that keeps only the solution
+ *                columns in shared memory for the whole solve and streams the
+ *                factor rows through small per-warp rings (cp.async, 8 rows ahead);
+ *                default 1 for hyperviscous bands (half width >= 4, set by
+ *                mlx_implicit_setup), else 0.
+ *   "solve_direct_cpw": real chains per warp of that variant, 8, 16 or 32
+ *                (default 8: fewer lanes per warp, more warps per SM to hide the
+ *                FP64 latency).
  *   "solve_ir":  1 = the implicit step (I - c L) x = b by mixed-precision
  *                iterative refinement: the band recurrence runs in FP32 with the
  *                FP32-rounded factors, and FP64 residuals b - (I - c L) x from the

@@ -17,6 +17,8 @@
 // mixed-precision refinement variant at k_band_solve_ir.
 #include "mlx_internal.cuh"
 
+#include <type_traits>
+
 namespace {
 
 __device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
@@ -787,10 +789,10 @@ int mlx_band_setup(mlx_ctx* c, cudaStream_t st) {
 // order, as k_band_solve.
 constexpr int DIR_AHEAD = 8;
 
-template <int KL>
+template <int KL, int CPWD>
 struct DirectSmem {
   static constexpr int W = 2 * KL + 1;
-  static constexpr int G = 8;
+  static constexpr int G = CPWD / 4;
   static constexpr int RB = 2 * KL + 1 + DIR_AHEAD;   // back-substitution ring rows
   static constexpr int RF = DIR_AHEAD + 1;            // forward ring rows
   static constexpr size_t bslot = (size_t)G * (W + 1) * sizeof(double);               // U rows + 1/diag
@@ -798,11 +800,11 @@ struct DirectSmem {
   static constexpr size_t fslot16 = (fslot + 15) / 16 * 16;
   static constexpr size_t ring = (RB * bslot > RF * fslot16) ? RB * bslot : RF * fslot16;
   __host__ __device__ static size_t per_warp(int nc) {
-    return ((size_t)nc * 32 * sizeof(double) + ring + 15) / 16 * 16;
+    return ((size_t)nc * CPWD * sizeof(double) + ring + 15) / 16 * 16;
   }
 };
 
-template <int KL>
+template <int KL, int CPWD>
 __global__ void k_band_solve_direct(int M, int nc, int Kz, int K, int groups_per_m, int step, double dt,
                                     const long long* __restrict__ soff, const long long* __restrict__ band_off,
                                     int kz_fac, int m0_shift, const double* __restrict__ U,
@@ -811,8 +813,8 @@ __global__ void k_band_solve_direct(int M, int nc, int Kz, int K, int groups_per
                                     const double* __restrict__ A, const double* __restrict__ Ap,
                                     double* __restrict__ out) {
   constexpr int W = 2 * KL + 1;
-  constexpr int CPW = 32, G = 8;
-  using SM = DirectSmem<KL>;
+  constexpr int CPW = CPWD, G = CPWD / 4;
+  using SM = DirectSmem<KL, CPWD>;
   constexpr int RB = SM::RB, RF = SM::RF, P = DIR_AHEAD;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -825,8 +827,8 @@ __global__ void k_band_solve_direct(int M, int nc, int Kz, int K, int groups_per
   const int Nm = nc - m;
   const int N = Nm - sh;
   unsigned char* wbase = smem_raw + (size_t)wib * SM::per_warp(nc);
-  double* Y = reinterpret_cast<double*>(wbase);                        // [N][32]
-  unsigned char* ring = wbase + (size_t)nc * 32 * sizeof(double);
+  double* Y = reinterpret_cast<double*>(wbase);                        // [N][CPW]
+  unsigned char* ring = wbase + (size_t)nc * CPW * sizeof(double);
   const long long fb = band_off[m];
   const long long sm = soff[m];
   // factor rows of one step: GS consecutive rows (the warp's |k| values), or a
@@ -992,17 +994,25 @@ static int launch_solve(mlx_ctx* c, int step, const BandLU& f, const long long* 
                         int m0_shift, const double2* s, const double2* A, const double2* Ap, double2* out,
                         cudaStream_t st) {
   if (c->solve_direct) {
-    const int gpm = (c->Kz + 7) / 8;
-    const int warps = c->M * gpm;
-    const size_t pw = DirectSmem<KL>::per_warp(c->nc);
-    int WPB = 4;
-    while (WPB > 1 && (size_t)WPB * pw > 200 * 1024) WPB /= 2;
-    if (pw > 200 * 1024) return MLX_EINVAL;
-    const size_t smem = (size_t)WPB * pw;
-    k_band_solve_direct<KL><<<(warps + WPB - 1) / WPB, 32 * WPB, smem, st>>>(
-        c->M, c->nc, c->Kz, c->K, gpm, step, c->dt, c->d_soff, fac_off, kz_fac, m0_shift, f.U, f.L, f.piv,
-        f.invd, (const double*)s, (const double*)A, (const double*)Ap, (double*)out);
-    return MLX_OK;
+    // chains per warp: 32 (every lane busy) or 16 (half the shared memory per
+    // warp, so twice the warps per SM hide the FP64 latency)
+    auto go = [&](auto cpw_tag) -> int {
+      constexpr int CPWD = decltype(cpw_tag)::value;
+      const int gpm = (c->Kz + CPWD / 4 - 1) / (CPWD / 4);
+      const int warps = c->M * gpm;
+      const size_t pw = DirectSmem<KL, CPWD>::per_warp(c->nc);
+      int WPB = 8;
+      while (WPB > 1 && (size_t)WPB * pw > 200 * 1024) WPB /= 2;
+      if (pw > 200 * 1024) return MLX_EINVAL;
+      const size_t smem = (size_t)WPB * pw;
+      k_band_solve_direct<KL, CPWD><<<(warps + WPB - 1) / WPB, 32 * WPB, smem, st>>>(
+          c->M, c->nc, c->Kz, c->K, gpm, step, c->dt, c->d_soff, fac_off, kz_fac, m0_shift, f.U, f.L, f.piv,
+          f.invd, (const double*)s, (const double*)A, (const double*)Ap, (double*)out);
+      return MLX_OK;
+    };
+    if (c->solve_direct_cpw == 8) return go(std::integral_constant<int, 8>());
+    if (c->solve_direct_cpw == 16) return go(std::integral_constant<int, 16>());
+    return go(std::integral_constant<int, 32>());
   }
   // Chains per warp and warps per CTA are launch-shape parameters (measured best
   // at the 128x128x64 workload: 8 chains per warp, 1-4 warps per CTA).
@@ -1171,11 +1181,14 @@ int mlx_band_prepare(mlx_ctx* c) {
   const int lim = 200 * 1024;
   MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_band_solve<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
   MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_band_solve<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-  MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_band_solve_direct<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-  MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_band_solve_direct<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-  MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_band_solve_direct<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-  MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_band_solve_direct<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-  MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_band_solve_direct<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+#define MLX_DIRECT_ATTR(KLV, CPWV)                                                                   \
+  MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_band_solve_direct<KLV, CPWV>,                               \
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, lim))
+  MLX_DIRECT_ATTR(2, 32); MLX_DIRECT_ATTR(3, 32); MLX_DIRECT_ATTR(4, 32); MLX_DIRECT_ATTR(6, 32);
+  MLX_DIRECT_ATTR(8, 32); MLX_DIRECT_ATTR(2, 16); MLX_DIRECT_ATTR(3, 16); MLX_DIRECT_ATTR(4, 16);
+  MLX_DIRECT_ATTR(6, 16); MLX_DIRECT_ATTR(8, 16); MLX_DIRECT_ATTR(2, 8); MLX_DIRECT_ATTR(3, 8);
+  MLX_DIRECT_ATTR(4, 8); MLX_DIRECT_ATTR(6, 8); MLX_DIRECT_ATTR(8, 8);
+#undef MLX_DIRECT_ATTR
   MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_band_solve<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
   MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_band_solve<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
   MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_band_solve<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));

@@ -143,7 +143,8 @@ struct mlx_ctx {
   double* d_setup_scratch = nullptr;
   int solve_cpw = 8;                   // real chains per warp in the banded solve (4..32)
   int solve_wpb = 4;                   // warps per CTA in the banded solve (1..4)
-  int solve_direct = 0;                // 1: direct-read solve variant (wide bands)
+  int solve_direct = 0;                // 1: ring-staged solve variant (wide bands, large Nc)
+  int solve_direct_cpw = 8;            // chains per warp of that variant: 8, 16 or 32
   int solve_ir = 0;                    // 1: FP32 solves refined to FP64 by FP64 residuals
   int solve_ir_max = 8;                // refinement steps at most (early exit at FP64 level)
 
