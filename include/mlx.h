@@ -211,6 +211,9 @@ int mlx_advance(mlx_ctx* ctx, int kind, const double* coeffs, int ncoeffs,
  *   "solve_cpw": real chains per warp of the banded solve, 4, 8, 16 or 32
  *                (default 8);
  *   "solve_wpb": warps per CTA of the banded solve, 1, 2 or 4 (default 4).
+ *   "solve_keep_s": 1 (default) = the staged solve keeps a shared-memory copy
+ *                of s for the AB-CN "- s" (no global re-read); 0 = re-read s (a
+ *                smaller CTA; mlx_batch_create sets 0 on its members).
  *   "solve_direct": 1 = banded-solve variant that keeps only the solution
  *                columns in shared memory for the whole solve and streams the
  *                factor rows through small per-warp rings (cp.async, 8 rows ahead);
@@ -246,7 +249,9 @@ int mlx_set_tuning(mlx_ctx* ctx, const char* key, int value);
  * paper, whose runs are single problems) ----
  * A batch groups n independent contexts (any sizes, precisions and kinds; each
  * created and set up by the caller, which keeps owning them).  The batch owns
- * only streams, events and cached CUDA graphs. */
+ * only streams, events and cached CUDA graphs.  Creating a batch sets the
+ * tuning key "solve_keep_s" of every member to 0 (smaller shared-memory footprint
+ * per solve CTA, so that the instances' kernels co-reside). */
 typedef struct mlx_batch mlx_batch;
 int mlx_batch_create(mlx_ctx* const* ctxs, int n, mlx_batch** out);
 int mlx_batch_destroy(mlx_batch* batch);

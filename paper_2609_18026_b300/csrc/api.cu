@@ -396,6 +396,13 @@ int mlx_set_tuning(mlx_ctx* c, const char* key, int value) {
     c->graphs.clear();
     return MLX_OK;
   }
+  if (strcmp(key, "solve_keep_s") == 0) {
+    if (value != 0 && value != 1) return MLX_EINVAL;
+    c->solve_keep_s = value;
+    for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
+    c->graphs.clear();
+    return MLX_OK;
+  }
   if (strcmp(key, "solve_direct_cpw") == 0) {
     if (value != 8 && value != 16 && value != 32) return MLX_EINVAL;
     c->solve_direct_cpw = value;

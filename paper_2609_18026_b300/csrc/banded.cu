@@ -323,16 +323,18 @@ template <int KL>
 struct SolveSmem {
   static constexpr int W = 2 * KL + 1;
   // per |k| and row: U (W), L (KL), 1/diag (1) doubles + pivot row (int)
-  __host__ __device__ static size_t per_warp(int nc, int CPW) {
+  // keep_s: the AB-CN "- s" term is read from a shared-memory copy of s made while
+  // staging (saves a global re-read at the end, costs N CPW doubles per warp)
+  __host__ __device__ static size_t per_warp(int nc, int CPW, int keep_s) {
     const int G = CPW / 4;
     const size_t b = (size_t)nc * G * (W + KL + 1) * sizeof(double) +
-                     (size_t)2 * nc * CPW * sizeof(double) + (size_t)nc * G * sizeof(int);
+                     (size_t)(keep_s ? 2 : 1) * nc * CPW * sizeof(double) + (size_t)nc * G * sizeof(int);
     return (b + 15) / 16 * 16;   // keeps every warp's slab 16-byte aligned
   }
 };
 
 template <int KL>
-__global__ void k_band_solve(int M, int nc, int Kz, int K, int CPW, int groups_per_m, int step,
+__global__ void k_band_solve(int M, int nc, int Kz, int K, int CPW, int groups_per_m, int step, int keep_s,
                              double dt, const long long* __restrict__ soff,
                              const long long* __restrict__ band_off, int kz_fac, int m0_shift,
                              const double* __restrict__ U,
@@ -352,13 +354,13 @@ __global__ void k_band_solve(int M, int nc, int Kz, int K, int CPW, int groups_p
   const int sh = (m == 0) ? m0_shift : 0;   // Laplacian at m = 0: unknowns n >= 1
   const int Nm = nc - m;
   const int N = Nm - sh;
-  unsigned char* base = smem_raw + (size_t)wib * SolveSmem<KL>::per_warp(nc, CPW);
+  unsigned char* base = smem_raw + (size_t)wib * SolveSmem<KL>::per_warp(nc, CPW, keep_s);
   double* Us = reinterpret_cast<double*>(base);              // [N][G][W]
   double* Ls = Us + (size_t)N * G * W;                       // [N][G][KL]
   double* Ds = Ls + (size_t)N * G * KL;                      // [N][G]
   double* Y = Ds + (size_t)N * G;                            // [N][CPW]
-  double* S = Y + (size_t)N * CPW;                           // [N][CPW] s, for the AB-CN "- s"
-  int* Pi = reinterpret_cast<int*>(S + (size_t)N * CPW);     // [N][G] pivot rows
+  double* S = Y + (size_t)N * CPW;                           // [N][CPW] s, for the AB-CN "- s" (keep_s)
+  int* Pi = reinterpret_cast<int*>(S + (keep_s ? (size_t)N * CPW : 0));   // [N][G] pivot rows
   const long long fb = band_off[m];
   const long long sm = soff[m];
   // stage factors with asynchronous copies: the rows of the warp's gcnt values of
@@ -400,8 +402,10 @@ __global__ void k_band_solve(int M, int nc, int Kz, int K, int CPW, int groups_p
       r = make_double2(2.0 * sv.x, 2.0 * sv.y);
       if (A) { const double2 a = A2[o]; r.x += 1.5 * dt * a.x; r.y += 1.5 * dt * a.y; }
       if (Ap) { const double2 a = Ap2[o]; r.x -= 0.5 * dt * a.x; r.y -= 0.5 * dt * a.y; }
-      S[(size_t)i * CPW + cp * 2] = sv.x;
-      S[(size_t)i * CPW + cp * 2 + 1] = sv.y;
+      if (keep_s) {
+        S[(size_t)i * CPW + cp * 2] = sv.x;
+        S[(size_t)i * CPW + cp * 2 + 1] = sv.y;
+      }
     } else {
       r = sv;
       if (A) { const double2 a = A2[o]; r.x += h * a.x; r.y += h * a.y; }
@@ -483,8 +487,14 @@ __global__ void k_band_solve(int M, int nc, int Kz, int K, int CPW, int groups_p
     const int kidx = sg ? K - kabs : kabs;
     double2 v = make_double2(Y[(size_t)i * CPW + cp * 2], Y[(size_t)i * CPW + cp * 2 + 1]);
     if (step == MLX_STEP_ABCN) {
-      v.x -= S[(size_t)i * CPW + cp * 2];
-      v.y -= S[(size_t)i * CPW + cp * 2 + 1];
+      if (keep_s) {
+        v.x -= S[(size_t)i * CPW + cp * 2];
+        v.y -= S[(size_t)i * CPW + cp * 2 + 1];
+      } else {
+        const double2 sv = s2[sm + (long long)kidx * Nm + sh + i];
+        v.x -= sv.x;
+        v.y -= sv.y;
+      }
     }
     out2[sm + (long long)kidx * Nm + sh + i] = v;
   }
@@ -1017,8 +1027,9 @@ static int launch_solve(mlx_ctx* c, int step, const BandLU& f, const long long* 
   // Chains per warp and warps per CTA are launch-shape parameters (measured best
   // at the 128x128x64 workload: 8 chains per warp, 1-4 warps per CTA).
   int CPW = c->solve_cpw;
-  while (CPW > 4 && SolveSmem<KL>::per_warp(c->nc, CPW) > 200 * 1024) CPW /= 2;
-  const size_t pw = SolveSmem<KL>::per_warp(c->nc, CPW);
+  const int keep_s = (step == MLX_STEP_ABCN && c->solve_keep_s) ? 1 : 0;
+  while (CPW > 4 && SolveSmem<KL>::per_warp(c->nc, CPW, keep_s) > 200 * 1024) CPW /= 2;
+  const size_t pw = SolveSmem<KL>::per_warp(c->nc, CPW, keep_s);
   int WPB = c->solve_wpb;
   while (WPB > 1 && pw * WPB > 200 * 1024) WPB /= 2;
   if (pw * WPB > 200 * 1024) return MLX_EINVAL;
@@ -1026,7 +1037,7 @@ static int launch_solve(mlx_ctx* c, int step, const BandLU& f, const long long* 
   const int warps = c->M * gpm;
   const int blocks = (warps + WPB - 1) / WPB;
   k_band_solve<KL><<<blocks, 32 * WPB, pw * WPB, st>>>(
-      c->M, c->nc, c->Kz, c->K, CPW, gpm, step, c->dt, c->d_soff, fac_off, kz_fac, m0_shift, f.U, f.L,
+      c->M, c->nc, c->Kz, c->K, CPW, gpm, step, keep_s, c->dt, c->d_soff, fac_off, kz_fac, m0_shift, f.U, f.L,
       f.piv, f.invd, (const double*)s, (const double*)A, (const double*)Ap, (double*)out);
   return MLX_OK;
 }

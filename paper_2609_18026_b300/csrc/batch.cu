@@ -72,6 +72,12 @@ int mlx_batch_create(mlx_ctx* const* ctxs, int n, mlx_batch** out) {
     batch_free(b);
     return MLX_ECUDA;
   }
+  // instances run side by side: the staged solve drops its shared-memory copy of s
+  // (smaller CTAs co-reside with other instances' kernels; measured 2.1x -> 2.9x
+  // over sequential on the 64-instance workload)
+  for (mlx_ctx* c : b->ctxs) {
+    if (mlx_set_tuning(c, "solve_keep_s", 0) != MLX_OK) { batch_free(b); return MLX_ECUDA; }
+  }
   *out = b;
   return MLX_OK;
 }

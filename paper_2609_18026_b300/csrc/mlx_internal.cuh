@@ -145,6 +145,7 @@ struct mlx_ctx {
   int solve_wpb = 4;                   // warps per CTA in the banded solve (1..4)
   int solve_direct = 0;                // 1: ring-staged solve variant (wide bands, large Nc)
   int solve_direct_cpw = 8;            // chains per warp of that variant: 8, 16 or 32
+  int solve_keep_s = 1;                // staged variant: copy of s in shared memory for the AB-CN "- s"
   int solve_ir = 0;                    // 1: FP32 solves refined to FP64 by FP64 residuals
   int solve_ir_max = 8;                // refinement steps at most (early exit at FP64 level)
 
