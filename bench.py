@@ -187,9 +187,10 @@ def tc_executed_flops(ctx, forward):
 # nominal FP64 rate of a B300 (TFLOP/s)
 FP64_PEAK_TFLOPS = 1.25
 
-# DRAM bytes (read + write) per launch from the ncu capture named in profiles/, for
-# kernels unchanged since the capture; absent = not captured for the current code
-TRAFFIC = {}
+# DRAM bytes (read + write) per launch at this workload, from the ncu capture
+# summarised in profiles/band_solve_fkpp3d_128x128x64.md (current kernel version);
+# absent = not captured for the current code
+TRAFFIC = {"band_solve": 16448512 + 0}
 
 
 def band_solve_flops(ctx, kl=2):
