@@ -310,6 +310,10 @@ int mlx_sur_create(int D, int width, int bmax, unsigned long long seed, mlx_sur*
 int mlx_sur_destroy(mlx_sur* sur);
 /* Number of FP32 parameters (w D + 2 w^2 + D w + 3 w + D), -1 for NULL. */
 long long mlx_sur_param_count(const mlx_sur* sur);
+/* Device status of the surrogate's tensor-core kernels: MLX_ETIMEOUT (and the word
+ * is cleared) if a bounded wait expired since the last call, else MLX_OK.
+ * Synchronises the device. */
+int mlx_sur_status(mlx_sur* sur);
 /* Host copies of the FP32 parameters and of the gradient of the last training
  * step (both in the parameter layout); set_params also refreshes the BF16 copies.
  * These synchronise the device. */

@@ -29,7 +29,7 @@ EXPORTS = ("mlx_strerror", "mlx_last_cuda_error", "mlx_create", "mlx_destroy", "
            "mlx_sur_create", "mlx_sur_destroy", "mlx_sur_param_count", "mlx_sur_get_params",
            "mlx_sur_set_params", "mlx_sur_get_grads", "mlx_sur_get_scales", "mlx_sur_set_scales",
            "mlx_sur_propagate", "mlx_sur_observe", "mlx_sur_finalize_scales", "mlx_sur_make_pair",
-           "mlx_sur_infer", "mlx_sur_train_step", "mlx_sur_advance")
+           "mlx_sur_infer", "mlx_sur_train_step", "mlx_sur_advance", "mlx_sur_status")
 
 
 class MlxError(RuntimeError):
@@ -97,6 +97,7 @@ def load():
     f = ctypes.c_float
     lib.mlx_sur_create.argtypes = [i, i, i, ctypes.c_ulonglong, ctypes.POINTER(vp)]
     lib.mlx_sur_destroy.argtypes = [vp]
+    lib.mlx_sur_status.argtypes = [vp]
     lib.mlx_sur_param_count.argtypes = [vp]
     lib.mlx_sur_param_count.restype = ctypes.c_longlong
     for name in ("mlx_sur_get_params", "mlx_sur_set_params", "mlx_sur_get_grads"):
@@ -333,6 +334,10 @@ class Surrogate:
             self.close()
         except Exception:
             pass
+
+    def status(self):
+        """Raise MlxError(MLX_ETIMEOUT) if a tensor-core kernel gave up a bounded wait."""
+        self._check(self.lib.mlx_sur_status(self._h))
 
     def offsets(self):
         """Offsets of W1, b1, W2, b2, W3, b3, W4, b4 in the flat parameter array."""

@@ -212,5 +212,9 @@ int mlx_legendre_tc_forward(mlx_ctx* c, double2* spec, cudaStream_t st);
 int mlx_legendre_tc_backward(mlx_ctx* c, const double2* spec, cudaStream_t st);
 int mlx_band_solve(mlx_ctx* c, int step, const double2* s, const double2* A,
                    const double2* Ap, double2* out, cudaStream_t st);
+// Dense BF16 GEMM on the tensor cores (gemm_tc.cu): C (+)= A * B^T, A with P in {1, 3}
+// BF16 parts [P][Ma][Kp], B [Nb][Kp], both K-major; see the file for the contract.
+int mlx_gemm_tc(int P, const void* A, long long Ma, const void* B, long long Nb, long long Kp, int M, int N, int K,
+                float* C, int split, int* err, cudaStream_t st, const float* bias = nullptr);
 int mlx_spec_axpby(mlx_ctx* c, double a, const double2* x, double b, const double2* y,
                    double2* out, cudaStream_t st, long long n = -1);

@@ -9,7 +9,10 @@
 // the real view of the coefficients (D = 4 n_spec reals):
 //   f(x) = W4 h3 + b4,  h_l = GELU(W_l h_{l-1} + b_l),  h_0 = x   (l = 1..3)
 // with BF16 weights and BF16 activations as GEMM operands, FP32 accumulation,
-// FP32 master weights and Adam moments.  The solver is the judge: with judging on,
+// FP32 master weights and Adam moments.  The GEMMs with a dimension D (layer 1
+// and layer 4, forward and backward) run on the tensor cores (gemm_tc.cu), FP32
+// gradient operands as three BF16 parts; the 64 x 64 layers use the tiled GEMM
+// below.  The solver is the judge: with judging on,
 // the same nsub steps run through the plain method (Richardson start, then
 // AB-CN) and a prediction whose relative residual exceeds the tolerance is
 // replaced by the solver's state.
@@ -24,6 +27,17 @@
 
 struct mlx_sur {
   int D = 0, w = 0, bmax = 0;
+  long long Dp = 0;              // D rounded up to 64: row stride of the BF16 copies of x and W1
+  __nv_bfloat16* W1p = nullptr;  // W1 in BF16 with row stride Dp (zero padding), the tensor-core operand
+  // tensor-core operands of the backward pass (Bp = bmax rounded up to 64)
+  long long Bp = 0;
+  __nv_bfloat16* W4T = nullptr;  // W4 transposed, [w][Dp]
+  __nv_bfloat16* dy3 = nullptr;  // dy split into three BF16 parts, [3][bmax][Dp]
+  __nv_bfloat16* dyT3 = nullptr; // dy transposed and split, [3][D][Bp] (Dp rows allocated)
+  __nv_bfloat16* xT = nullptr;   // x transposed, [Dp][Bp]
+  __nv_bfloat16* a3T = nullptr;  // a3 transposed, [w][Bp]
+  __nv_bfloat16* d1T3 = nullptr; // d1 transposed and split, [3][w][Bp]
+  int* err = nullptr;            // device status word (bounded waits of the tensor-core GEMM)
   long long nparam = 0;
   long long oW1, ob1, oW2, ob2, oW3, ob3, oW4, ob4;
   float* master = nullptr;       // FP32 parameters
@@ -32,12 +46,12 @@ struct mlx_sur {
   float* m2 = nullptr;
   __nv_bfloat16* wbf = nullptr;  // BF16 copies of the parameters (same offsets)
   float *z1 = nullptr, *z2 = nullptr, *z3 = nullptr, *y = nullptr;   // pre-activations, output
-  __nv_bfloat16 *x = nullptr, *a1 = nullptr, *a2 = nullptr, *a3 = nullptr;
+  __nv_bfloat16 *x = nullptr, *a1 = nullptr, *a2 = nullptr, *a3 = nullptr;   // x: [bmax][Dp]
   float *d1 = nullptr, *d2 = nullptr, *d3 = nullptr, *dy = nullptr;  // gradients w.r.t. z_l, y
-  float* tg = nullptr;           // gathered targets [bmax][D]
   float* in_scale = nullptr;     // sigma_in [D]
   float* out_scale = nullptr;    // sigma_out [D]
   float* loss = nullptr;         // device scalar
+  float* lpart = nullptr;        // per-CTA partial sums of the loss [MSE_CTAS]
   double* red = nullptr;         // device reductions [4]
   // scale statistics
   double* acc_s = nullptr;       // sum of s_i^2 over observed inputs [D]
@@ -147,19 +161,35 @@ __global__ void k_bias_act(int B, int N, float* __restrict__ z, const float* __r
 
 // Weighted squared error with w_i = sigma_out_i^2 / mean(sigma_out^2), the
 // coefficient-space squared error of the correction sigma_out * y relative to the
-// mean output scale:  loss += sum w (y - t)^2 / n,  dy = 2 w (y - t) / n.
-__global__ void k_mse(long long n, int D, const float* __restrict__ y, const float* __restrict__ tgt,
-                      const float* __restrict__ sout, float inv_wref, float* __restrict__ dy,
-                      float* __restrict__ loss) {
+// mean output scale:  loss = sum w (y - t)^2 / n,  dy = 2 w (y - t) / n, n = B D.
+// Targets are read through the sample index (row idx[b] of T [.][D]); dy is also
+// written as three BF16 parts (row stride Dp, part stride Rd Dp), the tensor-core
+// operand of the backward pass.  Grid-stride; one partial sum per CTA in part[].
+__global__ void __launch_bounds__(256) k_mse(int B, long long D, long long Dp, long long Rd,
+                                             const int* __restrict__ idx, const float* __restrict__ y,
+                                             const float* __restrict__ T, const float* __restrict__ sout,
+                                             float inv_wref, float* __restrict__ dy,
+                                             __nv_bfloat16* __restrict__ dy3, float* __restrict__ part) {
   __shared__ float red[256];
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long n = (long long)B * D;
+  const float invn = 1.f / (float)n;
   float e = 0.f;
-  if (i < n) {
-    const float so = sout[i % D];
-    const float w = so * so * inv_wref;
-    const float d = y[i] - tgt[i];
-    dy[i] = 2.f * w * d / (float)n;
-    e = w * d * d / (float)n;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const int b = (int)(i / D);
+    const long long k = i - (long long)b * D;
+    const float so = sout[k];
+    const float wgt = so * so * inv_wref;
+    const float d = y[i] - T[(long long)idx[b] * D + k];
+    const float g = 2.f * wgt * d * invn;
+    dy[i] = g;
+    const float h = __bfloat162float(__float2bfloat16_rn(g));
+    const float r1 = g - h;
+    const float mid = __bfloat162float(__float2bfloat16_rn(r1));
+    const long long o = (long long)b * Dp + k;
+    dy3[o] = __float2bfloat16_rn(g);
+    dy3[Rd * Dp + o] = __float2bfloat16_rn(r1);
+    dy3[2 * Rd * Dp + o] = __float2bfloat16_rn(r1 - mid);
+    e += wgt * d * d * invn;
   }
   red[threadIdx.x] = e;
   __syncthreads();
@@ -167,8 +197,24 @@ __global__ void k_mse(long long n, int D, const float* __restrict__ y, const flo
     if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
     __syncthreads();
   }
-  if (threadIdx.x == 0) atomicAdd(loss, red[0]);
+  if (threadIdx.x == 0) part[blockIdx.x] = red[0];
 }
+
+// *loss = sum of the per-CTA partials (one CTA)
+__global__ void k_sum_parts(int n, const float* __restrict__ part, float* __restrict__ loss) {
+  __shared__ float red[256];
+  float e = 0.f;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) e += part[i];
+  red[threadIdx.x] = e;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *loss = red[0];
+}
+
+constexpr int MSE_CTAS = 1184;   // 8 per SM
 
 __global__ void k_gelu_bwd(long long n, const float* __restrict__ z, float* __restrict__ d) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -184,9 +230,12 @@ __global__ void k_bias_grad(int B, int N, const float* __restrict__ d, float* __
   db[j] = s;
 }
 
+// W1 occupies the first nw1 = w D parameters; its BF16 value also goes to the
+// padded copy W1p (row stride Dp)
 __global__ void k_adam(long long n, float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m1,
                        float* __restrict__ m2, __nv_bfloat16* __restrict__ pb, float lr, float b1, float b2,
-                       float eps, float c1, float c2) {
+                       float eps, float c1, float c2, long long nw1, long long D, long long Dp,
+                       __nv_bfloat16* __restrict__ W1p) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const float gi = g[i];
@@ -196,7 +245,9 @@ __global__ void k_adam(long long n, float* __restrict__ p, const float* __restri
   m2[i] = b;
   const float v = p[i] - lr * (a / c1) / (sqrtf(b / c2) + eps);
   p[i] = v;
-  pb[i] = __float2bfloat16_rn(v);
+  const __nv_bfloat16 vb = __float2bfloat16_rn(v);
+  pb[i] = vb;
+  if (i < nw1) W1p[(i / D) * Dp + (i % D)] = vb;
 }
 
 __global__ void k_to_bf16(long long n, const float* __restrict__ p, __nv_bfloat16* __restrict__ pb) {
@@ -216,16 +267,82 @@ __global__ void k_init(long long n, float* __restrict__ p, unsigned long long se
   p[i] = (float)((2.0 * u - 1.0) * a);
 }
 
-// rows idx[b] of X [n][D] (BF16) and T [n][D] (FP32, optional) into x, tg
-__global__ void k_gather(long long D, int B, const int* __restrict__ idx, const __nv_bfloat16* __restrict__ X,
-                         const float* __restrict__ T, __nv_bfloat16* __restrict__ x, float* __restrict__ tg) {
+// rows idx[b] of X [n][D] (BF16) into x [B][Dp]
+__global__ void k_gather(long long D, long long Dp, int B, const int* __restrict__ idx,
+                         const __nv_bfloat16* __restrict__ X, __nv_bfloat16* __restrict__ x) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= (long long)B * D) return;
   const int b = (int)(i / D);
   const long long k = i - (long long)b * D;
-  const long long src = (long long)idx[b] * D + k;
-  x[i] = X[src];
-  if (T) tg[i] = T[src];
+  x[(long long)b * Dp + k] = X[(long long)idx[b] * D + k];
+}
+
+
+// three-part BF16 split x = hi + mid + lo of an FP32 value
+__device__ __forceinline__ void split3f(float x, __nv_bfloat16& h, __nv_bfloat16& m, __nv_bfloat16& l) {
+  h = __float2bfloat16_rn(x);
+  const float r1 = x - __bfloat162float(h);
+  m = __float2bfloat16_rn(r1);
+  l = __float2bfloat16_rn(r1 - __bfloat162float(m));
+}
+
+// Transpose through 32 x 32 shared tiles: dst[c][r] (row stride Rp) from src[r][c]
+// (row stride lds), r < Rp (rows r >= R written as zero), c < C.  With split the
+// FP32 source is written as three BF16 parts (part stride C * Rp), else the BF16
+// source is copied.
+template <bool SPLIT, typename TS>
+__global__ void k_transpose(int R, int Rp, long long C, long long lds, const TS* __restrict__ src,
+                            __nv_bfloat16* __restrict__ dst) {
+  __shared__ float tile[32][33];
+  const long long c0 = (long long)blockIdx.x * 32;
+  const int r0 = blockIdx.y * 32;
+  const int tx = threadIdx.x, ty = threadIdx.y;   // 32 x 8
+  for (int j = ty; j < 32; j += 8) {
+    const int r = r0 + j;
+    const long long c = c0 + tx;
+    float v = 0.f;
+    if (r < R && c < C) {
+      if constexpr (SPLIT) v = (float)src[(long long)r * lds + c];
+      else v = __bfloat162float(src[(long long)r * lds + c]);
+    }
+    tile[j][tx] = v;
+  }
+  __syncthreads();
+  for (int j = ty; j < 32; j += 8) {
+    const long long c = c0 + j;
+    const int r = r0 + tx;
+    if (c < C && r < Rp) {
+      const float v = tile[tx][j];
+      const long long o = c * Rp + r;
+      if constexpr (SPLIT) {
+        __nv_bfloat16 h, m, l;
+        split3f(v, h, m, l);
+        dst[o] = h;
+        dst[C * Rp + o] = m;
+        dst[2 * C * Rp + o] = l;
+      } else {
+        dst[o] = __float2bfloat16_rn(v);
+      }
+    }
+  }
+}
+
+// W4 [D][w] (BF16) into its transpose W4T [w][Dp]
+__global__ void k_pack_w4t(int w, long long D, long long Dp, const __nv_bfloat16* __restrict__ W4,
+                           __nv_bfloat16* __restrict__ W4T) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (long long)w * D) return;
+  const long long d = i / w, o = i - d * w;
+  W4T[o * Dp + d] = W4[i];
+}
+
+// W1 rows (BF16, stride D) into the padded copy (stride Dp)
+__global__ void k_pack_w1(int w, long long D, long long Dp, const __nv_bfloat16* __restrict__ W1,
+                          __nv_bfloat16* __restrict__ W1p) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (long long)w * D) return;
+  const long long o = i / D, k = i - o * D;
+  W1p[o * Dp + k] = W1[i];
 }
 
 // r[0] += sum (a - b)^2, r[1] += sum b^2
@@ -518,8 +635,9 @@ void sur_free(mlx_sur* s) {
   if (!s) return;
   void* ps[] = {s->master, s->grad, s->m1,   s->m2,   s->wbf,   s->z1,       s->z2,        s->z3,
                 s->y,      s->x,    s->a1,   s->a2,   s->a3,    s->d1,       s->d2,        s->d3,
-                s->dy,     s->tg,   s->loss, s->red,  s->acc_s, s->in_scale, s->out_scale, s->prop,
-                s->pred,   s->tmp,  s->Ascr, s->acc_r, s->Et, s->d_eoff, s->part, s->h3};
+                s->dy,     s->lpart, s->loss, s->red,  s->acc_s, s->in_scale, s->out_scale, s->prop,
+                s->pred,   s->tmp,  s->Ascr, s->acc_r, s->Et, s->d_eoff, s->part, s->h3, s->W1p, s->err,
+                s->W4T,    s->dy3,  s->dyT3, s->xT,    s->a3T, s->d1T3};
   for (void* p : ps)
     if (p) cudaFree(p);
   delete s;
@@ -532,31 +650,56 @@ int sur_forward(mlx_sur* s, int B, cudaStream_t st) {
   const float* P = s->master;
   using bf = __nv_bfloat16;
   int rc;
-  if ((rc = gemm<bf, bf>(B, w, D, s->x, D, 1, W + s->oW1, 1, D, s->z1, st))) return rc;
+  // layer 1 (K = D): tensor cores, K split over about one CTA per SM, partial sums added into z1
+  if (cudaMemsetAsync(s->z1, 0, sizeof(float) * (size_t)B * w, st) != cudaSuccess) return MLX_ECUDA;
+  if ((rc = mlx_gemm_tc(1, s->x, s->bmax, s->W1p, w, s->Dp, B, w, D, s->z1, 148, s->err, st))) return rc;
   k_bias_act<<<nb((long long)B * w), 256, 0, st>>>(B, w, s->z1, P + s->ob1, s->a1);
   if ((rc = gemm<bf, bf>(B, w, w, s->a1, w, 1, W + s->oW2, 1, w, s->z2, st))) return rc;
   k_bias_act<<<nb((long long)B * w), 256, 0, st>>>(B, w, s->z2, P + s->ob2, s->a2);
   if ((rc = gemm<bf, bf>(B, w, w, s->a2, w, 1, W + s->oW3, 1, w, s->z3, st))) return rc;
   k_bias_act<<<nb((long long)B * w), 256, 0, st>>>(B, w, s->z3, P + s->ob3, s->a3);
-  if ((rc = gemm<bf, bf>(B, D, w, s->a3, w, 1, W + s->oW4, 1, w, s->y, st))) return rc;
-  k_bias_act<<<nb((long long)B * D), 256, 0, st>>>(B, D, s->y, P + s->ob4, nullptr);
+  // layer 4 (N = D, K = w): tensor cores, one 128 x 256 tile per CTA
+  if (w % 8 == 0 && (s->oW4 % 8) == 0) {
+    // bias b4 added in the epilogue
+    if ((rc = mlx_gemm_tc(1, s->a3, s->bmax, W + s->oW4, D, w, B, D, w, s->y, 1, s->err, st, P + s->ob4))) return rc;
+  } else {
+    if ((rc = gemm<bf, bf>(B, D, w, s->a3, w, 1, W + s->oW4, 1, w, s->y, st))) return rc;
+    k_bias_act<<<nb((long long)B * D), 256, 0, st>>>(B, D, s->y, P + s->ob4, nullptr);
+  }
   return cudaGetLastError() == cudaSuccess ? MLX_OK : MLX_ECUDA;
 }
 
-// gradients of the mean squared error against s->tg, into s->grad
-int sur_backward(mlx_sur* s, int B, cudaStream_t st) {
+// gradients of the mean squared error against the rows idx of T, into s->grad
+int sur_backward(mlx_sur* s, int B, const int* idx, const float* T, cudaStream_t st) {
   const int D = s->D, w = s->w;
   const __nv_bfloat16* W = s->wbf;
   float* g = s->grad;
   using bf = __nv_bfloat16;
   int rc;
-  if (cudaMemsetAsync(s->loss, 0, sizeof(float), st) != cudaSuccess) return MLX_ECUDA;
-  k_mse<<<nb((long long)B * D), 256, 0, st>>>((long long)B * D, D, s->y, s->tg, s->out_scale, s->inv_wref, s->dy,
-                                              s->loss);
-  // layer 4: dW4 = dy^T a3, db4 = sum_b dy, d3 = (dy W4) * GELU'(z3)
-  if ((rc = gemm<float, bf>(D, w, B, s->dy, 1, D, s->a3, w, 1, g + s->oW4, st))) return rc;
+  {
+    const long long nblk = ((long long)B * D + 255) / 256;
+    const int ctas = (int)(nblk < MSE_CTAS ? nblk : MSE_CTAS);
+    k_mse<<<ctas, 256, 0, st>>>(B, D, s->Dp, s->bmax, idx, s->y, T, s->out_scale, s->inv_wref, s->dy, s->dy3,
+                                s->lpart);
+    k_sum_parts<<<1, 256, 0, st>>>(ctas, s->lpart, s->loss);
+  }
+  // layer 4: dW4 = dy^T a3, db4 = sum_b dy, d3 = (dy W4) * GELU'(z3).  On the tensor
+  // cores the FP32 operand dy enters as three BF16 parts (hi + mid + lo), so the
+  // products are exact and the sums FP32, as in the FP32-operand form.
+  const int tpb = (int)s->Bp;
+  {
+    const dim3 tb(32, 8);
+    k_transpose<true, float><<<dim3((unsigned)((D + 31) / 32), (unsigned)((tpb + 31) / 32)), tb, 0, st>>>(
+        B, tpb, D, D, s->dy, s->dyT3);
+    k_transpose<false, __nv_bfloat16><<<dim3((unsigned)((w + 31) / 32), (unsigned)((tpb + 31) / 32)), tb, 0, st>>>(
+        B, tpb, w, w, s->a3, s->a3T);
+  }
+  // dW4 [D][w] = dyT (3 parts, [D][Bp], part stride D Bp) x a3T ([w][Bp])^T, K = Bp
+  if ((rc = mlx_gemm_tc(3, s->dyT3, D, s->a3T, w, s->Bp, D, w, tpb, g + s->oW4, 1, s->err, st))) return rc;
   k_bias_grad<<<nb(D), 256, 0, st>>>(B, D, s->dy, g + s->ob4);
-  if ((rc = gemm<float, bf>(B, w, D, s->dy, D, 1, W + s->oW4, w, 1, s->d3, st))) return rc;
+  // d3 [B][w] = dy (3 parts, [bmax][Dp]) x W4T ([w][Dp])^T, K = D split over the SMs
+  if (cudaMemsetAsync(s->d3, 0, sizeof(float) * (size_t)B * w, st) != cudaSuccess) return MLX_ECUDA;
+  if ((rc = mlx_gemm_tc(3, s->dy3, s->bmax, s->W4T, w, s->Dp, B, w, D, s->d3, 148, s->err, st))) return rc;
   k_gelu_bwd<<<nb((long long)B * w), 256, 0, st>>>((long long)B * w, s->z3, s->d3);
   // layer 3
   if ((rc = gemm<float, bf>(w, w, B, s->d3, 1, w, s->a2, w, 1, g + s->oW3, st))) return rc;
@@ -568,8 +711,15 @@ int sur_backward(mlx_sur* s, int B, cudaStream_t st) {
   k_bias_grad<<<nb(w), 256, 0, st>>>(B, w, s->d2, g + s->ob2);
   if ((rc = gemm<float, bf>(B, w, w, s->d2, w, 1, W + s->oW2, w, 1, s->d1, st))) return rc;
   k_gelu_bwd<<<nb((long long)B * w), 256, 0, st>>>((long long)B * w, s->z1, s->d1);
-  // layer 1: dW1 = d1^T x
-  if ((rc = gemm<float, bf>(w, D, B, s->d1, 1, w, s->x, D, 1, g + s->oW1, st))) return rc;
+  // layer 1: dW1 [w][D] = d1T (3 parts, [w][Bp]) x xT ([Dp][Bp])^T, K = Bp
+  {
+    const dim3 tb(32, 8);
+    k_transpose<true, float><<<dim3((unsigned)((w + 31) / 32), (unsigned)((tpb + 31) / 32)), tb, 0, st>>>(
+        B, tpb, w, w, s->d1, s->d1T3);
+    k_transpose<false, __nv_bfloat16><<<dim3((unsigned)((s->Dp + 31) / 32), (unsigned)((tpb + 31) / 32)), tb, 0,
+                                        st>>>(B, tpb, s->Dp, s->Dp, s->x, s->xT);
+  }
+  if ((rc = mlx_gemm_tc(3, s->d1T3, w, s->xT, s->Dp, s->Bp, w, D, tpb, g + s->oW1, 1, s->err, st))) return rc;
   k_bias_grad<<<nb(w), 256, 0, st>>>(B, w, s->d1, g + s->ob1);
   return cudaGetLastError() == cudaSuccess ? MLX_OK : MLX_ECUDA;
 }
@@ -688,6 +838,7 @@ int mlx_sur_create(int D, int width, int bmax, unsigned long long seed, mlx_sur*
   if (D < 1 || width < 1 || width > 1024 || bmax < 1 || bmax > 4096) return MLX_EINVAL;
   mlx_sur* s = new mlx_sur();
   s->D = D; s->w = width; s->bmax = bmax;
+  s->Dp = ((long long)D + 63) / 64 * 64;
   const long long w = width, Dl = D, bm = bmax;
   long long o = 0;
   s->oW1 = o; o += w * Dl;
@@ -710,7 +861,16 @@ int mlx_sur_create(int D, int width, int bmax, unsigned long long seed, mlx_sur*
   A((void**)&s->z2, sizeof(float) * bm * w);
   A((void**)&s->z3, sizeof(float) * bm * w);
   A((void**)&s->y, sizeof(float) * bm * Dl);
-  A((void**)&s->x, sizeof(__nv_bfloat16) * bm * Dl);
+  A((void**)&s->x, sizeof(__nv_bfloat16) * bm * s->Dp);
+  A((void**)&s->W1p, sizeof(__nv_bfloat16) * w * s->Dp);
+  A((void**)&s->err, sizeof(int));
+  s->Bp = (bm + 63) / 64 * 64;
+  A((void**)&s->W4T, sizeof(__nv_bfloat16) * w * s->Dp);
+  A((void**)&s->dy3, sizeof(__nv_bfloat16) * 3 * bm * s->Dp);
+  A((void**)&s->dyT3, sizeof(__nv_bfloat16) * 3 * s->Dp * s->Bp);
+  A((void**)&s->xT, sizeof(__nv_bfloat16) * s->Dp * s->Bp);
+  A((void**)&s->a3T, sizeof(__nv_bfloat16) * w * s->Bp);
+  A((void**)&s->d1T3, sizeof(__nv_bfloat16) * 3 * w * s->Bp);
   A((void**)&s->a1, sizeof(__nv_bfloat16) * bm * w);
   A((void**)&s->a2, sizeof(__nv_bfloat16) * bm * w);
   A((void**)&s->a3, sizeof(__nv_bfloat16) * bm * w);
@@ -718,7 +878,7 @@ int mlx_sur_create(int D, int width, int bmax, unsigned long long seed, mlx_sur*
   A((void**)&s->d2, sizeof(float) * bm * w);
   A((void**)&s->d3, sizeof(float) * bm * w);
   A((void**)&s->dy, sizeof(float) * bm * Dl);
-  A((void**)&s->tg, sizeof(float) * bm * Dl);
+  A((void**)&s->lpart, sizeof(float) * MSE_CTAS);
   A((void**)&s->in_scale, sizeof(float) * Dl);
   A((void**)&s->out_scale, sizeof(float) * Dl);
   A((void**)&s->loss, sizeof(float));
@@ -739,9 +899,16 @@ int mlx_sur_create(int D, int width, int bmax, unsigned long long seed, mlx_sur*
            cudaMemset(s->m1, 0, sizeof(float) * o) == cudaSuccess &&
            cudaMemset(s->m2, 0, sizeof(float) * o) == cudaSuccess &&
            cudaMemset(s->acc_s, 0, sizeof(double) * Dl) == cudaSuccess &&
+           cudaMemset(s->x, 0, sizeof(__nv_bfloat16) * bm * s->Dp) == cudaSuccess &&
+           cudaMemset(s->W1p, 0, sizeof(__nv_bfloat16) * w * s->Dp) == cudaSuccess &&
+           cudaMemset(s->W4T, 0, sizeof(__nv_bfloat16) * w * s->Dp) == cudaSuccess &&
+           cudaMemset(s->dy3, 0, sizeof(__nv_bfloat16) * 3 * bm * s->Dp) == cudaSuccess &&
+           cudaMemset(s->err, 0, sizeof(int)) == cudaSuccess &&
            cudaMemset(s->acc_r, 0, sizeof(double) * Dl) == cudaSuccess &&
            cudaMemset(s->red, 0, sizeof(double) * 4) == cudaSuccess;
   k_to_bf16<<<nb(o), 256>>>(o, s->master, s->wbf);
+  k_pack_w1<<<nb(w * Dl), 256>>>(width, Dl, s->Dp, s->wbf + s->oW1, s->W1p);
+  k_pack_w4t<<<nb(w * Dl), 256>>>(width, Dl, s->Dp, s->wbf + s->oW4, s->W4T);
   // unit scales until fitted
   std::vector<float> one(D, 1.f);
   z = z && cudaMemcpy(s->in_scale, one.data(), sizeof(float) * Dl, cudaMemcpyHostToDevice) == cudaSuccess &&
@@ -760,6 +927,17 @@ int mlx_sur_destroy(mlx_sur* s) {
 
 long long mlx_sur_param_count(const mlx_sur* s) { return s ? s->nparam : -1; }
 
+int mlx_sur_status(mlx_sur* s) {
+  if (!s) return MLX_EINVAL;
+  int v = 0;
+  if (cudaMemcpy(&v, s->err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return MLX_ECUDA;
+  if (v) {
+    if (cudaMemset(s->err, 0, sizeof(int)) != cudaSuccess) return MLX_ECUDA;
+    return MLX_ETIMEOUT;
+  }
+  return MLX_OK;
+}
+
 int mlx_sur_get_params(const mlx_sur* s, float* host) {
   if (!s || !host) return MLX_EINVAL;
   return cudaMemcpy(host, s->master, sizeof(float) * s->nparam, cudaMemcpyDeviceToHost) == cudaSuccess
@@ -771,6 +949,8 @@ int mlx_sur_set_params(mlx_sur* s, const float* host) {
   if (cudaMemcpy(s->master, host, sizeof(float) * s->nparam, cudaMemcpyHostToDevice) != cudaSuccess)
     return MLX_ECUDA;
   k_to_bf16<<<nb(s->nparam), 256>>>(s->nparam, s->master, s->wbf);
+  k_pack_w1<<<nb((long long)s->w * s->D), 256>>>(s->w, s->D, s->Dp, s->wbf + s->oW1, s->W1p);
+  k_pack_w4t<<<nb((long long)s->w * s->D), 256>>>(s->w, s->D, s->Dp, s->wbf + s->oW4, s->W4T);
   return cudaDeviceSynchronize() == cudaSuccess ? MLX_OK : MLX_ECUDA;
 }
 
@@ -860,7 +1040,7 @@ int mlx_sur_make_pair(mlx_ctx* c, mlx_sur* s, const void* s0, const void* s1, in
 int mlx_sur_infer(mlx_sur* s, const void* X, const int* idx, int B, float* y, mlx_stream stream) {
   if (!s || !X || !idx || !y || B < 1 || B > s->bmax) return MLX_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
-  k_gather<<<nb((long long)B * s->D), 256, 0, st>>>(s->D, B, idx, (const __nv_bfloat16*)X, nullptr, s->x, nullptr);
+  k_gather<<<nb((long long)B * s->D), 256, 0, st>>>(s->D, s->Dp, B, idx, (const __nv_bfloat16*)X, s->x);
   int rc = sur_forward(s, B, st);
   if (rc) return rc;
   return cudaMemcpyAsync(y, s->y, sizeof(float) * B * (size_t)s->D, cudaMemcpyDeviceToDevice, st) == cudaSuccess
@@ -871,17 +1051,21 @@ int mlx_sur_train_step(mlx_sur* s, const void* X, const float* T, const int* idx
                        mlx_stream stream) {
   if (!s || !X || !T || !idx || B < 1 || B > s->bmax || !(lr >= 0.f)) return MLX_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
-  k_gather<<<nb((long long)B * s->D), 256, 0, st>>>(s->D, B, idx, (const __nv_bfloat16*)X, T, s->x, s->tg);
+  k_gather<<<nb((long long)B * s->D), 256, 0, st>>>(s->D, s->Dp, B, idx, (const __nv_bfloat16*)X, s->x);
   int rc = sur_forward(s, B, st);
   if (rc) return rc;
-  if ((rc = sur_backward(s, B, st))) return rc;
+  if ((rc = sur_backward(s, B, idx, T, st))) return rc;
   if (loss && cudaMemcpyAsync(loss, s->loss, sizeof(float), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
     return MLX_ECUDA;
   if (lr > 0.f) {
     s->t += 1;
     const float c1 = 1.f - powf(0.9f, (float)s->t), c2 = 1.f - powf(0.999f, (float)s->t);
     k_adam<<<nb(s->nparam), 256, 0, st>>>(s->nparam, s->master, s->grad, s->m1, s->m2, s->wbf, lr, 0.9f, 0.999f,
-                                          1e-8f, c1, c2);
+                                          1e-8f, c1, c2, (long long)s->w * s->D, s->D, s->Dp, s->W1p);
+    // the transposed BF16 copy of W4 (tensor-core operand of the backward), by tiles
+    k_transpose<false, __nv_bfloat16><<<dim3((unsigned)((s->w + 31) / 32), (unsigned)((s->Dp + 31) / 32)),
+                                        dim3(32, 8), 0, st>>>(s->D, (int)s->Dp, s->w, s->w, s->wbf + s->oW4,
+                                                              s->W4T);
   }
   return cudaGetLastError() == cudaSuccess ? MLX_OK : MLX_ECUDA;
 }
