@@ -217,9 +217,18 @@ int mlx_advance(mlx_ctx* ctx, int kind, const double* coeffs, int ncoeffs,
  *   "solve_direct": 1 = banded-solve variant that keeps only the solution
  *                columns in shared memory for the whole solve and streams the
  *                factor rows through small per-warp rings (cp.async, 8 rows ahead);
- *                default 1 for hyperviscous bands (half width >= 4, set by
- *                mlx_implicit_setup), else 0.
- *   "solve_direct_cpw": real chains per warp of that variant, 8, 16 or 32
+ *                2 = lean variant: 32 (or 16, "solve_lean_cpw") chains per warp,
+ *                the factors read as per-row records packed at setup (one
+ *                contiguous 16-byte-aligned block per row and |k|, cp.async 12 rows
+ *                ahead), the eliminated values in a global scratch of about
+ *                M * Kz * 4 * Nc doubles (allocated when 2 is first set;
+ *                MLX_ENOMEM if that fails);
+ *                default 2 for hyperviscous bands (half width >= 4, set by
+ *                mlx_implicit_setup), else 0.  Every variant other than
+ *                "solve_ir" gives bitwise-equal results.
+ *   "solve_lean_cpw": real chains per warp of the lean variant, 16 or 32
+ *                (default 32).
+ *   "solve_direct_cpw": real chains per warp of the ring-staged variant, 8, 16 or 32
  *                (default 8: fewer lanes per warp, more warps per SM to hide the
  *                FP64 latency).
  *   "solve_ir":  1 = the implicit step (I - c L) x = b by mixed-precision
@@ -272,7 +281,8 @@ int mlx_batch_advance(mlx_batch* batch, const int* kinds, const double* coeffs, 
  * CTA.  Results are cached in the text file cache_path (may be NULL), one line
  * "sizes precision kind band|bn cpw wpb"; a cached entry is applied without
  * timing.  chosen (may be NULL) receives {bn, cpw, wpb, from_cache}; cpw = wpb = 0
- * denotes the direct-read solve variant, cpw = 1 (wpb = 0) the mixed-precision
+ * denotes the ring-staged solve variant ("solve_direct" 1), cpw = 2 (wpb = 0) the
+ * lean variant ("solve_direct" 2), cpw = 1 (wpb = 0) the mixed-precision
  * refinement variant ("solve_ir").  The
  * context's temporaries are overwritten; call it before advancing.
  * Synchronises `stream`. */

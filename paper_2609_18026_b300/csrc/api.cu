@@ -30,7 +30,10 @@ void free_ctx(mlx_ctx* c) {
                   c->lu_helm.U, c->lu_helm.L, c->lu_helm.piv, c->lu_helm.invd, c->d_lap_off,
                   c->d_rdr, c->d_jac, c->d_vspec, c->d_vphys,
                   c->lu_Q.U, c->lu_Q.L, c->lu_Q.piv, c->lu_Q.invd, c->lu_H.U, c->lu_H.L, c->lu_H.piv,
-                  c->lu_H.invd, c->lu_G.U, c->lu_G.L, c->lu_G.piv, c->lu_G.invd};
+                  c->lu_H.invd, c->lu_G.U, c->lu_G.L, c->lu_G.piv, c->lu_G.invd, c->d_solve_y,
+                  c->lu_half.FS, c->lu_half.BS, c->lu_full.FS, c->lu_full.BS, c->lu_lap.FS, c->lu_lap.BS,
+                  c->lu_helm.FS, c->lu_helm.BS, c->lu_Q.FS, c->lu_Q.BS, c->lu_H.FS, c->lu_H.BS,
+                  c->lu_G.FS, c->lu_G.BS};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
@@ -277,7 +280,13 @@ int mlx_implicit_setup(mlx_ctx* c, double nu, double nu_h, int p, double dt, mlx
   c->graphs.clear();
   c->nu = nu; c->nu_h = nu_h; c->p = p; c->dt = dt;
   c->kl = (nu_h > 0.0) ? p : 2;
-  c->solve_direct = (c->kl >= 4) ? 1 : 0;   // wide hyperviscous bands: direct-read solve
+  // wide hyperviscous bands: the lean solve (32 chains per warp, packed records)
+  c->solve_direct = 0;
+  if (c->kl >= 4) {
+    const int rc = mlx_solve_scratch(c);
+    if (rc) return rc;
+    c->solve_direct = 2;
+  }
   // the refinement variant is opt-in: at the sizes measured it is slower than the
   // staged FP64 recurrence (one warp of chains per SM leaves its latencies exposed)
   c->solve_ir = 0;
@@ -410,8 +419,19 @@ int mlx_set_tuning(mlx_ctx* c, const char* key, int value) {
     c->graphs.clear();
     return MLX_OK;
   }
+  if (strcmp(key, "solve_lean_cpw") == 0) {
+    if (value != 16 && value != 32) return MLX_EINVAL;
+    c->solve_lean_cpw = value;
+    for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
+    c->graphs.clear();
+    return MLX_OK;
+  }
   if (strcmp(key, "solve_direct") == 0) {
-    if (value != 0 && value != 1) return MLX_EINVAL;
+    if (value < 0 || value > 2) return MLX_EINVAL;
+    if (value == 2) {
+      const int rc = mlx_solve_scratch(c);
+      if (rc) return rc;
+    }
     c->solve_direct = value;
     for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
     c->graphs.clear();

@@ -33,7 +33,26 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
   const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
 }
+__device__ __forceinline__ void cp_async16_s(unsigned sa, const void* gmem) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async8_s(unsigned sa, const void* gmem) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+
+// Right-hand sides of the implicit steps in one explicit rounding order, so that
+// every solve variant forms bit-identical values: AB-CN 2 s + (3/2) dt A -
+// (1/2) dt A_prev, FE-BE s + h A.
+__device__ __forceinline__ double rhs_abcn(double sv, double a, double ap, bool hasA, bool hasAp, double dt) {
+  double r = 2.0 * sv;
+  if (hasA) r = __fma_rn(1.5 * dt, a, r);
+  if (hasAp) r = __fma_rn(-0.5 * dt, ap, r);
+  return r;
+}
+__device__ __forceinline__ double rhs_febe(double sv, double a, bool hasA, double h) {
+  return hasA ? __fma_rn(h, a, sv) : sv;
+}
 
 // Copy nrows rows of row_bytes bytes (a multiple of 4) from global memory (row stride
 // src_stride bytes) to shared memory (row stride dst_stride bytes) with cp.async,
@@ -399,16 +418,16 @@ __global__ void k_band_solve(int M, int nc, int Kz, int K, int CPW, int groups_p
     if (step == MLX_STEP_PLAIN) {
       r = sv;
     } else if (step == MLX_STEP_ABCN) {
-      r = make_double2(2.0 * sv.x, 2.0 * sv.y);
-      if (A) { const double2 a = A2[o]; r.x += 1.5 * dt * a.x; r.y += 1.5 * dt * a.y; }
-      if (Ap) { const double2 a = Ap2[o]; r.x -= 0.5 * dt * a.x; r.y -= 0.5 * dt * a.y; }
+      const double2 a = A ? A2[o] : make_double2(0.0, 0.0);
+      const double2 ap = Ap ? Ap2[o] : make_double2(0.0, 0.0);
+      r = make_double2(rhs_abcn(sv.x, a.x, ap.x, A, Ap, dt), rhs_abcn(sv.y, a.y, ap.y, A, Ap, dt));
       if (keep_s) {
         S[(size_t)i * CPW + cp * 2] = sv.x;
         S[(size_t)i * CPW + cp * 2 + 1] = sv.y;
       }
     } else {
       r = sv;
-      if (A) { const double2 a = A2[o]; r.x += h * a.x; r.y += h * a.y; }
+      if (A) { const double2 a = A2[o]; r = make_double2(rhs_febe(sv.x, a.x, true, h), rhs_febe(sv.y, a.y, true, h)); }
     }
     Y[(size_t)i * CPW + cp * 2] = r.x;
     Y[(size_t)i * CPW + cp * 2 + 1] = r.y;
@@ -645,14 +664,8 @@ __global__ void __launch_bounds__(32) k_band_solve_ir(int M, int nc, int Kz, int
     const int kidx = sgn ? K - kabs : kabs;
     const long long o = 2 * (sm + (long long)kidx * N + i) + part;
     double r;
-    if (step == MLX_STEP_ABCN) {
-      r = 2.0 * s[o];
-      if (A) r += 1.5 * dt * A[o];
-      if (Ap) r -= 0.5 * dt * Ap[o];
-    } else {
-      r = s[o];
-      if (A) r += h * A[o];
-    }
+    if (step == MLX_STEP_ABCN) r = rhs_abcn(s[o], A ? A[o] : 0.0, Ap ? Ap[o] : 0.0, A, Ap, dt);
+    else r = rhs_febe(s[o], A ? A[o] : 0.0, A, h);
     Bv[(size_t)i * 32 + c] = r;
   }
   cp_async_wait_all();
@@ -742,7 +755,9 @@ int mlx_band_setup(mlx_ctx* c, cudaStream_t st) {
   cudaFree(c->d_Bplus);
   cudaFree(c->lu_half.U); cudaFree(c->lu_half.L); cudaFree(c->lu_half.piv); cudaFree(c->lu_half.invd);
   cudaFree(c->lu_full.U); cudaFree(c->lu_full.L); cudaFree(c->lu_full.piv); cudaFree(c->lu_full.invd);
-  for (BandLU* f : {&c->lu_half, &c->lu_full}) { cudaFree(f->U32); cudaFree(f->L32); cudaFree(f->invd32); }
+  for (BandLU* f : {&c->lu_half, &c->lu_full}) {
+    cudaFree(f->U32); cudaFree(f->L32); cudaFree(f->invd32); cudaFree(f->FS); cudaFree(f->BS);
+  }
   c->d_Bplus = nullptr;
   c->lu_half = BandLU();
   c->lu_full = BandLU();
@@ -778,6 +793,8 @@ int mlx_band_setup(mlx_ctx* c, cudaStream_t st) {
     k_to_f32<<<(unsigned)((rows * W + 255) / 256), 256, 0, st>>>(rows * W, f->U, f->U32);
     k_to_f32<<<(unsigned)((rows * kl + 255) / 256), 256, 0, st>>>(rows * kl, f->L, f->L32);
     k_to_f32<<<(unsigned)((rows + 255) / 256), 256, 0, st>>>(rows, f->invd, f->invd32);
+    const int rc = mlx_pack_lean(c, *f, kl, c->d_band_off, c->Kz, rows, st);
+    if (rc) return rc;
   }
   MLX_LAUNCH_CHECK(c);
   MLX_CUDA_TRY(c, cudaStreamSynchronize(st));
@@ -886,12 +903,12 @@ __global__ void k_band_solve_direct(int M, int nc, int Kz, int K, int groups_per
     if (step == MLX_STEP_PLAIN) {
       r = sv;
     } else if (step == MLX_STEP_ABCN) {
-      r = make_double2(2.0 * sv.x, 2.0 * sv.y);
-      if (A) { const double2 q = A2[o]; r.x += 1.5 * dt * q.x; r.y += 1.5 * dt * q.y; }
-      if (Ap) { const double2 q = Ap2[o]; r.x -= 0.5 * dt * q.x; r.y -= 0.5 * dt * q.y; }
+      const double2 q = A ? A2[o] : make_double2(0.0, 0.0);
+      const double2 qp = Ap ? Ap2[o] : make_double2(0.0, 0.0);
+      r = make_double2(rhs_abcn(sv.x, q.x, qp.x, A, Ap, dt), rhs_abcn(sv.y, q.y, qp.y, A, Ap, dt));
     } else {
       r = sv;
-      if (A) { const double2 q = A2[o]; r.x += h * q.x; r.y += h * q.y; }
+      if (A) { const double2 q = A2[o]; r = make_double2(rhs_febe(sv.x, q.x, true, h), rhs_febe(sv.y, q.y, true, h)); }
     }
     Y[(size_t)i * CPW + cp * 2] = r.x;
     Y[(size_t)i * CPW + cp * 2 + 1] = r.y;
@@ -999,10 +1016,340 @@ __global__ void k_band_solve_direct(int M, int nc, int Kz, int K, int groups_per
   }
 }
 
+// Lean variant: 32 (or 16) real chains per warp, every lane busy in every FP64
+// instruction, and few other instructions per row.  On this part an FP64 warp
+// instruction occupies the pipe as long with 8 active lanes as with 32, and a
+// warp running a recurrence issues one instruction every few cycles, so both the
+// lanes per FP64 instruction and the instructions per row decide the time:
+//  * the factors are read as per-row records written once by k_pack_lean:
+//    forward FS[row] = {L[row][0..KL-1], pivot offset mask (int), pad}, back
+//    substitution BS[row] = {U[row - t][t + 1] for t < 2KL, 1/diag[row - 2KL],
+//    pad}: the U column the pipelined back substitution touches at that step.  A
+//    step stages one contiguous 16-byte-aligned block per |k| with cp.async,
+//    LEAN_AHEAD rows ahead of use;
+//  * per-lane global addresses are formed once and offset per row, ring slots
+//    advance by a running index, the step kind is a template parameter;
+//  * the shared-memory operands of the next row are loaded into registers while
+//    the current row computes.
+// The forward-elimination values go to a per-warp global scratch [row][CPW] (one
+// coalesced row per step, read back through the ring, mostly from L2); the
+// solution is written straight to the output.  Arithmetic, and its order, is
+// that of k_band_solve: the results are bitwise equal.
+constexpr int LEAN_AHEAD = 12;
+constexpr int LEAN_PLAIN = 0, LEAN_FEBE = 1, LEAN_ABCN = 2;   // right-hand side s, s + h A, AB-CN
+
+template <int KL, int CPW>
+struct LeanSmem {
+  static constexpr int G = CPW / 4;                   // |k| values per warp
+  static constexpr int NP = CPW / 2;                  // complex pieces per row
+  static constexpr int P = LEAN_AHEAD;
+  static constexpr int FW = (KL + 2) & ~1;            // forward record (doubles)
+  static constexpr int BW = 2 * KL + 2;               // back-substitution record (doubles)
+  static constexpr int R = P + 1;                     // ring slots
+  static constexpr size_t f_rhs = (size_t)G * FW * sizeof(double);
+  static constexpr size_t fslot = f_rhs + 3 * NP * sizeof(double2);   // + s, A, A_prev pieces
+  static constexpr size_t b_y = (size_t)G * BW * sizeof(double);
+  static constexpr size_t b_s = b_y + CPW * sizeof(double);
+  static constexpr size_t bslot = b_s + NP * sizeof(double2);
+  static constexpr size_t per_warp = (R * (fslot > bslot ? fslot : bslot) + 15) / 16 * 16;
+};
+
+template <int KL, int CPW, int MODE>
+__global__ void __launch_bounds__(64, 1) k_band_solve_lean(
+    int M, int nc, int Kz, int K, int groups_per_m, double h, double dt, int hasA, int hasAp,
+    const long long* __restrict__ soff, const long long* __restrict__ band_off, int kz_fac, int m0_shift,
+    const double* __restrict__ FS, const double* __restrict__ BS, const double* __restrict__ invd,
+    const double* __restrict__ s, const double* __restrict__ A, const double* __restrict__ Ap,
+    double* __restrict__ out, double* __restrict__ scratch) {
+  using SM = LeanSmem<KL, CPW>;
+  constexpr int G = SM::G, NP = SM::NP, P = SM::P, FW = SM::FW, BW = SM::BW, RS = SM::R;
+  constexpr int NF = (G * FW / 2 + 31) / 32, NB = (G * BW / 2 + 31) / 32;   // 16-byte chunks per lane, at most
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int gw = blockIdx.x * (blockDim.x >> 5) + wib;
+  if (gw >= M * groups_per_m) return;
+  const int m = gw / groups_per_m;
+  const int k0 = (gw % groups_per_m) * G;
+  const int gcnt = min(G, Kz - k0);
+  const int sh = (m == 0) ? m0_shift : 0;
+  const int Nm = nc - m;
+  const int N = Nm - sh;
+  unsigned char* ring = smem_raw + (size_t)wib * SM::per_warp;
+  const unsigned ring_s = (unsigned)__cvta_generic_to_shared(ring);
+  double* Yg = scratch + (size_t)gw * nc * CPW;       // [row][CPW], this warp's columns
+  const long long sm = soff[m];
+  const int GS = (kz_fac == 1) ? 1 : gcnt;            // factor records per row
+  const long long row0 = band_off[m] + (kz_fac == 1 ? 0 : k0);
+  const double2* s2 = reinterpret_cast<const double2*>(s);
+  // offset (complex units) of complex piece cp = kq * 2 + sg at row 0, or -1
+  auto piece = [=](int cp) -> long long {
+    const int kq = cp >> 1, sg = cp & 1, kabs = k0 + kq;
+    if (kq >= gcnt || (sg && kabs == 0)) return -1;
+    const int kidx = sg ? K - kabs : kabs;
+    return sm + (long long)kidx * Nm + sh;
+  };
+  // ---- this lane's copies ----
+  const int nf = GS * FW / 2, nb = GS * BW / 2;
+  const double2* fsrc = reinterpret_cast<const double2*>(FS + row0 * FW) + lane;   // chunk `lane` of row 0
+  const double2* bsrc = reinterpret_cast<const double2*>(BS + row0 * BW) + lane;
+  const long long fstep = (long long)kz_fac * FW / 2, bstep = (long long)kz_fac * BW / 2;   // per row (double2)
+  const double2* rsrc0 = nullptr;                     // right-hand-side pieces e = lane, lane + 32 of [3][NP]
+  const double2* rsrc1 = nullptr;
+  if (MODE != LEAN_PLAIN) {
+    auto src_of = [=](int e) -> const double2* {
+      if (e >= 3 * NP) return nullptr;
+      const int a = e / NP;
+      const long long o = piece(e % NP);
+      const bool use = a == 0 || (a == 1 && hasA) || (a == 2 && MODE == LEAN_ABCN && hasAp);
+      if (o < 0 || !use) return nullptr;
+      return reinterpret_cast<const double2*>(a == 0 ? s : (a == 1 ? A : Ap)) + o;
+    };
+    rsrc0 = src_of(lane);
+    rsrc1 = src_of(lane + 32);
+  } else if (lane < NP) {
+    const long long o = piece(lane);
+    if (o >= 0) rsrc0 = s2 + o;
+  }
+  const long long so = (lane < NP) ? piece(lane) : -1;
+  const double2* ssrc = (MODE == LEAN_ABCN && so >= 0) ? s2 + so : nullptr;   // s for the AB-CN "- s"
+  const int c = lane;
+  const int kk = c >> 2, part = c & 1, cpx = c >> 1;
+  const bool act = c < CPW && kk < gcnt;
+  const bool valid = act && !(((c >> 1) & 1) && k0 + kk == 0);
+  const int ks = (kz_fac == 1) ? 0 : (kk < gcnt ? kk : 0);   // lane's record within a row block
+  const int cpl = (c < CPW) ? cpx : 0;                       // lane's piece (in range for idle lanes)
+  auto rhs = [=](double sv, double q, double qp) -> double {
+    if (MODE == LEAN_PLAIN) return sv;
+    if (MODE == LEAN_ABCN) return rhs_abcn(sv, q, qp, hasA, hasAp, dt);
+    return rhs_febe(sv, q, true, h);
+  };
+  const long long my0 = (c < CPW) ? piece(cpx) : -1;          // this lane's chain at row 0
+  // ---- forward elimination; slot of row r: its records and the pieces of row r + KL ----
+  auto stage_f = [=](int r, int slot) {
+    const unsigned d = ring_s + (unsigned)(slot * SM::fslot);
+    const double2* src = fsrc + r * fstep;
+#pragma unroll
+    for (int u = 0; u < NF; ++u)
+      if (lane + 32 * u < nf) cp_async16_s(d + (lane + 32 * u) * 16, src + 32 * u);
+    if (r + KL < N) {
+      if (rsrc0) cp_async16_s(d + (unsigned)SM::f_rhs + lane * 16, rsrc0 + r + KL);
+      if (rsrc1) cp_async16_s(d + (unsigned)SM::f_rhs + (lane + 32) * 16, rsrc1 + r + KL);
+    }
+  };
+  struct FOps { double l[KL]; int d; double sv, q, qp; };   // d: pivot offset mask
+  auto load_f = [=](int slot) -> FOps {
+    FOps o;
+    const unsigned char* sl = ring + (size_t)slot * SM::fslot;
+    const double* rec = reinterpret_cast<const double*>(sl) + ks * FW;
+#pragma unroll
+    for (int q = 0; q + 1 < KL; q += 2) {
+      const double2 v = *reinterpret_cast<const double2*>(rec + q);
+      o.l[q] = v.x; o.l[q + 1] = v.y;
+    }
+    if (KL & 1) {
+      const double2 v = *reinterpret_cast<const double2*>(rec + KL - 1);
+      o.l[KL - 1] = v.x;
+      o.d = __double2loint(v.y);
+    } else {
+      o.d = reinterpret_cast<const int*>(rec + KL)[0];
+    }
+    const double* rv = reinterpret_cast<const double*>(sl + SM::f_rhs);
+    o.sv = rv[cpl * 2 + part];
+    o.q = (MODE != LEAN_PLAIN) ? rv[(NP + cpl) * 2 + part] : 0.0;
+    o.qp = (MODE == LEAN_ABCN) ? rv[(2 * NP + cpl) * 2 + part] : 0.0;
+    return o;
+  };
+  for (int r = 0; r < P; ++r) {
+    if (r < N) stage_f(r, r);
+    cp_async_commit();
+  }
+  double w[KL + 1];
+#pragma unroll
+  for (int q = 0; q < KL; ++q) {
+    double v = 0.0;
+    if (act && my0 >= 0 && q < N) {
+      const long long o = 2 * (my0 + q) + part;
+      v = rhs(s[o], MODE != LEAN_PLAIN && hasA ? A[o] : 0.0, MODE == LEAN_ABCN && hasAp ? Ap[o] : 0.0);
+    }
+    w[q + 1] = v;
+  }
+  cp_async_wait_group<P - 1>();
+  __syncwarp();
+  FOps cur = load_f(0);
+  double* yw = Yg + c;
+  int swr = P, srd = 1;                                // slots: next row staged, next row loaded
+#pragma unroll 2
+  for (int j = 0; j < N; ++j) {
+    if (j + P < N) stage_f(j + P, swr);
+    cp_async_commit();
+    cp_async_wait_group<P - 1>();
+    __syncwarp();
+    const FOps nxt = load_f(srd);                                  // (a stale slot after the last row: unused)
+    swr = (swr == RS - 1) ? 0 : swr + 1;
+    srd = (srd == RS - 1) ? 0 : srd + 1;
+    if (act) {
+      const double nv = (j + KL < N) ? rhs(cur.sv, cur.q, cur.qp) : 0.0;
+#pragma unroll
+      for (int q = 0; q < KL; ++q) w[q] = w[q + 1];
+      w[KL] = nv;
+      {   // row interchange with the pivot row (bit q of cur.d: offset q), as selects
+        const double w0 = w[0];
+        double pv = w0;
+#pragma unroll
+        for (int q = 1; q <= KL; ++q) {
+          const bool sel = (cur.d >> q) & 1;
+          pv = sel ? w[q] : pv;
+          w[q] = sel ? w0 : w[q];
+        }
+        w[0] = pv;
+      }
+      yw[(size_t)j * CPW] = w[0];
+#pragma unroll
+      for (int q = 1; q <= KL; ++q) w[q] -= cur.l[q - 1] * w[0];
+    }
+    cur = nxt;
+  }
+  cp_async_wait_all();
+  __threadfence_block();
+  __syncwarp();
+  // ---- back substitution (software-pipelined: acc[t] is the partial sum of row i - t);
+  // slot of step i: back record of row i, y_{i - 2KL}, s_i ----
+  auto stage_b = [=](int i, int slot) {
+    const unsigned d = ring_s + (unsigned)(slot * SM::bslot);
+    const double2* src = bsrc + i * bstep;
+#pragma unroll
+    for (int u = 0; u < NB; ++u)
+      if (lane + 32 * u < nb) cp_async16_s(d + (lane + 32 * u) * 16, src + 32 * u);
+    if (lane < CPW && i - 2 * KL >= 0)
+      cp_async8_s(d + (unsigned)SM::b_y + lane * 8, Yg + (size_t)(i - 2 * KL) * CPW + lane);
+    if (MODE == LEAN_ABCN && ssrc) cp_async16_s(d + (unsigned)SM::b_s + lane * 16, ssrc + i);
+  };
+  struct BOps { double u[2 * KL]; double dinv, y, sv; };
+  auto load_b = [=](int slot) -> BOps {
+    BOps o;
+    const unsigned char* sl = ring + (size_t)slot * SM::bslot;
+    const double* rec = reinterpret_cast<const double*>(sl) + ks * BW;
+#pragma unroll
+    for (int t = 0; t < 2 * KL; t += 2) {
+      const double2 v = *reinterpret_cast<const double2*>(rec + t);
+      o.u[t] = v.x; o.u[t + 1] = v.y;
+    }
+    o.dinv = rec[2 * KL];
+    o.y = reinterpret_cast<const double*>(sl + SM::b_y)[c < CPW ? c : 0];
+    o.sv = (MODE == LEAN_ABCN) ? reinterpret_cast<const double*>(sl + SM::b_s)[cpl * 2 + part] : 0.0;
+    return o;
+  };
+  // steps N-1 .. N-P into slots 0 .. P-1
+  for (int t = 0; t < P; ++t) {
+    if (N - 1 - t >= 0) stage_b(N - 1 - t, t);
+    cp_async_commit();
+  }
+  double acc[2 * KL];
+  const long long drow = row0 + ks;                            // this lane's factor row at r = 0
+#pragma unroll
+  for (int t = 0; t < 2 * KL; ++t) {
+    const int r = N - 1 - t;
+    acc[t] = (act && r >= 0) ? yw[(size_t)r * CPW] * invd[drow + (long long)r * kz_fac] : 0.0;
+  }
+  cp_async_wait_group<P - 1>();
+  __syncwarp();
+  BOps bc = load_b(0);
+  double xn = 0.0;   // x_{i+1}
+  double* outc = out + 2 * (my0 < 0 ? 0 : my0) + part;
+  int bwr = P, brd = 1;
+#pragma unroll 2
+  for (int i = N - 1; i >= 0; --i) {
+    if (i - P >= 0) stage_b(i - P, bwr);
+    cp_async_commit();
+    cp_async_wait_group<P - 1>();
+    __syncwarp();
+    const BOps bn = load_b(brd);                                   // (a stale slot after row 0: unused)
+    bwr = (bwr == RS - 1) ? 0 : bwr + 1;
+    brd = (brd == RS - 1) ? 0 : brd + 1;
+    if (act) {
+      const double xi = acc[0] - bc.u[0] * xn;
+#pragma unroll
+      for (int t = 1; t < 2 * KL; ++t) acc[t] -= bc.u[t] * xn;
+      if (valid) {
+        outc[2 * (long long)i] = (MODE == LEAN_ABCN) ? xi - bc.sv : xi;
+        if (sh) yw[(size_t)i * CPW] = xi;
+      }
+#pragma unroll
+      for (int t = 0; t < 2 * KL - 1; ++t) acc[t] = acc[t + 1];
+      acc[2 * KL - 1] = (i - 2 * KL >= 0) ? bc.y * bc.dinv : 0.0;
+      xn = xi;
+    }
+    bc = bn;
+  }
+  cp_async_wait_all();
+  if (sh && valid) {
+    double dacc = 0.0;
+    for (int i = 0; i < N; ++i) dacc += sqrt((2.0 * (i + 1) + 1.0) * 0.5) * yw[(size_t)i * CPW];
+    out[2 * (my0 - sh) + part] = -dacc / sqrt(0.5);
+  }
+}
+
+// Lean-solve records of one factor family (see k_band_solve_lean): one thread per
+// factor row R = off[m] + r kz_fac + kk.  The pivot is stored as a one-hot mask of
+// its offset q from the row (bit q, q = 1 .. KL; 0 when the row is its own pivot),
+// an int in the low word of the slot after the multipliers.
+__global__ void k_pack_lean(int nc, int kcnt, int kz_fac, int KL, const long long* __restrict__ off,
+                            const double* __restrict__ U, const double* __restrict__ L,
+                            const int* __restrict__ piv, const double* __restrict__ invd,
+                            double* __restrict__ FS, double* __restrict__ BS) {
+  const int m = blockIdx.y;
+  const int Nm = nc - m;
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)Nm * kcnt) return;
+  const int r = (int)(idx / kcnt), kk = (int)(idx % kcnt);
+  const long long R = off[m] + (long long)r * kz_fac + kk;
+  const int W = 2 * KL + 1, FW = (KL + 2) & ~1, BW = 2 * KL + 2;
+  const int po = piv[R] - r;
+  const int mask = (po > 0 && po <= KL) ? (1 << po) : 0;
+  for (int q = 0; q < FW; ++q)
+    FS[R * FW + q] = (q < KL) ? L[R * KL + q] : (q == KL ? __hiloint2double(0, mask) : 0.0);
+  for (int t = 0; t < 2 * KL; ++t)
+    BS[R * BW + t] = (r - t >= 0) ? U[(R - (long long)t * kz_fac) * W + t + 1] : 0.0;
+  BS[R * BW + 2 * KL] = (r >= 2 * KL) ? invd[R - (long long)2 * KL * kz_fac] : 0.0;
+  BS[R * BW + 2 * KL + 1] = 0.0;
+}
+
 template <int KL>
 static int launch_solve(mlx_ctx* c, int step, const BandLU& f, const long long* fac_off, int kz_fac,
                         int m0_shift, const double2* s, const double2* A, const double2* Ap, double2* out,
                         cudaStream_t st) {
+  if (c->solve_direct == 2) {
+    if (!c->d_solve_y || !f.FS || !f.BS) return MLX_ESTATE;
+    const int mode = (step == MLX_STEP_ABCN) ? LEAN_ABCN
+                     : ((step == MLX_STEP_FEBE_HALF || step == MLX_STEP_FEBE_FULL) && A) ? LEAN_FEBE
+                                                                                          : LEAN_PLAIN;
+    const double h = (step == MLX_STEP_FEBE_FULL) ? c->dt : 0.5 * c->dt;
+    auto go = [&](auto cpw_tag, auto mode_tag) -> int {
+      constexpr int CPWL = decltype(cpw_tag)::value, MODE = decltype(mode_tag)::value;
+      const int gpm = (c->Kz + CPWL / 4 - 1) / (CPWL / 4);
+      const int warps = c->M * gpm;
+      const int WPB = (warps <= 2 * 148) ? 1 : 2;   // spread few warps over every SM
+      const size_t smem = (size_t)WPB * LeanSmem<KL, CPWL>::per_warp;
+      k_band_solve_lean<KL, CPWL, MODE><<<(warps + WPB - 1) / WPB, 32 * WPB, smem, st>>>(
+          c->M, c->nc, c->Kz, c->K, gpm, h, c->dt, A != nullptr, Ap != nullptr, c->d_soff, fac_off, kz_fac,
+          m0_shift, f.FS, f.BS, f.invd, (const double*)s, (const double*)A, (const double*)Ap, (double*)out,
+          c->d_solve_y);
+      return MLX_OK;
+    };
+    using I16 = std::integral_constant<int, 16>;
+    using I32 = std::integral_constant<int, 32>;
+    using MP = std::integral_constant<int, LEAN_PLAIN>;
+    using MF = std::integral_constant<int, LEAN_FEBE>;
+    using MA = std::integral_constant<int, LEAN_ABCN>;
+    if (c->solve_lean_cpw == 16) {
+      if (mode == LEAN_ABCN) return go(I16(), MA());
+      if (mode == LEAN_FEBE) return go(I16(), MF());
+      return go(I16(), MP());
+    }
+    if (mode == LEAN_ABCN) return go(I32(), MA());
+    if (mode == LEAN_FEBE) return go(I32(), MF());
+    return go(I32(), MP());
+  }
   if (c->solve_direct) {
     // chains per warp: 32 (every lane busy) or 16 (half the shared memory per
     // warp, so twice the warps per SM hide the FP64 latency)
@@ -1127,6 +1474,9 @@ int mlx_lap_setup(mlx_ctx* c, cudaStream_t st) {
                                                           c->d_lap_off, c->d_lap, c->lu_helm.U, c->lu_helm.L,
                                                           c->lu_helm.piv, c->lu_helm.invd, scratch, stride);
   MLX_LAUNCH_CHECK(c);
+  int rc = mlx_pack_lean(c, c->lu_lap, 2, c->d_lap_off, 1, rows_lap, st);
+  if (!rc) rc = mlx_pack_lean(c, c->lu_helm, 2, c->d_band_off, c->Kz, rows_helm, st);
+  if (rc) { cudaFree(scratch); return rc; }
   MLX_CUDA_TRY(c, cudaStreamSynchronize(st));
   cudaFree(scratch);
   c->lap_ready = true;
@@ -1157,6 +1507,9 @@ int mlx_proj_setup(mlx_ctx* c, cudaStream_t st) {
                                                       f == 2 ? c->d_band_off : c->d_lap_off, fams[f]->U,
                                                       fams[f]->L, fams[f]->piv, fams[f]->invd, scratch, stride);
     MLX_LAUNCH_CHECK(c);
+    const int rc = (f == 2) ? mlx_pack_lean(c, *fams[f], kl, c->d_band_off, c->Kz, c->band_rows, st)
+                            : mlx_pack_lean(c, *fams[f], kl, c->d_lap_off, 1, c->tri, st);
+    if (rc) { cudaFree(scratch); return rc; }
   }
   MLX_CUDA_TRY(c, cudaStreamSynchronize(st));
   cudaFree(scratch);
@@ -1188,6 +1541,44 @@ int mlx_lap_solve(mlx_ctx* c, int family, const double2* rhs, double2* out, cuda
   return MLX_OK;
 }
 
+template <int KL>
+static int set_lean_attrs(mlx_ctx* c, int lim) {
+  const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_band_solve_lean<KL, 16, LEAN_PLAIN>, at, lim));
+  MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_band_solve_lean<KL, 16, LEAN_FEBE>, at, lim));
+  MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_band_solve_lean<KL, 16, LEAN_ABCN>, at, lim));
+  MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_band_solve_lean<KL, 32, LEAN_PLAIN>, at, lim));
+  MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_band_solve_lean<KL, 32, LEAN_FEBE>, at, lim));
+  MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_band_solve_lean<KL, 32, LEAN_ABCN>, at, lim));
+  return MLX_OK;
+}
+
+// Lean-solve records (FS, BS) of a factor family just factorised on stream st.
+int mlx_pack_lean(mlx_ctx* c, BandLU& f, int kl, const long long* d_off, int kz_fac, long long rows,
+                  cudaStream_t st) {
+  const int FW = (kl + 2) & ~1, BW = 2 * kl + 2;
+  cudaFree(f.FS);
+  cudaFree(f.BS);
+  f.FS = f.BS = nullptr;
+  MLX_CUDA_TRY(c, cudaMalloc(&f.FS, sizeof(double) * rows * FW));
+  MLX_CUDA_TRY(c, cudaMalloc(&f.BS, sizeof(double) * rows * BW));
+  const int kcnt = (kz_fac == 1) ? 1 : c->Kz;
+  const dim3 grid((unsigned)(((long long)c->nc * kcnt + 127) / 128), (unsigned)c->M);
+  k_pack_lean<<<grid, 128, 0, st>>>(c->nc, kcnt, kz_fac, kl, d_off, f.U, f.L, f.piv, f.invd, f.FS, f.BS);
+  MLX_LAUNCH_CHECK(c);
+  return MLX_OK;
+}
+
+// Scratch of the lean solve: [warp][Nc][CPW] doubles, one warp per (m, CPW / 4 |k|),
+// sized for either chain count (16 or 32).
+int mlx_solve_scratch(mlx_ctx* c) {
+  if (c->d_solve_y) return MLX_OK;
+  const long long w32 = (long long)((c->Kz + 7) / 8) * 32, w16 = (long long)((c->Kz + 3) / 4) * 16;
+  const long long elems = (long long)c->M * c->nc * (w32 > w16 ? w32 : w16);
+  MLX_CUDA_TRY(c, cudaMalloc(&c->d_solve_y, sizeof(double) * elems));
+  return MLX_OK;
+}
+
 int mlx_band_prepare(mlx_ctx* c) {
   const int lim = 200 * 1024;
   MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_band_solve<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
@@ -1200,6 +1591,14 @@ int mlx_band_prepare(mlx_ctx* c) {
   MLX_DIRECT_ATTR(6, 16); MLX_DIRECT_ATTR(8, 16); MLX_DIRECT_ATTR(2, 8); MLX_DIRECT_ATTR(3, 8);
   MLX_DIRECT_ATTR(4, 8); MLX_DIRECT_ATTR(6, 8); MLX_DIRECT_ATTR(8, 8);
 #undef MLX_DIRECT_ATTR
+  {
+    int rc = set_lean_attrs<2>(c, lim);
+    if (!rc) rc = set_lean_attrs<3>(c, lim);
+    if (!rc) rc = set_lean_attrs<4>(c, lim);
+    if (!rc) rc = set_lean_attrs<6>(c, lim);
+    if (!rc) rc = set_lean_attrs<8>(c, lim);
+    if (rc) return rc;
+  }
   MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_band_solve<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
   MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_band_solve<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
   MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_band_solve<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));

@@ -160,9 +160,10 @@ int mlx_autotune(mlx_ctx* c, int kind, const double* coeffs, int ncoeffs, const 
   if (!c->implicit_ready) return MLX_ESTATE;
   if (kind == MLX_NONLIN_VORTEX && !c->vortex_ready) return MLX_ESTATE;
   const std::string key = tune_key(c, kind);
-  // solve variant encoding: cpw = 1 refinement, cpw = 0 direct-read, else staged (cpw, wpb)
+  // solve variant encoding: cpw = 1 refinement, cpw = 0 ring-staged, cpw = 2 lean,
+  // else staged (cpw, wpb)
   int bn = c->tc_bn;
-  int cpw = c->solve_ir ? 1 : (c->solve_direct ? 0 : c->solve_cpw);
+  int cpw = c->solve_ir ? 1 : (c->solve_direct == 2 ? 2 : (c->solve_direct ? 0 : c->solve_cpw));
   int wpb = (c->solve_ir || c->solve_direct) ? 0 : c->solve_wpb;
   bool found = false;
   if (cache_path) {
@@ -189,6 +190,7 @@ int mlx_autotune(mlx_ctx* c, int kind, const double* coeffs, int ncoeffs, const 
     if (!rc) rc = mlx_set_tuning(c, "solve_ir", cpw_ == 1 ? 1 : 0);
     if (cpw_ == 1) return rc;
     if (cpw_ == 0) return rc ? rc : mlx_set_tuning(c, "solve_direct", 1);
+    if (cpw_ == 2) return rc ? rc : mlx_set_tuning(c, "solve_direct", 2);
     if (!rc) rc = mlx_set_tuning(c, "solve_direct", 0);
     if (!rc) rc = mlx_set_tuning(c, "solve_cpw", cpw_);
     if (!rc) rc = mlx_set_tuning(c, "solve_wpb", wpb_);
@@ -232,9 +234,9 @@ int mlx_autotune(mlx_ctx* c, int kind, const double* coeffs, int ncoeffs, const 
       }
       bn = best_bn;
     }
-    // 2. banded-solve launch shape (cpw = 0 encodes the direct-read variant)
+    // 2. banded-solve variant and launch shape
     if (!rc) {
-      const int shapes[][2] = {{4, 1}, {8, 1}, {8, 4}, {16, 1}, {32, 1}, {0, 0}, {1, 0}};
+      const int shapes[][2] = {{4, 1}, {8, 1}, {8, 4}, {16, 1}, {32, 1}, {0, 0}, {2, 0}, {1, 0}};
       best = 1e30f;
       int bc = cpw, bw = wpb;
       for (auto& sh : shapes) {
@@ -261,7 +263,7 @@ int mlx_autotune(mlx_ctx* c, int kind, const double* coeffs, int ncoeffs, const 
   if (rc) return rc;
   if (chosen) {
     chosen[0] = c->tc_bn;
-    chosen[1] = c->solve_ir ? 1 : (c->solve_direct ? 0 : c->solve_cpw);
+    chosen[1] = c->solve_ir ? 1 : (c->solve_direct == 2 ? 2 : (c->solve_direct ? 0 : c->solve_cpw));
     chosen[2] = (c->solve_ir || c->solve_direct) ? 0 : c->solve_wpb;
     chosen[3] = found;
   }

@@ -59,6 +59,10 @@ struct BandLU {
   float* U32 = nullptr;
   float* L32 = nullptr;
   float* invd32 = nullptr;
+  // per-row records of the lean solve: forward {L row, pivot offset mask, pad}, back
+  // substitution {U[row - t][t + 1] (t < 2 kl), 1/diag[row - 2 kl], pad}
+  double* FS = nullptr;
+  double* BS = nullptr;
 };
 
 struct mlx_ctx {
@@ -143,7 +147,11 @@ struct mlx_ctx {
   double* d_setup_scratch = nullptr;
   int solve_cpw = 8;                   // real chains per warp in the banded solve (4..32)
   int solve_wpb = 4;                   // warps per CTA in the banded solve (1..4)
-  int solve_direct = 0;                // 1: ring-staged solve variant (wide bands, large Nc)
+  int solve_direct = 0;                // 1: ring-staged solve variant (wide bands, large Nc),
+                                       // 2: lean variant (16 or 32 chains per warp, packed
+                                       // factor records, global scratch)
+  int solve_lean_cpw = 32;             // chains per warp of the lean variant: 16 or 32
+  double* d_solve_y = nullptr;         // scratch of the lean variant, [warp][Nc][CPW]
   int solve_direct_cpw = 8;            // chains per warp of that variant: 8, 16 or 32
   int solve_keep_s = 1;                // staged variant: copy of s in shared memory for the AB-CN "- s"
   int solve_ir = 0;                    // 1: FP32 solves refined to FP64 by FP64 residuals
@@ -199,6 +207,9 @@ int mlx_legendre_forward(mlx_ctx* c, double2* spec, cudaStream_t st,
                          const double2* addsrc = nullptr, double alpha = 0.0);
 int mlx_legendre_backward(mlx_ctx* c, const double2* spec, cudaStream_t st); // spec -> d_mixed
 int mlx_band_setup(mlx_ctx* c, cudaStream_t st);
+int mlx_solve_scratch(mlx_ctx* c);                 // scratch of the lean solve variant
+int mlx_pack_lean(mlx_ctx* c, BandLU& f, int kl, const long long* d_off, int kz_fac, long long rows,
+                  cudaStream_t st);                 // lean-solve records of a factor family
 int mlx_lap_setup(mlx_ctx* c, cudaStream_t st);
 int mlx_lap_solve(mlx_ctx* c, int family, const double2* rhs, double2* out, cudaStream_t st);
 int mlx_proj_setup(mlx_ctx* c, cudaStream_t st);

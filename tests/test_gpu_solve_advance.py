@@ -176,18 +176,26 @@ def test_fkpp_fp32_per_step_error_along_trajectory():
 @pytest.mark.parametrize("nu_h,p", [(0.0, 8), (5e-7, 8)])
 @pytest.mark.parametrize("step", [B.STEP_ABCN, B.STEP_FEBE_FULL])
 def test_solve_variants_agree(nu_h, p, step):
-    # the staged (factor rows in shared memory), direct-read and mixed-precision
-    # refinement variants solve the same systems; each is within kappa u of the
+    # the staged (factor rows in shared memory), ring-staged, lean (packed factor
+    # records, full lanes) and mixed-precision refinement variants solve the same
+    # systems; each is within kappa u of the
     # exact solution, and the refined one also matches the oracle
     g, ctx = pair(40, 16, 8, 1.5, lz=3.0, policy="twothirds")
     ctx.implicit_setup(0.3, 2e-2, nu_h=nu_h, p=p)
     s, A, Ap = (to_gpu_spec(rand_spec(g, k)) for k in (1, 2, 3))
     outs = []
-    for ir, direct in ((0, 0), (0, 1), (1, 0)):
+    variants = ((0, 0, 8), (0, 1, 8), (0, 1, 16), (0, 1, 32), (0, 2, 16), (0, 2, 32), (1, 0, 8))
+    for ir, direct, cpw in variants:
         ctx.set_tuning("solve_ir", ir)
         ctx.set_tuning("solve_direct", direct)
+        ctx.set_tuning("solve_lean_cpw" if direct == 2 else "solve_direct_cpw", cpw)
         outs.append(ctx.implicit_solve(step, s, A, Ap, ctx.new_spec()).cpu().numpy())
     ctx.device_status()   # raises MLX_ENUMERIC if a refinement did not converge
+    # the staged, ring-staged and lean variants share one summation order:
+    # bitwise equal
+    for v, o in enumerate(outs[1:6], 1):
+        assert np.array_equal(o, outs[0]), (variants[v], float(np.max(np.abs(o - outs[0]))))
+    outs = [outs[0], outs[1], outs[6]]
     # bar: 1e-12, or 2 kappa u for the ill-conditioned hyperviscous systems
     st = O.Stepper(g, 0.3, 2e-2, nu_h=nu_h, p=p)
     c = 1e-2 if step == B.STEP_ABCN else 2e-2

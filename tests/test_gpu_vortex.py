@@ -34,6 +34,27 @@ def test_lap_h_solve_parity():
     assert O.spec_rel_err(g, spec_from_gpu(g, out), ref) <= 1e-12
 
 
+def test_projection_solve_variants_bitwise():
+    # the vortex term's Q, H (one factor per m, decay row at m = 0) and G (one per
+    # (m, |k|)) solves through the staged, ring-staged and lean kernels: one
+    # summation order, bitwise-equal results
+    g, ctx = pair(40, 16, 32, 1.0, lz=8.6, policy="twothirds")
+    ctx.vortex_setup()
+    psi, chi = _smooth_state(g, 21)
+    state = to_gpu_spec(np.concatenate([psi, chi]))
+    outs = []
+    variants = ((0, 8), (1, 8), (2, 16), (2, 32))
+    for direct, cpw in variants:
+        ctx.set_tuning("solve_direct", direct)
+        if direct == 2:
+            ctx.set_tuning("solve_lean_cpw", cpw)
+        out = ctx.nonlinear(B.NONLIN_VORTEX, [1.0], state, to_gpu_spec(np.zeros(2 * len(psi), np.complex128)))
+        outs.append(out.cpu().numpy())
+    assert np.all(np.isfinite(outs[0]))
+    for v in range(1, len(variants)):
+        assert np.array_equal(outs[v], outs[0]), (variants[v], float(np.max(np.abs(outs[v] - outs[0]))))
+
+
 @pytest.mark.parametrize("prec", [B.FP64, B.FP32, B.BF16X3])
 @pytest.mark.parametrize("grid", [(24, 16, 8, 1.0, 0.0), (33, 32, 16, 1.0, 1.0)])
 def test_vortex_nonlinear_parity(grid, prec):
