@@ -43,9 +43,12 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 
 // Right-hand sides of the implicit steps in one explicit rounding order, so that
 // every solve variant forms bit-identical values: AB-CN 2 s + (3/2) dt A -
-// (1/2) dt A_prev, FE-BE s + h A.
+// (1/2) dt A_prev, FE-BE s + h A.  The recurrences below likewise spell out each
+// fused multiply-add and each product (__fma_rn, __dmul_rn): a product feeding a
+// later subtraction could otherwise be fused either way, and the choice would
+// differ between kernels of different shape.
 __device__ __forceinline__ double rhs_abcn(double sv, double a, double ap, bool hasA, bool hasAp, double dt) {
-  double r = 2.0 * sv;
+  double r = __dmul_rn(2.0, sv);
   if (hasA) r = __fma_rn(1.5 * dt, a, r);
   if (hasAp) r = __fma_rn(-0.5 * dt, ap, r);
   return r;
@@ -57,23 +60,45 @@ __device__ __forceinline__ double rhs_febe(double sv, double a, bool hasA, doubl
 // Copy nrows rows of row_bytes bytes (a multiple of 4) from global memory (row stride
 // src_stride bytes) to shared memory (row stride dst_stride bytes) with cp.async,
 // in 16-byte pieces when every address, stride and length allows, else 8 or 4.
+// Each lane owns one piece position and walks the rows with fixed strides (one
+// division per call, none per piece).
+template <int CH>
+__device__ __forceinline__ void stage_rows_ch(unsigned char* d0, int dst_stride, const unsigned char* s0,
+                                              long long src_stride, int nrows, int per_row, int lane) {
+  if (per_row <= 32) {
+    const int rpp = 32 / per_row;                      // rows per pass of the warp
+    const int r0 = lane / per_row, j = lane - r0 * per_row;
+    if (r0 >= rpp) return;
+    unsigned char* d = d0 + (size_t)r0 * dst_stride + (size_t)j * CH;
+    const unsigned char* g = s0 + (long long)r0 * src_stride + (long long)j * CH;
+    const size_t dstep = (size_t)rpp * dst_stride;
+    const long long gstep = (long long)rpp * src_stride;
+    for (int i = r0; i < nrows; i += rpp, d += dstep, g += gstep) {
+      if (CH == 16) cp_async16(d, g);
+      else if (CH == 8) cp_async8(d, g);
+      else cp_async4(d, g);
+    }
+  } else {
+    for (int e = lane; e < nrows * per_row; e += 32) {
+      const int i = e / per_row, j = e - i * per_row;
+      unsigned char* d = d0 + (size_t)i * dst_stride + (size_t)j * CH;
+      const unsigned char* g = s0 + (long long)i * src_stride + (long long)j * CH;
+      if (CH == 16) cp_async16(d, g);
+      else if (CH == 8) cp_async8(d, g);
+      else cp_async4(d, g);
+    }
+  }
+}
 __device__ __forceinline__ void stage_rows(void* dst, int dst_stride, const void* src, long long src_stride,
                                            int nrows, int row_bytes, int lane) {
   const unsigned long long a = (unsigned long long)(uintptr_t)src | (unsigned long long)src_stride |
                                (unsigned long long)row_bytes | (unsigned long long)dst_stride |
                                (unsigned long long)__cvta_generic_to_shared(dst);
-  const int ch = (a & 15) == 0 ? 16 : ((a & 7) == 0 ? 8 : 4);
-  const int per_row = row_bytes / ch;
   unsigned char* d0 = reinterpret_cast<unsigned char*>(dst);
   const unsigned char* s0 = reinterpret_cast<const unsigned char*>(src);
-  for (int e = lane; e < nrows * per_row; e += 32) {
-    const int i = e / per_row, j = e - i * per_row;
-    unsigned char* d = d0 + (size_t)i * dst_stride + (size_t)j * ch;
-    const unsigned char* g = s0 + (long long)i * src_stride + (long long)j * ch;
-    if (ch == 16) cp_async16(d, g);
-    else if (ch == 8) cp_async8(d, g);
-    else cp_async4(d, g);
-  }
+  if ((a & 15) == 0) stage_rows_ch<16>(d0, dst_stride, s0, src_stride, nrows, row_bytes / 16, lane);
+  else if ((a & 7) == 0) stage_rows_ch<8>(d0, dst_stride, s0, src_stride, nrows, row_bytes / 8, lane);
+  else stage_rows_ch<4>(d0, dst_stride, s0, src_stride, nrows, row_bytes / 4, lane);
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 template <int N>
@@ -405,32 +430,46 @@ __global__ void k_band_solve(int M, int nc, int Kz, int K, int CPW, int groups_p
   const double2* s2 = reinterpret_cast<const double2*>(s);
   const double2* A2 = reinterpret_cast<const double2*>(A);
   const double2* Ap2 = reinterpret_cast<const double2*>(Ap);
-#pragma unroll 4
-  for (int e = lane; e < N * 2 * gcnt; e += 32) {
-    const int cp = e / N, i = e - cp * N;
-    const int kq = cp >> 1, sg = cp & 1;
-    const int kabs = k0 + kq;
-    if (sg && kabs == 0) continue;
-    const int kidx = sg ? K - kabs : kabs;
-    const long long o = sm + (long long)kidx * Nm + sh + i;
-    const double2 sv = s2[o];
-    double2 r;
-    if (step == MLX_STEP_PLAIN) {
-      r = sv;
-    } else if (step == MLX_STEP_ABCN) {
-      const double2 a = A ? A2[o] : make_double2(0.0, 0.0);
-      const double2 ap = Ap ? Ap2[o] : make_double2(0.0, 0.0);
-      r = make_double2(rhs_abcn(sv.x, a.x, ap.x, A, Ap, dt), rhs_abcn(sv.y, a.y, ap.y, A, Ap, dt));
-      if (keep_s) {
-        S[(size_t)i * CPW + cp * 2] = sv.x;
-        S[(size_t)i * CPW + cp * 2 + 1] = sv.y;
-      }
-    } else {
-      r = sv;
-      if (A) { const double2 a = A2[o]; r = make_double2(rhs_febe(sv.x, a.x, true, h), rhs_febe(sv.y, a.y, true, h)); }
+  // lane -> complex piece cp = lane / LP (cp = kq * 2 + sg) and rows lane % LP + LP t
+  const int LP = 16 / G;
+  const int cpl = lane / LP, il = lane - cpl * LP;
+  const int kql = cpl >> 1, sgl = cpl & 1, kabsl = k0 + kql;
+  const bool lane_piece = cpl < 2 * gcnt && !(sgl && kabsl == 0);
+  const long long pbase = sm + (long long)(sgl ? K - kabsl : kabsl) * Nm + sh;
+  // RB rows per lane per batch: their loads are all in flight before any is used
+  constexpr int RB = 8;
+  for (int i = il; i < (lane_piece ? N : 0); i += RB * LP) {
+    double2 sv[RB], av[RB], apv[RB];
+#pragma unroll
+    for (int u = 0; u < RB; ++u) {
+      const int ii = i + u * LP;
+      const bool in = ii < N;
+      const long long o = pbase + (in ? ii : i);
+      sv[u] = s2[o];
+      av[u] = (step != MLX_STEP_PLAIN && A) ? A2[o] : make_double2(0.0, 0.0);
+      apv[u] = (step == MLX_STEP_ABCN && Ap) ? Ap2[o] : make_double2(0.0, 0.0);
     }
-    Y[(size_t)i * CPW + cp * 2] = r.x;
-    Y[(size_t)i * CPW + cp * 2 + 1] = r.y;
+#pragma unroll
+    for (int u = 0; u < RB; ++u) {
+      const int ii = i + u * LP;
+      if (ii >= N) break;
+      double2 r;
+      if (step == MLX_STEP_PLAIN) {
+        r = sv[u];
+      } else if (step == MLX_STEP_ABCN) {
+        r = make_double2(rhs_abcn(sv[u].x, av[u].x, apv[u].x, A, Ap, dt),
+                         rhs_abcn(sv[u].y, av[u].y, apv[u].y, A, Ap, dt));
+        if (keep_s) {
+          S[(size_t)ii * CPW + cpl * 2] = sv[u].x;
+          S[(size_t)ii * CPW + cpl * 2 + 1] = sv[u].y;
+        }
+      } else {
+        r = sv[u];
+        if (A) r = make_double2(rhs_febe(sv[u].x, av[u].x, true, h), rhs_febe(sv[u].y, av[u].y, true, h));
+      }
+      Y[(size_t)ii * CPW + cpl * 2] = r.x;
+      Y[(size_t)ii * CPW + cpl * 2 + 1] = r.y;
+    }
   }
   cp_async_wait_all();
   __syncwarp();
@@ -456,7 +495,7 @@ __global__ void k_band_solve(int M, int nc, int Kz, int K, int CPW, int groups_p
       y[(size_t)j * CPW] = w[0];
       const double* l = Ls + ((size_t)j * G + kk) * KL;
 #pragma unroll
-      for (int q = 1; q <= KL; ++q) w[q] -= l[q - 1] * w[0];
+      for (int q = 1; q <= KL; ++q) w[q] = __fma_rn(-l[q - 1], w[0], w[q]);
     }
     // back substitution x_r = y_r / U_rr - sum_{q=1..2KL} (U_r,r+q / U_rr) x_{r+q},
     // software-pipelined: acc[t] is the partial sum of row i - t, and at step i
@@ -467,20 +506,20 @@ __global__ void k_band_solve(int M, int nc, int Kz, int K, int CPW, int groups_p
 #pragma unroll
     for (int t = 0; t < 2 * KL; ++t) {
       const int r = N - 1 - t;
-      acc[t] = (r >= 0) ? y[(size_t)r * CPW] * Ds[(size_t)r * G + kk] : 0.0;
+      acc[t] = (r >= 0) ? __dmul_rn(y[(size_t)r * CPW], Ds[(size_t)r * G + kk]) : 0.0;
     }
     double xn = 0.0;   // x_{i+1}
 #pragma unroll 2
     for (int i = N - 1; i >= 0; --i) {
-      const double xi = acc[0] - Us[((size_t)i * G + kk) * W + 1] * xn;
+      const double xi = __fma_rn(-Us[((size_t)i * G + kk) * W + 1], xn, acc[0]);
 #pragma unroll
       for (int t = 1; t < 2 * KL; ++t)
-        if (i - t >= 0) acc[t] -= Us[((size_t)(i - t) * G + kk) * W + t + 1] * xn;
+        if (i - t >= 0) acc[t] = __fma_rn(-Us[((size_t)(i - t) * G + kk) * W + t + 1], xn, acc[t]);
       y[(size_t)i * CPW] = xi;
 #pragma unroll
       for (int t = 0; t < 2 * KL - 1; ++t) acc[t] = acc[t + 1];
       const int rn = i - 2 * KL;
-      acc[2 * KL - 1] = (rn >= 0) ? y[(size_t)rn * CPW] * Ds[(size_t)rn * G + kk] : 0.0;
+      acc[2 * KL - 1] = (rn >= 0) ? __dmul_rn(y[(size_t)rn * CPW], Ds[(size_t)rn * G + kk]) : 0.0;
       xn = xi;
     }
   }
@@ -490,7 +529,7 @@ __global__ void k_band_solve(int M, int nc, int Kz, int K, int CPW, int groups_p
     // x_0 from the decay condition sum_n Pbar_n^0(1) x_n = 0, Pbar_n^0(1) = sqrt((2n+1)/2)
     if (c < 4 * gcnt && valid) {
       double acc = 0.0;
-      for (int i = 0; i < N; ++i) acc += sqrt((2.0 * (i + 1) + 1.0) * 0.5) * Y[(size_t)i * CPW + c];
+      for (int i = 0; i < N; ++i) acc = __fma_rn(sqrt((2.0 * (i + 1) + 1.0) * 0.5), Y[(size_t)i * CPW + c], acc);
       const int kabs = k0 + kk;
       const int kidx = sgn ? K - kabs : kabs;
       out[2 * (sm + (long long)kidx * Nm) + part] = -acc / sqrt(0.5);
@@ -498,24 +537,20 @@ __global__ void k_band_solve(int M, int nc, int Kz, int K, int CPW, int groups_p
   }
   double2* out2 = reinterpret_cast<double2*>(out);
 #pragma unroll 4
-  for (int e = lane; e < N * 2 * gcnt; e += 32) {
-    const int cp = e / N, i = e - cp * N;
-    const int kq = cp >> 1, sg = cp & 1;
-    const int kabs = k0 + kq;
-    if (sg && kabs == 0) continue;
-    const int kidx = sg ? K - kabs : kabs;
+  for (int i = il; i < (lane_piece ? N : 0); i += LP) {
+    const int cp = cpl;
     double2 v = make_double2(Y[(size_t)i * CPW + cp * 2], Y[(size_t)i * CPW + cp * 2 + 1]);
     if (step == MLX_STEP_ABCN) {
       if (keep_s) {
         v.x -= S[(size_t)i * CPW + cp * 2];
         v.y -= S[(size_t)i * CPW + cp * 2 + 1];
       } else {
-        const double2 sv = s2[sm + (long long)kidx * Nm + sh + i];
+        const double2 sv = s2[pbase + i];
         v.x -= sv.x;
         v.y -= sv.y;
       }
     }
-    out2[sm + (long long)kidx * Nm + sh + i] = v;
+    out2[pbase + i] = v;
   }
 }
 
@@ -941,7 +976,7 @@ __global__ void k_band_solve_direct(int M, int nc, int Kz, int K, int groups_per
         if (q == d) { const double t = w[0]; w[0] = w[q]; w[q] = t; }
       y[(size_t)j * CPW] = w[0];
 #pragma unroll
-      for (int q = 1; q <= KL; ++q) w[q] -= l[q - 1] * w[0];
+      for (int q = 1; q <= KL; ++q) w[q] = __fma_rn(-l[q - 1], w[0], w[q]);
     }
     __syncwarp();
   }
@@ -966,7 +1001,7 @@ __global__ void k_band_solve_direct(int M, int nc, int Kz, int K, int groups_per
 #pragma unroll
   for (int t = 0; t < 2 * KL; ++t) {
     const int r = N - 1 - t;
-    acc[t] = (act && r >= 0) ? y[(size_t)r * CPW] * Dval(r) : 0.0;
+    acc[t] = (act && r >= 0) ? __dmul_rn(y[(size_t)r * CPW], Dval(r)) : 0.0;
   }
   double xn = 0.0;   // x_{i+1}
   for (int i = N - 1; i >= 0; --i) {
@@ -976,15 +1011,15 @@ __global__ void k_band_solve_direct(int M, int nc, int Kz, int K, int groups_per
     cp_async_wait_group<P>();
     __syncwarp();
     if (act) {
-      const double xi = acc[0] - Urow(i)[1] * xn;
+      const double xi = __fma_rn(-Urow(i)[1], xn, acc[0]);
 #pragma unroll
       for (int t = 1; t < 2 * KL; ++t)
-        if (i - t >= 0) acc[t] -= Urow(i - t)[t + 1] * xn;
+        if (i - t >= 0) acc[t] = __fma_rn(-Urow(i - t)[t + 1], xn, acc[t]);
       y[(size_t)i * CPW] = xi;
 #pragma unroll
       for (int t = 0; t < 2 * KL - 1; ++t) acc[t] = acc[t + 1];
       const int rn = i - 2 * KL;
-      acc[2 * KL - 1] = (rn >= 0) ? y[(size_t)rn * CPW] * Dval(rn) : 0.0;
+      acc[2 * KL - 1] = (rn >= 0) ? __dmul_rn(y[(size_t)rn * CPW], Dval(rn)) : 0.0;
       xn = xi;
     }
     __syncwarp();
@@ -993,7 +1028,7 @@ __global__ void k_band_solve_direct(int M, int nc, int Kz, int K, int groups_per
   __syncwarp();
   if (sh && valid) {
     double dacc = 0.0;
-    for (int i = 0; i < N; ++i) dacc += sqrt((2.0 * (i + 1) + 1.0) * 0.5) * Y[(size_t)i * CPW + c];
+    for (int i = 0; i < N; ++i) dacc = __fma_rn(sqrt((2.0 * (i + 1) + 1.0) * 0.5), Y[(size_t)i * CPW + c], dacc);
     const int kidx = sgn ? K - (k0 + kk) : k0 + kk;
     out[2 * (sm + (long long)kidx * Nm) + part] = -dacc / sqrt(0.5);
   }
@@ -1205,7 +1240,7 @@ __global__ void __launch_bounds__(64, 1) k_band_solve_lean(
       }
       yw[(size_t)j * CPW] = w[0];
 #pragma unroll
-      for (int q = 1; q <= KL; ++q) w[q] -= cur.l[q - 1] * w[0];
+      for (int q = 1; q <= KL; ++q) w[q] = __fma_rn(-cur.l[q - 1], w[0], w[q]);
     }
     cur = nxt;
   }
@@ -1249,7 +1284,7 @@ __global__ void __launch_bounds__(64, 1) k_band_solve_lean(
 #pragma unroll
   for (int t = 0; t < 2 * KL; ++t) {
     const int r = N - 1 - t;
-    acc[t] = (act && r >= 0) ? yw[(size_t)r * CPW] * invd[drow + (long long)r * kz_fac] : 0.0;
+    acc[t] = (act && r >= 0) ? __dmul_rn(yw[(size_t)r * CPW], invd[drow + (long long)r * kz_fac]) : 0.0;
   }
   cp_async_wait_group<P - 1>();
   __syncwarp();
@@ -1267,16 +1302,16 @@ __global__ void __launch_bounds__(64, 1) k_band_solve_lean(
     bwr = (bwr == RS - 1) ? 0 : bwr + 1;
     brd = (brd == RS - 1) ? 0 : brd + 1;
     if (act) {
-      const double xi = acc[0] - bc.u[0] * xn;
+      const double xi = __fma_rn(-bc.u[0], xn, acc[0]);
 #pragma unroll
-      for (int t = 1; t < 2 * KL; ++t) acc[t] -= bc.u[t] * xn;
+      for (int t = 1; t < 2 * KL; ++t) acc[t] = __fma_rn(-bc.u[t], xn, acc[t]);
       if (valid) {
         outc[2 * (long long)i] = (MODE == LEAN_ABCN) ? xi - bc.sv : xi;
         if (sh) yw[(size_t)i * CPW] = xi;
       }
 #pragma unroll
       for (int t = 0; t < 2 * KL - 1; ++t) acc[t] = acc[t + 1];
-      acc[2 * KL - 1] = (i - 2 * KL >= 0) ? bc.y * bc.dinv : 0.0;
+      acc[2 * KL - 1] = (i - 2 * KL >= 0) ? __dmul_rn(bc.y, bc.dinv) : 0.0;
       xn = xi;
     }
     bc = bn;
@@ -1284,7 +1319,7 @@ __global__ void __launch_bounds__(64, 1) k_band_solve_lean(
   cp_async_wait_all();
   if (sh && valid) {
     double dacc = 0.0;
-    for (int i = 0; i < N; ++i) dacc += sqrt((2.0 * (i + 1) + 1.0) * 0.5) * yw[(size_t)i * CPW];
+    for (int i = 0; i < N; ++i) dacc = __fma_rn(sqrt((2.0 * (i + 1) + 1.0) * 0.5), yw[(size_t)i * CPW], dacc);
     out[2 * (my0 - sh) + part] = -dacc / sqrt(0.5);
   }
 }
