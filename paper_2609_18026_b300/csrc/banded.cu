@@ -47,8 +47,17 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 // fused multiply-add and each product (__fma_rn, __dmul_rn): a product feeding a
 // later subtraction could otherwise be fused either way, and the choice would
 // differ between kernels of different shape.
+// 2 v exactly: for normal v with a finite double, an exponent increment (integer
+// pipe); zero, subnormal, overflowing, infinite and NaN inputs take the FP64 product
+__device__ __forceinline__ double twice(double v) {
+  const long long b = __double_as_longlong(v);
+  const unsigned e = (unsigned)(b >> 52) & 0x7ffu;
+  if (e - 1u < 2045u) return __longlong_as_double(b + (1LL << 52));
+  if (((unsigned long long)b << 1) == 0) return v;
+  return __dmul_rn(2.0, v);
+}
 __device__ __forceinline__ double rhs_abcn(double sv, double a, double ap, bool hasA, bool hasAp, double dt) {
-  double r = __dmul_rn(2.0, sv);
+  double r = twice(sv);
   if (hasA) r = __fma_rn(1.5 * dt, a, r);
   if (hasAp) r = __fma_rn(-0.5 * dt, ap, r);
   return r;
@@ -497,6 +506,19 @@ __global__ void k_band_solve(int M, int nc, int Kz, int K, int CPW, int groups_p
 #pragma unroll
       for (int q = 1; q <= KL; ++q) w[q] = __fma_rn(-l[q - 1], w[0], w[q]);
     }
+  }
+  __syncwarp();
+  // y_r / U_rr for every row and chain with all lanes busy (an FP64 instruction
+  // costs the pipe as much with 8 active lanes as with 32): the back substitution
+  // takes these products as they are, the same rounded values it would form
+  for (int i = il; i < (lane_piece ? N : 0); i += LP) {
+    const double dv = Ds[(size_t)i * G + kql];
+    Y[(size_t)i * CPW + cpl * 2] = __dmul_rn(Y[(size_t)i * CPW + cpl * 2], dv);
+    Y[(size_t)i * CPW + cpl * 2 + 1] = __dmul_rn(Y[(size_t)i * CPW + cpl * 2 + 1], dv);
+  }
+  __syncwarp();
+  if (c < 4 * gcnt) {
+    double* y = Y + c;
     // back substitution x_r = y_r / U_rr - sum_{q=1..2KL} (U_r,r+q / U_rr) x_{r+q},
     // software-pipelined: acc[t] is the partial sum of row i - t, and at step i
     // every pending row takes its term with x_{i+1} (row r the term q = i + 1 - r).
@@ -506,7 +528,7 @@ __global__ void k_band_solve(int M, int nc, int Kz, int K, int CPW, int groups_p
 #pragma unroll
     for (int t = 0; t < 2 * KL; ++t) {
       const int r = N - 1 - t;
-      acc[t] = (r >= 0) ? __dmul_rn(y[(size_t)r * CPW], Ds[(size_t)r * G + kk]) : 0.0;
+      acc[t] = (r >= 0) ? y[(size_t)r * CPW] : 0.0;
     }
     double xn = 0.0;   // x_{i+1}
 #pragma unroll 2
@@ -519,7 +541,7 @@ __global__ void k_band_solve(int M, int nc, int Kz, int K, int CPW, int groups_p
 #pragma unroll
       for (int t = 0; t < 2 * KL - 1; ++t) acc[t] = acc[t + 1];
       const int rn = i - 2 * KL;
-      acc[2 * KL - 1] = (rn >= 0) ? __dmul_rn(y[(size_t)rn * CPW], Ds[(size_t)rn * G + kk]) : 0.0;
+      acc[2 * KL - 1] = (rn >= 0) ? y[(size_t)rn * CPW] : 0.0;
       xn = xi;
     }
   }
