@@ -190,7 +190,7 @@ FP64_PEAK_TFLOPS = 1.25
 # DRAM bytes (read + write) per launch at this workload, from the ncu capture
 # summarised in profiles/band_solve_fkpp3d_128x128x64.md (current kernel version);
 # absent = not captured for the current code
-TRAFFIC = {"band_solve": 16448512 + 0}
+TRAFFIC = {"band_solve": 16478464 + 0}
 
 
 def band_solve_flops(ctx, kl=2):
