@@ -226,6 +226,9 @@ int mlx_advance(mlx_ctx* ctx, int kind, const double* coeffs, int ncoeffs,
  *                default 2 for hyperviscous bands (half width >= 4, set by
  *                mlx_implicit_setup), else 0.  Every variant other than
  *                "solve_ir" gives bitwise-equal results.
+ *   "phi_tile", "z_tile": radii per CTA of the phi and z transform kernels,
+ *                2, 4, 8, 16 or 32; 0 (default) = the largest tile whose grid
+ *                still has 2 (phi) or 4 (z) CTAs per SM.
  *   "solve_lean_cpw": real chains per warp of the lean variant, 16 or 32
  *                (default 32).
  *   "solve_direct_cpw": real chains per warp of the ring-staged variant, 8, 16 or 32

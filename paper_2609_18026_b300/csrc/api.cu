@@ -419,6 +419,13 @@ int mlx_set_tuning(mlx_ctx* c, const char* key, int value) {
     c->graphs.clear();
     return MLX_OK;
   }
+  if (strcmp(key, "phi_tile") == 0 || strcmp(key, "z_tile") == 0) {
+    if (value != 0 && value != 2 && value != 4 && value != 8 && value != 16 && value != 32) return MLX_EINVAL;
+    (key[0] == 'p' ? c->phi_tile : c->z_tile) = value;
+    for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
+    c->graphs.clear();
+    return MLX_OK;
+  }
   if (strcmp(key, "solve_lean_cpw") == 0) {
     if (value != 16 && value != 32) return MLX_EINVAL;
     c->solve_lean_cpw = value;

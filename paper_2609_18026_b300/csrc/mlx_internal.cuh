@@ -154,6 +154,8 @@ struct mlx_ctx {
   double* d_solve_y = nullptr;         // scratch of the lean variant, [warp][Nc][CPW]
   int solve_direct_cpw = 8;            // chains per warp of that variant: 8, 16 or 32
   int solve_keep_s = 1;                // staged variant: copy of s in shared memory for the AB-CN "- s"
+  int phi_tile = 0;                    // radii per CTA of the phi kernels (2..32; 0 = automatic)
+  int z_tile = 0;                      // radii per CTA of the z kernels (1..32; 0 = automatic)
   int solve_ir = 0;                    // 1: FP32 solves refined to FP64 by FP64 residuals
   int solve_ir_max = 8;                // refinement steps at most (early exit at FP64 level)
 

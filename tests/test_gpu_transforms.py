@@ -105,6 +105,24 @@ def test_fkpp_nonlinear_parity(grid, prec):
     assert O.spec_rel_err(g, spec_from_gpu(g, out), ref) <= TOL[prec]
 
 
+@pytest.mark.parametrize("tile", [2, 4, 16])
+def test_fft_tile_sizes_agree(tile):
+    # the phi kernel pairs radii r and r + tile/2 into one complex line, the z
+    # kernel transforms tile radii per CTA: other tiles, same transforms (odd Nr)
+    g, ctx = pair(33, 16, 8, 1.7, lz=2 * np.pi * 8, policy="twothirds", precision=B.FP32)
+    r, phi, z = g.nodes3()
+    from paper_2609_18026_b300 import workloads as W
+    s0 = to_gpu_spec(O.to_flat(g, O.forward(g, W.fkpp_seed(r, phi, z))))
+    outs = []
+    for t in (32, tile):
+        ctx.set_tuning("phi_tile", t)
+        ctx.set_tuning("z_tile", t)
+        outs.append(ctx.nonlinear(B.NONLIN_FKPP, [1.0], s0, ctx.new_spec()).cpu().numpy())
+        outs.append(ctx.forward(ctx.backward(s0, ctx.new_phys()), ctx.new_spec()).cpu().numpy())
+    for a, b in ((outs[0], outs[2]), (outs[1], outs[3])):
+        assert np.linalg.norm(b - a) <= 1e-6 * np.linalg.norm(a)
+
+
 def test_bf16x3_device_status_clean():
     # the tensor-core kernels' bounded waits never expire on a normal run
     g, ctx = pair(128, 128, 64, 4.0, policy="twothirds", precision=B.BF16X3)
