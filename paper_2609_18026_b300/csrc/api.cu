@@ -33,7 +33,8 @@ void free_ctx(mlx_ctx* c) {
                   c->lu_H.invd, c->lu_G.U, c->lu_G.L, c->lu_G.piv, c->lu_G.invd, c->d_solve_y,
                   c->lu_half.FS, c->lu_half.BS, c->lu_full.FS, c->lu_full.BS, c->lu_lap.FS, c->lu_lap.BS,
                   c->lu_helm.FS, c->lu_helm.BS, c->lu_Q.FS, c->lu_Q.BS, c->lu_H.FS, c->lu_H.BS,
-                  c->lu_G.FS, c->lu_G.BS};
+                  c->lu_G.FS, c->lu_G.BS, c->lu_half.PHf, c->lu_half.PHb, c->lu_half.PSf,
+                  c->lu_full.PHf, c->lu_full.PHb, c->lu_full.PSf};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
@@ -422,6 +423,13 @@ int mlx_set_tuning(mlx_ctx* c, const char* key, int value) {
   if (strcmp(key, "phi_tile") == 0 || strcmp(key, "z_tile") == 0) {
     if (value != 0 && value != 2 && value != 4 && value != 8 && value != 16 && value != 32) return MLX_EINVAL;
     (key[0] == 'p' ? c->phi_tile : c->z_tile) = value;
+    for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
+    c->graphs.clear();
+    return MLX_OK;
+  }
+  if (strcmp(key, "solve_seg") == 0) {
+    if (value != 0 && value != 1) return MLX_EINVAL;
+    c->solve_seg = value;
     for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
     c->graphs.clear();
     return MLX_OK;

@@ -577,6 +577,346 @@ __global__ void k_band_solve(int M, int nc, int Kz, int K, int CPW, int groups_p
 }
 
 
+// Segmented variant for narrow bands (the diffusion / Fisher-KPP operators): each
+// real chain is cut into SEG row segments that run side by side on SEG lanes.
+// An FP64 instruction holds its sub-partition's unit for the same time with 8 or
+// 32 active lanes, and the recurrences of the staged kernel run one row at a time
+// with 8 of 32 lanes busy, so their cost is (rows) x (FP64 instructions per row);
+// here every lane works and a warp walks N / SEG rows.  With the factors fixed,
+// both substitutions are linear recurrences, and a segment's result is its
+// "particular" run from a zero entry state plus a precomputed linear function of
+// the entry state (k_seg_setup):
+//   forward: y_j = y^p_j + PHf[j] . w,   exit window = E^p + PSf . w,
+//            w = the KL pending rows that enter the segment (exact for segment 0);
+//   back:    x_i = x^p_i + PHb[i] . v,   v = x of the 2KL rows after the segment
+//            (zero for the last).
+// A short sequential pass over the segments (one state component per lane) then
+// fixes every entry state, and a full-lane pass adds the corrections.  The sums are
+// ordered differently from k_band_solve: results agree to rounding, not bitwise.
+constexpr int SEG = 4;
+
+template <int KL>
+struct SegSmem {
+  static constexpr int W = 2 * KL + 1;
+  static constexpr int CPW = 32 / SEG, G = CPW / 4;
+  // doubles per row and |k|: U (W), L (KL), 1/diag, PHf (KL), PHb (2 KL)
+  __host__ __device__ static size_t per_warp(int nc, int keep_s) {
+    const size_t d = (size_t)nc * G * (W + KL + 1 + KL + 2 * KL) + (size_t)G * SEG * KL * KL +
+                     (size_t)nc * CPW * (keep_s ? 2 : 1) + (size_t)SEG * CPW * (3 * KL + 2 * KL);
+    return (d * sizeof(double) + (size_t)nc * G * sizeof(int) + 15) / 16 * 16;
+  }
+};
+
+// rows [j0, j1) of segment s of an N-row chain: SEG - 1 segments of floor(N / SEG)
+// rows, the last takes the rest
+__host__ __device__ __forceinline__ void seg_range(int N, int s, int& j0, int& j1) {
+  const int L = N / SEG;
+  j0 = s * L;
+  j1 = (s == SEG - 1) ? N : j0 + L;
+}
+
+// Influence data of the segmented solve for one factor family (rows off[m] + r Kz + k):
+// thread = (system m * Kz + k, segment, unit u); u < KL: forward entry-window unit,
+// else back entry unit t = u - KL.
+template <int KL>
+__global__ void k_seg_setup(int M, int nc, int Kz, const long long* __restrict__ off,
+                            const double* __restrict__ U, const double* __restrict__ Lm,
+                            const int* __restrict__ piv, double* __restrict__ PHf, double* __restrict__ PHb,
+                            double* __restrict__ PSf) {
+  constexpr int W = 2 * KL + 1, NU = 3 * KL;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)M * Kz * SEG * NU) return;
+  const int u = (int)(t % NU);
+  const int s = (int)((t / NU) % SEG);
+  const long long sys = t / ((long long)NU * SEG);
+  const int m = (int)(sys / Kz), kabs = (int)(sys % Kz);
+  const int N = nc - m;
+  int j0, j1;
+  seg_range(N, s, j0, j1);
+  auto row = [&](int r) -> long long { return off[m] + (long long)r * Kz + kabs; };
+  if (u < KL) {
+    // forward: unit entry window w[1 + u] = 1, no right-hand side
+    double w[KL + 1];
+#pragma unroll
+    for (int q = 0; q <= KL; ++q) w[q] = (q == u + 1) ? 1.0 : 0.0;
+    for (int j = j0; j < j1; ++j) {
+      const long long R = row(j);
+#pragma unroll
+      for (int q = 0; q < KL; ++q) w[q] = w[q + 1];
+      w[KL] = 0.0;
+      const int d = piv[R] - j;
+#pragma unroll
+      for (int q = 1; q <= KL; ++q)
+        if (q == d) { const double x = w[0]; w[0] = w[q]; w[q] = x; }
+      PHf[R * KL + u] = w[0];
+#pragma unroll
+      for (int q = 1; q <= KL; ++q) w[q] = __fma_rn(-Lm[R * KL + q - 1], w[0], w[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < KL; ++q) PSf[((sys * SEG + s) * KL + q) * KL + u] = w[q + 1];
+  } else {
+    // back: unit value of x at row j1 + tu, zero y; x_i = -sum_q U_{i,i+q}/U_ii x_{i+q}
+    const int tu = u - KL;
+    double xv[2 * KL];                                 // x_{i+1} .. x_{i+2KL}
+#pragma unroll
+    for (int q = 0; q < 2 * KL; ++q) xv[q] = (q == tu) ? 1.0 : 0.0;   // at i = j1 - 1
+    for (int i = j1 - 1; i >= j0; --i) {
+      const long long R = row(i);
+      double x = 0.0;
+#pragma unroll
+      for (int q = 2 * KL; q >= 1; --q) x = __fma_rn(-U[R * W + q], xv[q - 1], x);
+      PHb[R * 2 * KL + tu] = x;
+#pragma unroll
+      for (int q = 2 * KL - 1; q >= 1; --q) xv[q] = xv[q - 1];
+      xv[0] = x;
+    }
+  }
+}
+
+template <int KL>
+__global__ void k_band_solve_seg(int M, int nc, int Kz, int K, int groups_per_m, int step, int keep_s,
+                                 double dt, const long long* __restrict__ soff,
+                                 const long long* __restrict__ band_off, const double* __restrict__ U,
+                                 const double* __restrict__ Lm, const int* __restrict__ piv,
+                                 const double* __restrict__ invd, const double* __restrict__ PHf,
+                                 const double* __restrict__ PHb, const double* __restrict__ PSf,
+                                 const double* __restrict__ s, const double* __restrict__ A,
+                                 const double* __restrict__ Ap, double* __restrict__ out) {
+  using SM = SegSmem<KL>;
+  constexpr int W = SM::W, CPW = SM::CPW, G = SM::G;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int gw = blockIdx.x * (blockDim.x >> 5) + wib;
+  if (gw >= M * groups_per_m) return;
+  const int m = gw / groups_per_m;
+  const int k0 = (gw % groups_per_m) * G;
+  const int gcnt = min(G, Kz - k0);
+  const int N = nc - m;
+  unsigned char* base = smem_raw + (size_t)wib * SM::per_warp(nc, keep_s);
+  double* Us = reinterpret_cast<double*>(base);              // [N][G][W]
+  double* Ls = Us + (size_t)N * G * W;                       // [N][G][KL]
+  double* Ds = Ls + (size_t)N * G * KL;                      // [N][G]
+  double* Pf = Ds + (size_t)N * G;                           // [N][G][KL]
+  double* Pb = Pf + (size_t)N * G * KL;                      // [N][G][2KL]
+  double* PS = Pb + (size_t)N * G * 2 * KL;                  // [G][SEG][KL][KL]
+  double* Y = PS + (size_t)G * SEG * KL * KL;                // [N][CPW]
+  double* Sv = Y + (size_t)N * CPW;                          // [N][CPW] (keep_s)
+  double* BH = Sv + (keep_s ? (size_t)N * CPW : 0);          // [SEG][KL][CPW] right-hand side heads
+  double* EP = BH + SEG * KL * CPW;                          // [SEG][KL][CPW] particular exit windows
+  double* SF = EP + SEG * KL * CPW;                          // [SEG][KL][CPW] entry windows
+  double* SB = SF + SEG * KL * CPW;                          // [SEG][2KL][CPW] back entry values
+  int* Pi = reinterpret_cast<int*>(SB + SEG * 2 * KL * CPW); // [N][G]
+  const long long fb = band_off[m];
+  const long long sm = soff[m];
+  {
+    const long long r0 = fb + k0;
+    stage_rows(Us, G * W * 8, U + r0 * W, (long long)Kz * W * 8, N, gcnt * W * 8, lane);
+    stage_rows(Ls, G * KL * 8, Lm + r0 * KL, (long long)Kz * KL * 8, N, gcnt * KL * 8, lane);
+    stage_rows(Ds, G * 8, invd + r0, (long long)Kz * 8, N, gcnt * 8, lane);
+    stage_rows(Pf, G * KL * 8, PHf + r0 * KL, (long long)Kz * KL * 8, N, gcnt * KL * 8, lane);
+    stage_rows(Pb, G * 2 * KL * 8, PHb + r0 * 2 * KL, (long long)Kz * 2 * KL * 8, N, gcnt * 2 * KL * 8, lane);
+    stage_rows(PS, G * SEG * KL * KL * 8, PSf + ((long long)m * Kz + k0) * SEG * KL * KL, 0, 1,
+               gcnt * SEG * KL * KL * 8, lane);
+    stage_rows(Pi, G * 4, piv + r0, (long long)Kz * 4, N, gcnt * 4, lane);
+  }
+  cp_async_commit();
+  // right-hand sides, every lane busy (as in k_band_solve)
+  const double h = (step == MLX_STEP_FEBE_FULL) ? dt : 0.5 * dt;
+  const double2* s2 = reinterpret_cast<const double2*>(s);
+  const double2* A2 = reinterpret_cast<const double2*>(A);
+  const double2* Ap2 = reinterpret_cast<const double2*>(Ap);
+  const int LP = 16 / G;
+  const int cpl = lane / LP, il = lane - cpl * LP;
+  const int kql = cpl >> 1, sgl = cpl & 1, kabsl = k0 + kql;
+  const bool lane_piece = cpl < 2 * gcnt && !(sgl && kabsl == 0);
+  const long long pbase = sm + (long long)(sgl ? K - kabsl : kabsl) * N;
+  constexpr int RB = 8;
+  for (int i = il; i < (lane_piece ? N : 0); i += RB * LP) {
+    double2 sv[RB], av[RB], apv[RB];
+#pragma unroll
+    for (int u = 0; u < RB; ++u) {
+      const int ii = i + u * LP;
+      const long long o = pbase + (ii < N ? ii : i);
+      sv[u] = s2[o];
+      av[u] = (step != MLX_STEP_PLAIN && A) ? A2[o] : make_double2(0.0, 0.0);
+      apv[u] = (step == MLX_STEP_ABCN && Ap) ? Ap2[o] : make_double2(0.0, 0.0);
+    }
+#pragma unroll
+    for (int u = 0; u < RB; ++u) {
+      const int ii = i + u * LP;
+      if (ii >= N) break;
+      double2 r;
+      if (step == MLX_STEP_PLAIN) {
+        r = sv[u];
+      } else if (step == MLX_STEP_ABCN) {
+        r = make_double2(rhs_abcn(sv[u].x, av[u].x, apv[u].x, A, Ap, dt),
+                         rhs_abcn(sv[u].y, av[u].y, apv[u].y, A, Ap, dt));
+        if (keep_s) {
+          Sv[(size_t)ii * CPW + cpl * 2] = sv[u].x;
+          Sv[(size_t)ii * CPW + cpl * 2 + 1] = sv[u].y;
+        }
+      } else {
+        r = sv[u];
+        if (A) r = make_double2(rhs_febe(sv[u].x, av[u].x, true, h), rhs_febe(sv[u].y, av[u].y, true, h));
+      }
+      Y[(size_t)ii * CPW + cpl * 2] = r.x;
+      Y[(size_t)ii * CPW + cpl * 2 + 1] = r.y;
+    }
+  }
+  cp_async_wait_all();
+  __syncwarp();
+  // lane = segment sg x chain c
+  const int c = lane % CPW, sg = lane / CPW;
+  const int kk = c >> 2;
+  const bool act = kk < gcnt;
+  int j0, j1;
+  seg_range(N, sg, j0, j1);
+  // heads of the right-hand side of every segment after the first: the previous
+  // segment's window reads them after their owner has overwritten them
+  for (int e = lane; e < SEG * KL * CPW; e += 32) {
+    const int ss = e / (KL * CPW), q = (e / CPW) % KL, cc = e % CPW;
+    int a0, a1;
+    seg_range(N, ss, a0, a1);
+    BH[e] = (ss > 0) ? Y[(size_t)(a0 + q) * CPW + cc] : 0.0;
+  }
+  __syncwarp();
+  double* y = Y + c;
+  // ---- forward, particular run of this segment ----
+  if (act) {
+    double w[KL + 1];
+    w[0] = 0.0;
+#pragma unroll
+    for (int q = 0; q < KL; ++q) w[q + 1] = (sg == 0 && q < N) ? y[(size_t)q * CPW] : 0.0;
+#pragma unroll 2
+    for (int j = j0; j < j1; ++j) {
+#pragma unroll
+      for (int q = 0; q < KL; ++q) w[q] = w[q + 1];
+      const int jn = j + KL;
+      w[KL] = (jn >= N) ? 0.0 : (jn >= j1 ? BH[((sg + 1) * KL + (jn - j1)) * CPW + c] : y[(size_t)jn * CPW]);
+      const int d = Pi[(size_t)j * G + kk] - j;
+#pragma unroll
+      for (int q = 1; q <= KL; ++q)
+        if (q == d) { const double t = w[0]; w[0] = w[q]; w[q] = t; }
+      y[(size_t)j * CPW] = w[0];
+      const double* l = Ls + ((size_t)j * G + kk) * KL;
+#pragma unroll
+      for (int q = 1; q <= KL; ++q) w[q] = __fma_rn(-l[q - 1], w[0], w[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < KL; ++q) EP[(sg * KL + q) * CPW + c] = w[q + 1];
+  }
+  __syncwarp();
+  // ---- entry windows, one component per lane: SF[1] = EP[0], SF[s] = EP[s-1] + PSf[s-1] SF[s-1] ----
+  for (int ss = 1; ss < SEG; ++ss) {
+    for (int q = sg; q < KL; q += SEG) {
+      if (act) {
+        double v = EP[((ss - 1) * KL + q) * CPW + c];
+        if (ss > 1) {
+          const double* ps = PS + ((size_t)(kk * SEG + ss - 1) * KL + q) * KL;
+#pragma unroll
+          for (int q2 = 0; q2 < KL; ++q2) v = __fma_rn(ps[q2], SF[((ss - 1) * KL + q2) * CPW + c], v);
+        }
+        SF[(ss * KL + q) * CPW + c] = v;
+      }
+    }
+    __syncwarp();
+  }
+  // ---- forward corrections, then y / U_rr for every row and chain ----
+  if (act && sg > 0) {
+    double wv[KL];
+#pragma unroll
+    for (int q = 0; q < KL; ++q) wv[q] = SF[(sg * KL + q) * CPW + c];
+    for (int j = j0; j < j1; ++j) {
+      const double* pf = Pf + ((size_t)j * G + kk) * KL;
+      double v = y[(size_t)j * CPW];
+#pragma unroll
+      for (int q = 0; q < KL; ++q) v = __fma_rn(pf[q], wv[q], v);
+      y[(size_t)j * CPW] = v;
+    }
+  }
+  __syncwarp();
+  for (int i = il; i < (lane_piece ? N : 0); i += LP) {
+    const double dv = Ds[(size_t)i * G + kql];
+    Y[(size_t)i * CPW + cpl * 2] = __dmul_rn(Y[(size_t)i * CPW + cpl * 2], dv);
+    Y[(size_t)i * CPW + cpl * 2 + 1] = __dmul_rn(Y[(size_t)i * CPW + cpl * 2 + 1], dv);
+  }
+  __syncwarp();
+  // ---- back substitution, particular run of this segment (zero x after it) ----
+  if (act) {
+    double acc[2 * KL];
+#pragma unroll
+    for (int t = 0; t < 2 * KL; ++t) {
+      const int r = j1 - 1 - t;
+      acc[t] = (r >= j0) ? y[(size_t)r * CPW] : 0.0;
+    }
+    double xn = 0.0;
+#pragma unroll 2
+    for (int i = j1 - 1; i >= j0; --i) {
+      const double xi = __fma_rn(-Us[((size_t)i * G + kk) * W + 1], xn, acc[0]);
+#pragma unroll
+      for (int t = 1; t < 2 * KL; ++t)
+        if (i - t >= j0) acc[t] = __fma_rn(-Us[((size_t)(i - t) * G + kk) * W + t + 1], xn, acc[t]);
+      y[(size_t)i * CPW] = xi;
+#pragma unroll
+      for (int t = 0; t < 2 * KL - 1; ++t) acc[t] = acc[t + 1];
+      const int rn = i - 2 * KL;
+      acc[2 * KL - 1] = (rn >= j0) ? y[(size_t)rn * CPW] : 0.0;
+      xn = xi;
+    }
+  }
+  __syncwarp();
+  // ---- back entry values, one component per lane, from the last segment down:
+  // SB[s][t] = x of row (start of segment s+1) + t = x^p + PHb . SB[s+1] ----
+  for (int ss = SEG - 2; ss >= 0; --ss) {
+    int a0, a1;
+    seg_range(N, ss + 1, a0, a1);
+    for (int t = sg; t < 2 * KL; t += SEG) {
+      if (act) {
+        const int r = a0 + t;
+        double v = y[(size_t)r * CPW];
+        if (ss + 1 < SEG - 1) {
+          const double* pb = Pb + ((size_t)r * G + kk) * 2 * KL;
+#pragma unroll
+          for (int t2 = 0; t2 < 2 * KL; ++t2) v = __fma_rn(pb[t2], SB[((ss + 1) * 2 * KL + t2) * CPW + c], v);
+        }
+        SB[(ss * 2 * KL + t) * CPW + c] = v;
+      }
+    }
+    __syncwarp();
+  }
+  // ---- back corrections ----
+  if (act && sg < SEG - 1) {
+    double vv[2 * KL];
+#pragma unroll
+    for (int t = 0; t < 2 * KL; ++t) vv[t] = SB[(sg * 2 * KL + t) * CPW + c];
+    for (int i = j0; i < j1; ++i) {
+      const double* pb = Pb + ((size_t)i * G + kk) * 2 * KL;
+      double v = y[(size_t)i * CPW];
+#pragma unroll
+      for (int t = 0; t < 2 * KL; ++t) v = __fma_rn(pb[t], vv[t], v);
+      y[(size_t)i * CPW] = v;
+    }
+  }
+  __syncwarp();
+  // ---- output ----
+  double2* out2 = reinterpret_cast<double2*>(out);
+#pragma unroll 4
+  for (int i = il; i < (lane_piece ? N : 0); i += LP) {
+    double2 v = make_double2(Y[(size_t)i * CPW + cpl * 2], Y[(size_t)i * CPW + cpl * 2 + 1]);
+    if (step == MLX_STEP_ABCN) {
+      if (keep_s) {
+        v.x -= Sv[(size_t)i * CPW + cpl * 2];
+        v.y -= Sv[(size_t)i * CPW + cpl * 2 + 1];
+      } else {
+        const double2 sv = s2[pbase + i];
+        v.x -= sv.x;
+        v.y -= sv.y;
+      }
+    }
+    out2[pbase + i] = v;
+  }
+}
+
 // FP32 copy of a factor array
 __global__ void k_to_f32(long long n, const double* __restrict__ a, float* __restrict__ b) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -814,6 +1154,7 @@ int mlx_band_setup(mlx_ctx* c, cudaStream_t st) {
   cudaFree(c->lu_full.U); cudaFree(c->lu_full.L); cudaFree(c->lu_full.piv); cudaFree(c->lu_full.invd);
   for (BandLU* f : {&c->lu_half, &c->lu_full}) {
     cudaFree(f->U32); cudaFree(f->L32); cudaFree(f->invd32); cudaFree(f->FS); cudaFree(f->BS);
+    cudaFree(f->PHf); cudaFree(f->PHb); cudaFree(f->PSf);
   }
   c->d_Bplus = nullptr;
   c->lu_half = BandLU();
@@ -852,6 +1193,15 @@ int mlx_band_setup(mlx_ctx* c, cudaStream_t st) {
     k_to_f32<<<(unsigned)((rows + 255) / 256), 256, 0, st>>>(rows, f->invd, f->invd32);
     const int rc = mlx_pack_lean(c, *f, kl, c->d_band_off, c->Kz, rows, st);
     if (rc) return rc;
+    // segmented-solve influence data: half width 2, every segment at least 2 kl rows
+    if (kl == 2 && (c->nc - (c->M - 1)) / SEG >= 2 * kl) {
+      MLX_CUDA_TRY(c, cudaMalloc(&f->PHf, sizeof(double) * rows * kl));
+      MLX_CUDA_TRY(c, cudaMalloc(&f->PHb, sizeof(double) * rows * 2 * kl));
+      MLX_CUDA_TRY(c, cudaMalloc(&f->PSf, sizeof(double) * (long long)c->M * c->Kz * SEG * kl * kl));
+      const long long nt = (long long)c->M * c->Kz * SEG * 3 * kl;
+      k_seg_setup<2><<<(unsigned)((nt + 127) / 128), 128, 0, st>>>(c->M, c->nc, c->Kz, c->d_band_off, f->U,
+                                                                   f->L, f->piv, f->PHf, f->PHb, f->PSf);
+    }
   }
   MLX_LAUNCH_CHECK(c);
   MLX_CUDA_TRY(c, cudaStreamSynchronize(st));
@@ -1428,6 +1778,23 @@ static int launch_solve(mlx_ctx* c, int step, const BandLU& f, const long long* 
     if (c->solve_direct_cpw == 16) return go(std::integral_constant<int, 16>());
     return go(std::integral_constant<int, 32>());
   }
+  if constexpr (KL == 2) {
+    if (c->solve_seg && f.PHf && kz_fac == c->Kz && m0_shift == 0) {
+      const int keep_s = (step == MLX_STEP_ABCN && c->solve_keep_s) ? 1 : 0;
+      const size_t pw = SegSmem<KL>::per_warp(c->nc, keep_s);
+      int WPB = 4;
+      while (WPB > 1 && pw * WPB > 200 * 1024) WPB /= 2;
+      if (pw * WPB <= 200 * 1024) {
+        const int G = SegSmem<KL>::G;
+        const int gpm = (c->Kz + G - 1) / G;
+        const int warps = c->M * gpm;
+        k_band_solve_seg<KL><<<(warps + WPB - 1) / WPB, 32 * WPB, pw * WPB, st>>>(
+            c->M, c->nc, c->Kz, c->K, gpm, step, keep_s, c->dt, c->d_soff, fac_off, f.U, f.L, f.piv, f.invd,
+            f.PHf, f.PHb, f.PSf, (const double*)s, (const double*)A, (const double*)Ap, (double*)out);
+        return MLX_OK;
+      }
+    }
+  }
   // Chains per warp and warps per CTA are launch-shape parameters (measured best
   // at the 128x128x64 workload: 8 chains per warp, 1-4 warps per CTA).
   int CPW = c->solve_cpw;
@@ -1638,6 +2005,7 @@ int mlx_solve_scratch(mlx_ctx* c) {
 
 int mlx_band_prepare(mlx_ctx* c) {
   const int lim = 200 * 1024;
+  MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_band_solve_seg<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
   MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_band_solve<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
   MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_band_solve<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
 #define MLX_DIRECT_ATTR(KLV, CPWV)                                                                   \

@@ -63,6 +63,11 @@ struct BandLU {
   // substitution {U[row - t][t + 1] (t < 2 kl), 1/diag[row - 2 kl], pad}
   double* FS = nullptr;
   double* BS = nullptr;
+  // segmented solve (half width 2): forward influence of the entry window per row
+  // [rows][kl] and per segment [system][seg][kl][kl], back influence [rows][2 kl]
+  double* PHf = nullptr;
+  double* PHb = nullptr;
+  double* PSf = nullptr;
 };
 
 struct mlx_ctx {
@@ -156,6 +161,7 @@ struct mlx_ctx {
   int solve_keep_s = 1;                // staged variant: copy of s in shared memory for the AB-CN "- s"
   int phi_tile = 0;                    // radii per CTA of the phi kernels (2..32; 0 = automatic)
   int z_tile = 0;                      // radii per CTA of the z kernels (1..32; 0 = automatic)
+  int solve_seg = 1;                   // 1: segmented solve for half width 2 where its data exist
   int solve_ir = 0;                    // 1: FP32 solves refined to FP64 by FP64 residuals
   int solve_ir_max = 8;                // refinement steps at most (early exit at FP64 level)
 

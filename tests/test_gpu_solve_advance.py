@@ -185,6 +185,7 @@ def test_solve_variants_agree(nu_h, p, step):
     s, A, Ap = (to_gpu_spec(rand_spec(g, k)) for k in (1, 2, 3))
     outs = []
     variants = ((0, 0, 8), (0, 1, 8), (0, 1, 16), (0, 1, 32), (0, 2, 16), (0, 2, 32), (1, 0, 8))
+    ctx.set_tuning("solve_seg", 0)
     for ir, direct, cpw in variants:
         ctx.set_tuning("solve_ir", ir)
         ctx.set_tuning("solve_direct", direct)
@@ -209,6 +210,33 @@ def test_solve_variants_agree(nu_h, p, step):
     else:
         ref = st.febe(S, False, Af)
     assert O.spec_rel_err(g, O.from_flat(g, outs[2]), ref) <= tol
+
+
+@pytest.mark.parametrize("grid", [(40, 16, 8, 1.5), (96, 32, 16, 1.0), (128, 128, 64, 4.0)])
+@pytest.mark.parametrize("step", [B.STEP_FEBE_HALF, B.STEP_FEBE_FULL, B.STEP_ABCN])
+def test_segmented_solve(grid, step):
+    # half width 2: the chains cut into 4 row segments solved side by side, entry
+    # states fixed by the precomputed influence data; same systems as the staged
+    # recurrence, sums in another order: within 1e-12 of the oracle and of it
+    nr, nphi, nz, ell = grid
+    g, ctx = pair(nr, nphi, nz, ell, lz=3.0, policy="twothirds")
+    dt, nu = 2e-2, 0.3
+    ctx.implicit_setup(nu, dt)
+    s, A, Ap = (rand_spec(g, k) for k in (7, 8, 9))
+    outs = []
+    for seg in (1, 0):
+        ctx.set_tuning("solve_seg", seg)
+        outs.append(ctx.implicit_solve(step, to_gpu_spec(s), to_gpu_spec(A), to_gpu_spec(Ap),
+                                       ctx.new_spec()).cpu().numpy())
+    assert np.linalg.norm(outs[0] - outs[1]) <= 1e-13 * np.linalg.norm(outs[1])
+    st = O.Stepper(g, nu, dt)
+    S, AA, AP = (O.from_flat(g, v) for v in (s, A, Ap))
+    ref = st.abcn(S, AA, AP) if step == B.STEP_ABCN else st.febe(S, step == B.STEP_FEBE_HALF, AA)
+    assert O.spec_rel_err(g, O.from_flat(g, outs[0]), ref) <= 1e-12
+    ctx.timing(True)
+    ctx.implicit_solve(step, to_gpu_spec(s), to_gpu_spec(A), to_gpu_spec(Ap), ctx.new_spec())
+    assert ctx.timing_read()["band_solve"][0] == 1
+    ctx.timing(False)
 
 
 def test_refined_solve_reaches_fp64_level():
