@@ -188,9 +188,9 @@ def tc_executed_flops(ctx, forward):
 FP64_PEAK_TFLOPS = 1.25
 
 # DRAM bytes (read + write) per launch at this workload, from the ncu capture
-# summarised in profiles/band_solve_fkpp3d_128x128x64.md (current kernel version);
+# summarised in profiles/band_solve_seg_fkpp3d_128x128x64.md (current kernel version);
 # absent = not captured for the current code
-TRAFFIC = {"band_solve": 16478464 + 0}
+TRAFFIC = {"band_solve": 21457152 + 256}
 
 
 def band_solve_flops(ctx, kl=2):

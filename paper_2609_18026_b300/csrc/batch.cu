@@ -77,6 +77,9 @@ int mlx_batch_create(mlx_ctx* const* ctxs, int n, mlx_batch** out) {
   // over sequential on the 64-instance workload)
   for (mlx_ctx* c : b->ctxs) {
     if (mlx_set_tuning(c, "solve_keep_s", 0) != MLX_OK) { batch_free(b); return MLX_ECUDA; }
+    // the segmented solve's CTAs (up to ~200 KB of shared memory) leave no room
+    // for the other members' kernels: 32.9k against 38.3k instance-steps/s
+    if (mlx_set_tuning(c, "solve_seg", 0) != MLX_OK) { batch_free(b); return MLX_ECUDA; }
   }
   *out = b;
   return MLX_OK;
