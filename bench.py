@@ -190,7 +190,7 @@ FP64_PEAK_TFLOPS = 1.25
 # DRAM bytes (read + write) per launch at this workload, from the ncu capture
 # summarised in profiles/band_solve_seg_fkpp3d_128x128x64.md (current kernel version);
 # absent = not captured for the current code
-TRAFFIC = {"band_solve": 21457152 + 256}
+TRAFFIC = {"band_solve": 21573120 + 0}
 
 
 def band_solve_flops(ctx, kl=2):

@@ -229,13 +229,15 @@ int mlx_advance(mlx_ctx* ctx, int kind, const double* coeffs, int ncoeffs,
  *   "phi_tile", "z_tile": radii per CTA of the phi and z transform kernels,
  *                2, 4, 8, 16 or 32; 0 (default) = the largest tile whose grid
  *                still has 2 (phi) or 4 (z) CTAs per SM.
- *   "solve_seg": 1 (default) = half-width-2 implicit solves (diffusion,
- *                Fisher-KPP) cut every chain into 4 row segments solved side by
- *                side: each segment's particular solution plus a linear function of
- *                its entry state, from influence data computed at
- *                mlx_implicit_setup (needs Nc - M + 1 >= 16, else the staged
- *                solve runs); results agree with the other variants to rounding,
- *                not bitwise; 0 = off.
+ *   "solve_seg": 8 (default) or 4 = half-width-2 implicit solves (diffusion,
+ *                Fisher-KPP) cut every chain into that many row segments solved
+ *                side by side: each segment's particular solution plus a linear
+ *                function of its entry state, from influence data computed at
+ *                mlx_implicit_setup or when this key changes (needs
+ *                Nc - M + 1 >= 4 x segments; 8 falls back to 4, else the staged
+ *                solve runs);
+ *                results agree with the other variants to rounding, not
+ *                bitwise; 0 = off.
  *   "solve_lean_cpw": real chains per warp of the lean variant, 16 or 32
  *                (default 32).
  *   "solve_direct_cpw": real chains per warp of the ring-staged variant, 8, 16 or 32

@@ -428,8 +428,15 @@ int mlx_set_tuning(mlx_ctx* c, const char* key, int value) {
     return MLX_OK;
   }
   if (strcmp(key, "solve_seg") == 0) {
-    if (value != 0 && value != 1) return MLX_EINVAL;
+    if (value != 0 && value != 4 && value != 8) return MLX_EINVAL;
     c->solve_seg = value;
+    if (c->implicit_ready) {
+      for (BandLU* f : {&c->lu_half, &c->lu_full}) {
+        const int rc = mlx_seg_build(c, *f, value, nullptr);
+        if (rc) return rc;
+      }
+      MLX_CUDA_TRY(c, cudaStreamSynchronize(nullptr));
+    }
     for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
     c->graphs.clear();
     return MLX_OK;

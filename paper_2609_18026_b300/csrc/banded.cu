@@ -593,9 +593,8 @@ __global__ void k_band_solve(int M, int nc, int Kz, int K, int CPW, int groups_p
 // A short sequential pass over the segments (one state component per lane) then
 // fixes every entry state, and a full-lane pass adds the corrections.  The sums are
 // ordered differently from k_band_solve: results agree to rounding, not bitwise.
-constexpr int SEG = 4;
 
-template <int KL>
+template <int KL, int SEG>
 struct SegSmem {
   static constexpr int W = 2 * KL + 1;
   static constexpr int CPW = 32 / SEG, G = CPW / 4;
@@ -609,6 +608,7 @@ struct SegSmem {
 
 // rows [j0, j1) of segment s of an N-row chain: SEG - 1 segments of floor(N / SEG)
 // rows, the last takes the rest
+template <int SEG>
 __host__ __device__ __forceinline__ void seg_range(int N, int s, int& j0, int& j1) {
   const int L = N / SEG;
   j0 = s * L;
@@ -618,7 +618,7 @@ __host__ __device__ __forceinline__ void seg_range(int N, int s, int& j0, int& j
 // Influence data of the segmented solve for one factor family (rows off[m] + r Kz + k):
 // thread = (system m * Kz + k, segment, unit u); u < KL: forward entry-window unit,
 // else back entry unit t = u - KL.
-template <int KL>
+template <int KL, int SEG>
 __global__ void k_seg_setup(int M, int nc, int Kz, const long long* __restrict__ off,
                             const double* __restrict__ U, const double* __restrict__ Lm,
                             const int* __restrict__ piv, double* __restrict__ PHf, double* __restrict__ PHb,
@@ -632,7 +632,7 @@ __global__ void k_seg_setup(int M, int nc, int Kz, const long long* __restrict__
   const int m = (int)(sys / Kz), kabs = (int)(sys % Kz);
   const int N = nc - m;
   int j0, j1;
-  seg_range(N, s, j0, j1);
+  seg_range<SEG>(N, s, j0, j1);
   auto row = [&](int r) -> long long { return off[m] + (long long)r * Kz + kabs; };
   if (u < KL) {
     // forward: unit entry window w[1 + u] = 1, no right-hand side
@@ -673,7 +673,7 @@ __global__ void k_seg_setup(int M, int nc, int Kz, const long long* __restrict__
   }
 }
 
-template <int KL>
+template <int KL, int SEG>
 __global__ void k_band_solve_seg(int M, int nc, int Kz, int K, int groups_per_m, int step, int keep_s,
                                  double dt, const long long* __restrict__ soff,
                                  const long long* __restrict__ band_off, const double* __restrict__ U,
@@ -682,7 +682,7 @@ __global__ void k_band_solve_seg(int M, int nc, int Kz, int K, int groups_per_m,
                                  const double* __restrict__ PHb, const double* __restrict__ PSf,
                                  const double* __restrict__ s, const double* __restrict__ A,
                                  const double* __restrict__ Ap, double* __restrict__ out) {
-  using SM = SegSmem<KL>;
+  using SM = SegSmem<KL, SEG>;
   constexpr int W = SM::W, CPW = SM::CPW, G = SM::G;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -770,13 +770,13 @@ __global__ void k_band_solve_seg(int M, int nc, int Kz, int K, int groups_per_m,
   const int kk = c >> 2;
   const bool act = kk < gcnt;
   int j0, j1;
-  seg_range(N, sg, j0, j1);
+  seg_range<SEG>(N, sg, j0, j1);
   // heads of the right-hand side of every segment after the first: the previous
   // segment's window reads them after their owner has overwritten them
   for (int e = lane; e < SEG * KL * CPW; e += 32) {
     const int ss = e / (KL * CPW), q = (e / CPW) % KL, cc = e % CPW;
     int a0, a1;
-    seg_range(N, ss, a0, a1);
+    seg_range<SEG>(N, ss, a0, a1);
     BH[e] = (ss > 0) ? Y[(size_t)(a0 + q) * CPW + cc] : 0.0;
   }
   __syncwarp();
@@ -869,7 +869,7 @@ __global__ void k_band_solve_seg(int M, int nc, int Kz, int K, int groups_per_m,
   // SB[s][t] = x of row (start of segment s+1) + t = x^p + PHb . SB[s+1] ----
   for (int ss = SEG - 2; ss >= 0; --ss) {
     int a0, a1;
-    seg_range(N, ss + 1, a0, a1);
+    seg_range<SEG>(N, ss + 1, a0, a1);
     for (int t = sg; t < 2 * KL; t += SEG) {
       if (act) {
         const int r = a0 + t;
@@ -1193,15 +1193,8 @@ int mlx_band_setup(mlx_ctx* c, cudaStream_t st) {
     k_to_f32<<<(unsigned)((rows + 255) / 256), 256, 0, st>>>(rows, f->invd, f->invd32);
     const int rc = mlx_pack_lean(c, *f, kl, c->d_band_off, c->Kz, rows, st);
     if (rc) return rc;
-    // segmented-solve influence data: half width 2, every segment at least 2 kl rows
-    if (kl == 2 && (c->nc - (c->M - 1)) / SEG >= 2 * kl) {
-      MLX_CUDA_TRY(c, cudaMalloc(&f->PHf, sizeof(double) * rows * kl));
-      MLX_CUDA_TRY(c, cudaMalloc(&f->PHb, sizeof(double) * rows * 2 * kl));
-      MLX_CUDA_TRY(c, cudaMalloc(&f->PSf, sizeof(double) * (long long)c->M * c->Kz * SEG * kl * kl));
-      const long long nt = (long long)c->M * c->Kz * SEG * 3 * kl;
-      k_seg_setup<2><<<(unsigned)((nt + 127) / 128), 128, 0, st>>>(c->M, c->nc, c->Kz, c->d_band_off, f->U,
-                                                                   f->L, f->piv, f->PHf, f->PHb, f->PSf);
-    }
+    const int rs = mlx_seg_build(c, *f, c->solve_seg, st);
+    if (rs) return rs;
   }
   MLX_LAUNCH_CHECK(c);
   MLX_CUDA_TRY(c, cudaStreamSynchronize(st));
@@ -1779,20 +1772,23 @@ static int launch_solve(mlx_ctx* c, int step, const BandLU& f, const long long* 
     return go(std::integral_constant<int, 32>());
   }
   if constexpr (KL == 2) {
-    if (c->solve_seg && f.PHf && kz_fac == c->Kz && m0_shift == 0) {
+    if (c->solve_seg && f.PHf && f.seg && kz_fac == c->Kz && m0_shift == 0) {
       const int keep_s = (step == MLX_STEP_ABCN && c->solve_keep_s) ? 1 : 0;
-      const size_t pw = SegSmem<KL>::per_warp(c->nc, keep_s);
-      int WPB = 4;
-      while (WPB > 1 && pw * WPB > 200 * 1024) WPB /= 2;
-      if (pw * WPB <= 200 * 1024) {
-        const int G = SegSmem<KL>::G;
+      auto go = [&](auto seg_tag) -> bool {
+        constexpr int S = decltype(seg_tag)::value;
+        const size_t pw = SegSmem<KL, S>::per_warp(c->nc, keep_s);
+        int WPB = 32 / (32 / S);                    // 4 warps (S = 4) or 8 (S = 8) per CTA
+        while (WPB > 1 && pw * WPB > 200 * 1024) WPB /= 2;
+        if (pw * WPB > 200 * 1024) return false;
+        const int G = SegSmem<KL, S>::G;
         const int gpm = (c->Kz + G - 1) / G;
         const int warps = c->M * gpm;
-        k_band_solve_seg<KL><<<(warps + WPB - 1) / WPB, 32 * WPB, pw * WPB, st>>>(
+        k_band_solve_seg<KL, S><<<(warps + WPB - 1) / WPB, 32 * WPB, pw * WPB, st>>>(
             c->M, c->nc, c->Kz, c->K, gpm, step, keep_s, c->dt, c->d_soff, fac_off, f.U, f.L, f.piv, f.invd,
             f.PHf, f.PHb, f.PSf, (const double*)s, (const double*)A, (const double*)Ap, (double*)out);
-        return MLX_OK;
-      }
+        return true;
+      };
+      if (f.seg == 8 ? go(std::integral_constant<int, 8>()) : go(std::integral_constant<int, 4>())) return MLX_OK;
     }
   }
   // Chains per warp and warps per CTA are launch-shape parameters (measured best
@@ -1977,6 +1973,33 @@ static int set_lean_attrs(mlx_ctx* c, int lim) {
   return MLX_OK;
 }
 
+// Segmented-solve influence data of an implicit-step factor family for S segments
+// (S = 0 frees it).  Built only for half width 2 when every segment has at least
+// 2 kl rows (S = 8 falls back to 4 when the shortest chain is too short); otherwise
+// the family keeps none and the staged solve runs.
+int mlx_seg_build(mlx_ctx* c, BandLU& f, int S, cudaStream_t st) {
+  cudaFree(f.PHf); cudaFree(f.PHb); cudaFree(f.PSf);
+  f.PHf = f.PHb = f.PSf = nullptr;
+  f.seg = 0;
+  const int kl = c->kl;
+  if (S == 8 && (c->nc - (c->M - 1)) / 8 < 2 * kl) S = 4;   // chains too short for 8 segments
+  if (S == 0 || kl != 2 || !f.U || (c->nc - (c->M - 1)) / S < 2 * kl) return MLX_OK;
+  const long long rows = c->band_rows;
+  MLX_CUDA_TRY(c, cudaMalloc(&f.PHf, sizeof(double) * rows * kl));
+  MLX_CUDA_TRY(c, cudaMalloc(&f.PHb, sizeof(double) * rows * 2 * kl));
+  MLX_CUDA_TRY(c, cudaMalloc(&f.PSf, sizeof(double) * (long long)c->M * c->Kz * S * kl * kl));
+  const long long nt = (long long)c->M * c->Kz * S * 3 * kl;
+  if (S == 8)
+    k_seg_setup<2, 8><<<(unsigned)((nt + 127) / 128), 128, 0, st>>>(c->M, c->nc, c->Kz, c->d_band_off, f.U,
+                                                                    f.L, f.piv, f.PHf, f.PHb, f.PSf);
+  else
+    k_seg_setup<2, 4><<<(unsigned)((nt + 127) / 128), 128, 0, st>>>(c->M, c->nc, c->Kz, c->d_band_off, f.U,
+                                                                    f.L, f.piv, f.PHf, f.PHb, f.PSf);
+  MLX_LAUNCH_CHECK(c);
+  f.seg = S;
+  return MLX_OK;
+}
+
 // Lean-solve records (FS, BS) of a factor family just factorised on stream st.
 int mlx_pack_lean(mlx_ctx* c, BandLU& f, int kl, const long long* d_off, int kz_fac, long long rows,
                   cudaStream_t st) {
@@ -2005,7 +2028,8 @@ int mlx_solve_scratch(mlx_ctx* c) {
 
 int mlx_band_prepare(mlx_ctx* c) {
   const int lim = 200 * 1024;
-  MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_band_solve_seg<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+  MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_band_solve_seg<2, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+  MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_band_solve_seg<2, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
   MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_band_solve<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
   MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_band_solve<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
 #define MLX_DIRECT_ATTR(KLV, CPWV)                                                                   \

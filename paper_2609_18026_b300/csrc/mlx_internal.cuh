@@ -68,6 +68,7 @@ struct BandLU {
   double* PHf = nullptr;
   double* PHb = nullptr;
   double* PSf = nullptr;
+  int seg = 0;             // segments the influence data were built for (0 = none)
 };
 
 struct mlx_ctx {
@@ -161,7 +162,7 @@ struct mlx_ctx {
   int solve_keep_s = 1;                // staged variant: copy of s in shared memory for the AB-CN "- s"
   int phi_tile = 0;                    // radii per CTA of the phi kernels (2..32; 0 = automatic)
   int z_tile = 0;                      // radii per CTA of the z kernels (1..32; 0 = automatic)
-  int solve_seg = 1;                   // 1: segmented solve for half width 2 where its data exist
+  int solve_seg = 8;                   // segments of the half-width-2 segmented solve (8, 4; 0 = off)
   int solve_ir = 0;                    // 1: FP32 solves refined to FP64 by FP64 residuals
   int solve_ir_max = 8;                // refinement steps at most (early exit at FP64 level)
 
@@ -216,6 +217,7 @@ int mlx_legendre_forward(mlx_ctx* c, double2* spec, cudaStream_t st,
 int mlx_legendre_backward(mlx_ctx* c, const double2* spec, cudaStream_t st); // spec -> d_mixed
 int mlx_band_setup(mlx_ctx* c, cudaStream_t st);
 int mlx_solve_scratch(mlx_ctx* c);                 // scratch of the lean solve variant
+int mlx_seg_build(mlx_ctx* c, BandLU& f, int S, cudaStream_t st);   // segmented-solve data (S = 0: none)
 int mlx_pack_lean(mlx_ctx* c, BandLU& f, int kl, const long long* d_off, int kz_fac, long long rows,
                   cudaStream_t st);                 // lean-solve records of a factor family
 int mlx_lap_setup(mlx_ctx* c, cudaStream_t st);

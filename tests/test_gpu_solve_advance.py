@@ -215,7 +215,7 @@ def test_solve_variants_agree(nu_h, p, step):
 @pytest.mark.parametrize("grid", [(40, 16, 8, 1.5), (96, 32, 16, 1.0), (128, 128, 64, 4.0)])
 @pytest.mark.parametrize("step", [B.STEP_FEBE_HALF, B.STEP_FEBE_FULL, B.STEP_ABCN])
 def test_segmented_solve(grid, step):
-    # half width 2: the chains cut into 4 row segments solved side by side, entry
+    # half width 2: the chains cut into 4 or 8 row segments solved side by side, entry
     # states fixed by the precomputed influence data; same systems as the staged
     # recurrence, sums in another order: within 1e-12 of the oracle and of it
     nr, nphi, nz, ell = grid
@@ -224,11 +224,12 @@ def test_segmented_solve(grid, step):
     ctx.implicit_setup(nu, dt)
     s, A, Ap = (rand_spec(g, k) for k in (7, 8, 9))
     outs = []
-    for seg in (1, 0):
+    for seg in (4, 8, 0):
         ctx.set_tuning("solve_seg", seg)
         outs.append(ctx.implicit_solve(step, to_gpu_spec(s), to_gpu_spec(A), to_gpu_spec(Ap),
                                        ctx.new_spec()).cpu().numpy())
-    assert np.linalg.norm(outs[0] - outs[1]) <= 1e-13 * np.linalg.norm(outs[1])
+    for o in outs[:2]:
+        assert np.linalg.norm(o - outs[2]) <= 1e-13 * np.linalg.norm(outs[2])
     st = O.Stepper(g, nu, dt)
     S, AA, AP = (O.from_flat(g, v) for v in (s, A, Ap))
     ref = st.abcn(S, AA, AP) if step == B.STEP_ABCN else st.febe(S, step == B.STEP_FEBE_HALF, AA)
