@@ -212,7 +212,9 @@ def test_solve_variants_agree(nu_h, p, step):
     assert O.spec_rel_err(g, O.from_flat(g, outs[2]), ref) <= tol
 
 
-@pytest.mark.parametrize("grid", [(40, 16, 8, 1.5), (96, 32, 16, 1.0), (128, 128, 64, 4.0)])
+@pytest.mark.parametrize("grid", [(40, 16, 8, 1.5), (96, 32, 16, 1.0), (128, 128, 64, 4.0),
+                                  (33, 16, 8, 1.0),    # shortest chain 28 rows: 8 segments fall back to 4
+                                  (16, 8, 4, 1.0)])    # 14 rows: no segments, staged solve
 @pytest.mark.parametrize("step", [B.STEP_FEBE_HALF, B.STEP_FEBE_FULL, B.STEP_ABCN])
 def test_segmented_solve(grid, step):
     # half width 2: the chains cut into 4 or 8 row segments solved side by side, entry
