@@ -123,6 +123,22 @@ def test_fft_tile_sizes_agree(tile):
         assert np.linalg.norm(b - a) <= 1e-6 * np.linalg.norm(a)
 
 
+@pytest.mark.parametrize("bn", [16, 48])
+def test_tc_column_tile_widths(bn):
+    # the tensor-core contraction at other column-tile widths (N = 16 is the
+    # smallest MMA width at M = 128) against the oracle, both directions
+    g, ctx = pair(128, 128, 64, 4.0, policy="twothirds", precision=B.BF16X3)
+    ctx.set_tuning("tc_bn", bn)
+    flat = rand_spec(g, 4)
+    phys = ctx.backward(to_gpu_spec(flat), ctx.new_phys())
+    ref = O.backward(g, O.from_flat(g, flat))
+    assert rel(phys.double().cpu().numpy(), ref) <= 1e-6
+    u = rand_phys(g, 5)
+    spec = ctx.forward(to_gpu_phys(ctx, u), ctx.new_spec())
+    assert O.spec_rel_err(g, spec_from_gpu(g, spec), O.forward(g, u.astype(np.float32).astype(np.float64))) <= 1e-6
+    ctx.device_status()
+
+
 def test_bf16x3_device_status_clean():
     # the tensor-core kernels' bounded waits never expire on a normal run
     g, ctx = pair(128, 128, 64, 4.0, policy="twothirds", precision=B.BF16X3)
