@@ -1777,7 +1777,7 @@ static int launch_solve(mlx_ctx* c, int step, const BandLU& f, const long long* 
       auto go = [&](auto seg_tag) -> bool {
         constexpr int S = decltype(seg_tag)::value;
         const size_t pw = SegSmem<KL, S>::per_warp(c->nc, keep_s);
-        int WPB = 32 / (32 / S);                    // 4 warps (S = 4) or 8 (S = 8) per CTA
+        int WPB = S;                                // S warps per CTA, halved until the CTA fits 200 KB
         while (WPB > 1 && pw * WPB > 200 * 1024) WPB /= 2;
         if (pw * WPB > 200 * 1024) return false;
         const int G = SegSmem<KL, S>::G;
