@@ -130,9 +130,10 @@ __device__ void phi_unpack_store(const C* L, int ld, int N, int B, int M, int Nr
                                  T* __restrict__ zre, T* __restrict__ zim, bool brev, int logN) {
   const T inv = (T)1 / (T)N;
   const int R = 2 * B;
+  const int lR = __ffs(R) - 1;          // tiles are powers of two: shifts, not divisions
   for (int t = threadIdx.x; t < M * R; t += blockDim.x) {
-    const int m = t / R, rr = t % R;
-    const int b = rr % B;
+    const int m = t >> lR, rr = t & (R - 1);
+    const int b = rr & (B - 1);
     const int pm = m, pc = (N - m) & (N - 1);
     const C zm = L[b * ld + (brev ? bitrev(pm, logN) : pm)];
     const C zc = L[b * ld + (brev ? bitrev(pc, logN) : pc)];
@@ -162,6 +163,7 @@ __global__ void __launch_bounds__(256) k_phi(int N, int logN, int M, int Nr, int
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* L = reinterpret_cast<C*>(smem_raw);
   const int B = R / 2;
+  const int lR = __ffs(R) - 1;          // R and B are powers of two
   const int ld = N + 1;
   const int r0 = blockIdx.x * R;
   const int z = blockIdx.y;
@@ -170,10 +172,10 @@ __global__ void __launch_bounds__(256) k_phi(int N, int logN, int M, int Nr, int
   if constexpr (MODE == PHI_FWD) {
 #pragma unroll 8
     for (int t = threadIdx.x; t < N * R; t += blockDim.x) {
-      const int j = t / R, rr = t % R;
+      const int j = t >> lR, rr = t & (R - 1);
       const int r = r0 + rr;
       const T v = (r < Nr) ? phys[plane + (long long)j * Nr + r] : (T)0;
-      T* slot = reinterpret_cast<T*>(&L[(rr % B) * ld + j]);
+      T* slot = reinterpret_cast<T*>(&L[(rr & (B - 1)) * ld + j]);
       slot[rr < B ? 0 : 1] = v;
     }
     __syncthreads();
@@ -196,7 +198,7 @@ __global__ void __launch_bounds__(256) k_phi(int N, int logN, int M, int Nr, int
     __syncthreads();
 #pragma unroll 8
     for (int t = threadIdx.x; t < M * B; t += blockDim.x) {
-      const int m = t / B, b = t % B;
+      const int m = t >> (lR - 1), b = t & (B - 1);
       const int ra = r0 + b, rb = r0 + b + B;
       T ar = 0, ai = 0, br = 0, bi = 0;
       const long long oa = ((long long)z * M + m) * Nr;
@@ -246,9 +248,9 @@ __global__ void __launch_bounds__(256) k_phi(int N, int logN, int M, int Nr, int
     __syncthreads();
     if constexpr (MODE == PHI_BWD) {
       for (int t = threadIdx.x; t < N * R; t += blockDim.x) {
-        const int j = t / R, rr = t % R;
+        const int j = t >> lR, rr = t & (R - 1);
         const int r = r0 + rr;
-        const C v = L[(rr % B) * ld + j];
+        const C v = L[(rr & (B - 1)) * ld + j];
         if (r < Nr) phys[plane + (long long)j * Nr + r] = (rr < B) ? v.x : v.y;
       }
     } else {
@@ -269,10 +271,11 @@ __global__ void __launch_bounds__(256) k_z(int Nz, int logN, int Kz, int K, int 
   const int ld = Nz + 1;
   const int r0 = blockIdx.x * R;
   const int m = blockIdx.y;
+  const int lR = __ffs(R) - 1;          // R is a power of two
   if (!INVERSE) {
 #pragma unroll 8
     for (int t = threadIdx.x; t < Nz * R; t += blockDim.x) {
-      const int l = t / R, b = t % R;
+      const int l = t >> lR, b = t & (R - 1);
       const int r = r0 + b;
       C v; v.x = 0; v.y = 0;
       if (r < Nr) {
@@ -286,7 +289,7 @@ __global__ void __launch_bounds__(256) k_z(int Nz, int logN, int Kz, int K, int 
     __syncthreads();
 #pragma unroll 8
     for (int t = threadIdx.x; t < K * R; t += blockDim.x) {
-      const int kk = t / R, b = t % R;
+      const int kk = t >> lR, b = t & (R - 1);
       const int r = r0 + b;
       const int pos = (kk < Kz) ? kk : Nz - (K - kk);
       if (r < Nr) {
@@ -316,7 +319,7 @@ __global__ void __launch_bounds__(256) k_z(int Nz, int logN, int Kz, int K, int 
   if (!INVERSE) {
     const T inv = (T)1 / (T)Nz;
     for (int t = threadIdx.x; t < K * R; t += blockDim.x) {
-      const int kk = t / R, b = t % R;
+      const int kk = t >> lR, b = t & (R - 1);
       const int r = r0 + b;
       const int pos = (kk < Kz) ? kk : Nz - (K - kk);
       if (r < Nr) {
@@ -328,7 +331,7 @@ __global__ void __launch_bounds__(256) k_z(int Nz, int logN, int Kz, int K, int 
     }
   } else {
     for (int t = threadIdx.x; t < Nz * R; t += blockDim.x) {
-      const int l = t / R, b = t % R;
+      const int l = t >> lR, b = t & (R - 1);
       const int r = r0 + b;
       if (r < Nr) {
         const C v = L[b * ld + l];
