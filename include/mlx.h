@@ -138,11 +138,12 @@ int mlx_forward(mlx_ctx* ctx, const void* phys, void* spec, mlx_stream stream);
  * exit) instead of the context's workspace; no device memory is allocated or
  * freed.  Grids whose intermediates exceed 16 MiB
  * (element size x 2 x (K M Nr + Nz M Nr when Nz > 1)) are rejected with
- * MLX_EINVAL and a message in mlx_last_cuda_error.  The first call on a device
- * looks up the array's device address (cudaGetSymbolAddress) with that device
- * current; make it before any stream capture.  All calls on a device share the
- * array: calls whose GPU work overlaps (other streams, other contexts) race, so
- * serialise them. */
+ * MLX_EINVAL and a message in mlx_last_cuda_error, and so are device ordinals of
+ * 64 and above.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current, once per device under a lock;
+ * make it before any stream capture.  That address, like every context, does not
+ * survive cudaDeviceReset.  All calls on a device share the array: calls whose
+ * GPU work overlaps (other streams, other contexts) race, so serialise them. */
 int mlx_forward_noalloc(mlx_ctx* ctx, const void* phys, void* spec, mlx_stream stream);
 
 /* Backward transform (spectral -> physical): Eq. (2) summed at the nodes,
@@ -152,14 +153,23 @@ int mlx_backward(mlx_ctx* ctx, const void* spec, void* phys, mlx_stream stream);
 /* Nonlinear term A(s) of Eq. (10) in spectral space (transforms with the
  * pointwise products between them, Sec. 3.3):
  *   MLX_NONLIN_FKPP: A = gamma u (1 - u), Eq. (17); coeffs[0] = gamma.
- *   MLX_NONLIN_VORTEX: (psi_N, chi_N) = P[(U + v) x omega], Eq. (19): velocity
- *     and vorticity from (psi, chi) with the banded r d/dr and D_m (six backward
- *     transforms), the cross product at the nodes, three forward transforms,
- *     r^2 curl_z and r^2 div_h in spectral space (two backward, 1/r^2, two
- *     forward), then psi_N = -D_m^{-1} (curl N)_z, g = (D_m - kappa^2)^{-1} div N,
- *     chi_N = -D_m^{-1} (N_z - i kappa g).  At m = 0 the singular row of D_m is
- *     the far-field decay condition sum_n Pbar_n^0(1) s_n = 0 (zero net
- *     circulation, log-proxy coefficient 0, Sec. 3.1).  coeffs[0] = U0.
+ *   MLX_NONLIN_VORTEX: (psi_N, chi_N) = P[(U + v) x omega], Eq. (19), evaluated
+ *     harmonic by harmonic in coefficient space (no division by r at the nodes):
+ *     the r-weighted velocity and vorticity r v_r, r v_phi, v_z, r w_r, r w_phi,
+ *     w_z from (psi, chi) with the banded r d/dr (R) and D_m (six backward
+ *     transforms), at the nodes A = r N_phi, B = r N_r, C = r^2 N_z of
+ *     N = (v + U) x omega (three forward transforms), X1 = R A - i m B
+ *     (= r^2 (curl N)_z), X2 = R B + i m A (= r^2 div_h N), then with
+ *     J = multiplication by x and Q = (I - J^2) diag(-n(n+1)) = r^2 lap_h:
+ *     Q psi_N = -X1; for k != 0 [(I - J) Q - kappa^2 ell^2 (I + J)] g =
+ *     (I - J)(X2 + i kappa C) (g = (lap - kappa^2)^{-1} div N) and
+ *     (I - J) Q chi_N = i kappa ell^2 (I + J) g - (I - J) C; for k = 0
+ *     (I - J) Q chi_N = -(I - J) C (all banded, half width 3; 9 transforms).
+ *     This equals psi_N = -lap_h^{-1} (curl N)_z, chi_N = -lap_h^{-1} (N_z -
+ *     i kappa g) of Eq. (9) up to the truncation of the products.  At m = 0 the
+ *     singular first row of Q and (I - J) Q is the far-field decay condition
+ *     sum_n Pbar_n^0(1) s_n = 0 (zero net circulation, log-proxy coefficient 0,
+ *     Sec. 3.1).  coeffs[0] = U0.
  * spec_in, spec_out: device complex128 ragged (may not alias); two fields each
  * for the vortex kind. */
 int mlx_nonlinear(mlx_ctx* ctx, int kind, const double* coeffs, int ncoeffs,

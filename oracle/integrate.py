@@ -25,7 +25,7 @@ import numpy as np
 import scipy.linalg as sla
 
 from .operators import linear_operator
-from .transform import backward, forward
+from .transform import backward, forward, serial
 
 
 def fkpp_nonlinear(g, gamma):
@@ -42,14 +42,15 @@ class Stepper:
         self.L = {}
         self.lu_half = {}
         self.lu_full = {}
-        for m in range(g.M):
-            for kabs in range(g.Kz):
-                kappa = 2.0 * np.pi * kabs / g.lz
-                L = linear_operator(m, kappa, g.nc, g.ell, nu, nu_h, p)
-                I = np.eye(L.shape[0])
-                self.L[(m, kabs)] = L
-                self.lu_half[(m, kabs)] = sla.lu_factor(I - 0.5 * self.dt * L)
-                self.lu_full[(m, kabs)] = sla.lu_factor(I - self.dt * L)
+        with serial():
+            for m in range(g.M):
+                for kabs in range(g.Kz):
+                    kappa = 2.0 * np.pi * kabs / g.lz
+                    L = linear_operator(m, kappa, g.nc, g.ell, nu, nu_h, p)
+                    I = np.eye(L.shape[0])
+                    self.L[(m, kabs)] = L
+                    self.lu_half[(m, kabs)] = sla.lu_factor(I - 0.5 * self.dt * L)
+                    self.lu_full[(m, kabs)] = sla.lu_factor(I - self.dt * L)
 
     def _kabs(self, kidx):
         return abs(int(self.g.kz[kidx]))
@@ -60,6 +61,10 @@ class Stepper:
         return self.nonlinear(s)
 
     def _solve(self, lus, rhs):
+        with serial():
+            return self._solve_blocks(lus, rhs)
+
+    def _solve_blocks(self, lus, rhs):
         # a state may hold several fields: block j belongs to order m = j mod M
         out = []
         for j, blk in enumerate(rhs):
@@ -74,6 +79,10 @@ class Stepper:
         return out
 
     def apply_L(self, s):
+        with serial():
+            return self._apply_L_blocks(s)
+
+    def _apply_L_blocks(self, s):
         out = []
         for j, blk in enumerate(s):
             m = j % self.g.M

@@ -34,6 +34,7 @@ analytic fields; exact decay of closed-form diffusion solutions (Sec. 5.1).
 """
 
 from fractions import Fraction
+import functools
 import math
 
 import numpy as np
@@ -82,9 +83,15 @@ def del2h_unnormalised(m, nc, ell):
     return D / (ell * ell)
 
 
-def del2h_closed(m, nc, ell):
-    m = abs(m)
+@functools.lru_cache(maxsize=4096)
+def _del2h_closed_cached(m, nc, ell):
     return _rescale(del2h_unnormalised(m, nc, ell), m, nc)
+
+
+def del2h_closed(m, nc, ell):
+    """D_m on the orthonormal coefficients (a fresh copy; the exact rescaling is
+    computed once per (m, Nc, ell) and reused, since it does not depend on kappa)."""
+    return _del2h_closed_cached(abs(int(m)), int(nc), float(ell)).copy()
 
 
 def del2h_quadrature(m, nc, ell):

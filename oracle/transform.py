@@ -23,9 +23,22 @@ Pins: round-trip identity spectral -> physical -> spectral, numpy.fft, azimuthal
 purity (Sec. 5.1), representation errors of Sec. 5.1.
 """
 
+import contextlib
 import math
 
 import numpy as np
+
+
+def serial():
+    """Context in which the BLAS/LAPACK calls run on one thread.  The oracle's
+    per-harmonic loops apply many small (<= 1024 x 1024) dense operations, for
+    which a multithreaded BLAS is slower than one thread; the arithmetic is the
+    same either way."""
+    try:
+        from threadpoolctl import threadpool_limits
+    except ImportError:          # pragma: no cover - threadpoolctl ships with scikit-learn
+        return contextlib.nullcontext()
+    return threadpool_limits(1)
 
 
 def _dft_matrix(nout_idx, npts, sign):

@@ -2,19 +2,17 @@
 
 Sec. 3.2 and Eq. (19): a solenoidal field V = curl(psi e_z) + curl curl(chi e_z)
 (Eq. (8)) evolves as d(psi, chi)/dt = P[(U + v) x omega] + L(psi, chi), with P the
-toroidal-poloidal projection recovered from Eq. (9).  The paper does not spell out
-how the vector components are transformed or how P is evaluated; the reading
-taken here (identical in the oracle and the CUDA path) works harmonic by harmonic,
-e^{i(m phi + kappa z)}, with banded coefficient-space operators only and never
-divides by r at the nodes (division by r^2 near the axis would amplify transform
-round-off by 1/r_min^2).
+toroidal-poloidal projection recovered from the two planar Poisson problems of
+Eq. (9), grad_h^2 chi = -V_z and grad_h^2 psi = -(curl V)_z, inverted with the
+banded Laplacian of Sec. 3.1.  The paper says neither how the vector components
+are transformed nor how the right-hand sides of Eq. (9) are formed from a field
+N that also carries a gradient part (Sec. 3.2: the projection removes it).  The
+definition taken here works harmonic by harmonic, e^{i(m phi + kappa z)}:
 
 Operators on the orthonormal coefficients of order m (n = m..Nc-1):
   R  = r d/dr (tridiagonal, Sec. 3.1),  D_m = horizontal Laplacian (Eq. (5)),
   J  = multiplication by x (the Jacobi matrix: x Pbar_n = a_{n+1} Pbar_{n+1} + a_n Pbar_{n-1},
-       a_n = sqrt((n^2 - m^2)/(4 n^2 - 1))),
-  Q  = r^2 grad_h^2 = (I - J^2) diag(-n(n+1))   (from Eq. (3): r^2 grad_h^2 Pbar_n = -n(n+1)(1-x^2) Pbar_n),
-  and (1 - x) r^2 = ell^2 (1 + x) (Eq. (1)).
+       a_n = sqrt((n^2 - m^2)/(4 n^2 - 1))).
 All products of truncated matrices (truncate, then compose).
 
 velocity (from Eq. (8))      r v_r   = i m psi + i kappa R chi
@@ -25,32 +23,52 @@ vorticity (curl of Eq. (8):  omega = curl(Psi e_z) + curl curl(psi e_z),
                              r w_r   = i m Psi + i kappa R psi
                              r w_phi = -R Psi - m kappa psi
                              w_z     = -D_m psi
-At the nodes (six backward transforms): N = (v + U) x omega with the uniform
-background U = U0 e_y (U_r = U0 sin phi, U_phi = U0 cos phi; Sec. 5.3 moving frame):
-    A = r N_phi = v_z (r w_r) - (r v_r + r U_r) w_z
-    B = r N_r   = (r v_phi + r U_phi) w_z - v_z (r w_phi)
-    C = r^2 N_z = (r v_r + r U_r)(r w_phi) - (r v_phi + r U_phi)(r w_r)
-Three forward transforms, then in coefficient space
-    X1 = R A - i m B   (= r^2 (curl N)_z),     X2 = R B + i m A   (= r^2 div_h N).
-Projection N = curl(psi_N e_z) + curl curl(chi_N e_z) + grad g (Eq. (9) for the
-solenoidal part; div N = lap g removes the gradient):
+
+project_plain (the oracle's definition of P; `nonlinear` uses it):
+  1. Six backward transforms of the fields above; at the nodes divide the
+     r-weighted ones by r_i, add the uniform background U = U0 e_y
+     (U_r = U0 sin phi, U_phi = U0 cos phi; Sec. 5.3 moving frame) and form the
+     primitive N = (v + U) x omega.
+  2. A = r N_phi, B = r N_r and N_z at the nodes; three forward transforms.
+  3. X1 = R A - i m B (= r^2 (curl N)_z) and X2 = R B + i m A (= r^2 div_h N).
+  4. Two backward transforms, division by r_i^2 at the nodes, two forward
+     transforms: (curl N)_z and div_h N; then div N = div_h N + i kappa N_z.
+  5. psi_N = -lap_h^{-1} (curl N)_z  (Eq. (9));
+     k != 0: g = (D_m - kappa^2)^{-1} div N and chi_N = -lap_h^{-1} (N_z - i kappa g);
+     k == 0: chi_N = -lap_h^{-1} N_z.
+     N = curl(psi_N e_z) + curl curl(chi_N e_z) + grad g is then the Helmholtz
+     split of N, so the gradient part is removed (Sec. 3.2).
+  13 transforms per evaluation.
+
+project_banded (a second form; it is the formulation the CUDA path runs): the
+same P with every step kept in coefficient space, so that nothing is divided by
+r at the nodes.  With Q = (I - J^2) diag(-n(n+1)) = r^2 grad_h^2 (from Eq. (3):
+r^2 grad_h^2 Pbar_n = -n(n+1)(1-x^2) Pbar_n) and (1 - x) r^2 = ell^2 (1 + x)
+(Eq. (1)), the products are transformed as A = r N_phi, B = r N_r, C = r^2 N_z
+(9 transforms per evaluation) and
     Q psi_N = -X1                                                   (lap_h psi_N = -(curl N)_z, times r^2)
     [(I - J) Q - kappa^2 ell^2 (I + J)] g = (I - J)(X2 + i kappa C)   (k != 0; (lap_h - kappa^2) g = div N, times (1-x) r^2)
     (I - J) Q chi_N = i kappa ell^2 (I + J) g - (I - J) C           (lap_h chi_N = i kappa g - N_z, times (1-x) r^2)
-(g = 0 at k = 0).  Q and (I - J) Q have a zero first column at m = 0 (the constant
-has zero Laplacian); there the first row is replaced by the far-field decay
+(g = 0 at k = 0).  The two forms agree in exact arithmetic; on a truncated
+expansion they differ by the truncation of the products, which falls
+spectrally with Nr for resolved fields (pinned in tests/test_oracle_vortex.py).
+
+At m = 0 the horizontal Laplacian (and Q, (I - J) Q) has a zero first column (the
+constant has zero Laplacian); its first row is replaced by the far-field decay
 condition sum_n Pbar_n^0(1) s_n = 0 with right-hand side 0 (log-proxy coefficient
 c = 0, Sec. 3.1 / Eq. (6): exact for the zero-net-circulation vortex pair).
-
 The inverse horizontal Laplacian with the same decay row (lap_h_inv) gives the
 initial stream function psi = -lap_h^{-1} omega_z of a vortex workload.
 
 Pins (tests/test_oracle_vortex.py): J against Gauss quadrature of <Pbar_j, x Pbar_n>;
-Q against quadrature of <Pbar_j, r^2 lap_h Pbar_n>; gradient fields project to
-zero; a solenoidal field built from known (psi, chi) projects back to them; an
-axisymmetric vortex has a pure-gradient N so P(N) = 0; analytic curl fields; the
-decay-row Laplacian inverse.  The full nonlinear evolution is checked against the
-oracle only: parity unpinned beyond these properties.
+Q against quadrature of <Pbar_j, r^2 lap_h Pbar_n>; for both forms: gradient fields
+project to zero, a solenoidal field built from known (psi, chi) projects back to
+them, an axisymmetric shielded vortex has a pure-gradient N so P(N) = 0, and in a
+uniform background U0 e_y its projected forcing is the translation
+psi_N = -U0 d(psi)/dy in closed form; analytic curl fields; the decay-row Laplacian
+inverse; plain and banded forms agree to a bound that falls spectrally with Nr.
+The full nonlinear evolution is checked against the oracle only: parity unpinned
+beyond these properties.
 """
 
 import math
@@ -59,7 +77,7 @@ import numpy as np
 import scipy.linalg as sla
 
 from .operators import del2h_closed, rdr_matrix
-from .transform import backward, forward
+from .transform import backward, forward, serial
 
 
 def jacobi_matrix(m, nc):
@@ -87,6 +105,10 @@ class VortexOps:
     """Band operators and solvers of the toroidal-poloidal formulation."""
 
     def __init__(self, g):
+        with serial():
+            self._setup(g)
+
+    def _setup(self, g):
         self.g = g
         self.D = [del2h_closed(m, g.nc, g.ell) for m in range(g.M)]
         self.R = [rdr_matrix(m, g.nc) for m in range(g.M)]
@@ -115,6 +137,13 @@ class VortexOps:
                 Hd[0, :] = pbar_at_one(0, g.nc)
             self.lu_Q.append(sla.lu_factor(Qd))
             self.lu_H.append(sla.lu_factor(Hd))
+        # (D_m - kappa^2) per (m, |k|), |k| >= 1 (nonsingular: no decay row)
+        self.lu_helm = {}
+        for m in range(g.M):
+            I = np.eye(g.nc - m)
+            for kabs in range(1, g.Kz):
+                kappa = 2.0 * math.pi * kabs / g.lz
+                self.lu_helm[(m, kabs)] = sla.lu_factor(self.D[m] - kappa * kappa * I)
         self.lu_G = {}
         for m in range(g.M):
             I = np.eye(g.nc - m)
@@ -147,6 +176,10 @@ class VortexOps:
 
     def fields(self, psi, chi):
         """Spectral (r v_r, r v_phi, v_z, r w_r, r w_phi, w_z) from (psi, chi)."""
+        with serial():
+            return self._fields(psi, chi)
+
+    def _fields(self, psi, chi):
         g = self.g
         out = [[None] * g.M for _ in range(6)]
         for m in range(g.M):
@@ -167,8 +200,85 @@ class VortexOps:
                 out[f][m] = v
         return out
 
-    def project(self, A, Bf, C):
+    def _nodes(self):
+        g = self.g
+        return g.r[None, None, :], g.phi[None, :, None]
+
+    # ---------------- the oracle's definition: project_plain (13 transforms)
+    def products_plain(self, psi, chi, U0=0.0):
+        """Spectral (A, B, Nz) = (r N_phi, r N_r, N_z) of N = (U + v) x omega,
+        formed from the primitive components at the nodes (steps 1-2 above)."""
+        g = self.g
+        rvr, rvp, vz, rwr, rwp, wz = (backward(g, f) for f in self.fields(psi, chi))
+        r, phi = self._nodes()
+        vr = rvr / r + U0 * np.sin(phi)        # v_r + U_r
+        vp = rvp / r + U0 * np.cos(phi)        # v_phi + U_phi
+        wr = rwr / r
+        wp = rwp / r
+        Nr = vp * wz - vz * wp
+        Np = vz * wr - vr * wz
+        Nz = vr * wp - vp * wr
+        return forward(g, r * Np), forward(g, r * Nr), forward(g, Nz)
+
+    def project_plain(self, A, Bf, Nz):
+        """P of the field with spectral r N_phi = A, r N_r = B and N_z (steps 3-5)."""
+        g = self.g
+        X1 = [np.empty_like(A[m]) for m in range(g.M)]
+        X2 = [np.empty_like(A[m]) for m in range(g.M)]
+        with serial():
+            for m in range(g.M):
+                R = self.R[m]
+                for kk in range(g.K):
+                    X1[m][kk] = R @ A[m][kk] - 1j * m * Bf[m][kk]
+                    X2[m][kk] = R @ Bf[m][kk] + 1j * m * A[m][kk]
+        r, _ = self._nodes()
+        curl_z = forward(g, backward(g, X1) / (r * r))
+        div_h = forward(g, backward(g, X2) / (r * r))
+        with serial():
+            return self._plain_solves(curl_z, div_h, Nz)
+
+    def _plain_solves(self, curl_z, div_h, Nz):
+        g = self.g
+        psiN, chiN = [], []
+        for m in range(g.M):
+            pb = np.empty((g.K, g.nc - m), dtype=np.complex128)
+            cb = np.empty_like(pb)
+            for kk in range(g.K):
+                kap = self.kappa(kk)
+                pb[kk] = -self.lap_h_inv(m, curl_z[m][kk])
+                if g.kz[kk] != 0:
+                    divN = div_h[m][kk] + 1j * kap * Nz[m][kk]
+                    gg = self._csolve(self.lu_helm[(m, abs(int(g.kz[kk])))], divN)
+                    cb[kk] = -self.lap_h_inv(m, Nz[m][kk] - 1j * kap * gg)
+                else:
+                    cb[kk] = -self.lap_h_inv(m, Nz[m][kk])
+            psiN.append(pb)
+            chiN.append(cb)
+        return psiN, chiN
+
+    def nonlinear_plain(self, psi, chi, U0=0.0):
+        return self.project_plain(*self.products_plain(psi, chi, U0))
+
+    # ---------------- the second form: project_banded (9 transforms)
+    def products_banded(self, psi, chi, U0=0.0):
+        """Spectral (A, B, C) = (r N_phi, r N_r, r^2 N_z) of N = (U + v) x omega,
+        formed from the r-weighted fields without division by r."""
+        g = self.g
+        rvr, rvp, vz, rwr, rwp, wz = (backward(g, f) for f in self.fields(psi, chi))
+        r, phi = self._nodes()
+        ar = rvr + r * U0 * np.sin(phi)       # r (v_r + U_r)
+        ap = rvp + r * U0 * np.cos(phi)       # r (v_phi + U_phi)
+        A = vz * rwr - ar * wz
+        Bn = ap * wz - vz * rwp
+        C = ar * rwp - ap * rwr
+        return forward(g, A), forward(g, Bn), forward(g, C)
+
+    def project_banded(self, A, Bf, C):
         """P of the field with spectral r N_phi = A, r N_r = B, r^2 N_z = C."""
+        with serial():
+            return self._project_banded(A, Bf, C)
+
+    def _project_banded(self, A, Bf, C):
         g = self.g
         psiN, chiN = [], []
         for m in range(g.M):
@@ -192,33 +302,25 @@ class VortexOps:
             chiN.append(cb)
         return psiN, chiN
 
-    def nonlinear(self, psi, chi, U0=0.0):
-        """P[(U + v) x omega] for the state (psi, chi)."""
-        return self.project(*self.products(psi, chi, U0))
+    def nonlinear_banded(self, psi, chi, U0=0.0):
+        return self.project_banded(*self.products_banded(psi, chi, U0))
 
-    def products(self, psi, chi, U0=0.0):
-        """Spectral (A, B, C) = (r N_phi, r N_r, r^2 N_z) of N = (U + v) x omega."""
-        g = self.g
-        sf = self.fields(psi, chi)
-        rvr, rvp, vz, rwr, rwp, wz = (backward(g, f) for f in sf)
-        r = g.r[None, None, :]
-        phi = g.phi[None, :, None]
-        rUr = r * U0 * np.sin(phi)
-        rUp = r * U0 * np.cos(phi)
-        ar = rvr + rUr
-        ap = rvp + rUp
-        A = vz * rwr - ar * wz
-        Bn = ap * wz - vz * rwp
-        C = ar * rwp - ap * rwr
-        return forward(g, A), forward(g, Bn), forward(g, C)
+    def nonlinear(self, psi, chi, U0=0.0, form="plain"):
+        """P[(U + v) x omega] for the state (psi, chi); form "plain" (the
+        definition) or "banded"."""
+        if form == "plain":
+            return self.nonlinear_plain(psi, chi, U0)
+        if form == "banded":
+            return self.nonlinear_banded(psi, chi, U0)
+        raise ValueError(form)
 
 
-def vortex_nonlinear(g, U0=0.0):
+def vortex_nonlinear(g, U0=0.0, form="plain"):
     """Nonlinear term for a two-field state [psi blocks..., chi blocks...] (2M blocks)."""
     ops = VortexOps(g)
 
     def A(state):
         psi, chi = state[:g.M], state[g.M:]
-        pN, cN = ops.nonlinear(psi, chi, U0)
+        pN, cN = ops.nonlinear(psi, chi, U0, form)
         return pN + cN
     return A, ops

@@ -186,3 +186,105 @@ def test_norm_ratio_matches_log_form():
                     continue
                 lg = math.exp(O.ln_norm(j, m) - O.ln_norm(n, m))
                 assert abs(norm_ratio(j, n, m) / lg - 1) < 1e-12
+
+
+def _iterated_laplacian(j, kappa):
+    """(d^2/dr^2 + 1/r d/dr - 4/r^2 - kappa^2)^j of r^2 e^{-r^2/2} (the m = 2
+    profile of s_B), in closed form by sympy, as a numpy function of r."""
+    import sympy as sp
+    rs = sp.symbols("r", positive=True)
+    f = rs ** 2 * sp.exp(-rs ** 2 / 2)
+    for _ in range(j):
+        f = sp.expand(sp.diff(f, rs, 2) + sp.diff(f, rs) / rs - 4 * f / rs ** 2 - sp.Float(kappa) ** 2 * f)
+    return sp.lambdify(rs, f, "numpy")
+
+
+@pytest.mark.parametrize("p,tol", [(4, 1e-9), (6, 1e-7), (8, 1e-5)])
+@pytest.mark.parametrize("kappa", [0.0, 0.7])
+def test_hyperviscous_power_against_iterated_laplacian(p, tol, kappa):
+    # Eq. (11) with nu = 0, nu_h = 1: L s = -(-lap)^{p/2} s = -(-1)^{p/2} lap^{p/2} s,
+    # lap = D_m - kappa^2 on the harmonic (m = 2, kappa) of s_B (Eq. (13)).  The
+    # expected coefficients come from the iterated analytic Laplacian of
+    # r^2 e^{-r^2/2}; rows below Nc - m - p are untouched by the truncation.  A
+    # wrong exponent (p instead of p/2) or sign fails by O(1).
+    g = O.Grid(64, 8, 1, 2.0)
+    r, phi, z = g.nodes3()
+    s = O.forward(g, W.field_sB(r, phi, z))[2][0]
+    L = O.linear_operator(2, kappa, g.nc, g.ell, 0.0, 1.0, p)
+    f = _iterated_laplacian(p // 2, kappa)
+    exact = -(-1) ** (p // 2) * f(r) * np.cos(2 * phi) + 0 * z
+    ref = O.forward(g, exact)[2][0]
+    k = g.nc - 2 - p
+    assert np.max(np.abs((L @ s)[:k] - ref[:k])) <= tol * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("m,nc,kappa", [(0, 24, 0.0), (3, 40, 1.3), (7, 33, 0.4)])
+@pytest.mark.parametrize("p", [4, 6, 8])
+def test_dissipation_truncate_then_compose(m, nc, kappa, p):
+    # Eq. (11) read as powers of the truncated (Nc - m) x (Nc - m) Laplacian
+    # ("shifting and composing", Sec. 3.1): built here from the independent
+    # quadrature construction of D_m (Eq. (3)) and a library matrix power, with
+    # nu and nu_h both nonzero.  Compose-then-truncate would differ in the last p
+    # rows; a wrong exponent or sign everywhere.
+    ell, nu, nu_h = 1.7, 0.3, 2e-3
+    D = O.del2h_quadrature(m, nc, ell)
+    lap = D - kappa * kappa * np.eye(nc - m)
+    ref = nu * lap - nu_h * np.linalg.matrix_power(-lap, p // 2)
+    L = O.linear_operator(m, kappa, nc, ell, nu, nu_h, p)
+    assert np.max(np.abs(L - ref)) <= 1e-10 * np.max(np.abs(ref))
+    # the reading is visible: the composed power of a larger matrix, truncated
+    # afterwards, differs in the last rows
+    Dbig = O.del2h_quadrature(m, nc + p, ell)
+    lbig = Dbig - kappa * kappa * np.eye(nc + p - m)
+    ctt = np.linalg.matrix_power(-lbig, p // 2)[: nc - m, : nc - m]
+    assert np.max(np.abs(ctt[-1] - np.linalg.matrix_power(-lap, p // 2)[-1])) > 1e-3 * np.max(np.abs(ctt))
+
+
+def _pbar_lib(n, m, x):
+    """Normalised associated Legendre function from scipy's Ferrers function
+    (which carries the (-1)^m Condon-Shortley phase) and the exact norm of Eq. (7)."""
+    import scipy.special as sp
+    return (-1) ** m * sp.lpmv(m, n, x) * math.sqrt((2 * n + 1) * math.factorial(n - m)
+                                                      / (2.0 * math.factorial(n + m)))
+
+
+@pytest.mark.parametrize("m1,k1,gamma", [(2, 1, 1.0), (3, 2, 0.25)])
+def test_fkpp_product_and_two_thirds_mask(m1, k1, gamma):
+    # Eq. (17): A = gamma u (1 - u) at the nodes, forward transform, two-thirds
+    # mask (Sec. 3.3).  u = a Pbar_5^{m1}(x) cos(m1 phi) cos(kappa_{k1} z)
+    # + b Pbar_3^0(x) is band-limited so that u^2 is alias-free on the grid
+    # (2 m1 < Nphi / 2, 2 k1 <= Nz / 2, radial degrees within the Gauss rule);
+    # the retained modes of gamma u (1 - u) are then exact.  Expected values:
+    # quadrature of the analytic product on an independent 80-point Gauss rule
+    # (numpy leggauss), basis from scipy's Ferrers functions, exact DFTs on 32
+    # points per periodic direction (numpy.fft).  (m1, k1) = (2, 1) keeps the
+    # m = 4, |k| = 2 products (M = 6, Kz = 3); (3, 2) masks them (2 m1 = 6 >= M,
+    # 2 k1 = 4 >= Kz).  A missing -gamma u^2 term, a wrong sign or an aliased
+    # product fails.
+    nr, nphi, nz, ell, lz = 16, 16, 8, 1.3, 5.0
+    a, b, n1, n2 = 0.6, 0.8, 5, 3
+    g = O.Grid(nr, nphi, nz, ell, lz=lz, policy="twothirds")
+    assert (g.M, g.Kz) == (6, 3)
+    spec = O.spec_zeros(g)
+    kidx = {int(k): i for i, k in enumerate(g.kz)}
+    spec[0][0, n2] = b
+    for sgn in (1, -1):
+        spec[m1][kidx[sgn * k1], n1 - m1] = a / 4.0
+    out = O.fkpp_nonlinear(g, gamma)(spec)
+
+    xq, wq = np.polynomial.legendre.leggauss(80)
+    nf = 32
+    ph = 2 * math.pi * np.arange(nf) / nf
+    zz = lz * np.arange(nf) / nf
+    kap1 = 2 * math.pi * k1 / lz
+    u = (a * _pbar_lib(n1, m1, xq)[:, None, None] * np.cos(m1 * ph)[None, :, None]
+         * np.cos(kap1 * zz)[None, None, :] + b * _pbar_lib(n2, 0, xq)[:, None, None])
+    F = gamma * u * (1.0 - u)
+    Fh = np.fft.fft(np.fft.fft(F, axis=1), axis=2) / (nf * nf)   # [x][m][k]
+    for m in range(g.M):
+        for kk in range(g.K):
+            k = int(g.kz[kk])
+            prof = Fh[:, m, k % nf]
+            for n in range(m, g.nc):
+                exp_c = np.sum(wq * _pbar_lib(n, m, xq) * prof)
+                assert abs(out[m][kk, n - m] - exp_c) < 1e-13, (m, k, n, out[m][kk, n - m], exp_c)

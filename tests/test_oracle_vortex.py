@@ -3,8 +3,10 @@
 import math
 
 import numpy as np
+import pytest
 
 import oracle as O
+from paper_2609_18026_b300 import workloads as W
 
 
 def _grid():
@@ -15,7 +17,8 @@ def _nodes(g):
     return g.nodes3()
 
 
-def test_gradient_field_projects_to_zero():
+@pytest.mark.parametrize("form", ["plain", "banded"])
+def test_gradient_field_projects_to_zero(form):
     # N = grad g with g = f(r) cos 2phi cos z, f = r^2/(r^2+a^2)^3 (rational, so
     # analytic in the mapped coordinate and resolved to round-off as s_A of
     # Sec. 5.1): curl N = 0 and the gradient part is removed, so P(N) = (0, 0)
@@ -30,14 +33,18 @@ def test_gradient_field_projects_to_zero():
     fp = 2 * r / q ** 3 - 6 * r ** 3 / q ** 4
     A = -2 * f * np.sin(2 * phi) * np.cos(kap * z)          # r N_phi = d_phi g
     Bf = r * fp * np.cos(2 * phi) * np.cos(kap * z)         # r N_r = r d_r g
-    C = -kap * r ** 2 * f * np.cos(2 * phi) * np.sin(kap * z)   # r^2 N_z = r^2 d_z g
-    psiN, chiN = ops.project(O.forward(g, A), O.forward(g, Bf), O.forward(g, C))
+    Nz = -kap * f * np.cos(2 * phi) * np.sin(kap * z)       # N_z = d_z g
+    if form == "plain":
+        psiN, chiN = ops.project_plain(O.forward(g, A), O.forward(g, Bf), O.forward(g, Nz))
+    else:
+        psiN, chiN = ops.project_banded(O.forward(g, A), O.forward(g, Bf), O.forward(g, r ** 2 * Nz))
     scale = O.spec_norm(g, O.forward(g, f * np.cos(2 * phi) * np.cos(kap * z)))
     assert O.spec_norm(g, psiN) < 1e-9 * scale
     assert O.spec_norm(g, chiN) < 1e-9 * scale
 
 
-def test_solenoidal_field_projects_back():
+@pytest.mark.parametrize("form", ["plain", "banded"])
+def test_solenoidal_field_projects_back(form):
     # V = curl(psi e_z) + curl curl(chi e_z) with rational decaying psi (m = 2)
     # and chi (m = 1): P(V) returns (psi, chi) (Eq. (8)-(9)).
     g = _grid()
@@ -48,8 +55,10 @@ def test_solenoidal_field_projects_back():
     psi = O.forward(g, r ** 2 / q ** 2 * np.cos(2 * phi) * np.cos(kap * z))
     chi = O.forward(g, r / q ** 2 * np.cos(phi) * np.sin(kap * z))
     rvr, rvp, vz, _, _, _ = ops.fields(psi, chi)
-    r2vz = O.forward(g, r ** 2 * O.backward(g, vz))
-    pN, cN = ops.project(rvp, rvr, r2vz)
+    if form == "plain":
+        pN, cN = ops.project_plain(rvp, rvr, vz)
+    else:
+        pN, cN = ops.project_banded(rvp, rvr, O.forward(g, r ** 2 * O.backward(g, vz)))
     assert O.spec_rel_err(g, pN, psi) < 1e-8
     assert O.spec_rel_err(g, cN, chi) < 1e-8
 
@@ -70,7 +79,8 @@ def test_vorticity_fields_match_analytic_curl():
     assert np.max(np.abs(rvr)) < 1e-12 and np.max(np.abs(vz)) < 1e-12
 
 
-def test_axisymmetric_vortex_has_no_projected_forcing():
+@pytest.mark.parametrize("form", ["plain", "banded"])
+def test_axisymmetric_vortex_has_no_projected_forcing(form):
     # A shielded axisymmetric vortex (psi = -e^{-r^2}, zero net circulation):
     # N = (v_phi w_z) e_r is a pure gradient, so P(N) = 0 (the steady Euler
     # balance of a columnar vortex).
@@ -79,9 +89,71 @@ def test_axisymmetric_vortex_has_no_projected_forcing():
     r, phi, z = g.nodes3()
     psi = O.forward(g, -np.exp(-r ** 2) + 0 * phi + 0 * z)
     chi = [np.zeros_like(b) for b in psi]
-    pN, cN = ops.nonlinear(psi, chi, U0=0.0)
+    pN, cN = ops.nonlinear(psi, chi, U0=0.0, form=form)
     assert O.spec_norm(g, pN) < 1e-9 * O.spec_norm(g, psi)
     assert O.spec_norm(g, cN) < 1e-9 * O.spec_norm(g, psi)
+
+
+@pytest.mark.parametrize("form", ["plain", "banded"])
+@pytest.mark.parametrize("U0", [1.0, -1.0])
+def test_uniform_background_translates_axisymmetric_vortex(form, U0):
+    # Moving frame (Sec. 5.3): a shielded axisymmetric vortex psi = -(1 + r^2)^-2
+    # (rational, resolved to round-off; zero net circulation) in the background
+    # U = U0 e_y.  v x omega is a gradient (previous test); U x omega =
+    # U0 w_z e_x has (curl)_z = -U0 d(w_z)/dy, so psi_N = -lap_h^{-1} of it =
+    # -U0 d(psi)/dy = -U0 psi'(r) sin(phi) = -4 U0 r (1 + r^2)^-3 sin(phi) in
+    # closed form (pure translation of psi along y), and chi_N = 0 (N_z = 0,
+    # k = 0).  A sin/cos swap or a sign error in U_r = U0 sin(phi),
+    # U_phi = U0 cos(phi) moves this to cos(phi) or flips it.
+    g = O.Grid(48, 8, 1, 1.0)
+    ops = O.VortexOps(g)
+    r, phi, z = g.nodes3()
+    psi = O.forward(g, -(1.0 + r ** 2) ** -2.0 + 0 * phi + 0 * z)
+    chi = [np.zeros_like(b) for b in psi]
+    pN, cN = ops.nonlinear(psi, chi, U0=U0, form=form)
+    exact = O.forward(g, -4.0 * U0 * r * (1.0 + r ** 2) ** -3.0 * np.sin(phi) + 0 * z)
+    assert O.spec_rel_err(g, pN, exact) < 1e-8
+    assert O.spec_norm(g, cN) < 1e-9 * O.spec_norm(g, exact)
+
+
+def test_plain_and_banded_projection_converge_to_one_limit():
+    # The two evaluations of P agree in exact arithmetic and differ on a
+    # truncated expansion only by the truncation of the products.  For one
+    # resolved input (Nc0 = 32 coefficients decaying like e^{-n}, zero-padded to
+    # larger Nr) the plain - banded difference must fall as Nr grows, and both
+    # forms must approach the finest plain result.  psi converges spectrally;
+    # chi more slowly, through g = (lap - kappa^2)^{-1} div N ~ e^{-kappa r},
+    # which is smooth but not analytic in the mapped coordinate at r = inf.
+    nphi, nz = 16, 8
+    g0 = O.Grid(32, nphi, nz, 1.0, lz=8.6, policy="twothirds")
+    psi0 = O.from_flat(g0, W.random_spectral(g0.nc, g0.M, g0.Kz, seed=11, scale_decay=1.0))
+    chi0 = O.from_flat(g0, W.random_spectral(g0.nc, g0.M, g0.Kz, seed=12, scale_decay=1.0))
+
+    def pad(g, s):
+        return [np.concatenate([s[m], np.zeros((g.K, g.nc - g0.nc), complex)], axis=1) for m in range(g.M)]
+
+    def cut(s):
+        return [s[m][:, :g0.nc - m] for m in range(g0.M)]
+
+    out = {}
+    for nr in (48, 96, 192):
+        g = O.Grid(nr, nphi, nz, 1.0, lz=8.6, policy="twothirds")
+        ops = O.VortexOps(g)
+        for form in ("plain", "banded"):
+            p, c = ops.nonlinear(pad(g, psi0), pad(g, chi0), 1.0, form)
+            out[(nr, form)] = (cut(p), cut(c))
+
+    def diff(a, b):
+        return max(O.spec_rel_err(g0, a[0], b[0]), O.spec_rel_err(g0, a[1], b[1]))
+
+    d = [diff(out[(nr, "banded")], out[(nr, "plain")]) for nr in (48, 96, 192)]
+    # measured: 8.4e-6, 1.0e-7, 1.4e-9
+    assert d[0] < 5e-5 and d[1] < 1e-6 and d[2] < 2e-8
+    assert d[0] > 10 * d[1] > 100 * d[2]
+    ref = out[(192, "plain")]
+    for form in ("plain", "banded"):
+        e48, e96 = diff(out[(48, form)], ref), diff(out[(96, form)], ref)
+        assert e96 < 0.1 * e48 and e96 < 1e-6
 
 
 def test_lap_h_inverse_decay_row():
