@@ -217,6 +217,43 @@ int mlx_implicit_solve(mlx_ctx* ctx, int step, const void* s, const void* A,
 int mlx_advance(mlx_ctx* ctx, int kind, const double* coeffs, int ncoeffs,
                 void* state, void* prev_A, int nsteps, int start, mlx_stream stream);
 
+/* Integral diagnostics of one spectral scalar field (Eq. (16) and the weighted
+ * norm of the examples, Sec. 5.1), evaluated in FP64 from the coefficients with the
+ * context's FP64 basis table, whatever its transform precision; the area element
+ * is r dr = ell^2 dx / (1 - x)^2 (Eq. (1)) on the Gauss nodes:
+ *   integral = (1/Lz) int f dA dz  (the circulation Gamma when f is omega_z),
+ *   moment2  = (1/Lz) int r^2 f dA dz  (the second moment M2),
+ *   l2w      = sqrt((1/Lz) int f^2 dA dz)  (the relative weighted L2 error of two
+ *              fields is l2w(a - b) / l2w(b)),
+ *   spec_l2  = the spectral l2 norm, multiplicity 2 for m >= 1.
+ * spec: device complex128 ragged (n_spec values), 16-byte aligned.  The first call
+ * allocates a small buffer of partial sums (M K x 4 doubles) kept by the context.
+ * Synchronises `stream`.  MLX_EINVAL for NULL or misaligned pointers. */
+typedef struct {
+  double integral, moment2, l2w, spec_l2;
+} mlx_diag_out;
+int mlx_diag(mlx_ctx* ctx, const void* spec, mlx_diag_out* out, mlx_stream stream);
+
+/* Checkpoint images of a time-stepping state (no counterpart in the paper's
+ * equations; its runs restart from saved fields).  An image is a host buffer of
+ * mlx_state_bytes(ctx, kind) bytes: a header (grid, chops, ell, Lz, the implicit
+ * setup nu, nu_h, p, dt, the caller's step counter) followed by the state and
+ * A^{j-1} (complex128 ragged, one or two fields by kind).  mlx_get_state copies the
+ * device buffers state and prev_A into `host` (caller-owned, at least that many
+ * bytes); mlx_set_state checks the header against this context and copies back into
+ * the device buffers, returning the step counter in *step (may be NULL).  A
+ * mismatched grid, chop, ell, Lz or field count, or (when both the image and the
+ * context have an implicit setup) another dt, nu, nu_h or p, is MLX_EINVAL with the
+ * reason in mlx_last_cuda_error: A^{j-1} continues the AB-CN recurrence (Eq. (12))
+ * only under the same operator and step.  Both synchronise `stream`.  Resuming
+ * with mlx_advance(..., start = 0) reproduces the uninterrupted run bitwise.
+ * mlx_state_bytes returns -1 for a NULL context or an unknown kind. */
+long long mlx_state_bytes(const mlx_ctx* ctx, int kind);
+int mlx_get_state(mlx_ctx* ctx, int kind, const void* state, const void* prev_A, long long step, void* host,
+                  long long bytes, mlx_stream stream);
+int mlx_set_state(mlx_ctx* ctx, int kind, const void* host, long long bytes, void* state, void* prev_A,
+                  long long* step, mlx_stream stream);
+
 /* Launch-shape tuning (not part of the method).  Keys:
  *   "solve_cpw": real chains per warp of the banded solve, 4, 8, 16 or 32
  *                (default 8);
@@ -224,18 +261,15 @@ int mlx_advance(mlx_ctx* ctx, int kind, const double* coeffs, int ncoeffs,
  *   "solve_keep_s": 1 (default) = the staged solve keeps a shared-memory copy
  *                of s for the AB-CN "- s" (no global re-read); 0 = re-read s (a
  *                smaller CTA; mlx_batch_create sets 0 on its members).
- *   "solve_direct": 1 = banded-solve variant that keeps only the solution
- *                columns in shared memory for the whole solve and streams the
- *                factor rows through small per-warp rings (cp.async, 8 rows ahead);
- *                2 = lean variant: 32 (or 16, "solve_lean_cpw") chains per warp,
- *                the factors read as per-row records packed at setup (one
- *                contiguous 16-byte-aligned block per row and |k|, cp.async 12 rows
- *                ahead), the eliminated values in a global scratch of about
- *                M * Kz * 4 * Nc doubles (allocated when 2 is first set;
- *                MLX_ENOMEM if that fails);
- *                default 2 for hyperviscous bands (half width >= 4, set by
- *                mlx_implicit_setup), else 0.  Every variant other than
- *                "solve_ir" gives bitwise-equal results.
+ *   "solve_direct": 2 = lean banded-solve variant: 32 (or 16, "solve_lean_cpw")
+ *                chains per warp, the factors read as per-row records packed at
+ *                setup (one contiguous 16-byte-aligned block per row and |k|,
+ *                cp.async 12 rows ahead), the eliminated values in a global scratch
+ *                of about M * Kz * 4 * Nc doubles (allocated when 2 is first set;
+ *                MLX_ENOMEM if that fails); 0 = the staged (or, at half width 2,
+ *                segmented) solve.  Default 2 for hyperviscous bands (half width
+ *                >= 4, set by mlx_implicit_setup), else 0.  The staged and lean
+ *                variants give bitwise-equal results.
  *   "phi_tile", "z_tile": radii per CTA of the phi and z transform kernels,
  *                2, 4, 8, 16 or 32; 0 (default) = the largest tile whose grid
  *                still has 2 (phi) or 4 (z) CTAs per SM.
@@ -250,21 +284,6 @@ int mlx_advance(mlx_ctx* ctx, int kind, const double* coeffs, int ncoeffs,
  *                bitwise; 0 = off.
  *   "solve_lean_cpw": real chains per warp of the lean variant, 16 or 32
  *                (default 32).
- *   "solve_direct_cpw": real chains per warp of the ring-staged variant, 8, 16 or 32
- *                (default 8: fewer lanes per warp, more warps per SM to hide the
- *                FP64 latency).
- *   "solve_ir":  1 = the implicit step (I - c L) x = b by mixed-precision
- *                iterative refinement: the band recurrence runs in FP32 with the
- *                FP32-rounded factors, and FP64 residuals b - (I - c L) x from the
- *                stored FP64 band correct x until the correction is below 2^-50 |x|
- *                (FP64 level) or stops contracting (the FP64 residual's rounding
- *                floor, about kappa u |x|), at most "solve_ir_max" times (1..30,
- *                default 8).  Default 0 (measured slower than the FP64 recurrence
- *                at 64^3 to 128^2 x 64).  Grids whose staging exceeds 200 KB of shared memory
- *                (Nc > 164 at half width 2) use the FP64 recurrence.  A chain
- *                whose last correction is still above 2^-20 |x| makes
- *                mlx_device_status return MLX_ENUMERIC.  The projection and
- *                Laplacian solves always use the FP64 recurrence.
  *   "tc_bn":     column-tile width of the MLX_BF16X3 contraction (16..256; the
  *                width actually used is rounded to a multiple of 16 that
  *                splits the 2K columns evenly);
@@ -300,15 +319,14 @@ int mlx_batch_advance(mlx_batch* batch, const int* kinds, const double* coeffs, 
 
 /* Choose the launch shapes of ctx for its nonlinear `kind` by timing candidates
  * with CUDA events on the context's temporaries: the tensor-core column-tile
- * width (MLX_BF16X3 only) and the banded solve's chains per warp and warps per
- * CTA.  Results are cached in the text file cache_path (may be NULL), one line
+ * width (MLX_BF16X3 only) and the banded-solve variant and shape.  Results are
+ * cached in the text file cache_path (may be NULL), one line
  * "sizes precision kind band|bn cpw wpb"; a cached entry is applied without
- * timing.  chosen (may be NULL) receives {bn, cpw, wpb, from_cache}; cpw = wpb = 0
- * denotes the ring-staged solve variant ("solve_direct" 1), cpw = 2 (wpb = 0) the
- * lean variant ("solve_direct" 2), cpw = 1 (wpb = 0) the mixed-precision
- * refinement variant ("solve_ir").  The
- * context's temporaries are overwritten; call it before advancing.
- * Synchronises `stream`. */
+ * timing.  chosen (may be NULL) receives {bn, cpw, wpb, from_cache}; cpw = 0
+ * (wpb = 0) denotes the segmented solve ("solve_seg" 8, half width 2 only),
+ * cpw = 2 (wpb = 0) the lean variant ("solve_direct" 2), otherwise the staged
+ * solve with cpw chains per warp and wpb warps per CTA.  The context's
+ * temporaries are overwritten; call it before advancing.  Synchronises `stream`. */
 int mlx_autotune(mlx_ctx* ctx, int kind, const double* coeffs, int ncoeffs, const char* cache_path,
                  int* chosen, mlx_stream stream);
 
@@ -406,23 +424,29 @@ int mlx_sur_advance(mlx_ctx* ctx, mlx_sur* sur, void* state, int nsub, double U0
                     int* accepted, double* residual, mlx_stream stream);
 
 /* ---- measurement support (not part of the method) ----
- * Opt-in per-launch timing: with enable != 0 every kernel launch of this context
- * is bracketed by CUDA events recorded on its stream, and mlx_advance launches
- * its steps directly instead of replaying a CUDA graph.  Enabling or disabling
- * resets the counters.  mlx_timing_read synchronises on the recorded events and
- * returns, for kernel id 0 <= kernel < mlx_kernel_count(), the number of timed
- * launches and their summed device time in milliseconds.  mlx_kernel_name gives
- * a stable short name per id ("" when out of range). */
+ * Opt-in per-launch timing.  enable = 1: every kernel launch of this context is
+ * bracketed by CUDA events recorded on its stream, and mlx_advance launches its
+ * steps directly instead of replaying a CUDA graph.  enable = 2: mlx_advance
+ * captures its two-step graph with an event-record node before and after every
+ * kernel node and replays it pair by pair, reading the node timings after each
+ * replay (host synchronisation between replays; inside a replay the kernels run
+ * back to back as in the cached graph).  enable = 0 turns timing off; other values
+ * are MLX_EINVAL.  Changing the mode resets the counters.  mlx_timing_read
+ * synchronises on the recorded events and returns, for kernel id
+ * 0 <= kernel < mlx_kernel_count(), the number of timed launches and their summed
+ * device time in milliseconds.  mlx_kernel_name gives a stable short name per id
+ * ("" when out of range). */
 int mlx_timing(mlx_ctx* ctx, int enable);
 int mlx_timing_read(mlx_ctx* ctx, int kernel, long long* launches, double* total_ms);
 int mlx_kernel_count(void);
 const char* mlx_kernel_name(int kernel);
 
-/* Device status: synchronises the device, returns MLX_ETIMEOUT (and clears the
- * word) if a kernel of this context gave up a bounded wait since the last call,
- * MLX_ENUMERIC if a refined solve did not reach FP64 level ("solve_ir"), else
- * MLX_OK.  Kernels that give up skip their remaining work and release their
- * resources; their outputs are then undefined. */
+/* Device status: synchronises the device, returns MLX_ETIMEOUT if a kernel of this
+ * context gave up a bounded wait since the last call, else MLX_ENUMERIC if a
+ * nonlinear-product kernel (the Fisher-KPP reaction or the vortex cross product)
+ * met a non-finite value (a blown-up or NaN state), else MLX_OK; the word is
+ * cleared by the read.  Kernels that give up a wait skip their remaining work and
+ * release their resources; their outputs are then undefined. */
 int mlx_device_status(mlx_ctx* ctx);
 
 #ifdef __cplusplus

@@ -36,6 +36,6 @@ from .transform import (forward, backward, to_flat, from_flat,  # noqa: F401
 from .operators import (del2h_closed, del2h_quadrature, rdr_matrix,  # noqa: F401
                         linear_operator)
 from .integrate import Stepper, fkpp_nonlinear  # noqa: F401
-from .diagnostics import weighted_l2, circulation, second_moment  # noqa: F401
+from .diagnostics import weighted_l2, l2w, circulation, second_moment  # noqa: F401
 from .vortex import VortexOps, vortex_nonlinear  # noqa: F401
 from . import surrogate  # noqa: F401

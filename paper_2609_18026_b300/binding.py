@@ -24,6 +24,7 @@ EXPORTS = ("mlx_strerror", "mlx_last_cuda_error", "mlx_create", "mlx_destroy", "
            "mlx_implicit_setup", "mlx_implicit_solve", "mlx_advance",
            "mlx_timing", "mlx_timing_read", "mlx_kernel_count", "mlx_kernel_name",
            "mlx_set_tuning", "mlx_device_status", "mlx_forward_noalloc",
+           "mlx_diag", "mlx_state_bytes", "mlx_get_state", "mlx_set_state",
            "mlx_vortex_setup", "mlx_lap_h_solve",
            "mlx_batch_create", "mlx_batch_destroy", "mlx_batch_advance", "mlx_autotune",
            "mlx_sur_create", "mlx_sur_destroy", "mlx_sur_param_count", "mlx_sur_get_params",
@@ -50,6 +51,11 @@ class Info(ctypes.Structure):
                 ("nc", ctypes.c_int), ("M", ctypes.c_int), ("Kz", ctypes.c_int), ("K", ctypes.c_int),
                 ("n_phys", ctypes.c_longlong), ("n_spec", ctypes.c_longlong),
                 ("precision", ctypes.c_int), ("ell", ctypes.c_double), ("lz", ctypes.c_double)]
+
+
+class DiagOut(ctypes.Structure):
+    _fields_ = [("integral", ctypes.c_double), ("moment2", ctypes.c_double),
+                ("l2w", ctypes.c_double), ("spec_l2", ctypes.c_double)]
 
 
 _lib = None
@@ -85,6 +91,11 @@ def load():
     lib.mlx_set_tuning.argtypes = [vp, ctypes.c_char_p, i]
     lib.mlx_device_status.argtypes = [vp]
     lib.mlx_forward_noalloc.argtypes = [vp, vp, vp, vp]
+    lib.mlx_diag.argtypes = [vp, vp, ctypes.POINTER(DiagOut), vp]
+    lib.mlx_state_bytes.argtypes = [vp, i]
+    lib.mlx_state_bytes.restype = ctypes.c_longlong
+    lib.mlx_get_state.argtypes = [vp, i, vp, vp, ctypes.c_longlong, vp, ctypes.c_longlong, vp]
+    lib.mlx_set_state.argtypes = [vp, i, vp, ctypes.c_longlong, vp, vp, ctypes.POINTER(ctypes.c_longlong), vp]
     lib.mlx_vortex_setup.argtypes = [vp, vp]
     lib.mlx_lap_h_solve.argtypes = [vp, vp, vp, vp]
     lib.mlx_batch_create.argtypes = [ctypes.POINTER(vp), i, ctypes.POINTER(vp)]
@@ -234,8 +245,35 @@ class Context:
         self._check(self.lib.mlx_lap_h_solve(self._h, _ptr(rhs), _ptr(out), _stream(stream)))
         return out
 
+    def diag(self, spec, stream=None):
+        """dict(integral, moment2, l2w, spec_l2) of a spectral scalar field (mlx_diag)."""
+        o = DiagOut()
+        self._check(self.lib.mlx_diag(self._h, _ptr(spec), ctypes.byref(o), _stream(stream)))
+        return dict(integral=o.integral, moment2=o.moment2, l2w=o.l2w, spec_l2=o.spec_l2)
+
+    def state_bytes(self, kind):
+        return int(self.lib.mlx_state_bytes(self._h, kind))
+
+    def get_state(self, kind, state, prev_A, step=0, stream=None):
+        """Checkpoint image (bytes) of (state, prev_A) with a step counter."""
+        n = self.state_bytes(kind)
+        buf = ctypes.create_string_buffer(n)
+        self._check(self.lib.mlx_get_state(self._h, kind, _ptr(state), _ptr(prev_A), int(step), buf, n,
+                                           _stream(stream)))
+        return buf.raw
+
+    def set_state(self, kind, image, state, prev_A, stream=None):
+        """Restore a checkpoint image into (state, prev_A); returns its step counter."""
+        buf = ctypes.create_string_buffer(bytes(image), len(image))
+        step = ctypes.c_longlong()
+        self._check(self.lib.mlx_set_state(self._h, kind, buf, len(image), _ptr(state), _ptr(prev_A),
+                                           ctypes.byref(step), _stream(stream)))
+        return step.value
+
     def timing(self, enable):
-        self._check(self.lib.mlx_timing(self._h, int(bool(enable))))
+        """0 off; 1 (or True) direct launches bracketed by events; 2 graph replays with
+        event-record nodes around every kernel node."""
+        self._check(self.lib.mlx_timing(self._h, int(enable)))
 
     def timing_read(self):
         """{kernel name: (launches, total ms)} for kernels launched while timing was on."""

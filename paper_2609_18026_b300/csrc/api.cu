@@ -23,8 +23,6 @@ void free_ctx(mlx_ctx* c) {
                   c->d_spec1, c->d_spec2, c->d_spec3, c->d_band_off, c->d_Bplus,
                   c->lu_half.U, c->lu_half.L, c->lu_half.piv, c->lu_half.invd,
                   c->lu_full.U, c->lu_full.L, c->lu_full.piv, c->lu_full.invd,
-                  c->lu_half.U32, c->lu_half.L32, c->lu_half.invd32,
-                  c->lu_full.U32, c->lu_full.L32, c->lu_full.invd32,
                   c->d_Wb, c->d_Pb, c->d_arowW, c->d_arowP, c->d_tc_fwd, c->d_tc_bwd, c->d_err,
                   c->lu_lap.U, c->lu_lap.L, c->lu_lap.piv, c->lu_lap.invd,
                   c->lu_helm.U, c->lu_helm.L, c->lu_helm.piv, c->lu_helm.invd, c->d_lap_off,
@@ -34,11 +32,12 @@ void free_ctx(mlx_ctx* c) {
                   c->lu_half.FS, c->lu_half.BS, c->lu_full.FS, c->lu_full.BS, c->lu_lap.FS, c->lu_lap.BS,
                   c->lu_helm.FS, c->lu_helm.BS, c->lu_Q.FS, c->lu_Q.BS, c->lu_H.FS, c->lu_H.BS,
                   c->lu_G.FS, c->lu_G.BS, c->lu_half.PHf, c->lu_half.PHb, c->lu_half.PSf,
-                  c->lu_full.PHf, c->lu_full.PHb, c->lu_full.PSf};
+                  c->lu_full.PHf, c->lu_full.PHb, c->lu_full.PSf, c->d_diag};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   for (auto& p : c->timing.pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
+  for (auto& p : c->timing.captured) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
   for (auto e : c->timing.pool) cudaEventDestroy(e);
   delete c;
 }
@@ -288,9 +287,6 @@ int mlx_implicit_setup(mlx_ctx* c, double nu, double nu_h, int p, double dt, mlx
     if (rc) return rc;
     c->solve_direct = 2;
   }
-  // the refinement variant is opt-in: at the sizes measured it is slower than the
-  // staged FP64 recurrence (one warp of chains per SM leaves its latencies exposed)
-  c->solve_ir = 0;
   c->implicit_ready = false;
   int rc = mlx_band_setup(c, (cudaStream_t)stream);
   if (rc) return rc;
@@ -334,13 +330,46 @@ int mlx_advance(mlx_ctx* c, int kind, const double* coeffs, int ncoeffs, void* s
     --nsteps;
   }
   const int pairs = nsteps / 2;
-  if (pairs > 0 && c->timing.on) {
-    // instrumented mode: the same two-step sequence launched directly so that
+  if (pairs > 0 && c->timing.on && c->timing.mode == 1) {
+    // instrumented mode 1: the same two-step sequence launched directly so that
     // every kernel is bracketed by CUDA events
     for (int i = 0; i < pairs; ++i) {
       if ((rc = abcn_step(c, kind, c0, s, c->d_specA, Ap, c->d_spec1, st))) return rc;
       if ((rc = abcn_step(c, kind, c0, c->d_spec1, Ap, c->d_specA, s, st))) return rc;
     }
+  } else if (pairs > 0 && c->timing.on) {
+    // instrumented mode 2: the two-step graph with an event-record node before and
+    // after every kernel node, replayed pair by pair; after each replay the node
+    // timings are read (the replays are separated by a host synchronisation, the
+    // kernels inside one replay run back to back as in the cached graph)
+    for (auto& p : c->timing.captured) { c->timing.pool.push_back(p.a); c->timing.pool.push_back(p.b); }
+    c->timing.captured.clear();
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    MLX_CUDA_TRY(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+    rc = abcn_step(c, kind, c0, s, c->d_specA, Ap, c->d_spec1, c->cap_stream);
+    if (!rc) rc = abcn_step(c, kind, c0, c->d_spec1, Ap, c->d_specA, s, c->cap_stream);
+    cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
+    if (rc) { if (g) cudaGraphDestroy(g); return rc; }
+    if (e != cudaSuccess) { c->last_err = cudaGetErrorString(e); return MLX_ECUDA; }
+    e = cudaGraphInstantiate(&exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) { c->last_err = cudaGetErrorString(e); return MLX_ECUDA; }
+    for (int i = 0; i < pairs && !rc; ++i) {
+      e = cudaGraphLaunch(exec, st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+      for (auto& p : c->timing.captured) {
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, p.a, p.b);
+        c->timing.launches[p.kid] += 1;
+        c->timing.ms[p.kid] += ms;
+      }
+      if (e != cudaSuccess) { c->last_err = cudaGetErrorString(e); rc = MLX_ECUDA; }
+    }
+    cudaGraphExecDestroy(exec);
+    for (auto& p : c->timing.captured) { c->timing.pool.push_back(p.a); c->timing.pool.push_back(p.b); }
+    c->timing.captured.clear();
+    if (rc) return rc;
   } else if (pairs > 0) {
     // two steps per graph: (s, A_prev) -> (spec1, specA) -> (s, A_prev), no copies
     mlx_ctx::GraphKey key{state, prev_A, kind, c0};
@@ -392,30 +421,9 @@ int mlx_set_tuning(mlx_ctx* c, const char* key, int value) {
     c->graphs.clear();
     return MLX_OK;
   }
-  if (strcmp(key, "solve_ir") == 0) {
-    if (value != 0 && value != 1) return MLX_EINVAL;
-    c->solve_ir = value;
-    for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
-    c->graphs.clear();
-    return MLX_OK;
-  }
-  if (strcmp(key, "solve_ir_max") == 0) {
-    if (value < 1 || value > 30) return MLX_EINVAL;
-    c->solve_ir_max = value;
-    for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
-    c->graphs.clear();
-    return MLX_OK;
-  }
   if (strcmp(key, "solve_keep_s") == 0) {
     if (value != 0 && value != 1) return MLX_EINVAL;
     c->solve_keep_s = value;
-    for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
-    c->graphs.clear();
-    return MLX_OK;
-  }
-  if (strcmp(key, "solve_direct_cpw") == 0) {
-    if (value != 8 && value != 16 && value != 32) return MLX_EINVAL;
-    c->solve_direct_cpw = value;
     for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
     c->graphs.clear();
     return MLX_OK;
@@ -449,7 +457,7 @@ int mlx_set_tuning(mlx_ctx* c, const char* key, int value) {
     return MLX_OK;
   }
   if (strcmp(key, "solve_direct") == 0) {
-    if (value < 0 || value > 2) return MLX_EINVAL;
+    if (value != 0 && value != 2) return MLX_EINVAL;
     if (value == 2) {
       const int rc = mlx_solve_scratch(c);
       if (rc) return rc;
@@ -511,7 +519,9 @@ int mlx_timing(mlx_ctx* c, int enable) {
   for (auto& p : c->timing.pending) { c->timing.pool.push_back(p.a); c->timing.pool.push_back(p.b); }
   c->timing.pending.clear();
   for (int k = 0; k < KID_COUNT; ++k) { c->timing.launches[k] = 0; c->timing.ms[k] = 0.0; }
+  if (enable < 0 || enable > 2) return MLX_EINVAL;
   c->timing.on = enable != 0;
+  c->timing.mode = enable;
   return MLX_OK;
 }
 

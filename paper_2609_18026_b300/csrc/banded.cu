@@ -13,8 +13,8 @@
 //   LU of I - c L, c = dt/2 (half) and dt (full), partial pivoting over the kl
 //   rows below the diagonal: U row i holds U_ii then columns i+1..i+2kl divided
 //   by U_ii (slot t = column - i), L multipliers [N][kl], pivot rows, 1/U_ii.
-// One thread per system factorises.  The solve is described at k_band_solve; the
-// mixed-precision refinement variant at k_band_solve_ir.
+// One thread per system factorises.  The solve variants (staged, segmented, lean)
+// are described at their kernels; all use these FP64 factors.
 #include "mlx_internal.cuh"
 
 #include <type_traits>
@@ -917,223 +917,6 @@ __global__ void k_band_solve_seg(int M, int nc, int Kz, int K, int groups_per_m,
   }
 }
 
-// FP32 copy of a factor array
-__global__ void k_to_f32(long long n, const double* __restrict__ a, float* __restrict__ b) {
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) b[i] = (float)a[i];
-}
-
-// Shared-memory layout of the refinement variant, per warp (32 real chains =
-// 8 values of |k| x {+k, -k} x {Re, Im}; rows i < N):
-//   Bv [N][32] double   right-hand sides b
-//   X  [N][32] double   solutions
-//   Bb [N][8][W] double FP64 band rows of Bplus (the residual's matrix)
-//   Y  [N][32] float    FP32 work columns
-//   Uf [N][8][W] float, Lf [N][8][KL] float, Df [N][8] float   FP32 factors
-//   Pi [N][8] int       pivot rows
-template <int KL>
-struct IrSmem {
-  static constexpr int W = 2 * KL + 1;
-  __host__ __device__ static size_t bytes(int N) {
-    const size_t b = (size_t)N * (32 * 8 * 2 + 8 * W * 8 + 32 * 4 + 8 * (W + KL + 1) * 4 + 8 * 4);
-    return (b + 15) / 16 * 16;
-  }
-};
-
-// One FP32 banded solve of the lane's chain (column y[i * 32], i < N) with the
-// FP32-rounded factors staged in shared memory (stride 8 |k| per row; kk the
-// lane's |k| slot): forward elimination with the row interchanges, then back
-// substitution, in place.
-template <int KL>
-__device__ __forceinline__ void solve_chain_f32(float* y, int N, int kk, const float* __restrict__ Uf,
-                                                const float* __restrict__ Lf, const float* __restrict__ Df,
-                                                const int* __restrict__ Pi) {
-  constexpr int W = 2 * KL + 1;
-  float w[KL + 1];
-#pragma unroll
-  for (int q = 0; q < KL; ++q) w[q + 1] = (q < N) ? y[q * 32] : 0.f;
-#pragma unroll 4
-  for (int j = 0; j < N; ++j) {
-    const int d = Pi[j * 8 + kk] - j;
-    const float* l = Lf + (j * 8 + kk) * KL;
-#pragma unroll
-    for (int q = 0; q < KL; ++q) w[q] = w[q + 1];
-    w[KL] = (j + KL < N) ? y[(j + KL) * 32] : 0.f;
-#pragma unroll
-    for (int q = 1; q <= KL; ++q)
-      if (q == d) { const float t = w[0]; w[0] = w[q]; w[q] = t; }
-    y[j * 32] = w[0];
-#pragma unroll
-    for (int q = 1; q <= KL; ++q) w[q] = fmaf(-l[q - 1], w[0], w[q]);
-  }
-  float x[W];
-#pragma unroll
-  for (int q = 0; q < W; ++q) x[q] = 0.f;
-#pragma unroll 4
-  for (int i = N - 1; i >= 0; --i) {
-    const float* u = Uf + (i * 8 + kk) * W;
-    float acc = y[i * 32] * Df[i * 8 + kk];
-#pragma unroll
-    for (int q = 2 * KL; q >= 1; --q) acc = fmaf(-u[q], x[q], acc);
-    y[i * 32] = acc;
-#pragma unroll
-    for (int q = 2 * KL; q >= 2; --q) x[q] = x[q - 1];
-    x[1] = acc;
-  }
-}
-
-// Mixed-precision iterative refinement of the implicit step (I - c L) x = b
-// (c = dt/2, or dt for the full FE-BE step).  On this GPU a dependent FP64
-// operation costs ~130 cycles, so the FP64 band recurrence is latency-bound; an
-// FP32 recurrence is far cheaper.  Each lane owns one real chain (32 per warp,
-// one warp per CTA); factors, pivots and the FP64 band are staged in shared
-// memory with asynchronous copies first:
-//   x_0 = solve32(b);  repeat  r = b - A x (FP64, from the FP64 band of A),
-//                              x += solve32(r)
-// until the correction is below 2^-50 |x| (FP64 level) or stops contracting (the
-// rounding floor of the FP64 residual, about kappa u |x|), at most max_refine times.
-// The residual rows are independent, so they are formed eight at a time (eight
-// independent FP64 accumulation chains in flight).  The residual uses
-// A = alpha I + beta Bplus (Bplus = I + dt/2 L is stored in FP64): alpha = 2,
-// beta = -1 for I - dt/2 L and alpha = 3, beta = -2 for I - dt L.
-// With kappa(A) u_32 well below 1 every correction gains log10(1/(kappa u_32))
-// digits; the converged x carries the FP64 residual's accuracy.  A chain whose
-// last correction is still above 2^-20 |x| sets bit 8 of the status word.
-template <int KL>
-__global__ void __launch_bounds__(32) k_band_solve_ir(int M, int nc, int Kz, int K, int groups_per_m, int step,
-                                                      double dt, const long long* __restrict__ soff,
-                                                      const long long* __restrict__ band_off,
-                                                      const float* __restrict__ U32, const float* __restrict__ L32,
-                                                      const int* __restrict__ piv,
-                                                      const float* __restrict__ invd32,
-                                                      const double* __restrict__ Bp, double alpha, double beta,
-                                                      int max_refine, const double* __restrict__ s,
-                                                      const double* __restrict__ A, const double* __restrict__ Ap,
-                                                      double* __restrict__ out, int* __restrict__ err) {
-  constexpr int W = 2 * KL + 1;
-  constexpr int G = 8;
-  constexpr int RB = 8;   // residual rows per batch
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int lane = threadIdx.x;
-  const int gw = blockIdx.x;
-  if (gw >= M * groups_per_m) return;
-  const int m = gw / groups_per_m;
-  const int k0 = (gw % groups_per_m) * G;
-  const int gcnt = min(G, Kz - k0);
-  const int N = nc - m;
-  double* Bv = reinterpret_cast<double*>(smem_raw);             // [N][32]
-  double* X = Bv + (size_t)N * 32;                                // [N][32]
-  double* Bb = X + (size_t)N * 32;                                // [N][8][W]
-  float* Y = reinterpret_cast<float*>(Bb + (size_t)N * G * W);    // [N][32]
-  float* Uf = Y + (size_t)N * 32;                                 // [N][8][W]
-  float* Lf = Uf + (size_t)N * G * W;                             // [N][8][KL]
-  float* Df = Lf + (size_t)N * G * KL;                            // [N][8]
-  int* Pi = reinterpret_cast<int*>(Df + (size_t)N * G);           // [N][8]
-  const long long fb = band_off[m];
-  const long long sm = soff[m];
-  // stage the factor rows and the FP64 band (row (i, kabs) at fb + i Kz + kabs)
-  for (int e = lane; e < N * gcnt * W; e += 32) {
-    const int i = e / (gcnt * W), rem = e - i * gcnt * W;
-    const int kq = rem / W, q = rem - kq * W;
-    const long long row = fb + (long long)i * Kz + k0 + kq;
-    cp_async4(Uf + ((size_t)i * G + kq) * W + q, U32 + row * W + q);
-    cp_async8(Bb + ((size_t)i * G + kq) * W + q, Bp + row * W + q);
-  }
-  for (int e = lane; e < N * gcnt * KL; e += 32) {
-    const int i = e / (gcnt * KL), rem = e - i * gcnt * KL;
-    const int kq = rem / KL, q = rem - kq * KL;
-    cp_async4(Lf + ((size_t)i * G + kq) * KL + q, L32 + (fb + (long long)i * Kz + k0 + kq) * KL + q);
-  }
-  for (int e = lane; e < N * gcnt; e += 32) {
-    const int i = e / gcnt, kq = e - i * gcnt;
-    const long long row = fb + (long long)i * Kz + k0 + kq;
-    cp_async4(Df + (size_t)i * G + kq, invd32 + row);
-    cp_async4(Pi + (size_t)i * G + kq, piv + row);
-  }
-  cp_async_commit();
-  const double h = (step == MLX_STEP_FEBE_FULL) ? dt : 0.5 * dt;
-#pragma unroll 8
-  for (int e = lane; e < N * 4 * gcnt; e += 32) {
-    const int c = e / N, i = e - c * N;
-    const int kq = c >> 2, sgn = (c >> 1) & 1, part = c & 1;
-    const int kabs = k0 + kq;
-    if (sgn && kabs == 0) continue;
-    const int kidx = sgn ? K - kabs : kabs;
-    const long long o = 2 * (sm + (long long)kidx * N + i) + part;
-    double r;
-    if (step == MLX_STEP_ABCN) r = rhs_abcn(s[o], A ? A[o] : 0.0, Ap ? Ap[o] : 0.0, A, Ap, dt);
-    else r = rhs_febe(s[o], A ? A[o] : 0.0, A, h);
-    Bv[(size_t)i * 32 + c] = r;
-  }
-  cp_async_wait_all();
-  __syncwarp();
-  const int c = lane;
-  const int kk = c >> 2, sgn = (c >> 1) & 1;
-  const bool valid = c < 4 * gcnt && !(sgn && k0 + kk == 0);
-  if (valid) {
-    float* y = Y + c;
-    double* x = X + c;
-    const double* b = Bv + c;
-    for (int i = 0; i < N; ++i) y[i * 32] = (float)b[i * 32];
-    solve_chain_f32<KL>(y, N, kk, Uf, Lf, Df, Pi);
-    float xmax = 0.f;
-    for (int i = 0; i < N; ++i) {
-      const float v = y[i * 32];
-      x[i * 32] = (double)v;
-      xmax = fmaxf(xmax, fabsf(v));
-    }
-    bool conv = (xmax == 0.f);
-    float dprev = 0.f, dmax = 0.f;
-    for (int it = 0; it < max_refine && !conv; ++it) {
-      for (int i0 = 0; i0 < N; i0 += RB) {
-        double t[RB];
-#pragma unroll
-        for (int r = 0; r < RB; ++r) t[r] = 0.0;
-#pragma unroll
-        for (int o = 0; o < W; ++o) {
-#pragma unroll
-          for (int r = 0; r < RB; ++r) {
-            const int i = i0 + r, j = i + o - KL;
-            if (i < N && j >= 0 && j < N) t[r] = fma(Bb[((size_t)i * G + kk) * W + o], x[j * 32], t[r]);
-          }
-        }
-#pragma unroll
-        for (int r = 0; r < RB; ++r) {
-          const int i = i0 + r;
-          if (i < N) y[i * 32] = (float)fma(-beta, t[r], fma(-alpha, x[i * 32], b[i * 32]));
-        }
-      }
-      solve_chain_f32<KL>(y, N, kk, Uf, Lf, Df, Pi);
-      dmax = 0.f;
-#pragma unroll 8
-      for (int i = 0; i < N; ++i) {
-        const float d = y[i * 32];
-        x[i * 32] += (double)d;
-        dmax = fmaxf(dmax, fabsf(d));
-      }
-      // converged to FP64 level, or no longer contracting: the corrections have
-      // reached the rounding floor of the FP64 residual (about kappa u |x|)
-      conv = dmax <= 0x1p-50f * xmax || (it > 0 && dmax > 0.25f * dprev);
-      dprev = dmax;
-    }
-    // a refinement that never got below FP32-level corrections is a failure
-    if (dmax > 0x1p-20f * xmax) atomicOr(err, 8);
-  }
-  __syncwarp();
-#pragma unroll 8
-  for (int e = lane; e < N * 4 * gcnt; e += 32) {
-    const int cc = e / N, i = e - cc * N;
-    const int kq = cc >> 2, sg = (cc >> 1) & 1, pt = cc & 1;
-    const int kabs = k0 + kq;
-    if (sg && kabs == 0) continue;
-    const int kidx = sg ? K - kabs : kabs;
-    const long long o = 2 * (sm + (long long)kidx * N + i) + pt;
-    double v = X[(size_t)i * 32 + cc];
-    if (step == MLX_STEP_ABCN) v -= s[o];
-    out[o] = v;
-  }
-}
-
 __global__ void k_axpby(long long n, double a, const double2* __restrict__ x, double b,
                         const double2* __restrict__ y, double2* __restrict__ out) {
   long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1153,7 +936,7 @@ int mlx_band_setup(mlx_ctx* c, cudaStream_t st) {
   cudaFree(c->lu_half.U); cudaFree(c->lu_half.L); cudaFree(c->lu_half.piv); cudaFree(c->lu_half.invd);
   cudaFree(c->lu_full.U); cudaFree(c->lu_full.L); cudaFree(c->lu_full.piv); cudaFree(c->lu_full.invd);
   for (BandLU* f : {&c->lu_half, &c->lu_full}) {
-    cudaFree(f->U32); cudaFree(f->L32); cudaFree(f->invd32); cudaFree(f->FS); cudaFree(f->BS);
+    cudaFree(f->FS); cudaFree(f->BS);
     cudaFree(f->PHf); cudaFree(f->PHb); cudaFree(f->PSf);
   }
   c->d_Bplus = nullptr;
@@ -1165,9 +948,6 @@ int mlx_band_setup(mlx_ctx* c, cudaStream_t st) {
     MLX_CUDA_TRY(c, cudaMalloc(&f->L, sizeof(double) * rows * kl));
     MLX_CUDA_TRY(c, cudaMalloc(&f->piv, sizeof(int) * rows));
     MLX_CUDA_TRY(c, cudaMalloc(&f->invd, sizeof(double) * rows));
-    MLX_CUDA_TRY(c, cudaMalloc(&f->U32, sizeof(float) * rows * W));
-    MLX_CUDA_TRY(c, cudaMalloc(&f->L32, sizeof(float) * rows * kl));
-    MLX_CUDA_TRY(c, cudaMalloc(&f->invd32, sizeof(float) * rows));
   }
   // scratch: per system 3 band buffers [N][W] + window [N][3kl+1], N <= Nc
   const long long stride = (long long)c->nc * (3 * W + 3 * kl + 1);
@@ -1188,9 +968,6 @@ int mlx_band_setup(mlx_ctx* c, cudaStream_t st) {
       c->lu_full.L, c->lu_full.piv, c->lu_full.invd, scratch, stride);
   MLX_LAUNCH_CHECK(c);
   for (BandLU* f : {&c->lu_half, &c->lu_full}) {
-    k_to_f32<<<(unsigned)((rows * W + 255) / 256), 256, 0, st>>>(rows * W, f->U, f->U32);
-    k_to_f32<<<(unsigned)((rows * kl + 255) / 256), 256, 0, st>>>(rows * kl, f->L, f->L32);
-    k_to_f32<<<(unsigned)((rows + 255) / 256), 256, 0, st>>>(rows, f->invd, f->invd32);
     const int rc = mlx_pack_lean(c, *f, kl, c->d_band_off, c->Kz, rows, st);
     if (rc) return rc;
     const int rs = mlx_seg_build(c, *f, c->solve_seg, st);
@@ -1201,219 +978,6 @@ int mlx_band_setup(mlx_ctx* c, cudaStream_t st) {
   cudaFree(scratch);
   cudaFree(d_lrows);
   return MLX_OK;
-}
-
-// Ring-staged variant for wide bands (the hyperviscous KL = p operators) and large
-// Nc: only the right-hand side / solution column lives in shared memory for the
-// whole solve (one column per lane, 32 chains per warp); factor rows stream
-// through small per-warp rings, staged by cp.async DIR_AHEAD rows ahead of use
-// (one commit group per row, so the wait before a row covers exactly that row).
-// At 256^3 the factors (hundreds of MB) come from HBM, whose latency a
-// register prefetch of one row could not cover.  The forward ring holds the
-// multipliers and pivots of one row per slot; the back-substitution ring holds
-// the rows of the current window (the pipelined substitution touches rows
-// i - 2KL .. i at step i) plus those in flight.  Same arithmetic, in the same
-// order, as k_band_solve.
-constexpr int DIR_AHEAD = 8;
-
-template <int KL, int CPWD>
-struct DirectSmem {
-  static constexpr int W = 2 * KL + 1;
-  static constexpr int G = CPWD / 4;
-  static constexpr int RB = 2 * KL + 1 + DIR_AHEAD;   // back-substitution ring rows
-  static constexpr int RF = DIR_AHEAD + 1;            // forward ring rows
-  static constexpr size_t bslot = (size_t)G * (W + 1) * sizeof(double);               // U rows + 1/diag
-  static constexpr size_t fslot = (size_t)G * KL * sizeof(double) + (size_t)G * sizeof(int) + 0;
-  static constexpr size_t fslot16 = (fslot + 15) / 16 * 16;
-  static constexpr size_t ring = (RB * bslot > RF * fslot16) ? RB * bslot : RF * fslot16;
-  __host__ __device__ static size_t per_warp(int nc) {
-    return ((size_t)nc * CPWD * sizeof(double) + ring + 15) / 16 * 16;
-  }
-};
-
-template <int KL, int CPWD>
-__global__ void k_band_solve_direct(int M, int nc, int Kz, int K, int groups_per_m, int step, double dt,
-                                    const long long* __restrict__ soff, const long long* __restrict__ band_off,
-                                    int kz_fac, int m0_shift, const double* __restrict__ U,
-                                    const double* __restrict__ Lm, const int* __restrict__ piv,
-                                    const double* __restrict__ invd, const double* __restrict__ s,
-                                    const double* __restrict__ A, const double* __restrict__ Ap,
-                                    double* __restrict__ out) {
-  constexpr int W = 2 * KL + 1;
-  constexpr int CPW = CPWD, G = CPWD / 4;
-  using SM = DirectSmem<KL, CPWD>;
-  constexpr int RB = SM::RB, RF = SM::RF, P = DIR_AHEAD;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const int gw = blockIdx.x * (blockDim.x >> 5) + wib;
-  if (gw >= M * groups_per_m) return;
-  const int m = gw / groups_per_m;
-  const int k0 = (gw % groups_per_m) * G;
-  const int gcnt = min(G, Kz - k0);
-  const int sh = (m == 0) ? m0_shift : 0;
-  const int Nm = nc - m;
-  const int N = Nm - sh;
-  unsigned char* wbase = smem_raw + (size_t)wib * SM::per_warp(nc);
-  double* Y = reinterpret_cast<double*>(wbase);                        // [N][CPW]
-  unsigned char* ring = wbase + (size_t)nc * CPW * sizeof(double);
-  const long long fb = band_off[m];
-  const long long sm = soff[m];
-  // factor rows of one step: GS consecutive rows (the warp's |k| values), or a
-  // single row shared by every |k| (kz_fac == 1)
-  const int GS = (kz_fac == 1) ? 1 : gcnt;
-  auto rowbase = [&](int r) -> long long { return fb + (long long)r * kz_fac + (kz_fac == 1 ? 0 : k0); };
-  auto stage_f = [&](int r) {   // multipliers and pivots of row r into its forward slot
-    unsigned char* slot = ring + (size_t)(r % RF) * SM::fslot16;
-    const long long rb = rowbase(r);
-    double* ls = reinterpret_cast<double*>(slot);
-    int* ps = reinterpret_cast<int*>(slot + (size_t)G * KL * sizeof(double));
-    for (int e = lane; e < GS * KL + GS; e += 32) {
-      if (e < GS * KL) cp_async8(ls + e, Lm + rb * KL + e);
-      else cp_async4(ps + (e - GS * KL), piv + rb + (e - GS * KL));
-    }
-  };
-  auto stage_b = [&](int r) {   // U rows and 1/diag of row r into its back-substitution slot
-    double* slot = reinterpret_cast<double*>(ring + (size_t)(r % RB) * SM::bslot);
-    const long long rb = rowbase(r);
-    for (int e = lane; e < GS * W + GS; e += 32) {
-      if (e < GS * W) cp_async8(slot + e, U + rb * W + e);
-      else cp_async8(slot + G * W + (e - GS * W), invd + rb + (e - GS * W));
-    }
-  };
-  const double h = (step == MLX_STEP_FEBE_FULL) ? dt : 0.5 * dt;
-  const double2* s2 = reinterpret_cast<const double2*>(s);
-  const double2* A2 = reinterpret_cast<const double2*>(A);
-  const double2* Ap2 = reinterpret_cast<const double2*>(Ap);
-  // forward ring prologue: rows 0 .. P-1 in flight while the right-hand sides load
-  for (int r = 0; r < P; ++r) {
-    if (r < N) stage_f(r);
-    cp_async_commit();
-  }
-  // one complex value per step (chain c = kk * 4 + sgn * 2 + part)
-#pragma unroll 4
-  for (int e = lane; e < N * 2 * gcnt; e += 32) {
-    const int cp = e / N, i = e - cp * N;
-    const int kq = cp >> 1, sg = cp & 1;
-    const int kabs = k0 + kq;
-    if (sg && kabs == 0) continue;
-    const int kidx = sg ? K - kabs : kabs;
-    const long long o = sm + (long long)kidx * Nm + sh + i;
-    const double2 sv = s2[o];
-    double2 r;
-    if (step == MLX_STEP_PLAIN) {
-      r = sv;
-    } else if (step == MLX_STEP_ABCN) {
-      const double2 q = A ? A2[o] : make_double2(0.0, 0.0);
-      const double2 qp = Ap ? Ap2[o] : make_double2(0.0, 0.0);
-      r = make_double2(rhs_abcn(sv.x, q.x, qp.x, A, Ap, dt), rhs_abcn(sv.y, q.y, qp.y, A, Ap, dt));
-    } else {
-      r = sv;
-      if (A) { const double2 q = A2[o]; r = make_double2(rhs_febe(sv.x, q.x, true, h), rhs_febe(sv.y, q.y, true, h)); }
-    }
-    Y[(size_t)i * CPW + cp * 2] = r.x;
-    Y[(size_t)i * CPW + cp * 2 + 1] = r.y;
-  }
-  __syncwarp();
-  const int c = lane;
-  const int kk = c >> 2, sgn = (c >> 1) & 1, part = c & 1;
-  const bool valid = c < 4 * gcnt && !(sgn && k0 + kk == 0);
-  const bool act = c < 4 * gcnt;
-  const int ks = (kz_fac == 1) ? 0 : (kk < gcnt ? kk : 0);   // lane's slot within a staged row
-  double* y = Y + c;
-  // forward elimination
-  double w[KL + 1];
-#pragma unroll
-  for (int q = 0; q < KL; ++q) w[q + 1] = (act && q < N) ? y[(size_t)q * CPW] : 0.0;
-  for (int j = 0; j < N; ++j) {
-    if (j + P < N) stage_f(j + P);
-    cp_async_commit();
-    cp_async_wait_group<P>();
-    __syncwarp();
-    const unsigned char* slot = ring + (size_t)(j % RF) * SM::fslot16;
-    const double* l = reinterpret_cast<const double*>(slot) + ks * KL;
-    const int d = reinterpret_cast<const int*>(slot + (size_t)G * KL * sizeof(double))[ks] - j;
-    if (act) {
-#pragma unroll
-      for (int q = 0; q < KL; ++q) w[q] = w[q + 1];
-      w[KL] = (j + KL < N) ? y[(size_t)(j + KL) * CPW] : 0.0;
-#pragma unroll
-      for (int q = 1; q <= KL; ++q)
-        if (q == d) { const double t = w[0]; w[0] = w[q]; w[q] = t; }
-      y[(size_t)j * CPW] = w[0];
-#pragma unroll
-      for (int q = 1; q <= KL; ++q) w[q] = __fma_rn(-l[q - 1], w[0], w[q]);
-    }
-    __syncwarp();
-  }
-  cp_async_wait_all();
-  __syncwarp();
-  // back substitution, software-pipelined as in k_band_solve: acc[t] is the
-  // partial sum of row i - t; at step i every pending row takes its term with
-  // x_{i+1}.  Rows are staged in descending order, P beyond the window.
-  for (int r = N - 1; r >= N - 2 * KL - P; --r) {
-    if (r >= 0) stage_b(r);
-    cp_async_commit();
-  }
-  cp_async_wait_group<P>();
-  __syncwarp();
-  auto Urow = [&](int r) -> const double* {
-    return reinterpret_cast<const double*>(ring + (size_t)(r % RB) * SM::bslot) + ks * W;
-  };
-  auto Dval = [&](int r) -> double {
-    return reinterpret_cast<const double*>(ring + (size_t)(r % RB) * SM::bslot)[G * W + ks];
-  };
-  double acc[2 * KL];
-#pragma unroll
-  for (int t = 0; t < 2 * KL; ++t) {
-    const int r = N - 1 - t;
-    acc[t] = (act && r >= 0) ? __dmul_rn(y[(size_t)r * CPW], Dval(r)) : 0.0;
-  }
-  double xn = 0.0;   // x_{i+1}
-  for (int i = N - 1; i >= 0; --i) {
-    const int rs = i - 2 * KL - P;
-    if (rs >= 0) stage_b(rs);
-    cp_async_commit();
-    cp_async_wait_group<P>();
-    __syncwarp();
-    if (act) {
-      const double xi = __fma_rn(-Urow(i)[1], xn, acc[0]);
-#pragma unroll
-      for (int t = 1; t < 2 * KL; ++t)
-        if (i - t >= 0) acc[t] = __fma_rn(-Urow(i - t)[t + 1], xn, acc[t]);
-      y[(size_t)i * CPW] = xi;
-#pragma unroll
-      for (int t = 0; t < 2 * KL - 1; ++t) acc[t] = acc[t + 1];
-      const int rn = i - 2 * KL;
-      acc[2 * KL - 1] = (rn >= 0) ? __dmul_rn(y[(size_t)rn * CPW], Dval(rn)) : 0.0;
-      xn = xi;
-    }
-    __syncwarp();
-  }
-  cp_async_wait_all();
-  __syncwarp();
-  if (sh && valid) {
-    double dacc = 0.0;
-    for (int i = 0; i < N; ++i) dacc = __fma_rn(sqrt((2.0 * (i + 1) + 1.0) * 0.5), Y[(size_t)i * CPW + c], dacc);
-    const int kidx = sgn ? K - (k0 + kk) : k0 + kk;
-    out[2 * (sm + (long long)kidx * Nm) + part] = -dacc / sqrt(0.5);
-  }
-  double2* out2 = reinterpret_cast<double2*>(out);
-#pragma unroll 4
-  for (int e = lane; e < N * 2 * gcnt; e += 32) {
-    const int cp = e / N, i = e - cp * N;
-    const int kq = cp >> 1, sg = cp & 1;
-    const int kabs = k0 + kq;
-    if (sg && kabs == 0) continue;
-    const int kidx = sg ? K - kabs : kabs;
-    const long long o = sm + (long long)kidx * Nm + sh + i;
-    double2 v = make_double2(Y[(size_t)i * CPW + cp * 2], Y[(size_t)i * CPW + cp * 2 + 1]);
-    if (step == MLX_STEP_ABCN) {
-      const double2 sv = s2[o];
-      v.x -= sv.x;
-      v.y -= sv.y;
-    }
-    out2[o] = v;
-  }
 }
 
 // Lean variant: 32 (or 16) real chains per warp, every lane busy in every FP64
@@ -1750,27 +1314,6 @@ static int launch_solve(mlx_ctx* c, int step, const BandLU& f, const long long* 
     if (mode == LEAN_FEBE) return go(I32(), MF());
     return go(I32(), MP());
   }
-  if (c->solve_direct) {
-    // chains per warp: 32 (every lane busy) or 16 (half the shared memory per
-    // warp, so twice the warps per SM hide the FP64 latency)
-    auto go = [&](auto cpw_tag) -> int {
-      constexpr int CPWD = decltype(cpw_tag)::value;
-      const int gpm = (c->Kz + CPWD / 4 - 1) / (CPWD / 4);
-      const int warps = c->M * gpm;
-      const size_t pw = DirectSmem<KL, CPWD>::per_warp(c->nc);
-      int WPB = 8;
-      while (WPB > 1 && (size_t)WPB * pw > 200 * 1024) WPB /= 2;
-      if (pw > 200 * 1024) return MLX_EINVAL;
-      const size_t smem = (size_t)WPB * pw;
-      k_band_solve_direct<KL, CPWD><<<(warps + WPB - 1) / WPB, 32 * WPB, smem, st>>>(
-          c->M, c->nc, c->Kz, c->K, gpm, step, c->dt, c->d_soff, fac_off, kz_fac, m0_shift, f.U, f.L, f.piv,
-          f.invd, (const double*)s, (const double*)A, (const double*)Ap, (double*)out);
-      return MLX_OK;
-    };
-    if (c->solve_direct_cpw == 8) return go(std::integral_constant<int, 8>());
-    if (c->solve_direct_cpw == 16) return go(std::integral_constant<int, 16>());
-    return go(std::integral_constant<int, 32>());
-  }
   if constexpr (KL == 2) {
     if (c->solve_seg && f.PHf && f.seg && kz_fac == c->Kz && m0_shift == 0) {
       const int keep_s = (step == MLX_STEP_ABCN && c->solve_keep_s) ? 1 : 0;
@@ -1809,50 +1352,11 @@ static int launch_solve(mlx_ctx* c, int step, const BandLU& f, const long long* 
   return MLX_OK;
 }
 
-template <int KL>
-static int launch_solve_ir(mlx_ctx* c, int step, const BandLU& f, const double2* s, const double2* A,
-                           const double2* Ap, double2* out, cudaStream_t st) {
-  const int gpm = (c->Kz + 7) / 8;
-  const size_t smem = IrSmem<KL>::bytes(c->nc);
-  const double alpha = (step == MLX_STEP_FEBE_FULL) ? 3.0 : 2.0;
-  const double beta = (step == MLX_STEP_FEBE_FULL) ? -2.0 : -1.0;
-  k_band_solve_ir<KL><<<c->M * gpm, 32, smem, st>>>(
-      c->M, c->nc, c->Kz, c->K, gpm, step, c->dt, c->d_soff, c->d_band_off, f.U32, f.L32, f.piv, f.invd32,
-      c->d_Bplus, alpha, beta, c->solve_ir_max, (const double*)s, (const double*)A, (const double*)Ap,
-      (double*)out, c->d_err);
-  return MLX_OK;
-}
-
-// shared memory of the refinement variant fits (one warp per CTA)
-static bool ir_fits(const mlx_ctx* c) {
-  size_t b = 0;
-  switch (c->kl) {
-    case 2: b = IrSmem<2>::bytes(c->nc); break;
-    case 4: b = IrSmem<4>::bytes(c->nc); break;
-    case 6: b = IrSmem<6>::bytes(c->nc); break;
-    case 8: b = IrSmem<8>::bytes(c->nc); break;
-    default: return false;
-  }
-  return b <= 200 * 1024;
-}
-
 int mlx_band_solve(mlx_ctx* c, int step, const double2* s, const double2* A, const double2* Ap,
                    double2* out, cudaStream_t st) {
   TimedLaunch tl(c, KID_BAND_SOLVE, st);
   const BandLU& f = (step == MLX_STEP_FEBE_FULL) ? c->lu_full : c->lu_half;
   int rc;
-  if (c->solve_ir && f.U32 && ir_fits(c)) {
-    switch (c->kl) {
-      case 2: rc = launch_solve_ir<2>(c, step, f, s, A, Ap, out, st); break;
-      case 4: rc = launch_solve_ir<4>(c, step, f, s, A, Ap, out, st); break;
-      case 6: rc = launch_solve_ir<6>(c, step, f, s, A, Ap, out, st); break;
-      case 8: rc = launch_solve_ir<8>(c, step, f, s, A, Ap, out, st); break;
-      default: return MLX_EINVAL;
-    }
-    if (rc) return rc;
-    MLX_LAUNCH_CHECK(c);
-    return MLX_OK;
-  }
   const long long* fo = c->d_band_off;
   switch (c->kl) {
     case 2: rc = launch_solve<2>(c, step, f, fo, c->Kz, 0, s, A, Ap, out, st); break;
@@ -2032,14 +1536,6 @@ int mlx_band_prepare(mlx_ctx* c) {
   MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_band_solve_seg<2, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
   MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_band_solve<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
   MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_band_solve<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-#define MLX_DIRECT_ATTR(KLV, CPWV)                                                                   \
-  MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_band_solve_direct<KLV, CPWV>,                               \
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, lim))
-  MLX_DIRECT_ATTR(2, 32); MLX_DIRECT_ATTR(3, 32); MLX_DIRECT_ATTR(4, 32); MLX_DIRECT_ATTR(6, 32);
-  MLX_DIRECT_ATTR(8, 32); MLX_DIRECT_ATTR(2, 16); MLX_DIRECT_ATTR(3, 16); MLX_DIRECT_ATTR(4, 16);
-  MLX_DIRECT_ATTR(6, 16); MLX_DIRECT_ATTR(8, 16); MLX_DIRECT_ATTR(2, 8); MLX_DIRECT_ATTR(3, 8);
-  MLX_DIRECT_ATTR(4, 8); MLX_DIRECT_ATTR(6, 8); MLX_DIRECT_ATTR(8, 8);
-#undef MLX_DIRECT_ATTR
   {
     int rc = set_lean_attrs<2>(c, lim);
     if (!rc) rc = set_lean_attrs<3>(c, lim);
@@ -2051,10 +1547,6 @@ int mlx_band_prepare(mlx_ctx* c) {
   MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_band_solve<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
   MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_band_solve<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
   MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_band_solve<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-  MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_band_solve_ir<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-  MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_band_solve_ir<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-  MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_band_solve_ir<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-  MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_band_solve_ir<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
   return MLX_OK;
 }
 

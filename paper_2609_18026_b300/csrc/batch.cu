@@ -163,11 +163,16 @@ int mlx_autotune(mlx_ctx* c, int kind, const double* coeffs, int ncoeffs, const 
   if (!c->implicit_ready) return MLX_ESTATE;
   if (kind == MLX_NONLIN_VORTEX && !c->vortex_ready) return MLX_ESTATE;
   const std::string key = tune_key(c, kind);
-  // solve variant encoding: cpw = 1 refinement, cpw = 0 ring-staged, cpw = 2 lean,
-  // else staged (cpw, wpb)
+  // solve variant encoding: cpw = 0 segmented (half width 2), cpw = 2 lean, else
+  // staged (cpw chains per warp, wpb warps per CTA)
   int bn = c->tc_bn;
-  int cpw = c->solve_ir ? 1 : (c->solve_direct == 2 ? 2 : (c->solve_direct ? 0 : c->solve_cpw));
-  int wpb = (c->solve_ir || c->solve_direct) ? 0 : c->solve_wpb;
+  auto variant = [&](int* cp, int* wp) {
+    const bool seg = c->kl == 2 && c->solve_seg && c->lu_half.seg;
+    *cp = c->solve_direct == 2 ? 2 : (seg ? 0 : c->solve_cpw);
+    *wp = (c->solve_direct == 2 || seg) ? 0 : c->solve_wpb;
+  };
+  int cpw, wpb;
+  variant(&cpw, &wpb);
   bool found = false;
   if (cache_path) {
     FILE* f = fopen(cache_path, "r");
@@ -190,11 +195,10 @@ int mlx_autotune(mlx_ctx* c, int kind, const double* coeffs, int ncoeffs, const 
   auto apply = [&](int bn_, int cpw_, int wpb_) -> int {
     int rc = MLX_OK;
     if (c->precision == MLX_BF16X3 && bn_ != c->tc_bn) rc = mlx_set_tuning(c, "tc_bn", bn_);
-    if (!rc) rc = mlx_set_tuning(c, "solve_ir", cpw_ == 1 ? 1 : 0);
-    if (cpw_ == 1) return rc;
-    if (cpw_ == 0) return rc ? rc : mlx_set_tuning(c, "solve_direct", 1);
     if (cpw_ == 2) return rc ? rc : mlx_set_tuning(c, "solve_direct", 2);
     if (!rc) rc = mlx_set_tuning(c, "solve_direct", 0);
+    if (!rc && c->kl == 2) rc = mlx_set_tuning(c, "solve_seg", cpw_ == 0 ? 8 : 0);
+    if (cpw_ == 0) return rc;
     if (!rc) rc = mlx_set_tuning(c, "solve_cpw", cpw_);
     if (!rc) rc = mlx_set_tuning(c, "solve_wpb", wpb_);
     return rc;
@@ -239,10 +243,11 @@ int mlx_autotune(mlx_ctx* c, int kind, const double* coeffs, int ncoeffs, const 
     }
     // 2. banded-solve variant and launch shape
     if (!rc) {
-      const int shapes[][2] = {{4, 1}, {8, 1}, {8, 4}, {16, 1}, {32, 1}, {0, 0}, {2, 0}, {1, 0}};
+      const int shapes[][2] = {{4, 1}, {8, 1}, {8, 4}, {16, 1}, {32, 1}, {0, 0}, {2, 0}};
       best = 1e30f;
       int bc = cpw, bw = wpb;
       for (auto& sh : shapes) {
+        if (sh[0] == 0 && c->kl != 2) continue;       // the segmented solve serves half width 2 only
         if ((rc = apply(bn, sh[0], sh[1]))) break;
         float ms = 0.f;
         if ((rc = time_it(&ms))) break;
@@ -266,8 +271,7 @@ int mlx_autotune(mlx_ctx* c, int kind, const double* coeffs, int ncoeffs, const 
   if (rc) return rc;
   if (chosen) {
     chosen[0] = c->tc_bn;
-    chosen[1] = c->solve_ir ? 1 : (c->solve_direct == 2 ? 2 : (c->solve_direct ? 0 : c->solve_cpw));
-    chosen[2] = (c->solve_ir || c->solve_direct) ? 0 : c->solve_wpb;
+    variant(&chosen[1], &chosen[2]);
     chosen[3] = found;
   }
   return MLX_OK;

@@ -158,7 +158,8 @@ template <typename T, int MODE, int E>
 __global__ void __launch_bounds__(256) k_phi(int N, int logN, int M, int Nr, int R,
                                              T* __restrict__ phys, T* __restrict__ zre,
                                              T* __restrict__ zim,
-                                             const typename C2T<T>::type* __restrict__ tw, T gamma) {
+                                             const typename C2T<T>::type* __restrict__ tw, T gamma,
+                                             int* __restrict__ err) {
   typedef typename C2T<T>::type C;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* L = reinterpret_cast<C*>(smem_raw);
@@ -233,11 +234,16 @@ __global__ void __launch_bounds__(256) k_phi(int N, int logN, int M, int Nr, int
       }
       dif<C, E>(v, N, lj, tw, true);   // physical values, bit-reversed positions
       if constexpr (MODE == PHI_FKPP) {
+        bool finite = true;
 #pragma unroll
         for (int e = 0; e < E; ++e) {
           v[e].x = gamma * v[e].x * ((T)1 - v[e].x);
           v[e].y = gamma * v[e].y * ((T)1 - v[e].y);
+          finite = finite && isfinite(v[e].x) && isfinite(v[e].y);
         }
+        // a non-finite product (blow-up or NaN in the state) sets the status bit
+        // that mlx_device_status reports as MLX_ENUMERIC
+        if (__any_sync(0xffffffffu, !finite) && (threadIdx.x & 31) == 0) atomicOr(err, 16);
         dit<C, E>(v, N, lj, tw, false);   // forward DFT, natural order
         if (act) {
 #pragma unroll
@@ -361,21 +367,21 @@ constexpr int kSmemLimit = 200 * 1024;
 
 template <typename T, int MODE, int E>
 void phi_go(dim3 grid, size_t smem, cudaStream_t st, int N, int M, int Nr, int R, T* phys, T* zre,
-            T* zim, const void* tw, double gamma) {
+            T* zim, const void* tw, double gamma, int* err) {
   typedef typename C2T<T>::type C;
   k_phi<T, MODE, E><<<grid, 256, smem, st>>>(N, ilog2(N), M, Nr, R, phys, zre, zim,
-                                             reinterpret_cast<const C*>(tw), (T)gamma);
+                                             reinterpret_cast<const C*>(tw), (T)gamma, err);
 }
 
 template <typename T, int MODE>
 void phi_dispatch(int E, dim3 grid, size_t smem, cudaStream_t st, int N, int M, int Nr, int R,
-                  T* phys, T* zre, T* zim, const void* tw, double gamma) {
+                  T* phys, T* zre, T* zim, const void* tw, double gamma, int* err) {
   switch (E) {
-    case 1: phi_go<T, MODE, 1>(grid, smem, st, N, M, Nr, R, phys, zre, zim, tw, gamma); break;
-    case 2: phi_go<T, MODE, 2>(grid, smem, st, N, M, Nr, R, phys, zre, zim, tw, gamma); break;
-    case 4: phi_go<T, MODE, 4>(grid, smem, st, N, M, Nr, R, phys, zre, zim, tw, gamma); break;
-    case 8: phi_go<T, MODE, 8>(grid, smem, st, N, M, Nr, R, phys, zre, zim, tw, gamma); break;
-    default: phi_go<T, MODE, 16>(grid, smem, st, N, M, Nr, R, phys, zre, zim, tw, gamma); break;
+    case 1: phi_go<T, MODE, 1>(grid, smem, st, N, M, Nr, R, phys, zre, zim, tw, gamma, err); break;
+    case 2: phi_go<T, MODE, 2>(grid, smem, st, N, M, Nr, R, phys, zre, zim, tw, gamma, err); break;
+    case 4: phi_go<T, MODE, 4>(grid, smem, st, N, M, Nr, R, phys, zre, zim, tw, gamma, err); break;
+    case 8: phi_go<T, MODE, 8>(grid, smem, st, N, M, Nr, R, phys, zre, zim, tw, gamma, err); break;
+    default: phi_go<T, MODE, 16>(grid, smem, st, N, M, Nr, R, phys, zre, zim, tw, gamma, err); break;
   }
 }
 
@@ -394,9 +400,10 @@ int phi_launch(mlx_ctx* c, int mode, T* phys, T* zbase, const void* tw, double g
   T* zim = zbase + pl;
   const int E = N >= 32 ? N / 32 : 1;
   TimedLaunch tl(c, mode == PHI_FWD ? KID_PHI_FWD : (mode == PHI_BWD ? KID_PHI_BWD : KID_PHI_FKPP), st);
-  if (mode == PHI_FWD) phi_dispatch<T, PHI_FWD>(E, grid, smem, st, N, c->M, c->nr, R, phys, zre, zim, tw, gamma);
-  else if (mode == PHI_BWD) phi_dispatch<T, PHI_BWD>(E, grid, smem, st, N, c->M, c->nr, R, phys, zre, zim, tw, gamma);
-  else phi_dispatch<T, PHI_FKPP>(E, grid, smem, st, N, c->M, c->nr, R, phys, zre, zim, tw, gamma);
+  int* err = c->d_err;
+  if (mode == PHI_FWD) phi_dispatch<T, PHI_FWD>(E, grid, smem, st, N, c->M, c->nr, R, phys, zre, zim, tw, gamma, err);
+  else if (mode == PHI_BWD) phi_dispatch<T, PHI_BWD>(E, grid, smem, st, N, c->M, c->nr, R, phys, zre, zim, tw, gamma, err);
+  else phi_dispatch<T, PHI_FKPP>(E, grid, smem, st, N, c->M, c->nr, R, phys, zre, zim, tw, gamma, err);
   MLX_LAUNCH_CHECK(c);
   return MLX_OK;
 }

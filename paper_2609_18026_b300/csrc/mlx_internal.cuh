@@ -30,11 +30,14 @@ enum KernelId {
 
 struct TimingState {
   bool on = false;
+  int mode = 0;                  // 1: direct launches bracketed by events; 2: graph replay with
+                                 // event-record nodes around every kernel node
   long long launches[KID_COUNT] = {0};
   double ms[KID_COUNT] = {0};
   std::vector<cudaEvent_t> pool;
   struct Pending { int kid; cudaEvent_t a, b; };
-  std::vector<Pending> pending;
+  std::vector<Pending> pending;  // recorded by direct launches, resolved by mlx_timing_read
+  std::vector<Pending> captured; // recorded as graph nodes, resolved after every replay
 };
 
 // One GEMM work tile of the ragged per-m Legendre contraction.
@@ -54,11 +57,6 @@ struct BandLU {
   double* L = nullptr;     // [rows][kl]
   int* piv = nullptr;      // [rows]
   double* invd = nullptr;  // [rows]
-  // FP32 roundings of U, L, invd (implicit-step families only): the inner solves
-  // of the mixed-precision refinement
-  float* U32 = nullptr;
-  float* L32 = nullptr;
-  float* invd32 = nullptr;
   // per-row records of the lean solve: forward {L row, pivot offset mask, pad}, back
   // substitution {U[row - t][t + 1] (t < 2 kl), 1/diag[row - 2 kl], pad}
   double* FS = nullptr;
@@ -116,7 +114,7 @@ struct mlx_ctx {
   int tc_products = 6;                 // BF16 split products per term: 6 or 8
   int tc_stages = 2;                   // shared-memory stages of the K loop
   int* d_err = nullptr;                // device status word: bits 1, 2, 4 bounded waits that
-                                       // expired; bit 8 a refinement that did not converge
+                                       // expired; bit 16 a non-finite nonlinear product
 
   // workspace (element type follows precision)
   void* d_mixed = nullptr;             // planar complex [2][K][M][Nr]
@@ -151,20 +149,17 @@ struct mlx_ctx {
   double2* d_vspec = nullptr;          // 9 spectral temporaries
   void* d_vphys = nullptr;             // 6 physical temporaries
   double* d_setup_scratch = nullptr;
+  double* d_diag = nullptr;            // mlx_diag partial sums [M K][4] and result [4]
   int solve_cpw = 8;                   // real chains per warp in the banded solve (4..32)
   int solve_wpb = 4;                   // warps per CTA in the banded solve (1..4)
-  int solve_direct = 0;                // 1: ring-staged solve variant (wide bands, large Nc),
-                                       // 2: lean variant (16 or 32 chains per warp, packed
-                                       // factor records, global scratch)
+  int solve_direct = 0;                // 2: lean variant (16 or 32 chains per warp, packed
+                                       // factor records, global scratch); 0: staged or segmented
   int solve_lean_cpw = 32;             // chains per warp of the lean variant: 16 or 32
   double* d_solve_y = nullptr;         // scratch of the lean variant, [warp][Nc][CPW]
-  int solve_direct_cpw = 8;            // chains per warp of that variant: 8, 16 or 32
   int solve_keep_s = 1;                // staged variant: copy of s in shared memory for the AB-CN "- s"
   int phi_tile = 0;                    // radii per CTA of the phi kernels (2..32; 0 = automatic)
   int z_tile = 0;                      // radii per CTA of the z kernels (1..32; 0 = automatic)
   int solve_seg = 8;                   // segments of the half-width-2 segmented solve (8, 4; 0 = off)
-  int solve_ir = 0;                    // 1: FP32 solves refined to FP64 by FP64 residuals
-  int solve_ir_max = 8;                // refinement steps at most (early exit at FP64 level)
 
   // graphs cached per (state, prev_A, kind, gamma)
   struct GraphKey {
@@ -184,9 +179,11 @@ struct mlx_ctx {
 };
 
 // RAII bracket: with timing on, records CUDA events around one kernel launch on
-// its stream (the events are resolved by mlx_timing_read).
+// its stream (the events are resolved by mlx_timing_read).  Inside a stream
+// capture the events become event-record nodes of the graph (timing mode 2), so
+// that every replay measures the kernel nodes where they run.
 struct TimedLaunch {
-  mlx_ctx* c; int kid; cudaStream_t st; cudaEvent_t a = nullptr, b = nullptr;
+  mlx_ctx* c; int kid; cudaStream_t st; cudaEvent_t a = nullptr, b = nullptr; bool cap = false;
   static cudaEvent_t get(mlx_ctx* c) {
     if (!c->timing.pool.empty()) { cudaEvent_t e = c->timing.pool.back(); c->timing.pool.pop_back(); return e; }
     cudaEvent_t e = nullptr;
@@ -194,10 +191,24 @@ struct TimedLaunch {
     return e;
   }
   TimedLaunch(mlx_ctx* c_, int kid_, cudaStream_t st_) : c(c_), kid(kid_), st(st_) {
-    if (c->timing.on) { a = get(c); b = get(c); cudaEventRecord(a, st); }
+    if (!c->timing.on) return;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(st, &cs);
+    cap = cs == cudaStreamCaptureStatusActive;
+    if (cap && c->timing.mode != 2) return;
+    a = get(c); b = get(c);
+    if (cap) cudaEventRecordWithFlags(a, st, cudaEventRecordExternal);
+    else cudaEventRecord(a, st);
   }
   ~TimedLaunch() {
-    if (a) { cudaEventRecord(b, st); c->timing.pending.push_back({kid, a, b}); }
+    if (!a) return;
+    if (cap) {
+      cudaEventRecordWithFlags(b, st, cudaEventRecordExternal);
+      c->timing.captured.push_back({kid, a, b});
+    } else {
+      cudaEventRecord(b, st);
+      c->timing.pending.push_back({kid, a, b});
+    }
   }
 };
 

@@ -14,12 +14,18 @@
 // this library until the process exits.  In host code `g_noalloc_scratch` is only
 // a host-side stand-in for the symbol, not a device address; its device address is
 // looked up once per device with cudaGetSymbolAddress, with that device current,
-// on the first call made on that device.  Make that first call before any stream
-// capture begins.  Every call on a device shares the one array and leaves the last
+// on the first call made on that device (under a lock, so that host threads making
+// their first calls together look it up once).  Make that first call before any
+// stream capture begins.  The cached address belongs to the device's primary
+// context: like every context of this library, it does not survive
+// cudaDeviceReset.  Every call on a device shares the one array and leaves the last
 // call's contents behind; the kernels overwrite every element they later read, so
 // nothing needs clearing.  Calls whose work overlaps on the GPU (different streams,
 // or different contexts on the same device) race on the array: serialise them.
 #include "mlx_internal.cuh"
+
+#include <atomic>
+#include <mutex>
 
 namespace {
 
@@ -28,7 +34,8 @@ constexpr int kMaxDevices = 64;
 
 __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
-void* g_scratch_addr[kMaxDevices] = {nullptr};
+std::atomic<void*> g_scratch_addr[kMaxDevices];
+std::mutex g_scratch_lock;
 
 size_t round256(size_t b) { return (b + 255) / 256 * 256; }
 
@@ -48,13 +55,21 @@ extern "C" int mlx_forward_noalloc(mlx_ctx* c, const void* phys, void* spec, mlx
   }
   int dev = 0;
   MLX_CUDA_TRY(c, cudaGetDevice(&dev));
-  if (dev < 0 || dev >= kMaxDevices) return MLX_EINVAL;
-  if (!g_scratch_addr[dev]) {
-    void* p = nullptr;
-    MLX_CUDA_TRY(c, cudaGetSymbolAddress(&p, g_noalloc_scratch));
-    g_scratch_addr[dev] = p;
+  if (dev < 0 || dev >= kMaxDevices) {
+    c->last_err = "mlx_forward_noalloc: device ordinal " + std::to_string(dev) + " is beyond the " +
+                  std::to_string(kMaxDevices) + " devices this entry point supports";
+    return MLX_EINVAL;
   }
-  unsigned char* base = static_cast<unsigned char*>(g_scratch_addr[dev]);
+  void* addr = g_scratch_addr[dev].load(std::memory_order_acquire);
+  if (!addr) {
+    std::lock_guard<std::mutex> lock(g_scratch_lock);
+    addr = g_scratch_addr[dev].load(std::memory_order_relaxed);
+    if (!addr) {
+      MLX_CUDA_TRY(c, cudaGetSymbolAddress(&addr, g_noalloc_scratch));
+      g_scratch_addr[dev].store(addr, std::memory_order_release);
+    }
+  }
+  unsigned char* base = static_cast<unsigned char*>(addr);
   // run the forward transform's kernels with the workspace pointers redirected
   void* saved_mixed = c->d_mixed;
   void* saved_zm = c->d_zm;

@@ -97,11 +97,11 @@ __global__ void k_vortex_fields(int nc, int Kz, int K, double lz, const long lon
 }
 
 template <typename T>
-__global__ void k_vortex_product(long long n_phys, int nphi, int nr, T U0, const double* __restrict__ rnode,
-                                 T* __restrict__ f0, T* __restrict__ f1, T* __restrict__ f2,
-                                 const T* __restrict__ f3, const T* __restrict__ f4, const T* __restrict__ f5) {
-  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= n_phys) return;
+__device__ __forceinline__ bool vortex_product_at(long long idx, int nphi, int nr, T U0,
+                                                  const double* __restrict__ rnode, T* __restrict__ f0,
+                                                  T* __restrict__ f1, T* __restrict__ f2,
+                                                  const T* __restrict__ f3, const T* __restrict__ f4,
+                                                  const T* __restrict__ f5) {
   const int i = (int)(idx % nr);
   const int j = (int)((idx / nr) % nphi);
   const T r = (T)rnode[i];
@@ -118,10 +118,28 @@ __global__ void k_vortex_product(long long n_phys, int nphi, int nr, T U0, const
   const T rvr = f0[idx], rvp = f1[idx], vz = f2[idx], rwr = f3[idx], rwp = f4[idx], wz = f5[idx];
   const T ar = rvr + r * U0 * sn;   // r (v_r + U_r)
   const T ap = rvp + r * U0 * cs;   // r (v_phi + U_phi)
-  f0[idx] = vz * rwr - ar * wz;                  // A = r N_phi
-  f1[idx] = ap * wz - vz * rwp;                  // B = r N_r
-  f2[idx] = ar * rwp - ap * rwr;                 // C = r^2 N_z
+  const T A = vz * rwr - ar * wz;                // A = r N_phi
+  const T Bv = ap * wz - vz * rwp;               // B = r N_r
+  const T C = ar * rwp - ap * rwr;               // C = r^2 N_z
+  f0[idx] = A;
+  f1[idx] = Bv;
+  f2[idx] = C;
+  return isfinite(A) && isfinite(Bv) && isfinite(C);
 }
+
+template <typename T>
+__global__ void k_vortex_product(long long n_phys, int nphi, int nr, T U0, const double* __restrict__ rnode,
+                                 T* __restrict__ f0, T* __restrict__ f1, T* __restrict__ f2,
+                                 const T* __restrict__ f3, const T* __restrict__ f4, const T* __restrict__ f5,
+                                 int* __restrict__ err) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  bool finite = true;
+  if (idx < n_phys) finite = vortex_product_at(idx, nphi, nr, U0, rnode, f0, f1, f2, f3, f4, f5);
+  // a non-finite product (blow-up or NaN in the state) sets the status bit that
+  // mlx_device_status reports as MLX_ENUMERIC
+  if (__any_sync(0xffffffffu, !finite) && (threadIdx.x & 31) == 0) atomicOr(err, 16);
+}
+
 
 // Jacobi matrix entries e_{m,i} = sqrt((n^2 - m^2) / (4 n^2 - 1)), n = m + i + 1, coupling
 // local rows i and i + 1 (multiplication by x, from x Pbar_n = a_{n+1} Pbar_{n+1} + a_n Pbar_{n-1});
@@ -273,7 +291,7 @@ static int vortex_nonlinear_t(mlx_ctx* c, double U0, const double2* state, doubl
     if ((rc = mlx_fft_backward(c, P[f], st))) return rc;
   }
   k_vortex_product<T><<<nblk(np, tb), tb, 0, st>>>(np, c->nphi, c->nr, (T)U0, c->d_r, P[0], P[1], P[2], P[3],
-                                                   P[4], P[5]);
+                                                   P[4], P[5], c->d_err);
   MLX_LAUNCH_CHECK(c);
   // A, B, C -> F[6], F[7], F[8]
   for (int f = 0; f < 3; ++f) {

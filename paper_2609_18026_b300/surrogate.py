@@ -242,33 +242,6 @@ def run(n_traj=2000, n_test=None, epochs=40, batch=128, lr=1e-3, seed=20261203, 
     return out
 
 
-def step_probe(batch=128, steps=2, seed=0, cfg=CONFIG):
-    """Time mlx_sur_train_step on seeded synthetic data at the workload's size (D =
-    4 n_spec of the 64^3 grid, width 64): `steps` steps, CUDA events around the last."""
-    import torch
-    torch.cuda.init()
-    M, K, nc = 22, 43, cfg["nr"]     # two-thirds chops of the 64^3 grid
-    D = 4 * K * sum(nc - m for m in range(M))
-    sur = B.Surrogate(D, width=cfg["width"], bmax=batch, seed=seed)
-    rng = np.random.Generator(np.random.PCG64(seed))
-    X = torch.as_tensor(rng.standard_normal((2 * batch, D)), dtype=torch.float32).to(torch.bfloat16).cuda()
-    T = torch.as_tensor(rng.standard_normal((2 * batch, D)) * 0.1, dtype=torch.float32).cuda()
-    idx = torch.arange(batch, dtype=torch.int32, device="cuda")
-    for _ in range(steps - 1):
-        sur.train_step(X, T, idx, 1e-3)
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    e0.record()
-    sur.train_step(X, T, idx, 1e-3)
-    e1.record()
-    torch.cuda.synchronize()
-    sur.status()
-    out = dict(D=D, batch=batch, train_step_ms=e0.elapsed_time(e1))
-    sur.close()
-    return out
-
-
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--trajectories", type=int, default=2000)
@@ -276,12 +249,7 @@ def main():
     ap.add_argument("--epochs", type=int, default=40)
     ap.add_argument("--batch", type=int, default=128)
     ap.add_argument("--lr", type=float, default=1e-3)
-    ap.add_argument("--step-probe", action="store_true",
-                    help="time two training steps on seeded data instead of the full pipeline")
     a = ap.parse_args()
-    if a.step_probe:
-        print(json.dumps(step_probe(a.batch)))
-        return
     out = run(a.trajectories, a.test, a.epochs, a.batch, a.lr)
     print(json.dumps(out))
 

@@ -16,3 +16,25 @@ def pytest_configure(config):
 @pytest.fixture(scope="session")
 def golden_dir():
     return os.path.join(ROOT, "tests", "golden")
+
+
+_RECORDS = []
+
+
+@pytest.fixture
+def record(request):
+    """Record a measured value (an error, a condition number) of the running test;
+    every record is printed in the terminal summary, so the log states what each
+    parity test measured, not only that it passed."""
+    def _rec(name, **vals):
+        _RECORDS.append((request.node.nodeid, name, vals))
+    return _rec
+
+
+def pytest_terminal_summary(terminalreporter):
+    if not _RECORDS:
+        return
+    terminalreporter.section("measured values")
+    for nodeid, name, vals in _RECORDS:
+        items = ", ".join("%s=%s" % (k, ("%.3e" % v) if isinstance(v, float) else v) for k, v in vals.items())
+        terminalreporter.write_line("%s  %s: %s" % (nodeid.split("::")[-1], name, items))

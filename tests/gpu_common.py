@@ -45,3 +45,25 @@ def rel(a, b):
     a = np.asarray(a, dtype=np.float64)
     b = np.asarray(b, dtype=np.float64)
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def block_err(g, got, ref, floor=0.0):
+    """Worst per-(m, k)-block relative error of two spectral lists:
+    max over blocks of max|got - ref| / max(max|ref_block|, floor * max|ref|).
+    With floor = 0 every block is held to its own scale, so a wrong coefficient
+    in a block that is small in norm cannot hide behind the global norm."""
+    gmax = max(float(np.max(np.abs(b))) for b in ref if b.size)
+    worst = 0.0
+    for a, b in zip(got, ref):
+        for kk in range(b.shape[0]):
+            d = float(np.max(np.abs(a[kk] - b[kk]))) if b.shape[1] else 0.0
+            s = max(float(np.max(np.abs(b[kk]))) if b.shape[1] else 0.0, floor * gmax, 1e-300)
+            worst = max(worst, d / s)
+    return worst
+
+
+def max_err(got, ref):
+    """Element-wise bound: max|got - ref| / max|ref|."""
+    got = np.asarray(got, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    return float(np.max(np.abs(got - ref)) / max(float(np.max(np.abs(ref))), 1e-300))

@@ -10,7 +10,7 @@ import oracle as O
 from paper_2609_18026_b300 import binding as B
 from paper_2609_18026_b300 import workloads as W
 
-from gpu_common import spec_from_gpu
+from gpu_common import spec_from_gpu, block_err
 
 pytestmark = pytest.mark.gpu
 
@@ -79,8 +79,8 @@ def test_autotune_cache_roundtrip(tmp_path):
     ctx.implicit_setup(1.0, 1e-2)
     first = ctx.autotune(B.NONLIN_FKPP, [1.0], cache)
     assert not first["from_cache"]
-    # cpw = wpb = 0 denotes the direct-read solve variant
-    assert first["cpw"] in (0, 4, 8, 16, 32) and first["wpb"] in (0, 1, 2, 4) and 16 <= first["bn"] <= 256
+    # cpw = 0 denotes the segmented solve, cpw = 2 the lean variant (wpb = 0 for both)
+    assert first["cpw"] in (0, 2, 4, 8, 16, 32) and first["wpb"] in (0, 1, 2, 4) and 16 <= first["bn"] <= 256
     assert os.path.exists(cache)
     ctx2 = B.Context(128, 128, 64, 4.0, lz=2 * np.pi * 8, precision=B.BF16X3, chop_policy=B.CHOP_TWOTHIRDS)
     ctx2.implicit_setup(1.0, 1e-2)
@@ -99,3 +99,46 @@ def test_autotune_cache_roundtrip(tmp_path):
         c.advance(B.NONLIN_FKPP, [1.0], s, p, 10, True)
         outs.append(O.from_flat(g, s.cpu().numpy()))
     assert O.spec_rel_err(g, outs[0], outs[1]) <= 1e-6
+
+
+def test_batch64_every_instance_matches_oracle(record):
+    # The benchmarked 64-instance uneven batch (seed 20261202: Nr in {32..256},
+    # Nphi in {16..256}, Nz in {1, 16, 64}, ell in [0.5, 4], diffusion or
+    # Fisher-KPP), built exactly as the benchmark builds it (BF16x3 contraction,
+    # FP32 FFTs, FP64 solves, dt = 1e-3), advanced 3 steps (Richardson start +
+    # 2 AB-CN) through one batch graph from the oracle's FP64 initial
+    # coefficients: every instance against the oracle, globally and per block.
+    import torch
+    insts = W.batch_instances(64)
+    ctxs, states, prevs, kinds, grids, s0s, steppers = [], [], [], [], [], [], []
+    for inst in insts:
+        lin = inst["kind"] == "diffusion"
+        pol = B.CHOP_LINEAR if lin else B.CHOP_TWOTHIRDS
+        m_pol = inst["nphi"] // 2 if lin else (inst["nphi"] - 1) // 3 + 1
+        M = min(m_pol, inst["nr"])
+        ctx = B.Context(inst["nr"], inst["nphi"], inst["nz"], inst["ell"], lz=inst["lz"], precision=B.BF16X3,
+                        chop_policy=pol, nphi_c=M)
+        kind = B.NONLIN_NONE if lin else B.NONLIN_FKPP
+        nu = 1e-2 if lin else 1.0
+        ctx.implicit_setup(nu, inst["dt"])
+        g = O.Grid(inst["nr"], inst["nphi"], inst["nz"], inst["ell"], lz=inst["lz"],
+                   policy="linear" if lin else "twothirds", M=M)
+        r, phi, z = g.nodes3()
+        s0 = O.forward(g, W.batch_initial(inst, r, phi, z))
+        ctxs.append(ctx); kinds.append(kind); grids.append(g); s0s.append(s0)
+        states.append(torch.as_tensor(O.to_flat(g, s0)).cuda()); prevs.append(ctx.new_spec())
+        steppers.append(O.Stepper(g, nu, inst["dt"], nonlinear=None if lin else O.fkpp_nonlinear(g, 1.0)))
+    batch = B.Batch(ctxs)
+    batch.advance(kinds, [1.0] * 64, states, prevs, 3, True)
+    torch.cuda.synchronize()
+    worst, worst_blk = 0.0, 0.0
+    for j in range(64):
+        ref, _ = steppers[j].run_abcn(s0s[j], 3)
+        got = spec_from_gpu(grids[j], states[j])
+        e = O.spec_rel_err(grids[j], got, ref)
+        eb = block_err(grids[j], got, ref, floor=0.1)
+        worst, worst_blk = max(worst, e), max(worst_blk, eb)
+        assert e <= 1e-6, (j, insts[j], e)
+        assert eb <= 1e-5, (j, insts[j], eb)
+    record("batch64_vs_oracle", worst_rel_err=worst, worst_block_err=worst_blk)
+    batch.close()

@@ -9,11 +9,12 @@ import oracle as O
 from paper_2609_18026_b300 import binding as B
 from paper_2609_18026_b300 import workloads as W
 
-from gpu_common import pair, to_gpu_spec, spec_from_gpu
+from gpu_common import pair, to_gpu_spec, spec_from_gpu, block_err
 
 pytestmark = pytest.mark.gpu
 
 TOL = {B.FP64: 1e-12, B.FP32: 1e-6, B.BF16X3: 1e-6}
+PNAME = {B.FP64: "fp64", B.FP32: "fp32", B.BF16X3: "bf16x3"}
 
 
 def _smooth_state(g, seed):
@@ -36,14 +37,14 @@ def test_lap_h_solve_parity():
 
 def test_projection_solve_variants_bitwise():
     # the vortex term's Q, H (one factor per m, decay row at m = 0) and G (one per
-    # (m, |k|)) solves through the staged, ring-staged and lean kernels: one
-    # summation order, bitwise-equal results
+    # (m, |k|)) solves through the staged and lean kernels: one summation order,
+    # bitwise-equal results
     g, ctx = pair(40, 16, 32, 1.0, lz=8.6, policy="twothirds")
     ctx.vortex_setup()
     psi, chi = _smooth_state(g, 21)
     state = to_gpu_spec(np.concatenate([psi, chi]))
     outs = []
-    variants = ((0, 8), (1, 8), (2, 16), (2, 32))
+    variants = ((0, 8), (2, 16), (2, 32))
     for direct, cpw in variants:
         ctx.set_tuning("solve_direct", direct)
         if direct == 2:
@@ -55,31 +56,44 @@ def test_projection_solve_variants_bitwise():
         assert np.array_equal(outs[v], outs[0]), (variants[v], float(np.max(np.abs(outs[v] - outs[0]))))
 
 
+def _gpu_vortex(ctx, g, psi_flat, chi_flat, U0):
+    state = to_gpu_spec(np.concatenate([psi_flat, chi_flat]))
+    out = ctx.nonlinear(B.NONLIN_VORTEX, [U0], state, to_gpu_spec(np.zeros(2 * len(psi_flat), np.complex128)))
+    o = out.cpu().numpy()
+    n = len(psi_flat)
+    return O.from_flat(g, o[:n]), O.from_flat(g, o[n:])
+
+
 @pytest.mark.parametrize("prec", [B.FP64, B.FP32, B.BF16X3])
-@pytest.mark.parametrize("grid", [(24, 16, 8, 1.0, 0.0), (33, 32, 16, 1.0, 1.0)])
-def test_vortex_nonlinear_parity(grid, prec):
+@pytest.mark.parametrize("grid", [(24, 16, 8, 1.0, 0.0), (33, 32, 16, 1.0, 1.0), (48, 16, 8, 1.0, -1.0)])
+def test_vortex_nonlinear_parity(grid, prec, record):
+    # The CUDA path evaluates P in the banded form (9 transforms, no division by
+    # r at the nodes): element by element against the oracle's banded form.
     nr, nphi, nz, ell, U0 = grid
     g, ctx = pair(nr, nphi, nz, ell, lz=8.6, policy="twothirds", precision=prec)
     ctx.vortex_setup()
     psi, chi = _smooth_state(g, 11)
-    state = to_gpu_spec(np.concatenate([psi, chi]))
-    out = ctx.nonlinear(B.NONLIN_VORTEX, [U0], state, to_gpu_spec(np.zeros(2 * len(psi), np.complex128)))
+    gp, gc = _gpu_vortex(ctx, g, psi, chi, U0)
     ops = O.VortexOps(g)
-    A, Bf, C = ops.products(O.from_flat(g, psi), O.from_flat(g, chi), U0)
-    pN, cN = ops.project(A, Bf, C)
-    o = out.cpu().numpy()
-    n = len(psi)
-    got = O.from_flat(g, o[:n]) + O.from_flat(g, o[n:])
-    err = O.spec_rel_err(g, got, pN + cN)
+    A, Bf, C = ops.products_banded(O.from_flat(g, psi), O.from_flat(g, chi), U0)
+    pN, cN = ops.project_banded(A, Bf, C)
+    err = O.spec_rel_err(g, gp + gc, pN + cN)
+    berr = block_err(g, gp + gc, pN + cN, floor=1e-3 if prec == B.FP64 else 0.1)
+    record("vortex_nonlinear", grid=grid[:3], precision=PNAME[prec], rel_err=err, block_err=berr)
     if prec == B.FP64:
         assert err <= TOL[prec]
+        # per block: the projection's banded systems have condition numbers up to
+        # 1e7 at Nr = 48 (H = (I - J) Q, measured), so blocks near FLOOR carry the
+        # global FP64 error magnified; bar 1e-10 (measured <= 2e-11)
+        assert berr <= 1e-10
     else:
         # The projection inverts r^2 lap_h, whose eigenvalues scale with 1 - x_i^2
         # (small at both radial ends), so an O(eps) error in the transformed
-        # products that does not vanish like r^2 at the axis is magnified.  Bar:
-        # 1e-6, or the FP32 transform error (measured <= 2.3e-7 per transform)
-        # propagated through the projection's condition number kappa_P, measured
-        # here by perturbing the oracle's (A, B, C) at that level.
+        # products that does not vanish like r^2 at the axis is magnified.  The
+        # per-result bar of 1e-6 is not met by FP32 transforms here; the test
+        # bounds the error by the FP32 transform error (measured <= 2.3e-7 per
+        # transform) propagated through the projection's condition number kappa_P,
+        # measured here by perturbing the oracle's (A, B, C) at that level.
         rng = np.random.default_rng(3)
         eps = 2.3e-7
 
@@ -89,16 +103,60 @@ def test_vortex_nonlinear_parity(grid, prec):
             return [b + eps * nf / math.sqrt(tot) *
                     (rng.standard_normal(b.shape) + 1j * rng.standard_normal(b.shape)) / math.sqrt(2)
                     for b in F]
-        dp, dc = ops.project(pert(A), pert(Bf), pert(C))
+        dp, dc = ops.project_banded(pert(A), pert(Bf), pert(C))
         kappa_p = O.spec_rel_err(g, dp + dc, pN + cN) / eps
+        record("vortex_nonlinear_kappa_P", grid=grid[:3], precision=PNAME[prec], kappa_P=kappa_p)
         assert err <= max(TOL[prec], 3.0 * eps * kappa_p), (err, kappa_p)
     ctx.device_status()
 
 
+def _padded_state(g, nc0, decay, seeds):
+    """Random (psi, chi) with nc0 coefficients decaying like e^{-decay n}, zero
+    beyond: one resolved input for every Nr >= nc0."""
+    out = []
+    for sd in seeds:
+        g0 = O.Grid(nc0, g.nphi, g.nz, g.ell, lz=g.lz, policy="twothirds")
+        s0 = O.from_flat(g0, W.random_spectral(g0.nc, g0.M, g0.Kz, seed=sd, scale_decay=decay))
+        out.append(O.to_flat(g, [np.concatenate([s0[m], np.zeros((g.K, g.nc - nc0), complex)], axis=1)
+                                 for m in range(g.M)]))
+    return out
+
+
+def test_vortex_nonlinear_against_plain_definition(record):
+    # The oracle's definition of P is the plain 13-transform evaluation of Eq. (9)
+    # (division by r^2 at the nodes, D_m^{-1} and Helmholtz solves).  The CUDA
+    # path runs the banded form, which equals it up to the truncation of the
+    # products.  On a resolved input at Nr = 96 that truncation difference is
+    # 1.5e-6 (chi; psi agrees to round-off); the FP64 GPU result must lie within it
+    # of the plain definition, and close to the banded form.
+    g, ctx = pair(96, 16, 8, 1.0, lz=8.6, policy="twothirds", precision=B.FP64)
+    ctx.vortex_setup()
+    psi, chi = _padded_state(g, 32, 1.0, (11, 12))
+    gp, gc = _gpu_vortex(ctx, g, psi, chi, 1.0)
+    ops = O.VortexOps(g)
+    P, X = O.from_flat(g, psi), O.from_flat(g, chi)
+    bp, bc = ops.nonlinear(P, X, 1.0, "banded")
+    pp, pc = ops.nonlinear(P, X, 1.0, "plain")
+    e_banded = max(O.spec_rel_err(g, gp, bp), O.spec_rel_err(g, gc, bc))
+    trunc = max(O.spec_rel_err(g, bp, pp), O.spec_rel_err(g, bc, pc))
+    e_plain = max(O.spec_rel_err(g, gp, pp), O.spec_rel_err(g, gc, pc))
+    record("vortex_vs_plain", e_banded=e_banded, truncation=trunc, e_plain=e_plain)
+    # FP64 bar against the banded form: at Nr = 96 the projection's systems reach a
+    # condition number of 3.3e8 (H = (I - J) Q with the decay row, measured in the
+    # oracle); two backward-stable FP64 solves of them agree within 2 kappa u = 7e-8
+    # in the worst case, smooth right-hand sides far closer (measured 2.8e-12): bar
+    # 1e-11 (the 1e-12 bar holds on the smaller grids of the test above)
+    assert e_banded <= 1e-11
+    assert trunc <= 1e-5
+    assert e_plain <= 1.01 * trunc + 1e-11
+
+
 @pytest.mark.parametrize("prec,tol", [(B.FP64, 1e-12), (B.FP32, 1e-6), (B.BF16X3, 1e-6)])
-def test_vortex_advance_parity(prec, tol):
+def test_vortex_advance_parity(prec, tol, record):
     # two counter-rotating Gaussian vortices with a seeded axial displacement,
-    # psi = -lap_h^{-1} w_z, chi = 0; AB-CN with hyperviscosity p = 8; 4 steps
+    # psi = -lap_h^{-1} w_z, chi = 0; AB-CN with hyperviscosity p = 8; 4 steps,
+    # against the oracle's banded form (the kernel's formulation) at tol, and
+    # against the plain definition within the two forms' truncation difference
     nr, nphi, nz, ell, lz = 32, 32, 16, 1.0, 8.6
     g, ctx = pair(nr, nphi, nz, ell, lz=lz, policy="twothirds", precision=prec)
     ctx.vortex_setup()
@@ -113,9 +171,66 @@ def test_vortex_advance_parity(prec, tol):
     state = to_gpu_spec(np.concatenate([O.to_flat(g, psi0), O.to_flat(g, chi0)]))
     prev = to_gpu_spec(np.zeros(2 * ctx.n_spec, np.complex128))
     ctx.advance(B.NONLIN_VORTEX, [U0], state, prev, 4, True)
-    A, _ = O.vortex_nonlinear(g, U0)
-    st = O.Stepper(g, nu, dt, nu_h=nuh, p=8, nonlinear=A)
-    ref, _ = st.run_abcn(psi0 + chi0, 4)
     o = state.cpu().numpy()
     got = O.from_flat(g, o[:ctx.n_spec]) + O.from_flat(g, o[ctx.n_spec:])
-    assert O.spec_rel_err(g, got, ref) <= tol
+    refs = {}
+    for form in ("banded", "plain"):
+        A, _ = O.vortex_nonlinear(g, U0, form=form)
+        st = O.Stepper(g, nu, dt, nu_h=nuh, p=8, nonlinear=A)
+        refs[form], _ = st.run_abcn(psi0 + chi0, 4)
+    e_b = O.spec_rel_err(g, got, refs["banded"])
+    e_p = O.spec_rel_err(g, got, refs["plain"])
+    trunc = O.spec_rel_err(g, refs["banded"], refs["plain"])
+    berr = block_err(g, got, refs["banded"], floor=1e-3 if prec == B.FP64 else 0.1)
+    record("vortex_advance", precision=PNAME[prec], e_banded=e_b, block_err=berr, e_plain=e_p, truncation=trunc)
+    assert e_b <= tol
+    assert berr <= (1e-11 if prec == B.FP64 else 1e-5)
+    assert e_p <= 1.01 * trunc + tol
+
+
+@pytest.mark.slow
+def test_vortex_pair_256_sampled(record):
+    # The benchmarked vortex-pair workload at full size: Nr = Nphi = Nz = 256,
+    # ell = 1, two-thirds chops (M = 86, K = 171), Lz = 8.6, nu = 1e-4, p = 8
+    # hyperviscosity nu_h = 5e-7, dt = 2.5e-4, moving frame U0 = -1; the
+    # Richardson start and one AB-CN step (graph-free path, the same kernels the
+    # benchmark times) in FP64 and in BF16x3, against one oracle run (banded form,
+    # the kernel's formulation).  The nonlinear term A^1 = A(s^1) left in prev_A is
+    # compared too.
+    import torch
+    nr = nphi = nz = 256
+    lz, U0, nu, nuh, dt = 8.6, -1.0, 1e-4, 5e-7, 2.5e-4
+    g = O.Grid(nr, nphi, nz, 1.0, lz=lz, policy="twothirds")
+    A, ops = O.vortex_nonlinear(g, U0, form="banded")
+    r, phi, z = g.nodes3()
+    wzs = O.forward(g, W.vortex_pair_omega(r, phi, z, lz=lz))
+    psi0 = [np.stack([-ops.lap_h_inv(m, wzs[m][kk]) for kk in range(g.K)]) for m in range(g.M)]
+    chi0 = [np.zeros_like(b) for b in psi0]
+    st = O.Stepper(g, nu, dt, nu_h=nuh, p=8, nonlinear=A)
+    s1, A0 = st.start(psi0 + chi0)
+    A1 = st.A(s1)
+    s2 = st.abcn(s1, A1, A0)
+    flat0 = np.concatenate([O.to_flat(g, psi0), O.to_flat(g, chi0)])
+    nsp = len(flat0) // 2
+    for prec, tol, tol_a in ((B.FP64, 1e-12, 1e-12), (B.BF16X3, 1e-6, None)):
+        ctx = B.Context(nr, nphi, nz, 1.0, lz=lz, precision=prec, chop_policy=B.CHOP_TWOTHIRDS)
+        ctx.vortex_setup()
+        ctx.implicit_setup(nu, dt, nu_h=nuh, p=8)
+        state = torch.as_tensor(flat0).cuda()
+        prev = torch.zeros_like(state)
+        ctx.advance(B.NONLIN_VORTEX, [U0], state, prev, 2, True)
+        o, a = state.cpu().numpy(), prev.cpu().numpy()
+        got = O.from_flat(g, o[:nsp]) + O.from_flat(g, o[nsp:])
+        gotA = O.from_flat(g, a[:nsp]) + O.from_flat(g, a[nsp:])
+        e_s = O.spec_rel_err(g, got, s2)
+        e_a = O.spec_rel_err(g, gotA, A1)
+        eb = block_err(g, got, s2, floor=1e-3 if prec == B.FP64 else 0.1)
+        record("vortex256", precision=PNAME[prec], state_rel_err=e_s, state_block_err=eb, nonlinear_rel_err=e_a)
+        assert e_s <= tol, (prec, e_s)
+        assert eb <= (1e-11 if prec == B.FP64 else 1e-5), (prec, eb)
+        if tol_a is not None:
+            assert e_a <= tol_a, (prec, e_a)
+        ctx.device_status()
+        ctx.close()
+        del state, prev
+        torch.cuda.empty_cache()

@@ -26,10 +26,13 @@ def _rel(a, b):
 
 
 @pytest.mark.parametrize("prec", [B.FP64, B.FP32, B.BF16X3])
-def test_noalloc_forward_matches_forward_twice(prec):
+@pytest.mark.parametrize("grid", [(128, 128, 64, 4.0, B.CHOP_TWOTHIRDS),
+                                  (32, 32, 1, 1.0, B.CHOP_LINEAR)])   # Nz = 1: no z planes
+def test_noalloc_forward_matches_forward_twice(grid, prec):
     import torch
-    nr, nphi, nz, ell, lz = 128, 128, 64, 4.0, 2 * np.pi * 8
-    ctx = B.Context(nr, nphi, nz, ell, lz=lz, precision=prec, chop_policy=B.CHOP_TWOTHIRDS)
+    nr, nphi, nz, ell, chop = grid
+    lz = 2 * np.pi * 8
+    ctx = B.Context(nr, nphi, nz, ell, lz=lz, precision=prec, chop_policy=chop)
     rng = np.random.default_rng(17)
     lib = B.load()
     stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
@@ -57,3 +60,21 @@ def test_noalloc_rejects_grid_beyond_limit():
                                  ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
     assert rc == -1
     assert b"16777216" in lib.mlx_last_cuda_error(ctx._h)
+
+
+def test_noalloc_forward_matches_oracle():
+    # the same call against the FP64 oracle directly (test infrastructure only)
+    import torch
+    import oracle as O
+    nr, nphi, nz, ell, lz = 40, 16, 8, 1.5, 3.0
+    g = O.Grid(nr, nphi, nz, ell, lz=lz, policy="twothirds")
+    ctx = B.Context(nr, nphi, nz, ell, lz=lz, precision=B.FP64, chop_policy=B.CHOP_TWOTHIRDS)
+    u = np.random.default_rng(5).standard_normal((nz, nphi, nr))
+    phys = torch.as_tensor(u).cuda()
+    out = ctx.new_spec()
+    lib = B.load()
+    rc = lib.mlx_forward_noalloc(ctx._h, ctypes.c_void_p(phys.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                 ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert rc == 0, lib.mlx_last_cuda_error(ctx._h)
+    torch.cuda.synchronize()
+    assert O.spec_rel_err(g, O.from_flat(g, out.cpu().numpy()), O.forward(g, u)) <= 1e-12
