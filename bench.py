@@ -36,6 +36,7 @@ NR, NPHI, NZ, ELL = 128, 128, 64, 4.0
 LZ = 2.0 * math.pi * 8.0
 DT, D_COEF, GAMMA = 1e-2, 1.0, 1.0
 STEPS_PER_BENCH_STEP = 100
+ARGS_T0 = 0.0
 WORKLOAD = "fkpp3d_128x128x64"
 METRIC = "timesteps/s"
 
@@ -113,26 +114,34 @@ class ClockSampler:
 _ORACLE = {}
 
 
-def oracle_sample(nsteps):
+def oracle_sample(nsteps, threads=None):
     """Time the FP64 oracle, as it stands, on the full-size workload for `nsteps`
     time steps from t = 0 (the first is the Richardson start); the grid and LU
-    factors are built once, outside the timing.  Returns (timesteps/s, threads, s)."""
+    factors are built once, outside the timing.  threads limits the BLAS calls to
+    that many threads (None leaves the library's default).  Returns (timesteps/s,
+    threads used, seconds)."""
+    import contextlib
     import oracle as O
     from paper_2609_18026_b300 import workloads as W
     try:
-        from threadpoolctl import threadpool_info
-        threads = max([d.get("num_threads", 1) for d in threadpool_info()] or [1])
+        from threadpoolctl import threadpool_info, threadpool_limits
+        ctxm = threadpool_limits(threads) if threads else contextlib.nullcontext()
     except Exception:
-        threads = 1
+        threadpool_info = None
+        ctxm = contextlib.nullcontext()
     if not _ORACLE:
         g = O.Grid(NR, NPHI, NZ, ELL, lz=LZ, policy="twothirds")
         r, phi, z = g.nodes3()
         _ORACLE["st"] = O.Stepper(g, D_COEF, DT, nonlinear=O.fkpp_nonlinear(g, GAMMA))
         _ORACLE["s0"] = O.forward(g, W.fkpp_seed(r, phi, z))
-    t0 = time.perf_counter()
-    _ORACLE["st"].run_abcn(_ORACLE["s0"], nsteps)
-    sec = time.perf_counter() - t0
-    return nsteps / sec, threads, sec
+    with ctxm:
+        used = 1
+        if threadpool_info is not None:
+            used = max([d.get("num_threads", 1) for d in threadpool_info()] or [1])
+        t0 = time.perf_counter()
+        _ORACLE["st"].run_abcn(_ORACLE["s0"], nsteps)
+        sec = time.perf_counter() - t0
+    return nsteps / sec, used, sec
 
 
 def run_reference(args, rank, world):
@@ -184,22 +193,40 @@ def tc_executed_flops(ctx, forward):
     return 6.0 * 2.0 * 128 * bn * tot
 
 
-# nominal FP64 rate of a B300 (TFLOP/s)
-FP64_PEAK_TFLOPS = 1.25
+# FP64 FMA rate of this GPU measured with independent FMA chains (148 SMs x 2 FMA
+# per cycle at 2032 MHz): 1.20 TFLOP/s, against the nominal 1.25
+FP64_PEAK_TFLOPS = 1.20
 
-# DRAM bytes (read + write) per launch at this workload, from the ncu capture
-# summarised in profiles/band_solve_seg_fkpp3d_128x128x64.md (current kernel version);
-# absent = not captured for the current code
-TRAFFIC = {"band_solve": 21573120 + 0}
+# DRAM bytes (read + write) per launch of the dominant kernel at this workload, from
+# one ncu capture of the current kernel version (None = not captured for it)
+TRAFFIC = {"band_solve": 21573120}
 
 
 def band_solve_flops(ctx, kl=2):
     """Algorithmic FP64 flops of one AB-CN banded solve launch: per row of every real
     chain (2 K T rows), the right-hand side 2s + dt/2 (3A - A_prev) (5), forward
-    elimination with kl multipliers (2 kl), back substitution over 2 kl upper entries
-    and the diagonal (4 kl + 1) and the final "- s" (1)."""
+    elimination with kl multipliers (2 kl), back substitution over kl upper entries
+    and the diagonal (2 kl + 1) and the final "- s" (1) (no row interchanges occur
+    in these systems, so the pivoting fill is zero)."""
     tri = sum(ctx.nc - m for m in range(ctx.M))
-    return 2.0 * ctx.K * tri * (5 + 2 * kl + 4 * kl + 1 + 1)
+    return 2.0 * ctx.K * tri * (5 + 2 * kl + 2 * kl + 1 + 1)
+
+
+def band_solve_bytes(ctx):
+    """Algorithmic DRAM bytes of one banded-solve launch in the survey's unit: the
+    cached fill-free LU factors (5 doubles per system row (m, |k|, n), Kz T rows: 4 MB
+    at 128 x 128 x 64) plus one right-hand side in and one solution out (n_spec
+    complex128 each)."""
+    tri = sum(ctx.nc - m for m in range(ctx.M))
+    return 5 * 8 * ctx.Kz * tri + 2 * 16 * ctx.n_spec
+
+
+def band_solve_bytes_full(ctx):
+    """What the fused AB-CN launch must move at least: s, A^j, A^{j-1} in and
+    s^{j+1} out, plus fill-free LU factors (2 multipliers, diagonal and 2 upper
+    entries: 5 doubles per system row)."""
+    tri = sum(ctx.nc - m for m in range(ctx.M))
+    return 4 * 16 * ctx.n_spec + 5 * 8 * ctx.Kz * tri
 
 
 def algorithmic(kernel, ctx, nz_gt1=True):
@@ -227,7 +254,7 @@ def algorithmic(kernel, ctx, nz_gt1=True):
     return 0, 0.0
 
 
-def measure_vortex(B, W, torch, dev, stream, steps=20, prec=None):
+def measure_vortex(B, W, torch, dev, stream, steps=20, prec=None, with_errors=True):
     """256^3 counter-rotating vortex pair (Nr = Nphi = Nz = 256, ell = 1, two-thirds
     chops, Lz = 8.6, nu = 1e-4, nu_h = 5e-7, p = 8, dt = 2.5e-4, in the frame moving
     with the pair: U0 = -Gamma / (2 pi b) = -1): AB-CN steps
@@ -262,10 +289,10 @@ def measure_vortex(B, W, torch, dev, stream, steps=20, prec=None):
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
-    ctx.timing(True)
+    ctx.timing(2)
     ctx.advance(B.NONLIN_VORTEX, [U0], state, prev, 2, False)
     kt = ctx.timing_read()
-    ctx.timing(False)
+    ctx.timing(0)
     ok = bool(torch.isfinite(state.real).all().item())
     ctx.device_status()
     tot = sum(v[1] for v in kt.values())
@@ -273,21 +300,89 @@ def measure_vortex(B, W, torch, dev, stream, steps=20, prec=None):
            "timed_steps": steps, "setup_s": setup_s, "finite": ok,
            "precision": {B.BF16X3: "bf16x3", B.FP32: "fp32", B.FP64: "fp64"}[prec],
            "transforms_per_step": 9, "kernel_share": {k: round(v[1] / tot, 3) for k, v in kt.items()},
-           "kernel_avg_us": {k: 1000.0 * v[1] / v[0] for k, v in kt.items()}}
+           "kernel_avg_us": {k: round(1000.0 * v[1] / v[0], 1) for k, v in kt.items()}}
+    if with_errors and prec != B.FP64:
+        # accuracy per result against the FP64 form (itself within 1e-14 of the
+        # oracle at this size): the nonlinear term at the current state, and one
+        # AB-CN step from the same (state, A^{j-1})
+        c64 = B.Context(nr, nphi, nz, 1.0, lz=lz, precision=B.FP64, chop_policy=B.CHOP_TWOTHIRDS)
+        c64.vortex_setup()
+        c64.implicit_setup(1e-4, 2.5e-4, nu_h=5e-7, p=8)
+
+        def rel2(a_, b_):
+            return float(torch.linalg.norm(a_ - b_).item() / torch.linalg.norm(b_).item())
+        n_mix = ctx.nonlinear(B.NONLIN_VORTEX, [U0], state, torch.zeros_like(state))
+        n_64 = c64.nonlinear(B.NONLIN_VORTEX, [U0], state, torch.zeros_like(state))
+        out["nonlinear_rel_err_vs_fp64"] = rel2(n_mix, n_64)
+        s_a, p_a = state.clone(), prev.clone()
+        s_b, p_b = state.clone(), prev.clone()
+        ctx.advance(B.NONLIN_VORTEX, [U0], s_a, p_a, 1, False)
+        c64.advance(B.NONLIN_VORTEX, [U0], s_b, p_b, 1, False)
+        out["state_rel_err_vs_fp64"] = rel2(s_a, s_b)
+        c64.device_status()
+        c64.close()
+        del n_mix, n_64, s_a, p_a, s_b, p_b
     ctx.close()
     return out
+
+
+def measure_vortex_long(B, W, torch, dev, stream, steps=2000, prec=None):
+    """Boundedness of the 256^3 vortex pair (the benchmarked configuration) over
+    `steps` AB-CN steps at dt = 2.5e-4 (t = 0.5 for 2000 steps): spectral l2 norms of
+    psi and chi and the circulation diagnostic of psi every 100 steps, finiteness,
+    and the device status word (MLX_ENUMERIC on any non-finite product)."""
+    import math as _m
+    prec = B.FP64 if prec is None else prec
+    nr = nphi = nz = 256
+    lz, U0 = 8.6, -1.0
+    ctx = B.Context(nr, nphi, nz, 1.0, lz=lz, precision=prec, chop_policy=B.CHOP_TWOTHIRDS)
+    ctx.vortex_setup()
+    ctx.implicit_setup(1e-4, 2.5e-4, nu_h=5e-7, p=8)
+    x, w, r = ctx.nodes()
+    phi = 2 * _m.pi * np.arange(nphi) / nphi
+    zz = lz * np.arange(nz) / nz
+    wz = W.vortex_pair_omega(r[None, None, :], phi[None, :, None], zz[:, None, None], lz=lz)
+    ws = ctx.forward(torch.as_tensor(wz, dtype=ctx.phys_dtype, device=dev), ctx.new_spec())
+    psi = ctx.lap_h_solve(-ws, ctx.new_spec())
+    state = torch.zeros(2 * ctx.n_spec, dtype=torch.complex128, device=dev)
+    state[:ctx.n_spec] = psi
+    prev = torch.zeros_like(state)
+    hist = []
+    t0 = time.perf_counter()
+    done = 0
+    while done < steps:
+        k = min(100, steps - done)
+        ctx.advance(B.NONLIN_VORTEX, [U0], state, prev, k, done == 0)
+        done += k
+        d = ctx.diag(state[:ctx.n_spec])
+        hist.append({"step": done, "psi_l2": ctx.diag(state[:ctx.n_spec])["spec_l2"],
+                     "chi_l2": ctx.diag(state[ctx.n_spec:])["spec_l2"], "psi_integral": d["integral"]})
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    ok = bool(torch.isfinite(state.real).all().item() and torch.isfinite(state.imag).all().item())
+    status = "ok"
+    try:
+        ctx.device_status()
+    except B.MlxError as e:
+        status = str(e)
+    ctx.close()
+    return {"workload": "vortex_pair_256^3_long", "precision": {B.BF16X3: "bf16x3", B.FP64: "fp64"}.get(prec, prec),
+            "steps": steps, "dt": 2.5e-4, "t_end": steps * 2.5e-4, "finite": ok, "device_status": status,
+            "wall_s": wall, "history": hist}
 
 
 def measure_batch(B, W, torch, dev, stream, steps=100, n=64, tune_cache=None):
     """64 uneven independent 2-D/3-D diffusion and Fisher-KPP instances (seed
     20261202: Nr in {32..256}, Nphi in {16..256}, Nz in {1, 16, 64}, ell in
     [0.5, 4]), FP32 transforms (BF16x3 contraction), FP64 solves, dt = 1e-3,
-    advanced together by one CUDA graph per step pair."""
+    advanced together by one CUDA graph per step pair.  Timed twice: with the
+    batch's default launch shapes, and with every member's shapes chosen by the
+    autotuner (read from tune_cache when it holds them, else timed now and
+    appended to it)."""
     import math as _m
     t0 = time.perf_counter()
     insts = W.batch_instances(n)
     ctxs, states, prevs, kinds, coeffs = [], [], [], [], []
-    tuned = 0
     for inst in insts:
         pol = B.CHOP_LINEAR if inst["kind"] == "diffusion" else B.CHOP_TWOTHIRDS
         m_pol = inst["nphi"] // 2 if pol == B.CHOP_LINEAR else (inst["nphi"] - 1) // 3 + 1
@@ -296,9 +391,6 @@ def measure_batch(B, W, torch, dev, stream, steps=100, n=64, tune_cache=None):
                         chop_policy=pol, nphi_c=min(m_pol, inst["nr"]))
         kind = B.NONLIN_NONE if inst["kind"] == "diffusion" else B.NONLIN_FKPP
         ctx.implicit_setup(1e-2 if kind == B.NONLIN_NONE else 1.0, inst["dt"])
-        if tune_cache and os.path.exists(tune_cache):
-            if ctx.autotune(kind, [1.0], tune_cache)["from_cache"]:
-                tuned += 1
         x, w, r = ctx.nodes()
         phi = 2 * _m.pi * np.arange(inst["nphi"]) / inst["nphi"]
         zz = inst["lz"] * np.arange(inst["nz"]) / inst["nz"]
@@ -307,16 +399,20 @@ def measure_batch(B, W, torch, dev, stream, steps=100, n=64, tune_cache=None):
         ctxs.append(ctx); states.append(s); prevs.append(ctx.new_spec()); kinds.append(kind); coeffs.append(1.0)
     setup_s = time.perf_counter() - t0
     batch = B.Batch(ctxs)
-    batch.advance(kinds, coeffs, states, prevs, 3, True)
-    batch.advance(kinds, coeffs, states, prevs, 4, False)
-    torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    batch.advance(kinds, coeffs, states, prevs, steps, False)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
+
+    def timed_batch():
+        batch.advance(kinds, coeffs, states, prevs, 3, True)
+        batch.advance(kinds, coeffs, states, prevs, 4, False)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        batch.advance(kinds, coeffs, states, prevs, steps, False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    ms = timed_batch()
     # the same instances one after another (graph per instance), for comparison
     e0.record(stream)
     for j, ctx in enumerate(ctxs):
@@ -324,14 +420,28 @@ def measure_batch(B, W, torch, dev, stream, steps=100, n=64, tune_cache=None):
     e1.record(stream)
     torch.cuda.synchronize()
     ms_seq = e0.elapsed_time(e1)
+    tuned = from_cache = 0
+    ms_tuned = None
+    if tune_cache is not None:
+        t1 = time.perf_counter()
+        for j, ctx in enumerate(ctxs):
+            got = ctx.autotune(kinds[j], [1.0], tune_cache)
+            tuned += 1
+            from_cache += int(got["from_cache"])
+        tune_s = time.perf_counter() - t1
+        ms_tuned = timed_batch()
     ok = all(bool(torch.isfinite(s.real).all().item()) for s in states)
     batch.close()
     for c in ctxs:
         c.close()
-    return {"workload": "batch64_uneven", "instances": n, "instance_timesteps_per_s": n * steps / (ms / 1000.0),
-            "batch_step_ms": ms / steps, "sequential_instance_timesteps_per_s": n * steps / (ms_seq / 1000.0),
-            "speedup_vs_sequential": ms_seq / ms, "timed_steps": steps, "setup_s": setup_s,
-            "autotuned_from_cache": tuned, "finite": ok}
+    out = {"workload": "batch64_uneven", "instances": n, "instance_timesteps_per_s": n * steps / (ms / 1000.0),
+           "batch_step_ms": ms / steps, "sequential_instance_timesteps_per_s": n * steps / (ms_seq / 1000.0),
+           "speedup_vs_sequential": ms_seq / ms, "timed_steps": steps, "setup_s": setup_s, "finite": ok}
+    if ms_tuned is not None:
+        out["autotuned"] = {"instances": tuned, "from_cache": from_cache, "tune_s": tune_s,
+                            "instance_timesteps_per_s": n * steps / (ms_tuned / 1000.0),
+                            "batch_step_ms": ms_tuned / steps}
+    return out
 
 
 def measure_surrogate(torch, n_traj=96, n_test=16, epochs=150, batch=128, lr=2e-3):
@@ -345,6 +455,35 @@ def measure_surrogate(torch, n_traj=96, n_test=16, epochs=150, batch=128, lr=2e-
     out = SG.run(n_traj, n_test, epochs=epochs, batch=batch, lr=lr, log=None)
     out["workload"] = "vortex_pair_64^3_surrogate"
     out["tolerance"] = 1e-4
+    return out
+
+
+def measure_surrogate_step(batch=128, steps=2, seed=0):
+    """Time mlx_sur_train_step on seeded synthetic data at the workload's size (D =
+    4 n_spec of the 64^3 grid, width 64): `steps` steps, CUDA events around the last."""
+    import torch
+    from paper_2609_18026_b300 import binding as B
+    from paper_2609_18026_b300.surrogate import CONFIG as cfg
+    torch.cuda.init()
+    M, K, nc = 22, 43, cfg["nr"]     # two-thirds chops of the 64^3 grid
+    D = 4 * K * sum(nc - m for m in range(M))
+    sur = B.Surrogate(D, width=cfg["width"], bmax=batch, seed=seed)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    X = torch.as_tensor(rng.standard_normal((2 * batch, D)), dtype=torch.float32).to(torch.bfloat16).cuda()
+    T = torch.as_tensor(rng.standard_normal((2 * batch, D)) * 0.1, dtype=torch.float32).cuda()
+    idx = torch.arange(batch, dtype=torch.int32, device="cuda")
+    for _ in range(steps - 1):
+        sur.train_step(X, T, idx, 1e-3)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    sur.train_step(X, T, idx, 1e-3)
+    e1.record()
+    torch.cuda.synchronize()
+    sur.status()
+    out = dict(D=D, batch=batch, train_step_ms=e0.elapsed_time(e1))
+    sur.close()
     return out
 
 
@@ -459,6 +598,11 @@ def run_gpu(args, rank, world):
     ctx.advance(B.NONLIN_FKPP, [GAMMA], p32, q32, 1, False)
     step_err = spec_rel(p32, p64)
     nonl_err = spec_rel(q32, q64)
+    # conditioning of A = gamma u (1 - u) at that state: a transform error du gives
+    # dA = gamma (1 - 2u) du, so the relative error of A can exceed that of u by
+    # kappa_A = max|1 - 2u| ||u|| / ||u (1 - u)||
+    u_phys = ctx64.backward(s64, ctx64.new_phys()).cpu().numpy()
+    kappa_a = float(np.max(np.abs(1 - 2 * u_phys)) * np.linalg.norm(u_phys) / np.linalg.norm(u_phys * (1 - u_phys)))
 
     # ---- transform pair alone (backward + forward through the C-ABI)
     spec_in = s.clone()
@@ -479,46 +623,83 @@ def run_gpu(args, rank, world):
     torch.cuda.synchronize()
     pair_per_s = npair / (e0.elapsed_time(e1) / 1000.0)
 
-    # ---- per-kernel CUDA-event timing of the same bench steps (instrumented pass)
+    # ---- per-kernel device times inside the replayed graphs: the same bench steps
+    # with an event-record node before and after every kernel node (timing mode 2;
+    # the replays of one step pair are separated by a host synchronisation)
     s_i, a_i = fresh(ctx, u0_32)
-    ctx.timing(True)
-    run_steps(ctx, s_i, a_i, 2, False)          # bench steps 1-2 exactly as timed above
+    ctx.timing(2)
+    flush.fill_(7)
+    run_steps(ctx, s_i, a_i, 1, False)          # bench step 1 exactly as timed above
     kt = ctx.timing_read()
-    ctx.timing(False)
-    launches_2 = sum(v[0] for v in kt.values())
-    ctx.timing(True)
-    ctx.advance(B.NONLIN_FKPP, [GAMMA], s_i, a_i, 10, False)
-    steady = sum(v[0] for v in ctx.timing_read().values()) / 10.0   # launches per AB-CN step
-    ctx.timing(False)
-    first_step_launches = launches_2 - steady * STEPS_PER_BENCH_STEP
-    gpu_launches = int(round(first_step_launches + steady * STEPS_PER_BENCH_STEP * (args.steps - 1)))
-    total_k = sum(v[1] for v in kt.values())
-    top = max(kt.items(), key=lambda kv: kv[1][1])
-    top_name, (top_n, top_ms) = top[0], top[1]
-    avg_s = top_ms / top_n / 1000.0
-    bytes_, flops_ = algorithmic(top_name, ctx)
-    hbm_peak, peak_kind = peaks()
-    achieved = bytes_ / avg_s / 1e9
-    hbm_view = {"kernel": top_name, "bound": "hbm", "achieved": achieved, "peak": hbm_peak,
-                "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": TRAFFIC.get(top_name),
-                "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs, copy)",
-                "algorithmic_bytes_per_launch": bytes_, "avg_launch_us": avg_s * 1e6,
-                "share_of_kernel_time": top_ms / total_k}
+    ctx.timing(0)
+    launches_first = sum(v[0] for v in kt.values())
+    ctx.timing(2)
+    ctx.advance(B.NONLIN_FKPP, [GAMMA], s_i, a_i, STEPS_PER_BENCH_STEP, False)
+    kt_steady = ctx.timing_read()
+    ctx.timing(0)
+    launches_steady = sum(v[0] for v in kt_steady.values())   # per later bench step
+    gpu_launches = int(launches_first + launches_steady * (args.steps - 1))
+    total_k = sum(v[1] for v in kt_steady.values())
+    top_name, (top_n, top_ms) = max(kt_steady.items(), key=lambda kv: kv[1][1])
+    avg_s = top_ms / top_n / 1000.0                 # with the event nodes beside it
+    step_us = 1000.0 * total_ms / args.steps / STEPS_PER_BENCH_STEP
+    # The event nodes separate the kernel nodes (each kernel then starts only after
+    # the previous one and the event have retired), which lengthens every kernel a
+    # little: the in-graph times give the shares; the dominant kernel's launch
+    # duration is taken from a graph of back-to-back launches of it alone, inputs
+    # L2-resident as inside the step.
+    avg_alone_s = None
     if top_name == "band_solve":
-        # the FP64 banded substitution: bound by the FP64 pipe, not by memory
-        f64 = band_solve_flops(ctx)
-        roofline = {"kernel": top_name, "bound": "alu", "achieved": f64 / avg_s / 1e12,
-                    "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": f64 / avg_s / 1e12 / FP64_PEAK_TFLOPS, "traffic": TRAFFIC.get(top_name),
-                    "peak_source": "nominal B300 FP64 rate (148 SMs, one FP64 pipe each); no measured FP64 peak",
-                    "algorithmic_fp64_flops_per_launch": f64, "avg_launch_us": avg_s * 1e6,
-                    "share_of_kernel_time": top_ms / total_k}
-        roofline_hbm_view = hbm_view
+        gs, ga, gp, go = (ctx.new_spec() for _ in range(4))
+        gs.copy_(s); ga.copy_(a); gp.copy_(a)
+        for _ in range(3):
+            ctx.implicit_solve(B.STEP_ABCN, gs, ga, gp, go)
+        nrep = 50
+        cg = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(cg):
+            for _ in range(nrep):
+                ctx.implicit_solve(B.STEP_ABCN, gs, ga, gp, go)
+        cg.replay()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        cg.replay()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        avg_alone_s = e0.elapsed_time(e1) / nrep / 1000.0
+        del cg
+        avg_s = avg_alone_s
+    hbm_peak, peak_kind = peaks()
+    if top_name == "band_solve":
+        bytes_ = band_solve_bytes(ctx)
+        bytes_full = band_solve_bytes_full(ctx)
     else:
-        roofline = hbm_view
-        roofline_hbm_view = None
-    kernels = {k: {"launches": v[0], "avg_us": 1000.0 * v[1] / v[0], "share": v[1] / total_k}
-               for k, v in sorted(kt.items(), key=lambda kv: -kv[1][1])}
+        bytes_, _ = algorithmic(top_name, ctx)
+        bytes_full = bytes_
+    achieved = bytes_ / avg_s / 1e9
+    roofline = {"kernel": top_name, "bound": "hbm", "achieved": achieved, "peak": hbm_peak,
+                "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": TRAFFIC.get(top_name),
+                "peak_source": peak_kind + " hbm_gbs (MEASURED_PEAKS.json, copy), of measured",
+                "algorithmic_bytes_per_launch": bytes_, "avg_launch_us": avg_s * 1e6,
+                "avg_launch_us_source": ("back-to-back launches of the kernel alone in one CUDA graph"
+                                         if avg_alone_s else "event-record nodes around the kernel in the step graph"),
+                "avg_launch_us_in_step_graph": 1000.0 * top_ms / top_n,
+                "share_of_kernel_time": top_ms / total_k,
+                "timestep_us": step_us,
+                "kernel_node_time_per_timestep_us": 1000.0 * total_k / STEPS_PER_BENCH_STEP}
+    if top_name == "band_solve":
+        f64 = band_solve_flops(ctx)
+        roofline["fuller_bytes_view"] = {
+            "bytes_per_launch": bytes_full, "achieved_gbs": bytes_full / avg_s / 1e9,
+            "frac": bytes_full / avg_s / 1e9 / hbm_peak,
+            "note": "s, A^j, A^{j-1} in and s^{j+1} out (right-hand side fused) plus fill-free LU factors"}
+        roofline["fp64_pipe_view"] = {
+            "bound": "alu", "achieved": f64 / avg_s / 1e12, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": f64 / avg_s / 1e12 / FP64_PEAK_TFLOPS, "algorithmic_fp64_flops_per_launch": f64,
+            "peak_source": "measured FP64 FMA rate of this GPU model (independent chains), of measured"}
+    kernels = {k: {"launches": v[0], "avg_us": round(1000.0 * v[1] / v[0], 2), "share": round(v[1] / total_k, 4)}
+               for k, v in sorted(kt_steady.items(), key=lambda kv: -kv[1][1])}
     roofline_contraction = None
     if ctx.precision == B.BF16X3:
         pk = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
@@ -526,9 +707,9 @@ def run_gpu(args, rank, world):
         tpeak = pk.get("bf16_tflops_sustained", 1400.0)
         roofline_contraction = {}
         for name, fwd in (("legendre_forward", True), ("legendre_backward", False)):
-            if name not in kt:
+            if name not in kt_steady:
                 continue
-            n_, ms_ = kt[name]
+            n_, ms_ = kt_steady[name]
             avg = ms_ / n_ / 1000.0
             ex = tc_executed_flops(ctx, fwd)
             _, useful = algorithmic(name, ctx)
@@ -536,7 +717,7 @@ def run_gpu(args, rank, world):
                 "bound": "tensor", "achieved": ex / avg / 1e12, "peak": tpeak, "unit": "TFLOP/s",
                 "frac": ex / avg / 1e12 / tpeak, "executed_tflop_per_launch": ex / 1e12,
                 "useful_tflop_per_launch": useful / 1e12, "avg_launch_us": avg * 1e6,
-                "peak_source": "measured bf16_tflops_sustained (MEASURED_PEAKS.json)"}
+                "peak_source": "bf16_tflops_sustained (MEASURED_PEAKS.json), of measured"}
 
     # ---- end to end through the C-ABI with host buffers
     host_in = torch.empty((NZ, NPHI, NR), dtype=torch.float32, pin_memory=True)
@@ -565,9 +746,7 @@ def run_gpu(args, rank, world):
     others = {}
     if not args.no_other_workloads:
         for name, fn in (("vortex", lambda: measure_vortex(B, W, torch, dev, stream)),
-                         ("batch", lambda: measure_batch(B, W, torch, dev, stream,
-                                                         tune_cache=os.path.join(ROOT, "paper_2609_18026_b300",
-                                                                                 "tuning_cache.txt"))),
+                         ("batch", lambda: measure_batch(B, W, torch, dev, stream, tune_cache=args.tune_cache)),
                          ("surrogate", lambda: measure_surrogate(torch))):
             try:
                 others[name] = fn()
@@ -578,9 +757,12 @@ def run_gpu(args, rank, world):
         return
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
-        v, threads, sec = oracle_sample(2)
-        cpu = {"value": v, "unit": "timesteps/s", "cores": threads, "kind": "oracle",
-               "sample": "2 full-size time steps of the same workload (Richardson start + 1 AB-CN), %.1f s" % sec}
+        v, threads, sec = oracle_sample(2, threads=os.cpu_count())
+        v1, _, sec1 = oracle_sample(2, threads=1)
+        cpu = {"value": v, "unit": "timesteps/s", "cores": threads, "host_cores": os.cpu_count(), "kind": "oracle",
+               "sample": "2 full-size time steps of the same workload (Richardson start + 1 AB-CN), %.1f s" % sec,
+               "single_thread": {"value": v1, "cores": 1, "sample": "the same 2 steps, %.1f s" % sec1}}
+    t_end = ARGS_T0 + args.steps * STEPS_PER_BENCH_STEP * DT
     line = {
         "metric": METRIC, "value": value, "unit": "timesteps/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup,
@@ -597,11 +779,7 @@ def run_gpu(args, rank, world):
         "transform_pairs_per_s": pair_per_s,
         "fp64_form": {"value": fp64_value, "unit": "timesteps/s", "speedup_mixed_vs_fp64": value / world / fp64_value},
         "fp32_simt_form": None if fp32_value is None else {"value": fp32_value, "unit": "timesteps/s"},
-        "rel_err_fp32_vs_fp64": {"per_time_step_state": step_err, "per_time_step_nonlinear_term": nonl_err,
-                                 "trajectory_at_t10": rel_err,
-                                 "note": "per-step errors are the precision claim; the trajectory deviation is the per-step error amplified ~e^{gamma t} by the linear instability of u = 0 in the reaction term"},
         "roofline": roofline,
-        "roofline_hbm_view": roofline_hbm_view,
         "roofline_contraction": roofline_contraction,
         "kernels": kernels,
         "clocks": clk,
@@ -612,6 +790,15 @@ def run_gpu(args, rank, world):
         "wall_s_timed": t_wall,
         "cpu_baseline": cpu,
         "other_workloads": others,
+        "per_result_error_vs_fp64_form": {
+            "bar": 1e-6,
+            "fkpp_state_one_step": step_err, "fkpp_nonlinear_term": nonl_err,
+            "fkpp_nonlinear_kappa_A": kappa_a, "fkpp_nonlinear_bar_kappa_A": 1e-6 * max(1.0, kappa_a),
+            "vortex256_nonlinear_term": others.get("vortex", {}).get("nonlinear_rel_err_vs_fp64"),
+            "vortex256_state_one_step": others.get("vortex", {}).get("state_rel_err_vs_fp64"),
+            "at_t": t_end,
+            "trajectory_at_t": rel_err,
+            "note": "per-step errors are the precision claim; the trajectory deviation is the per-step error amplified ~e^{gamma t} by the linear instability of u = 0"},
     }
     print(json.dumps(line), flush=True)
 
@@ -625,9 +812,12 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-other-workloads", action="store_true",
                     help="skip the 256^3 vortex, 64-instance batch and 64^3 surrogate measurements")
+    ap.add_argument("--tune-cache", default=os.path.join(ROOT, "paper_2609_18026_b300", "tuning_cache.txt"),
+                    help="launch-shape cache of the batch members (read, and appended to for members it lacks)")
     ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "fp32", "fp64"],
                     help="transform arithmetic of the timed form (the FP64 form is always timed beside it)")
-    ap.add_argument("--profile-workload", default=None, choices=["vortex", "batch", "surrogate"],
+    ap.add_argument("--profile-workload", default=None,
+                    choices=["vortex", "vortex_long", "batch", "surrogate", "surrogate_step"],
                     help="run only that secondary workload and print its measurement (for profiler captures; "
                          "not the benchmark line)")
     args = ap.parse_args()
@@ -640,9 +830,11 @@ def main():
         torch.cuda.init()
         dev = torch.device("cuda:0")
         stream = torch.cuda.current_stream()
-        fn = {"vortex": lambda: measure_vortex(B, W, torch, dev, stream),
-              "batch": lambda: measure_batch(B, W, torch, dev, stream),
-              "surrogate": lambda: measure_surrogate(torch)}[args.profile_workload]
+        fn = {"vortex": lambda: measure_vortex(B, W, torch, dev, stream, with_errors=False),
+              "vortex_long": lambda: measure_vortex_long(B, W, torch, dev, stream),
+              "batch": lambda: measure_batch(B, W, torch, dev, stream, tune_cache=args.tune_cache),
+              "surrogate": lambda: measure_surrogate(torch),
+              "surrogate_step": lambda: measure_surrogate_step()}[args.profile_workload]
         print(json.dumps(fn()), flush=True)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))

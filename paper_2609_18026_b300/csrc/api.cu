@@ -15,8 +15,7 @@ bool aligned16(const void* p) { return (((uintptr_t)p) & 15u) == 0; }
 
 void free_ctx(mlx_ctx* c) {
   if (!c) return;
-  for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
-  c->graphs.clear();
+  mlx_invalidate_graphs(c);
   void* ptrs[] = {c->d_soff, c->d_boff, c->d_x, c->d_w, c->d_r, c->d_P64, c->d_W64, c->d_P32,
                   c->d_W32, c->d_lap, c->d_twphi64, c->d_twz64, c->d_twphi32, c->d_twz32,
                   c->d_tiles_fwd, c->d_tiles_bwd, c->d_mixed, c->d_zm, c->d_phys, c->d_specA,
@@ -276,8 +275,7 @@ int mlx_nonlinear(mlx_ctx* c, int kind, const double* coeffs, int ncoeffs, const
 int mlx_implicit_setup(mlx_ctx* c, double nu, double nu_h, int p, double dt, mlx_stream stream) {
   if (!c || !(dt > 0.0) || nu < 0.0 || nu_h < 0.0) return MLX_EINVAL;
   if (nu_h > 0.0 && p != 4 && p != 6 && p != 8) return MLX_EINVAL;
-  for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
-  c->graphs.clear();
+  mlx_invalidate_graphs(c);
   c->nu = nu; c->nu_h = nu_h; c->p = p; c->dt = dt;
   c->kl = (nu_h > 0.0) ? p : 2;
   // wide hyperviscous bands: the lean solve (32 chains per warp, packed records)
@@ -417,22 +415,19 @@ int mlx_set_tuning(mlx_ctx* c, const char* key, int value) {
   if (strcmp(key, "solve_cpw") == 0) {
     if (value != 4 && value != 8 && value != 16 && value != 32) return MLX_EINVAL;
     c->solve_cpw = value;
-    for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
-    c->graphs.clear();
+    mlx_invalidate_graphs(c);
     return MLX_OK;
   }
   if (strcmp(key, "solve_keep_s") == 0) {
     if (value != 0 && value != 1) return MLX_EINVAL;
     c->solve_keep_s = value;
-    for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
-    c->graphs.clear();
+    mlx_invalidate_graphs(c);
     return MLX_OK;
   }
   if (strcmp(key, "phi_tile") == 0 || strcmp(key, "z_tile") == 0) {
     if (value != 0 && value != 2 && value != 4 && value != 8 && value != 16 && value != 32) return MLX_EINVAL;
     (key[0] == 'p' ? c->phi_tile : c->z_tile) = value;
-    for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
-    c->graphs.clear();
+    mlx_invalidate_graphs(c);
     return MLX_OK;
   }
   if (strcmp(key, "solve_seg") == 0) {
@@ -445,15 +440,13 @@ int mlx_set_tuning(mlx_ctx* c, const char* key, int value) {
       }
       MLX_CUDA_TRY(c, cudaStreamSynchronize(nullptr));
     }
-    for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
-    c->graphs.clear();
+    mlx_invalidate_graphs(c);
     return MLX_OK;
   }
   if (strcmp(key, "solve_lean_cpw") == 0) {
     if (value != 16 && value != 32) return MLX_EINVAL;
     c->solve_lean_cpw = value;
-    for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
-    c->graphs.clear();
+    mlx_invalidate_graphs(c);
     return MLX_OK;
   }
   if (strcmp(key, "solve_direct") == 0) {
@@ -463,15 +456,13 @@ int mlx_set_tuning(mlx_ctx* c, const char* key, int value) {
       if (rc) return rc;
     }
     c->solve_direct = value;
-    for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
-    c->graphs.clear();
+    mlx_invalidate_graphs(c);
     return MLX_OK;
   }
   if (strcmp(key, "tc_products") == 0) {
     if (value != 6 && value != 8) return MLX_EINVAL;
     c->tc_products = value;
-    for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
-    c->graphs.clear();
+    mlx_invalidate_graphs(c);
     return MLX_OK;
   }
   if (strcmp(key, "tc_bn") == 0) {
@@ -479,15 +470,13 @@ int mlx_set_tuning(mlx_ctx* c, const char* key, int value) {
     int rc = mlx_tc_retile(c, value, nullptr);
     if (rc) return rc;
     MLX_CUDA_TRY(c, cudaDeviceSynchronize());
-    for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
-    c->graphs.clear();
+    mlx_invalidate_graphs(c);
     return MLX_OK;
   }
   if (strcmp(key, "solve_wpb") == 0) {
     if (value != 1 && value != 2 && value != 4) return MLX_EINVAL;
     c->solve_wpb = value;
-    for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
-    c->graphs.clear();
+    mlx_invalidate_graphs(c);
     return MLX_OK;
   }
   return MLX_EINVAL;

@@ -22,6 +22,7 @@ struct mlx_batch {
   cudaEvent_t fork = nullptr;
   cudaStream_t cap = nullptr;
   std::map<std::vector<uintptr_t>, cudaGraphExec_t> graphs;
+  std::vector<unsigned long long> gens;   // members' graph generations the cached graphs were made at
 };
 
 namespace {
@@ -112,6 +113,16 @@ int mlx_batch_advance(mlx_batch* b, const int* kinds, const double* coeffs, void
   }
   const int pairs = nsteps / 2;
   if (pairs > 0) {
+    // a member whose launch shapes or setup changed since the graphs were
+    // captured (its generation moved) invalidates them: their kernel nodes may
+    // hold buffers that member has since replaced
+    std::vector<unsigned long long> gens(n);
+    for (int i = 0; i < n; ++i) gens[i] = b->ctxs[i]->graph_gen;
+    if (gens != b->gens) {
+      for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second);
+      b->graphs.clear();
+      b->gens = gens;
+    }
     std::vector<uintptr_t> key;
     for (int i = 0; i < n; ++i) {
       key.push_back((uintptr_t)states[i]);

@@ -172,6 +172,8 @@ struct mlx_ctx {
     }
   };
   std::map<GraphKey, cudaGraphExec_t> graphs;
+  unsigned long long graph_gen = 0;    // bumped whenever the cached graphs are invalidated: a
+                                       // batch holding graphs of this context recaptures them
   cudaStream_t cap_stream = nullptr;
 
   TimingState timing;
@@ -211,6 +213,15 @@ struct TimedLaunch {
     }
   }
 };
+
+// Drop the context's cached CUDA graphs (their kernel nodes hold launch shapes and
+// internal pointers that a tuning change or a new setup replaces) and bump the
+// generation, so that batches holding graphs of this context recapture theirs.
+inline void mlx_invalidate_graphs(mlx_ctx* c) {
+  for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
+  c->graphs.clear();
+  ++c->graph_gen;
+}
 
 // internal solve mode: right-hand side is the input itself
 #define MLX_STEP_PLAIN 3

@@ -261,8 +261,7 @@ int mlx_vortex_prepare(mlx_ctx* c, cudaStream_t st) {
     *p = nullptr;
     MLX_CUDA_TRY(c, cudaMalloc(p, sizeof(double2) * c->n_spec * 2));
   }
-  for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
-  c->graphs.clear();
+  mlx_invalidate_graphs(c);
   MLX_CUDA_TRY(c, cudaStreamSynchronize(st));
   c->vortex_ready = true;
   return MLX_OK;

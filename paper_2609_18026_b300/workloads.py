@@ -122,8 +122,8 @@ def batch_instances(n=64, seed=20261202):
 
     Nr in {32,64,128,256}, Nphi in {16,32,64,128,256}, Nz in {1,16,64},
     ell ~ U[0.5, 4], kind diffusion (nu = 1e-2) or Fisher-KPP (D = 1, gamma = 1)
-    with probability 1/2, Gaussian centre and width as documented in the design
-    notes.  Lz = 2 pi, dt = 1e-3.
+    with probability 1/2, an off-centre Gaussian of width sigma ~ U[0.5, 2] ell
+    centred at (x0, y0) uniform in [-ell, ell]^2.  Lz = 2 pi, dt = 1e-3.
     """
     rng = np.random.Generator(np.random.PCG64(seed))
     out = []
