@@ -284,9 +284,16 @@ int mlx_set_state(mlx_ctx* ctx, int kind, const void* host, long long bytes, voi
  *                bitwise; 0 = off.
  *   "solve_lean_cpw": real chains per warp of the lean variant, 16 or 32
  *                (default 32).
- *   "tc_bn":     column-tile width of the MLX_BF16X3 contraction (16..256; the
- *                width actually used is rounded to a multiple of 16 that
- *                splits the 2K columns evenly);
+ *   "tc_bn":     column-tile width of the MLX_BF16X3 contraction (16..256, used
+ *                up to 128; the width actually used is rounded to a multiple of 16
+ *                that splits the 2K columns evenly);
+ *   "tc_expire": test hook of the bounded waits: 1 makes the MLX_BF16X3
+ *                contraction's first shared-memory stage-reuse wait report expiry
+ *                at once (the kernel then drains the copies and MMAs it issued, frees
+ *                its tensor memory and returns; mlx_device_status reports
+ *                MLX_ETIMEOUT; results of that call are undefined); 0 (default) off.
+ *                Only launches whose CTAs walk more than four 32-wide K chunks reach
+ *                a stage reuse.
  *   "tc_products": BF16 split products per term in the MLX_BF16X3 contraction,
  *                6 (hi*hi, hi*mid, mid*hi, hi*lo, lo*hi, mid*mid) or 8 (adds
  *                mid*lo, lo*mid); default 6.

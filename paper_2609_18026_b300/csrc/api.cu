@@ -459,6 +459,12 @@ int mlx_set_tuning(mlx_ctx* c, const char* key, int value) {
     mlx_invalidate_graphs(c);
     return MLX_OK;
   }
+  if (strcmp(key, "tc_expire") == 0) {
+    if (value != 0 && value != 1) return MLX_EINVAL;
+    c->tc_expire = value;
+    mlx_invalidate_graphs(c);
+    return MLX_OK;
+  }
   if (strcmp(key, "tc_products") == 0) {
     if (value != 6 && value != 8) return MLX_EINVAL;
     c->tc_products = value;

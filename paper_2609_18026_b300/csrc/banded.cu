@@ -673,7 +673,11 @@ __global__ void k_seg_setup(int M, int nc, int Kz, const long long* __restrict__
   }
 }
 
-template <int KL, int SEG>
+// NP (no pivoting): the factorisation made no row interchange in any system of
+// the family, so the pivoted U rows carry exact zeros beyond the KL-th upper
+// entry; the recurrences then skip the swaps and those zero terms (the same
+// products in the same order: bitwise equal results, up to the sign of zero).
+template <int KL, int SEG, bool NP>
 __global__ void k_band_solve_seg(int M, int nc, int Kz, int K, int groups_per_m, int step, int keep_s,
                                  double dt, const long long* __restrict__ soff,
                                  const long long* __restrict__ band_off, const double* __restrict__ U,
@@ -684,6 +688,7 @@ __global__ void k_band_solve_seg(int M, int nc, int Kz, int K, int groups_per_m,
                                  const double* __restrict__ Ap, double* __restrict__ out) {
   using SM = SegSmem<KL, SEG>;
   constexpr int W = SM::W, CPW = SM::CPW, G = SM::G;
+  constexpr int UW = NP ? KL : 2 * KL;                      // upper entries the substitution reads
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int gw = blockIdx.x * (blockDim.x >> 5) + wib;
@@ -717,7 +722,7 @@ __global__ void k_band_solve_seg(int M, int nc, int Kz, int K, int groups_per_m,
     stage_rows(Pb, G * 2 * KL * 8, PHb + r0 * 2 * KL, (long long)Kz * 2 * KL * 8, N, gcnt * 2 * KL * 8, lane);
     stage_rows(PS, G * SEG * KL * KL * 8, PSf + ((long long)m * Kz + k0) * SEG * KL * KL, 0, 1,
                gcnt * SEG * KL * KL * 8, lane);
-    stage_rows(Pi, G * 4, piv + r0, (long long)Kz * 4, N, gcnt * 4, lane);
+    if (!NP) stage_rows(Pi, G * 4, piv + r0, (long long)Kz * 4, N, gcnt * 4, lane);
   }
   cp_async_commit();
   // right-hand sides, every lane busy (as in k_band_solve)
@@ -793,10 +798,12 @@ __global__ void k_band_solve_seg(int M, int nc, int Kz, int K, int groups_per_m,
       for (int q = 0; q < KL; ++q) w[q] = w[q + 1];
       const int jn = j + KL;
       w[KL] = (jn >= N) ? 0.0 : (jn >= j1 ? BH[((sg + 1) * KL + (jn - j1)) * CPW + c] : y[(size_t)jn * CPW]);
-      const int d = Pi[(size_t)j * G + kk] - j;
+      if (!NP) {
+        const int d = Pi[(size_t)j * G + kk] - j;
 #pragma unroll
-      for (int q = 1; q <= KL; ++q)
-        if (q == d) { const double t = w[0]; w[0] = w[q]; w[q] = t; }
+        for (int q = 1; q <= KL; ++q)
+          if (q == d) { const double t = w[0]; w[0] = w[q]; w[q] = t; }
+      }
       y[(size_t)j * CPW] = w[0];
       const double* l = Ls + ((size_t)j * G + kk) * KL;
 #pragma unroll
@@ -843,9 +850,9 @@ __global__ void k_band_solve_seg(int M, int nc, int Kz, int K, int groups_per_m,
   __syncwarp();
   // ---- back substitution, particular run of this segment (zero x after it) ----
   if (act) {
-    double acc[2 * KL];
+    double acc[UW];
 #pragma unroll
-    for (int t = 0; t < 2 * KL; ++t) {
+    for (int t = 0; t < UW; ++t) {
       const int r = j1 - 1 - t;
       acc[t] = (r >= j0) ? y[(size_t)r * CPW] : 0.0;
     }
@@ -854,13 +861,13 @@ __global__ void k_band_solve_seg(int M, int nc, int Kz, int K, int groups_per_m,
     for (int i = j1 - 1; i >= j0; --i) {
       const double xi = __fma_rn(-Us[((size_t)i * G + kk) * W + 1], xn, acc[0]);
 #pragma unroll
-      for (int t = 1; t < 2 * KL; ++t)
+      for (int t = 1; t < UW; ++t)
         if (i - t >= j0) acc[t] = __fma_rn(-Us[((size_t)(i - t) * G + kk) * W + t + 1], xn, acc[t]);
       y[(size_t)i * CPW] = xi;
 #pragma unroll
-      for (int t = 0; t < 2 * KL - 1; ++t) acc[t] = acc[t + 1];
-      const int rn = i - 2 * KL;
-      acc[2 * KL - 1] = (rn >= j0) ? y[(size_t)rn * CPW] : 0.0;
+      for (int t = 0; t < UW - 1; ++t) acc[t] = acc[t + 1];
+      const int rn = i - UW;
+      acc[UW - 1] = (rn >= j0) ? y[(size_t)rn * CPW] : 0.0;
       xn = xi;
     }
   }
@@ -870,14 +877,14 @@ __global__ void k_band_solve_seg(int M, int nc, int Kz, int K, int groups_per_m,
   for (int ss = SEG - 2; ss >= 0; --ss) {
     int a0, a1;
     seg_range<SEG>(N, ss + 1, a0, a1);
-    for (int t = sg; t < 2 * KL; t += SEG) {
+    for (int t = sg; t < UW; t += SEG) {
       if (act) {
         const int r = a0 + t;
         double v = y[(size_t)r * CPW];
         if (ss + 1 < SEG - 1) {
           const double* pb = Pb + ((size_t)r * G + kk) * 2 * KL;
 #pragma unroll
-          for (int t2 = 0; t2 < 2 * KL; ++t2) v = __fma_rn(pb[t2], SB[((ss + 1) * 2 * KL + t2) * CPW + c], v);
+          for (int t2 = 0; t2 < UW; ++t2) v = __fma_rn(pb[t2], SB[((ss + 1) * 2 * KL + t2) * CPW + c], v);
         }
         SB[(ss * 2 * KL + t) * CPW + c] = v;
       }
@@ -886,14 +893,14 @@ __global__ void k_band_solve_seg(int M, int nc, int Kz, int K, int groups_per_m,
   }
   // ---- back corrections ----
   if (act && sg < SEG - 1) {
-    double vv[2 * KL];
+    double vv[UW];
 #pragma unroll
-    for (int t = 0; t < 2 * KL; ++t) vv[t] = SB[(sg * 2 * KL + t) * CPW + c];
+    for (int t = 0; t < UW; ++t) vv[t] = SB[(sg * 2 * KL + t) * CPW + c];
     for (int i = j0; i < j1; ++i) {
       const double* pb = Pb + ((size_t)i * G + kk) * 2 * KL;
       double v = y[(size_t)i * CPW];
 #pragma unroll
-      for (int t = 0; t < 2 * KL; ++t) v = __fma_rn(pb[t], vv[t], v);
+      for (int t = 0; t < UW; ++t) v = __fma_rn(pb[t], vv[t], v);
       y[(size_t)i * CPW] = v;
     }
   }
@@ -967,6 +974,21 @@ int mlx_band_setup(mlx_ctx* c, cudaStream_t st) {
       c->d_Bplus, c->lu_half.U, c->lu_half.L, c->lu_half.piv, c->lu_half.invd, c->lu_full.U,
       c->lu_full.L, c->lu_full.piv, c->lu_full.invd, scratch, stride);
   MLX_LAUNCH_CHECK(c);
+  // did any system interchange rows?  (the pivot of column i is the local row i
+  // when it did not); a family without interchanges runs the pivot-free recurrences
+  {
+    std::vector<int> hp((size_t)rows);
+    for (BandLU* f : {&c->lu_half, &c->lu_full}) {
+      MLX_CUDA_TRY(c, cudaMemcpyAsync(hp.data(), f->piv, sizeof(int) * rows, cudaMemcpyDeviceToHost, st));
+      MLX_CUDA_TRY(c, cudaStreamSynchronize(st));
+      bool none = true;
+      for (int m = 0; m < c->M && none; ++m)
+        for (int i = 0; i < c->nc - m && none; ++i)
+          for (int kz = 0; kz < c->Kz; ++kz)
+            if (hp[(size_t)(c->band_off[m] + (long long)i * c->Kz + kz)] != i) { none = false; break; }
+      f->nopiv = none && c->solve_nopiv;
+    }
+  }
   for (BandLU* f : {&c->lu_half, &c->lu_full}) {
     const int rc = mlx_pack_lean(c, *f, kl, c->d_band_off, c->Kz, rows, st);
     if (rc) return rc;
@@ -1326,7 +1348,8 @@ static int launch_solve(mlx_ctx* c, int step, const BandLU& f, const long long* 
         const int G = SegSmem<KL, S>::G;
         const int gpm = (c->Kz + G - 1) / G;
         const int warps = c->M * gpm;
-        k_band_solve_seg<KL, S><<<(warps + WPB - 1) / WPB, 32 * WPB, pw * WPB, st>>>(
+        auto kern = f.nopiv ? k_band_solve_seg<KL, S, true> : k_band_solve_seg<KL, S, false>;
+        kern<<<(warps + WPB - 1) / WPB, 32 * WPB, pw * WPB, st>>>(
             c->M, c->nc, c->Kz, c->K, gpm, step, keep_s, c->dt, c->d_soff, fac_off, f.U, f.L, f.piv, f.invd,
             f.PHf, f.PHb, f.PSf, (const double*)s, (const double*)A, (const double*)Ap, (double*)out);
         return true;
@@ -1532,8 +1555,10 @@ int mlx_solve_scratch(mlx_ctx* c) {
 
 int mlx_band_prepare(mlx_ctx* c) {
   const int lim = 200 * 1024;
-  MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_band_solve_seg<2, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-  MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_band_solve_seg<2, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+  MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_band_solve_seg<2, 4, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+  MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_band_solve_seg<2, 8, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+  MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_band_solve_seg<2, 4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+  MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_band_solve_seg<2, 8, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
   MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_band_solve<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
   MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_band_solve<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
   {

@@ -16,6 +16,7 @@
 // status word, the tile skips its remaining work, waits (bounded) for what it
 // issued, frees its TMEM and returns.
 #include "mlx_internal.cuh"
+#include "tc_ptx.cuh"
 
 #include <cuda_bf16.h>
 
@@ -24,39 +25,6 @@ namespace {
 constexpr int G_BM = 128;
 constexpr int G_BK = 64;
 constexpr int G_THREADS = 128;
-constexpr long long kGSpin = 1LL << 22;
-
-__device__ __forceinline__ unsigned g_smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ bool g_mbar_try(unsigned bar, unsigned phase) {
-  unsigned ok;
-  asm volatile(
-      "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
-      : "=r"(ok)
-      : "r"(bar), "r"(phase)
-      : "memory");
-  return ok != 0;
-}
-
-__device__ __forceinline__ bool g_mbar_wait(unsigned bar, unsigned phase) {
-  for (long long it = 0; it < kGSpin; ++it)
-    if (g_mbar_try(bar, phase)) return true;
-  return false;
-}
-
-// K-major operand, 128-byte swizzle: rows of 128 bytes, 8-row groups 1024 bytes apart
-__device__ __forceinline__ uint64_t g_sw128_desc(unsigned saddr) {
-  return ((uint64_t)((saddr >> 4) & 0x3FFF)) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
-         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
-}
-
-__device__ __forceinline__ void g_mma(unsigned tmem, uint64_t da, uint64_t db, unsigned idesc, unsigned acc) {
-  asm volatile(
-      "{ .reg .pred p; setp.ne.b32 p, %4, 0; tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p; }"
-      ::"r"(tmem), "l"(da), "l"(db), "r"(idesc), "r"(acc)
-      : "memory");
-}
-
 template <int P>
 __global__ void __launch_bounds__(G_THREADS, 1)
 k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int M, int N,
@@ -66,7 +34,7 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
   __shared__ uint64_t bar_tma[8], bar_mma[8];
   __shared__ unsigned tmem_slot;
   __shared__ int bad_flag;
-  const unsigned raw = g_smem_u32(smem_raw);
+  const unsigned raw = tcx::smem_u32(smem_raw);
   const unsigned pad = (1024u - (raw & 1023u)) & 1023u;
   const unsigned a_bytes = (unsigned)P * G_BM * 128u;
   const unsigned b_bytes = (unsigned)BN * 128u;
@@ -78,14 +46,14 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
 
   if (tid == 0) {
     for (int s = 0; s < stages; ++s) {
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(g_smem_u32(&bar_tma[s])));
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(g_smem_u32(&bar_mma[s])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tcx::smem_u32(&bar_tma[s])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tcx::smem_u32(&bar_mma[s])));
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     bad_flag = 0;
   }
   if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(g_smem_u32(&tmem_slot)),
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tcx::smem_u32(&tmem_slot)),
                  "r"(tmem_cols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
@@ -102,7 +70,7 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
       const int s = j % stages;
       const unsigned sA = raw + pad + (unsigned)s * stage_bytes;
       const unsigned sB = sA + a_bytes;
-      const unsigned bt = g_smem_u32(&bar_tma[s]);
+      const unsigned bt = tcx::smem_u32(&bar_tma[s]);
       const int kx = (kc0 + j) * G_BK;
       asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bt), "r"(stage_bytes) : "memory");
       for (int p = 0; p < P; ++p)
@@ -125,25 +93,25 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
       const int s = j % stages;
       const unsigned sA = raw + pad + (unsigned)s * stage_bytes;
       const unsigned sB = sA + a_bytes;
-      if (!g_mbar_wait(g_smem_u32(&bar_tma[s]), (unsigned)((j / stages) & 1))) { ok = false; atomicOr(err, 16); break; }
+      if (!tcx::mbar_wait(tcx::smem_u32(&bar_tma[s]), (unsigned)((j / stages) & 1))) { ok = false; atomicOr(err, 16); break; }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
       for (int ks = 0; ks < G_BK / 16; ++ks) {
-        const uint64_t db = g_sw128_desc(sB) + (uint64_t)(2 * ks);
+        const uint64_t db = tcx::desc_sw128(sB) + (uint64_t)(2 * ks);
         for (int p = 0; p < P; ++p) {
-          const uint64_t da = g_sw128_desc(sA + (unsigned)p * G_BM * 128u) + (uint64_t)(2 * ks);
+          const uint64_t da = tcx::desc_sw128(sA + (unsigned)p * G_BM * 128u) + (uint64_t)(2 * ks);
           const unsigned dt = tmem + (p == 0 ? 0u : (unsigned)BN);
           const unsigned acc = (j | ks) ? 1u : (p > 1 ? 1u : 0u);
-          g_mma(dt, da, db, idesc, acc);
+          tcx::mma_bf16(dt, da, db, idesc, acc);
         }
       }
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                       g_smem_u32(&bar_mma[s]))
+                       tcx::smem_u32(&bar_mma[s]))
                    : "memory");
       last_commit = j;
       if (issued < nk) {
         // stage s is refilled once the MMAs that read it have completed
-        if (!g_mbar_wait(g_smem_u32(&bar_mma[s]), (unsigned)((j / stages) & 1))) { ok = false; atomicOr(err, 16); break; }
+        if (!tcx::mbar_wait(tcx::smem_u32(&bar_mma[s]), (unsigned)((j / stages) & 1))) { ok = false; atomicOr(err, 16); break; }
         issue(issued);
         ++issued;
       }
@@ -151,13 +119,13 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
     // the last commit covers every MMA issued before it; TMA still in flight on
     // failure is waited for (bounded) so that no copy lands after the CTA exits
     if (last_commit >= 0)
-      if (!g_mbar_wait(g_smem_u32(&bar_mma[last_commit % stages]), (unsigned)((last_commit / stages) & 1))) {
+      if (!tcx::mbar_wait(tcx::smem_u32(&bar_mma[last_commit % stages]), (unsigned)((last_commit / stages) & 1))) {
         ok = false;
         atomicOr(err, 16);
       }
     if (!ok) {
       for (int j = last_commit + 1; j < issued; ++j)
-        g_mbar_wait(g_smem_u32(&bar_tma[j % stages]), (unsigned)((j / stages) & 1));
+        tcx::mbar_wait(tcx::smem_u32(&bar_tma[j % stages]), (unsigned)((j / stages) & 1));
       bad_flag = 1;
     }
   }

@@ -2,7 +2,7 @@
 // pair (Eq. (2) and its Gauss-quadrature inverse, Sec. 3.1) on the 5th-generation
 // tensor cores, split-BF16 with FP32 accumulation.
 //
-// Every FP32/FP64 operand x is split into three BF16 parts
+// Every operand value x is split into three BF16 parts
 //   x_hi = bf16(x), x_mid = bf16(x - x_hi), x_lo = bf16(x - x_hi - x_mid)
 // and a*b is formed from the products hi*hi, hi*mid, mid*hi, hi*lo, lo*hi, mid*mid
 // (six; with eight also mid*lo and lo*mid).  hi*hi accumulates in one FP32 TMEM
@@ -11,67 +11,51 @@
 // This reaches FP32-level accuracy (<= 1e-6 relative per transform) on the BF16
 // tensor pipe.
 //
-// Per output tile (m, 128 rows, BN <= 256 columns):
-//   A (basis, static): BF16 split tables in global memory, staged into shared
-//     memory by TMA (3-D tensor map [split][row][k], 128-byte swizzle, box
-//     64 k x 128 rows), one 64-wide K chunk at a time;
-//   B (data): converted in the kernel from FP32 (mixed layout, forward) or FP64
-//     (spectral state, backward) into the three BF16 parts and written into the
-//     same 128-byte-swizzled K-major layout by all threads;
-//   D: 128 lanes x BN columns of TMEM (FP32) per accumulator, issued by one
-//     thread as tcgen05.mma.cta_group::1.kind::f16 (M = 128, N = BN, K = 16),
-//     4 K-steps x 6 products per chunk, completion tracked by tcgen05.commit ->
-//     mbarrier; two shared-memory stages so the B conversion of chunk k+1 runs
-//     while the tensor core works on chunk k;
-//   epilogue: each of the 4 warps reads its 32 TMEM lanes with tcgen05.ld and
-//     writes its rows (FP64 spectral coefficients, or FP32 mixed values).
 // Forward  D[n - m][c] = sum_i W_m[n][i] X_c[i]     (W = w_i Pbar_n^m(x_i))
 // Backward D[i][c]     = sum_n P_m[n][i] S_c[n]     (A = P_m^T, stored [m][i][n])
-// Column c < K is the real part of wavenumber slot c, c >= K the imaginary part.
-// Every wait on an mbarrier is bounded; on expiry the kernel records an error
-// code in a device word, still waits (bounded) for its issued work, frees its
-// TMEM and returns.
+// Column c of a tile is (wavenumber slot c / 2, Re if c even, Im if odd).
+//
+// One persistent CTA per SM walks its share of the work items (m, 128-row tile,
+// BN-column tile) with warp-specialised roles:
+//   warps 0-3  epilogue: TMEM -> registers -> global (each warp owns its 32 TMEM
+//              lanes), on two TMEM accumulator pairs so that the epilogue of one
+//              tile runs while the tensor core works on the next;
+//   warp 4     TMA producer of the basis operand A (three BF16 parts of a 128 x 32
+//              chunk, 64-byte swizzle) into a four-stage shared-memory ring;
+//   warp 5     one thread issues tcgen05.mma (M = 128, N = BN, K = 16) and commits
+//              each stage back to the ring;
+//   warps 6-13 data operand B: the chunk's FP32 mixed values (forward) or FP64
+//              spectral coefficients (backward) are loaded two chunks ahead into
+//              registers, split into three BF16 parts (FP64 -> FP32 rounding by
+//              integer operations: no FP64 instruction in the kernel) and written in
+//              the same 64-byte-swizzled K-major layout.
+// Every wait on an mbarrier is bounded.  A role that gives up records an error
+// bit in the device word and raises a CTA-wide abort flag; every role then
+// leaves its loop, the producer waits (bounded) for the tensor copies it issued
+// and the MMA thread for the MMAs it issued, and the TMEM is freed only after
+// that.  `expire` (a test hook) makes the producer's first stage-reuse wait
+// report expiry at once.
 #include "mlx_internal.cuh"
+#include "tc_ptx.cuh"
 
 #include <cuda_bf16.h>
 
 namespace {
 
-constexpr int TC_BM = 128;     // tile rows = TMEM lanes
-constexpr int TC_BK = 64;      // K chunk: one 128-byte swizzle atom of BF16
-constexpr int TC_THREADS = 128;
-constexpr long long kSpinLimit = 1LL << 22;
+constexpr int TC_BM = 128;                 // tile rows = TMEM lanes
+constexpr int TC_BK = 32;                  // K chunk: one 64-byte swizzled row of BF16
+constexpr int TC_STAGES = 4;
+constexpr int TC_PROD_WARP = 4;
+constexpr int TC_MMA_WARP = 5;
+constexpr int TC_CONV_WARP0 = 6;
+constexpr int TC_CONV_WARPS = 8;
+constexpr int TC_CONV_THREADS = 32 * TC_CONV_WARPS;
+constexpr int TC_THREADS = 32 * (TC_CONV_WARP0 + TC_CONV_WARPS);   // 448
+constexpr int TC_MAX_BN = 128;
+constexpr unsigned TC_A_PART = TC_BM * 64;                         // one BF16 part of a 128 x 32 chunk
+constexpr unsigned TC_A_BYTES = 3 * TC_A_PART;
 
-__device__ __forceinline__ unsigned smem_u32(const void* p) {
-  return (unsigned)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ bool mbar_try(unsigned bar, unsigned phase) {
-  unsigned ok;
-  asm volatile(
-      "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
-      : "=r"(ok)
-      : "r"(bar), "r"(phase)
-      : "memory");
-  return ok != 0;
-}
-
-__device__ __forceinline__ bool mbar_wait_bounded(unsigned bar, unsigned phase) {
-  for (long long it = 0; it < kSpinLimit; ++it)
-    if (mbar_try(bar, phase)) return true;
-  return false;
-}
-
-// K-major operand in 128-byte-swizzled layout: rows of 128 bytes (64 BF16),
-// 8-row groups 1024 bytes apart, 16-byte chunk index XOR (row mod 8).
-__device__ __forceinline__ uint64_t sw128_desc(unsigned saddr) {
-  return ((uint64_t)((saddr >> 4) & 0x3FFF)) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
-         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
-}
-
-__device__ __forceinline__ unsigned sw128_offset(int row, int k) {
-  return (unsigned)(row * 128 + ((((k >> 3) ^ (row & 7)) & 7) << 4) + ((k & 7) << 1));
-}
+__host__ __device__ constexpr unsigned tc_stage_bytes(int bn) { return TC_A_BYTES + 3u * (unsigned)bn * 64u; }
 
 template <typename T>
 __device__ __forceinline__ void split3(T x, __nv_bfloat16& h, __nv_bfloat16& m, __nv_bfloat16& l) {
@@ -82,207 +66,382 @@ __device__ __forceinline__ void split3(T x, __nv_bfloat16& h, __nv_bfloat16& m, 
   l = __float2bfloat16_rn((float)r2);
 }
 
-__device__ __forceinline__ void mma_bf16(unsigned tmem, uint64_t da, uint64_t db, unsigned idesc,
-                                         unsigned acc) {
-  asm volatile(
-      "{ .reg .pred p; setp.ne.b32 p, %4, 0; tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p; }"
-      ::"r"(tmem), "l"(da), "l"(db), "r"(idesc), "r"(acc)
-      : "memory");
+// FP64 -> FP32 round to nearest even, by integer operations on the two words
+// (h = high word, l = low word); results below 2^-126 flush to zero, above FLT_MAX
+// (and inf / NaN) become inf.
+__device__ __forceinline__ float f64w_to_f32(unsigned h, unsigned l) {
+  const unsigned sign = h & 0x80000000u;
+  const unsigned ah = h & 0x7fffffffu;
+  unsigned f = ((ah - (896u << 20)) << 3) | (l >> 29);
+  const unsigned rem = l & 0x1fffffffu;
+  f += (rem > 0x10000000u) | ((rem == 0x10000000u) & (f & 1u));
+  f = (ah < (897u << 20)) ? 0u : f;
+  f = (ah >= (1151u << 20)) ? 0x7f800000u : f;
+  return __uint_as_float(sign | f);
 }
 
-__device__ __forceinline__ void store_split4(unsigned char* pB, int BN, int col, int k, const float* v) {
-  // four consecutive k (same 16-byte chunk, k % 4 == 0) of one column, three parts
+// FP32 -> FP64 (exact) by integer operations; FP32 subnormals (< 1.2e-38) flush to zero
+__device__ __forceinline__ double f32_to_f64(float v) {
+  const unsigned b = __float_as_uint(v);
+  const unsigned sign = b & 0x80000000u, e = (b >> 23) & 0xffu, mant = b & 0x7fffffu;
+  const unsigned eh = (e == 255u) ? 2047u : e + 896u;
+  const unsigned hi = (e == 0u) ? sign : (sign | (eh << 20) | (mant >> 3));
+  const unsigned lo = (e == 0u) ? 0u : (mant << 29);
+  return __hiloint2double((int)hi, (int)lo);
+}
+
+__device__ __forceinline__ unsigned pack2(__nv_bfloat16 a, __nv_bfloat16 b) {
+  return (unsigned)__bfloat16_as_ushort(a) | ((unsigned)__bfloat16_as_ushort(b) << 16);
+}
+
+// four consecutive k (k % 4 == 0, one 8-byte piece of a 16-byte chunk) of one
+// column, three BF16 parts
+__device__ __forceinline__ void store_split4(unsigned char* pB, int bn, int col, int k, const float (&v)[4]) {
   __nv_bfloat16 h[4], md[4], lo[4];
 #pragma unroll
   for (int j = 0; j < 4; ++j) split3<float>(v[j], h[j], md[j], lo[j]);
-  const unsigned off = sw128_offset(col, k);
-  uint2 a, b, c;
-  a.x = (unsigned)__bfloat16_as_ushort(h[0]) | ((unsigned)__bfloat16_as_ushort(h[1]) << 16);
-  a.y = (unsigned)__bfloat16_as_ushort(h[2]) | ((unsigned)__bfloat16_as_ushort(h[3]) << 16);
-  b.x = (unsigned)__bfloat16_as_ushort(md[0]) | ((unsigned)__bfloat16_as_ushort(md[1]) << 16);
-  b.y = (unsigned)__bfloat16_as_ushort(md[2]) | ((unsigned)__bfloat16_as_ushort(md[3]) << 16);
-  c.x = (unsigned)__bfloat16_as_ushort(lo[0]) | ((unsigned)__bfloat16_as_ushort(lo[1]) << 16);
-  c.y = (unsigned)__bfloat16_as_ushort(lo[2]) | ((unsigned)__bfloat16_as_ushort(lo[3]) << 16);
-  *reinterpret_cast<uint2*>(pB + off) = a;
-  *reinterpret_cast<uint2*>(pB + (size_t)BN * 128 + off) = b;
-  *reinterpret_cast<uint2*>(pB + (size_t)2 * BN * 128 + off) = c;
+  const unsigned off = tcx::sw64_offset(col, k);
+  *reinterpret_cast<uint2*>(pB + off) = make_uint2(pack2(h[0], h[1]), pack2(h[2], h[3]));
+  *reinterpret_cast<uint2*>(pB + (size_t)bn * 64 + off) = make_uint2(pack2(md[0], md[1]), pack2(md[2], md[3]));
+  *reinterpret_cast<uint2*>(pB + (size_t)2 * bn * 64 + off) = make_uint2(pack2(lo[0], lo[1]), pack2(lo[2], lo[3]));
 }
 
-// Columns of a tile are interleaved: column c is (slot c / 2, Re if c even, Im if
-// odd), so one 16-byte complex load feeds two columns and the epilogue writes
-// whole complex values.
+// Walk of one CTA's work: items blockIdx.x, blockIdx.x + gridDim.x, ...; chunks of
+// 32 along the contraction within each item.  Every role walks the same sequence.
+struct Walk {
+  int t, kc, nch, tl;
+  __device__ __forceinline__ bool valid(int nitems) const { return t < nitems; }
+};
+template <bool FWD>
+__device__ __forceinline__ int item_chunks(const LegTile* items, int t, int nc, int nr) {
+  const int kdim = FWD ? nr : nc - items[t].m;
+  return (kdim + TC_BK - 1) / TC_BK;
+}
+template <bool FWD>
+__device__ __forceinline__ Walk walk_begin(const LegTile* items, int nitems, int nc, int nr) {
+  Walk w{(int)blockIdx.x, 0, 0, 0};
+  if (w.t < nitems) w.nch = item_chunks<FWD>(items, w.t, nc, nr);
+  return w;
+}
+template <bool FWD>
+__device__ __forceinline__ void walk_next(Walk& w, const LegTile* items, int nitems, int nc, int nr) {
+  if (++w.kc < w.nch) return;
+  w.kc = 0;
+  w.t += gridDim.x;
+  ++w.tl;
+  if (w.t < nitems) w.nch = item_chunks<FWD>(items, w.t, nc, nr);
+}
+
+// 1 = completed, 0 = left because another role raised the abort flag, -1 = expired
+__device__ __forceinline__ int wait3(unsigned bar, unsigned parity, volatile int* abort) {
+  for (long long it = 0; it < tcx::kSpinLimit; ++it) {
+    if (tcx::mbar_try(bar, parity)) return 1;
+    if ((it & 63) == 63 && *abort) return 0;
+  }
+  return -1;
+}
+
+// Registers of one data chunk: forward, up to 4 units of (column, 4 k) FP32;
+// backward, up to 2 units of (slot, 4 k) complex128 as 4 x 32-bit words each.
+struct ConvRegsF { float4 v[4]; };
+struct ConvRegsB { uint4 v[2][4]; };
+
+template <bool FWD>
+struct Conv;
+
+template <>
+struct Conv<true> {
+  typedef ConvRegsF R;
+  // load the chunk (t, kc) of the mixed FP32 planes [2][K][M][Nr]
+  static __device__ __forceinline__ void load(R& r, const Walk& w, int nitems, const LegTile* items, int ct, int bn,
+                                              int nr, int M, int K, long long plane, bool vec,
+                                              const float* __restrict__ mixed) {
+    const int nunits = bn * 8;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) r.v[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (!w.valid(nitems)) return;
+    const LegTile tile = items[w.t];
+    const int k0 = w.kc * TC_BK;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int u = ct + TC_CONV_THREADS * j;
+      if (u >= nunits) break;
+      const int col = u >> 3, q = u & 7;
+      const int kidx = (tile.col0 >> 1) + (col >> 1);
+      const int k = k0 + 4 * q;
+      if (kidx >= K || k >= nr) continue;
+      const float* p = mixed + (col & 1) * plane + ((long long)kidx * M + tile.m) * nr + k;
+      if (vec && k + 3 < nr) {
+        r.v[j] = __ldg(reinterpret_cast<const float4*>(p));
+      } else {
+        float e[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+          if (k + i < nr) e[i] = __ldg(p + i);
+        r.v[j] = make_float4(e[0], e[1], e[2], e[3]);
+      }
+    }
+  }
+  static __device__ __forceinline__ void store(const R& r, unsigned char* pB, int ct, int bn) {
+    const int nunits = bn * 8;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int u = ct + TC_CONV_THREADS * j;
+      if (u >= nunits) break;
+      const float v[4] = {r.v[j].x, r.v[j].y, r.v[j].z, r.v[j].w};
+      store_split4(pB, bn, u >> 3, 4 * (u & 7), v);
+    }
+  }
+};
+
+template <>
+struct Conv<false> {
+  typedef ConvRegsB R;
+  // load the chunk (t, kc) of the ragged complex128 spectral field
+  static __device__ __forceinline__ void load(R& r, const Walk& w, int nitems, const LegTile* items, int ct, int bn,
+                                              int nc, const long long* __restrict__ soff, int K,
+                                              const double2* __restrict__ spec) {
+    const int nunits = (bn >> 1) * 8;
+#pragma unroll
+    for (int j = 0; j < 2; ++j)
+#pragma unroll
+      for (int i = 0; i < 4; ++i) r.v[j][i] = make_uint4(0u, 0u, 0u, 0u);
+    if (!w.valid(nitems)) return;
+    const LegTile tile = items[w.t];
+    const int Nm = nc - tile.m;
+    const int k0 = w.kc * TC_BK;
+    const long long so = soff[tile.m];
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int u = ct + TC_CONV_THREADS * j;
+      if (u >= nunits) break;
+      const int sl = u >> 3, q = u & 7;
+      const int kidx = (tile.col0 >> 1) + sl;
+      const int k = k0 + 4 * q;
+      if (kidx >= K) continue;
+      const uint4* p = reinterpret_cast<const uint4*>(spec + so + (long long)kidx * Nm + k);
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        if (k + i < Nm) r.v[j][i] = __ldg(p + i);
+    }
+  }
+  static __device__ __forceinline__ void store(const R& r, unsigned char* pB, int ct, int bn) {
+    const int nunits = (bn >> 1) * 8;
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int u = ct + TC_CONV_THREADS * j;
+      if (u >= nunits) break;
+      float re[4], im[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        re[i] = f64w_to_f32(r.v[j][i].y, r.v[j][i].x);
+        im[i] = f64w_to_f32(r.v[j][i].w, r.v[j][i].z);
+      }
+      const int sl = u >> 3, k = 4 * (u & 7);
+      store_split4(pB, bn, 2 * sl, k, re);
+      store_split4(pB, bn, 2 * sl + 1, k, im);
+    }
+  }
+};
+
 template <bool FWD>
 __global__ void __launch_bounds__(TC_THREADS, 1)
-k_leg_tc(const __grid_constant__ CUtensorMap tmapA, const LegTile* __restrict__ tiles, int nc, int nr,
-         int M, int K, int BN, int tmem_cols, int nprod, int stages, const long long* __restrict__ soff,
+k_leg_tc(const __grid_constant__ CUtensorMap tmapA, const LegTile* __restrict__ items, int nitems, int nc, int nr,
+         int M, int K, int bn, int tmem_cols, int nprod, int vec, int expire, const long long* __restrict__ soff,
          const long long* __restrict__ arow_base, const float* __restrict__ mixed_in,
-         const double2* __restrict__ spec_in, double2* __restrict__ spec_out,
-         float* __restrict__ mixed_out, int* __restrict__ err) {
+         const double2* __restrict__ spec_in, double2* __restrict__ spec_out, float* __restrict__ mixed_out,
+         int* __restrict__ err) {
   extern __shared__ unsigned char smem_raw[];
-  __shared__ uint64_t bar_tma[2], bar_mma[2];
+  __shared__ uint64_t full_a[TC_STAGES], full_b[TC_STAGES], empty[TC_STAGES], tfull[2], tempty[2], drain;
   __shared__ unsigned tmem_slot;
-  const unsigned raw = smem_u32(smem_raw);
+  __shared__ int abort_flag;
+  volatile int* abortp = &abort_flag;
+  const unsigned raw = tcx::smem_u32(smem_raw);
   const unsigned pad = (1024u - (raw & 1023u)) & 1023u;
-  const unsigned stage_bytes = 3u * TC_BM * 128u + 3u * (unsigned)BN * 128u;
-
-  const LegTile tile = tiles[blockIdx.x];
-  const int m = tile.m;
-  const int Nm = nc - m;
-  const int rows = FWD ? Nm : nr;
-  const int kdim = FWD ? nr : Nm;
-  const int ncol = 2 * K;
-  const long long plane = (long long)K * M * nr;
-  const long long so = soff[m];
+  const unsigned sbytes = tc_stage_bytes(bn);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const long long plane = (long long)K * M * nr;
 
   if (tid == 0) {
-    for (int s = 0; s < 2; ++s) {
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar_tma[s])));
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar_mma[s])));
+    for (int s = 0; s < TC_STAGES; ++s) {
+      tcx::mbar_init(tcx::smem_u32(&full_a[s]), 1);
+      tcx::mbar_init(tcx::smem_u32(&full_b[s]), TC_CONV_THREADS);
+      tcx::mbar_init(tcx::smem_u32(&empty[s]), 1);
     }
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    for (int b = 0; b < 2; ++b) {
+      tcx::mbar_init(tcx::smem_u32(&tfull[b]), 1);
+      tcx::mbar_init(tcx::smem_u32(&tempty[b]), 4);
+    }
+    tcx::mbar_init(tcx::smem_u32(&drain), 1);
+    abort_flag = 0;
+    tcx::fence_mbar_init();
   }
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
-                 "r"(tmem_cols));
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-  }
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  if (warp == 0) tcx::tmem_alloc(tcx::smem_u32(&tmem_slot), (unsigned)tmem_cols);
+  tcx::tc_fence_before();
   __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  tcx::tc_fence_after();
   const unsigned tmem = tmem_slot;
 
-  const unsigned idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(BN >> 3) << 17) |
-                         ((unsigned)(TC_BM >> 4) << 24);
-  const int nchunks = (kdim + TC_BK - 1) / TC_BK;
-  const int arow = (int)arow_base[m] + tile.row0;
-  const int kslot0 = tile.col0 >> 1;            // first wavenumber slot of this tile
-  const int nslot = BN >> 1;
-  bool bad = false;
-
-  for (int kc = 0; kc < nchunks; ++kc) {
-    const int s = kc % stages;
-    const unsigned sA = raw + pad + (unsigned)s * stage_bytes;
-    const unsigned sB = sA + 3u * TC_BM * 128u;
-    unsigned char* pB = smem_raw + pad + (size_t)s * stage_bytes + 3 * TC_BM * 128;
-    // stage reuse: the MMAs of chunk kc - stages must have finished reading it
-    if (kc >= stages) {
-      const bool ok = mbar_wait_bounded(smem_u32(&bar_mma[s]), (unsigned)(((kc / stages) - 1) & 1));
-      if (__syncthreads_or(!ok)) { bad = true; if (tid == 0) atomicOr(err, 2); break; }
-    }
-    if (tid == 0) {
-      const unsigned bt = smem_u32(&bar_tma[s]);
-      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bt), "r"(3 * TC_BM * 128)
-                   : "memory");
-      for (int sp = 0; sp < 3; ++sp)
-        asm volatile(
-            "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
-            ::"r"(sA + (unsigned)sp * TC_BM * 128u), "l"(&tmapA), "r"(kc * TC_BK), "r"(arow), "r"(sp), "r"(bt)
-            : "memory");
-    }
-    // B chunk: (slot, 4 consecutive k) per thread step
-    const int k0 = kc * TC_BK;
-    for (int e = tid; e < nslot * (TC_BK / 4); e += TC_THREADS) {
-      const int sl = e / (TC_BK / 4), kq = (e - sl * (TC_BK / 4)) * 4;
-      const int kidx = kslot0 + sl;
-      float re[4] = {0.f, 0.f, 0.f, 0.f}, im[4] = {0.f, 0.f, 0.f, 0.f};
-      if (kidx < K) {
-        if (FWD) {
-          const float* pr = mixed_in + ((long long)kidx * M + m) * nr + k0 + kq;
-          const float* pi = pr + plane;
-          if (((nr & 3) == 0) && k0 + kq + 3 < kdim) {
-            const float4 a = *reinterpret_cast<const float4*>(pr);
-            const float4 b = *reinterpret_cast<const float4*>(pi);
-            re[0] = a.x; re[1] = a.y; re[2] = a.z; re[3] = a.w;
-            im[0] = b.x; im[1] = b.y; im[2] = b.z; im[3] = b.w;
-          } else {
-#pragma unroll
-            for (int j = 0; j < 4; ++j)
-              if (k0 + kq + j < kdim) { re[j] = pr[j]; im[j] = pi[j]; }
-          }
-        } else {
-          const double2* ps = spec_in + so + (long long)kidx * Nm + k0 + kq;
-#pragma unroll
-          for (int j = 0; j < 4; ++j)
-            if (k0 + kq + j < kdim) { const double2 v = ps[j]; re[j] = (float)v.x; im[j] = (float)v.y; }
+  if (warp == TC_PROD_WARP) {
+    // ---- basis operand A by TMA
+    if (lane == 0) {
+      unsigned fills[TC_STAGES] = {0u, 0u, 0u, 0u};
+      int g = 0;
+      for (Walk w = walk_begin<FWD>(items, nitems, nc, nr); w.valid(nitems); walk_next<FWD>(w, items, nitems, nc, nr), ++g) {
+        const int s = g % TC_STAGES, u = g / TC_STAGES;
+        if (u > 0) {
+          if (expire && g == TC_STAGES) { atomicOr(err, 2); *abortp = 1; break; }
+          const int r = wait3(tcx::smem_u32(&empty[s]), (unsigned)((u - 1) & 1), abortp);
+          if (r < 0) { atomicOr(err, 2); *abortp = 1; }
+          if (r <= 0) break;
         }
+        const LegTile tile = items[w.t];
+        const unsigned sA = raw + pad + (unsigned)s * sbytes;
+        const unsigned bar = tcx::smem_u32(&full_a[s]);
+        tcx::mbar_expect_tx(bar, TC_A_BYTES);
+        const int arow = (int)arow_base[tile.m] + tile.row0;
+        for (int p = 0; p < 3; ++p) tcx::tma_load_3d(sA + (unsigned)p * TC_A_PART, &tmapA, w.kc * TC_BK, arow, p, bar);
+        ++fills[s];
       }
-      store_split4(pB, BN, 2 * sl, kq, re);
-      store_split4(pB, BN, 2 * sl + 1, kq, im);
+      // drain: every tensor copy issued must land before the CTA leaves
+      for (int s = 0; s < TC_STAGES; ++s)
+        if (fills[s] && !tcx::mbar_wait(tcx::smem_u32(&full_a[s]), (fills[s] - 1u) & 1u)) atomicOr(err, 1);
     }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
-    if (tid == 0) {
-      if (!mbar_wait_bounded(smem_u32(&bar_tma[s]), (unsigned)((kc / stages) & 1))) {
-        atomicOr(err, 1);
-        bad = true;
-      } else {
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const int pa[8] = {0, 0, 1, 0, 2, 1, 1, 2};
-        const int pb[8] = {0, 1, 0, 2, 0, 1, 2, 1};
+  } else if (warp == TC_MMA_WARP) {
+    // ---- tensor-core issue
+    if (lane == 0) {
+      const unsigned idesc = tcx::idesc_bf16(TC_BM, bn);
+      const int pa[8] = {0, 0, 1, 0, 2, 1, 1, 2};
+      const int pb[8] = {0, 1, 0, 2, 0, 1, 2, 1};
+      bool issued = false, ok = true;
+      int g = 0, tl_cur = -1;
+      for (Walk w = walk_begin<FWD>(items, nitems, nc, nr); w.valid(nitems) && ok;) {
+        const int buf = w.tl & 1;
+        if (w.tl != tl_cur) {
+          tl_cur = w.tl;
+          if (w.tl >= 2) {
+            const int r = wait3(tcx::smem_u32(&tempty[buf]), (unsigned)(((w.tl >> 1) - 1) & 1), abortp);
+            if (r < 0) { atomicOr(err, 4); *abortp = 1; }
+            if (r <= 0) { ok = false; break; }
+            tcx::tc_fence_after();
+          }
+        }
+        const int s = g % TC_STAGES, u = g / TC_STAGES;
+        int r = wait3(tcx::smem_u32(&full_a[s]), (unsigned)(u & 1), abortp);
+        if (r > 0) r = wait3(tcx::smem_u32(&full_b[s]), (unsigned)(u & 1), abortp);
+        if (r < 0) { atomicOr(err, 1); *abortp = 1; }
+        if (r <= 0) { ok = false; break; }
+        tcx::tc_fence_after();
+        const unsigned sA = raw + pad + (unsigned)s * sbytes;
+        const unsigned sB = sA + TC_A_BYTES;
+        const unsigned dt0 = tmem + (unsigned)(buf * 2 * bn);
 #pragma unroll
         for (int ks = 0; ks < TC_BK / 16; ++ks) {
           for (int q = 0; q < nprod; ++q) {
-            const uint64_t da = sw128_desc(sA + (unsigned)pa[q] * TC_BM * 128u) + (uint64_t)(2 * ks);
-            const uint64_t db = sw128_desc(sB + (unsigned)pb[q] * BN * 128u) + (uint64_t)(2 * ks);
-            const unsigned dt = tmem + (q == 0 ? 0u : (unsigned)BN);
-            const unsigned acc = (kc | ks) ? 1u : (q > 1 ? 1u : 0u);
-            mma_bf16(dt, da, db, idesc, acc);
+            const uint64_t da = tcx::desc_sw64(sA + (unsigned)pa[q] * TC_A_PART) + (uint64_t)(2 * ks);
+            const uint64_t db = tcx::desc_sw64(sB + (unsigned)pb[q] * (unsigned)bn * 64u) + (uint64_t)(2 * ks);
+            const unsigned acc = (w.kc | ks) ? 1u : (q > 1 ? 1u : 0u);
+            tcx::mma_bf16(dt0 + (q == 0 ? 0u : (unsigned)bn), da, db, idesc, acc);
           }
         }
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                         smem_u32(&bar_mma[s]))
-                     : "memory");
+        tcx::mma_commit(tcx::smem_u32(&empty[s]));
+        issued = true;
+        const bool last = w.kc + 1 == w.nch;
+        if (last) tcx::mma_commit(tcx::smem_u32(&tfull[buf]));
+        walk_next<FWD>(w, items, nitems, nc, nr);
+        ++g;
+      }
+      // drain: every MMA issued must complete before the TMEM is freed
+      if (issued) {
+        tcx::mma_commit(tcx::smem_u32(&drain));
+        if (!tcx::mbar_wait(tcx::smem_u32(&drain), 0u)) atomicOr(err, 4);
       }
     }
-    if (__syncthreads_or(bad)) { bad = true; break; }
-  }
-  // the last commit covers every MMA issued before it
-  if (!bad && nchunks > 0) {
-    const int kl = nchunks - 1;
-    const bool ok = mbar_wait_bounded(smem_u32(&bar_mma[kl % stages]), (unsigned)((kl / stages) & 1));
-    if (__syncthreads_or(!ok)) { bad = true; if (tid == 0) atomicOr(err, 4); }
-  }
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-
-  if (!bad) {
-    const int row = tile.row0 + warp * 32 + lane;
-    const unsigned tbase = tmem + ((unsigned)(warp * 32) << 16);
-    for (int c0 = 0; c0 < BN; c0 += 16) {
-      unsigned r[16], q[16];
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-          : "r"(tbase + (unsigned)c0));
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-          : "=r"(q[0]), "=r"(q[1]), "=r"(q[2]), "=r"(q[3]), "=r"(q[4]), "=r"(q[5]), "=r"(q[6]), "=r"(q[7]),
-            "=r"(q[8]), "=r"(q[9]), "=r"(q[10]), "=r"(q[11]), "=r"(q[12]), "=r"(q[13]), "=r"(q[14]), "=r"(q[15])
-          : "r"(tbase + (unsigned)(BN + c0)));
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      if (row < rows) {
+  } else if (warp >= TC_CONV_WARP0) {
+    // ---- data operand B: two chunks in flight in registers
+    typedef Conv<FWD> CV;
+    typename CV::R ra, rb;
+    const int ct = tid - 32 * TC_CONV_WARP0;
+    Walk ld = walk_begin<FWD>(items, nitems, nc, nr);
+    auto load = [&](typename CV::R& r, const Walk& w) {
+      if constexpr (FWD) CV::load(r, w, nitems, items, ct, bn, nr, M, K, plane, vec != 0, mixed_in);
+      else CV::load(r, w, nitems, items, ct, bn, nc, soff, K, spec_in);
+    };
+    load(ra, ld);
+    walk_next<FWD>(ld, items, nitems, nc, nr);
+    load(rb, ld);
+    walk_next<FWD>(ld, items, nitems, nc, nr);
+    int g = 0;
+    bool odd = false;
+    for (Walk w = walk_begin<FWD>(items, nitems, nc, nr); w.valid(nitems); walk_next<FWD>(w, items, nitems, nc, nr), ++g) {
+      const int s = g % TC_STAGES, u = g / TC_STAGES;
+      if (u > 0) {
+        const int r = wait3(tcx::smem_u32(&empty[s]), (unsigned)((u - 1) & 1), abortp);
+        if (r < 0) { atomicOr(err, 2); *abortp = 1; }
+        if (r <= 0) break;
+      }
+      unsigned char* pB = smem_raw + pad + (size_t)s * sbytes + TC_A_BYTES;
+      if (!odd) { CV::store(ra, pB, ct, bn); load(ra, ld); }
+      else      { CV::store(rb, pB, ct, bn); load(rb, ld); }
+      walk_next<FWD>(ld, items, nitems, nc, nr);
+      odd = !odd;
+      tcx::fence_proxy_async();
+      tcx::mbar_arrive(tcx::smem_u32(&full_b[s]));
+    }
+  } else {
+    // ---- epilogue (warps 0-3): TMEM lanes 32 warp .. 32 warp + 31
+    for (Walk w = walk_begin<FWD>(items, nitems, nc, nr); w.valid(nitems);) {
+      const int buf = w.tl & 1;
+      int r = 0;
+      if (lane == 0) {
+        r = wait3(tcx::smem_u32(&tfull[buf]), (unsigned)((w.tl >> 1) & 1), abortp);
+        if (r < 0) { atomicOr(err, 4); *abortp = 1; }
+      }
+      r = __shfl_sync(0xffffffffu, r, 0);
+      if (r <= 0) break;
+      tcx::tc_fence_after();
+      const LegTile tile = items[w.t];
+      const int m = tile.m, Nm = nc - m;
+      const int rows = FWD ? Nm : nr;
+      const int row = tile.row0 + warp * 32 + lane;
+      const int kslot0 = tile.col0 >> 1;
+      const long long so = soff[m];
+      const unsigned tb = tmem + ((unsigned)(warp * 32) << 16) + (unsigned)(buf * 2 * bn);
+      for (int c0 = 0; c0 < bn; c0 += 16) {
+        unsigned hi[16], co[16];
+        tcx::tmem_ld16(tb + (unsigned)c0, hi);
+        tcx::tmem_ld16(tb + (unsigned)(bn + c0), co);
+        tcx::tmem_wait_ld();
+        if (row < rows) {
 #pragma unroll
-        for (int j = 0; j < 16; j += 2) {
-          const int kidx = kslot0 + ((c0 + j) >> 1);
-          if (kidx >= K) break;
-          const float vr = __uint_as_float(r[j]) + __uint_as_float(q[j]);
-          const float vi = __uint_as_float(r[j + 1]) + __uint_as_float(q[j + 1]);
-          if (FWD) {
-            spec_out[so + (long long)kidx * Nm + row] = make_double2((double)vr, (double)vi);
-          } else {
-            const long long o = ((long long)kidx * M + m) * nr + row;
-            mixed_out[o] = vr;
-            mixed_out[plane + o] = vi;
+          for (int j = 0; j < 16; j += 2) {
+            const int kidx = kslot0 + ((c0 + j) >> 1);
+            if (kidx >= K) break;
+            const float vr = __uint_as_float(hi[j]) + __uint_as_float(co[j]);
+            const float vi = __uint_as_float(hi[j + 1]) + __uint_as_float(co[j + 1]);
+            if (FWD) {
+              spec_out[so + (long long)kidx * Nm + row] = make_double2(f32_to_f64(vr), f32_to_f64(vi));
+            } else {
+              const long long o = ((long long)kidx * M + m) * nr + row;
+              mixed_out[o] = vr;
+              mixed_out[plane + o] = vi;
+            }
           }
         }
       }
+      tcx::tc_fence_before();
+      __syncwarp();
+      if (lane == 0) tcx::mbar_arrive(tcx::smem_u32(&tempty[buf]));
+      // next tile of this CTA
+      do { walk_next<FWD>(w, items, nitems, nc, nr); } while (w.valid(nitems) && w.kc != 0);
     }
   }
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  tcx::tc_fence_before();
   __syncthreads();
-  if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols));
+  if (warp == 0) {
+    tcx::tc_fence_after();
+    tcx::tmem_dealloc(tmem, (unsigned)tmem_cols);
+  }
 }
 
 // BF16 split tables from the FP64 basis.
@@ -335,17 +494,25 @@ int encode_map(mlx_ctx* c, CUtensorMap* map, void* base, long long kpad, long lo
   }
   cuuint64_t dims[3] = {(cuuint64_t)kpad, (cuuint64_t)rows, 3};
   cuuint64_t strides[2] = {(cuuint64_t)kpad * 2, (cuuint64_t)(kpad * rows * 2)};
-  cuuint32_t box[3] = {TC_BK, TC_BM, 1};
+  cuuint32_t box[3] = {TC_BK, TC_BM, 1};   // 32 BF16 = one 64-byte swizzled row
   cuuint32_t estr[3] = {1, 1, 1};
   CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides, box, estr,
-                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) { c->last_err = "cuTensorMapEncodeTiled failed"; return MLX_ECUDA; }
   return MLX_OK;
 }
 
-size_t tc_smem(int BN, int stages) {
-  return (size_t)stages * (3 * TC_BM * 128 + (size_t)3 * BN * 128) + 1024;
+size_t tc_smem(int bn) { return (size_t)TC_STAGES * tc_stage_bytes(bn) + 1024; }
+
+int sm_count() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 148;
+  }
+  return n;
 }
 
 }  // namespace
@@ -374,14 +541,15 @@ int mlx_tc_prepare(mlx_ctx* c, cudaStream_t st) {
   MLX_CUDA_TRY(c, cudaMalloc(&c->d_arowP, sizeof(long long) * c->M));
   MLX_CUDA_TRY(c, cudaMemcpyAsync(c->d_arowW, aw.data(), sizeof(long long) * c->M, cudaMemcpyHostToDevice, st));
   MLX_CUDA_TRY(c, cudaMemcpyAsync(c->d_arowP, ap.data(), sizeof(long long) * c->M, cudaMemcpyHostToDevice, st));
-  // columns per tile (interleaved Re/Im pairs, multiple of 16): narrow tiles when
-  // the grid would otherwise leave SMs idle
+  // columns per tile (interleaved Re/Im pairs, multiple of 16, at most 128): the
+  // widest tile whose item list still gives every SM work, else 32
   const int ncol = 2 * c->K;
-  int bn = 256;
+  int bn = 32;
   {
     int rt = 0;
     for (int m = 0; m < c->M; ++m) rt += (c->nc - m + TC_BM - 1) / TC_BM;
-    while (bn > 32 && (long long)rt * ((ncol + bn - 1) / bn) < 148) bn -= 16;
+    for (int cand = TC_MAX_BN; cand >= 32; cand -= 16)
+      if ((long long)rt * ((ncol + cand - 1) / cand) >= sm_count()) { bn = cand; break; }
   }
   return mlx_tc_retile(c, bn, st);
 }
@@ -390,12 +558,15 @@ int mlx_tc_prepare(mlx_ctx* c, cudaStream_t st) {
 int mlx_tc_retile(mlx_ctx* c, int bn_req, cudaStream_t st) {
   const int ncol = 2 * c->K;
   if (bn_req < 16 || bn_req > 256) return MLX_EINVAL;
+  if (bn_req > TC_MAX_BN) bn_req = TC_MAX_BN;
   const int nct = (ncol + bn_req - 1) / bn_req;
   c->tc_bn = ((ncol + nct - 1) / nct + 15) / 16 * 16;
-  if (c->tc_bn > 256) c->tc_bn = 256;
+  if (c->tc_bn > TC_MAX_BN) c->tc_bn = TC_MAX_BN;
   cudaFree(c->d_tc_fwd);
   cudaFree(c->d_tc_bwd);
   c->d_tc_fwd = c->d_tc_bwd = nullptr;
+  // items ordered (m, row tile, column tile): consecutive CTAs share the basis
+  // chunks of one (m, row tile) through L2
   std::vector<LegTile> tf, tb;
   for (int m = 0; m < c->M; ++m) {
     for (int r0 = 0; r0 < c->nc - m; r0 += TC_BM)
@@ -410,12 +581,11 @@ int mlx_tc_retile(mlx_ctx* c, int bn_req, cudaStream_t st) {
   MLX_CUDA_TRY(c, cudaMemcpyAsync(c->d_tc_fwd, tf.data(), sizeof(LegTile) * tf.size(), cudaMemcpyHostToDevice, st));
   MLX_CUDA_TRY(c, cudaMemcpyAsync(c->d_tc_bwd, tb.data(), sizeof(LegTile) * tb.size(), cudaMemcpyHostToDevice, st));
   int cols = 32;
-  while (cols < 2 * c->tc_bn) cols <<= 1;   // two accumulators of BN columns
+  while (cols < 4 * c->tc_bn) cols <<= 1;   // two tiles in flight x two accumulators of BN columns
   c->tc_tmem_cols = cols;
-  c->tc_stages = tc_smem(c->tc_bn, 2) <= 220 * 1024 ? 2 : 1;
-  // the attribute is a per-function ceiling shared by every context: set it to
-  // the largest size any tile width uses
-  const int smem = 220 * 1024 + 1024;
+  // the attribute is a per-function ceiling shared by every context: the largest
+  // size any tile width uses
+  const int smem = (int)tc_smem(TC_MAX_BN);
   MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_leg_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_leg_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   return MLX_OK;
@@ -423,20 +593,21 @@ int mlx_tc_retile(mlx_ctx* c, int bn_req, cudaStream_t st) {
 
 int mlx_legendre_tc_forward(mlx_ctx* c, double2* spec, cudaStream_t st) {
   TimedLaunch tl(c, KID_LEG_FWD, st);
-  k_leg_tc<true><<<c->ntc_fwd, TC_THREADS, tc_smem(c->tc_bn, c->tc_stages), st>>>(
-      c->tmapW, c->d_tc_fwd, c->nc, c->nr, c->M, c->K, c->tc_bn, c->tc_tmem_cols, c->tc_products, c->tc_stages,
-      c->d_soff, c->d_arowW,
-      (const float*)c->d_mixed, nullptr, spec, nullptr, c->d_err);
+  const int grid = c->ntc_fwd < sm_count() ? c->ntc_fwd : sm_count();
+  k_leg_tc<true><<<grid, TC_THREADS, tc_smem(c->tc_bn), st>>>(
+      c->tmapW, c->d_tc_fwd, c->ntc_fwd, c->nc, c->nr, c->M, c->K, c->tc_bn, c->tc_tmem_cols, c->tc_products,
+      (c->nr & 3) == 0 ? 1 : 0, c->tc_expire, c->d_soff, c->d_arowW, (const float*)c->d_mixed, nullptr, spec,
+      nullptr, c->d_err);
   MLX_LAUNCH_CHECK(c);
   return MLX_OK;
 }
 
 int mlx_legendre_tc_backward(mlx_ctx* c, const double2* spec, cudaStream_t st) {
   TimedLaunch tl(c, KID_LEG_BWD, st);
-  k_leg_tc<false><<<c->ntc_bwd, TC_THREADS, tc_smem(c->tc_bn, c->tc_stages), st>>>(
-      c->tmapP, c->d_tc_bwd, c->nc, c->nr, c->M, c->K, c->tc_bn, c->tc_tmem_cols, c->tc_products, c->tc_stages,
-      c->d_soff, c->d_arowP,
-      nullptr, spec, nullptr, (float*)c->d_mixed, c->d_err);
+  const int grid = c->ntc_bwd < sm_count() ? c->ntc_bwd : sm_count();
+  k_leg_tc<false><<<grid, TC_THREADS, tc_smem(c->tc_bn), st>>>(
+      c->tmapP, c->d_tc_bwd, c->ntc_bwd, c->nc, c->nr, c->M, c->K, c->tc_bn, c->tc_tmem_cols, c->tc_products,
+      0, c->tc_expire, c->d_soff, c->d_arowP, nullptr, spec, nullptr, (float*)c->d_mixed, c->d_err);
   MLX_LAUNCH_CHECK(c);
   return MLX_OK;
 }

@@ -67,6 +67,7 @@ struct BandLU {
   double* PHb = nullptr;
   double* PSf = nullptr;
   int seg = 0;             // segments the influence data were built for (0 = none)
+  bool nopiv = false;      // no system of the family interchanged rows (segmented solve skips pivoting)
 };
 
 struct mlx_ctx {
@@ -112,7 +113,7 @@ struct mlx_ctx {
   LegTile* d_tc_bwd = nullptr;
   int ntc_fwd = 0, ntc_bwd = 0, tc_bn = 0, tc_tmem_cols = 0;
   int tc_products = 6;                 // BF16 split products per term: 6 or 8
-  int tc_stages = 2;                   // shared-memory stages of the K loop
+  int tc_expire = 0;                   // test hook: the contraction's first stage-reuse wait reports expiry
   int* d_err = nullptr;                // device status word: bits 1, 2, 4 bounded waits that
                                        // expired; bit 16 a non-finite nonlinear product
 
@@ -160,6 +161,7 @@ struct mlx_ctx {
   int phi_tile = 0;                    // radii per CTA of the phi kernels (2..32; 0 = automatic)
   int z_tile = 0;                      // radii per CTA of the z kernels (1..32; 0 = automatic)
   int solve_seg = 8;                   // segments of the half-width-2 segmented solve (8, 4; 0 = off)
+  int solve_nopiv = 1;                 // 1: the segmented solve skips pivoting for families without interchanges
 
   // graphs cached per (state, prev_A, kind, gamma)
   struct GraphKey {

@@ -184,3 +184,33 @@ def test_bf16x3_device_status_clean():
     flat = rand_spec(g, 4)
     ctx.forward(ctx.backward(to_gpu_spec(flat), ctx.new_phys()), ctx.new_spec())
     ctx.device_status()
+
+
+@pytest.mark.parametrize("direction", ["forward", "backward"])
+def test_tc_forced_wait_expiry_reports_timeout(direction):
+    # The tensor-core contraction's bounded waits: with the test hook "tc_expire"
+    # the first shared-memory stage-reuse wait reports expiry at once; the kernel
+    # must drain what it issued, free its tensor memory and return, the context
+    # must report MLX_ETIMEOUT once, and the next normal call must be clean and
+    # correct.  Nr = 256 gives 6-8 K chunks per work item (more than the 4 stages).
+    g, ctx = pair(256, 64, 16, 1.0, lz=8.6, policy="twothirds", precision=B.BF16X3)
+    u = rand_phys(g, 7).astype(np.float32).astype(np.float64)
+    flat = rand_spec(g, 6)
+
+    def run():
+        if direction == "forward":
+            return ctx.forward(to_gpu_phys(ctx, u), ctx.new_spec())
+        return ctx.backward(to_gpu_spec(flat), ctx.new_phys())
+    ctx.device_status()
+    ctx.set_tuning("tc_expire", 1)
+    run()
+    with pytest.raises(B.MlxError) as e:
+        ctx.device_status()
+    assert e.value.code == -4
+    ctx.set_tuning("tc_expire", 0)
+    out = run()
+    ctx.device_status()
+    if direction == "forward":
+        assert O.spec_rel_err(g, spec_from_gpu(g, out), O.forward(g, u)) <= 1e-6
+    else:
+        assert rel(out.double().cpu().numpy(), O.backward(g, O.from_flat(g, flat))) <= 1e-6
