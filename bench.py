@@ -371,6 +371,70 @@ def measure_vortex_long(B, W, torch, dev, stream, steps=2000, prec=None):
             "wall_s": wall, "history": hist}
 
 
+def measure_crow(B, W, torch, dev, stream, t_end=60.0, dt=5e-3, nr=176, nphi=128, nz=64, ell=2.0, nu_h=5e-8,
+                 prec=None, every=0.5):
+    """Crow instability of the counter-rotating pair (Sec. 5.3): b = 4, Lamb-Oseen
+    cores a = 0.5 (a / b = 0.125), Gamma = 2 pi, Lz = 8.6 b (one Crow wavelength),
+    nu = 1e-4, p = 8 hyperviscosity nu_h = 5e-8, cores displaced by 0.002 b along z
+    (the k = 1 fundamental) mirror-symmetrically in planes inclined 48 degrees, in
+    the frame moving with the pair (U0 = -Gamma / (2 pi b)).  Records the axial modal
+    energies every `every` time units to t_end and fits the rate
+    alpha = (pi b^2 / Gamma) d ln E_1 / dt over t = 10-18 and 33-60, beside Crow's
+    dispersion relation at the run's beta = 2 pi b / Lz."""
+    import math as _m
+    from paper_2609_18026_b300 import analysis as AN
+    prec = B.BF16X3 if prec is None else prec
+    b, a, gam = 4.0, 0.5, 2.0 * _m.pi
+    lz = 8.6 * b
+    U0 = -gam / (2.0 * _m.pi * b)
+    ctx = B.Context(nr, nphi, nz, ell, lz=lz, precision=prec, chop_policy=B.CHOP_TWOTHIRDS)
+    ctx.vortex_setup()
+    ctx.implicit_setup(1e-4, dt, nu_h=nu_h, p=8)
+    x, w, r = ctx.nodes()
+    phi = 2 * _m.pi * np.arange(nphi) / nphi
+    zz = lz * np.arange(nz) / nz
+    wz = W.vortex_pair_omega(r[None, None, :], phi[None, :, None], zz[:, None, None], lz=lz, b=b, a=a,
+                             gamma=gam, amp=0.002 * b, incl_deg=48.0, kseed=1)
+    ws = ctx.forward(torch.as_tensor(wz, dtype=ctx.phys_dtype, device=dev), ctx.new_spec())
+    psi = ctx.lap_h_solve(-ws, ctx.new_spec())
+    state = torch.zeros(2 * ctx.n_spec, dtype=torch.complex128, device=dev)
+    state[:ctx.n_spec] = psi
+    prev = torch.zeros_like(state)
+    chunk = max(1, int(round(every / dt)))
+    nsteps = int(round(t_end / dt))
+    ts, E1, E2, E0 = [0.0], [], [], []
+    e = ctx.axial_energy(state)
+    E0.append(e[0]); E1.append(e[1]); E2.append(e[2] if len(e) > 2 else 0.0)
+    done = 0
+    t0 = time.perf_counter()
+    status = "ok"
+    while done < nsteps:
+        k = min(chunk, nsteps - done)
+        ctx.advance(B.NONLIN_VORTEX, [U0], state, prev, k, done == 0)
+        done += k
+        e = ctx.axial_energy(state)
+        ts.append(done * dt); E0.append(e[0]); E1.append(e[1]); E2.append(e[2] if len(e) > 2 else 0.0)
+        if not all(_m.isfinite(v) for v in e):
+            status = "non-finite at t = %.3f" % (done * dt)
+            break
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    try:
+        ctx.device_status()
+    except B.MlxError as exc:
+        status = str(exc)
+    beta = 2.0 * _m.pi * b / lz
+    out = {"workload": "crow_pair_%dx%dx%d" % (nr, nphi, nz), "precision": {B.BF16X3: "bf16x3", B.FP64: "fp64"}.get(prec),
+           "ell": ell, "dt": dt, "nu_h": nu_h, "steps": done, "t_end": done * dt, "wall_s": wall, "status": status,
+           "alpha_10_18": AN.growth_rate(ts, E1, b, gam, (10.0, 18.0)),
+           "alpha_33_60": AN.growth_rate(ts, E1, b, gam, (33.0, 60.0)),
+           "alpha_theory": AN.crow_alpha(beta, a / b), "beta": beta,
+           "paper": {"alpha_plateau_33_60": 0.8197, "alpha_theory": 0.798},
+           "history": {"t": ts[::4], "E0": E0[::4], "E1": E1[::4], "E2": E2[::4]}}
+    ctx.close()
+    return out
+
+
 def measure_batch(B, W, torch, dev, stream, steps=100, n=64, tune_cache=None):
     """64 uneven independent 2-D/3-D diffusion and Fisher-KPP instances (seed
     20261202: Nr in {32..256}, Nphi in {16..256}, Nz in {1, 16, 64}, ell in
@@ -817,7 +881,7 @@ def main():
     ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "fp32", "fp64"],
                     help="transform arithmetic of the timed form (the FP64 form is always timed beside it)")
     ap.add_argument("--profile-workload", default=None,
-                    choices=["vortex", "vortex_long", "batch", "surrogate", "surrogate_step"],
+                    choices=["vortex", "vortex_long", "crow", "batch", "surrogate", "surrogate_step"],
                     help="run only that secondary workload and print its measurement (for profiler captures; "
                          "not the benchmark line)")
     args = ap.parse_args()
@@ -832,6 +896,8 @@ def main():
         stream = torch.cuda.current_stream()
         fn = {"vortex": lambda: measure_vortex(B, W, torch, dev, stream, with_errors=False),
               "vortex_long": lambda: measure_vortex_long(B, W, torch, dev, stream),
+              "crow": lambda: measure_crow(B, W, torch, dev, stream, dt=float(os.environ.get("MLX_CROW_DT", "5e-3")),
+                                           ell=float(os.environ.get("MLX_CROW_ELL", "2.0"))),
               "batch": lambda: measure_batch(B, W, torch, dev, stream, tune_cache=args.tune_cache),
               "surrogate": lambda: measure_surrogate(torch),
               "surrogate_step": lambda: measure_surrogate_step()}[args.profile_workload]

@@ -181,6 +181,17 @@ int mlx_nonlinear(mlx_ctx* ctx, int kind, const double* coeffs, int ncoeffs,
  * Synchronises `stream`. */
 int mlx_vortex_setup(mlx_ctx* ctx, mlx_stream stream);
 
+/* Axial kinetic-energy spectrum of a two-field vortex state (psi, chi) (Eq. (8); the
+ * modal energy E_k of Sec. 5.3 from which the Crow growth rate is measured):
+ * E[|k|] = (1/2) int over one axial period of |v_{+k}|^2 + |v_{-k}|^2 dV (for k = 0 the
+ * k = 0 part alone), |k| < Kz, so that sum_k E[k] is the kinetic energy per period.
+ * The velocity comes from the banded r d/dr and D_m as in the vortex term; each
+ * harmonic is evaluated on the Gauss nodes with the FP64 basis table (whatever the
+ * context's transform precision) under the area element r dr = ell^2 dx / (1 - x)^2.
+ * state: device, 2 n_spec complex128; E: host, Kz doubles.  Needs mlx_vortex_setup
+ * (MLX_ESTATE); overwrites the vortex term's temporaries; synchronises `stream`. */
+int mlx_axial_energy(mlx_ctx* ctx, const void* state, double* E, mlx_stream stream);
+
 /* Solve grad_h^2 x = rhs harmonic by harmonic (Eq. (9)'s inverse Laplacian):
  * D_m x = rhs with the far-field decay condition in place of the singular first
  * equation at m = 0 (rhs's m = 0, n = 0 entries are not used).  FP64, device
@@ -216,6 +227,33 @@ int mlx_implicit_solve(mlx_ctx* ctx, int step, const void* s, const void* A,
  * replayed; the graph is launched on `stream`. */
 int mlx_advance(mlx_ctx* ctx, int kind, const double* coeffs, int ncoeffs,
                 void* state, void* prev_A, int nsteps, int start, mlx_stream stream);
+
+/* Adaptive modal filter applied between time steps (Sec. 3.3).  Every
+ * coefficient whose normalised mode index zeta = max(n/(Nc-1), m/(M-1), |k|/(Kz-1))
+ * (a term is 0 when its chop keeps a single index) lies above zeta_c is multiplied by
+ * exp(-eps ((zeta - zeta_c)/(1 - zeta_c))^8).  Each field's amplitude eps follows the
+ * fraction f of its spectral energy (|shat|^2, multiplicity 2 for m >= 1) above the
+ * cutoff, measured before the filter acts: target eps* = eps_max min(1, max(0,
+ * (f - tau)/tau)) (inactive below tau, saturated at 2 tau), relaxed as
+ * eps <- eps + relax (eps* - eps) and kept in [0, eps_max].  The paper fixes the form,
+ * the tail-fraction rule and tau = 2e-2; the other defaults are this library's
+ * readings: zeta_c = 2/3, eps_max = 36, relax = 1/4.
+ * mlx_filter_setup: enable != 0 turns the filter on in mlx_advance (after the
+ * Richardson start and after every AB-CN step; every field of the state has its own
+ * eps) and resets eps to 0, params NULL = the defaults (MLX_EINVAL unless
+ * 0 <= zeta_c < 1, tau > 0, eps_max >= 0, 0 < relax <= 1); enable = 0 turns it off.
+ * The first enable allocates a small state (partial sums and multiplier tables).
+ * Invalidates cached graphs.
+ * mlx_filter_apply: one filter step on a device state of nfields (1 or 2)
+ * complex128 ragged fields, in place, updating the amplitudes (MLX_ESTATE before
+ * the first enable).  mlx_filter_state: host copies of eps and of the last tail
+ * fraction f per field (2 values each, may be NULL); synchronous. */
+typedef struct {
+  double zeta_c, tau, eps_max, relax;
+} mlx_filter_params;
+int mlx_filter_setup(mlx_ctx* ctx, int enable, const mlx_filter_params* params);
+int mlx_filter_apply(mlx_ctx* ctx, void* state, int nfields, mlx_stream stream);
+int mlx_filter_state(mlx_ctx* ctx, double* eps, double* tail);
 
 /* Integral diagnostics of one spectral scalar field (Eq. (16) and the weighted
  * norm of the examples, Sec. 5.1), evaluated in FP64 from the coefficients with the

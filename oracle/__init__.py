@@ -18,6 +18,7 @@ for unbounded domains", Lee & Wang):
 * vortex.py      -- toroidal-poloidal velocity/vorticity Eq. (8), projection Eq. (9),
                     nonlinear term of Eq. (19)
 * diagnostics.py -- weighted L2 norm, circulation and second moment Eq. (16)
+* filter.py      -- adaptive modal filter applied between steps (Sec. 3.3)
 * surrogate.py   -- FP64 reference of the learned surrogate's network, its
                     backward pass and Adam (not in the paper; gradient reference)
 
@@ -39,3 +40,4 @@ from .integrate import Stepper, fkpp_nonlinear  # noqa: F401
 from .diagnostics import weighted_l2, l2w, circulation, second_moment  # noqa: F401
 from .vortex import VortexOps, vortex_nonlinear  # noqa: F401
 from . import surrogate  # noqa: F401
+from . import filter as modal_filter  # noqa: F401

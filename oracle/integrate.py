@@ -36,9 +36,12 @@ def fkpp_nonlinear(g, gamma):
 
 
 class Stepper:
-    def __init__(self, g, nu, dt, nu_h=0.0, p=8, nonlinear=None):
+    def __init__(self, g, nu, dt, nu_h=0.0, p=8, nonlinear=None, post=None):
+        """post: optional map applied to the state after every completed step (the
+        modal filter of Sec. 3.3 is applied between steps)."""
         self.g, self.dt = g, float(dt)
         self.nonlinear = nonlinear
+        self.post = post
         self.L = {}
         self.lu_half = {}
         self.lu_full = {}
@@ -113,6 +116,8 @@ class Stepper:
         z = self.febe(y, True)
         v = self.febe(s0, False, A0)
         s1 = [2.0 * z[m] - v[m] for m in range(len(s0))]
+        if self.post is not None:
+            s1 = self.post(s1)
         return s1, A0
 
     def run_abcn(self, s0, nsteps, callback=None):
@@ -125,6 +130,8 @@ class Stepper:
         for j in range(1, nsteps):
             A = self.A(s)
             s = self.abcn(s, A, A_prev)
+            if self.post is not None:
+                s = self.post(s)
             A_prev = A
             if callback:
                 callback(j + 1, s)
@@ -135,6 +142,8 @@ class Stepper:
         for _ in range(nsteps):
             A = self.A(s)
             s = self.abcn(s, A, A_prev)
+            if self.post is not None:
+                s = self.post(s)
             A_prev = A
         return s, A_prev
 

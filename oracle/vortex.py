@@ -66,7 +66,9 @@ project to zero, a solenoidal field built from known (psi, chi) projects back to
 them, an axisymmetric shielded vortex has a pure-gradient N so P(N) = 0, and in a
 uniform background U0 e_y its projected forcing is the translation
 psi_N = -U0 d(psi)/dy in closed form; analytic curl fields; the decay-row Laplacian
-inverse; plain and banded forms agree to a bound that falls spectrally with Nr.
+inverse; plain and banded forms agree to a bound that falls spectrally with Nr;
+the axial energy spectrum (axial_energy) of a shielded axisymmetric vortex against
+its closed form.
 The full nonlinear evolution is checked against the oracle only: parity unpinned
 beyond these properties.
 """
@@ -324,3 +326,25 @@ def vortex_nonlinear(g, U0=0.0, form="plain"):
         pN, cN = ops.nonlinear(psi, chi, U0, form)
         return pN + cN
     return A, ops
+
+
+def axial_energy(g, ops, psi, chi):
+    """Kinetic energy per axial wavenumber |k| of the velocity of (psi, chi), Eq. (8):
+    E_|k| = (1/2) int |v_{+k}|^2 + |v_{-k}|^2 dV over one axial period, with v_k the
+    k-th axial Fourier component of v (E_0: the k = 0 part alone), so that
+    sum_|k| E_|k| = (1/2) int |v|^2 dV.  v = (r v_r / r, r v_phi / r, v_z) at the nodes
+    (six backward transforms of the fields), the axial DFT along z, the mapped
+    area quadrature r dr = ell^2 dx / (1 - x)^2 and the uniform phi rule."""
+    rvr, rvp, vz = (backward(g, f) for f in ops.fields(psi, chi)[:3])
+    r = g.r[None, None, :]
+    v = [rvr / r, rvp / r, vz]
+    a = g.w / (1.0 - g.x) ** 2
+    E = np.zeros(g.nz // 2 + 1)
+    for comp in v:
+        vh = np.fft.fft(comp, axis=0) / g.nz                     # [k][phi][r]
+        dens = np.sum(np.abs(vh) ** 2 * a[None, None, :], axis=(1, 2))   # sum over phi and the radial rule
+        for k in range(g.nz):
+            kk = k if k <= g.nz // 2 else g.nz - k
+            E[kk] += dens[k]
+    # (1/2) Lz * ell^2 * (2 pi / Nphi) * sum
+    return 0.5 * g.lz * g.ell ** 2 * (2.0 * math.pi / g.nphi) * E[:g.Kz]

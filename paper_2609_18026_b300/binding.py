@@ -25,6 +25,7 @@ EXPORTS = ("mlx_strerror", "mlx_last_cuda_error", "mlx_create", "mlx_destroy", "
            "mlx_timing", "mlx_timing_read", "mlx_kernel_count", "mlx_kernel_name",
            "mlx_set_tuning", "mlx_device_status", "mlx_forward_noalloc",
            "mlx_diag", "mlx_state_bytes", "mlx_get_state", "mlx_set_state",
+           "mlx_filter_setup", "mlx_filter_apply", "mlx_filter_state", "mlx_axial_energy",
            "mlx_vortex_setup", "mlx_lap_h_solve",
            "mlx_batch_create", "mlx_batch_destroy", "mlx_batch_advance", "mlx_autotune",
            "mlx_sur_create", "mlx_sur_destroy", "mlx_sur_param_count", "mlx_sur_get_params",
@@ -51,6 +52,11 @@ class Info(ctypes.Structure):
                 ("nc", ctypes.c_int), ("M", ctypes.c_int), ("Kz", ctypes.c_int), ("K", ctypes.c_int),
                 ("n_phys", ctypes.c_longlong), ("n_spec", ctypes.c_longlong),
                 ("precision", ctypes.c_int), ("ell", ctypes.c_double), ("lz", ctypes.c_double)]
+
+
+class FilterParams(ctypes.Structure):
+    _fields_ = [("zeta_c", ctypes.c_double), ("tau", ctypes.c_double),
+                ("eps_max", ctypes.c_double), ("relax", ctypes.c_double)]
 
 
 class DiagOut(ctypes.Structure):
@@ -92,6 +98,10 @@ def load():
     lib.mlx_device_status.argtypes = [vp]
     lib.mlx_forward_noalloc.argtypes = [vp, vp, vp, vp]
     lib.mlx_diag.argtypes = [vp, vp, ctypes.POINTER(DiagOut), vp]
+    lib.mlx_filter_setup.argtypes = [vp, i, ctypes.POINTER(FilterParams)]
+    lib.mlx_filter_apply.argtypes = [vp, vp, i, vp]
+    lib.mlx_filter_state.argtypes = [vp, vp, vp]
+    lib.mlx_axial_energy.argtypes = [vp, vp, vp, vp]
     lib.mlx_state_bytes.argtypes = [vp, i]
     lib.mlx_state_bytes.restype = ctypes.c_longlong
     lib.mlx_get_state.argtypes = [vp, i, vp, vp, ctypes.c_longlong, vp, ctypes.c_longlong, vp]
@@ -250,6 +260,31 @@ class Context:
         o = DiagOut()
         self._check(self.lib.mlx_diag(self._h, _ptr(spec), ctypes.byref(o), _stream(stream)))
         return dict(integral=o.integral, moment2=o.moment2, l2w=o.l2w, spec_l2=o.spec_l2)
+
+    def filter_setup(self, enable=True, zeta_c=None, tau=None, eps_max=None, relax=None):
+        """Adaptive modal filter between steps (mlx_filter_setup); None = the default."""
+        p = None
+        if any(v is not None for v in (zeta_c, tau, eps_max, relax)):
+            p = FilterParams(2.0 / 3.0 if zeta_c is None else zeta_c, 2e-2 if tau is None else tau,
+                             36.0 if eps_max is None else eps_max, 0.25 if relax is None else relax)
+        self._check(self.lib.mlx_filter_setup(self._h, int(bool(enable)), ctypes.byref(p) if p else None))
+
+    def filter_apply(self, state, nfields=1, stream=None):
+        self._check(self.lib.mlx_filter_apply(self._h, _ptr(state), int(nfields), _stream(stream)))
+        return state
+
+    def filter_state(self):
+        """(eps[2], tail[2]) of the filter."""
+        e = (ctypes.c_double * 2)()
+        t = (ctypes.c_double * 2)()
+        self._check(self.lib.mlx_filter_state(self._h, e, t))
+        return list(e), list(t)
+
+    def axial_energy(self, state, stream=None):
+        """Kinetic energy per axial wavenumber |k| < Kz of a two-field vortex state."""
+        E = (ctypes.c_double * self.Kz)()
+        self._check(self.lib.mlx_axial_energy(self._h, _ptr(state), E, _stream(stream)))
+        return list(E)
 
     def state_bytes(self, kind):
         return int(self.lib.mlx_state_bytes(self._h, kind))

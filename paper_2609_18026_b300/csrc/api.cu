@@ -31,7 +31,8 @@ void free_ctx(mlx_ctx* c) {
                   c->lu_half.FS, c->lu_half.BS, c->lu_full.FS, c->lu_full.BS, c->lu_lap.FS, c->lu_lap.BS,
                   c->lu_helm.FS, c->lu_helm.BS, c->lu_Q.FS, c->lu_Q.BS, c->lu_H.FS, c->lu_H.BS,
                   c->lu_G.FS, c->lu_G.BS, c->lu_half.PHf, c->lu_half.PHb, c->lu_half.PSf,
-                  c->lu_full.PHf, c->lu_full.PHb, c->lu_full.PSf, c->d_diag};
+                  c->lu_full.PHf, c->lu_full.PHb, c->lu_full.PSf, c->d_diag,
+                  c->d_bsf, c->d_bsb, c->d_filt};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
@@ -86,7 +87,9 @@ int abcn_step(mlx_ctx* c, int kind, double c0, const double2* s, double2* Anew,
               const double2* Aprev, double2* out, cudaStream_t st) {
   int rc = nonlinear_into(c, kind, c0, s, Anew, st);
   if (rc) return rc;
-  return solve_fields(c, kind, MLX_STEP_ABCN, s, Anew, Aprev, out, st);
+  rc = solve_fields(c, kind, MLX_STEP_ABCN, s, Anew, Aprev, out, st);
+  if (rc || !c->filter_on) return rc;
+  return mlx_filter_fields(c, nfields(kind), out, st);   // the modal filter acts between steps
 }
 
 }  // namespace
@@ -325,6 +328,7 @@ int mlx_advance(mlx_ctx* c, int kind, const double* coeffs, int ncoeffs, void* s
     if ((rc = solve_fields(c, kind, MLX_STEP_FEBE_HALF, c->d_spec1, c->d_specA, nullptr, c->d_spec2, st))) return rc;
     if ((rc = solve_fields(c, kind, MLX_STEP_FEBE_FULL, s, Ap, nullptr, c->d_spec3, st))) return rc;
     if ((rc = mlx_spec_axpby(c, 2.0, c->d_spec2, -1.0, c->d_spec3, s, st, nst))) return rc;
+    if (c->filter_on && (rc = mlx_filter_fields(c, nfields(kind), s, st))) return rc;
     --nsteps;
   }
   const int pairs = nsteps / 2;
@@ -490,7 +494,7 @@ int mlx_set_tuning(mlx_ctx* c, const char* key, int value) {
 
 static const char* kKernelNames[KID_COUNT] = {
     "phi_analysis", "phi_synthesis", "phi_fkpp_fused", "z_forward", "z_inverse",
-    "legendre_forward", "legendre_backward", "band_solve", "spec_axpby"};
+    "legendre_forward", "legendre_backward", "band_solve", "spec_axpby", "legendre_split"};
 
 int mlx_kernel_count(void) { return KID_COUNT; }
 

@@ -20,6 +20,8 @@
 // registers.
 #include "mlx_internal.cuh"
 
+#include <cuda_bf16.h>
+
 namespace {
 
 template <typename T> struct C2T;
@@ -121,13 +123,39 @@ __device__ __forceinline__ void for_lines(int N, int nlines, F f) {
 
 enum PhiMode { PHI_FWD = 0, PHI_BWD = 1, PHI_FKPP = 2 };
 
+// Forward output for the MLX_BF16X3 contraction: the value of (m, slot kk, part p
+// = Re/Im, radius r) as three BF16 parts hi, mid, lo (round to nearest, FP32
+// residuals) in the planes bs[part][(m * 2K + 2 kk + p) * Kp + r], the K-major data
+// operand that the tensor-core kernel loads by TMA.
+struct SplitOut {
+  unsigned short* bs = nullptr;   // null: write the FP32 planes instead
+  long long part;                 // elements per part plane
+  int Kp, K2;                     // row length (padded K-dim) and columns per m (2K)
+};
+template <typename T>
+__device__ __forceinline__ void split_store(const SplitOut& so, int m, int kk, int p, int r, T vt) {
+  if constexpr (sizeof(T) == 4) {
+    const float v = (float)vt;
+    const unsigned short h = __bfloat16_as_ushort(__float2bfloat16_rn(v));
+    const float r1 = v - __bfloat162float(__ushort_as_bfloat16(h));
+    const unsigned short md = __bfloat16_as_ushort(__float2bfloat16_rn(r1));
+    const float r2 = r1 - __bfloat162float(__ushort_as_bfloat16(md));
+    const unsigned short lo = __bfloat16_as_ushort(__float2bfloat16_rn(r2));
+    const long long o = ((long long)m * so.K2 + 2 * kk + p) * so.Kp + r;
+    so.bs[o] = h;
+    so.bs[so.part + o] = md;
+    so.bs[2 * so.part + o] = lo;
+  }
+}
+
 // Real analysis of packed line pairs held in L[b][m] (natural order, forward
 // DFT), scaled by 1/N, written to zm for this (z, r-tile).
 // With brev the line holds frequency p at position bitrev(p) (DIF output kept in
 // register order), so only the M retained frequencies are looked up scattered.
 template <typename T, typename C>
 __device__ void phi_unpack_store(const C* L, int ld, int N, int B, int M, int Nr, int r0, int z,
-                                 T* __restrict__ zre, T* __restrict__ zim, bool brev, int logN) {
+                                 T* __restrict__ zre, T* __restrict__ zim, bool brev, int logN,
+                                 const SplitOut& so) {
   const T inv = (T)1 / (T)N;
   const int R = 2 * B;
   const int lR = __ffs(R) - 1;          // tiles are powers of two: shifts, not divisions
@@ -147,9 +175,14 @@ __device__ void phi_unpack_store(const C* L, int ld, int N, int B, int M, int Nr
     }
     const int r = r0 + rr;
     if (r < Nr) {
-      const long long o = ((long long)z * M + m) * Nr + r;
-      zre[o] = re * inv;
-      zim[o] = im * inv;
+      if (so.bs) {
+        split_store<T>(so, m, 0, 0, r, re * inv);
+        split_store<T>(so, m, 0, 1, r, im * inv);
+      } else {
+        const long long o = ((long long)z * M + m) * Nr + r;
+        zre[o] = re * inv;
+        zim[o] = im * inv;
+      }
     }
   }
 }
@@ -159,7 +192,7 @@ __global__ void __launch_bounds__(256) k_phi(int N, int logN, int M, int Nr, int
                                              T* __restrict__ phys, T* __restrict__ zre,
                                              T* __restrict__ zim,
                                              const typename C2T<T>::type* __restrict__ tw, T gamma,
-                                             int* __restrict__ err) {
+                                             int* __restrict__ err, SplitOut so) {
   typedef typename C2T<T>::type C;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* L = reinterpret_cast<C*>(smem_raw);
@@ -191,7 +224,7 @@ __global__ void __launch_bounds__(256) k_phi(int N, int logN, int M, int Nr, int
       }
     });
     __syncthreads();
-    phi_unpack_store<T, C>(L, ld, N, B, M, Nr, r0, z, zre, zim, true, logN);
+    phi_unpack_store<T, C>(L, ld, N, B, M, Nr, r0, z, zre, zim, true, logN, so);
   } else {
     // packed Hermitian spectrum of each line pair: Zhat[m] = A_m + i B_m,
     // Zhat[N-m] = conj(A_m) + i conj(B_m), Zhat[0] = Re A_0 + i Re B_0
@@ -260,7 +293,7 @@ __global__ void __launch_bounds__(256) k_phi(int N, int logN, int M, int Nr, int
         if (r < Nr) phys[plane + (long long)j * Nr + r] = (rr < B) ? v.x : v.y;
       }
     } else {
-      phi_unpack_store<T, C>(L, ld, N, B, M, Nr, r0, z, zre, zim, false, logN);
+      phi_unpack_store<T, C>(L, ld, N, B, M, Nr, r0, z, zre, zim, false, logN, so);
     }
   }
 }
@@ -270,7 +303,7 @@ template <typename T, bool INVERSE, int E>
 __global__ void __launch_bounds__(256) k_z(int Nz, int logN, int Kz, int K, int M, int Nr, int R,
                                            T* __restrict__ zre, T* __restrict__ zim,
                                            T* __restrict__ mre, T* __restrict__ mim,
-                                           const typename C2T<T>::type* __restrict__ tw) {
+                                           const typename C2T<T>::type* __restrict__ tw, SplitOut so) {
   typedef typename C2T<T>::type C;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* L = reinterpret_cast<C*>(smem_raw);
@@ -330,9 +363,14 @@ __global__ void __launch_bounds__(256) k_z(int Nz, int logN, int Kz, int K, int 
       const int pos = (kk < Kz) ? kk : Nz - (K - kk);
       if (r < Nr) {
         const C v = L[b * ld + bitrev(pos, logN)];
-        const long long o = ((long long)kk * M + m) * Nr + r;
-        mre[o] = v.x * inv;
-        mim[o] = v.y * inv;
+        if (so.bs) {
+          split_store<T>(so, m, kk, 0, r, v.x * inv);
+          split_store<T>(so, m, kk, 1, r, v.y * inv);
+        } else {
+          const long long o = ((long long)kk * M + m) * Nr + r;
+          mre[o] = v.x * inv;
+          mim[o] = v.y * inv;
+        }
       }
     }
   } else {
@@ -367,27 +405,38 @@ constexpr int kSmemLimit = 200 * 1024;
 
 template <typename T, int MODE, int E>
 void phi_go(dim3 grid, size_t smem, cudaStream_t st, int N, int M, int Nr, int R, T* phys, T* zre,
-            T* zim, const void* tw, double gamma, int* err) {
+            T* zim, const void* tw, double gamma, int* err, const SplitOut& so) {
   typedef typename C2T<T>::type C;
   k_phi<T, MODE, E><<<grid, 256, smem, st>>>(N, ilog2(N), M, Nr, R, phys, zre, zim,
-                                             reinterpret_cast<const C*>(tw), (T)gamma, err);
+                                             reinterpret_cast<const C*>(tw), (T)gamma, err, so);
 }
 
 template <typename T, int MODE>
 void phi_dispatch(int E, dim3 grid, size_t smem, cudaStream_t st, int N, int M, int Nr, int R,
-                  T* phys, T* zre, T* zim, const void* tw, double gamma, int* err) {
+                  T* phys, T* zre, T* zim, const void* tw, double gamma, int* err, const SplitOut& so) {
   switch (E) {
-    case 1: phi_go<T, MODE, 1>(grid, smem, st, N, M, Nr, R, phys, zre, zim, tw, gamma, err); break;
-    case 2: phi_go<T, MODE, 2>(grid, smem, st, N, M, Nr, R, phys, zre, zim, tw, gamma, err); break;
-    case 4: phi_go<T, MODE, 4>(grid, smem, st, N, M, Nr, R, phys, zre, zim, tw, gamma, err); break;
-    case 8: phi_go<T, MODE, 8>(grid, smem, st, N, M, Nr, R, phys, zre, zim, tw, gamma, err); break;
-    default: phi_go<T, MODE, 16>(grid, smem, st, N, M, Nr, R, phys, zre, zim, tw, gamma, err); break;
+    case 1: phi_go<T, MODE, 1>(grid, smem, st, N, M, Nr, R, phys, zre, zim, tw, gamma, err, so); break;
+    case 2: phi_go<T, MODE, 2>(grid, smem, st, N, M, Nr, R, phys, zre, zim, tw, gamma, err, so); break;
+    case 4: phi_go<T, MODE, 4>(grid, smem, st, N, M, Nr, R, phys, zre, zim, tw, gamma, err, so); break;
+    case 8: phi_go<T, MODE, 8>(grid, smem, st, N, M, Nr, R, phys, zre, zim, tw, gamma, err, so); break;
+    default: phi_go<T, MODE, 16>(grid, smem, st, N, M, Nr, R, phys, zre, zim, tw, gamma, err, so); break;
   }
+}
+
+// the split-plane output of the BF16X3 context (forward data of the contraction)
+SplitOut split_out(mlx_ctx* c) {
+  SplitOut so;
+  if (c->precision != MLX_BF16X3 || !c->d_bsf) return so;
+  so.bs = reinterpret_cast<unsigned short*>(c->d_bsf);
+  so.Kp = (int)c->tc_kp;
+  so.K2 = 2 * c->K;
+  so.part = (long long)c->M * so.K2 * so.Kp;
+  return so;
 }
 
 template <typename T>
 int phi_launch(mlx_ctx* c, int mode, T* phys, T* zbase, const void* tw, double gamma,
-               cudaStream_t st) {
+               cudaStream_t st, const SplitOut& so = SplitOut()) {
   typedef typename C2T<T>::type C;
   const int N = c->nphi;
   int R = c->phi_tile ? c->phi_tile : auto_tile(c->nr, c->nz, 2 * 148);
@@ -401,36 +450,38 @@ int phi_launch(mlx_ctx* c, int mode, T* phys, T* zbase, const void* tw, double g
   const int E = N >= 32 ? N / 32 : 1;
   TimedLaunch tl(c, mode == PHI_FWD ? KID_PHI_FWD : (mode == PHI_BWD ? KID_PHI_BWD : KID_PHI_FKPP), st);
   int* err = c->d_err;
-  if (mode == PHI_FWD) phi_dispatch<T, PHI_FWD>(E, grid, smem, st, N, c->M, c->nr, R, phys, zre, zim, tw, gamma, err);
-  else if (mode == PHI_BWD) phi_dispatch<T, PHI_BWD>(E, grid, smem, st, N, c->M, c->nr, R, phys, zre, zim, tw, gamma, err);
-  else phi_dispatch<T, PHI_FKPP>(E, grid, smem, st, N, c->M, c->nr, R, phys, zre, zim, tw, gamma, err);
+  if (mode == PHI_FWD) phi_dispatch<T, PHI_FWD>(E, grid, smem, st, N, c->M, c->nr, R, phys, zre, zim, tw, gamma, err, so);
+  else if (mode == PHI_BWD) phi_dispatch<T, PHI_BWD>(E, grid, smem, st, N, c->M, c->nr, R, phys, zre, zim, tw, gamma, err, so);
+  else phi_dispatch<T, PHI_FKPP>(E, grid, smem, st, N, c->M, c->nr, R, phys, zre, zim, tw, gamma, err, so);
   MLX_LAUNCH_CHECK(c);
   return MLX_OK;
 }
 
 template <typename T, bool INV, int E>
-void z_go(dim3 grid, size_t smem, cudaStream_t st, mlx_ctx* c, int R, T* zb, T* mb, const void* tw) {
+void z_go(dim3 grid, size_t smem, cudaStream_t st, mlx_ctx* c, int R, T* zb, T* mb, const void* tw,
+          const SplitOut& so) {
   typedef typename C2T<T>::type C;
   const long long plz = (long long)c->nz * c->M * c->nr;
   const long long plm = (long long)c->K * c->M * c->nr;
   k_z<T, INV, E><<<grid, 256, smem, st>>>(c->nz, ilog2(c->nz), c->Kz, c->K, c->M, c->nr, R, zb,
-                                          zb + plz, mb, mb + plm, reinterpret_cast<const C*>(tw));
+                                          zb + plz, mb, mb + plm, reinterpret_cast<const C*>(tw), so);
 }
 
 template <typename T, bool INV>
 void z_dispatch(int E, dim3 grid, size_t smem, cudaStream_t st, mlx_ctx* c, int R, T* zb, T* mb,
-                const void* tw) {
+                const void* tw, const SplitOut& so) {
   switch (E) {
-    case 1: z_go<T, INV, 1>(grid, smem, st, c, R, zb, mb, tw); break;
-    case 2: z_go<T, INV, 2>(grid, smem, st, c, R, zb, mb, tw); break;
-    case 4: z_go<T, INV, 4>(grid, smem, st, c, R, zb, mb, tw); break;
-    case 8: z_go<T, INV, 8>(grid, smem, st, c, R, zb, mb, tw); break;
-    default: z_go<T, INV, 16>(grid, smem, st, c, R, zb, mb, tw); break;
+    case 1: z_go<T, INV, 1>(grid, smem, st, c, R, zb, mb, tw, so); break;
+    case 2: z_go<T, INV, 2>(grid, smem, st, c, R, zb, mb, tw, so); break;
+    case 4: z_go<T, INV, 4>(grid, smem, st, c, R, zb, mb, tw, so); break;
+    case 8: z_go<T, INV, 8>(grid, smem, st, c, R, zb, mb, tw, so); break;
+    default: z_go<T, INV, 16>(grid, smem, st, c, R, zb, mb, tw, so); break;
   }
 }
 
 template <typename T>
-int z_launch(mlx_ctx* c, bool inverse, T* zbase, T* mbase, const void* tw, cudaStream_t st) {
+int z_launch(mlx_ctx* c, bool inverse, T* zbase, T* mbase, const void* tw, cudaStream_t st,
+             const SplitOut& so = SplitOut()) {
   typedef typename C2T<T>::type C;
   int R = c->z_tile ? c->z_tile : auto_tile(c->nr, c->M, 4 * 148);
   auto need = [&](int R_) { return (size_t)R_ * (c->nz + 1) * sizeof(C); };
@@ -439,8 +490,8 @@ int z_launch(mlx_ctx* c, bool inverse, T* zbase, T* mbase, const void* tw, cudaS
   dim3 grid((c->nr + R - 1) / R, c->M);
   const int E = c->nz >= 32 ? c->nz / 32 : 1;
   TimedLaunch tl(c, inverse ? KID_Z_BWD : KID_Z_FWD, st);
-  if (!inverse) z_dispatch<T, false>(E, grid, smem, st, c, R, zbase, mbase, tw);
-  else z_dispatch<T, true>(E, grid, smem, st, c, R, zbase, mbase, tw);
+  if (!inverse) z_dispatch<T, false>(E, grid, smem, st, c, R, zbase, mbase, tw, so);
+  else z_dispatch<T, true>(E, grid, smem, st, c, R, zbase, mbase, tw, SplitOut());
   MLX_LAUNCH_CHECK(c);
   return MLX_OK;
 }
@@ -448,11 +499,12 @@ int z_launch(mlx_ctx* c, bool inverse, T* zbase, T* mbase, const void* tw, cudaS
 template <typename T>
 int fft_forward_t(mlx_ctx* c, const void* phys, cudaStream_t st, const void* twphi, const void* twz) {
   T* mixed = reinterpret_cast<T*>(c->d_mixed);
-  if (c->nz == 1) return phi_launch<T>(c, PHI_FWD, (T*)phys, mixed, twphi, 0.0, st);
+  const SplitOut so = split_out(c);
+  if (c->nz == 1) return phi_launch<T>(c, PHI_FWD, (T*)phys, mixed, twphi, 0.0, st, so);
   T* zm = reinterpret_cast<T*>(c->d_zm);
   int rc = phi_launch<T>(c, PHI_FWD, (T*)phys, zm, twphi, 0.0, st);
   if (rc) return rc;
-  return z_launch<T>(c, false, zm, mixed, twz, st);
+  return z_launch<T>(c, false, zm, mixed, twz, st, so);
 }
 
 template <typename T>
@@ -468,13 +520,14 @@ int fft_backward_t(mlx_ctx* c, void* phys, cudaStream_t st, const void* twphi, c
 template <typename T>
 int fft_fkpp_t(mlx_ctx* c, double gamma, cudaStream_t st, const void* twphi, const void* twz) {
   T* mixed = reinterpret_cast<T*>(c->d_mixed);
-  if (c->nz == 1) return phi_launch<T>(c, PHI_FKPP, nullptr, mixed, twphi, gamma, st);
+  const SplitOut so = split_out(c);
+  if (c->nz == 1) return phi_launch<T>(c, PHI_FKPP, nullptr, mixed, twphi, gamma, st, so);
   T* zm = reinterpret_cast<T*>(c->d_zm);
   int rc = z_launch<T>(c, true, zm, mixed, twz, st);
   if (rc) return rc;
   rc = phi_launch<T>(c, PHI_FKPP, nullptr, zm, twphi, gamma, st);
   if (rc) return rc;
-  return z_launch<T>(c, false, zm, mixed, twz, st);
+  return z_launch<T>(c, false, zm, mixed, twz, st, so);
 }
 
 template <typename T, int MODE, int E>

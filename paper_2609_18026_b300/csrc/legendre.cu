@@ -111,7 +111,8 @@ __global__ void __launch_bounds__(NT) k_legendre(const LegTile* __restrict__ til
 
 int mlx_legendre_forward(mlx_ctx* c, double2* spec, cudaStream_t st, const double2* addsrc,
                          double alpha) {
-  if (c->precision == MLX_BF16X3 && !addsrc) return mlx_legendre_tc_forward(c, spec, st);
+  // the BF16X3 forward FFT writes the split planes of the tensor-core form only
+  if (c->precision == MLX_BF16X3) return addsrc ? MLX_EINVAL : mlx_legendre_tc_forward(c, spec, st);
   TimedLaunch tl(c, KID_LEG_FWD, st);
   if (c->precision == MLX_FP64)
     k_legendre<double, true><<<c->ntiles_fwd, NT, 0, st>>>(c->d_tiles_fwd, c->nc, c->nr, c->M, c->K,

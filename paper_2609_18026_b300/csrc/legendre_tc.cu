@@ -15,20 +15,18 @@
 // Backward D[i][c]     = sum_n P_m[n][i] S_c[n]     (A = P_m^T, stored [m][i][n])
 // Column c of a tile is (wavenumber slot c / 2, Re if c even, Im if odd).
 //
-// One persistent CTA per SM walks its share of the work items (m, 128-row tile,
+// The data operand arrives as three BF16 planes in global memory, K-major:
+// Bs[part][m * 2K + c][k] (forward: written by the FFT kernel that produces the
+// mixed values; backward: by k_split_spec from the FP64 spectral field).  One
+// persistent CTA per SM walks its share of the work items (m, 128-row tile,
 // BN-column tile) with warp-specialised roles:
 //   warps 0-3  epilogue: TMEM -> registers -> global (each warp owns its 32 TMEM
 //              lanes), on two TMEM accumulator pairs so that the epilogue of one
 //              tile runs while the tensor core works on the next;
-//   warp 4     TMA producer of the basis operand A (three BF16 parts of a 128 x 32
-//              chunk, 64-byte swizzle) into a four-stage shared-memory ring;
+//   warp 4     TMA producer: three BF16 parts of the basis chunk (128 x 32) and of
+//              the data chunk (BN x 32), 64-byte swizzle, into a four-stage ring;
 //   warp 5     one thread issues tcgen05.mma (M = 128, N = BN, K = 16) and commits
-//              each stage back to the ring;
-//   warps 6-13 data operand B: the chunk's FP32 mixed values (forward) or FP64
-//              spectral coefficients (backward) are loaded two chunks ahead into
-//              registers, split into three BF16 parts (FP64 -> FP32 rounding by
-//              integer operations: no FP64 instruction in the kernel) and written in
-//              the same 64-byte-swizzled K-major layout.
+//              each stage back to the ring.
 // Every wait on an mbarrier is bounded.  A role that gives up records an error
 // bit in the device word and raises a CTA-wide abort flag; every role then
 // leaves its loop, the producer waits (bounded) for the tensor copies it issued
@@ -47,10 +45,7 @@ constexpr int TC_BK = 32;                  // K chunk: one 64-byte swizzled row 
 constexpr int TC_STAGES = 4;
 constexpr int TC_PROD_WARP = 4;
 constexpr int TC_MMA_WARP = 5;
-constexpr int TC_CONV_WARP0 = 6;
-constexpr int TC_CONV_WARPS = 8;
-constexpr int TC_CONV_THREADS = 32 * TC_CONV_WARPS;
-constexpr int TC_THREADS = 32 * (TC_CONV_WARP0 + TC_CONV_WARPS);   // 448
+constexpr int TC_THREADS = 32 * 6;
 constexpr int TC_MAX_BN = 128;
 constexpr unsigned TC_A_PART = TC_BM * 64;                         // one BF16 part of a 128 x 32 chunk
 constexpr unsigned TC_A_BYTES = 3 * TC_A_PART;
@@ -90,22 +85,6 @@ __device__ __forceinline__ double f32_to_f64(float v) {
   return __hiloint2double((int)hi, (int)lo);
 }
 
-__device__ __forceinline__ unsigned pack2(__nv_bfloat16 a, __nv_bfloat16 b) {
-  return (unsigned)__bfloat16_as_ushort(a) | ((unsigned)__bfloat16_as_ushort(b) << 16);
-}
-
-// four consecutive k (k % 4 == 0, one 8-byte piece of a 16-byte chunk) of one
-// column, three BF16 parts
-__device__ __forceinline__ void store_split4(unsigned char* pB, int bn, int col, int k, const float (&v)[4]) {
-  __nv_bfloat16 h[4], md[4], lo[4];
-#pragma unroll
-  for (int j = 0; j < 4; ++j) split3<float>(v[j], h[j], md[j], lo[j]);
-  const unsigned off = tcx::sw64_offset(col, k);
-  *reinterpret_cast<uint2*>(pB + off) = make_uint2(pack2(h[0], h[1]), pack2(h[2], h[3]));
-  *reinterpret_cast<uint2*>(pB + (size_t)bn * 64 + off) = make_uint2(pack2(md[0], md[1]), pack2(md[2], md[3]));
-  *reinterpret_cast<uint2*>(pB + (size_t)2 * bn * 64 + off) = make_uint2(pack2(lo[0], lo[1]), pack2(lo[2], lo[3]));
-}
-
 // Walk of one CTA's work: items blockIdx.x, blockIdx.x + gridDim.x, ...; chunks of
 // 32 along the contraction within each item.  Every role walks the same sequence.
 struct Walk {
@@ -141,118 +120,14 @@ __device__ __forceinline__ int wait3(unsigned bar, unsigned parity, volatile int
   return -1;
 }
 
-// Registers of one data chunk: forward, up to 4 units of (column, 4 k) FP32;
-// backward, up to 2 units of (slot, 4 k) complex128 as 4 x 32-bit words each.
-struct ConvRegsF { float4 v[4]; };
-struct ConvRegsB { uint4 v[2][4]; };
-
-template <bool FWD>
-struct Conv;
-
-template <>
-struct Conv<true> {
-  typedef ConvRegsF R;
-  // load the chunk (t, kc) of the mixed FP32 planes [2][K][M][Nr]
-  static __device__ __forceinline__ void load(R& r, const Walk& w, int nitems, const LegTile* items, int ct, int bn,
-                                              int nr, int M, int K, long long plane, bool vec,
-                                              const float* __restrict__ mixed) {
-    const int nunits = bn * 8;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) r.v[j] = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (!w.valid(nitems)) return;
-    const LegTile tile = items[w.t];
-    const int k0 = w.kc * TC_BK;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int u = ct + TC_CONV_THREADS * j;
-      if (u >= nunits) break;
-      const int col = u >> 3, q = u & 7;
-      const int kidx = (tile.col0 >> 1) + (col >> 1);
-      const int k = k0 + 4 * q;
-      if (kidx >= K || k >= nr) continue;
-      const float* p = mixed + (col & 1) * plane + ((long long)kidx * M + tile.m) * nr + k;
-      if (vec && k + 3 < nr) {
-        r.v[j] = __ldg(reinterpret_cast<const float4*>(p));
-      } else {
-        float e[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-          if (k + i < nr) e[i] = __ldg(p + i);
-        r.v[j] = make_float4(e[0], e[1], e[2], e[3]);
-      }
-    }
-  }
-  static __device__ __forceinline__ void store(const R& r, unsigned char* pB, int ct, int bn) {
-    const int nunits = bn * 8;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int u = ct + TC_CONV_THREADS * j;
-      if (u >= nunits) break;
-      const float v[4] = {r.v[j].x, r.v[j].y, r.v[j].z, r.v[j].w};
-      store_split4(pB, bn, u >> 3, 4 * (u & 7), v);
-    }
-  }
-};
-
-template <>
-struct Conv<false> {
-  typedef ConvRegsB R;
-  // load the chunk (t, kc) of the ragged complex128 spectral field
-  static __device__ __forceinline__ void load(R& r, const Walk& w, int nitems, const LegTile* items, int ct, int bn,
-                                              int nc, const long long* __restrict__ soff, int K,
-                                              const double2* __restrict__ spec) {
-    const int nunits = (bn >> 1) * 8;
-#pragma unroll
-    for (int j = 0; j < 2; ++j)
-#pragma unroll
-      for (int i = 0; i < 4; ++i) r.v[j][i] = make_uint4(0u, 0u, 0u, 0u);
-    if (!w.valid(nitems)) return;
-    const LegTile tile = items[w.t];
-    const int Nm = nc - tile.m;
-    const int k0 = w.kc * TC_BK;
-    const long long so = soff[tile.m];
-#pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      const int u = ct + TC_CONV_THREADS * j;
-      if (u >= nunits) break;
-      const int sl = u >> 3, q = u & 7;
-      const int kidx = (tile.col0 >> 1) + sl;
-      const int k = k0 + 4 * q;
-      if (kidx >= K) continue;
-      const uint4* p = reinterpret_cast<const uint4*>(spec + so + (long long)kidx * Nm + k);
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-        if (k + i < Nm) r.v[j][i] = __ldg(p + i);
-    }
-  }
-  static __device__ __forceinline__ void store(const R& r, unsigned char* pB, int ct, int bn) {
-    const int nunits = (bn >> 1) * 8;
-#pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      const int u = ct + TC_CONV_THREADS * j;
-      if (u >= nunits) break;
-      float re[4], im[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        re[i] = f64w_to_f32(r.v[j][i].y, r.v[j][i].x);
-        im[i] = f64w_to_f32(r.v[j][i].w, r.v[j][i].z);
-      }
-      const int sl = u >> 3, k = 4 * (u & 7);
-      store_split4(pB, bn, 2 * sl, k, re);
-      store_split4(pB, bn, 2 * sl + 1, k, im);
-    }
-  }
-};
-
-template <bool FWD>
+template <bool FWD, int NPROD>
 __global__ void __launch_bounds__(TC_THREADS, 1)
-k_leg_tc(const __grid_constant__ CUtensorMap tmapA, const LegTile* __restrict__ items, int nitems, int nc, int nr,
-         int M, int K, int bn, int tmem_cols, int nprod, int vec, int expire, const long long* __restrict__ soff,
-         const long long* __restrict__ arow_base, const float* __restrict__ mixed_in,
-         const double2* __restrict__ spec_in, double2* __restrict__ spec_out, float* __restrict__ mixed_out,
-         int* __restrict__ err) {
+k_leg_tc(const __grid_constant__ CUtensorMap tmapA, const __grid_constant__ CUtensorMap tmapB,
+         const LegTile* __restrict__ items, int nitems, int nc, int nr, int M, int K, int bn, int tmem_cols,
+         int expire, const long long* __restrict__ soff, const long long* __restrict__ arow_base,
+         double2* __restrict__ spec_out, float* __restrict__ mixed_out, int* __restrict__ err) {
   extern __shared__ unsigned char smem_raw[];
-  __shared__ uint64_t full_a[TC_STAGES], full_b[TC_STAGES], empty[TC_STAGES], tfull[2], tempty[2], drain;
+  __shared__ uint64_t full_a[TC_STAGES], empty[TC_STAGES], tfull[2], tempty[2], drain;
   __shared__ unsigned tmem_slot;
   __shared__ int abort_flag;
   volatile int* abortp = &abort_flag;
@@ -265,7 +140,6 @@ k_leg_tc(const __grid_constant__ CUtensorMap tmapA, const LegTile* __restrict__ 
   if (tid == 0) {
     for (int s = 0; s < TC_STAGES; ++s) {
       tcx::mbar_init(tcx::smem_u32(&full_a[s]), 1);
-      tcx::mbar_init(tcx::smem_u32(&full_b[s]), TC_CONV_THREADS);
       tcx::mbar_init(tcx::smem_u32(&empty[s]), 1);
     }
     for (int b = 0; b < 2; ++b) {
@@ -297,10 +171,19 @@ k_leg_tc(const __grid_constant__ CUtensorMap tmapA, const LegTile* __restrict__ 
         }
         const LegTile tile = items[w.t];
         const unsigned sA = raw + pad + (unsigned)s * sbytes;
+        const unsigned sB = sA + TC_A_BYTES;
+        if (w.kc == 0 && w.t + (int)gridDim.x < nitems) {
+          // warm the next item's tile record and basis-row base into L1
+          asm volatile("prefetch.global.L1 [%0];" ::"l"(items + w.t + gridDim.x));
+        }
         const unsigned bar = tcx::smem_u32(&full_a[s]);
-        tcx::mbar_expect_tx(bar, TC_A_BYTES);
+        tcx::mbar_expect_tx(bar, TC_A_BYTES + 3u * (unsigned)bn * 64u);
         const int arow = (int)arow_base[tile.m] + tile.row0;
-        for (int p = 0; p < 3; ++p) tcx::tma_load_3d(sA + (unsigned)p * TC_A_PART, &tmapA, w.kc * TC_BK, arow, p, bar);
+        const int brow = tile.m * 2 * K + tile.col0;
+        for (int p = 0; p < 3; ++p) {
+          tcx::tma_load_3d(sA + (unsigned)p * TC_A_PART, &tmapA, w.kc * TC_BK, arow, p, bar);
+          tcx::tma_load_3d(sB + (unsigned)p * (unsigned)bn * 64u, &tmapB, w.kc * TC_BK, brow, p, bar);
+        }
         ++fills[s];
       }
       // drain: every tensor copy issued must land before the CTA leaves
@@ -311,8 +194,6 @@ k_leg_tc(const __grid_constant__ CUtensorMap tmapA, const LegTile* __restrict__ 
     // ---- tensor-core issue
     if (lane == 0) {
       const unsigned idesc = tcx::idesc_bf16(TC_BM, bn);
-      const int pa[8] = {0, 0, 1, 0, 2, 1, 1, 2};
-      const int pb[8] = {0, 1, 0, 2, 0, 1, 2, 1};
       bool issued = false, ok = true;
       int g = 0, tl_cur = -1;
       for (Walk w = walk_begin<FWD>(items, nitems, nc, nr); w.valid(nitems) && ok;) {
@@ -327,21 +208,31 @@ k_leg_tc(const __grid_constant__ CUtensorMap tmapA, const LegTile* __restrict__ 
           }
         }
         const int s = g % TC_STAGES, u = g / TC_STAGES;
-        int r = wait3(tcx::smem_u32(&full_a[s]), (unsigned)(u & 1), abortp);
-        if (r > 0) r = wait3(tcx::smem_u32(&full_b[s]), (unsigned)(u & 1), abortp);
+        const int r = wait3(tcx::smem_u32(&full_a[s]), (unsigned)(u & 1), abortp);
         if (r < 0) { atomicOr(err, 1); *abortp = 1; }
         if (r <= 0) { ok = false; break; }
         tcx::tc_fence_after();
         const unsigned sA = raw + pad + (unsigned)s * sbytes;
         const unsigned sB = sA + TC_A_BYTES;
-        const unsigned dt0 = tmem + (unsigned)(buf * 2 * bn);
+        const unsigned dhi = tmem + (unsigned)(buf * 2 * bn), dco = dhi + (unsigned)bn;
+        // descriptors of the three parts of each operand, once per chunk
+        const uint64_t a0 = tcx::desc_sw64(sA), a1 = tcx::desc_sw64(sA + TC_A_PART),
+                       a2 = tcx::desc_sw64(sA + 2 * TC_A_PART);
+        const uint64_t b0 = tcx::desc_sw64(sB), b1 = tcx::desc_sw64(sB + (unsigned)bn * 64u),
+                       b2 = tcx::desc_sw64(sB + 2u * (unsigned)bn * 64u);
 #pragma unroll
         for (int ks = 0; ks < TC_BK / 16; ++ks) {
-          for (int q = 0; q < nprod; ++q) {
-            const uint64_t da = tcx::desc_sw64(sA + (unsigned)pa[q] * TC_A_PART) + (uint64_t)(2 * ks);
-            const uint64_t db = tcx::desc_sw64(sB + (unsigned)pb[q] * (unsigned)bn * 64u) + (uint64_t)(2 * ks);
-            const unsigned acc = (w.kc | ks) ? 1u : (q > 1 ? 1u : 0u);
-            tcx::mma_bf16(dt0 + (q == 0 ? 0u : (unsigned)bn), da, db, idesc, acc);
+          const uint64_t o = (uint64_t)(2 * ks);           // 32 bytes per 16-wide K step
+          const unsigned first = (w.kc | ks) ? 1u : 0u;    // 0: the tile's first step overwrites
+          tcx::mma_bf16(dhi, a0 + o, b0 + o, idesc, first);   // hi * hi
+          tcx::mma_bf16(dco, a0 + o, b1 + o, idesc, first);   // hi * mid
+          tcx::mma_bf16(dco, a1 + o, b0 + o, idesc, 1u);      // mid * hi
+          tcx::mma_bf16(dco, a0 + o, b2 + o, idesc, 1u);      // hi * lo
+          tcx::mma_bf16(dco, a2 + o, b0 + o, idesc, 1u);      // lo * hi
+          tcx::mma_bf16(dco, a1 + o, b1 + o, idesc, 1u);      // mid * mid
+          if (NPROD == 8) {
+            tcx::mma_bf16(dco, a1 + o, b2 + o, idesc, 1u);    // mid * lo
+            tcx::mma_bf16(dco, a2 + o, b1 + o, idesc, 1u);    // lo * mid
           }
         }
         tcx::mma_commit(tcx::smem_u32(&empty[s]));
@@ -357,38 +248,7 @@ k_leg_tc(const __grid_constant__ CUtensorMap tmapA, const LegTile* __restrict__ 
         if (!tcx::mbar_wait(tcx::smem_u32(&drain), 0u)) atomicOr(err, 4);
       }
     }
-  } else if (warp >= TC_CONV_WARP0) {
-    // ---- data operand B: two chunks in flight in registers
-    typedef Conv<FWD> CV;
-    typename CV::R ra, rb;
-    const int ct = tid - 32 * TC_CONV_WARP0;
-    Walk ld = walk_begin<FWD>(items, nitems, nc, nr);
-    auto load = [&](typename CV::R& r, const Walk& w) {
-      if constexpr (FWD) CV::load(r, w, nitems, items, ct, bn, nr, M, K, plane, vec != 0, mixed_in);
-      else CV::load(r, w, nitems, items, ct, bn, nc, soff, K, spec_in);
-    };
-    load(ra, ld);
-    walk_next<FWD>(ld, items, nitems, nc, nr);
-    load(rb, ld);
-    walk_next<FWD>(ld, items, nitems, nc, nr);
-    int g = 0;
-    bool odd = false;
-    for (Walk w = walk_begin<FWD>(items, nitems, nc, nr); w.valid(nitems); walk_next<FWD>(w, items, nitems, nc, nr), ++g) {
-      const int s = g % TC_STAGES, u = g / TC_STAGES;
-      if (u > 0) {
-        const int r = wait3(tcx::smem_u32(&empty[s]), (unsigned)((u - 1) & 1), abortp);
-        if (r < 0) { atomicOr(err, 2); *abortp = 1; }
-        if (r <= 0) break;
-      }
-      unsigned char* pB = smem_raw + pad + (size_t)s * sbytes + TC_A_BYTES;
-      if (!odd) { CV::store(ra, pB, ct, bn); load(ra, ld); }
-      else      { CV::store(rb, pB, ct, bn); load(rb, ld); }
-      walk_next<FWD>(ld, items, nitems, nc, nr);
-      odd = !odd;
-      tcx::fence_proxy_async();
-      tcx::mbar_arrive(tcx::smem_u32(&full_b[s]));
-    }
-  } else {
+  } else if (warp < 4) {
     // ---- epilogue (warps 0-3): TMEM lanes 32 warp .. 32 warp + 31
     for (Walk w = walk_begin<FWD>(items, nitems, nc, nr); w.valid(nitems);) {
       const int buf = w.tl & 1;
@@ -444,6 +304,30 @@ k_leg_tc(const __grid_constant__ CUtensorMap tmapA, const LegTile* __restrict__ 
   }
 }
 
+// Backward data operand: the FP64 spectral field split into three BF16 parts,
+// Bs[part][m * 2K + 2 k + (0 Re, 1 Im)][n - m] (row length Kq; the rows' tails
+// n - m >= Nc - m stay zero from allocation).  FP64 -> FP32 by integer rounding,
+// then FP32 residuals.  One thread per complex coefficient.
+__global__ void k_split_spec(int nc, int K, int Kq, long long part, const long long* __restrict__ soff,
+                             const double2* __restrict__ spec, unsigned short* __restrict__ bs) {
+  const int m = blockIdx.z, kidx = blockIdx.y;
+  const int Nm = nc - m;
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= Nm) return;
+  const long long idx = soff[m] + (long long)kidx * Nm + a;
+  const uint4 wv = __ldg(reinterpret_cast<const uint4*>(spec) + idx);
+  const float v[2] = {f64w_to_f32(wv.y, wv.x), f64w_to_f32(wv.w, wv.z)};
+#pragma unroll
+  for (int p = 0; p < 2; ++p) {
+    __nv_bfloat16 h, md, l;
+    split3<float>(v[p], h, md, l);
+    const long long o = ((long long)m * 2 * K + 2 * kidx + p) * Kq + a;
+    bs[o] = __bfloat16_as_ushort(h);
+    bs[part + o] = __bfloat16_as_ushort(md);
+    bs[2 * part + o] = __bfloat16_as_ushort(l);
+  }
+}
+
 // BF16 split tables from the FP64 basis.
 //  Wb[sp][t][k]  t = row (m, n - m) of W, k = i < Nr (zero up to Kp)
 //  Pb[sp][m * Nr + i][k]  k = n - m < Nc - m (zero up to Kq)
@@ -483,7 +367,10 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
-int encode_map(mlx_ctx* c, CUtensorMap* map, void* base, long long kpad, long long rows) {
+// 3-D map [part][row][k] of BF16 values: kdim valid elements per row (TMA fills
+// zeros beyond), row length kpad elements, `rows` rows, box 32 x box_rows x 1.
+int encode_map(mlx_ctx* c, CUtensorMap* map, void* base, long long kdim, long long kpad, long long rows,
+               int box_rows) {
   static EncodeTiledFn fn = nullptr;
   if (!fn) {
     void* p = nullptr;
@@ -492,9 +379,9 @@ int encode_map(mlx_ctx* c, CUtensorMap* map, void* base, long long kpad, long lo
     if (q != cudaDriverEntryPointSuccess || !p) { c->last_err = "cuTensorMapEncodeTiled unavailable"; return MLX_ECUDA; }
     fn = (EncodeTiledFn)p;
   }
-  cuuint64_t dims[3] = {(cuuint64_t)kpad, (cuuint64_t)rows, 3};
+  cuuint64_t dims[3] = {(cuuint64_t)kdim, (cuuint64_t)rows, 3};
   cuuint64_t strides[2] = {(cuuint64_t)kpad * 2, (cuuint64_t)(kpad * rows * 2)};
-  cuuint32_t box[3] = {TC_BK, TC_BM, 1};   // 32 BF16 = one 64-byte swizzled row
+  cuuint32_t box[3] = {TC_BK, (cuuint32_t)box_rows, 1};   // 32 BF16 = one 64-byte swizzled row
   cuuint32_t estr[3] = {1, 1, 1};
   CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides, box, estr,
                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -529,10 +416,20 @@ int mlx_tc_prepare(mlx_ctx* c, cudaStream_t st) {
                                                                 c->d_boff, c->d_W64, c->d_P64,
                                                                 (__nv_bfloat16*)c->d_Wb, (__nv_bfloat16*)c->d_Pb);
   MLX_LAUNCH_CHECK(c);
-  int rc = encode_map(c, &c->tmapW, c->d_Wb, Kp, c->tri);
+  int rc = encode_map(c, &c->tmapW, c->d_Wb, Kp, Kp, c->tri, TC_BM);
   if (rc) return rc;
-  rc = encode_map(c, &c->tmapP, c->d_Pb, Kq, (long long)c->M * c->nr);
+  rc = encode_map(c, &c->tmapP, c->d_Pb, Kq, Kq, (long long)c->M * c->nr, TC_BM);
   if (rc) return rc;
+  // data-operand planes [3][M * 2K][K pad]: forward (written by the FFT kernels,
+  // rows of Nr radii; the map reads zeros beyond Nr) and backward (written by
+  // k_split_spec, rows of Nc - m coefficients; the tails stay zero from here)
+  c->tc_kp = Kp;
+  c->tc_kq = Kq;
+  const long long brows = (long long)c->M * 2 * c->K;
+  MLX_CUDA_TRY(c, cudaMalloc(&c->d_bsf, sizeof(__nv_bfloat16) * 3 * brows * Kp));
+  MLX_CUDA_TRY(c, cudaMalloc(&c->d_bsb, sizeof(__nv_bfloat16) * 3 * brows * Kq));
+  MLX_CUDA_TRY(c, cudaMemsetAsync(c->d_bsf, 0, sizeof(__nv_bfloat16) * 3 * brows * Kp, st));
+  MLX_CUDA_TRY(c, cudaMemsetAsync(c->d_bsb, 0, sizeof(__nv_bfloat16) * 3 * brows * Kq, st));
   // A-row bases: W rows of m start at sum_{m'<m}(Nc - m'); P^T rows at m * Nr
   std::vector<long long> aw(c->M), ap(c->M);
   long long t = 0;
@@ -583,31 +480,48 @@ int mlx_tc_retile(mlx_ctx* c, int bn_req, cudaStream_t st) {
   int cols = 32;
   while (cols < 4 * c->tc_bn) cols <<= 1;   // two tiles in flight x two accumulators of BN columns
   c->tc_tmem_cols = cols;
+  // data-operand maps: boxes of BN rows (columns of the tile)
+  const long long brows = (long long)c->M * 2 * c->K;
+  int rc = encode_map(c, &c->tmapBf, c->d_bsf, c->nr, c->tc_kp, brows, c->tc_bn);
+  if (rc) return rc;
+  rc = encode_map(c, &c->tmapBb, c->d_bsb, c->tc_kq, c->tc_kq, brows, c->tc_bn);
+  if (rc) return rc;
   // the attribute is a per-function ceiling shared by every context: the largest
   // size any tile width uses
   const int smem = (int)tc_smem(TC_MAX_BN);
-  MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_leg_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-  MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_leg_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_leg_tc<true, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_leg_tc<false, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_leg_tc<true, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_leg_tc<false, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   return MLX_OK;
 }
 
 int mlx_legendre_tc_forward(mlx_ctx* c, double2* spec, cudaStream_t st) {
   TimedLaunch tl(c, KID_LEG_FWD, st);
   const int grid = c->ntc_fwd < sm_count() ? c->ntc_fwd : sm_count();
-  k_leg_tc<true><<<grid, TC_THREADS, tc_smem(c->tc_bn), st>>>(
-      c->tmapW, c->d_tc_fwd, c->ntc_fwd, c->nc, c->nr, c->M, c->K, c->tc_bn, c->tc_tmem_cols, c->tc_products,
-      (c->nr & 3) == 0 ? 1 : 0, c->tc_expire, c->d_soff, c->d_arowW, (const float*)c->d_mixed, nullptr, spec,
-      nullptr, c->d_err);
+  auto kern = c->tc_products == 8 ? k_leg_tc<true, 8> : k_leg_tc<true, 6>;
+  kern<<<grid, TC_THREADS, tc_smem(c->tc_bn), st>>>(
+      c->tmapW, c->tmapBf, c->d_tc_fwd, c->ntc_fwd, c->nc, c->nr, c->M, c->K, c->tc_bn, c->tc_tmem_cols,
+      c->tc_expire, c->d_soff, c->d_arowW, spec, nullptr, c->d_err);
   MLX_LAUNCH_CHECK(c);
   return MLX_OK;
 }
 
 int mlx_legendre_tc_backward(mlx_ctx* c, const double2* spec, cudaStream_t st) {
+  {
+    TimedLaunch tl(c, KID_LEG_SPLIT, st);
+    const int tb = c->nc >= 128 ? 128 : 64;
+    k_split_spec<<<dim3((c->nc + tb - 1) / tb, c->K, c->M), tb, 0, st>>>(
+        c->nc, c->K, (int)c->tc_kq, (long long)c->M * 2 * c->K * c->tc_kq, c->d_soff, spec,
+        (unsigned short*)c->d_bsb);
+    MLX_LAUNCH_CHECK(c);
+  }
   TimedLaunch tl(c, KID_LEG_BWD, st);
   const int grid = c->ntc_bwd < sm_count() ? c->ntc_bwd : sm_count();
-  k_leg_tc<false><<<grid, TC_THREADS, tc_smem(c->tc_bn), st>>>(
-      c->tmapP, c->d_tc_bwd, c->ntc_bwd, c->nc, c->nr, c->M, c->K, c->tc_bn, c->tc_tmem_cols, c->tc_products,
-      0, c->tc_expire, c->d_soff, c->d_arowP, nullptr, spec, nullptr, (float*)c->d_mixed, c->d_err);
+  auto kern = c->tc_products == 8 ? k_leg_tc<false, 8> : k_leg_tc<false, 6>;
+  kern<<<grid, TC_THREADS, tc_smem(c->tc_bn), st>>>(
+      c->tmapP, c->tmapBb, c->d_tc_bwd, c->ntc_bwd, c->nc, c->nr, c->M, c->K, c->tc_bn, c->tc_tmem_cols,
+      c->tc_expire, c->d_soff, c->d_arowP, nullptr, (float*)c->d_mixed, c->d_err);
   MLX_LAUNCH_CHECK(c);
   return MLX_OK;
 }

@@ -25,7 +25,7 @@
 // Kernel identifiers for the opt-in per-launch CUDA-event timing.
 enum KernelId {
   KID_PHI_FWD = 0, KID_PHI_BWD, KID_PHI_FKPP, KID_Z_FWD, KID_Z_BWD,
-  KID_LEG_FWD, KID_LEG_BWD, KID_BAND_SOLVE, KID_AXPBY, KID_COUNT
+  KID_LEG_FWD, KID_LEG_BWD, KID_BAND_SOLVE, KID_AXPBY, KID_LEG_SPLIT, KID_COUNT
 };
 
 struct TimingState {
@@ -107,6 +107,10 @@ struct mlx_ctx {
   void* d_Wb = nullptr;                // BF16 splits of W: [3][T][Kp]
   void* d_Pb = nullptr;                // BF16 splits of P^T: [3][M*Nr][Kq]
   CUtensorMap tmapW, tmapP;
+  void* d_bsf = nullptr;               // BF16 splits of the forward data operand: [3][M*2K][Kp]
+  void* d_bsb = nullptr;               // ... of the backward data operand: [3][M*2K][Kq]
+  CUtensorMap tmapBf, tmapBb;
+  long long tc_kp = 0, tc_kq = 0;      // padded contraction lengths (multiples of 32)
   long long* d_arowW = nullptr;
   long long* d_arowP = nullptr;
   LegTile* d_tc_fwd = nullptr;
@@ -151,6 +155,11 @@ struct mlx_ctx {
   void* d_vphys = nullptr;             // 6 physical temporaries
   double* d_setup_scratch = nullptr;
   double* d_diag = nullptr;            // mlx_diag partial sums [M K][4] and result [4]
+  // adaptive modal filter (between steps): per-field [eps, tail] x 2, partials [M K][2],
+  // multiplier tables [2][Nc + M + Kz]
+  bool filter_on = false;
+  double* d_filt = nullptr;
+  double filt_zeta_c = 2.0 / 3.0, filt_tau = 2e-2, filt_eps_max = 36.0, filt_relax = 0.25;
   int solve_cpw = 8;                   // real chains per warp in the banded solve (4..32)
   int solve_wpb = 4;                   // warps per CTA in the banded solve (1..4)
   int solve_direct = 0;                // 2: lean variant (16 or 32 chains per warp, packed
@@ -261,5 +270,6 @@ int mlx_band_solve(mlx_ctx* c, int step, const double2* s, const double2* A,
 // BF16 parts [P][Ma][Kp], B [Nb][Kp], both K-major; see the file for the contract.
 int mlx_gemm_tc(int P, const void* A, long long Ma, const void* B, long long Nb, long long Kp, int M, int N, int K,
                 float* C, int split, int* err, cudaStream_t st, const float* bias = nullptr);
+int mlx_filter_fields(mlx_ctx* c, int nfields, double2* state, cudaStream_t st);   // filter.cu
 int mlx_spec_axpby(mlx_ctx* c, double a, const double2* x, double b, const double2* y,
                    double2* out, cudaStream_t st, long long n = -1);

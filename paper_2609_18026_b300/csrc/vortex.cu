@@ -238,6 +238,54 @@ __global__ void k_rdr_band(int M, int nc, const long long* __restrict__ rows, do
 
 inline unsigned nblk(long long n, int tb) { return (unsigned)((n + tb - 1) / tb); }
 
+// Kinetic-energy density of one (m, k) harmonic of the velocity, on the Gauss nodes:
+// part[m K + k] = mult_m sum_i w_i / (1 - x_i)^2 (|r v_r|^2 / r_i^2 + |r v_phi|^2 / r_i^2 + |v_z|^2)
+// with each component evaluated from its coefficients by the FP64 basis table.
+constexpr int kEnThreads = 128;
+__global__ void __launch_bounds__(kEnThreads) k_energy_blocks(int nc, int nr, int K, const long long* __restrict__ soff,
+                                                              const long long* __restrict__ boff,
+                                                              const double* __restrict__ x, const double* __restrict__ w,
+                                                              const double* __restrict__ rn, const double* __restrict__ P64,
+                                                              const double2* __restrict__ rvr,
+                                                              const double2* __restrict__ rvp,
+                                                              const double2* __restrict__ vz, double* __restrict__ part) {
+  extern __shared__ double2 ev[];      // [3][Nc - m]
+  __shared__ double red[kEnThreads];
+  const int kidx = blockIdx.x, m = blockIdx.y;
+  const int Nm = nc - m;
+  const long long base = soff[m] + (long long)kidx * Nm;
+  for (int a = threadIdx.x; a < Nm; a += blockDim.x) {
+    ev[a] = rvr[base + a];
+    ev[Nm + a] = rvp[base + a];
+    ev[2 * Nm + a] = vz[base + a];
+  }
+  __syncthreads();
+  const double* Pm = P64 + boff[m];
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < nr; i += blockDim.x) {
+    double f[6] = {0, 0, 0, 0, 0, 0};
+    for (int a = 0; a < Nm; ++a) {
+      const double pv = Pm[(long long)a * nr + i];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        f[2 * c] = fma(pv, ev[c * Nm + a].x, f[2 * c]);
+        f[2 * c + 1] = fma(pv, ev[c * Nm + a].y, f[2 * c + 1]);
+      }
+    }
+    const double om = 1.0 - x[i];
+    const double r2 = rn[i] * rn[i];
+    const double e = (fma(f[0], f[0], f[1] * f[1]) + fma(f[2], f[2], f[3] * f[3])) / r2 + fma(f[4], f[4], f[5] * f[5]);
+    acc = fma(w[i] / (om * om), e, acc);
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int h = kEnThreads / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[(long long)m * K + kidx] = (m == 0 ? 1.0 : 2.0) * red[0];
+}
+
 }  // namespace
 
 int mlx_vortex_prepare(mlx_ctx* c, cudaStream_t st) {
@@ -315,4 +363,39 @@ int mlx_vortex_nonlinear(mlx_ctx* c, double U0, const double2* state, double2* o
   if (!c->vortex_ready) return MLX_ESTATE;
   if (c->precision == MLX_FP64) return vortex_nonlinear_t<double>(c, U0, state, out, st);
   return vortex_nonlinear_t<float>(c, U0, state, out, st);
+}
+
+// Axial energy spectrum of the two-field state: E[|k|] for |k| < Kz (host), see mlx.h.
+extern "C" int mlx_axial_energy(mlx_ctx* c, const void* state, double* E, mlx_stream stream) {
+  if (!c || !state || !E || (((uintptr_t)state) & 15u)) return MLX_EINVAL;
+  if (!c->vortex_ready) return MLX_ESTATE;
+  cudaStream_t st = (cudaStream_t)stream;
+  const long long ns = c->n_spec;
+  const double2* psi = (const double2*)state;
+  const double2* chi = psi + ns;
+  double2* F[6];
+  for (int i = 0; i < 6; ++i) F[i] = c->d_vspec + ns * i;
+  const int vt = c->nc >= 256 ? 256 : ((c->nc + 31) / 32) * 32;
+  k_vortex_fields<<<dim3(c->K, c->M), vt, sizeof(double2) * 4 * c->nc, st>>>(
+      c->nc, c->Kz, c->K, c->lz, c->d_soff, c->d_lap_off, c->d_rdr, c->d_lap, psi, chi, F[0], F[1], F[2], F[3],
+      F[4], F[5]);
+  MLX_LAUNCH_CHECK(c);
+  // the partial sums go to the (then unused) seventh spectral temporary
+  double* part = reinterpret_cast<double*>(c->d_vspec + ns * 6);
+  if ((long long)c->M * c->K > 2 * ns) return MLX_EINVAL;
+  k_energy_blocks<<<dim3(c->K, c->M), kEnThreads, sizeof(double2) * 3 * c->nc, st>>>(
+      c->nc, c->nr, c->K, c->d_soff, c->d_boff, c->d_x, c->d_w, c->d_r, c->d_P64, F[0], F[1], F[2], part);
+  MLX_LAUNCH_CHECK(c);
+  std::vector<double> h((size_t)c->M * c->K);
+  MLX_CUDA_TRY(c, cudaMemcpyAsync(h.data(), part, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, st));
+  MLX_CUDA_TRY(c, cudaStreamSynchronize(st));
+  const double scale = M_PI * c->lz * c->ell * c->ell;
+  for (int k = 0; k < c->Kz; ++k) E[k] = 0.0;
+  for (int m = 0; m < c->M; ++m)
+    for (int kidx = 0; kidx < c->K; ++kidx) {
+      const int k = kidx < c->Kz ? kidx : c->K - kidx;
+      E[k] += h[(size_t)m * c->K + kidx];
+    }
+  for (int k = 0; k < c->Kz; ++k) E[k] *= scale;
+  return MLX_OK;
 }

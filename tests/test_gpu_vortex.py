@@ -234,3 +234,22 @@ def test_vortex_pair_256_sampled(record):
         ctx.close()
         del state, prev
         torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("prec", [B.FP64, B.BF16X3])
+def test_axial_energy_parity(prec, record):
+    # the axial kinetic-energy spectrum of a perturbed vortex pair against the oracle
+    nr, nphi, nz, ell, lz = 32, 32, 16, 1.0, 8.6
+    g, ctx = pair(nr, nphi, nz, ell, lz=lz, policy="twothirds", precision=prec)
+    ctx.vortex_setup()
+    r, phi, z = g.nodes3()
+    ops = O.VortexOps(g)
+    wzs = O.forward(g, W.vortex_pair_omega(r, phi, z, lz=lz, amp=0.05))
+    psi = [np.stack([-ops.lap_h_inv(m, wzs[m][kk]) for kk in range(g.K)]) for m in range(g.M)]
+    chi = O.from_flat(g, W.random_spectral(g.nc, g.M, g.Kz, seed=3, scale_decay=0.5) * 1e-3)
+    from oracle.vortex import axial_energy
+    ref = axial_energy(g, ops, psi, chi)
+    got = np.array(ctx.axial_energy(to_gpu_spec(np.concatenate([O.to_flat(g, psi), O.to_flat(g, chi)]))))
+    err = np.abs(got - ref) / np.abs(ref)
+    record("axial_energy", precision=PNAME[prec], E0=float(ref[0]), E1=float(ref[1]), max_rel_err=float(np.max(err)))
+    assert np.max(err) <= 1e-11

@@ -187,3 +187,25 @@ def test_jacobi_and_r2_laplacian_by_quadrature():
         Q = ops.Q[m]
         k = nc - m - 2
         assert np.max(np.abs(Q[:k, :k] - Qq[:k, :k])) < 1e-11 * np.max(np.abs(Qq))
+
+
+def test_axial_energy_closed_form():
+    # psi = -(1 + r^2)^-2 (axisymmetric, k = 0): v_phi = 4 r (1 + r^2)^-3 and
+    # E_0 = (1/2) Lz 2 pi int 16 r^3 (1 + r^2)^-6 dr = 16 pi Lz / 40 = 0.4 pi Lz;
+    # adding a k = 1 poloidal perturbation puts energy in E_1 only (linear in the
+    # perturbation's square), leaving E_0 unchanged to round-off
+    from oracle.vortex import axial_energy
+    g = O.Grid(48, 8, 8, 1.0, lz=5.0)
+    ops = O.VortexOps(g)
+    r, phi, z = g.nodes3()
+    psi = O.forward(g, -(1.0 + r ** 2) ** -2.0 + 0 * phi + 0 * z)
+    chi = [np.zeros_like(b) for b in psi]
+    E = axial_energy(g, ops, psi, chi)
+    assert abs(E[0] - 0.4 * math.pi * g.lz) <= 1e-10 * E[0]
+    assert np.all(np.abs(E[1:]) <= 1e-20)
+    kap = 2 * math.pi / g.lz
+    chi1 = O.forward(g, 1e-3 * r ** 2 / (1 + r ** 2) ** 2 * np.cos(kap * z) + 0 * phi)
+    E2 = axial_energy(g, ops, psi, chi1)
+    E3 = axial_energy(g, ops, psi, [2.0 * b for b in chi1])
+    assert abs(E2[0] - E[0]) <= 1e-10 * E[0]
+    assert E2[1] > 0 and abs(E3[1] / E2[1] - 4.0) <= 1e-10
