@@ -326,6 +326,60 @@ def measure_vortex(B, W, torch, dev, stream, steps=20, prec=None, with_errors=Tr
     return out
 
 
+def measure_production(B, W, torch, dev, stream, prec=None, steps=30, dt=1e-2):
+    """The 256^3 production run of the scaling measurements (Sec. 4.2, Table 3): the
+    co-rotating q-vortex pair at (+-2, 0), q = 1, U_z = -0.5, ell = 4, Lz = 2 pi,
+    nu = 1e-4 (Gamma / nu = 6.3e4), a 1e-10 seed; Nr = Nphi = Nz = 256, Nc = 256,
+    |m| <= 128 and |k| <= 128 (the Nyquist-keeping chop: 6.37 million complex
+    coefficients per potential), p = 8 hyperviscosity nu_h = 5e-7, the adaptive
+    filter on, and 30 steps at dt = 1e-2 (the Richardson start, then AB-CN).  The
+    pair's net circulation and axial flux are carried by the log proxies.  One
+    untimed 30-step run captures the graphs; the state is then reset and the 30
+    steps are timed with CUDA events (the number to set beside Table 3's seconds
+    per 30 steps)."""
+    import math as _m
+    prec = B.BF16X3 if prec is None else prec
+    t0 = time.perf_counter()
+    ctx, state0, cs = _qvortex_setup(B, W, torch, dev, (256, 256, 256), 4.0, 2.0 * _m.pi, prec, B.CHOP_NYQUIST, dt)
+    setup_s = time.perf_counter() - t0
+    state = state0.clone()
+    prev = torch.zeros_like(state)
+    ctx.advance(B.NONLIN_VORTEX, [0.0], state, prev, steps, True)     # untimed: graphs captured
+    torch.cuda.synchronize()
+    state.copy_(state0)
+    prev.zero_()
+    # (the filter amplitudes carry over from the untimed run: resetting them through
+    # mlx_filter_setup would drop the captured graphs, and the filter's cost does
+    # not depend on them)
+    z0 = ctx.vortex_diag(state)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    ctx.advance(B.NONLIN_VORTEX, [0.0], state, prev, steps, True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    ok = bool(torch.isfinite(state.real).all().item())
+    ctx.device_status()
+    z1 = ctx.vortex_diag(state)
+    ctx.timing(2)
+    ctx.advance(B.NONLIN_VORTEX, [0.0], state, prev, 2, False)
+    kt = ctx.timing_read()
+    ctx.timing(0)
+    tot = sum(v[1] for v in kt.values())
+    out = {"workload": "production_256^3_corot_qvortex_nyquist_chop",
+           "precision": {B.BF16X3: "bf16x3", B.FP64: "fp64"}.get(prec),
+           "M": ctx.M, "Kz": ctx.Kz, "coefficients_per_potential": ctx.n_spec, "steps": steps, "dt": dt,
+           "c_psi": cs[0], "c_chi": cs[1],
+           "s_per_30_steps": ms / 1000.0 * 30.0 / steps, "ms_per_step": ms / steps, "setup_s": setup_s,
+           "finite": ok, "enstrophy_t0": z0["enstrophy"], "enstrophy_t_end": z1["enstrophy"],
+           "filter": ctx.filter_state(),
+           "kernel_share": {k: round(v[1] / tot, 3) for k, v in kt.items()},
+           "paper_table3_s_per_30_steps": {"16_ranks": 410.1, "512_ranks": 30.4}}
+    ctx.close()
+    return out
+
+
 def measure_vortex_long(B, W, torch, dev, stream, steps=2000, prec=None):
     """Boundedness of the 256^3 vortex pair (the benchmarked configuration) over
     `steps` AB-CN steps at dt = 2.5e-4 (t = 0.5 for 2000 steps): spectral l2 norms of
@@ -371,8 +425,8 @@ def measure_vortex_long(B, W, torch, dev, stream, steps=2000, prec=None):
             "wall_s": wall, "history": hist}
 
 
-def measure_crow(B, W, torch, dev, stream, t_end=60.0, dt=5e-3, nr=176, nphi=128, nz=64, ell=2.0, nu_h=5e-8,
-                 prec=None, every=0.5):
+def measure_crow(B, W, torch, dev, stream, t_end=60.0, dt=5e-3, grid="176x128x64", ell=2.0, nu_h=5e-8,
+                 prec=None, every=0.5, amp_b=0.002):
     """Crow instability of the counter-rotating pair (Sec. 5.3): b = 4, Lamb-Oseen
     cores a = 0.5 (a / b = 0.125), Gamma = 2 pi, Lz = 8.6 b (one Crow wavelength),
     nu = 1e-4, p = 8 hyperviscosity nu_h = 5e-8, cores displaced by 0.002 b along z
@@ -384,6 +438,7 @@ def measure_crow(B, W, torch, dev, stream, t_end=60.0, dt=5e-3, nr=176, nphi=128
     import math as _m
     from paper_2609_18026_b300 import analysis as AN
     prec = B.BF16X3 if prec is None else prec
+    nr, nphi, nz = (int(v) for v in grid.split("x"))
     b, a, gam = 4.0, 0.5, 2.0 * _m.pi
     lz = 8.6 * b
     U0 = -gam / (2.0 * _m.pi * b)
@@ -394,7 +449,7 @@ def measure_crow(B, W, torch, dev, stream, t_end=60.0, dt=5e-3, nr=176, nphi=128
     phi = 2 * _m.pi * np.arange(nphi) / nphi
     zz = lz * np.arange(nz) / nz
     wz = W.vortex_pair_omega(r[None, None, :], phi[None, :, None], zz[:, None, None], lz=lz, b=b, a=a,
-                             gamma=gam, amp=0.002 * b, incl_deg=48.0, kseed=1)
+                             gamma=gam, amp=amp_b * b, incl_deg=48.0, kseed=1)
     ws = ctx.forward(torch.as_tensor(wz, dtype=ctx.phys_dtype, device=dev), ctx.new_spec())
     psi = ctx.lap_h_solve(-ws, ctx.new_spec())
     state = torch.zeros(2 * ctx.n_spec, dtype=torch.complex128, device=dev)
@@ -402,9 +457,11 @@ def measure_crow(B, W, torch, dev, stream, t_end=60.0, dt=5e-3, nr=176, nphi=128
     prev = torch.zeros_like(state)
     chunk = max(1, int(round(every / dt)))
     nsteps = int(round(t_end / dt))
-    ts, E1, E2, E0 = [0.0], [], [], []
+    ts, E1, E2, E0, Z, WM = [0.0], [], [], [], [], []
     e = ctx.axial_energy(state)
     E0.append(e[0]); E1.append(e[1]); E2.append(e[2] if len(e) > 2 else 0.0)
+    d = ctx.vortex_diag(state)
+    Z.append(d["enstrophy"]); WM.append(d["peak_vorticity"])
     done = 0
     t0 = time.perf_counter()
     status = "ok"
@@ -414,6 +471,8 @@ def measure_crow(B, W, torch, dev, stream, t_end=60.0, dt=5e-3, nr=176, nphi=128
         done += k
         e = ctx.axial_energy(state)
         ts.append(done * dt); E0.append(e[0]); E1.append(e[1]); E2.append(e[2] if len(e) > 2 else 0.0)
+        d = ctx.vortex_diag(state)
+        Z.append(d["enstrophy"]); WM.append(d["peak_vorticity"])
         if not all(_m.isfinite(v) for v in e):
             status = "non-finite at t = %.3f" % (done * dt)
             break
@@ -424,14 +483,101 @@ def measure_crow(B, W, torch, dev, stream, t_end=60.0, dt=5e-3, nr=176, nphi=128
     except B.MlxError as exc:
         status = str(exc)
     beta = 2.0 * _m.pi * b / lz
+    # the initial enstrophy of the large-amplitude run of the paper's snapshots
+    # (the same pair seeded with a 0.15 b displacement; the paper's history starts at 867)
+    wz15 = W.vortex_pair_omega(r[None, None, :], phi[None, :, None], zz[:, None, None], lz=lz, b=b, a=a,
+                               gamma=gam, amp=0.15 * b, incl_deg=48.0, kseed=1)
+    ws15 = ctx.forward(torch.as_tensor(wz15, dtype=ctx.phys_dtype, device=dev), ctx.new_spec())
+    st15 = torch.zeros_like(state)
+    st15[:ctx.n_spec] = ctx.lap_h_solve(-ws15, ctx.new_spec())
+    z15 = ctx.vortex_diag(st15)["enstrophy"]
+    del wz15, ws15, st15
     out = {"workload": "crow_pair_%dx%dx%d" % (nr, nphi, nz), "precision": {B.BF16X3: "bf16x3", B.FP64: "fp64"}.get(prec),
-           "ell": ell, "dt": dt, "nu_h": nu_h, "steps": done, "t_end": done * dt, "wall_s": wall, "status": status,
+           "seed_amplitude_over_b": amp_b, "ell": ell, "dt": dt, "nu_h": nu_h, "steps": done, "t_end": done * dt, "wall_s": wall, "status": status,
            "alpha_10_18": AN.growth_rate(ts, E1, b, gam, (10.0, 18.0)),
            "alpha_33_60": AN.growth_rate(ts, E1, b, gam, (33.0, 60.0)),
            "alpha_theory": AN.crow_alpha(beta, a / b), "beta": beta,
-           "paper": {"alpha_plateau_33_60": 0.8197, "alpha_theory": 0.798},
-           "history": {"t": ts[::4], "E0": E0[::4], "E1": E1[::4], "E2": E2[::4]}}
+           "enstrophy_t0": Z[0], "peak_vorticity_drop_0_60": 1.0 - WM[-1] / WM[0],
+           "enstrophy_t0_seed_0.15b": z15,
+           "paper": {"alpha_plateau_33_60": 0.8197, "alpha_theory": 0.798, "enstrophy_t0_seed_0.15b": 867.0,
+                     "peak_vorticity_drop_0_60_nu_h_5e-8": 0.314, "peak_vorticity_drop_0_60_nu_h_5e-7": 0.499},
+           "history": {"t": ts[::4], "E0": E0[::4], "E1": E1[::4], "E2": E2[::4], "Z": Z[::4], "w_max": WM[::4]}}
     ctx.close()
+    return out
+
+
+def _qvortex_setup(B, W, torch, dev, n, ell, lz, prec, policy, dt, nu=1e-4, nu_h=5e-7, Uz=-0.5, amp=1e-10):
+    """Context and initial state (psi, chi) of the co-rotating q-vortex pair of
+    Sec. 5.3 (b = 4, q = 1, U_z = -0.5): omega_z and v_z at the nodes, forward
+    transforms, and the inverse Laplacians with the log-proxy amplitudes solved for
+    (net circulation 4 pi: c_psi = -1; net axial flux 2 pi: c_chi = -1/2)."""
+    import math as _m
+    nr, nphi, nz = n
+    ctx = B.Context(nr, nphi, nz, ell, lz=lz, precision=prec, chop_policy=policy)
+    ctx.vortex_setup()
+    ctx.implicit_setup(nu, dt, nu_h=nu_h, p=8)
+    ctx.filter_setup()
+    x, w, r = ctx.nodes()
+    phi = 2 * _m.pi * np.arange(nphi) / nphi
+    zz = lz * np.arange(nz) / nz
+    wz, vz = W.q_vortex_pair(r[None, None, :], phi[None, :, None], zz[:, None, None], lz=lz, amp=amp)
+    state = torch.zeros(2 * ctx.n_spec, dtype=torch.complex128, device=dev)
+    cs = []
+    for f, sl in ((wz, slice(0, ctx.n_spec)), (vz, slice(ctx.n_spec, 2 * ctx.n_spec))):
+        s = ctx.forward(torch.as_tensor(f, dtype=ctx.phys_dtype, device=dev), ctx.new_spec())
+        out, c = ctx.lap_h_solve_log(-s, ctx.new_spec(), B.LOGPROXY_SOLVE)
+        state[sl] = out
+        cs.append(c)
+    ctx.vortex_logproxy(cs[0], cs[1], Uz)
+    return ctx, state, cs
+
+
+def measure_corot(B, W, torch, dev, stream, prec=None, t_end=10.0, every=0.5):
+    """Resolution ladder of the co-rotating q-vortex pair (Sec. 5.3, Fig. corot):
+    ell = 4, Lz = 2 pi, nu = 1e-4 (Gamma / nu = 6.3e4), p = 8 hyperviscosity
+    nu_h = 5e-7, the adaptive filter, dt = 1e-2 (the time step and dissipation of
+    the paper's benchmark of this flow; the ladder's own are not stated), two-thirds
+    chops.  Enstrophy at t = 10 on each grid and its difference from the finest
+    rung at half the time step (the paper's reference), beside the paper's
+    62.5397 from a 200 x 128 x 128 run."""
+    import math as _m
+    prec = B.FP64 if prec is None else prec
+    lz = 2.0 * _m.pi
+    rungs = [((64, 32, 32), 1e-2), ((128, 64, 64), 1e-2), ((128, 64, 64), 5e-3), ((200, 128, 128), 1e-2)]
+    out = {"workload": "corot_qvortex_ladder", "precision": {B.BF16X3: "bf16x3", B.FP64: "fp64"}.get(prec),
+           "t_end": t_end, "paper": {"Z_t10_200x128x128": 62.5397,
+                                      "rel_diff_t10": {"64x32x32": 9.9e-4, "96x48x48": 1.9e-5, "128x64x64": 1.2e-5}},
+           "runs": []}
+    for n, dt in rungs:
+        t0 = time.perf_counter()
+        ctx, state, cs = _qvortex_setup(B, W, torch, dev, n, 4.0, lz, prec, B.CHOP_TWOTHIRDS, dt)
+        prev = torch.zeros_like(state)
+        nsteps = int(round(t_end / dt))
+        chunk = max(1, int(round(every / dt)))
+        d = ctx.vortex_diag(state)
+        hist = {"t": [0.0], "Z": [d["enstrophy"]], "w_max": [d["peak_vorticity"]]}
+        done, status = 0, "ok"
+        while done < nsteps:
+            k = min(chunk, nsteps - done)
+            ctx.advance(B.NONLIN_VORTEX, [0.0], state, prev, k, done == 0)
+            done += k
+            d = ctx.vortex_diag(state)
+            hist["t"].append(done * dt); hist["Z"].append(d["enstrophy"]); hist["w_max"].append(d["peak_vorticity"])
+            if not _m.isfinite(d["enstrophy"]):
+                status = "non-finite at t = %.3f" % (done * dt)
+                break
+        try:
+            ctx.device_status()
+        except B.MlxError as exc:
+            status = str(exc)
+        out["runs"].append({"grid": "%dx%dx%d" % n, "dt": dt, "c_psi": cs[0], "c_chi": cs[1], "status": status,
+                            "wall_s": time.perf_counter() - t0, "Z_t_end": hist["Z"][-1],
+                            "filter": ctx.filter_state(), "history": hist})
+        ctx.close()
+        del state, prev
+    ref = [r for r in out["runs"] if r["grid"] == "128x64x64" and r["dt"] == 5e-3][0]["Z_t_end"]
+    for r in out["runs"]:
+        r["rel_diff_vs_128x64x64_half_dt"] = abs(r["Z_t_end"] - ref) / abs(ref)
     return out
 
 
@@ -881,7 +1027,8 @@ def main():
     ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "fp32", "fp64"],
                     help="transform arithmetic of the timed form (the FP64 form is always timed beside it)")
     ap.add_argument("--profile-workload", default=None,
-                    choices=["vortex", "vortex_long", "crow", "batch", "surrogate", "surrogate_step"],
+                    choices=["vortex", "vortex_long", "production", "production_fp64", "corot", "crow", "batch",
+                             "surrogate", "surrogate_step"],
                     help="run only that secondary workload and print its measurement (for profiler captures; "
                          "not the benchmark line)")
     args = ap.parse_args()
@@ -896,8 +1043,15 @@ def main():
         stream = torch.cuda.current_stream()
         fn = {"vortex": lambda: measure_vortex(B, W, torch, dev, stream, with_errors=False),
               "vortex_long": lambda: measure_vortex_long(B, W, torch, dev, stream),
+              "production": lambda: measure_production(B, W, torch, dev, stream),
+              "corot": lambda: measure_corot(B, W, torch, dev, stream),
+              "production_fp64": lambda: measure_production(B, W, torch, dev, stream, prec=B.FP64),
               "crow": lambda: measure_crow(B, W, torch, dev, stream, dt=float(os.environ.get("MLX_CROW_DT", "5e-3")),
-                                           ell=float(os.environ.get("MLX_CROW_ELL", "2.0"))),
+                                           ell=float(os.environ.get("MLX_CROW_ELL", "2.0")),
+                                           nu_h=float(os.environ.get("MLX_CROW_NUH", "5e-8")),
+                                           amp_b=float(os.environ.get("MLX_CROW_AMP", "0.002")),
+                                           grid=os.environ.get("MLX_CROW_GRID", "176x128x64"),
+                                           t_end=float(os.environ.get("MLX_CROW_TEND", "60"))),
               "batch": lambda: measure_batch(B, W, torch, dev, stream, tune_cache=args.tune_cache),
               "surrogate": lambda: measure_surrogate(torch),
               "surrogate_step": lambda: measure_surrogate_step()}[args.profile_workload]

@@ -66,8 +66,15 @@ enum { MLX_FP64 = 0, MLX_FP32 = 1, MLX_BF16X3 = 2 };
 /* Chop policy used when the corresponding chop in mlx_params is 0.
  * LINEAR: M = Nphi/2, Kz = max(1, Nz/2) (Nyquist dropped).
  * TWOTHIRDS: M = (Nphi-1)/3 + 1, Kz = (Nz-1)/3 + 1 -- the two-thirds mask of
- * Sec. 3.3 realised as storage truncation.  Nc = Nr unless nr_c is given. */
-enum { MLX_CHOP_LINEAR = 0, MLX_CHOP_TWOTHIRDS = 1 };
+ * Sec. 3.3 realised as storage truncation.
+ * NYQUIST: M = Nphi/2 + 1, Kz = Nz/2 + 1 (1 if Nz = 1): |m| <= Nphi/2 and
+ * |k| <= Nz/2, the layout of the 256^3 production run of Sec. 4.2 (|m| <= 128,
+ * |k| <= 128).  The members of each Nyquist pair (m = +-Nphi/2; the stored rows
+ * k = +Nz/2 and k = -Nz/2) multiply the same grid function, so the forward
+ * transform gives each half of the grid's bin and the backward transform sums
+ * them.  The m = Nphi/2 block is Hermitian in k after a forward transform.
+ * Nc = Nr unless nr_c is given. */
+enum { MLX_CHOP_LINEAR = 0, MLX_CHOP_TWOTHIRDS = 1, MLX_CHOP_NYQUIST = 2 };
 
 /* Nonlinear term kinds for mlx_nonlinear / mlx_advance.
  *   MLX_NONLIN_FKPP:   one scalar, A = gamma u (1 - u) (Eq. (17)); coeffs[0] = gamma.
@@ -85,12 +92,12 @@ typedef struct {
   int nr, nphi, nz;          /* collocation counts: 2 <= Nr <= 1024; Nphi a power of
                                 two in [4, 512]; Nz 1 or a power of two <= 512       */
   int nr_c, nphi_c, nz_c;    /* chops Nc, M, Kz (0 = from chop_policy); bounds of
-                                Sec. 3.1: Nc <= Nr, M <= Nphi/2, Kz <= Nz/2 (1 if Nz=1),
-                                and M <= Nc                                           */
+                                Sec. 3.1: Nc <= Nr, M <= Nphi/2 + 1, Kz <= Nz/2 + 1
+                                (1 if Nz=1), and M <= Nc                              */
   double ell;                /* map scale ell > 0, Eq. (1)                            */
   double lz;                 /* axial period Lz > 0 (kappa_k = 2 pi k / Lz)           */
   int precision;             /* MLX_FP64 | MLX_FP32 | MLX_BF16X3                      */
-  int chop_policy;           /* MLX_CHOP_LINEAR | MLX_CHOP_TWOTHIRDS                  */
+  int chop_policy;           /* MLX_CHOP_LINEAR | MLX_CHOP_TWOTHIRDS | MLX_CHOP_NYQUIST */
 } mlx_params;
 
 typedef struct {
@@ -168,8 +175,10 @@ int mlx_backward(mlx_ctx* ctx, const void* spec, void* phys, mlx_stream stream);
  *     This equals psi_N = -lap_h^{-1} (curl N)_z, chi_N = -lap_h^{-1} (N_z -
  *     i kappa g) of Eq. (9) up to the truncation of the products.  At m = 0 the
  *     singular first row of Q and (I - J) Q is the far-field decay condition
- *     sum_n Pbar_n^0(1) s_n = 0 (zero net circulation, log-proxy coefficient 0,
- *     Sec. 3.1).  coeffs[0] = U0.
+ *     sum_n Pbar_n^0(1) s_n = 0 (for the basis part of the state;
+ *     the log proxies of mlx_vortex_logproxy carry the net circulation and
+ *     flux, Sec. 3.1).  coeffs[0] = U0; the axial background Uz and the proxies'
+ *     velocity and vorticity come from mlx_vortex_logproxy.
  * spec_in, spec_out: device complex128 ragged (may not alias); two fields each
  * for the vortex kind. */
 int mlx_nonlinear(mlx_ctx* ctx, int kind, const double* coeffs, int ncoeffs,
@@ -188,6 +197,11 @@ int mlx_vortex_setup(mlx_ctx* ctx, mlx_stream stream);
  * The velocity comes from the banded r d/dr and D_m as in the vortex term; each
  * harmonic is evaluated on the Gauss nodes with the FP64 basis table (whatever the
  * context's transform precision) under the area element r dr = ell^2 dx / (1 - x)^2.
+ * The sum is the energy of the backward-transformed field on the grid: with the
+ * Nyquist chop the pairs m = +-Nphi/2 and k = +-Nz/2 enter as the grid sees them
+ * (the m = 0 and m = Nphi/2 blocks through their Hermitian part in k; the two rows
+ * k = +-Nz/2 summed into E[Nz/2]).  Only the basis part of the state counts: the
+ * log proxies' swirl (mlx_vortex_logproxy) has unbounded energy.
  * state: device, 2 n_spec complex128; E: host, Kz doubles.  Needs mlx_vortex_setup
  * (MLX_ESTATE); overwrites the vortex term's temporaries; synchronises `stream`. */
 int mlx_axial_energy(mlx_ctx* ctx, const void* state, double* E, mlx_stream stream);
@@ -197,6 +211,49 @@ int mlx_axial_energy(mlx_ctx* ctx, const void* state, double* E, mlx_stream stre
  * equation at m = 0 (rhs's m = 0, n = 0 entries are not used).  FP64, device
  * complex128 ragged buffers (may not alias).  MLX_ESTATE before mlx_vortex_setup. */
 int mlx_lap_h_solve(mlx_ctx* ctx, const void* rhs, void* out, mlx_stream stream);
+
+/* Log proxy of a scalar with a nonzero planar integral (Sec. 3.1, Eq. (6)).  The
+ * decaying basis cannot represent the logarithmic far field of a Poisson solution
+ * whose source integrates to a nonzero value, so a scalar carries one extra real
+ * amplitude c of Lambda = ln(r^2 + ell^2), whose horizontal Laplacian
+ * (4/3 P_0 - 2 P_1 + 2/3 P_2) / ell^2 lies in the basis.  mlx_lap_h_solve_log
+ * inverts grad_h^2 (c Lambda + x) = rhs; only the (m, k) = (0, 0) block differs
+ * from mlx_lap_h_solve:
+ *   MLX_LOGPROXY_PRESCRIBE: *c given: D_0 x = rhs - c lam with the far-field decay
+ *     condition in place of the singular first equation (x -> 0 at infinity);
+ *   MLX_LOGPROXY_SOLVE: c unknown: D_0's first column (zero: a constant has zero
+ *     Laplacian) replaced by lam; the unknown in its place is returned in *c (from
+ *     the real part: the (0, 0) block of a real field is real), and x's Pbar_0^0
+ *     coefficient is 0.
+ * The two results differ only in that constant coefficient.  FP64, device
+ * complex128 ragged buffers (may not alias); *c is a host double.  The solve
+ * variant synchronises `stream`.  MLX_ESTATE before mlx_vortex_setup. */
+enum { MLX_LOGPROXY_PRESCRIBE = 0, MLX_LOGPROXY_SOLVE = 1 };
+int mlx_lap_h_solve_log(mlx_ctx* ctx, const void* rhs, void* out, int variant, double* c, mlx_stream stream);
+
+/* Log-proxy amplitudes of the vortex state and its axial background: psi carries
+ * c_psi Lambda, chi carries c_chi Lambda (net circulation -4 pi c_psi, net axial
+ * flux -4 pi c_chi), and the background becomes U = U0 e_y + Uz e_z (U0 = the
+ * vortex kind's coeffs[0]).  The amplitudes are constants of the motion: the
+ * vortex term (mlx_nonlinear) adds the proxies' velocity and vorticity to the
+ * (0, 0) blocks of its fields, and the time steps (mlx_advance, the batch) add the
+ * proxies' dissipation c L Lambda (Eq. (11) at (m, k) = (0, 0)) to the (0, 0)
+ * blocks of each field's tendency.  Zero amplitudes and Uz = 0 give the default
+ * vortex term.  Needs mlx_vortex_setup (MLX_ESTATE); drops the cached step graphs;
+ * synchronises `stream`. */
+int mlx_vortex_logproxy(mlx_ctx* ctx, double c_psi, double c_chi, double Uz, mlx_stream stream);
+
+/* Enstrophy Z = (1/2) int |omega|^2 dV over one axial period and the largest |omega|
+ * over the nodes, of a two-field vortex state with its log proxies: the vorticity
+ * fields of the vortex term, backward transforms in the context's precision, the
+ * mapped area rule r dr = ell^2 dx / (1 - x)^2 and the uniform phi and z rules.
+ * state: device, 2 n_spec complex128; out: host.  Needs mlx_vortex_setup
+ * (MLX_ESTATE); overwrites the vortex term's temporaries; synchronises `stream`. */
+typedef struct {
+  double enstrophy;
+  double peak_vorticity;
+} mlx_vortex_diag_out;
+int mlx_vortex_diag(mlx_ctx* ctx, const void* state, mlx_vortex_diag_out* out, mlx_stream stream);
 
 /* Set up the implicit operators for time step dt: per harmonic (m, |k|) the
  * band matrix of L = nu (D_m - kappa^2) - nu_h (-(D_m - kappa^2))^{p/2}
@@ -275,13 +332,15 @@ int mlx_diag(mlx_ctx* ctx, const void* spec, mlx_diag_out* out, mlx_stream strea
 /* Checkpoint images of a time-stepping state (no counterpart in the paper's
  * equations; its runs restart from saved fields).  An image is a host buffer of
  * mlx_state_bytes(ctx, kind) bytes: a header (grid, chops, ell, Lz, the implicit
- * setup nu, nu_h, p, dt, the caller's step counter) followed by the state and
+ * setup nu, nu_h, p, dt, the caller's step counter; for the vortex kind the
+ * log-proxy amplitudes and axial background of mlx_vortex_logproxy) followed by the state and
  * A^{j-1} (complex128 ragged, one or two fields by kind).  mlx_get_state copies the
  * device buffers state and prev_A into `host` (caller-owned, at least that many
  * bytes); mlx_set_state checks the header against this context and copies back into
  * the device buffers, returning the step counter in *step (may be NULL).  A
  * mismatched grid, chop, ell, Lz or field count, or (when both the image and the
- * context have an implicit setup) another dt, nu, nu_h or p, is MLX_EINVAL with the
+ * context have an implicit setup) another dt, nu, nu_h or p, or (vortex kind) other
+ * log-proxy amplitudes or axial background, is MLX_EINVAL with the
  * reason in mlx_last_cuda_error: A^{j-1} continues the AB-CN recurrence (Eq. (12))
  * only under the same operator and step.  Both synchronise `stream`.  Resuming
  * with mlx_advance(..., start = 0) reproduces the uninterrupted run bitwise.

@@ -8,7 +8,11 @@
   0..Kz-1, -(Kz-1)..-1 (K = 2 Kz - 1 stored wavenumbers), n = m..Nc-1.
   Policies: "linear" keeps M = Nphi/2, Kz = max(1, Nz/2) (Nyquist dropped);
   "twothirds" keeps M = (Nphi-1)//3 + 1, Kz = (Nz-1)//3 + 1 (the two-thirds
-  mask of Sec. 3.3 realised as storage truncation); Nc = Nr unless given.
+  mask of Sec. 3.3 realised as storage truncation); "nyquist" keeps
+  |m| <= Nphi/2 and |k| <= Nz/2 (M = Nphi/2 + 1, Kz = Nz/2 + 1, or 1 when
+  Nz = 1), the |m| <= 128, |k| <= 128 layout of the 256^3 production run of
+  Sec. 4.2; Nc = Nr unless given.  With the Nyquist kept, the pairs m = +-Nphi/2
+  and k = +-Nz/2 coincide on the grid; see transform.py for how they are split.
 
 Pins: numpy.polynomial.legendre.leggauss, exact integration of x^k, half the
 nodes inside r < ell (Sec. 3.1), outermost node 20.36 ell at Nr = 24 (Sec. 1).
@@ -64,6 +68,9 @@ def chops(nphi, nz, policy):
     elif policy == "twothirds":
         M = (nphi - 1) // 3 + 1
         Kz = (nz - 1) // 3 + 1
+    elif policy == "nyquist":
+        M = nphi // 2 + 1
+        Kz = nz // 2 + 1 if nz > 1 else 1
     else:
         raise ValueError(policy)
     return M, Kz

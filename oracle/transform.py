@@ -9,6 +9,13 @@ the m = 0 sum is taken).
 Forward (physical -> spectral): the naive DFTs with 1/Nphi and 1/Nz, then Gauss
 quadrature against the orthonormal basis:
     shat_nmk = sum_i w_i Pbar_n^m(x_i) f_mk(r_i).
+When the chop keeps the Nyquist index (|m| = Nphi/2, or |k| = Nz/2), the two
+members of the pair (+N/2, -N/2) multiply the same grid function (-1)^j, so the
+grid fixes only their sum.  The paper does not say how the sum is shared; the
+reading taken is the minimum-norm one, equal halves: the Nyquist DFT row carries
+a factor 1/2 in the forward direction, and the backward direction is Eq. (2)
+summed over both members as written (the m = Nphi/2 term enters with the factor
+2 of every m >= 1, the rows k = +Nz/2 and k = -Nz/2 are both summed).
 The DFTs are explicit matrices with phases 2 pi ((j m) mod N) / N (integer-reduced
 angle), applied with a library matmul.  The radial step is the dense triangular
 quadrature per m (the paper's Sec. 4.1 calls it a banded product along r; only
@@ -58,8 +65,12 @@ def forward(g, phys):
     phys = np.asarray(phys, dtype=np.float64)
     assert phys.shape == (g.nz, g.nphi, g.nr)
     Ephi = _dft_matrix(np.arange(g.M), g.nphi, -1.0) / g.nphi       # [M][Nphi]
+    if g.nphi >= 2 and g.M - 1 == g.nphi // 2:
+        Ephi[g.M - 1] *= 0.5                                           # m = +-Nphi/2 halves
     f1 = np.einsum("mj,zji->zmi", Ephi, phys)                         # [Nz][M][Nr]
     Ez = _dft_matrix(g.kz, g.nz, -1.0) / g.nz                          # [K][Nz]
+    if g.nz > 1:
+        Ez[np.abs(g.kz) == g.nz // 2] *= 0.5                           # k = +-Nz/2 halves
     f2 = np.einsum("kz,zmi->kmi", Ez, f1)                              # [K][M][Nr]
     out = []
     for m in range(g.M):

@@ -78,6 +78,7 @@ import math
 import numpy as np
 import scipy.linalg as sla
 
+from . import logproxy
 from .operators import del2h_closed, rdr_matrix
 from .transform import backward, forward, serial
 
@@ -207,16 +208,27 @@ class VortexOps:
         return g.r[None, None, :], g.phi[None, :, None]
 
     # ---------------- the oracle's definition: project_plain (13 transforms)
-    def products_plain(self, psi, chi, U0=0.0):
-        """Spectral (A, B, Nz) = (r N_phi, r N_r, N_z) of N = (U + v) x omega,
-        formed from the primitive components at the nodes (steps 1-2 above)."""
+    def primitive_fields(self, psi, chi, cpsi=0.0, cchi=0.0):
+        """(v_r, v_phi, v_z, w_r, w_phi, w_z) at the nodes: six backward transforms
+        of the spectral fields, the division by r at the nodes, and the velocity and
+        vorticity of the log proxies c_psi Lambda, c_chi Lambda in closed form."""
         g = self.g
         rvr, rvp, vz, rwr, rwp, wz = (backward(g, f) for f in self.fields(psi, chi))
+        r, _ = self._nodes()
+        lp = logproxy.node_fields(r, g.ell, cpsi, cchi)
+        return (rvr / r, rvp / r + lp["v_phi"], vz + lp["v_z"],
+                rwr / r, rwp / r + lp["w_phi"], wz + lp["w_z"])
+
+    def products_plain(self, psi, chi, U0=0.0, Uz=0.0, cpsi=0.0, cchi=0.0):
+        """Spectral (A, B, Nz) = (r N_phi, r N_r, N_z) of N = (U + v) x omega with
+        U = U0 e_y + Uz e_z, formed from the primitive components at the nodes
+        (steps 1-2 above)."""
+        g = self.g
+        vr, vp, vz, wr, wp, wz = self.primitive_fields(psi, chi, cpsi, cchi)
         r, phi = self._nodes()
-        vr = rvr / r + U0 * np.sin(phi)        # v_r + U_r
-        vp = rvp / r + U0 * np.cos(phi)        # v_phi + U_phi
-        wr = rwr / r
-        wp = rwp / r
+        vr = vr + U0 * np.sin(phi)             # v_r + U_r
+        vp = vp + U0 * np.cos(phi)             # v_phi + U_phi
+        vz = vz + Uz                           # v_z + U_z
         Nr = vp * wz - vz * wp
         Np = vz * wr - vr * wz
         Nz = vr * wp - vp * wr
@@ -258,16 +270,22 @@ class VortexOps:
             chiN.append(cb)
         return psiN, chiN
 
-    def nonlinear_plain(self, psi, chi, U0=0.0):
-        return self.project_plain(*self.products_plain(psi, chi, U0))
+    def nonlinear_plain(self, psi, chi, U0=0.0, Uz=0.0, cpsi=0.0, cchi=0.0):
+        return self.project_plain(*self.products_plain(psi, chi, U0, Uz, cpsi, cchi))
 
     # ---------------- the second form: project_banded (9 transforms)
-    def products_banded(self, psi, chi, U0=0.0):
+    def products_banded(self, psi, chi, U0=0.0, Uz=0.0, cpsi=0.0, cchi=0.0):
         """Spectral (A, B, C) = (r N_phi, r N_r, r^2 N_z) of N = (U + v) x omega,
-        formed from the r-weighted fields without division by r."""
+        formed from the r-weighted fields without division by r (the proxies'
+        r-weighted fields in closed form at the nodes)."""
         g = self.g
         rvr, rvp, vz, rwr, rwp, wz = (backward(g, f) for f in self.fields(psi, chi))
         r, phi = self._nodes()
+        lp = logproxy.node_fields(r, g.ell, cpsi, cchi)
+        rvp = rvp + r * lp["v_phi"]
+        vz = vz + lp["v_z"] + Uz
+        rwp = rwp + r * lp["w_phi"]
+        wz = wz + lp["w_z"]
         ar = rvr + r * U0 * np.sin(phi)       # r (v_r + U_r)
         ap = rvp + r * U0 * np.cos(phi)       # r (v_phi + U_phi)
         A = vz * rwr - ar * wz
@@ -304,28 +322,55 @@ class VortexOps:
             chiN.append(cb)
         return psiN, chiN
 
-    def nonlinear_banded(self, psi, chi, U0=0.0):
-        return self.project_banded(*self.products_banded(psi, chi, U0))
+    def nonlinear_banded(self, psi, chi, U0=0.0, Uz=0.0, cpsi=0.0, cchi=0.0):
+        return self.project_banded(*self.products_banded(psi, chi, U0, Uz, cpsi, cchi))
 
-    def nonlinear(self, psi, chi, U0=0.0, form="plain"):
-        """P[(U + v) x omega] for the state (psi, chi); form "plain" (the
+    def nonlinear(self, psi, chi, U0=0.0, form="plain", Uz=0.0, cpsi=0.0, cchi=0.0):
+        """P[(U + v) x omega] for the state (psi, chi) with log-proxy amplitudes
+        (cpsi, cchi) and background U = U0 e_y + Uz e_z; form "plain" (the
         definition) or "banded"."""
         if form == "plain":
-            return self.nonlinear_plain(psi, chi, U0)
+            return self.nonlinear_plain(psi, chi, U0, Uz, cpsi, cchi)
         if form == "banded":
-            return self.nonlinear_banded(psi, chi, U0)
+            return self.nonlinear_banded(psi, chi, U0, Uz, cpsi, cchi)
         raise ValueError(form)
 
 
-def vortex_nonlinear(g, U0=0.0, form="plain"):
-    """Nonlinear term for a two-field state [psi blocks..., chi blocks...] (2M blocks)."""
+def vortex_nonlinear(g, U0=0.0, form="plain", Uz=0.0, cpsi=0.0, cchi=0.0, source=None):
+    """Nonlinear term for a two-field state [psi blocks..., chi blocks...] (2M blocks).
+
+    With log proxies, source = (nu, nu_h, p) adds the proxies' constant forcing
+    (cpsi, cchi) L Lambda to the (m, k) = (0, 0) blocks, so that a Stepper built
+    with this term advances (psi, chi) with c Lambda included (see logproxy.py)."""
     ops = VortexOps(g)
+    src = None
+    if source is not None and (cpsi != 0.0 or cchi != 0.0):
+        lam = logproxy.image(g.nc, g.ell)
+        src = logproxy.source(ops.D[0], lam, *source)
 
     def A(state):
         psi, chi = state[:g.M], state[g.M:]
-        pN, cN = ops.nonlinear(psi, chi, U0, form)
+        pN, cN = ops.nonlinear(psi, chi, U0, form, Uz, cpsi, cchi)
+        if src is not None:
+            pN[0] = pN[0].copy()
+            cN[0] = cN[0].copy()
+            pN[0][0] += cpsi * src
+            cN[0][0] += cchi * src
         return pN + cN
     return A, ops
+
+
+def enstrophy(g, ops, psi, chi, cpsi=0.0, cchi=0.0):
+    """(Z, w_max): Z = (1/2) int |omega|^2 dV over one axial period and the largest
+    |omega| over the nodes, from the primitive vorticity at the nodes (the proxies'
+    included), the mapped area quadrature r dr = ell^2 dx / (1 - x)^2, the uniform
+    phi and z rules.  The paper reports enstrophy without defining its factor; the
+    reading taken is the one half of the usual definition (Sec. 5.3)."""
+    _, _, _, wr, wp, wz = ops.primitive_fields(psi, chi, cpsi, cchi)
+    w2 = wr * wr + wp * wp + wz * wz
+    a = g.w * g.ell ** 2 / (1.0 - g.x) ** 2
+    Z = 0.5 * (g.lz / g.nz) * (2.0 * math.pi / g.nphi) * float(np.sum(w2 * a[None, None, :]))
+    return Z, float(np.sqrt(np.max(w2)))
 
 
 def axial_energy(g, ops, psi, chi):

@@ -14,7 +14,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libmlx.so")
 
 FP64, FP32, BF16X3 = 0, 1, 2
-CHOP_LINEAR, CHOP_TWOTHIRDS = 0, 1
+CHOP_LINEAR, CHOP_TWOTHIRDS, CHOP_NYQUIST = 0, 1, 2
+LOGPROXY_PRESCRIBE, LOGPROXY_SOLVE = 0, 1
 NONLIN_NONE, NONLIN_FKPP, NONLIN_VORTEX = 0, 1, 2
 STEP_FEBE_HALF, STEP_FEBE_FULL, STEP_ABCN = 0, 1, 2
 
@@ -26,7 +27,8 @@ EXPORTS = ("mlx_strerror", "mlx_last_cuda_error", "mlx_create", "mlx_destroy", "
            "mlx_set_tuning", "mlx_device_status", "mlx_forward_noalloc",
            "mlx_diag", "mlx_state_bytes", "mlx_get_state", "mlx_set_state",
            "mlx_filter_setup", "mlx_filter_apply", "mlx_filter_state", "mlx_axial_energy",
-           "mlx_vortex_setup", "mlx_lap_h_solve",
+           "mlx_vortex_setup", "mlx_lap_h_solve", "mlx_lap_h_solve_log", "mlx_vortex_logproxy",
+           "mlx_vortex_diag",
            "mlx_batch_create", "mlx_batch_destroy", "mlx_batch_advance", "mlx_autotune",
            "mlx_sur_create", "mlx_sur_destroy", "mlx_sur_param_count", "mlx_sur_get_params",
            "mlx_sur_set_params", "mlx_sur_get_grads", "mlx_sur_get_scales", "mlx_sur_set_scales",
@@ -62,6 +64,10 @@ class FilterParams(ctypes.Structure):
 class DiagOut(ctypes.Structure):
     _fields_ = [("integral", ctypes.c_double), ("moment2", ctypes.c_double),
                 ("l2w", ctypes.c_double), ("spec_l2", ctypes.c_double)]
+
+
+class VortexDiagOut(ctypes.Structure):
+    _fields_ = [("enstrophy", ctypes.c_double), ("peak_vorticity", ctypes.c_double)]
 
 
 _lib = None
@@ -108,6 +114,9 @@ def load():
     lib.mlx_set_state.argtypes = [vp, i, vp, ctypes.c_longlong, vp, vp, ctypes.POINTER(ctypes.c_longlong), vp]
     lib.mlx_vortex_setup.argtypes = [vp, vp]
     lib.mlx_lap_h_solve.argtypes = [vp, vp, vp, vp]
+    lib.mlx_lap_h_solve_log.argtypes = [vp, vp, vp, i, ctypes.POINTER(d), vp]
+    lib.mlx_vortex_logproxy.argtypes = [vp, d, d, d, vp]
+    lib.mlx_vortex_diag.argtypes = [vp, vp, ctypes.POINTER(VortexDiagOut), vp]
     lib.mlx_batch_create.argtypes = [ctypes.POINTER(vp), i, ctypes.POINTER(vp)]
     lib.mlx_batch_destroy.argtypes = [vp]
     lib.mlx_batch_advance.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(d), ctypes.POINTER(vp),
@@ -254,6 +263,24 @@ class Context:
     def lap_h_solve(self, rhs, out, stream=None):
         self._check(self.lib.mlx_lap_h_solve(self._h, _ptr(rhs), _ptr(out), _stream(stream)))
         return out
+
+    def lap_h_solve_log(self, rhs, out, variant, c=0.0, stream=None):
+        """mlx_lap_h_solve_log: returns (out, c); c is the input amplitude for
+        LOGPROXY_PRESCRIBE and the solved one for LOGPROXY_SOLVE."""
+        cv = ctypes.c_double(float(c))
+        self._check(self.lib.mlx_lap_h_solve_log(self._h, _ptr(rhs), _ptr(out), int(variant), ctypes.byref(cv),
+                                                 _stream(stream)))
+        return out, cv.value
+
+    def vortex_logproxy(self, c_psi, c_chi, Uz=0.0, stream=None):
+        """Log-proxy amplitudes of (psi, chi) and the axial background (mlx_vortex_logproxy)."""
+        self._check(self.lib.mlx_vortex_logproxy(self._h, float(c_psi), float(c_chi), float(Uz), _stream(stream)))
+
+    def vortex_diag(self, state, stream=None):
+        """dict(enstrophy, peak_vorticity) of a two-field vortex state (mlx_vortex_diag)."""
+        o = VortexDiagOut()
+        self._check(self.lib.mlx_vortex_diag(self._h, _ptr(state), ctypes.byref(o), _stream(stream)))
+        return dict(enstrophy=o.enstrophy, peak_vorticity=o.peak_vorticity)
 
     def diag(self, spec, stream=None):
         """dict(integral, moment2, l2w, spec_l2) of a spectral scalar field (mlx_diag)."""

@@ -32,7 +32,7 @@ void free_ctx(mlx_ctx* c) {
                   c->lu_helm.FS, c->lu_helm.BS, c->lu_Q.FS, c->lu_Q.BS, c->lu_H.FS, c->lu_H.BS,
                   c->lu_G.FS, c->lu_G.BS, c->lu_half.PHf, c->lu_half.PHb, c->lu_half.PSf,
                   c->lu_full.PHf, c->lu_full.PHb, c->lu_full.PSf, c->d_diag,
-                  c->d_bsf, c->d_bsb, c->d_filt};
+                  c->d_bsf, c->d_bsb, c->d_filt, c->d_lp, c->d_enst};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
@@ -54,12 +54,19 @@ int dalloc(mlx_ctx* c, P** p, size_t bytes) {
 
 // Nonlinear term A(s) into A.  Fisher-KPP: A = P[gamma u (1 - u)] with u = B s
 // (B backward, P forward transform), the product formed at the nodes (Sec. 3.3).
-int nonlinear_into(mlx_ctx* c, int kind, double c0, const double2* s, double2* A, cudaStream_t st) {
+// In the time steps (src) the vortex tendency also carries the log proxies' constant
+// forcing c L Lambda in its (0, 0) blocks.
+int nonlinear_into(mlx_ctx* c, int kind, double c0, const double2* s, double2* A, cudaStream_t st,
+                   bool src = true) {
   if (kind == MLX_NONLIN_NONE) {
     MLX_CUDA_TRY(c, cudaMemsetAsync(A, 0, sizeof(double2) * c->n_spec, st));
     return MLX_OK;
   }
-  if (kind == MLX_NONLIN_VORTEX) return mlx_vortex_nonlinear(c, c0, s, A, st);
+  if (kind == MLX_NONLIN_VORTEX) {
+    int rc = mlx_vortex_nonlinear(c, c0, s, A, st);
+    if (rc || !src) return rc;
+    return mlx_lp_add_source(c, A, st);
+  }
   int rc = mlx_legendre_backward(c, s, st);
   if (rc) return rc;
   rc = mlx_fft_fkpp(c, c0, st);
@@ -128,21 +135,25 @@ int mlx_create(const mlx_params* p, mlx_stream stream, mlx_ctx** out) {
   if (!(p->nz == 1 || (is_pow2(p->nz) && p->nz <= 512))) return MLX_EINVAL;
   if (!(p->ell > 0.0) || !(p->lz > 0.0)) return MLX_EINVAL;
   if (p->precision != MLX_FP64 && p->precision != MLX_FP32 && p->precision != MLX_BF16X3) return MLX_EINVAL;
-  if (p->chop_policy != MLX_CHOP_LINEAR && p->chop_policy != MLX_CHOP_TWOTHIRDS) return MLX_EINVAL;
+  if (p->chop_policy != MLX_CHOP_LINEAR && p->chop_policy != MLX_CHOP_TWOTHIRDS &&
+      p->chop_policy != MLX_CHOP_NYQUIST) return MLX_EINVAL;
   if (p->nr_c < 0 || p->nphi_c < 0 || p->nz_c < 0) return MLX_EINVAL;
   int nc = p->nr_c ? p->nr_c : p->nr;
   int M, Kz;
   if (p->chop_policy == MLX_CHOP_LINEAR) {
     M = p->nphi / 2;
     Kz = p->nz > 1 ? p->nz / 2 : 1;
+  } else if (p->chop_policy == MLX_CHOP_NYQUIST) {
+    M = p->nphi / 2 + 1;
+    Kz = p->nz > 1 ? p->nz / 2 + 1 : 1;
   } else {
     M = (p->nphi - 1) / 3 + 1;
     Kz = (p->nz - 1) / 3 + 1;
   }
   if (p->nphi_c) M = p->nphi_c;
   if (p->nz_c) Kz = p->nz_c;
-  if (nc > p->nr || M > p->nphi / 2 || M > nc || M < 1) return MLX_EINVAL;
-  if (Kz < 1 || (p->nz == 1 && Kz != 1) || (p->nz > 1 && Kz > p->nz / 2)) return MLX_EINVAL;
+  if (nc > p->nr || M > p->nphi / 2 + 1 || M > nc || M < 1) return MLX_EINVAL;
+  if (Kz < 1 || (p->nz == 1 && Kz != 1) || (p->nz > 1 && Kz > p->nz / 2 + 1)) return MLX_EINVAL;
 
   mlx_ctx* c = new mlx_ctx();
   c->nr = p->nr; c->nphi = p->nphi; c->nz = p->nz;
@@ -272,7 +283,7 @@ int mlx_nonlinear(mlx_ctx* c, int kind, const double* coeffs, int ncoeffs, const
   if (kind != MLX_NONLIN_FKPP && kind != MLX_NONLIN_NONE && kind != MLX_NONLIN_VORTEX) return MLX_EINVAL;
   if (kind == MLX_NONLIN_VORTEX && !c->vortex_ready) return MLX_ESTATE;
   return nonlinear_into(c, kind, coeffs ? coeffs[0] : 0.0, (const double2*)spec_in,
-                        (double2*)spec_out, (cudaStream_t)stream);
+                        (double2*)spec_out, (cudaStream_t)stream, false);
 }
 
 int mlx_implicit_setup(mlx_ctx* c, double nu, double nu_h, int p, double dt, mlx_stream stream) {
@@ -292,6 +303,8 @@ int mlx_implicit_setup(mlx_ctx* c, double nu, double nu_h, int p, double dt, mlx
   int rc = mlx_band_setup(c, (cudaStream_t)stream);
   if (rc) return rc;
   c->implicit_ready = true;
+  // the log proxies' forcing c L Lambda depends on the operator
+  if (c->d_lp && (rc = mlx_lp_refresh(c, (cudaStream_t)stream))) return rc;
   return MLX_OK;
 }
 

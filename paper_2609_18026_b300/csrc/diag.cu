@@ -105,12 +105,13 @@ __global__ void k_diag_sum(long long nblocks, double ell, const double* __restri
 
 // checkpoint image header (host side only)
 struct StateHeader {
-  char magic[8];                 // "MLXSTAT1"
+  char magic[8];                 // "MLXSTAT2"
   int nr, nphi, nz, nc, M, Kz, nfields, p;
   double ell, lz, nu, nu_h, dt;
   long long step;
   long long n_spec;
   int implicit_ready, pad;
+  double lp_cpsi, lp_cchi, vortex_uz;   // log-proxy amplitudes and axial background (vortex)
 };
 
 int nfields_of(int kind) { return kind == MLX_NONLIN_VORTEX ? 2 : 1; }
@@ -151,7 +152,7 @@ int mlx_get_state(mlx_ctx* c, int kind, const void* state, const void* prev_A, l
   if (need < 0 || !state || !prev_A || !host || bytes < need) return MLX_EINVAL;
   StateHeader hd;
   memset(&hd, 0, sizeof(hd));
-  memcpy(hd.magic, "MLXSTAT1", 8);
+  memcpy(hd.magic, "MLXSTAT2", 8);
   hd.nr = c->nr; hd.nphi = c->nphi; hd.nz = c->nz; hd.nc = c->nc; hd.M = c->M; hd.Kz = c->Kz;
   hd.nfields = nfields_of(kind);
   hd.p = c->p;
@@ -159,6 +160,9 @@ int mlx_get_state(mlx_ctx* c, int kind, const void* state, const void* prev_A, l
   hd.step = step;
   hd.n_spec = c->n_spec;
   hd.implicit_ready = c->implicit_ready ? 1 : 0;
+  if (kind == MLX_NONLIN_VORTEX) {
+    hd.lp_cpsi = c->lp_cpsi; hd.lp_cchi = c->lp_cchi; hd.vortex_uz = c->vortex_uz;
+  }
   memcpy(host, &hd, sizeof(hd));
   const size_t fb = sizeof(double2) * (size_t)hd.nfields * (size_t)c->n_spec;
   unsigned char* dst = static_cast<unsigned char*>(host) + sizeof(hd);
@@ -179,7 +183,7 @@ int mlx_set_state(mlx_ctx* c, int kind, const void* host, long long bytes, void*
     c->last_err = std::string("mlx_set_state: ") + why;
     return MLX_EINVAL;
   };
-  if (memcmp(hd.magic, "MLXSTAT1", 8) != 0) return reject("not a checkpoint image");
+  if (memcmp(hd.magic, "MLXSTAT2", 8) != 0) return reject("not a checkpoint image");
   if (hd.nr != c->nr || hd.nphi != c->nphi || hd.nz != c->nz || hd.nc != c->nc || hd.M != c->M ||
       hd.Kz != c->Kz || hd.n_spec != c->n_spec || hd.ell != c->ell || hd.lz != c->lz)
     return reject("grid, chops, ell or Lz differ from this context");
@@ -188,6 +192,11 @@ int mlx_set_state(mlx_ctx* c, int kind, const void* host, long long bytes, void*
   if (hd.implicit_ready && c->implicit_ready &&
       (hd.dt != c->dt || hd.nu != c->nu || hd.nu_h != c->nu_h || (hd.nu_h > 0.0 && hd.p != c->p)))
     return reject("dt, nu, nu_h or p differ from this context's implicit setup");
+  // the proxy amplitudes are part of a vortex state: set them (mlx_vortex_logproxy)
+  // before restoring it
+  if (kind == MLX_NONLIN_VORTEX &&
+      (hd.lp_cpsi != c->lp_cpsi || hd.lp_cchi != c->lp_cchi || hd.vortex_uz != c->vortex_uz))
+    return reject("the log-proxy amplitudes or the axial background differ from this context's");
   const size_t fb = sizeof(double2) * (size_t)hd.nfields * (size_t)c->n_spec;
   const unsigned char* src = static_cast<const unsigned char*>(host) + sizeof(hd);
   cudaStream_t st = (cudaStream_t)stream;

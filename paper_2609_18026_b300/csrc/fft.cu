@@ -173,6 +173,9 @@ __device__ void phi_unpack_store(const C* L, int ld, int N, int B, int M, int Nr
       re = (zm.y + zc.y) * (T)0.5;
       im = (zc.x - zm.x) * (T)0.5;
     }
+    // Nyquist chop: m = +-N/2 share the grid function (-1)^j, and each stored
+    // member takes half of the (real) bin
+    if (m == (N >> 1)) re *= (T)0.5;
     const int r = r0 + rr;
     if (r < Nr) {
       if (so.bs) {
@@ -245,6 +248,11 @@ __global__ void __launch_bounds__(256) k_phi(int N, int logN, int M, int Nr, int
       if (m == 0) {
         C v; v.x = ar; v.y = br;
         L[b * ld] = v;
+      } else if (m == (N >> 1)) {
+        // Nyquist chop: the m and N - m slots coincide; the bin receives both
+        // members of the pair, A_m + conj(A_m) + i (B_m + conj(B_m))
+        C v; v.x = ar + ar; v.y = br + br;
+        L[b * ld + p1] = v;
       } else {
         C v1; v1.x = ar - bi; v1.y = ai + br;
         C v2; v2.x = ar + bi; v2.y = br - ai;
@@ -326,14 +334,22 @@ __global__ void __launch_bounds__(256) k_z(int Nz, int logN, int Kz, int K, int 
   } else {
     for (int t = threadIdx.x; t < R * ld; t += blockDim.x) L[t] = C{};
     __syncthreads();
+    // Nyquist chop (K = Nz + 1): rows k = +Nz/2 (kk = Kz - 1) and k = -Nz/2
+    // (kk = Kz) feed the same bin, which receives their sum
+    const bool nyq = K == Nz + 1;
 #pragma unroll 8
     for (int t = threadIdx.x; t < K * R; t += blockDim.x) {
       const int kk = t >> lR, b = t & (R - 1);
       const int r = r0 + b;
       const int pos = (kk < Kz) ? kk : Nz - (K - kk);
-      if (r < Nr) {
+      if (r < Nr && !(nyq && kk == Kz)) {
         const long long o = ((long long)kk * M + m) * Nr + r;
         C v; v.x = mre[o]; v.y = mim[o];
+        if (nyq && kk == Kz - 1) {
+          const long long o2 = ((long long)Kz * M + m) * Nr + r;
+          v.x += mre[o2];
+          v.y += mim[o2];
+        }
         L[b * ld + bitrev(pos, logN)] = v;   // bit-reversed input of the DIT below
       }
     }
@@ -357,12 +373,14 @@ __global__ void __launch_bounds__(256) k_z(int Nz, int logN, int Kz, int K, int 
   __syncthreads();
   if (!INVERSE) {
     const T inv = (T)1 / (T)Nz;
+    const bool nyq = K == Nz + 1;     // Nyquist chop: rows k = +-Nz/2 take half the bin each
     for (int t = threadIdx.x; t < K * R; t += blockDim.x) {
       const int kk = t >> lR, b = t & (R - 1);
       const int r = r0 + b;
       const int pos = (kk < Kz) ? kk : Nz - (K - kk);
       if (r < Nr) {
-        const C v = L[b * ld + bitrev(pos, logN)];
+        C v = L[b * ld + bitrev(pos, logN)];
+        if (nyq && (kk == Kz - 1 || kk == Kz)) { v.x *= (T)0.5; v.y *= (T)0.5; }
         if (so.bs) {
           split_store<T>(so, m, kk, 0, r, v.x * inv);
           split_store<T>(so, m, kk, 1, r, v.y * inv);

@@ -155,6 +155,11 @@ struct mlx_ctx {
   void* d_vphys = nullptr;             // 6 physical temporaries
   double* d_setup_scratch = nullptr;
   double* d_diag = nullptr;            // mlx_diag partial sums [M K][4] and result [4]
+  double* d_enst = nullptr;            // mlx_vortex_diag partials [blocks][2] and result [2]
+  // log proxies of the vortex state (Sec. 3.1, Eq. (6)) and the axial background
+  bool lp_on = false;                  // c_psi or c_chi nonzero
+  double lp_cpsi = 0, lp_cchi = 0, vortex_uz = 0;
+  double* d_lp = nullptr;              // proxy tables (field additions, lap_h Lambda, L Lambda, scratch)
   // adaptive modal filter (between steps): per-field [eps, tail] x 2, partials [M K][2],
   // multiplier tables [2][Nc + M + Kz]
   bool filter_on = false;
@@ -259,6 +264,8 @@ int mlx_proj_setup(mlx_ctx* c, cudaStream_t st);
 int mlx_proj_solve(mlx_ctx* c, int family, const double2* rhs, double2* out, cudaStream_t st);
 int mlx_vortex_prepare(mlx_ctx* c, cudaStream_t st);
 int mlx_vortex_nonlinear(mlx_ctx* c, double U0, const double2* state, double2* out, cudaStream_t st);
+int mlx_lp_refresh(mlx_ctx* c, cudaStream_t st);
+int mlx_lp_add_source(mlx_ctx* c, double2* A, cudaStream_t st);
 int mlx_tc_prepare(mlx_ctx* c, cudaStream_t st);
 int mlx_tc_retile(mlx_ctx* c, int bn, cudaStream_t st);
 int mlx_enqueue_step_pair(mlx_ctx* c, int kind, double c0, double2* s, double2* Ap, cudaStream_t st);

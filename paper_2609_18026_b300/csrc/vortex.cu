@@ -14,7 +14,15 @@
 //   [(I - J) Q - kappa^2 ell^2 (I + J)] g = (I - J)(X2 + i kappa C)     (k != 0)
 //   (I - J) Q chi_N = i kappa ell^2 (I + J) g - (I - J) C               (g = 0 at k = 0)
 // with the far-field decay condition replacing the singular first row at m = 0.
+//
+// Log proxies (Sec. 3.1, Eq. (6)): a flow with net circulation or net axial flux
+// carries psi = c_psi Lambda + ..., chi = c_chi Lambda + ... with
+// Lambda = ln(r^2 + ell^2).  The proxies' r-weighted velocity and vorticity are
+// polynomials of degree <= 3 in x at (m, k) = (0, 0) and are added to those blocks
+// of the fields; the background is U = U0 e_y + Uz e_z.
 #include "mlx_internal.cuh"
+
+#include <cmath>
 
 namespace {
 
@@ -61,7 +69,8 @@ __global__ void k_vortex_fields(int nc, int Kz, int K, double lz, const long lon
                                 const double* __restrict__ lap, const double2* __restrict__ psi,
                                 const double2* __restrict__ chi, double2* __restrict__ rvr,
                                 double2* __restrict__ rvp, double2* __restrict__ vz, double2* __restrict__ rwr,
-                                double2* __restrict__ rwp, double2* __restrict__ wz) {
+                                double2* __restrict__ rwp, double2* __restrict__ wz,
+                                const double* __restrict__ lpf) {
   extern __shared__ double2 vsh[];   // [4][nc]: psi, chi, D chi, Psi
   const int kidx = blockIdx.x, m = blockIdx.y;
   const int Nm = nc - m;
@@ -87,17 +96,164 @@ __global__ void k_vortex_fields(int nc, int Kz, int K, double lz, const long lon
     const double2 Rpsi = apply_R(rb, P, a, Nm);
     const double2 Rchi = apply_R(rb, Ch, a, Nm);
     const double2 RPsi = apply_R(rb, Ps, a, Nm);
+    double2 fvp = csub(cmulr(-1.0, Rpsi), cmulr(mm * kap, Ch[a]));
+    double2 fvz = cmulr(-1.0, Dc[a]);
+    double2 fwp = csub(cmulr(-1.0, RPsi), cmulr(mm * kap, P[a]));
+    double2 fwz = cmulr(-1.0, apply_D(db, P, a, Nm));
+    if (lpf && m == 0 && kidx == 0 && a < 4) {   // log proxies: real coefficients, n <= 3
+      fvp.x += lpf[a];
+      fvz.x += lpf[4 + a];
+      fwp.x += lpf[8 + a];
+      fwz.x += lpf[12 + a];
+    }
     rvr[idx] = cadd(cimul(mm, P[a]), cimul(kap, Rchi));
-    rvp[idx] = csub(cmulr(-1.0, Rpsi), cmulr(mm * kap, Ch[a]));
-    vz[idx] = cmulr(-1.0, Dc[a]);
+    rvp[idx] = fvp;
+    vz[idx] = fvz;
     rwr[idx] = cadd(cimul(mm, Ps[a]), cimul(kap, Rpsi));
-    rwp[idx] = csub(cmulr(-1.0, RPsi), cmulr(mm * kap, P[a]));
-    wz[idx] = cmulr(-1.0, apply_D(db, P, a, Nm));
+    rwp[idx] = fwp;
+    wz[idx] = fwz;
   }
 }
 
+// ---- log-proxy tables -----------------------------------------------------------
+// d_lp layout: [16] field additions (r v_phi, v_z, r w_phi, w_z; n = 0..3), [nc] lam =
+// lap_h Lambda, [nc] L Lambda, [2 nc] matvec scratch, [1] c of the last solve, then
+// [7 nc + 2 nc] scratch of the solve-for-c elimination.
+constexpr int kLpFields = 0, kLpLam = 16;
+__host__ __device__ inline long long lp_ll(int nc) { return 16 + (long long)nc; }
+__host__ __device__ inline long long lp_scr(int nc) { return 16 + 2LL * nc; }
+__host__ __device__ inline long long lp_c(int nc) { return 16 + 4LL * nc; }
+__host__ __device__ inline long long lp_elim(int nc) { return 17 + 4LL * nc; }
+__host__ __device__ inline long long lp_size(int nc) { return 17 + 13LL * nc; }
+
+// (D_0 v)_i with the m = 0 Laplacian band (row i, column i + o - 2)
+__device__ double lap0_row(const double* lap0, const double* v, int i, int nc) {
+  double acc = 0.0;
+  for (int o = 0; o < 5; ++o) {
+    const int j = i + o - 2;
+    if (j >= 0 && j < nc) acc = fma(lap0[i * 5 + o], v[j], acc);
+  }
+  return acc;
+}
+
+// One thread.  With N_n = sqrt((2n + 1) / 2) (a Legendre sum a_n P_n has the basis
+// coefficients a_n / N_n) and the expansions
+//   1 + x = P_0 + P_1,  (1 - x)^2 = 4/3 P_0 - 2 P_1 + 2/3 P_2 (Eq. (6)),
+//   (1 - x)(1 - x^2) = 2/3 P_0 - 2/5 P_1 - 2/3 P_2 + 2/5 P_3,
+// the proxies add  r v_phi = -c_psi (1 + x),  w_z = -c_psi (1 - x)^2 / ell^2,
+// v_z = -c_chi (1 - x)^2 / ell^2,  r w_phi = -2 c_chi (1 - x)(1 - x^2) / ell^2, and
+// L Lambda = nu lam - nu_h (-1)^{p/2} D_0^{p/2 - 1} lam  (Eq. (11) at (m, k) = (0, 0)).
+__global__ void k_lp_setup(int nc, double ell, double cpsi, double cchi, double nu, double nu_h, int p,
+                           const double* __restrict__ lap0, double* __restrict__ lp) {
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  const double e2 = ell * ell;
+  const double sq[4] = {sqrt(0.5), sqrt(1.5), sqrt(2.5), sqrt(3.5)};
+  const double onepx[4] = {1.0, 1.0, 0.0, 0.0};
+  const double omx2[4] = {4.0 / 3.0, -2.0, 2.0 / 3.0, 0.0};
+  const double cub[4] = {2.0 / 3.0, -0.4, -2.0 / 3.0, 0.4};
+  for (int n = 0; n < 4; ++n) {
+    const bool in = n < nc;
+    lp[kLpFields + n] = in ? -cpsi * onepx[n] / sq[n] : 0.0;
+    lp[kLpFields + 4 + n] = in ? -cchi * omx2[n] / sq[n] / e2 : 0.0;
+    lp[kLpFields + 8 + n] = in ? -2.0 * cchi * cub[n] / sq[n] / e2 : 0.0;
+    lp[kLpFields + 12 + n] = in ? -cpsi * omx2[n] / sq[n] / e2 : 0.0;
+  }
+  double* lam = lp + kLpLam;
+  double* LL = lp + lp_ll(nc);
+  double* v = lp + lp_scr(nc);
+  double* w = v + nc;
+  for (int i = 0; i < nc; ++i) {
+    lam[i] = i < 3 ? omx2[i] / sq[i] / e2 : 0.0;
+    v[i] = lam[i];
+    LL[i] = nu * lam[i];
+  }
+  if (nu_h > 0.0) {
+    for (int it = 0; it < p / 2 - 1; ++it) {
+      for (int i = 0; i < nc; ++i) w[i] = lap0_row(lap0, v, i, nc);
+      for (int i = 0; i < nc; ++i) v[i] = w[i];
+    }
+    const double sgn = ((p / 2) % 2 == 0) ? 1.0 : -1.0;
+    for (int i = 0; i < nc; ++i) LL[i] -= nu_h * sgn * v[i];
+  }
+}
+
+// the proxies' constant forcing c L Lambda of the (0, 0) blocks of a two-field tendency
+__global__ void k_lp_source(int nc, double cpsi, double cchi, const double* __restrict__ LL,
+                            double2* __restrict__ Apsi, double2* __restrict__ Achi) {
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= nc) return;
+  Apsi[a].x += cpsi * LL[a];
+  Achi[a].x += cchi * LL[a];
+}
+
+// prescribed-c inversion: the (0, 0) block of the right-hand side minus c lam
+__global__ void k_lp_shift(int nc, double cval, const double* __restrict__ lam, double2* __restrict__ f) {
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a < nc) f[a].x -= cval * lam[a];
+}
+
+// solve-for-c inversion of the (0, 0) block, one thread: D_0 with its (zero) column 0
+// replaced by lam, half width 2 below and (with the fill of partial pivoting) 4
+// above, eliminated for the real and imaginary right-hand sides together.  The
+// unknown in column 0 is c (from the real part; a real field's (0, 0) block has a
+// zero imaginary part, whose column-0 unknown is dropped), and the block's Pbar_0^0
+// coefficient is 0.
+__global__ void k_lp_solve_c(int nc, const double* __restrict__ lap0, double* __restrict__ lp,
+                             const double2* __restrict__ f, double2* __restrict__ out) {
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  constexpr int KLO = 2, KUP = 4, WB = KLO + KUP + 1;   // band columns j - i in [-2, 4]
+  const double* lam = lp + kLpLam;
+  double* ab = lp + lp_elim(nc);                          // [nc][WB]
+  double* br = ab + (long long)nc * WB;                   // [nc]
+  double* bi = br + nc;                                   // [nc]
+  auto at = [&](int i, int j) -> double& { return ab[(long long)i * WB + (j - i + KLO)]; };
+  for (int i = 0; i < nc; ++i) {
+    for (int o = 0; o < WB; ++o) ab[(long long)i * WB + o] = 0.0;
+    for (int o = 0; o < 5; ++o) {
+      const int j = i + o - 2;
+      if (j >= 1 && j < nc) at(i, j) = lap0[i * 5 + o];
+    }
+    if (i < 3) at(i, 0) = lam[i];
+    br[i] = f[i].x;
+    bi[i] = f[i].y;
+  }
+  for (int k = 0; k < nc; ++k) {
+    int piv = k;
+    double best = fabs(at(k, k));
+    for (int i = k + 1; i <= min(nc - 1, k + KLO); ++i)
+      if (fabs(at(i, k)) > best) { best = fabs(at(i, k)); piv = i; }
+    if (piv != k) {
+      for (int j = k; j <= min(nc - 1, k + KUP); ++j) {
+        const double t = at(k, j); at(k, j) = at(piv, j); at(piv, j) = t;
+      }
+      double t = br[k]; br[k] = br[piv]; br[piv] = t;
+      t = bi[k]; bi[k] = bi[piv]; bi[piv] = t;
+    }
+    const double d = at(k, k);
+    for (int i = k + 1; i <= min(nc - 1, k + KLO); ++i) {
+      const double l = at(i, k) / d;
+      if (l == 0.0) continue;
+      for (int j = k + 1; j <= min(nc - 1, k + KUP); ++j) at(i, j) -= l * at(k, j);
+      br[i] -= l * br[k];
+      bi[i] -= l * bi[k];
+    }
+  }
+  for (int k = nc - 1; k >= 0; --k) {
+    double sr = br[k], si = bi[k];
+    for (int j = k + 1; j <= min(nc - 1, k + KUP); ++j) {
+      sr -= at(k, j) * br[j];
+      si -= at(k, j) * bi[j];
+    }
+    br[k] = sr / at(k, k);
+    bi[k] = si / at(k, k);
+  }
+  lp[lp_c(nc)] = br[0];
+  out[0] = make_double2(0.0, 0.0);
+  for (int i = 1; i < nc; ++i) out[i] = make_double2(br[i], bi[i]);
+}
+
 template <typename T>
-__device__ __forceinline__ bool vortex_product_at(long long idx, int nphi, int nr, T U0,
+__device__ __forceinline__ bool vortex_product_at(long long idx, int nphi, int nr, T U0, T Uz,
                                                   const double* __restrict__ rnode, T* __restrict__ f0,
                                                   T* __restrict__ f1, T* __restrict__ f2,
                                                   const T* __restrict__ f3, const T* __restrict__ f4,
@@ -115,7 +271,8 @@ __device__ __forceinline__ bool vortex_product_at(long long idx, int nphi, int n
     sincospif(2.0f * (float)j / (float)nphi, &sf, &cf);
     sn = (T)sf; cs = (T)cf;
   }
-  const T rvr = f0[idx], rvp = f1[idx], vz = f2[idx], rwr = f3[idx], rwp = f4[idx], wz = f5[idx];
+  const T rvr = f0[idx], rvp = f1[idx], rwr = f3[idx], rwp = f4[idx], wz = f5[idx];
+  const T vz = f2[idx] + Uz;        // v_z + U_z
   const T ar = rvr + r * U0 * sn;   // r (v_r + U_r)
   const T ap = rvp + r * U0 * cs;   // r (v_phi + U_phi)
   const T A = vz * rwr - ar * wz;                // A = r N_phi
@@ -128,13 +285,13 @@ __device__ __forceinline__ bool vortex_product_at(long long idx, int nphi, int n
 }
 
 template <typename T>
-__global__ void k_vortex_product(long long n_phys, int nphi, int nr, T U0, const double* __restrict__ rnode,
+__global__ void k_vortex_product(long long n_phys, int nphi, int nr, T U0, T Uz, const double* __restrict__ rnode,
                                  T* __restrict__ f0, T* __restrict__ f1, T* __restrict__ f2,
                                  const T* __restrict__ f3, const T* __restrict__ f4, const T* __restrict__ f5,
                                  int* __restrict__ err) {
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   bool finite = true;
-  if (idx < n_phys) finite = vortex_product_at(idx, nphi, nr, U0, rnode, f0, f1, f2, f3, f4, f5);
+  if (idx < n_phys) finite = vortex_product_at(idx, nphi, nr, U0, Uz, rnode, f0, f1, f2, f3, f4, f5);
   // a non-finite product (blow-up or NaN in the state) sets the status bit that
   // mlx_device_status reports as MLX_ENUMERIC
   if (__any_sync(0xffffffffu, !finite) && (threadIdx.x & 31) == 0) atomicOr(err, 16);
@@ -241,8 +398,14 @@ inline unsigned nblk(long long n, int tb) { return (unsigned)((n + tb - 1) / tb)
 // Kinetic-energy density of one (m, k) harmonic of the velocity, on the Gauss nodes:
 // part[m K + k] = mult_m sum_i w_i / (1 - x_i)^2 (|r v_r|^2 / r_i^2 + |r v_phi|^2 / r_i^2 + |v_z|^2)
 // with each component evaluated from its coefficients by the FP64 basis table.
+// The sum is the grid's energy (that of the backward transform): the blocks m = 0
+// and m = Nphi/2 (Nyquist chop), whose grid functions are real parts, contribute
+// their Hermitian part in k, (f_k + conj f_{-k}) / 2, with mult 1 and 4; the other
+// orders f_k with mult 2; and with the axial Nyquist kept (K = Nz + 1) the rows
+// k = +-Nz/2 share one grid bin, which takes their sum (row k = -Nz/2 adds nothing).
 constexpr int kEnThreads = 128;
-__global__ void __launch_bounds__(kEnThreads) k_energy_blocks(int nc, int nr, int K, const long long* __restrict__ soff,
+__global__ void __launch_bounds__(kEnThreads) k_energy_blocks(int nc, int nr, int K, int Kz, int nz, int nphi,
+                                                              const long long* __restrict__ soff,
                                                               const long long* __restrict__ boff,
                                                               const double* __restrict__ x, const double* __restrict__ w,
                                                               const double* __restrict__ rn, const double* __restrict__ P64,
@@ -253,12 +416,32 @@ __global__ void __launch_bounds__(kEnThreads) k_energy_blocks(int nc, int nr, in
   __shared__ double red[kEnThreads];
   const int kidx = blockIdx.x, m = blockIdx.y;
   const int Nm = nc - m;
-  const long long base = soff[m] + (long long)kidx * Nm;
-  for (int a = threadIdx.x; a < Nm; a += blockDim.x) {
-    ev[a] = rvr[base + a];
-    ev[Nm + a] = rvp[base + a];
-    ev[2 * Nm + a] = vz[base + a];
+  const bool nyz = K == nz + 1;
+  if (nyz && kidx == Kz) {             // folded into the row k = +Nz/2
+    if (threadIdx.x == 0) part[(long long)m * K + kidx] = 0.0;
+    return;
   }
+  const bool herm = m == 0 || 2 * m == nphi;
+  const int prow = (kidx == 0 || (nyz && kidx == Kz - 1)) ? kidx : K - kidx;
+  const double2* src[3] = {rvr, rvp, vz};
+  auto row = [&](const double2* f, int kk, int a) {
+    double2 v = f[soff[m] + (long long)kk * Nm + a];
+    if (nyz && kk == Kz - 1) {
+      const double2 u = f[soff[m] + (long long)Kz * Nm + a];
+      v.x += u.x;
+      v.y += u.y;
+    }
+    return v;
+  };
+  for (int a = threadIdx.x; a < Nm; a += blockDim.x)
+    for (int c = 0; c < 3; ++c) {
+      double2 v = row(src[c], kidx, a);
+      if (herm) {
+        const double2 u = row(src[c], prow, a);
+        v = make_double2(0.5 * (v.x + u.x), 0.5 * (v.y - u.y));
+      }
+      ev[c * Nm + a] = v;
+    }
   __syncthreads();
   const double* Pm = P64 + boff[m];
   double acc = 0.0;
@@ -283,7 +466,57 @@ __global__ void __launch_bounds__(kEnThreads) k_energy_blocks(int nc, int nr, in
     if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
     __syncthreads();
   }
-  if (threadIdx.x == 0) part[(long long)m * K + kidx] = (m == 0 ? 1.0 : 2.0) * red[0];
+  if (threadIdx.x == 0)
+    part[(long long)m * K + kidx] = (m == 0 ? 1.0 : (2 * m == nphi ? 4.0 : 2.0)) * red[0];
+}
+
+// Enstrophy and peak vorticity over the nodes from the physical r w_r, r w_phi, w_z:
+// per CTA the partial sum of q_i |w|^2 (q_i = w_i ell^2 / (1 - x_i)^2, the mapped
+// area rule) and the largest |w|^2; k_enst_sum folds the partials in a fixed order.
+constexpr int kEsThreads = 256, kEnstBlocks = 4 * 148;
+template <typename T>
+__global__ void __launch_bounds__(kEsThreads) k_enst_blocks(long long n_phys, int nr, double ell,
+                                                            const double* __restrict__ x, const double* __restrict__ w,
+                                                            const double* __restrict__ rn, const T* __restrict__ rwr,
+                                                            const T* __restrict__ rwp, const T* __restrict__ wz,
+                                                            double* __restrict__ part) {
+  __shared__ double rs[kEsThreads], rm[kEsThreads];
+  double s = 0.0, mx = 0.0;
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < n_phys;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(idx % nr);
+    const double r = rn[i];
+    const double a = (double)rwr[idx] / r, b = (double)rwp[idx] / r, c = (double)wz[idx];
+    const double q2 = fma(a, a, fma(b, b, c * c));
+    const double om = 1.0 - x[i];
+    s = fma(w[i] * ell * ell / (om * om), q2, s);
+    mx = fmax(mx, q2);
+  }
+  rs[threadIdx.x] = s;
+  rm[threadIdx.x] = mx;
+  __syncthreads();
+  for (int h = kEsThreads / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h) {
+      rs[threadIdx.x] += rs[threadIdx.x + h];
+      rm[threadIdx.x] = fmax(rm[threadIdx.x], rm[threadIdx.x + h]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    part[2 * blockIdx.x] = rs[0];
+    part[2 * blockIdx.x + 1] = rm[0];
+  }
+}
+
+__global__ void k_enst_sum(int nb, const double* __restrict__ part, double* __restrict__ out) {
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  double s = 0.0, mx = 0.0;
+  for (int b = 0; b < nb; ++b) {
+    s += part[2 * b];
+    mx = fmax(mx, part[2 * b + 1]);
+  }
+  out[0] = s;
+  out[1] = mx;
 }
 
 }  // namespace
@@ -329,7 +562,7 @@ static int vortex_nonlinear_t(mlx_ctx* c, double U0, const double2* state, doubl
     const int vt = c->nc >= 256 ? 256 : ((c->nc + 31) / 32) * 32;
     k_vortex_fields<<<dim3(c->K, c->M), vt, sizeof(double2) * 4 * c->nc, st>>>(
         c->nc, c->Kz, c->K, c->lz, c->d_soff, c->d_lap_off, c->d_rdr, c->d_lap, psi, chi, F[0], F[1], F[2], F[3],
-        F[4], F[5]);
+        F[4], F[5], c->lp_on ? c->d_lp + kLpFields : nullptr);
   }
   MLX_LAUNCH_CHECK(c);
   int rc;
@@ -337,7 +570,7 @@ static int vortex_nonlinear_t(mlx_ctx* c, double U0, const double2* state, doubl
     if ((rc = mlx_legendre_backward(c, F[f], st))) return rc;
     if ((rc = mlx_fft_backward(c, P[f], st))) return rc;
   }
-  k_vortex_product<T><<<nblk(np, tb), tb, 0, st>>>(np, c->nphi, c->nr, (T)U0, c->d_r, P[0], P[1], P[2], P[3],
+  k_vortex_product<T><<<nblk(np, tb), tb, 0, st>>>(np, c->nphi, c->nr, (T)U0, (T)c->vortex_uz, c->d_r, P[0], P[1], P[2], P[3],
                                                    P[4], P[5], c->d_err);
   MLX_LAUNCH_CHECK(c);
   // A, B, C -> F[6], F[7], F[8]
@@ -376,15 +609,17 @@ extern "C" int mlx_axial_energy(mlx_ctx* c, const void* state, double* E, mlx_st
   double2* F[6];
   for (int i = 0; i < 6; ++i) F[i] = c->d_vspec + ns * i;
   const int vt = c->nc >= 256 ? 256 : ((c->nc + 31) / 32) * 32;
+  // the basis part only: the log proxy's swirl has unbounded energy
   k_vortex_fields<<<dim3(c->K, c->M), vt, sizeof(double2) * 4 * c->nc, st>>>(
       c->nc, c->Kz, c->K, c->lz, c->d_soff, c->d_lap_off, c->d_rdr, c->d_lap, psi, chi, F[0], F[1], F[2], F[3],
-      F[4], F[5]);
+      F[4], F[5], nullptr);
   MLX_LAUNCH_CHECK(c);
   // the partial sums go to the (then unused) seventh spectral temporary
   double* part = reinterpret_cast<double*>(c->d_vspec + ns * 6);
   if ((long long)c->M * c->K > 2 * ns) return MLX_EINVAL;
   k_energy_blocks<<<dim3(c->K, c->M), kEnThreads, sizeof(double2) * 3 * c->nc, st>>>(
-      c->nc, c->nr, c->K, c->d_soff, c->d_boff, c->d_x, c->d_w, c->d_r, c->d_P64, F[0], F[1], F[2], part);
+      c->nc, c->nr, c->K, c->Kz, c->nz, c->nphi, c->d_soff, c->d_boff, c->d_x, c->d_w, c->d_r, c->d_P64, F[0],
+      F[1], F[2], part);
   MLX_LAUNCH_CHECK(c);
   std::vector<double> h((size_t)c->M * c->K);
   MLX_CUDA_TRY(c, cudaMemcpyAsync(h.data(), part, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, st));
@@ -398,4 +633,108 @@ extern "C" int mlx_axial_energy(mlx_ctx* c, const void* state, double* E, mlx_st
     }
   for (int k = 0; k < c->Kz; ++k) E[k] *= scale;
   return MLX_OK;
+}
+
+// ---- log proxies and the axial background (see mlx.h) ----------------------------
+
+// (Re)build the proxy tables from the context's amplitudes and implicit operator.
+int mlx_lp_refresh(mlx_ctx* c, cudaStream_t st) {
+  if (!c->d_lp) MLX_CUDA_TRY(c, cudaMalloc(&c->d_lp, sizeof(double) * lp_size(c->nc)));
+  k_lp_setup<<<1, 32, 0, st>>>(c->nc, c->ell, c->lp_cpsi, c->lp_cchi, c->implicit_ready ? c->nu : 0.0,
+                               c->implicit_ready ? c->nu_h : 0.0, c->p, c->d_lap, c->d_lp);
+  MLX_LAUNCH_CHECK(c);
+  return MLX_OK;
+}
+
+// Add the proxies' forcing c L Lambda to a two-field tendency (the time steps).
+int mlx_lp_add_source(mlx_ctx* c, double2* A, cudaStream_t st) {
+  if (!c->lp_on) return MLX_OK;
+  k_lp_source<<<nblk(c->nc, 128), 128, 0, st>>>(c->nc, c->lp_cpsi, c->lp_cchi, c->d_lp + lp_ll(c->nc), A,
+                                                A + c->n_spec);
+  MLX_LAUNCH_CHECK(c);
+  return MLX_OK;
+}
+
+extern "C" int mlx_vortex_logproxy(mlx_ctx* c, double c_psi, double c_chi, double Uz, mlx_stream stream) {
+  if (!c || !std::isfinite(c_psi) || !std::isfinite(c_chi) || !std::isfinite(Uz)) return MLX_EINVAL;
+  if (!c->vortex_ready) return MLX_ESTATE;
+  cudaStream_t st = (cudaStream_t)stream;
+  c->lp_cpsi = c_psi;
+  c->lp_cchi = c_chi;
+  c->vortex_uz = Uz;
+  c->lp_on = c_psi != 0.0 || c_chi != 0.0;
+  int rc = mlx_lp_refresh(c, st);
+  if (rc) return rc;
+  mlx_invalidate_graphs(c);
+  MLX_CUDA_TRY(c, cudaStreamSynchronize(st));
+  return MLX_OK;
+}
+
+extern "C" int mlx_lap_h_solve_log(mlx_ctx* c, const void* rhs, void* out, int variant, double* cval,
+                                   mlx_stream stream) {
+  if (!c || !rhs || !out || rhs == out || !cval) return MLX_EINVAL;
+  if ((((uintptr_t)rhs) & 15u) || (((uintptr_t)out) & 15u)) return MLX_EINVAL;
+  if (variant != MLX_LOGPROXY_PRESCRIBE && variant != MLX_LOGPROXY_SOLVE) return MLX_EINVAL;
+  if (variant == MLX_LOGPROXY_PRESCRIBE && !std::isfinite(*cval)) return MLX_EINVAL;
+  if (!c->lap_ready || !c->vortex_ready) return MLX_ESTATE;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (!c->d_lp) {
+    int rc = mlx_lp_refresh(c, st);
+    if (rc) return rc;
+  }
+  const double2* f = (const double2*)rhs;
+  if (variant == MLX_LOGPROXY_PRESCRIBE) {
+    double2* tmp = c->d_spec3;
+    MLX_CUDA_TRY(c, cudaMemcpyAsync(tmp, f, sizeof(double2) * c->n_spec, cudaMemcpyDeviceToDevice, st));
+    k_lp_shift<<<nblk(c->nc, 128), 128, 0, st>>>(c->nc, *cval, c->d_lp + kLpLam, tmp);
+    MLX_LAUNCH_CHECK(c);
+    return mlx_lap_solve(c, 0, tmp, (double2*)out, st);
+  }
+  int rc = mlx_lap_solve(c, 0, f, (double2*)out, st);   // every other harmonic: the ordinary solve
+  if (rc) return rc;
+  k_lp_solve_c<<<1, 32, 0, st>>>(c->nc, c->d_lap, c->d_lp, f, (double2*)out);
+  MLX_LAUNCH_CHECK(c);
+  MLX_CUDA_TRY(c, cudaMemcpyAsync(cval, c->d_lp + lp_c(c->nc), sizeof(double), cudaMemcpyDeviceToHost, st));
+  MLX_CUDA_TRY(c, cudaStreamSynchronize(st));
+  return MLX_OK;
+}
+
+template <typename T>
+static int vortex_diag_t(mlx_ctx* c, const double2* state, mlx_vortex_diag_out* out, cudaStream_t st) {
+  const long long ns = c->n_spec, np = c->n_phys;
+  double2* F[6];
+  for (int i = 0; i < 6; ++i) F[i] = c->d_vspec + ns * i;
+  T* P[6];
+  for (int i = 0; i < 6; ++i) P[i] = reinterpret_cast<T*>(c->d_vphys) + np * i;
+  const int vt = c->nc >= 256 ? 256 : ((c->nc + 31) / 32) * 32;
+  k_vortex_fields<<<dim3(c->K, c->M), vt, sizeof(double2) * 4 * c->nc, st>>>(
+      c->nc, c->Kz, c->K, c->lz, c->d_soff, c->d_lap_off, c->d_rdr, c->d_lap, state, state + ns, F[0], F[1], F[2],
+      F[3], F[4], F[5], c->lp_on ? c->d_lp + kLpFields : nullptr);
+  MLX_LAUNCH_CHECK(c);
+  int rc;
+  for (int f = 3; f < 6; ++f) {
+    if ((rc = mlx_legendre_backward(c, F[f], st))) return rc;
+    if ((rc = mlx_fft_backward(c, P[f], st))) return rc;
+  }
+  const int nb = kEnstBlocks;
+  if (!c->d_enst) MLX_CUDA_TRY(c, cudaMalloc(&c->d_enst, sizeof(double) * (2 * nb + 2)));
+  double* part = c->d_enst;
+  k_enst_blocks<T><<<nb, kEsThreads, 0, st>>>(np, c->nr, c->ell, c->d_x, c->d_w, c->d_r, P[3], P[4], P[5], part);
+  MLX_LAUNCH_CHECK(c);
+  k_enst_sum<<<1, 32, 0, st>>>(nb, part, part + 2 * nb);
+  MLX_LAUNCH_CHECK(c);
+  double h[2];
+  MLX_CUDA_TRY(c, cudaMemcpyAsync(h, part + 2 * nb, sizeof(h), cudaMemcpyDeviceToHost, st));
+  MLX_CUDA_TRY(c, cudaStreamSynchronize(st));
+  out->enstrophy = 0.5 * (c->lz / c->nz) * (2.0 * M_PI / c->nphi) * h[0];
+  out->peak_vorticity = sqrt(h[1]);
+  return MLX_OK;
+}
+
+extern "C" int mlx_vortex_diag(mlx_ctx* c, const void* state, mlx_vortex_diag_out* out, mlx_stream stream) {
+  if (!c || !state || !out || (((uintptr_t)state) & 15u)) return MLX_EINVAL;
+  if (!c->vortex_ready) return MLX_ESTATE;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (c->precision == MLX_FP64) return vortex_diag_t<double>(c, (const double2*)state, out, st);
+  return vortex_diag_t<float>(c, (const double2*)state, out, st);
 }

@@ -15,6 +15,7 @@ Workloads (all analytic, as in the paper's examples; no dataset is involved):
 * field_sA / field_sB -- rational and Gaussian fields of Eq. (13)
 * kpp_linear          -- linearised Fisher-KPP solution, Eq. (18)
 * vortex_pair_omega   -- counter-rotating Lamb-Oseen pair with a seeded axial displacement
+* q_vortex_pair       -- co-rotating q-vortex pair (axial vorticity and axial velocity)
 * random_spectral     -- seeded random coefficients in the flat ragged layout
 * batch_instances     -- the uneven batch of independent 2-D/3-D solves
 * surrogate_trajectories -- seeded vortex-pair variants the learned surrogate trains on
@@ -94,6 +95,24 @@ def vortex_pair_omega(r, phi, z, lz, b=1.0, a=0.2, gamma=2.0 * math.pi, amp=1e-3
         rr = (x - xc - dx) ** 2 + (y - dy) ** 2
         out += sgn * gamma / (math.pi * a * a) * np.exp(-rr / (a * a))
     return out
+
+
+def q_vortex_pair(r, phi, z, lz, b=4.0, q=1.0, amp=1e-10, kseed=1):
+    """(omega_z, v_z) of two co-rotating q-vortices (v_phi = (1 - e^{-rho^2}) / rho and
+    v_z = e^{-rho^2} / q about each centre, so omega_z = 2 e^{-rho^2}) at (x, y) =
+    (+-b/2, 0), each centre displaced along x by amp cos(2 pi kseed z / lz) in
+    opposite directions (a deterministic seed of the given amplitude)."""
+    r, phi, z = _b(r, phi, z)
+    x = r * np.cos(phi)
+    y = r * np.sin(phi)
+    d = amp * np.cos(2.0 * math.pi * kseed * z / lz)
+    wz = np.zeros_like(x)
+    vz = np.zeros_like(x)
+    for xc, sgn in ((0.5 * b, 1.0), (-0.5 * b, -1.0)):
+        e = np.exp(-((x - xc - sgn * d) ** 2 + y ** 2))
+        wz += 2.0 * e
+        vz += e / q
+    return wz, vz
 
 
 def random_spectral(nc, M, Kz, seed=0, scale_decay=0.0):

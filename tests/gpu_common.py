@@ -11,7 +11,8 @@ def pair(nr, nphi, nz, ell, lz=2 * np.pi, policy="linear", precision=B.FP64, **c
     g = O.Grid(nr, nphi, nz, ell, lz=lz, policy=policy,
                nr_c=chops.get("nr_c"), M=chops.get("nphi_c"), Kz=chops.get("nz_c"))
     ctx = B.Context(nr, nphi, nz, ell, lz=lz, precision=precision,
-                    chop_policy=B.CHOP_LINEAR if policy == "linear" else B.CHOP_TWOTHIRDS,
+                    chop_policy={"linear": B.CHOP_LINEAR, "twothirds": B.CHOP_TWOTHIRDS,
+                                 "nyquist": B.CHOP_NYQUIST}[policy],
                     nr_c=chops.get("nr_c") or 0, nphi_c=chops.get("nphi_c") or 0,
                     nz_c=chops.get("nz_c") or 0)
     assert (ctx.M, ctx.Kz, ctx.nc) == (g.M, g.Kz, g.nc)

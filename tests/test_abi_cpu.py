@@ -42,11 +42,15 @@ def test_strerror(lib):
     dict(nr=1, nphi=8, nz=1, ell=1.0), dict(nr=8, nphi=12, nz=1, ell=1.0),
     dict(nr=8, nphi=8, nz=3, ell=1.0), dict(nr=8, nphi=8, nz=1, ell=0.0), dict(nr=8, nphi=1024, nz=1, ell=1.0),
     dict(nr=8, nphi=8, nz=1, ell=1.0, lz=-1.0), dict(nr=8, nphi=8, nz=1, ell=1.0, precision=7),
-    dict(nr=8, nphi=8, nz=1, ell=1.0, nphi_c=5), dict(nr=8, nphi=8, nz=4, ell=1.0, nz_c=3),
-    dict(nr=8, nphi=8, nz=1, ell=1.0, nr_c=9), dict(nr=4, nphi=16, nz=1, ell=1.0, nphi_c=8)])
+    dict(nr=8, nphi=8, nz=1, ell=1.0, nphi_c=6), dict(nr=8, nphi=8, nz=4, ell=1.0, nz_c=4),
+    dict(nr=8, nphi=8, nz=1, ell=1.0, nr_c=9), dict(nr=4, nphi=16, nz=1, ell=1.0, nphi_c=8),
+    dict(nr=8, nphi=8, nz=1, ell=1.0, chop_policy=3), dict(nr=4, nphi=8, nz=1, ell=1.0, chop_policy=2)])
 def test_create_rejects_invalid(lib, kw):
+    # chops one past the Nyquist-keeping bounds (M = Nphi/2 + 1, Kz = Nz/2 + 1), an
+    # unknown policy, and a Nyquist chop whose M = 5 exceeds Nc = 4
     p = B.Params(kw["nr"], kw["nphi"], kw["nz"], kw.get("nr_c", 0), kw.get("nphi_c", 0),
-                 kw.get("nz_c", 0), kw["ell"], kw.get("lz", 1.0), kw.get("precision", 0), 0)
+                 kw.get("nz_c", 0), kw["ell"], kw.get("lz", 1.0), kw.get("precision", 0),
+                 kw.get("chop_policy", 0))
     h = ctypes.c_void_p(123)
     assert lib.mlx_create(ctypes.byref(p), None, ctypes.byref(h)) == -1
     assert not h.value

@@ -1,0 +1,189 @@
+"""GPU parity of the log proxy (Sec. 3.1, Eq. (6)), the axial background, the enstrophy
+diagnostic and the Nyquist chop's energy spectrum against the oracle."""
+
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle import logproxy as LP
+from oracle.vortex import axial_energy, enstrophy
+from paper_2609_18026_b300 import binding as B
+from paper_2609_18026_b300 import workloads as W
+
+from gpu_common import pair, to_gpu_spec, spec_from_gpu, block_err
+from vortex_states import q_vortex_state
+
+pytestmark = pytest.mark.gpu
+
+PNAME = {B.FP64: "fp64", B.FP32: "fp32", B.BF16X3: "bf16x3"}
+
+
+def _flat2(g, psi, chi):
+    return np.concatenate([O.to_flat(g, psi), O.to_flat(g, chi)])
+
+
+def _split(g, flat):
+    n = len(flat) // 2
+    return O.from_flat(g, flat[:n]), O.from_flat(g, flat[n:])
+
+
+def _perturbed_pair(g, ops, amp=1e-3, seed=7):
+    """Co-rotating q-vortex pair at (+-2, 0) plus a seeded smooth 3-D perturbation
+    of the basis parts (the (0, 0) blocks untouched)."""
+    psi, chi, cp, cc, _ = q_vortex_state(g, [(2.0, 0.0), (-2.0, 0.0)], ops=ops)
+    for s, sd in ((psi, seed), (chi, seed + 1)):
+        d = O.from_flat(g, W.random_spectral(g.nc, g.M, g.Kz, seed=sd, scale_decay=0.4))
+        for m in range(g.M):
+            for kk in range(g.K):
+                if m == 0 and kk == 0:
+                    continue
+                s[m][kk] = s[m][kk] + amp * d[m][kk]
+    return psi, chi, cp, cc
+
+
+@pytest.mark.parametrize("variant", [B.LOGPROXY_PRESCRIBE, B.LOGPROXY_SOLVE])
+def test_lap_h_solve_log_parity(variant, record):
+    # a Lamb-Oseen vortex (net circulation 2 pi) plus seeded smooth harmonics
+    g, ctx = pair(48, 16, 8, 1.5, lz=3.0, policy="twothirds")
+    ctx.vortex_setup()
+    ops = O.VortexOps(g)
+    r, phi, z = g.nodes3()
+    gam, a = 2.0 * math.pi, 0.7
+    f = O.forward(g, -gam / (math.pi * a * a) * np.exp(-r ** 2 / (a * a)) + 0 * phi + 0 * z)
+    d = O.from_flat(g, W.random_spectral(g.nc, g.M, g.Kz, seed=12, scale_decay=0.3))
+    for m in range(g.M):
+        for kk in range(g.K):
+            if not (m == 0 and kk == 0):
+                f[m][kk] = f[m][kk] + 0.1 * d[m][kk]
+    c_in = -gam / (4.0 * math.pi)
+    out, c = ctx.lap_h_solve_log(to_gpu_spec(O.to_flat(g, f)), ctx.new_spec(), variant, c=c_in)
+    ref = [np.stack([ops.lap_h_inv(m, f[m][kk]) for kk in range(g.K)]) for m in range(g.M)]
+    lam = LP.image(g.nc, g.ell)
+    if variant == B.LOGPROXY_PRESCRIBE:
+        ref[0][0] = LP.solve_prescribed(ops.D[0], lam, f[0][0], c_in)
+        c_ref = c_in
+    else:
+        ref[0][0], c_ref = LP.solve_for_c(ops.D[0], lam, f[0][0])
+    got = spec_from_gpu(g, out)
+    e = O.spec_rel_err(g, got, ref)
+    record("lap_h_solve_log", variant=int(variant), rel_err=e, c=c, c_ref=c_ref)
+    assert e <= 1e-12
+    assert abs(c - c_ref) <= 1e-12 * abs(c_ref)
+    if variant == B.LOGPROXY_SOLVE:
+        assert abs(c - c_in) < 1e-9               # the amplitude of the far field, -Gamma / 4 pi
+
+
+@pytest.mark.parametrize("prec", [B.FP64, B.FP32, B.BF16X3])
+@pytest.mark.parametrize("grid", [(48, 32, 1, 4.0), (32, 32, 8, 4.0)])
+def test_vortex_nonlinear_logproxy_parity(grid, prec, record):
+    # the co-rotating q-vortex pair (net circulation 4 pi, net axial flux 2 pi) in an
+    # axial background U_z = -0.5, against the oracle's banded form (the kernel's
+    # formulation) with the proxies' fields in closed form at the nodes
+    nr, nphi, nz, ell = grid
+    g, ctx = pair(nr, nphi, nz, ell, lz=2.0 * math.pi, policy="twothirds", precision=prec)
+    ctx.vortex_setup()
+    ops = O.VortexOps(g)
+    psi, chi, cp, cc = _perturbed_pair(g, ops)
+    Uz, U0 = -0.5, 0.3
+    ctx.vortex_logproxy(cp, cc, Uz)
+    state = to_gpu_spec(_flat2(g, psi, chi))
+    out = ctx.nonlinear(B.NONLIN_VORTEX, [U0], state, to_gpu_spec(np.zeros(2 * ctx.n_spec, np.complex128)))
+    gp, gc = _split(g, out.cpu().numpy())
+    pN, cN = ops.nonlinear(psi, chi, U0, "banded", Uz, cp, cc)
+    e = O.spec_rel_err(g, gp + gc, pN + cN)
+    eb = block_err(g, gp + gc, pN + cN, floor=1e-3 if prec == B.FP64 else 0.1)
+    # the proxies matter: without them the term is far from the reference
+    p0, c0 = ops.nonlinear(psi, chi, U0, "banded", Uz, 0.0, 0.0)
+    e_drop = O.spec_rel_err(g, p0 + c0, pN + cN)
+    record("vortex_nonlinear_logproxy", grid=grid[:3], precision=PNAME[prec], rel_err=e, block_err=eb,
+           rel_err_without_proxies=e_drop)
+    assert e_drop > 1e-3
+    if prec == B.FP64:
+        assert e <= 1e-12
+        assert eb <= 1e-10
+    else:
+        # FP32 transforms through the projection (whose conditioning magnifies
+        # them; the vortex term's FP32 bar is derived in test_gpu_vortex.py)
+        assert e <= 1e-4
+    ctx.device_status()
+
+
+@pytest.mark.parametrize("prec,tol", [(B.FP64, 1e-12), (B.BF16X3, 1e-5)])
+def test_vortex_advance_logproxy_parity(prec, tol, record):
+    # the Richardson start and 3 AB-CN steps with nu and p = 8 hyperviscosity: the
+    # proxies' forcing c L Lambda in the (0, 0) blocks of the tendency
+    g, ctx = pair(32, 32, 8, 4.0, lz=2.0 * math.pi, policy="twothirds", precision=prec)
+    ctx.vortex_setup()
+    ops = O.VortexOps(g)
+    psi, chi, cp, cc = _perturbed_pair(g, ops)
+    nu, nuh, dt, Uz = 1e-3, 1e-4, 1e-2, -0.5
+    ctx.implicit_setup(nu, dt, nu_h=nuh, p=8)
+    ctx.vortex_logproxy(cp, cc, Uz)
+    state = to_gpu_spec(_flat2(g, psi, chi))
+    prev = to_gpu_spec(np.zeros(2 * ctx.n_spec, np.complex128))
+    ctx.advance(B.NONLIN_VORTEX, [0.0], state, prev, 4, True)
+    gp, gc = _split(g, state.cpu().numpy())
+    A, _ = O.vortex_nonlinear(g, 0.0, form="banded", Uz=Uz, cpsi=cp, cchi=cc, source=(nu, nuh, 8))
+    ref, _ = O.Stepper(g, nu, dt, nu_h=nuh, p=8, nonlinear=A).run_abcn(psi + chi, 4)
+    A0, _ = O.vortex_nonlinear(g, 0.0, form="banded", Uz=Uz, cpsi=cp, cchi=cc)
+    ref0, _ = O.Stepper(g, nu, dt, nu_h=nuh, p=8, nonlinear=A0).run_abcn(psi + chi, 4)
+    e = O.spec_rel_err(g, gp + gc, ref)
+    e_nosrc = O.spec_rel_err(g, ref0, ref)
+    record("vortex_advance_logproxy", precision=PNAME[prec], rel_err=e, rel_err_without_source=e_nosrc)
+    assert e <= tol
+    if prec == B.FP64:
+        assert e_nosrc > 1e3 * tol         # the source term is visible at this bar
+
+
+@pytest.mark.parametrize("prec,tol", [(B.FP64, 1e-12), (B.FP32, 1e-6), (B.BF16X3, 1e-6)])
+def test_vortex_diag_parity(prec, tol, record):
+    g, ctx = pair(48, 32, 8, 4.0, lz=2.0 * math.pi, policy="twothirds", precision=prec)
+    ctx.vortex_setup()
+    ops = O.VortexOps(g)
+    psi, chi, cp, cc = _perturbed_pair(g, ops, amp=1e-2)
+    ctx.vortex_logproxy(cp, cc, 0.0)
+    got = ctx.vortex_diag(to_gpu_spec(_flat2(g, psi, chi)))
+    Z, wmax = enstrophy(g, ops, psi, chi, cp, cc)
+    eZ = abs(got["enstrophy"] - Z) / Z
+    ew = abs(got["peak_vorticity"] - wmax) / wmax
+    record("vortex_diag", precision=PNAME[prec], enstrophy=got["enstrophy"], rel_err=eZ,
+           peak=got["peak_vorticity"], peak_rel_err=ew)
+    assert eZ <= tol and ew <= tol
+    # near the closed form of the unperturbed pair, (1/2) Lz (6 pi - 10 pi e^{-8})
+    assert abs(Z / (0.5 * g.lz * (6 * math.pi - 10 * math.pi * math.exp(-8.0))) - 1.0) < 0.05
+
+
+@pytest.mark.parametrize("prec", [B.FP64, B.BF16X3])
+def test_axial_energy_nyquist_chop(prec, record):
+    # the grid energy with the Nyquist pairs kept, on a general state (the m = Nphi/2
+    # block not Hermitian, the k = +-Nz/2 rows unequal)
+    g, ctx = pair(24, 16, 8, 1.0, lz=3.0, policy="nyquist", precision=prec)
+    ctx.vortex_setup()
+    ops = O.VortexOps(g)
+    psi = O.from_flat(g, W.random_spectral(g.nc, g.M, g.Kz, seed=31, scale_decay=0.3))
+    chi = O.from_flat(g, W.random_spectral(g.nc, g.M, g.Kz, seed=32, scale_decay=0.3))
+    ref = axial_energy(g, ops, psi, chi)
+    got = np.array(ctx.axial_energy(to_gpu_spec(_flat2(g, psi, chi))))
+    err = np.max(np.abs(got - ref) / np.abs(ref))
+    record("axial_energy_nyquist", precision=PNAME[prec], max_rel_err=float(err))
+    assert len(got) == g.Kz == g.nz // 2 + 1
+    assert err <= 1e-11
+
+
+def test_checkpoint_carries_the_proxies():
+    g, ctx = pair(24, 16, 4, 2.0, lz=2.0 * math.pi, policy="twothirds")
+    ctx.vortex_setup()
+    ctx.implicit_setup(1e-3, 1e-2)
+    ops = O.VortexOps(g)
+    psi, chi, cp, cc, _ = q_vortex_state(g, [(1.0, 0.0)], ops=ops)
+    ctx.vortex_logproxy(cp, cc, -0.5)
+    state = to_gpu_spec(_flat2(g, psi, chi))
+    prev = to_gpu_spec(np.zeros(2 * ctx.n_spec, np.complex128))
+    img = ctx.get_state(B.NONLIN_VORTEX, state, prev, 3)
+    ctx.vortex_logproxy(cp, 0.0, -0.5)
+    with pytest.raises(B.MlxError):
+        ctx.set_state(B.NONLIN_VORTEX, img, state, prev)
+    ctx.vortex_logproxy(cp, cc, -0.5)
+    assert ctx.set_state(B.NONLIN_VORTEX, img, state, prev) == 3

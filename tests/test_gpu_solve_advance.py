@@ -12,10 +12,11 @@ from gpu_common import pair, to_gpu_spec, spec_from_gpu, rand_spec
 pytestmark = pytest.mark.gpu
 
 
+@pytest.mark.parametrize("pol", ["twothirds", "nyquist"])
 @pytest.mark.parametrize("nu_h,p", [(0.0, 8), (5e-3, 4), (5e-7, 8)])
 @pytest.mark.parametrize("step", [B.STEP_FEBE_HALF, B.STEP_FEBE_FULL, B.STEP_ABCN])
-def test_implicit_solve_parity(step, nu_h, p):
-    g, ctx = pair(40, 16, 8, 1.5, lz=3.0, policy="twothirds")
+def test_implicit_solve_parity(step, nu_h, p, pol):
+    g, ctx = pair(40, 16, 8, 1.5, lz=3.0, policy=pol)
     dt, nu = 2e-2, 0.3
     ctx.implicit_setup(nu, dt, nu_h=nu_h, p=p)
     st = O.Stepper(g, nu, dt, nu_h=nu_h, p=p)
@@ -78,9 +79,10 @@ def test_polar_diffusion_100_steps():
     assert O.spec_rel_err(g, spec_from_gpu(g, state), ref) <= 1e-12
 
 
+@pytest.mark.parametrize("pol", ["twothirds", "nyquist"])
 @pytest.mark.parametrize("prec,tol", [(B.FP64, 1e-12), (B.FP32, 1e-6), (B.BF16X3, 1e-6)])
-def test_fkpp_advance_small(prec, tol):
-    g, ctx = pair(24, 16, 8, 4.0, lz=2 * np.pi * 8, policy="twothirds", precision=prec)
+def test_fkpp_advance_small(prec, tol, pol):
+    g, ctx = pair(24, 16, 8, 4.0, lz=2 * np.pi * 8, policy=pol, precision=prec)
     r, phi, z = g.nodes3()
     s0 = O.forward(g, W.fkpp_seed(r, phi, z))
     dt = 1e-2

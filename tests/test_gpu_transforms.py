@@ -26,6 +26,14 @@ GRIDS = [
     (9, 256, 32, 1.0, "linear", 7),       # in-lane butterfly stages (E = 8), M = 7
     (6, 512, 2, 1.0, "twothirds", 5),     # E = 16, Nz = 2, M = 5
     (12, 4, 256, 0.7, "linear"),          # lane groups for Nphi = 4, long z lines
+    # Nyquist-keeping chop (|m| <= Nphi/2, |k| <= Nz/2): the pair splitting of the
+    # forward direction and the pair sums of the backward one
+    (9, 8, 2, 1.0, "nyquist"),            # Nz = 2: K = 3, both k = +-1 rows are the pair
+    (24, 16, 8, 1.3, "nyquist"),
+    (70, 32, 16, 2.0, "nyquist"),
+    (40, 64, 1, 2.0, "nyquist"),          # 2-D: azimuthal pair only
+    (12, 4, 256, 0.7, "nyquist"),         # M = 3 with Nphi = 4, K = 257
+    (256, 256, 32, 4.0, "nyquist"),       # M = 129: the production run's azimuthal chop
 ]
 TOL = {B.FP64: 1e-12, B.FP32: 1e-6, B.BF16X3: 1e-6}
 # element-wise bars: every (m, k) block of a spectral result (or every node of a
@@ -107,10 +115,12 @@ def test_azimuthal_purity_exact():
 
 
 @pytest.mark.parametrize("prec", PRECS)
-@pytest.mark.parametrize("grid", [(5, 8, 4, 0.8), (40, 16, 8, 2.0), (128, 128, 64, 4.0)])
+@pytest.mark.parametrize("grid", [(5, 8, 4, 0.8), (40, 16, 8, 2.0), (128, 128, 64, 4.0),
+                                  (40, 16, 8, 2.0, "nyquist"), (64, 32, 1, 2.0, "nyquist")])
 def test_fkpp_nonlinear_parity(grid, prec, record):
-    nr, nphi, nz, ell = grid
-    g, ctx = pair(nr, nphi, nz, ell, lz=2 * np.pi * 8, policy="twothirds", precision=prec)
+    nr, nphi, nz, ell = grid[:4]
+    pol = grid[4] if len(grid) > 4 else "twothirds"
+    g, ctx = pair(nr, nphi, nz, ell, lz=2 * np.pi * 8, policy=pol, precision=prec)
     r, phi, z = g.nodes3()
     from paper_2609_18026_b300 import workloads as W
     s0 = O.forward(g, W.fkpp_seed(r, phi, z))
@@ -118,7 +128,7 @@ def test_fkpp_nonlinear_parity(grid, prec, record):
     ref = O.fkpp_nonlinear(g, 1.0)(s0)
     got = spec_from_gpu(g, out)
     e, eb = O.spec_rel_err(g, got, ref), block_err(g, got, ref, floor=FLOOR[prec])
-    record("fkpp_nonlinear", grid=grid, precision=PNAME[prec], rel_err=e, block_err=eb)
+    record("fkpp_nonlinear", grid=grid[:3], policy=pol, precision=PNAME[prec], rel_err=e, block_err=eb)
     assert e <= TOL[prec]
     assert eb <= BLOCK[prec]
 

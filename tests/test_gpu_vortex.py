@@ -65,12 +65,14 @@ def _gpu_vortex(ctx, g, psi_flat, chi_flat, U0):
 
 
 @pytest.mark.parametrize("prec", [B.FP64, B.FP32, B.BF16X3])
-@pytest.mark.parametrize("grid", [(24, 16, 8, 1.0, 0.0), (33, 32, 16, 1.0, 1.0), (48, 16, 8, 1.0, -1.0)])
+@pytest.mark.parametrize("grid", [(24, 16, 8, 1.0, 0.0), (33, 32, 16, 1.0, 1.0), (48, 16, 8, 1.0, -1.0),
+                                  (24, 16, 8, 1.0, 0.5, "nyquist"), (40, 32, 1, 1.0, -0.5, "nyquist")])
 def test_vortex_nonlinear_parity(grid, prec, record):
     # The CUDA path evaluates P in the banded form (9 transforms, no division by
     # r at the nodes): element by element against the oracle's banded form.
-    nr, nphi, nz, ell, U0 = grid
-    g, ctx = pair(nr, nphi, nz, ell, lz=8.6, policy="twothirds", precision=prec)
+    nr, nphi, nz, ell, U0 = grid[:5]
+    pol = grid[5] if len(grid) > 5 else "twothirds"
+    g, ctx = pair(nr, nphi, nz, ell, lz=8.6, policy=pol, precision=prec)
     ctx.vortex_setup()
     psi, chi = _smooth_state(g, 11)
     gp, gc = _gpu_vortex(ctx, g, psi, chi, U0)

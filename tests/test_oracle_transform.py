@@ -130,3 +130,96 @@ def test_flat_layout_roundtrip():
     for m in range(g.M):
         assert np.array_equal(flat[off:off + g.K * (g.nc - m)], s[m].reshape(-1))
         off += g.K * (g.nc - m)
+
+
+# --- Nyquist-keeping chop (|m| <= Nphi/2, |k| <= Nz/2): the aliased pair is split
+# --- in equal halves in the forward direction and summed in the backward one.
+
+def test_nyquist_chop_sizes():
+    g = O.Grid(12, 8, 6, 1.0, policy="nyquist")
+    assert (g.M, g.Kz, g.K) == (5, 4, 7)
+    assert sorted(g.kz.tolist()) == [-3, -2, -1, 0, 1, 2, 3]
+    g1 = O.Grid(12, 8, 1, 1.0, policy="nyquist")
+    assert (g1.M, g1.Kz, g1.K) == (5, 1, 1)
+
+
+@pytest.mark.parametrize("nphi,nz", [(8, 6), (16, 4), (4, 2)])
+def test_nyquist_cosines_split_in_halves(nphi, nz):
+    # cos(A) = (e^{iA} + e^{-iA}) / 2: a pure Nyquist cosine times a basis function
+    # must come back as 1/2 in each stored member of the pair (1/4 per row for the
+    # product of the azimuthal and the axial Nyquist cosines), and nothing else.
+    g = O.Grid(nphi + 2, nphi, nz, 1.2, lz=3.0, policy="nyquist")
+    r, phi, z = g.nodes3()
+    mq, kq = nphi // 2, nz // 2
+    prof_m = g.P[mq][0][None, None, :]       # Pbar_{mq}^{mq}(x_i), discrete-orthonormal
+    prof_0 = g.P[0][0][None, None, :]
+    cz = np.cos(2.0 * math.pi * kq * z / g.lz)
+    cases = [
+        (np.cos(mq * phi) * prof_m + 0 * z, mq, {0: 0.5}),
+        (cz * prof_0 + 0 * phi, 0, {kq: 0.5, -kq: 0.5}),
+        (np.cos(mq * phi) * cz * prof_m, mq, {kq: 0.25, -kq: 0.25}),
+    ]
+    for phys, m, want in cases:
+        s = O.forward(g, phys)
+        for mm in range(g.M):
+            for kk in range(g.K):
+                exp0 = want.get(int(g.kz[kk]), 0.0) if mm == m else 0.0
+                assert abs(s[mm][kk, 0] - exp0) < 1e-14, (mm, kk)
+                assert np.all(np.abs(s[mm][kk, 1:]) < 1e-14)
+
+
+def test_nyquist_backward_closed_form():
+    # one coefficient c at (n, m, k) = (Nphi/2, Nphi/2, 0): Eq. (2) with its
+    # conjugate partner gives 2 Re(c e^{i (Nphi/2) phi_j}) = 2 Re(c) (-1)^j on the grid
+    g = O.Grid(9, 8, 4, 0.9, lz=2.0, policy="nyquist")
+    s = O.spec_zeros(g)
+    c = 0.37 - 1.9j
+    s[4][0, 0] = c
+    phys = O.backward(g, s)
+    r, phi, z = g.nodes3()
+    want = 2.0 * c.real * np.cos(4 * phi) * g.P[4][0][None, None, :] + 0 * z
+    assert np.max(np.abs(phys - want)) < 1e-14
+
+
+def _nyquist_projection(g, s):
+    """What forward(backward(s)) must return with the Nyquist kept: the m = Nphi/2
+    block becomes its Hermitian part in k (its grid function is real), and the rows
+    k = +-Nz/2 are replaced by their mean (they share one grid function)."""
+    out = [b.copy() for b in s]
+    idx = {int(k): i for i, k in enumerate(g.kz)}
+    if g.nphi >= 2 and g.M - 1 == g.nphi // 2:
+        b = out[g.M - 1]
+        h = b.copy()
+        for i, k in enumerate(g.kz):
+            h[i] = 0.5 * (b[i] + np.conj(b[idx[-int(k)]]))
+        out[g.M - 1] = h
+    if g.nz > 1 and g.Kz - 1 == g.nz // 2:
+        ip, im = idx[g.nz // 2], idx[-(g.nz // 2)]
+        for b in out:
+            avg = 0.5 * (b[ip] + b[im])
+            b[ip] = avg
+            b[im] = avg
+    return out
+
+
+@pytest.mark.parametrize("nr,nphi,nz", [(6, 4, 2), (9, 8, 4), (20, 16, 8), (33, 32, 16)])
+def test_nyquist_roundtrip_is_the_pair_projection(nr, nphi, nz):
+    g = O.Grid(nr, nphi, nz, 1.3, lz=5.0, policy="nyquist")
+    s = _rand_spec(g, 11)
+    back = O.forward(g, O.backward(g, s))
+    want = _nyquist_projection(g, s)
+    assert O.spec_rel_err(g, back, want) < 1e-13
+    # and the projection is the identity on its own image
+    again = O.forward(g, O.backward(g, want))
+    assert O.spec_rel_err(g, again, want) < 1e-13
+
+
+def test_nyquist_coefficient_matches_numpy_rfft():
+    # the stored Nyquist coefficient of a random grid function equals numpy's real
+    # DFT bin N/2 divided by 2N (Nz = 1, so only the azimuthal pair is involved)
+    g = O.Grid(10, 16, 1, 1.0, policy="nyquist")
+    rng = np.random.default_rng(4)
+    a = rng.standard_normal(g.nphi)
+    phys = a[None, :, None] * g.P[8][0][None, None, :]
+    s = O.forward(g, phys)
+    assert abs(s[8][0, 0] - np.fft.rfft(a)[8] / (2 * g.nphi)) < 1e-15
