@@ -510,24 +510,32 @@ def _qvortex_setup(B, W, torch, dev, n, ell, lz, prec, policy, dt, nu=1e-4, nu_h
     """Context and initial state (psi, chi) of the co-rotating q-vortex pair of
     Sec. 5.3 (b = 4, q = 1, U_z = -0.5): omega_z and v_z at the nodes, forward
     transforms, and the inverse Laplacians with the log-proxy amplitudes solved for
-    (net circulation 4 pi: c_psi = -1; net axial flux 2 pi: c_chi = -1/2)."""
+    (net circulation 4 pi: c_psi = -1; net axial flux 2 pi: c_chi = -1/2).  The
+    initial state is always built with FP64 transforms: the solved amplitude is the
+    source's planar integral, whose mapped area weight 1 / (1 - x)^2 magnifies
+    FP32 round-off at the outermost nodes (c_psi = -1.0094 instead of -1 from FP32
+    transforms at 256^3)."""
     import math as _m
     nr, nphi, nz = n
+    ic = B.Context(nr, nphi, nz, ell, lz=lz, precision=B.FP64, chop_policy=policy)
+    ic.vortex_setup()
+    x, w, r = ic.nodes()
+    phi = 2 * _m.pi * np.arange(nphi) / nphi
+    zz = lz * np.arange(nz) / nz
+    wz, vz = W.q_vortex_pair(r[None, None, :], phi[None, :, None], zz[:, None, None], lz=lz, amp=amp)
+    state = torch.zeros(2 * ic.n_spec, dtype=torch.complex128, device=dev)
+    cs = []
+    for f, sl in ((wz, slice(0, ic.n_spec)), (vz, slice(ic.n_spec, 2 * ic.n_spec))):
+        s = ic.forward(torch.as_tensor(f, dtype=torch.float64, device=dev), ic.new_spec())
+        out, c = ic.lap_h_solve_log(-s, ic.new_spec(), B.LOGPROXY_SOLVE)
+        state[sl] = out
+        cs.append(c)
+    ic.close()
+    del wz, vz
     ctx = B.Context(nr, nphi, nz, ell, lz=lz, precision=prec, chop_policy=policy)
     ctx.vortex_setup()
     ctx.implicit_setup(nu, dt, nu_h=nu_h, p=8)
     ctx.filter_setup()
-    x, w, r = ctx.nodes()
-    phi = 2 * _m.pi * np.arange(nphi) / nphi
-    zz = lz * np.arange(nz) / nz
-    wz, vz = W.q_vortex_pair(r[None, None, :], phi[None, :, None], zz[:, None, None], lz=lz, amp=amp)
-    state = torch.zeros(2 * ctx.n_spec, dtype=torch.complex128, device=dev)
-    cs = []
-    for f, sl in ((wz, slice(0, ctx.n_spec)), (vz, slice(ctx.n_spec, 2 * ctx.n_spec))):
-        s = ctx.forward(torch.as_tensor(f, dtype=ctx.phys_dtype, device=dev), ctx.new_spec())
-        out, c = ctx.lap_h_solve_log(-s, ctx.new_spec(), B.LOGPROXY_SOLVE)
-        state[sl] = out
-        cs.append(c)
     ctx.vortex_logproxy(cs[0], cs[1], Uz)
     return ctx, state, cs
 

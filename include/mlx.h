@@ -225,7 +225,10 @@ int mlx_lap_h_solve(mlx_ctx* ctx, const void* rhs, void* out, mlx_stream stream)
  *     Laplacian) replaced by lam; the unknown in its place is returned in *c (from
  *     the real part: the (0, 0) block of a real field is real), and x's Pbar_0^0
  *     coefficient is 0.
- * The two results differ only in that constant coefficient.  FP64, device
+ * The two results differ only in that constant coefficient.  The solved c is the
+ * source's planar integral over 4 pi, in which the mapped area weight
+ * 1 / (1 - x)^2 magnifies errors of rhs at the outermost nodes: form rhs with FP64
+ * transforms (at 256^3, FP32 transforms shift c by 1 %).  FP64, device
  * complex128 ragged buffers (may not alias); *c is a host double.  The solve
  * variant synchronises `stream`.  MLX_ESTATE before mlx_vortex_setup. */
 enum { MLX_LOGPROXY_PRESCRIBE = 0, MLX_LOGPROXY_SOLVE = 1 };
