@@ -465,6 +465,7 @@ def measure_crow(B, W, torch, dev, stream, t_end=60.0, dt=5e-3, grid="176x128x64
     done = 0
     t0 = time.perf_counter()
     status = "ok"
+    bad_step = None
     while done < nsteps:
         k = min(chunk, nsteps - done)
         ctx.advance(B.NONLIN_VORTEX, [U0], state, prev, k, done == 0)
@@ -473,8 +474,9 @@ def measure_crow(B, W, torch, dev, stream, t_end=60.0, dt=5e-3, grid="176x128x64
         ts.append(done * dt); E0.append(e[0]); E1.append(e[1]); E2.append(e[2] if len(e) > 2 else 0.0)
         d = ctx.vortex_diag(state)
         Z.append(d["enstrophy"]); WM.append(d["peak_vorticity"])
-        if not all(_m.isfinite(v) for v in e):
+        if not (all(_m.isfinite(v) for v in e) and _m.isfinite(d["enstrophy"])):
             status = "non-finite at t = %.3f" % (done * dt)
+            bad_step = done
             break
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
@@ -493,7 +495,8 @@ def measure_crow(B, W, torch, dev, stream, t_end=60.0, dt=5e-3, grid="176x128x64
     z15 = ctx.vortex_diag(st15)["enstrophy"]
     del wz15, ws15, st15
     out = {"workload": "crow_pair_%dx%dx%d" % (nr, nphi, nz), "precision": {B.BF16X3: "bf16x3", B.FP64: "fp64"}.get(prec),
-           "seed_amplitude_over_b": amp_b, "ell": ell, "dt": dt, "nu_h": nu_h, "steps": done, "t_end": done * dt, "wall_s": wall, "status": status,
+           "seed_amplitude_over_b": amp_b, "first_nonfinite_step": bad_step,
+           "ell": ell, "dt": dt, "nu_h": nu_h, "steps": done, "t_end": done * dt, "wall_s": wall, "status": status,
            "alpha_10_18": AN.growth_rate(ts, E1, b, gam, (10.0, 18.0)),
            "alpha_33_60": AN.growth_rate(ts, E1, b, gam, (33.0, 60.0)),
            "alpha_theory": AN.crow_alpha(beta, a / b), "beta": beta,
@@ -587,6 +590,34 @@ def measure_corot(B, W, torch, dev, stream, prec=None, t_end=10.0, every=0.5):
     for r in out["runs"]:
         r["rel_diff_vs_128x64x64_half_dt"] = abs(r["Z_t_end"] - ref) / abs(ref)
     return out
+
+
+def measure_fkpp_steps(B, W, torch, dev, stream, bench_steps=2):
+    """The benchmarked Fisher-KPP step alone (the headline workload's context,
+    BF16x3 contraction, FP32 FFTs, FP64 solve): bench_steps x 100 time steps from
+    t = 0, graph-replayed.  The command an ncu launch list of the step runs on."""
+    ctx = B.Context(NR, NPHI, NZ, ELL, lz=LZ, precision=B.BF16X3, chop_policy=B.CHOP_TWOTHIRDS)
+    ctx.implicit_setup(D_COEF, DT)
+    x, w, r = ctx.nodes()
+    phi = 2 * np.pi * np.arange(NPHI) / NPHI
+    zz = LZ * np.arange(NZ) / NZ
+    u0 = torch.as_tensor(W.fkpp_seed(r[None, None, :], phi[None, :, None], zz[:, None, None], seed=2),
+                         dtype=ctx.phys_dtype, device=dev)
+    s = ctx.forward(u0, ctx.new_spec())
+    a = ctx.new_spec()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(bench_steps):
+        ctx.advance(B.NONLIN_FKPP, [GAMMA], s, a, STEPS_PER_BENCH_STEP, i == 0)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    ctx.device_status()
+    ctx.close()
+    return {"workload": "fkpp3d_128x128x64_steps", "timesteps": bench_steps * STEPS_PER_BENCH_STEP,
+            "us_per_timestep": 1000.0 * ms / (bench_steps * STEPS_PER_BENCH_STEP),
+            "note": "includes the graph captures of the first call"}
 
 
 def measure_batch(B, W, torch, dev, stream, steps=100, n=64, tune_cache=None):
@@ -1035,7 +1066,8 @@ def main():
     ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "fp32", "fp64"],
                     help="transform arithmetic of the timed form (the FP64 form is always timed beside it)")
     ap.add_argument("--profile-workload", default=None,
-                    choices=["vortex", "vortex_long", "production", "production_fp64", "corot", "crow", "batch",
+                    choices=["vortex", "vortex_long", "production", "production_fp64", "corot", "fkpp_steps",
+                             "crow", "batch",
                              "surrogate", "surrogate_step"],
                     help="run only that secondary workload and print its measurement (for profiler captures; "
                          "not the benchmark line)")
@@ -1053,13 +1085,15 @@ def main():
               "vortex_long": lambda: measure_vortex_long(B, W, torch, dev, stream),
               "production": lambda: measure_production(B, W, torch, dev, stream),
               "corot": lambda: measure_corot(B, W, torch, dev, stream),
+              "fkpp_steps": lambda: measure_fkpp_steps(B, W, torch, dev, stream),
               "production_fp64": lambda: measure_production(B, W, torch, dev, stream, prec=B.FP64),
               "crow": lambda: measure_crow(B, W, torch, dev, stream, dt=float(os.environ.get("MLX_CROW_DT", "5e-3")),
                                            ell=float(os.environ.get("MLX_CROW_ELL", "2.0")),
                                            nu_h=float(os.environ.get("MLX_CROW_NUH", "5e-8")),
                                            amp_b=float(os.environ.get("MLX_CROW_AMP", "0.002")),
                                            grid=os.environ.get("MLX_CROW_GRID", "176x128x64"),
-                                           t_end=float(os.environ.get("MLX_CROW_TEND", "60"))),
+                                           t_end=float(os.environ.get("MLX_CROW_TEND", "60")),
+                                           every=float(os.environ.get("MLX_CROW_EVERY", "0.5"))),
               "batch": lambda: measure_batch(B, W, torch, dev, stream, tune_cache=args.tune_cache),
               "surrogate": lambda: measure_surrogate(torch),
               "surrogate_step": lambda: measure_surrogate_step()}[args.profile_workload]
