@@ -994,11 +994,21 @@ def run_gpu(args, rank, world):
 
     others = {}
     if not args.no_other_workloads:
+        def compact(d):
+            """The line keeps each workload's results, not its time histories."""
+            if isinstance(d, dict):
+                return {k: compact(v) for k, v in d.items() if k != "history"}
+            if isinstance(d, list):
+                return [compact(v) for v in d]
+            return d
         for name, fn in (("vortex", lambda: measure_vortex(B, W, torch, dev, stream)),
+                         ("production_256", lambda: measure_production(B, W, torch, dev, stream)),
                          ("batch", lambda: measure_batch(B, W, torch, dev, stream, tune_cache=args.tune_cache)),
-                         ("surrogate", lambda: measure_surrogate(torch))):
+                         ("surrogate", lambda: measure_surrogate(torch)),
+                         ("crow", lambda: measure_crow(B, W, torch, dev, stream)),
+                         ("corot_ladder", lambda: measure_corot(B, W, torch, dev, stream))):
             try:
-                others[name] = fn()
+                others[name] = compact(fn())
             except Exception as exc:   # reported, never hides the main line
                 others[name] = {"error": repr(exc)}
 

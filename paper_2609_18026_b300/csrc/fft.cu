@@ -50,56 +50,94 @@ __device__ __forceinline__ int bitrev(int p, int logn) {
   return logn ? (int)(__brev((unsigned)p) >> (32 - logn)) : 0;
 }
 
+template <typename T> __device__ __forceinline__ T fmaT(T a, T b, T c);
+template <> __device__ __forceinline__ float fmaT<float>(float a, float b, float c) { return fmaf(a, b, c); }
+template <> __device__ __forceinline__ double fmaT<double>(double a, double b, double c) { return fma(a, b, c); }
+
+// The CTA's copy of the twiddle table exp(-2 pi i t / N), t < N/2, in shared memory
+// (staged once per CTA, before the tile's first barrier).
+template <typename C>
+__device__ __forceinline__ void stage_twiddles(C* __restrict__ tws, const C* __restrict__ tw, int half) {
+  for (int t = threadIdx.x; t < half; t += blockDim.x) tws[t] = tw[t];
+}
+
 // Decimation in frequency: natural order in, bit-reversed order out.
-// j = lj + 32 e is the point held in v[e]; N = 32 E when E > 1, else N <= 32.
+// j = lj + 32 e is the point held in v[e]; N = 32 E when E > 1 (all strides then
+// compile-time constants), else N <= 32.  tw: the shared-memory twiddle copy.
+// Lane-exchange stage at distance d (the partner holds p): the lower lane keeps
+// v + p, the upper lane (p - v) w.  Both are written as (p + sgn v) weff with
+// sgn = +-1 and weff = 1 or w chosen once per stage, with no select per point.
 template <typename C, int E>
 __device__ __forceinline__ void dif(C (&v)[E], int N, int lj, const C* __restrict__ tw, bool inv) {
+  typedef decltype(C().x) T;
 #pragma unroll
   for (int de = E / 2; de >= 1; de >>= 1) {
-    const int d = 32 * de;
+    const int stride = E / (2 * de);                   // N / (2 d), d = 32 de
 #pragma unroll
     for (int e = 0; e < E; ++e) {
       if ((e & de) == 0) {
-        const int j = lj + 32 * e;
-        const C w = twid(tw, (j & (d - 1)) * (N / (2 * d)), inv);
+        const C w = twid(tw, (lj + 32 * (e & (de - 1))) * stride, inv);
         const C a = v[e], b = v[e + de];
         v[e] = cadd(a, b);
         v[e + de] = cmul(csub(a, b), w);
       }
     }
   }
-  for (int d = (N >= 32 ? 16 : N / 2); d >= 1; d >>= 1) {
-    const C w = twid(tw, (lj & (d - 1)) * (N / (2 * d)), inv);
+  auto stage = [&](int d, int stride) {
     const bool upper = (lj & d) != 0;
+    C w = twid(tw, (lj & (d - 1)) * stride, inv);
+    if (!upper) { w.x = (T)1; w.y = (T)0; }
+    const T sg = upper ? (T)-1 : (T)1;
 #pragma unroll
     for (int e = 0; e < E; ++e) {
       const C p = shfl_xor(v[e], d);
-      v[e] = upper ? cmul(csub(p, v[e]), w) : cadd(v[e], p);
+      C t;
+      t.x = fmaT(sg, v[e].x, p.x);
+      t.y = fmaT(sg, v[e].y, p.y);
+      v[e] = cmul(t, w);
     }
+  };
+  if constexpr (E > 1) {
+#pragma unroll
+    for (int d = 16; d >= 1; d >>= 1) stage(d, 16 * E / d);
+  } else {
+    for (int d = N >> 1, stride = 1; d >= 1; d >>= 1, stride <<= 1) stage(d, stride);
   }
 }
 
-// Decimation in time: bit-reversed order in, natural order out.
+// Decimation in time: bit-reversed order in, natural order out.  Lane-exchange
+// stage: the lower lane keeps v + w p, the upper lane p - w v, both as
+// r0 + sgn (w q) with (q, r0) = (p, v) or (v, p) chosen per lane.
 template <typename C, int E>
 __device__ __forceinline__ void dit(C (&v)[E], int N, int lj, const C* __restrict__ tw, bool inv) {
-  const int dmax = (N >= 32 ? 16 : N / 2);
-  for (int d = 1; d <= dmax; d <<= 1) {
-    const C w = twid(tw, (lj & (d - 1)) * (N / (2 * d)), inv);
+  typedef decltype(C().x) T;
+  auto stage = [&](int d, int stride) {
     const bool upper = (lj & d) != 0;
+    const C w = twid(tw, (lj & (d - 1)) * stride, inv);
+    const T sg = upper ? (T)-1 : (T)1;
 #pragma unroll
     for (int e = 0; e < E; ++e) {
       const C p = shfl_xor(v[e], d);
-      v[e] = upper ? csub(p, cmul(w, v[e])) : cadd(v[e], cmul(w, p));
+      const C q = upper ? v[e] : p;
+      const C r0 = upper ? p : v[e];
+      const C wq = cmul(w, q);
+      v[e].x = fmaT(sg, wq.x, r0.x);
+      v[e].y = fmaT(sg, wq.y, r0.y);
     }
+  };
+  if constexpr (E > 1) {
+#pragma unroll
+    for (int d = 1; d <= 16; d <<= 1) stage(d, 16 * E / d);
+  } else {
+    for (int d = 1, stride = N >> 1; d < N; d <<= 1, stride >>= 1) stage(d, stride);
   }
 #pragma unroll
   for (int de = 1; de <= E / 2; de <<= 1) {
-    const int d = 32 * de;
+    const int stride = E / (2 * de);
 #pragma unroll
     for (int e = 0; e < E; ++e) {
       if ((e & de) == 0) {
-        const int j = lj + 32 * e;
-        const C w = twid(tw, (j & (d - 1)) * (N / (2 * d)), inv);
+        const C w = twid(tw, (lj + 32 * (e & (de - 1))) * stride, inv);
         const C a = v[e], b = cmul(w, v[e + de]);
         v[e] = cadd(a, b);
         v[e + de] = csub(a, b);
@@ -205,6 +243,8 @@ __global__ void __launch_bounds__(256) k_phi(int N, int logN, int M, int Nr, int
   const int r0 = blockIdx.x * R;
   const int z = blockIdx.y;
   const long long plane = (long long)z * N * Nr;
+  C* tws = L + (size_t)B * ld;          // the twiddle copy after the tile
+  stage_twiddles(tws, tw, N >> 1);
 
   if constexpr (MODE == PHI_FWD) {
 #pragma unroll 8
@@ -220,7 +260,7 @@ __global__ void __launch_bounds__(256) k_phi(int N, int logN, int M, int Nr, int
       C v[E];
 #pragma unroll
       for (int e = 0; e < E; ++e) v[e] = act ? L[b * ld + lj + 32 * e] : C{};
-      dif<C, E>(v, N, lj, tw, false);
+      dif<C, E>(v, N, lj, tws, false);
       if (act) {
 #pragma unroll
         for (int e = 0; e < E; ++e) L[b * ld + lj + 32 * e] = v[e];   // bit-reversed order
@@ -266,14 +306,14 @@ __global__ void __launch_bounds__(256) k_phi(int N, int logN, int M, int Nr, int
 #pragma unroll
       for (int e = 0; e < E; ++e) v[e] = act ? L[b * ld + lj + 32 * e] : C{};
       if constexpr (MODE == PHI_BWD) {
-        dit<C, E>(v, N, lj, tw, true);   // bit-reversed spectrum in, physical values in natural order
+        dit<C, E>(v, N, lj, tws, true);   // bit-reversed spectrum in, physical values in natural order
         if (act) {
 #pragma unroll
           for (int e = 0; e < E; ++e) L[b * ld + lj + 32 * e] = v[e];
         }
         return;
       }
-      dif<C, E>(v, N, lj, tw, true);   // physical values, bit-reversed positions
+      dif<C, E>(v, N, lj, tws, true);   // physical values, bit-reversed positions
       if constexpr (MODE == PHI_FKPP) {
         bool finite = true;
 #pragma unroll
@@ -285,7 +325,7 @@ __global__ void __launch_bounds__(256) k_phi(int N, int logN, int M, int Nr, int
         // a non-finite product (blow-up or NaN in the state) sets the status bit
         // that mlx_device_status reports as MLX_ENUMERIC
         if (__any_sync(0xffffffffu, !finite) && (threadIdx.x & 31) == 0) atomicOr(err, 16);
-        dit<C, E>(v, N, lj, tw, false);   // forward DFT, natural order
+        dit<C, E>(v, N, lj, tws, false);   // forward DFT, natural order
         if (act) {
 #pragma unroll
           for (int e = 0; e < E; ++e) L[b * ld + lj + 32 * e] = v[e];
@@ -319,6 +359,8 @@ __global__ void __launch_bounds__(256) k_z(int Nz, int logN, int Kz, int K, int 
   const int r0 = blockIdx.x * R;
   const int m = blockIdx.y;
   const int lR = __ffs(R) - 1;          // R is a power of two
+  C* tws = L + (size_t)R * ld;          // the twiddle copy after the tile
+  stage_twiddles(tws, tw, Nz >> 1);
   if (!INVERSE) {
 #pragma unroll 8
     for (int t = threadIdx.x; t < Nz * R; t += blockDim.x) {
@@ -363,8 +405,8 @@ __global__ void __launch_bounds__(256) k_z(int Nz, int logN, int Kz, int K, int 
     // from the bit-reversed input, natural output.  Either way the dense line is
     // written back in register order, and only the K retained wavenumbers are
     // addressed through the bit reversal.
-    if (INVERSE) dit<C, E>(v, Nz, lj, tw, true);
-    else dif<C, E>(v, Nz, lj, tw, false);
+    if (INVERSE) dit<C, E>(v, Nz, lj, tws, true);
+    else dif<C, E>(v, Nz, lj, tws, false);
     if (act) {
 #pragma unroll
       for (int e = 0; e < E; ++e) L[b * ld + lj + 32 * e] = v[e];
@@ -458,7 +500,7 @@ int phi_launch(mlx_ctx* c, int mode, T* phys, T* zbase, const void* tw, double g
   typedef typename C2T<T>::type C;
   const int N = c->nphi;
   int R = c->phi_tile ? c->phi_tile : auto_tile(c->nr, c->nz, 2 * 148);
-  auto need = [&](int R_) { return (size_t)(R_ / 2) * (N + 1) * sizeof(C); };
+  auto need = [&](int R_) { return ((size_t)(R_ / 2) * (N + 1) + N / 2) * sizeof(C); };   // tile + twiddles
   while (need(R) > kSmemLimit && R > 2) R /= 2;
   const size_t smem = need(R);
   dim3 grid((c->nr + R - 1) / R, c->nz);
@@ -502,8 +544,13 @@ int z_launch(mlx_ctx* c, bool inverse, T* zbase, T* mbase, const void* tw, cudaS
              const SplitOut& so = SplitOut()) {
   typedef typename C2T<T>::type C;
   int R = c->z_tile ? c->z_tile : auto_tile(c->nr, c->M, 4 * 148);
-  auto need = [&](int R_) { return (size_t)R_ * (c->nz + 1) * sizeof(C); };
+  auto need = [&](int R_) { return ((size_t)R_ * (c->nz + 1) + c->nz / 2) * sizeof(C); };   // tile + twiddles
   while (need(R) > kSmemLimit && R > 1) R /= 2;
+  // automatic tiles keep at least 6 CTAs per SM (tiles <= 34 KB): at 256^3 the z
+  // kernels take 47.3 / 57.0 us (inverse / forward) with 66 KB tiles of 32 radii
+  // and 40.6 / 44.6 us with 16
+  if (!c->z_tile)
+    while (R > 8 && need(R) > 34 * 1024) R /= 2;
   const size_t smem = need(R);
   dim3 grid((c->nr + R - 1) / R, c->M);
   const int E = c->nz >= 32 ? c->nz / 32 : 1;
