@@ -54,11 +54,39 @@ template <typename T> __device__ __forceinline__ T fmaT(T a, T b, T c);
 template <> __device__ __forceinline__ float fmaT<float>(float a, float b, float c) { return fmaf(a, b, c); }
 template <> __device__ __forceinline__ double fmaT<double>(double a, double b, double c) { return fma(a, b, c); }
 
-// The CTA's copy of the twiddle table exp(-2 pi i t / N), t < N/2, in shared memory
-// (staged once per CTA, before the tile's first barrier).
+// The CTA's per-stage twiddle tables in shared memory (staged once per CTA, before
+// the tile's first barrier): the butterflies at distance d (d = N/2, ..., 1) use
+// exp(-2 pi i t (N / 2d) / N) for t < d, stored contiguously at offset N - 2d (N - 1
+// entries in all), so that the lanes of a stage read consecutive entries or one
+// entry (a strided read of the single table exp(-2 pi i t / N) conflicts on the
+// banks).  tw: the global table exp(-2 pi i t / N), t < N/2.
 template <typename C>
-__device__ __forceinline__ void stage_twiddles(C* __restrict__ tws, const C* __restrict__ tw, int half) {
-  for (int t = threadIdx.x; t < half; t += blockDim.x) tws[t] = tw[t];
+__device__ __forceinline__ void stage_twiddles(C* __restrict__ tws, const C* __restrict__ tw, int N) {
+  for (int u = threadIdx.x; u < N - 1; u += blockDim.x) {
+    int d = N >> 1, off = 0;
+    while (u >= off + d) { off += d; d >>= 1; }
+    tws[u] = tw[(u - off) * (N / (2 * d))];
+  }
+}
+// twiddle of stage d, index t < d, from the per-stage tables (conjugated for inverse)
+template <typename C>
+__device__ __forceinline__ C stw(const C* __restrict__ tws, int N, int d, int t, bool inv) {
+  return twid(tws, N - 2 * d + t, inv);
+}
+
+// asynchronous global -> shared copy of one element (4 or 8 bytes): the tile loads
+// keep every element in flight at once instead of staging them through registers
+template <typename T>
+__device__ __forceinline__ void cp_async_el(T* smem_dst, const T* gsrc) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  if constexpr (sizeof(T) == 4)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(gsrc) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_all() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
 }
 
 // Decimation in frequency: natural order in, bit-reversed order out.
@@ -72,20 +100,19 @@ __device__ __forceinline__ void dif(C (&v)[E], int N, int lj, const C* __restric
   typedef decltype(C().x) T;
 #pragma unroll
   for (int de = E / 2; de >= 1; de >>= 1) {
-    const int stride = E / (2 * de);                   // N / (2 d), d = 32 de
 #pragma unroll
     for (int e = 0; e < E; ++e) {
       if ((e & de) == 0) {
-        const C w = twid(tw, (lj + 32 * (e & (de - 1))) * stride, inv);
+        const C w = stw(tw, 32 * E, 32 * de, lj + 32 * (e & (de - 1)), inv);
         const C a = v[e], b = v[e + de];
         v[e] = cadd(a, b);
         v[e + de] = cmul(csub(a, b), w);
       }
     }
   }
-  auto stage = [&](int d, int stride) {
+  auto stage = [&](int d) {
     const bool upper = (lj & d) != 0;
-    C w = twid(tw, (lj & (d - 1)) * stride, inv);
+    C w = stw(tw, N, d, lj & (d - 1), inv);
     if (!upper) { w.x = (T)1; w.y = (T)0; }
     const T sg = upper ? (T)-1 : (T)1;
 #pragma unroll
@@ -99,9 +126,9 @@ __device__ __forceinline__ void dif(C (&v)[E], int N, int lj, const C* __restric
   };
   if constexpr (E > 1) {
 #pragma unroll
-    for (int d = 16; d >= 1; d >>= 1) stage(d, 16 * E / d);
+    for (int d = 16; d >= 1; d >>= 1) stage(d);
   } else {
-    for (int d = N >> 1, stride = 1; d >= 1; d >>= 1, stride <<= 1) stage(d, stride);
+    for (int d = N >> 1; d >= 1; d >>= 1) stage(d);
   }
 }
 
@@ -111,9 +138,9 @@ __device__ __forceinline__ void dif(C (&v)[E], int N, int lj, const C* __restric
 template <typename C, int E>
 __device__ __forceinline__ void dit(C (&v)[E], int N, int lj, const C* __restrict__ tw, bool inv) {
   typedef decltype(C().x) T;
-  auto stage = [&](int d, int stride) {
+  auto stage = [&](int d) {
     const bool upper = (lj & d) != 0;
-    const C w = twid(tw, (lj & (d - 1)) * stride, inv);
+    const C w = stw(tw, N, d, lj & (d - 1), inv);
     const T sg = upper ? (T)-1 : (T)1;
 #pragma unroll
     for (int e = 0; e < E; ++e) {
@@ -127,17 +154,16 @@ __device__ __forceinline__ void dit(C (&v)[E], int N, int lj, const C* __restric
   };
   if constexpr (E > 1) {
 #pragma unroll
-    for (int d = 1; d <= 16; d <<= 1) stage(d, 16 * E / d);
+    for (int d = 1; d <= 16; d <<= 1) stage(d);
   } else {
-    for (int d = 1, stride = N >> 1; d < N; d <<= 1, stride >>= 1) stage(d, stride);
+    for (int d = 1; d < N; d <<= 1) stage(d);
   }
 #pragma unroll
   for (int de = 1; de <= E / 2; de <<= 1) {
-    const int stride = E / (2 * de);
 #pragma unroll
     for (int e = 0; e < E; ++e) {
       if ((e & de) == 0) {
-        const C w = twid(tw, (lj + 32 * (e & (de - 1))) * stride, inv);
+        const C w = stw(tw, 32 * E, 32 * de, lj + 32 * (e & (de - 1)), inv);
         const C a = v[e], b = cmul(w, v[e + de]);
         v[e] = cadd(a, b);
         v[e + de] = csub(a, b);
@@ -243,18 +269,18 @@ __global__ void __launch_bounds__(256) k_phi(int N, int logN, int M, int Nr, int
   const int r0 = blockIdx.x * R;
   const int z = blockIdx.y;
   const long long plane = (long long)z * N * Nr;
-  C* tws = L + (size_t)B * ld;          // the twiddle copy after the tile
-  stage_twiddles(tws, tw, N >> 1);
+  C* tws = L + (size_t)B * ld;          // the twiddle tables after the tile
+  stage_twiddles(tws, tw, N);
 
   if constexpr (MODE == PHI_FWD) {
-#pragma unroll 8
     for (int t = threadIdx.x; t < N * R; t += blockDim.x) {
       const int j = t >> lR, rr = t & (R - 1);
       const int r = r0 + rr;
-      const T v = (r < Nr) ? phys[plane + (long long)j * Nr + r] : (T)0;
-      T* slot = reinterpret_cast<T*>(&L[(rr & (B - 1)) * ld + j]);
-      slot[rr < B ? 0 : 1] = v;
+      T* slot = reinterpret_cast<T*>(&L[(rr & (B - 1)) * ld + j]) + (rr < B ? 0 : 1);
+      if (r < Nr) cp_async_el(slot, phys + plane + (long long)j * Nr + r);
+      else *slot = (T)0;
     }
+    cp_async_all();
     __syncthreads();
     for_lines(N, B, [&](int b, int lj, bool act) {
       C v[E];
@@ -359,20 +385,23 @@ __global__ void __launch_bounds__(256) k_z(int Nz, int logN, int Kz, int K, int 
   const int r0 = blockIdx.x * R;
   const int m = blockIdx.y;
   const int lR = __ffs(R) - 1;          // R is a power of two
-  C* tws = L + (size_t)R * ld;          // the twiddle copy after the tile
-  stage_twiddles(tws, tw, Nz >> 1);
+  C* tws = L + (size_t)R * ld;          // the twiddle tables after the tile
+  stage_twiddles(tws, tw, Nz);
   if (!INVERSE) {
-#pragma unroll 8
     for (int t = threadIdx.x; t < Nz * R; t += blockDim.x) {
       const int l = t >> lR, b = t & (R - 1);
       const int r = r0 + b;
-      C v; v.x = 0; v.y = 0;
+      C* slot = &L[b * ld + l];
       if (r < Nr) {
         const long long o = ((long long)l * M + m) * Nr + r;
-        v.x = zre[o]; v.y = zim[o];
+        cp_async_el(&slot->x, zre + o);
+        cp_async_el(&slot->y, zim + o);
+      } else {
+        slot->x = 0;
+        slot->y = 0;
       }
-      L[b * ld + l] = v;
     }
+    cp_async_all();
   } else {
     for (int t = threadIdx.x; t < R * ld; t += blockDim.x) L[t] = C{};
     __syncthreads();
@@ -386,15 +415,20 @@ __global__ void __launch_bounds__(256) k_z(int Nz, int logN, int Kz, int K, int 
       const int pos = (kk < Kz) ? kk : Nz - (K - kk);
       if (r < Nr && !(nyq && kk == Kz)) {
         const long long o = ((long long)kk * M + m) * Nr + r;
-        C v; v.x = mre[o]; v.y = mim[o];
+        C* slot = &L[b * ld + bitrev(pos, logN)];   // bit-reversed input of the DIT below
         if (nyq && kk == Kz - 1) {
           const long long o2 = ((long long)Kz * M + m) * Nr + r;
-          v.x += mre[o2];
-          v.y += mim[o2];
+          C v;
+          v.x = mre[o] + mre[o2];
+          v.y = mim[o] + mim[o2];
+          *slot = v;
+        } else {
+          cp_async_el(&slot->x, mre + o);
+          cp_async_el(&slot->y, mim + o);
         }
-        L[b * ld + bitrev(pos, logN)] = v;   // bit-reversed input of the DIT below
       }
     }
+    cp_async_all();
   }
   __syncthreads();
   for_lines(Nz, R, [&](int b, int lj, bool act) {
@@ -500,7 +534,7 @@ int phi_launch(mlx_ctx* c, int mode, T* phys, T* zbase, const void* tw, double g
   typedef typename C2T<T>::type C;
   const int N = c->nphi;
   int R = c->phi_tile ? c->phi_tile : auto_tile(c->nr, c->nz, 2 * 148);
-  auto need = [&](int R_) { return ((size_t)(R_ / 2) * (N + 1) + N / 2) * sizeof(C); };   // tile + twiddles
+  auto need = [&](int R_) { return ((size_t)(R_ / 2) * (N + 1) + N) * sizeof(C); };   // tile + twiddles
   while (need(R) > kSmemLimit && R > 2) R /= 2;
   const size_t smem = need(R);
   dim3 grid((c->nr + R - 1) / R, c->nz);
@@ -544,7 +578,7 @@ int z_launch(mlx_ctx* c, bool inverse, T* zbase, T* mbase, const void* tw, cudaS
              const SplitOut& so = SplitOut()) {
   typedef typename C2T<T>::type C;
   int R = c->z_tile ? c->z_tile : auto_tile(c->nr, c->M, 4 * 148);
-  auto need = [&](int R_) { return ((size_t)R_ * (c->nz + 1) + c->nz / 2) * sizeof(C); };   // tile + twiddles
+  auto need = [&](int R_) { return ((size_t)R_ * (c->nz + 1) + c->nz) * sizeof(C); };   // tile + twiddles
   while (need(R) > kSmemLimit && R > 1) R /= 2;
   // automatic tiles keep at least 6 CTAs per SM (tiles <= 34 KB): at 256^3 the z
   // kernels take 47.3 / 57.0 us (inverse / forward) with 66 KB tiles of 32 radii
