@@ -199,10 +199,11 @@ FP64_PEAK_TFLOPS = 1.20
 
 # DRAM bytes (read + write) per launch of the dominant kernel at this workload, from
 # one ncu capture of the current kernel version (None = not captured for it):
-# k_band_solve_seg<2, 8, 1> (the pivot-free segmented solve), dram__bytes_read.sum
-# 21,159,424 and dram__bytes_write.sum 0 (its output stays in L2) in each of three
-# captured launches of `--profile-workload fkpp_steps`
-TRAFFIC = {"band_solve": 21159424}
+# k_band_solve_seg<2, 8, 1> (the pivot-free segmented solve, staging one contiguous
+# record per system row), dram__bytes_read.sum 17,905,152 and dram__bytes_write.sum 0
+# (its output stays in L2) in each of three captured launches of
+# `--profile-workload fkpp_steps`
+TRAFFIC = {"band_solve": 17905152}
 
 
 def band_solve_flops(ctx, kl=2):

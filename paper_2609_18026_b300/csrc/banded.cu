@@ -598,13 +598,45 @@ template <int KL, int SEG>
 struct SegSmem {
   static constexpr int W = 2 * KL + 1;
   static constexpr int CPW = 32 / SEG, G = CPW / 4;
-  // doubles per row and |k|: U (W), L (KL), 1/diag, PHf (KL), PHb (2 KL)
-  __host__ __device__ static size_t per_warp(int nc, int keep_s) {
-    const size_t d = (size_t)nc * G * (W + KL + 1 + KL + 2 * KL) + (size_t)G * SEG * KL * KL +
+  // pivot-free record: L (KL), 1/diag, U upper (KL), PHf (KL), PHb (KL), padded to
+  // an even count (16-byte records)
+  static constexpr int RW = (4 * KL + 1 + 1) & ~1;
+  static constexpr int RO_L = 0, RO_D = KL, RO_U = KL + 1, RO_F = 2 * KL + 1, RO_B = 3 * KL + 1;
+  // doubles per row and |k|: U (W), L (KL), 1/diag, PHf (KL), PHb (2 KL); or the
+  // pivot-free record (RW, no pivot rows)
+  __host__ __device__ static size_t per_warp(int nc, int keep_s, bool np = false) {
+    const size_t rowd = np ? (size_t)RW : (size_t)(W + KL + 1 + KL + 2 * KL);
+    const size_t d = (size_t)nc * G * rowd + (size_t)G * SEG * KL * KL +
                      (size_t)nc * CPW * (keep_s ? 2 : 1) + (size_t)SEG * CPW * (3 * KL + 2 * KL);
-    return (d * sizeof(double) + (size_t)nc * G * sizeof(int) + 15) / 16 * 16;
+    return (d * sizeof(double) + (np ? 0 : (size_t)nc * G * sizeof(int)) + 15) / 16 * 16;
   }
 };
+
+// Pivot-free records of one family (see BandLU::RNP): thread = (m, |k| x row).
+template <int KL>
+__global__ void k_pack_seg_np(int nc, int Kz, const long long* __restrict__ off, const double* __restrict__ U,
+                              const double* __restrict__ Lm, const double* __restrict__ invd,
+                              const double* __restrict__ PHf, const double* __restrict__ PHb,
+                              double* __restrict__ RNP) {
+  using SM = SegSmem<KL, 8>;
+  constexpr int W = 2 * KL + 1, RW = SM::RW;
+  const int m = blockIdx.y;
+  const int Nm = nc - m;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)Kz * Nm) return;
+  const int kabs = (int)(t / Nm), i = (int)(t % Nm);
+  const long long R = off[m] + (long long)i * Kz + kabs;       // factor row
+  double* rec = RNP + (off[m] + (long long)kabs * Nm + i) * RW;
+#pragma unroll
+  for (int q = 0; q < KL; ++q) {
+    rec[SM::RO_L + q] = Lm[R * KL + q];
+    rec[SM::RO_U + q] = U[R * W + q + 1];
+    rec[SM::RO_F + q] = PHf[R * KL + q];
+    rec[SM::RO_B + q] = PHb[R * 2 * KL + q];
+  }
+  rec[SM::RO_D] = invd[R];
+  for (int q = 4 * KL + 1; q < RW; ++q) rec[q] = 0.0;
+}
 
 // rows [j0, j1) of segment s of an N-row chain: SEG - 1 segments of floor(N / SEG)
 // rows, the last takes the rest
@@ -684,10 +716,11 @@ __global__ void k_band_solve_seg(int M, int nc, int Kz, int K, int groups_per_m,
                                  const double* __restrict__ Lm, const int* __restrict__ piv,
                                  const double* __restrict__ invd, const double* __restrict__ PHf,
                                  const double* __restrict__ PHb, const double* __restrict__ PSf,
+                                 const double* __restrict__ RNP,
                                  const double* __restrict__ s, const double* __restrict__ A,
                                  const double* __restrict__ Ap, double* __restrict__ out) {
   using SM = SegSmem<KL, SEG>;
-  constexpr int W = SM::W, CPW = SM::CPW, G = SM::G;
+  constexpr int W = SM::W, CPW = SM::CPW, G = SM::G, RW = SM::RW;
   constexpr int UW = NP ? KL : 2 * KL;                      // upper entries the substitution reads
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -697,13 +730,16 @@ __global__ void k_band_solve_seg(int M, int nc, int Kz, int K, int groups_per_m,
   const int k0 = (gw % groups_per_m) * G;
   const int gcnt = min(G, Kz - k0);
   const int N = nc - m;
-  unsigned char* base = smem_raw + (size_t)wib * SM::per_warp(nc, keep_s);
-  double* Us = reinterpret_cast<double*>(base);              // [N][G][W]
-  double* Ls = Us + (size_t)N * G * W;                       // [N][G][KL]
-  double* Ds = Ls + (size_t)N * G * KL;                      // [N][G]
-  double* Pf = Ds + (size_t)N * G;                           // [N][G][KL]
-  double* Pb = Pf + (size_t)N * G * KL;                      // [N][G][2KL]
-  double* PS = Pb + (size_t)N * G * 2 * KL;                  // [G][SEG][KL][KL]
+  unsigned char* base = smem_raw + (size_t)wib * SM::per_warp(nc, keep_s, NP);
+  // pivoting form: U [N][G][W], L [N][G][KL], 1/diag [N][G], PHf [N][G][KL],
+  // PHb [N][G][2KL]; pivot-free form: the records [G][N][RW]
+  double* Us = reinterpret_cast<double*>(base);
+  double* Ls = Us + (size_t)N * G * W;
+  double* Ds = Ls + (size_t)N * G * KL;
+  double* Pf = Ds + (size_t)N * G;
+  double* Pb = Pf + (size_t)N * G * KL;
+  double* Rs = reinterpret_cast<double*>(base);
+  double* PS = NP ? Rs + (size_t)G * N * RW : Pb + (size_t)N * G * 2 * KL;   // [G][SEG][KL][KL]
   double* Y = PS + (size_t)G * SEG * KL * KL;                // [N][CPW]
   double* Sv = Y + (size_t)N * CPW;                          // [N][CPW] (keep_s)
   double* BH = Sv + (keep_s ? (size_t)N * CPW : 0);          // [SEG][KL][CPW] right-hand side heads
@@ -713,7 +749,13 @@ __global__ void k_band_solve_seg(int M, int nc, int Kz, int K, int groups_per_m,
   int* Pi = reinterpret_cast<int*>(SB + SEG * 2 * KL * CPW); // [N][G]
   const long long fb = band_off[m];
   const long long sm = soff[m];
-  {
+  if constexpr (NP) {
+    // the warp's gcnt systems are consecutive blocks of N records
+    const int bytes = gcnt * N * RW * 8;
+    stage_rows(Rs, bytes, RNP + (fb + (long long)k0 * N) * RW, bytes, 1, bytes, lane);
+    stage_rows(PS, G * SEG * KL * KL * 8, PSf + ((long long)m * Kz + k0) * SEG * KL * KL, 0, 1,
+               gcnt * SEG * KL * KL * 8, lane);
+  } else {
     const long long r0 = fb + k0;
     stage_rows(Us, G * W * 8, U + r0 * W, (long long)Kz * W * 8, N, gcnt * W * 8, lane);
     stage_rows(Ls, G * KL * 8, Lm + r0 * KL, (long long)Kz * KL * 8, N, gcnt * KL * 8, lane);
@@ -722,8 +764,24 @@ __global__ void k_band_solve_seg(int M, int nc, int Kz, int K, int groups_per_m,
     stage_rows(Pb, G * 2 * KL * 8, PHb + r0 * 2 * KL, (long long)Kz * 2 * KL * 8, N, gcnt * 2 * KL * 8, lane);
     stage_rows(PS, G * SEG * KL * KL * 8, PSf + ((long long)m * Kz + k0) * SEG * KL * KL, 0, 1,
                gcnt * SEG * KL * KL * 8, lane);
-    if (!NP) stage_rows(Pi, G * 4, piv + r0, (long long)Kz * 4, N, gcnt * 4, lane);
+    stage_rows(Pi, G * 4, piv + r0, (long long)Kz * 4, N, gcnt * 4, lane);
   }
+  // operand accessors: row i of system kq
+  auto Lrow = [&](int i, int kq) -> const double* {
+    return NP ? Rs + ((size_t)kq * N + i) * RW + SM::RO_L : Ls + ((size_t)i * G + kq) * KL;
+  };
+  auto Dval = [&](int i, int kq) -> double {
+    return NP ? Rs[((size_t)kq * N + i) * RW + SM::RO_D] : Ds[(size_t)i * G + kq];
+  };
+  auto Uup = [&](int i, int kq, int t) -> double {     // U_{i, i+1+t}
+    return NP ? Rs[((size_t)kq * N + i) * RW + SM::RO_U + t] : Us[((size_t)i * G + kq) * W + t + 1];
+  };
+  auto PFrow = [&](int i, int kq) -> const double* {
+    return NP ? Rs + ((size_t)kq * N + i) * RW + SM::RO_F : Pf + ((size_t)i * G + kq) * KL;
+  };
+  auto PBrow = [&](int i, int kq) -> const double* {
+    return NP ? Rs + ((size_t)kq * N + i) * RW + SM::RO_B : Pb + ((size_t)i * G + kq) * 2 * KL;
+  };
   cp_async_commit();
   // right-hand sides, every lane busy (as in k_band_solve)
   const double h = (step == MLX_STEP_FEBE_FULL) ? dt : 0.5 * dt;
@@ -805,7 +863,7 @@ __global__ void k_band_solve_seg(int M, int nc, int Kz, int K, int groups_per_m,
           if (q == d) { const double t = w[0]; w[0] = w[q]; w[q] = t; }
       }
       y[(size_t)j * CPW] = w[0];
-      const double* l = Ls + ((size_t)j * G + kk) * KL;
+      const double* l = Lrow(j, kk);
 #pragma unroll
       for (int q = 1; q <= KL; ++q) w[q] = __fma_rn(-l[q - 1], w[0], w[q]);
     }
@@ -834,7 +892,7 @@ __global__ void k_band_solve_seg(int M, int nc, int Kz, int K, int groups_per_m,
 #pragma unroll
     for (int q = 0; q < KL; ++q) wv[q] = SF[(sg * KL + q) * CPW + c];
     for (int j = j0; j < j1; ++j) {
-      const double* pf = Pf + ((size_t)j * G + kk) * KL;
+      const double* pf = PFrow(j, kk);
       double v = y[(size_t)j * CPW];
 #pragma unroll
       for (int q = 0; q < KL; ++q) v = __fma_rn(pf[q], wv[q], v);
@@ -843,7 +901,7 @@ __global__ void k_band_solve_seg(int M, int nc, int Kz, int K, int groups_per_m,
   }
   __syncwarp();
   for (int i = il; i < (lane_piece ? N : 0); i += LP) {
-    const double dv = Ds[(size_t)i * G + kql];
+    const double dv = Dval(i, kql);
     Y[(size_t)i * CPW + cpl * 2] = __dmul_rn(Y[(size_t)i * CPW + cpl * 2], dv);
     Y[(size_t)i * CPW + cpl * 2 + 1] = __dmul_rn(Y[(size_t)i * CPW + cpl * 2 + 1], dv);
   }
@@ -859,10 +917,10 @@ __global__ void k_band_solve_seg(int M, int nc, int Kz, int K, int groups_per_m,
     double xn = 0.0;
 #pragma unroll 2
     for (int i = j1 - 1; i >= j0; --i) {
-      const double xi = __fma_rn(-Us[((size_t)i * G + kk) * W + 1], xn, acc[0]);
+      const double xi = __fma_rn(-Uup(i, kk, 0), xn, acc[0]);
 #pragma unroll
       for (int t = 1; t < UW; ++t)
-        if (i - t >= j0) acc[t] = __fma_rn(-Us[((size_t)(i - t) * G + kk) * W + t + 1], xn, acc[t]);
+        if (i - t >= j0) acc[t] = __fma_rn(-Uup(i - t, kk, t), xn, acc[t]);
       y[(size_t)i * CPW] = xi;
 #pragma unroll
       for (int t = 0; t < UW - 1; ++t) acc[t] = acc[t + 1];
@@ -882,7 +940,7 @@ __global__ void k_band_solve_seg(int M, int nc, int Kz, int K, int groups_per_m,
         const int r = a0 + t;
         double v = y[(size_t)r * CPW];
         if (ss + 1 < SEG - 1) {
-          const double* pb = Pb + ((size_t)r * G + kk) * 2 * KL;
+          const double* pb = PBrow(r, kk);
 #pragma unroll
           for (int t2 = 0; t2 < UW; ++t2) v = __fma_rn(pb[t2], SB[((ss + 1) * 2 * KL + t2) * CPW + c], v);
         }
@@ -897,7 +955,7 @@ __global__ void k_band_solve_seg(int M, int nc, int Kz, int K, int groups_per_m,
 #pragma unroll
     for (int t = 0; t < UW; ++t) vv[t] = SB[(sg * 2 * KL + t) * CPW + c];
     for (int i = j0; i < j1; ++i) {
-      const double* pb = Pb + ((size_t)i * G + kk) * 2 * KL;
+      const double* pb = PBrow(i, kk);
       double v = y[(size_t)i * CPW];
 #pragma unroll
       for (int t = 0; t < UW; ++t) v = __fma_rn(pb[t], vv[t], v);
@@ -944,7 +1002,7 @@ int mlx_band_setup(mlx_ctx* c, cudaStream_t st) {
   cudaFree(c->lu_full.U); cudaFree(c->lu_full.L); cudaFree(c->lu_full.piv); cudaFree(c->lu_full.invd);
   for (BandLU* f : {&c->lu_half, &c->lu_full}) {
     cudaFree(f->FS); cudaFree(f->BS);
-    cudaFree(f->PHf); cudaFree(f->PHb); cudaFree(f->PSf);
+    cudaFree(f->PHf); cudaFree(f->PHb); cudaFree(f->PSf); cudaFree(f->RNP);
   }
   c->d_Bplus = nullptr;
   c->lu_half = BandLU();
@@ -1341,17 +1399,18 @@ static int launch_solve(mlx_ctx* c, int step, const BandLU& f, const long long* 
       const int keep_s = (step == MLX_STEP_ABCN && c->solve_keep_s) ? 1 : 0;
       auto go = [&](auto seg_tag) -> bool {
         constexpr int S = decltype(seg_tag)::value;
-        const size_t pw = SegSmem<KL, S>::per_warp(c->nc, keep_s);
+        const bool np = f.nopiv && f.RNP;
+        const size_t pw = SegSmem<KL, S>::per_warp(c->nc, keep_s, np);
         int WPB = S;                                // S warps per CTA, halved until the CTA fits 200 KB
         while (WPB > 1 && pw * WPB > 200 * 1024) WPB /= 2;
         if (pw * WPB > 200 * 1024) return false;
         const int G = SegSmem<KL, S>::G;
         const int gpm = (c->Kz + G - 1) / G;
         const int warps = c->M * gpm;
-        auto kern = f.nopiv ? k_band_solve_seg<KL, S, true> : k_band_solve_seg<KL, S, false>;
+        auto kern = np ? k_band_solve_seg<KL, S, true> : k_band_solve_seg<KL, S, false>;
         kern<<<(warps + WPB - 1) / WPB, 32 * WPB, pw * WPB, st>>>(
             c->M, c->nc, c->Kz, c->K, gpm, step, keep_s, c->dt, c->d_soff, fac_off, f.U, f.L, f.piv, f.invd,
-            f.PHf, f.PHb, f.PSf, (const double*)s, (const double*)A, (const double*)Ap, (double*)out);
+            f.PHf, f.PHb, f.PSf, f.RNP, (const double*)s, (const double*)A, (const double*)Ap, (double*)out);
         return true;
       };
       if (f.seg == 8 ? go(std::integral_constant<int, 8>()) : go(std::integral_constant<int, 4>())) return MLX_OK;
@@ -1505,8 +1564,8 @@ static int set_lean_attrs(mlx_ctx* c, int lim) {
 // 2 kl rows (S = 8 falls back to 4 when the shortest chain is too short); otherwise
 // the family keeps none and the staged solve runs.
 int mlx_seg_build(mlx_ctx* c, BandLU& f, int S, cudaStream_t st) {
-  cudaFree(f.PHf); cudaFree(f.PHb); cudaFree(f.PSf);
-  f.PHf = f.PHb = f.PSf = nullptr;
+  cudaFree(f.PHf); cudaFree(f.PHb); cudaFree(f.PSf); cudaFree(f.RNP);
+  f.PHf = f.PHb = f.PSf = f.RNP = nullptr;
   f.seg = 0;
   const int kl = c->kl;
   if (S == 8 && (c->nc - (c->M - 1)) / 8 < 2 * kl) S = 4;   // chains too short for 8 segments
@@ -1523,6 +1582,12 @@ int mlx_seg_build(mlx_ctx* c, BandLU& f, int S, cudaStream_t st) {
     k_seg_setup<2, 4><<<(unsigned)((nt + 127) / 128), 128, 0, st>>>(c->M, c->nc, c->Kz, c->d_band_off, f.U,
                                                                     f.L, f.piv, f.PHf, f.PHb, f.PSf);
   MLX_LAUNCH_CHECK(c);
+  if (f.nopiv) {
+    MLX_CUDA_TRY(c, cudaMalloc(&f.RNP, sizeof(double) * rows * SegSmem<2, 8>::RW));
+    dim3 grid((unsigned)(((long long)c->Kz * c->nc + 127) / 128), c->M);
+    k_pack_seg_np<2><<<grid, 128, 0, st>>>(c->nc, c->Kz, c->d_band_off, f.U, f.L, f.invd, f.PHf, f.PHb, f.RNP);
+    MLX_LAUNCH_CHECK(c);
+  }
   f.seg = S;
   return MLX_OK;
 }

@@ -68,6 +68,10 @@ struct BandLU {
   double* PSf = nullptr;
   int seg = 0;             // segments the influence data were built for (0 = none)
   bool nopiv = false;      // no system of the family interchanged rows (segmented solve skips pivoting)
+  // pivot-free segmented solve: one contiguous record per system row, the system's
+  // rows back to back ([m][|k|][row], record = {L[kl], 1/diag, U upper[kl], PHf[kl],
+  // PHb[kl], pad}), so that a warp stages its systems as one block
+  double* RNP = nullptr;
 };
 
 struct mlx_ctx {
