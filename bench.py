@@ -371,6 +371,28 @@ def measure_production(B, W, torch, dev, stream, prec=None, steps=30, dt=1e-2):
     kt = ctx.timing_read()
     ctx.timing(0)
     tot = sum(v[1] for v in kt.values())
+    errs = {}
+    if prec != B.FP64:
+        # per result against the FP64 form at the same state: the nonlinear term
+        # and one AB-CN step
+        c64 = B.Context(256, 256, 256, 4.0, lz=2.0 * _m.pi, precision=B.FP64, chop_policy=B.CHOP_NYQUIST)
+        c64.vortex_setup()
+        c64.implicit_setup(1e-4, dt, nu_h=5e-7, p=8)
+        c64.vortex_logproxy(cs[0], cs[1], -0.5)
+
+        def rel2(a_, b_):
+            return float(torch.linalg.norm(a_ - b_).item() / torch.linalg.norm(b_).item())
+        n_mix = ctx.nonlinear(B.NONLIN_VORTEX, [0.0], state, torch.zeros_like(state))
+        n_64 = c64.nonlinear(B.NONLIN_VORTEX, [0.0], state, torch.zeros_like(state))
+        errs["nonlinear_rel_err_vs_fp64"] = rel2(n_mix, n_64)
+        s_a, p_a = state.clone(), prev.clone()
+        s_b, p_b = state.clone(), prev.clone()
+        ctx.advance(B.NONLIN_VORTEX, [0.0], s_a, p_a, 1, False)
+        c64.advance(B.NONLIN_VORTEX, [0.0], s_b, p_b, 1, False)
+        errs["state_rel_err_vs_fp64"] = rel2(s_a, s_b)
+        c64.device_status()
+        c64.close()
+        del n_mix, n_64, s_a, p_a, s_b, p_b
     out = {"workload": "production_256^3_corot_qvortex_nyquist_chop",
            "precision": {B.BF16X3: "bf16x3", B.FP64: "fp64"}.get(prec),
            "M": ctx.M, "Kz": ctx.Kz, "coefficients_per_potential": ctx.n_spec, "steps": steps, "dt": dt,
@@ -380,6 +402,7 @@ def measure_production(B, W, torch, dev, stream, prec=None, steps=30, dt=1e-2):
            "filter": ctx.filter_state(),
            "kernel_share": {k: round(v[1] / tot, 3) for k, v in kt.items()},
            "paper_table3_s_per_30_steps": {"16_ranks": 410.1, "512_ranks": 30.4}}
+    out.update(errs)
     ctx.close()
     return out
 

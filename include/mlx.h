@@ -384,6 +384,10 @@ int mlx_set_state(mlx_ctx* ctx, int kind, const void* host, long long bytes, voi
  *                bitwise; 0 = off.
  *   "solve_lean_cpw": real chains per warp of the lean variant, 16 or 32
  *                (default 32).
+ *   "solve_fields2": 1 (default) = the lean variant solves both fields of a
+ *                vortex state in one launch (each staged factor record serves
+ *                the 8 real chains of both fields at one |k|, so a step reads the
+ *                factors once); 0 = one launch per field.  Bitwise-equal results.
  *   "tc_bn":     column-tile width of the MLX_BF16X3 contraction (16..256, used
  *                up to 128; the width actually used is rounded to a multiple of 16
  *                that splits the 2K columns evenly);

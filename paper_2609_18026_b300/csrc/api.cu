@@ -79,9 +79,12 @@ int nonlinear_into(mlx_ctx* c, int kind, double c0, const double2* s, double2* A
 
 int nfields(int kind) { return kind == MLX_NONLIN_VORTEX ? 2 : 1; }
 
-// implicit step applied to every field of the state (fields share the factors)
+// implicit step applied to every field of the state (fields share the factors; the
+// lean solve takes both fields of a vortex state in one launch, reading the factors once)
 int solve_fields(mlx_ctx* c, int kind, int step, const double2* s, const double2* A, const double2* Ap,
                  double2* out, cudaStream_t st) {
+  if (nfields(kind) == 2 && c->solve_direct == 2 && c->solve_fields2)
+    return mlx_band_solve(c, step, s, A, Ap, out, st, 2);
   for (int f = 0; f < nfields(kind); ++f) {
     const long long o = (long long)f * c->n_spec;
     int rc = mlx_band_solve(c, step, s + o, A ? A + o : nullptr, Ap ? Ap + o : nullptr, out + o, st);
@@ -463,6 +466,12 @@ int mlx_set_tuning(mlx_ctx* c, const char* key, int value) {
   if (strcmp(key, "solve_lean_cpw") == 0) {
     if (value != 16 && value != 32) return MLX_EINVAL;
     c->solve_lean_cpw = value;
+    mlx_invalidate_graphs(c);
+    return MLX_OK;
+  }
+  if (strcmp(key, "solve_fields2") == 0) {
+    if (value != 0 && value != 1) return MLX_EINVAL;
+    c->solve_fields2 = value;
     mlx_invalidate_graphs(c);
     return MLX_OK;
   }

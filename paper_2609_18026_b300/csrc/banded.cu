@@ -1082,9 +1082,9 @@ int mlx_band_setup(mlx_ctx* c, cudaStream_t st) {
 constexpr int LEAN_AHEAD = 12;
 constexpr int LEAN_PLAIN = 0, LEAN_FEBE = 1, LEAN_ABCN = 2;   // right-hand side s, s + h A, AB-CN
 
-template <int KL, int CPW>
+template <int KL, int CPW, int NFLD = 1>
 struct LeanSmem {
-  static constexpr int G = CPW / 4;                   // |k| values per warp
+  static constexpr int G = CPW / (4 * NFLD);          // |k| values per warp (4 NFLD real chains each)
   static constexpr int NP = CPW / 2;                  // complex pieces per row
   static constexpr int P = LEAN_AHEAD;
   static constexpr int FW = (KL + 2) & ~1;            // forward record (doubles)
@@ -1098,14 +1098,18 @@ struct LeanSmem {
   static constexpr size_t per_warp = (R * (fslot > bslot ? fslot : bslot) + 15) / 16 * 16;
 };
 
-template <int KL, int CPW, int MODE>
+// NFLD = 2: the two fields of a vortex state (psi, chi; fstride complex values apart)
+// in one launch, sharing each staged factor record between 8 real chains per |k|
+// (field, sign of k, Re/Im), so that the factors are read once per step.
+template <int KL, int CPW, int MODE, int NFLD>
 __global__ void __launch_bounds__(64, 1) k_band_solve_lean(
     int M, int nc, int Kz, int K, int groups_per_m, double h, double dt, int hasA, int hasAp,
     const long long* __restrict__ soff, const long long* __restrict__ band_off, int kz_fac, int m0_shift,
+    long long fstride,
     const double* __restrict__ FS, const double* __restrict__ BS, const double* __restrict__ invd,
     const double* __restrict__ s, const double* __restrict__ A, const double* __restrict__ Ap,
     double* __restrict__ out, double* __restrict__ scratch) {
-  using SM = LeanSmem<KL, CPW>;
+  using SM = LeanSmem<KL, CPW, NFLD>;
   constexpr int G = SM::G, NP = SM::NP, P = SM::P, FW = SM::FW, BW = SM::BW, RS = SM::R;
   constexpr int NF = (G * FW / 2 + 31) / 32, NB = (G * BW / 2 + 31) / 32;   // 16-byte chunks per lane, at most
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1125,12 +1129,12 @@ __global__ void __launch_bounds__(64, 1) k_band_solve_lean(
   const int GS = (kz_fac == 1) ? 1 : gcnt;            // factor records per row
   const long long row0 = band_off[m] + (kz_fac == 1 ? 0 : k0);
   const double2* s2 = reinterpret_cast<const double2*>(s);
-  // offset (complex units) of complex piece cp = kq * 2 + sg at row 0, or -1
+  // offset (complex units) of complex piece cp = (kq NFLD + field) 2 + sg at row 0, or -1
   auto piece = [=](int cp) -> long long {
-    const int kq = cp >> 1, sg = cp & 1, kabs = k0 + kq;
+    const int sg = cp & 1, fld = (cp >> 1) % NFLD, kq = (cp >> 1) / NFLD, kabs = k0 + kq;
     if (kq >= gcnt || (sg && kabs == 0)) return -1;
     const int kidx = sg ? K - kabs : kabs;
-    return sm + (long long)kidx * Nm + sh;
+    return (long long)fld * fstride + sm + (long long)kidx * Nm + sh;
   };
   // ---- this lane's copies ----
   const int nf = GS * FW / 2, nb = GS * BW / 2;
@@ -1157,7 +1161,7 @@ __global__ void __launch_bounds__(64, 1) k_band_solve_lean(
   const long long so = (lane < NP) ? piece(lane) : -1;
   const double2* ssrc = (MODE == LEAN_ABCN && so >= 0) ? s2 + so : nullptr;   // s for the AB-CN "- s"
   const int c = lane;
-  const int kk = c >> 2, part = c & 1, cpx = c >> 1;
+  const int kk = c / (4 * NFLD), part = c & 1, cpx = c >> 1;
   const bool act = c < CPW && kk < gcnt;
   const bool valid = act && !(((c >> 1) & 1) && k0 + kk == 0);
   const int ks = (kz_fac == 1) ? 0 : (kk < gcnt ? kk : 0);   // lane's record within a row block
@@ -1361,24 +1365,31 @@ __global__ void k_pack_lean(int nc, int kcnt, int kz_fac, int KL, const long lon
 template <int KL>
 static int launch_solve(mlx_ctx* c, int step, const BandLU& f, const long long* fac_off, int kz_fac,
                         int m0_shift, const double2* s, const double2* A, const double2* Ap, double2* out,
-                        cudaStream_t st) {
+                        cudaStream_t st, int nfields = 1) {
+  if (nfields == 2 && c->solve_direct != 2) return MLX_EINVAL;   // two fields per launch: lean only
   if (c->solve_direct == 2) {
     if (!c->d_solve_y || !f.FS || !f.BS) return MLX_ESTATE;
     const int mode = (step == MLX_STEP_ABCN) ? LEAN_ABCN
                      : ((step == MLX_STEP_FEBE_HALF || step == MLX_STEP_FEBE_FULL) && A) ? LEAN_FEBE
                                                                                           : LEAN_PLAIN;
     const double h = (step == MLX_STEP_FEBE_FULL) ? c->dt : 0.5 * c->dt;
-    auto go = [&](auto cpw_tag, auto mode_tag) -> int {
+    auto go1 = [&](auto cpw_tag, auto mode_tag, auto nf_tag) -> int {
       constexpr int CPWL = decltype(cpw_tag)::value, MODE = decltype(mode_tag)::value;
-      const int gpm = (c->Kz + CPWL / 4 - 1) / (CPWL / 4);
+      constexpr int NFLD = decltype(nf_tag)::value;
+      constexpr int G = LeanSmem<KL, CPWL, NFLD>::G;
+      const int gpm = (c->Kz + G - 1) / G;
       const int warps = c->M * gpm;
       const int WPB = (warps <= 2 * 148) ? 1 : 2;   // spread few warps over every SM
-      const size_t smem = (size_t)WPB * LeanSmem<KL, CPWL>::per_warp;
-      k_band_solve_lean<KL, CPWL, MODE><<<(warps + WPB - 1) / WPB, 32 * WPB, smem, st>>>(
+      const size_t smem = (size_t)WPB * LeanSmem<KL, CPWL, NFLD>::per_warp;
+      k_band_solve_lean<KL, CPWL, MODE, NFLD><<<(warps + WPB - 1) / WPB, 32 * WPB, smem, st>>>(
           c->M, c->nc, c->Kz, c->K, gpm, h, c->dt, A != nullptr, Ap != nullptr, c->d_soff, fac_off, kz_fac,
-          m0_shift, f.FS, f.BS, f.invd, (const double*)s, (const double*)A, (const double*)Ap, (double*)out,
-          c->d_solve_y);
+          m0_shift, c->n_spec, f.FS, f.BS, f.invd, (const double*)s, (const double*)A, (const double*)Ap,
+          (double*)out, c->d_solve_y);
       return MLX_OK;
+    };
+    auto go = [&](auto cpw_tag, auto mode_tag) -> int {
+      if (nfields == 2) return go1(cpw_tag, mode_tag, std::integral_constant<int, 2>());
+      return go1(cpw_tag, mode_tag, std::integral_constant<int, 1>());
     };
     using I16 = std::integral_constant<int, 16>;
     using I32 = std::integral_constant<int, 32>;
@@ -1435,16 +1446,16 @@ static int launch_solve(mlx_ctx* c, int step, const BandLU& f, const long long* 
 }
 
 int mlx_band_solve(mlx_ctx* c, int step, const double2* s, const double2* A, const double2* Ap,
-                   double2* out, cudaStream_t st) {
+                   double2* out, cudaStream_t st, int nfields) {
   TimedLaunch tl(c, KID_BAND_SOLVE, st);
   const BandLU& f = (step == MLX_STEP_FEBE_FULL) ? c->lu_full : c->lu_half;
   int rc;
   const long long* fo = c->d_band_off;
   switch (c->kl) {
-    case 2: rc = launch_solve<2>(c, step, f, fo, c->Kz, 0, s, A, Ap, out, st); break;
-    case 4: rc = launch_solve<4>(c, step, f, fo, c->Kz, 0, s, A, Ap, out, st); break;
-    case 6: rc = launch_solve<6>(c, step, f, fo, c->Kz, 0, s, A, Ap, out, st); break;
-    case 8: rc = launch_solve<8>(c, step, f, fo, c->Kz, 0, s, A, Ap, out, st); break;
+    case 2: rc = launch_solve<2>(c, step, f, fo, c->Kz, 0, s, A, Ap, out, st, nfields); break;
+    case 4: rc = launch_solve<4>(c, step, f, fo, c->Kz, 0, s, A, Ap, out, st, nfields); break;
+    case 6: rc = launch_solve<6>(c, step, f, fo, c->Kz, 0, s, A, Ap, out, st, nfields); break;
+    case 8: rc = launch_solve<8>(c, step, f, fo, c->Kz, 0, s, A, Ap, out, st, nfields); break;
     default: return MLX_EINVAL;
   }
   if (rc) return rc;
@@ -1547,16 +1558,21 @@ int mlx_lap_solve(mlx_ctx* c, int family, const double2* rhs, double2* out, cuda
   return MLX_OK;
 }
 
+template <int KL, int NF>
+static int set_lean_attrs_nf(mlx_ctx* c, int lim) {
+  const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_band_solve_lean<KL, 16, LEAN_PLAIN, NF>, at, lim));
+  MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_band_solve_lean<KL, 16, LEAN_FEBE, NF>, at, lim));
+  MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_band_solve_lean<KL, 16, LEAN_ABCN, NF>, at, lim));
+  MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_band_solve_lean<KL, 32, LEAN_PLAIN, NF>, at, lim));
+  MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_band_solve_lean<KL, 32, LEAN_FEBE, NF>, at, lim));
+  MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_band_solve_lean<KL, 32, LEAN_ABCN, NF>, at, lim));
+  return MLX_OK;
+}
 template <int KL>
 static int set_lean_attrs(mlx_ctx* c, int lim) {
-  const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
-  MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_band_solve_lean<KL, 16, LEAN_PLAIN>, at, lim));
-  MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_band_solve_lean<KL, 16, LEAN_FEBE>, at, lim));
-  MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_band_solve_lean<KL, 16, LEAN_ABCN>, at, lim));
-  MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_band_solve_lean<KL, 32, LEAN_PLAIN>, at, lim));
-  MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_band_solve_lean<KL, 32, LEAN_FEBE>, at, lim));
-  MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_band_solve_lean<KL, 32, LEAN_ABCN>, at, lim));
-  return MLX_OK;
+  const int rc = set_lean_attrs_nf<KL, 1>(c, lim);
+  return rc ? rc : set_lean_attrs_nf<KL, 2>(c, lim);
 }
 
 // Segmented-solve influence data of an implicit-step factor family for S segments
@@ -1612,8 +1628,16 @@ int mlx_pack_lean(mlx_ctx* c, BandLU& f, int kl, const long long* d_off, int kz_
 // sized for either chain count (16 or 32).
 int mlx_solve_scratch(mlx_ctx* c) {
   if (c->d_solve_y) return MLX_OK;
-  const long long w32 = (long long)((c->Kz + 7) / 8) * 32, w16 = (long long)((c->Kz + 3) / 4) * 16;
-  const long long elems = (long long)c->M * c->nc * (w32 > w16 ? w32 : w16);
+  // [warp][Nc][CPW]: the largest warp count of the variants (32 or 16 chains per warp,
+  // one or two fields per launch: 4 NF chains per |k|)
+  long long w = 0;
+  for (int cpw : {16, 32})
+    for (int nf : {1, 2}) {
+      const int g = cpw / (4 * nf);
+      const long long v = (long long)((c->Kz + g - 1) / g) * cpw;
+      w = v > w ? v : w;
+    }
+  const long long elems = (long long)c->M * c->nc * w;
   MLX_CUDA_TRY(c, cudaMalloc(&c->d_solve_y, sizeof(double) * elems));
   return MLX_OK;
 }

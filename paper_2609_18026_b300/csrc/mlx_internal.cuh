@@ -180,6 +180,7 @@ struct mlx_ctx {
   int z_tile = 0;                      // radii per CTA of the z kernels (1..32; 0 = automatic)
   int solve_seg = 8;                   // segments of the half-width-2 segmented solve (8, 4; 0 = off)
   int solve_nopiv = 1;                 // 1: the segmented solve skips pivoting for families without interchanges
+  int solve_fields2 = 1;               // 1: the lean solve takes both vortex fields in one launch
 
   // graphs cached per (state, prev_A, kind, gamma)
   struct GraphKey {
@@ -275,8 +276,10 @@ int mlx_tc_retile(mlx_ctx* c, int bn, cudaStream_t st);
 int mlx_enqueue_step_pair(mlx_ctx* c, int kind, double c0, double2* s, double2* Ap, cudaStream_t st);
 int mlx_legendre_tc_forward(mlx_ctx* c, double2* spec, cudaStream_t st);
 int mlx_legendre_tc_backward(mlx_ctx* c, const double2* spec, cudaStream_t st);
+// nfields = 2: both fields of a vortex state (n_spec apart) in one launch (lean
+// variant only; MLX_EINVAL otherwise)
 int mlx_band_solve(mlx_ctx* c, int step, const double2* s, const double2* A,
-                   const double2* Ap, double2* out, cudaStream_t st);
+                   const double2* Ap, double2* out, cudaStream_t st, int nfields = 1);
 // Dense BF16 GEMM on the tensor cores (gemm_tc.cu): C (+)= A * B^T, A with P in {1, 3}
 // BF16 parts [P][Ma][Kp], B [Nb][Kp], both K-major; see the file for the contract.
 int mlx_gemm_tc(int P, const void* A, long long Ma, const void* B, long long Nb, long long Kp, int M, int N, int K,

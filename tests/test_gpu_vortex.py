@@ -255,3 +255,24 @@ def test_axial_energy_parity(prec, record):
     err = np.abs(got - ref) / np.abs(ref)
     record("axial_energy", precision=PNAME[prec], E0=float(ref[0]), E1=float(ref[1]), max_rel_err=float(np.max(err)))
     assert np.max(err) <= 1e-11
+
+
+@pytest.mark.parametrize("cpw", [32, 16])
+def test_lean_two_field_launch_bitwise(cpw):
+    # the p = 8 implicit solve of a vortex state runs the lean variant; one launch
+    # for both fields (each staged factor record shared by the 8 real chains of a
+    # |k|) and one launch per field give the same bits
+    g, ctx = pair(40, 16, 8, 1.0, lz=8.6, policy="twothirds")
+    ctx.vortex_setup()
+    ctx.implicit_setup(1e-3, 1e-2, nu_h=1e-5, p=8)
+    ctx.set_tuning("solve_lean_cpw", cpw)
+    psi, chi = _smooth_state(g, 41)
+    outs = []
+    for two in (1, 0):
+        ctx.set_tuning("solve_fields2", two)
+        state = to_gpu_spec(np.concatenate([psi, chi]))
+        prev = to_gpu_spec(np.zeros(2 * len(psi), np.complex128))
+        ctx.advance(B.NONLIN_VORTEX, [0.5], state, prev, 3, True)
+        outs.append(state.cpu().numpy())
+    assert np.all(np.isfinite(outs[0]))
+    assert np.array_equal(outs[0], outs[1])
