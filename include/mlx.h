@@ -384,6 +384,11 @@ int mlx_set_state(mlx_ctx* ctx, int kind, const void* host, long long bytes, voi
  *                bitwise; 0 = off.
  *   "solve_lean_cpw": real chains per warp of the lean variant, 16 or 32
  *                (default 32).
+ *   "plane_reuse": 1 (default) = in the graph-replayed MLX_BF16X3 Fisher-KPP steps
+ *                (no filter) the segmented solve also writes the BF16x3 split
+ *                planes of its output, and every step of the call after its first
+ *                takes them instead of splitting the state again; 0 = split every
+ *                step.  Bitwise-equal results.
  *   "solve_fields2": 1 (default) = the lean variant solves both fields of a
  *                vortex state in one launch (each staged factor record serves
  *                the 8 real chains of both fields at one |k|, so a step reads the

@@ -57,7 +57,7 @@ int dalloc(mlx_ctx* c, P** p, size_t bytes) {
 // In the time steps (src) the vortex tendency also carries the log proxies' constant
 // forcing c L Lambda in its (0, 0) blocks.
 int nonlinear_into(mlx_ctx* c, int kind, double c0, const double2* s, double2* A, cudaStream_t st,
-                   bool src = true) {
+                   bool src = true, bool planes_ready = false) {
   if (kind == MLX_NONLIN_NONE) {
     MLX_CUDA_TRY(c, cudaMemsetAsync(A, 0, sizeof(double2) * c->n_spec, st));
     return MLX_OK;
@@ -67,7 +67,7 @@ int nonlinear_into(mlx_ctx* c, int kind, double c0, const double2* s, double2* A
     if (rc || !src) return rc;
     return mlx_lp_add_source(c, A, st);
   }
-  int rc = mlx_legendre_backward(c, s, st);
+  int rc = mlx_legendre_backward(c, s, st, planes_ready);
   if (rc) return rc;
   rc = mlx_fft_fkpp(c, c0, st);
   if (rc) return rc;
@@ -80,11 +80,14 @@ int nonlinear_into(mlx_ctx* c, int kind, double c0, const double2* s, double2* A
 int nfields(int kind) { return kind == MLX_NONLIN_VORTEX ? 2 : 1; }
 
 // implicit step applied to every field of the state (fields share the factors; the
-// lean solve takes both fields of a vortex state in one launch, reading the factors once)
+// lean solve takes both fields of a vortex state in one launch, reading the factors once).
+// sp / wrote: the split planes of a one-field output (see mlx_band_solve).
 int solve_fields(mlx_ctx* c, int kind, int step, const double2* s, const double2* A, const double2* Ap,
-                 double2* out, cudaStream_t st) {
+                 double2* out, cudaStream_t st, const SplitPlanes* sp = nullptr, bool* wrote = nullptr) {
+  if (wrote) *wrote = false;
   if (nfields(kind) == 2 && c->solve_direct == 2 && c->solve_fields2)
     return mlx_band_solve(c, step, s, A, Ap, out, st, 2);
+  if (nfields(kind) == 1) return mlx_band_solve(c, step, s, A, Ap, out, st, 1, sp, wrote);
   for (int f = 0; f < nfields(kind); ++f) {
     const long long o = (long long)f * c->n_spec;
     int rc = mlx_band_solve(c, step, s + o, A ? A + o : nullptr, Ap ? Ap + o : nullptr, out + o, st);
@@ -93,13 +96,45 @@ int solve_fields(mlx_ctx* c, int kind, int step, const double2* s, const double2
   return MLX_OK;
 }
 
+// Split-plane reuse between the graph-replayed steps of one mlx_advance call: in the
+// BF16X3 Fisher-KPP step (no filter) the segmented solve also writes the split
+// planes of its output, the state the next step's backward contraction transforms,
+// so that step skips k_split_spec.  Only the steps of one call chain this way (the
+// caller may change the state between calls).
+bool plane_reuse_ok(const mlx_ctx* c, int kind) {
+  return c->plane_reuse && c->precision == MLX_BF16X3 && kind == MLX_NONLIN_FKPP && !c->filter_on && c->d_bsb;
+}
+
+// planes_in: d_bsb holds the split planes of s; planes_out (may be NULL): set when
+// the solve wrote the split planes of out
 int abcn_step(mlx_ctx* c, int kind, double c0, const double2* s, double2* Anew,
-              const double2* Aprev, double2* out, cudaStream_t st) {
-  int rc = nonlinear_into(c, kind, c0, s, Anew, st);
+              const double2* Aprev, double2* out, cudaStream_t st, bool planes_in = false,
+              bool* planes_out = nullptr) {
+  if (planes_out) *planes_out = false;
+  int rc = nonlinear_into(c, kind, c0, s, Anew, st, true, planes_in);
   if (rc) return rc;
-  rc = solve_fields(c, kind, MLX_STEP_ABCN, s, Anew, Aprev, out, st);
+  if (planes_out && plane_reuse_ok(c, kind)) {
+    SplitPlanes sp;
+    sp.bs = reinterpret_cast<unsigned short*>(c->d_bsb);
+    sp.Kq = (int)c->tc_kq;
+    sp.K2 = 2 * c->K;
+    sp.part = (long long)c->M * sp.K2 * sp.Kq;
+    rc = solve_fields(c, kind, MLX_STEP_ABCN, s, Anew, Aprev, out, st, &sp, planes_out);
+  } else {
+    rc = solve_fields(c, kind, MLX_STEP_ABCN, s, Anew, Aprev, out, st);
+  }
   if (rc || !c->filter_on) return rc;
   return mlx_filter_fields(c, nfields(kind), out, st);   // the modal filter acts between steps
+}
+
+// the two AB-CN steps of one replayed pair; planes_in: d_bsb holds the split planes
+// of s (the previous pair wrote them); *planes_out: the pair left those of its output s
+int pair_steps(mlx_ctx* c, int kind, double c0, double2* s, double2* Ap, cudaStream_t st, bool planes_in,
+               bool* planes_out) {
+  bool mid = false;
+  int rc = abcn_step(c, kind, c0, s, c->d_specA, Ap, c->d_spec1, st, planes_in, &mid);
+  if (rc) return rc;
+  return abcn_step(c, kind, c0, c->d_spec1, Ap, c->d_specA, s, st, mid, planes_out);
 }
 
 }  // namespace
@@ -107,9 +142,10 @@ int abcn_step(mlx_ctx* c, int kind, double c0, const double2* s, double2* Anew,
 // Two AB-CN steps (s, A_prev) -> (s, A_prev) through the context's temporaries,
 // enqueued on st (the unit that graphs replay).
 int mlx_enqueue_step_pair(mlx_ctx* c, int kind, double c0, double2* s, double2* Ap, cudaStream_t st) {
-  int rc = abcn_step(c, kind, c0, s, c->d_specA, Ap, c->d_spec1, st);
-  if (rc) return rc;
-  return abcn_step(c, kind, c0, c->d_spec1, Ap, c->d_specA, s, st);
+  // each pair starts from the caller's state (split afresh); its second step takes
+  // the split planes its first step's solve left
+  bool left = false;
+  return pair_steps(c, kind, c0, s, Ap, st, false, &left);
 }
 
 extern "C" {
@@ -348,35 +384,52 @@ int mlx_advance(mlx_ctx* c, int kind, const double* coeffs, int ncoeffs, void* s
     --nsteps;
   }
   const int pairs = nsteps / 2;
+  // capture one pair (planes_in: reuse the split planes the previous pair left) into
+  // an executable graph; *left: the pair leaves the split planes of its output s
+  auto capture_pair = [&](bool planes_in, cudaGraphExec_t* exec, bool* left) -> int {
+    cudaGraph_t g = nullptr;
+    MLX_CUDA_TRY(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+    const int r = pair_steps(c, kind, c0, s, Ap, c->cap_stream, planes_in, left);
+    cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
+    if (r) { if (g) cudaGraphDestroy(g); return r; }
+    if (e != cudaSuccess) { c->last_err = cudaGetErrorString(e); return MLX_ECUDA; }
+    e = cudaGraphInstantiate(exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) { c->last_err = cudaGetErrorString(e); return MLX_ECUDA; }
+    return MLX_OK;
+  };
   if (pairs > 0 && c->timing.on && c->timing.mode == 1) {
     // instrumented mode 1: the same two-step sequence launched directly so that
     // every kernel is bracketed by CUDA events
-    for (int i = 0; i < pairs; ++i) {
-      if ((rc = abcn_step(c, kind, c0, s, c->d_specA, Ap, c->d_spec1, st))) return rc;
-      if ((rc = abcn_step(c, kind, c0, c->d_spec1, Ap, c->d_specA, s, st))) return rc;
-    }
+    bool planes = false;
+    for (int i = 0; i < pairs; ++i)
+      if ((rc = pair_steps(c, kind, c0, s, Ap, st, planes, &planes))) return rc;
   } else if (pairs > 0 && c->timing.on) {
-    // instrumented mode 2: the two-step graph with an event-record node before and
-    // after every kernel node, replayed pair by pair; after each replay the node
-    // timings are read (the replays are separated by a host synchronisation, the
-    // kernels inside one replay run back to back as in the cached graph)
-    for (auto& p : c->timing.captured) { c->timing.pool.push_back(p.a); c->timing.pool.push_back(p.b); }
-    c->timing.captured.clear();
-    cudaGraph_t g = nullptr;
-    cudaGraphExec_t exec = nullptr;
-    MLX_CUDA_TRY(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
-    rc = abcn_step(c, kind, c0, s, c->d_specA, Ap, c->d_spec1, c->cap_stream);
-    if (!rc) rc = abcn_step(c, kind, c0, c->d_spec1, Ap, c->d_specA, s, c->cap_stream);
-    cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
-    if (rc) { if (g) cudaGraphDestroy(g); return rc; }
-    if (e != cudaSuccess) { c->last_err = cudaGetErrorString(e); return MLX_ECUDA; }
-    e = cudaGraphInstantiate(&exec, g, 0);
-    cudaGraphDestroy(g);
-    if (e != cudaSuccess) { c->last_err = cudaGetErrorString(e); return MLX_ECUDA; }
+    // instrumented mode 2: the two-step graphs (the call's first pair, then the pair
+    // that reuses the previous pair's split planes) with an event-record node before
+    // and after every kernel node, replayed pair by pair; after each replay the node
+    // timings of that graph are read (the replays are separated by a host
+    // synchronisation, the kernels inside one replay run back to back as in the
+    // cached graphs)
+    auto release = [&](std::vector<TimingState::Pending>& v) {
+      for (auto& p : v) { c->timing.pool.push_back(p.a); c->timing.pool.push_back(p.b); }
+      v.clear();
+    };
+    release(c->timing.captured);
+    cudaGraphExec_t ex[2] = {nullptr, nullptr};
+    std::vector<TimingState::Pending> cap[2];
+    bool left = false, left2 = false;
+    rc = capture_pair(false, &ex[0], &left);
+    cap[0].swap(c->timing.captured);
+    if (!rc && left && pairs > 1) {
+      rc = capture_pair(true, &ex[1], &left2);
+      cap[1].swap(c->timing.captured);
+    }
     for (int i = 0; i < pairs && !rc; ++i) {
-      e = cudaGraphLaunch(exec, st);
+      const int v = (i > 0 && ex[1]) ? 1 : 0;
+      cudaError_t e = cudaGraphLaunch(ex[v], st);
       if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-      for (auto& p : c->timing.captured) {
+      for (auto& p : cap[v]) {
         float ms = 0.f;
         if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, p.a, p.b);
         c->timing.launches[p.kid] += 1;
@@ -384,31 +437,33 @@ int mlx_advance(mlx_ctx* c, int kind, const double* coeffs, int ncoeffs, void* s
       }
       if (e != cudaSuccess) { c->last_err = cudaGetErrorString(e); rc = MLX_ECUDA; }
     }
-    cudaGraphExecDestroy(exec);
-    for (auto& p : c->timing.captured) { c->timing.pool.push_back(p.a); c->timing.pool.push_back(p.b); }
-    c->timing.captured.clear();
+    for (auto* x : ex) if (x) cudaGraphExecDestroy(x);
+    release(cap[0]);
+    release(cap[1]);
+    release(c->timing.captured);
     if (rc) return rc;
   } else if (pairs > 0) {
-    // two steps per graph: (s, A_prev) -> (spec1, specA) -> (s, A_prev), no copies
-    mlx_ctx::GraphKey key{state, prev_A, kind, c0};
-    auto it = c->graphs.find(key);
-    cudaGraphExec_t exec = nullptr;
-    if (it == c->graphs.end()) {
-      cudaGraph_t g = nullptr;
-      MLX_CUDA_TRY(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
-      rc = abcn_step(c, kind, c0, s, c->d_specA, Ap, c->d_spec1, c->cap_stream);
-      if (!rc) rc = abcn_step(c, kind, c0, c->d_spec1, Ap, c->d_specA, s, c->cap_stream);
-      cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
-      if (rc) { if (g) cudaGraphDestroy(g); return rc; }
-      if (e != cudaSuccess) { c->last_err = cudaGetErrorString(e); return MLX_ECUDA; }
-      e = cudaGraphInstantiate(&exec, g, 0);
-      cudaGraphDestroy(g);
-      if (e != cudaSuccess) { c->last_err = cudaGetErrorString(e); return MLX_ECUDA; }
-      c->graphs[key] = exec;
-    } else {
-      exec = it->second;
+    // two steps per graph: (s, A_prev) -> (spec1, specA) -> (s, A_prev), no copies;
+    // variant 0 starts from the caller's state, variant 1 (the later pairs of the
+    // call) reuses the split planes the previous pair left
+    cudaGraphExec_t ex[2] = {nullptr, nullptr};
+    bool left = false;
+    for (int v = 0; v < 2; ++v) {
+      if (v == 1 && !(left && pairs > 1)) break;
+      mlx_ctx::GraphKey key{state, prev_A, kind, c0, v};
+      auto it = c->graphs.find(key);
+      if (it == c->graphs.end()) {
+        bool l = false;
+        if ((rc = capture_pair(v == 1, &ex[v], &l))) return rc;
+        c->graphs[key] = ex[v];
+        c->graph_left[key] = l;
+        if (v == 0) left = l;
+      } else {
+        ex[v] = it->second;
+        if (v == 0) left = c->graph_left[key];
+      }
     }
-    for (int i = 0; i < pairs; ++i) MLX_CUDA_TRY(c, cudaGraphLaunch(exec, st));
+    for (int i = 0; i < pairs; ++i) MLX_CUDA_TRY(c, cudaGraphLaunch(ex[(i > 0 && ex[1]) ? 1 : 0], st));
   }
   if (nsteps % 2) {
     if ((rc = abcn_step(c, kind, c0, s, c->d_specA, Ap, c->d_spec1, st))) return rc;
@@ -466,6 +521,12 @@ int mlx_set_tuning(mlx_ctx* c, const char* key, int value) {
   if (strcmp(key, "solve_lean_cpw") == 0) {
     if (value != 16 && value != 32) return MLX_EINVAL;
     c->solve_lean_cpw = value;
+    mlx_invalidate_graphs(c);
+    return MLX_OK;
+  }
+  if (strcmp(key, "plane_reuse") == 0) {
+    if (value != 0 && value != 1) return MLX_EINVAL;
+    c->plane_reuse = value;
     mlx_invalidate_graphs(c);
     return MLX_OK;
   }

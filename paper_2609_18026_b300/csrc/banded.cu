@@ -16,6 +16,7 @@
 // One thread per system factorises.  The solve variants (staged, segmented, lean)
 // are described at their kernels; all use these FP64 factors.
 #include "mlx_internal.cuh"
+#include "bf16_split.cuh"
 
 #include <type_traits>
 
@@ -718,7 +719,8 @@ __global__ void k_band_solve_seg(int M, int nc, int Kz, int K, int groups_per_m,
                                  const double* __restrict__ PHb, const double* __restrict__ PSf,
                                  const double* __restrict__ RNP,
                                  const double* __restrict__ s, const double* __restrict__ A,
-                                 const double* __restrict__ Ap, double* __restrict__ out) {
+                                 const double* __restrict__ Ap, double* __restrict__ out,
+                                 SplitPlanes sp) {
   using SM = SegSmem<KL, SEG>;
   constexpr int W = SM::W, CPW = SM::CPW, G = SM::G, RW = SM::RW;
   constexpr int UW = NP ? KL : 2 * KL;                      // upper entries the substitution reads
@@ -963,8 +965,10 @@ __global__ void k_band_solve_seg(int M, int nc, int Kz, int K, int groups_per_m,
     }
   }
   __syncwarp();
-  // ---- output ----
+  // ---- output (and, when sp.bs is set, its three BF16 parts in the split planes of
+  // the backward contraction, exactly as k_split_spec would write them) ----
   double2* out2 = reinterpret_cast<double2*>(out);
+  const long long prow = sp.bs ? ((long long)m * sp.K2 + 2 * (sgl ? K - kabsl : kabsl)) * sp.Kq : 0;
 #pragma unroll 4
   for (int i = il; i < (lane_piece ? N : 0); i += LP) {
     double2 v = make_double2(Y[(size_t)i * CPW + cpl * 2], Y[(size_t)i * CPW + cpl * 2 + 1]);
@@ -979,6 +983,14 @@ __global__ void k_band_solve_seg(int M, int nc, int Kz, int K, int groups_per_m,
       }
     }
     out2[pbase + i] = v;
+    if (sp.bs) {
+      unsigned short h, md, lo;
+      split3_f64(v.x, h, md, lo);
+      const long long o = prow + i;
+      sp.bs[o] = h; sp.bs[sp.part + o] = md; sp.bs[2 * sp.part + o] = lo;
+      split3_f64(v.y, h, md, lo);
+      sp.bs[o + sp.Kq] = h; sp.bs[sp.part + o + sp.Kq] = md; sp.bs[2 * sp.part + o + sp.Kq] = lo;
+    }
   }
 }
 
@@ -1365,7 +1377,8 @@ __global__ void k_pack_lean(int nc, int kcnt, int kz_fac, int KL, const long lon
 template <int KL>
 static int launch_solve(mlx_ctx* c, int step, const BandLU& f, const long long* fac_off, int kz_fac,
                         int m0_shift, const double2* s, const double2* A, const double2* Ap, double2* out,
-                        cudaStream_t st, int nfields = 1) {
+                        cudaStream_t st, int nfields = 1, const SplitPlanes* sp = nullptr, bool* wrote = nullptr) {
+  if (wrote) *wrote = false;
   if (nfields == 2 && c->solve_direct != 2) return MLX_EINVAL;   // two fields per launch: lean only
   if (c->solve_direct == 2) {
     if (!c->d_solve_y || !f.FS || !f.BS) return MLX_ESTATE;
@@ -1421,7 +1434,9 @@ static int launch_solve(mlx_ctx* c, int step, const BandLU& f, const long long* 
         auto kern = np ? k_band_solve_seg<KL, S, true> : k_band_solve_seg<KL, S, false>;
         kern<<<(warps + WPB - 1) / WPB, 32 * WPB, pw * WPB, st>>>(
             c->M, c->nc, c->Kz, c->K, gpm, step, keep_s, c->dt, c->d_soff, fac_off, f.U, f.L, f.piv, f.invd,
-            f.PHf, f.PHb, f.PSf, f.RNP, (const double*)s, (const double*)A, (const double*)Ap, (double*)out);
+            f.PHf, f.PHb, f.PSf, f.RNP, (const double*)s, (const double*)A, (const double*)Ap, (double*)out,
+            sp ? *sp : SplitPlanes());
+        if (wrote && sp && sp->bs) *wrote = true;
         return true;
       };
       if (f.seg == 8 ? go(std::integral_constant<int, 8>()) : go(std::integral_constant<int, 4>())) return MLX_OK;
@@ -1446,13 +1461,14 @@ static int launch_solve(mlx_ctx* c, int step, const BandLU& f, const long long* 
 }
 
 int mlx_band_solve(mlx_ctx* c, int step, const double2* s, const double2* A, const double2* Ap,
-                   double2* out, cudaStream_t st, int nfields) {
+                   double2* out, cudaStream_t st, int nfields, const SplitPlanes* sp, bool* wrote) {
   TimedLaunch tl(c, KID_BAND_SOLVE, st);
   const BandLU& f = (step == MLX_STEP_FEBE_FULL) ? c->lu_full : c->lu_half;
   int rc;
   const long long* fo = c->d_band_off;
+  if (wrote) *wrote = false;
   switch (c->kl) {
-    case 2: rc = launch_solve<2>(c, step, f, fo, c->Kz, 0, s, A, Ap, out, st, nfields); break;
+    case 2: rc = launch_solve<2>(c, step, f, fo, c->Kz, 0, s, A, Ap, out, st, nfields, sp, wrote); break;
     case 4: rc = launch_solve<4>(c, step, f, fo, c->Kz, 0, s, A, Ap, out, st, nfields); break;
     case 6: rc = launch_solve<6>(c, step, f, fo, c->Kz, 0, s, A, Ap, out, st, nfields); break;
     case 8: rc = launch_solve<8>(c, step, f, fo, c->Kz, 0, s, A, Ap, out, st, nfields); break;

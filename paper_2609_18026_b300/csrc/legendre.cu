@@ -126,8 +126,8 @@ int mlx_legendre_forward(mlx_ctx* c, double2* spec, cudaStream_t st, const doubl
   return MLX_OK;
 }
 
-int mlx_legendre_backward(mlx_ctx* c, const double2* spec, cudaStream_t st) {
-  if (c->precision == MLX_BF16X3) return mlx_legendre_tc_backward(c, spec, st);
+int mlx_legendre_backward(mlx_ctx* c, const double2* spec, cudaStream_t st, bool planes_ready) {
+  if (c->precision == MLX_BF16X3) return mlx_legendre_tc_backward(c, spec, st, planes_ready);
   TimedLaunch tl(c, KID_LEG_BWD, st);
   if (c->precision == MLX_FP64)
     k_legendre<double, false><<<c->ntiles_bwd, NT, 0, st>>>(c->d_tiles_bwd, c->nc, c->nr, c->M, c->K,

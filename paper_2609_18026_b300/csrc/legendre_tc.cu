@@ -34,6 +34,7 @@
 // that.  `expire` (a test hook) makes the producer's first stage-reuse wait
 // report expiry at once.
 #include "mlx_internal.cuh"
+#include "bf16_split.cuh"
 #include "tc_ptx.cuh"
 
 #include <cuda_bf16.h>
@@ -52,28 +53,7 @@ constexpr unsigned TC_A_BYTES = 3 * TC_A_PART;
 
 __host__ __device__ constexpr unsigned tc_stage_bytes(int bn) { return TC_A_BYTES + 3u * (unsigned)bn * 64u; }
 
-template <typename T>
-__device__ __forceinline__ void split3(T x, __nv_bfloat16& h, __nv_bfloat16& m, __nv_bfloat16& l) {
-  h = __float2bfloat16_rn((float)x);
-  const T r1 = x - (T)__bfloat162float(h);
-  m = __float2bfloat16_rn((float)r1);
-  const T r2 = r1 - (T)__bfloat162float(m);
-  l = __float2bfloat16_rn((float)r2);
-}
-
-// FP64 -> FP32 round to nearest even, by integer operations on the two words
-// (h = high word, l = low word); results below 2^-126 flush to zero, above FLT_MAX
-// (and inf / NaN) become inf.
-__device__ __forceinline__ float f64w_to_f32(unsigned h, unsigned l) {
-  const unsigned sign = h & 0x80000000u;
-  const unsigned ah = h & 0x7fffffffu;
-  unsigned f = ((ah - (896u << 20)) << 3) | (l >> 29);
-  const unsigned rem = l & 0x1fffffffu;
-  f += (rem > 0x10000000u) | ((rem == 0x10000000u) & (f & 1u));
-  f = (ah < (897u << 20)) ? 0u : f;
-  f = (ah >= (1151u << 20)) ? 0x7f800000u : f;
-  return __uint_as_float(sign | f);
-}
+// split3 and f64w_to_f32: bf16_split.cuh
 
 // FP32 -> FP64 (exact) by integer operations; FP32 subnormals (< 1.2e-38) flush to zero
 __device__ __forceinline__ double f32_to_f64(float v) {
@@ -507,8 +487,8 @@ int mlx_legendre_tc_forward(mlx_ctx* c, double2* spec, cudaStream_t st) {
   return MLX_OK;
 }
 
-int mlx_legendre_tc_backward(mlx_ctx* c, const double2* spec, cudaStream_t st) {
-  {
+int mlx_legendre_tc_backward(mlx_ctx* c, const double2* spec, cudaStream_t st, bool planes_ready) {
+  if (!planes_ready) {   // (planes_ready: the solve that wrote spec also wrote its split planes)
     TimedLaunch tl(c, KID_LEG_SPLIT, st);
     const int tb = c->nc >= 128 ? 128 : 64;
     k_split_spec<<<dim3((c->nc + tb - 1) / tb, c->K, c->M), tb, 0, st>>>(

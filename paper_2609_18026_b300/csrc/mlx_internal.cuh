@@ -52,6 +52,14 @@ struct LegTile {
 // rows i = 0..N_m-1 (N_m = Nc - m).  U row i holds columns i..i+kl+ku
 // (ku_f = kl + ku entries after the diagonal), L holds kl multipliers per
 // column, piv the pivot row of each column, invd 1/U[i][i].
+// Destination of the BF16x3 split planes of a spectral field, the backward
+// contraction's data operand: bs[part][(m 2K + 2 kidx + (0 Re, 1 Im)) Kq + (n - m)]
+struct SplitPlanes {
+  unsigned short* bs = nullptr;
+  long long part = 0;
+  int Kq = 0, K2 = 0;
+};
+
 struct BandLU {
   double* U = nullptr;     // [rows][W_u] with W_u = 1 + kl + ku
   double* L = nullptr;     // [rows][kl]
@@ -181,18 +189,22 @@ struct mlx_ctx {
   int solve_seg = 8;                   // segments of the half-width-2 segmented solve (8, 4; 0 = off)
   int solve_nopiv = 1;                 // 1: the segmented solve skips pivoting for families without interchanges
   int solve_fields2 = 1;               // 1: the lean solve takes both vortex fields in one launch
+  int plane_reuse = 1;                 // 1: the graph-replayed FKPP steps reuse the solve's split planes
 
-  // graphs cached per (state, prev_A, kind, gamma)
+  // graphs cached per (state, prev_A, kind, gamma, variant); variant 1 is the pair
+  // that reuses the split planes the previous pair left (graph_left: the pair leaves them)
   struct GraphKey {
-    void* s; void* a; int kind; double c0;
+    void* s; void* a; int kind; double c0; int variant;
     bool operator<(const GraphKey& o) const {
       if (s != o.s) return s < o.s;
       if (a != o.a) return a < o.a;
       if (kind != o.kind) return kind < o.kind;
-      return c0 < o.c0;
+      if (c0 != o.c0) return c0 < o.c0;
+      return variant < o.variant;
     }
   };
   std::map<GraphKey, cudaGraphExec_t> graphs;
+  std::map<GraphKey, bool> graph_left;
   unsigned long long graph_gen = 0;    // bumped whenever the cached graphs are invalidated: a
                                        // batch holding graphs of this context recaptures them
   cudaStream_t cap_stream = nullptr;
@@ -241,6 +253,7 @@ struct TimedLaunch {
 inline void mlx_invalidate_graphs(mlx_ctx* c) {
   for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
   c->graphs.clear();
+  c->graph_left.clear();
   ++c->graph_gen;
 }
 
@@ -257,7 +270,8 @@ int mlx_fft_fkpp(mlx_ctx* c, double gamma, cudaStream_t st);           // d_mixe
 // d_mixed -> spec; with addsrc != NULL adds alpha * addsrc in FP64 to every coefficient
 int mlx_legendre_forward(mlx_ctx* c, double2* spec, cudaStream_t st,
                          const double2* addsrc = nullptr, double alpha = 0.0);
-int mlx_legendre_backward(mlx_ctx* c, const double2* spec, cudaStream_t st); // spec -> d_mixed
+// spec -> d_mixed; planes_ready (BF16X3): d_bsb already holds spec's split planes
+int mlx_legendre_backward(mlx_ctx* c, const double2* spec, cudaStream_t st, bool planes_ready = false);
 int mlx_band_setup(mlx_ctx* c, cudaStream_t st);
 int mlx_solve_scratch(mlx_ctx* c);                 // scratch of the lean solve variant
 int mlx_seg_build(mlx_ctx* c, BandLU& f, int S, cudaStream_t st);   // segmented-solve data (S = 0: none)
@@ -275,11 +289,14 @@ int mlx_tc_prepare(mlx_ctx* c, cudaStream_t st);
 int mlx_tc_retile(mlx_ctx* c, int bn, cudaStream_t st);
 int mlx_enqueue_step_pair(mlx_ctx* c, int kind, double c0, double2* s, double2* Ap, cudaStream_t st);
 int mlx_legendre_tc_forward(mlx_ctx* c, double2* spec, cudaStream_t st);
-int mlx_legendre_tc_backward(mlx_ctx* c, const double2* spec, cudaStream_t st);
+int mlx_legendre_tc_backward(mlx_ctx* c, const double2* spec, cudaStream_t st, bool planes_ready = false);
 // nfields = 2: both fields of a vortex state (n_spec apart) in one launch (lean
-// variant only; MLX_EINVAL otherwise)
+// variant only; MLX_EINVAL otherwise).  sp: where the segmented solve also writes
+// the BF16x3 split planes of its output for the backward contraction; *wrote says
+// whether it did (only the segmented variant does).
 int mlx_band_solve(mlx_ctx* c, int step, const double2* s, const double2* A,
-                   const double2* Ap, double2* out, cudaStream_t st, int nfields = 1);
+                   const double2* Ap, double2* out, cudaStream_t st, int nfields = 1,
+                   const SplitPlanes* sp = nullptr, bool* wrote = nullptr);
 // Dense BF16 GEMM on the tensor cores (gemm_tc.cu): C (+)= A * B^T, A with P in {1, 3}
 // BF16 parts [P][Ma][Kp], B [Nb][Kp], both K-major; see the file for the contract.
 int mlx_gemm_tc(int P, const void* A, long long Ma, const void* B, long long Nb, long long Kp, int M, int N, int K,

@@ -187,3 +187,35 @@ def test_checkpoint_carries_the_proxies():
         ctx.set_state(B.NONLIN_VORTEX, img, state, prev)
     ctx.vortex_logproxy(cp, cc, -0.5)
     assert ctx.set_state(B.NONLIN_VORTEX, img, state, prev) == 3
+
+
+@pytest.mark.parametrize("prec,tol", [(B.FP64, 1e-12), (B.BF16X3, 1e-5)])
+def test_production_path_small_advance_parity(prec, tol, record):
+    # every piece of the production run at a small size: the Nyquist-keeping chop,
+    # the co-rotating q-vortex pair with its log proxies and U_z = -0.5, p = 8
+    # hyperviscosity, the adaptive filter (a low target so that it acts), the
+    # Richardson start and 3 AB-CN steps; against the oracle's banded form
+    from oracle.filter import FieldFilter
+    g, ctx = pair(32, 32, 8, 4.0, lz=2.0 * math.pi, policy="nyquist", precision=prec)
+    assert (ctx.M, ctx.Kz) == (17, 5)
+    ctx.vortex_setup()
+    ops = O.VortexOps(g)
+    psi, chi, cp, cc = _perturbed_pair(g, ops)
+    nu, nuh, dt, Uz, tau = 1e-3, 1e-5, 1e-2, -0.5, 1e-6
+    ctx.implicit_setup(nu, dt, nu_h=nuh, p=8)
+    ctx.vortex_logproxy(cp, cc, Uz)
+    ctx.filter_setup(tau=tau)
+    state = to_gpu_spec(_flat2(g, psi, chi))
+    prev = to_gpu_spec(np.zeros(2 * ctx.n_spec, np.complex128))
+    ctx.advance(B.NONLIN_VORTEX, [0.0], state, prev, 4, True)
+    gp, gc = _split(g, state.cpu().numpy())
+    A, _ = O.vortex_nonlinear(g, 0.0, form="banded", Uz=Uz, cpsi=cp, cchi=cc, source=(nu, nuh, 8))
+    filt = FieldFilter(g, 2, params={"tau": tau})
+    ref, _ = O.Stepper(g, nu, dt, nu_h=nuh, p=8, nonlinear=A, post=filt).run_abcn(psi + chi, 4)
+    e = O.spec_rel_err(g, gp + gc, ref)
+    eps_gpu, _ = ctx.filter_state()
+    record("production_path_small", precision=PNAME[prec], rel_err=e, eps_gpu=eps_gpu, eps_oracle=filt.eps)
+    assert max(eps_gpu) > 0.0                   # the filter acted
+    assert np.allclose(eps_gpu, filt.eps, rtol=1e-9 if prec == B.FP64 else 1e-3, atol=0)
+    assert e <= tol
+    ctx.device_status()

@@ -232,3 +232,35 @@ def test_segmented_solve(grid, step):
     ctx.implicit_solve(step, to_gpu_spec(s), to_gpu_spec(A), to_gpu_spec(Ap), ctx.new_spec())
     assert ctx.timing_read()["band_solve"][0] == 1
     ctx.timing(False)
+
+
+def test_fkpp_plane_reuse_bitwise_and_split_count():
+    # BF16x3 Fisher-KPP: within one mlx_advance call the segmented solve writes the
+    # split planes of its output and the next step's backward contraction takes
+    # them; the trajectory is bitwise that of splitting every step, and the split
+    # kernel runs only for the Richardson start, the call's first pair and the odd
+    # trailing step
+    g, ctx = pair(40, 32, 16, 2.0, lz=2 * np.pi * 4, policy="twothirds", precision=B.BF16X3)
+    r, phi, z = g.nodes3()
+    s0 = O.to_flat(g, O.forward(g, W.fkpp_seed(r, phi, z)))
+    ctx.implicit_setup(1.0, 1e-2)
+    outs, splits = [], []
+    for reuse in (1, 0):
+        ctx.set_tuning("plane_reuse", reuse)
+        state = to_gpu_spec(s0)
+        prev = ctx.new_spec()
+        ctx.timing(1)
+        ctx.advance(B.NONLIN_FKPP, [1.0], state, prev, 21, True)
+        kt = ctx.timing_read()
+        ctx.timing(0)
+        splits.append(kt.get("legendre_split", (0, 0.0))[0])
+        state2 = to_gpu_spec(s0)
+        prev2 = ctx.new_spec()
+        ctx.advance(B.NONLIN_FKPP, [1.0], state2, prev2, 21, True)     # graph-replayed
+        outs.append((state.cpu().numpy(), state2.cpu().numpy()))
+    assert np.all(np.isfinite(outs[0][0]))
+    assert np.array_equal(outs[0][0], outs[1][0])        # timing mode 1, reuse on / off
+    assert np.array_equal(outs[0][1], outs[1][1])        # graphs, reuse on / off
+    assert np.array_equal(outs[0][0], outs[0][1])        # direct launches = graphs
+    # start (2 evaluations) + 20 AB-CN steps = 10 pairs: 2 + 1 with reuse, 2 + 20 without
+    assert splits == [3, 22], splits
