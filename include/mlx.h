@@ -384,6 +384,11 @@ int mlx_set_state(mlx_ctx* ctx, int kind, const void* host, long long bytes, voi
  *                bitwise; 0 = off.
  *   "solve_lean_cpw": real chains per warp of the lean variant, 16 or 32
  *                (default 32).
+ *   "vortex_planes": 1 (default) = an MLX_BF16X3 vortex term writes its six
+ *                velocity and vorticity fields straight into the backward
+ *                contraction's split planes (one set per field, allocated by
+ *                mlx_vortex_setup) instead of as FP64 fields split afterwards;
+ *                0 = the FP64 fields.  Bitwise-equal results.
  *   "plane_reuse": 1 (default) = in the graph-replayed MLX_BF16X3 Fisher-KPP steps
  *                (no filter) the segmented solve also writes the BF16x3 split
  *                planes of its output, and every step of the call after its first

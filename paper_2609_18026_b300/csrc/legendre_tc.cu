@@ -466,6 +466,11 @@ int mlx_tc_retile(mlx_ctx* c, int bn_req, cudaStream_t st) {
   if (rc) return rc;
   rc = encode_map(c, &c->tmapBb, c->d_bsb, c->tc_kq, c->tc_kq, brows, c->tc_bn);
   if (rc) return rc;
+  if (c->d_bsv)
+    for (int f = 0; f < 6; ++f) {
+      unsigned short* base = reinterpret_cast<unsigned short*>(c->d_bsv) + (long long)f * 3 * brows * c->tc_kq;
+      if ((rc = encode_map(c, &c->tmapBv[f], base, c->tc_kq, c->tc_kq, brows, c->tc_bn))) return rc;
+    }
   // the attribute is a per-function ceiling shared by every context: the largest
   // size any tile width uses
   const int smem = (int)tc_smem(TC_MAX_BN);
@@ -483,6 +488,26 @@ int mlx_legendre_tc_forward(mlx_ctx* c, double2* spec, cudaStream_t st) {
   kern<<<grid, TC_THREADS, tc_smem(c->tc_bn), st>>>(
       c->tmapW, c->tmapBf, c->d_tc_fwd, c->ntc_fwd, c->nc, c->nr, c->M, c->K, c->tc_bn, c->tc_tmem_cols,
       c->tc_expire, c->d_soff, c->d_arowW, spec, nullptr, c->d_err);
+  MLX_LAUNCH_CHECK(c);
+  return MLX_OK;
+}
+
+int mlx_tc_vortex_planes(mlx_ctx* c, cudaStream_t st) {
+  if (c->d_bsv) return MLX_OK;
+  const long long brows = (long long)c->M * 2 * c->K;
+  const size_t bytes = sizeof(__nv_bfloat16) * 6 * 3 * brows * c->tc_kq;
+  MLX_CUDA_TRY(c, cudaMalloc(&c->d_bsv, bytes));
+  MLX_CUDA_TRY(c, cudaMemsetAsync(c->d_bsv, 0, bytes, st));   // row tails n - m >= Nc - m stay zero
+  return mlx_tc_retile(c, c->tc_bn, st);                       // encodes the six maps
+}
+
+int mlx_legendre_tc_backward_field(mlx_ctx* c, int f, cudaStream_t st) {
+  TimedLaunch tl(c, KID_LEG_BWD, st);
+  const int grid = c->ntc_bwd < sm_count() ? c->ntc_bwd : sm_count();
+  auto kern = c->tc_products == 8 ? k_leg_tc<false, 8> : k_leg_tc<false, 6>;
+  kern<<<grid, TC_THREADS, tc_smem(c->tc_bn), st>>>(
+      c->tmapP, c->tmapBv[f], c->d_tc_bwd, c->ntc_bwd, c->nc, c->nr, c->M, c->K, c->tc_bn, c->tc_tmem_cols,
+      c->tc_expire, c->d_soff, c->d_arowP, nullptr, (float*)c->d_mixed, c->d_err);
   MLX_LAUNCH_CHECK(c);
   return MLX_OK;
 }

@@ -122,6 +122,10 @@ struct mlx_ctx {
   void* d_bsf = nullptr;               // BF16 splits of the forward data operand: [3][M*2K][Kp]
   void* d_bsb = nullptr;               // ... of the backward data operand: [3][M*2K][Kq]
   CUtensorMap tmapBf, tmapBb;
+  // the six vortex fields' backward data operands, written by the fields kernel:
+  // [6][3][M*2K][Kq] with one tensor map per field (BF16X3 vortex contexts)
+  void* d_bsv = nullptr;
+  CUtensorMap tmapBv[6];
   long long tc_kp = 0, tc_kq = 0;      // padded contraction lengths (multiples of 32)
   long long* d_arowW = nullptr;
   long long* d_arowP = nullptr;
@@ -190,6 +194,7 @@ struct mlx_ctx {
   int solve_nopiv = 1;                 // 1: the segmented solve skips pivoting for families without interchanges
   int solve_fields2 = 1;               // 1: the lean solve takes both vortex fields in one launch
   int plane_reuse = 1;                 // 1: the graph-replayed FKPP steps reuse the solve's split planes
+  int vortex_planes = 1;               // 1: the BF16X3 vortex fields are written as split planes directly
 
   // graphs cached per (state, prev_A, kind, gamma, variant); variant 1 is the pair
   // that reuses the split planes the previous pair left (graph_left: the pair leaves them)
@@ -290,6 +295,10 @@ int mlx_tc_retile(mlx_ctx* c, int bn, cudaStream_t st);
 int mlx_enqueue_step_pair(mlx_ctx* c, int kind, double c0, double2* s, double2* Ap, cudaStream_t st);
 int mlx_legendre_tc_forward(mlx_ctx* c, double2* spec, cudaStream_t st);
 int mlx_legendre_tc_backward(mlx_ctx* c, const double2* spec, cudaStream_t st, bool planes_ready = false);
+// the backward contraction of vortex field f from its split planes in d_bsv
+int mlx_legendre_tc_backward_field(mlx_ctx* c, int f, cudaStream_t st);
+// allocate d_bsv (zero tails) and encode its maps (BF16X3 vortex contexts)
+int mlx_tc_vortex_planes(mlx_ctx* c, cudaStream_t st);
 // nfields = 2: both fields of a vortex state (n_spec apart) in one launch (lean
 // variant only; MLX_EINVAL otherwise).  sp: where the segmented solve also writes
 // the BF16x3 split planes of its output for the backward contraction; *wrote says

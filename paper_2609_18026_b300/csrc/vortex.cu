@@ -21,6 +21,7 @@
 // polynomials of degree <= 3 in x at (m, k) = (0, 0) and are added to those blocks
 // of the fields; the background is U = U0 e_y + Uz e_z.
 #include "mlx_internal.cuh"
+#include "bf16_split.cuh"
 
 #include <cmath>
 
@@ -70,7 +71,7 @@ __global__ void k_vortex_fields(int nc, int Kz, int K, double lz, const long lon
                                 const double2* __restrict__ chi, double2* __restrict__ rvr,
                                 double2* __restrict__ rvp, double2* __restrict__ vz, double2* __restrict__ rwr,
                                 double2* __restrict__ rwp, double2* __restrict__ wz,
-                                const double* __restrict__ lpf) {
+                                const double* __restrict__ lpf, SplitPlanes vp) {
   extern __shared__ double2 vsh[];   // [4][nc]: psi, chi, D chi, Psi
   const int kidx = blockIdx.x, m = blockIdx.y;
   const int Nm = nc - m;
@@ -106,12 +107,30 @@ __global__ void k_vortex_fields(int nc, int Kz, int K, double lz, const long lon
       fwp.x += lpf[8 + a];
       fwz.x += lpf[12 + a];
     }
-    rvr[idx] = cadd(cimul(mm, P[a]), cimul(kap, Rchi));
-    rvp[idx] = fvp;
-    vz[idx] = fvz;
-    rwr[idx] = cadd(cimul(mm, Ps[a]), cimul(kap, Rpsi));
-    rwp[idx] = fwp;
-    wz[idx] = fwz;
+    const double2 fvr = cadd(cimul(mm, P[a]), cimul(kap, Rchi));
+    const double2 fwr = cadd(cimul(mm, Ps[a]), cimul(kap, Rpsi));
+    if (vp.bs) {
+      // BF16X3: the six fields straight into their split planes (the backward
+      // contraction's data operands), as k_split_spec would write them
+      const double2 fv[6] = {fvr, fvp, fvz, fwr, fwp, fwz};
+      const long long o = ((long long)m * vp.K2 + 2 * kidx) * vp.Kq + a;
+#pragma unroll
+      for (int f = 0; f < 6; ++f) {
+        unsigned short* b = vp.bs + (long long)f * 3 * vp.part;
+        unsigned short h, md, lo;
+        split3_f64(fv[f].x, h, md, lo);
+        b[o] = h; b[vp.part + o] = md; b[2 * vp.part + o] = lo;
+        split3_f64(fv[f].y, h, md, lo);
+        b[o + vp.Kq] = h; b[vp.part + o + vp.Kq] = md; b[2 * vp.part + o + vp.Kq] = lo;
+      }
+    } else {
+      rvr[idx] = fvr;
+      rvp[idx] = fvp;
+      vz[idx] = fvz;
+      rwr[idx] = fwr;
+      rwp[idx] = fwp;
+      wz[idx] = fwz;
+    }
   }
 }
 
@@ -535,6 +554,7 @@ int mlx_vortex_prepare(mlx_ctx* c, cudaStream_t st) {
   k_jac_table<<<nblk(c->tri, 256), 256, 0, st>>>(c->M, c->nc, c->d_lap_off, c->d_jac);
   MLX_LAUNCH_CHECK(c);
   MLX_CUDA_TRY(c, cudaMalloc(&c->d_vspec, sizeof(double2) * c->n_spec * 9));
+  if (c->precision == MLX_BF16X3 && (rc = mlx_tc_vortex_planes(c, st))) return rc;
   MLX_CUDA_TRY(c, cudaMalloc(&c->d_vphys, es * c->n_phys * 6));
   // two-field state temporaries for the Richardson start and the graph-replayed pair
   for (double2** p : {&c->d_specA, &c->d_spec1, &c->d_spec2, &c->d_spec3}) {
@@ -558,16 +578,23 @@ static int vortex_nonlinear_t(mlx_ctx* c, double U0, const double2* state, doubl
   T* P[6];
   for (int i = 0; i < 6; ++i) P[i] = reinterpret_cast<T*>(c->d_vphys) + np * i;
   const int tb = 256;
+  SplitPlanes planes;   // BF16X3: the fields go straight to the backward contraction's planes
+  if (c->precision == MLX_BF16X3 && c->d_bsv && c->vortex_planes) {
+    planes.bs = reinterpret_cast<unsigned short*>(c->d_bsv);
+    planes.Kq = (int)c->tc_kq;
+    planes.K2 = 2 * c->K;
+    planes.part = (long long)c->M * planes.K2 * planes.Kq;
+  }
   {
     const int vt = c->nc >= 256 ? 256 : ((c->nc + 31) / 32) * 32;
     k_vortex_fields<<<dim3(c->K, c->M), vt, sizeof(double2) * 4 * c->nc, st>>>(
         c->nc, c->Kz, c->K, c->lz, c->d_soff, c->d_lap_off, c->d_rdr, c->d_lap, psi, chi, F[0], F[1], F[2], F[3],
-        F[4], F[5], c->lp_on ? c->d_lp + kLpFields : nullptr);
+        F[4], F[5], c->lp_on ? c->d_lp + kLpFields : nullptr, planes);
   }
   MLX_LAUNCH_CHECK(c);
   int rc;
   for (int f = 0; f < 6; ++f) {
-    if ((rc = mlx_legendre_backward(c, F[f], st))) return rc;
+    if ((rc = planes.bs ? mlx_legendre_tc_backward_field(c, f, st) : mlx_legendre_backward(c, F[f], st))) return rc;
     if ((rc = mlx_fft_backward(c, P[f], st))) return rc;
   }
   k_vortex_product<T><<<nblk(np, tb), tb, 0, st>>>(np, c->nphi, c->nr, (T)U0, (T)c->vortex_uz, c->d_r, P[0], P[1], P[2], P[3],
@@ -612,7 +639,7 @@ extern "C" int mlx_axial_energy(mlx_ctx* c, const void* state, double* E, mlx_st
   // the basis part only: the log proxy's swirl has unbounded energy
   k_vortex_fields<<<dim3(c->K, c->M), vt, sizeof(double2) * 4 * c->nc, st>>>(
       c->nc, c->Kz, c->K, c->lz, c->d_soff, c->d_lap_off, c->d_rdr, c->d_lap, psi, chi, F[0], F[1], F[2], F[3],
-      F[4], F[5], nullptr);
+      F[4], F[5], nullptr, SplitPlanes());
   MLX_LAUNCH_CHECK(c);
   // the partial sums go to the (then unused) seventh spectral temporary
   double* part = reinterpret_cast<double*>(c->d_vspec + ns * 6);
@@ -709,7 +736,7 @@ static int vortex_diag_t(mlx_ctx* c, const double2* state, mlx_vortex_diag_out* 
   const int vt = c->nc >= 256 ? 256 : ((c->nc + 31) / 32) * 32;
   k_vortex_fields<<<dim3(c->K, c->M), vt, sizeof(double2) * 4 * c->nc, st>>>(
       c->nc, c->Kz, c->K, c->lz, c->d_soff, c->d_lap_off, c->d_rdr, c->d_lap, state, state + ns, F[0], F[1], F[2],
-      F[3], F[4], F[5], c->lp_on ? c->d_lp + kLpFields : nullptr);
+      F[3], F[4], F[5], c->lp_on ? c->d_lp + kLpFields : nullptr, SplitPlanes());
   MLX_LAUNCH_CHECK(c);
   int rc;
   for (int f = 3; f < 6; ++f) {

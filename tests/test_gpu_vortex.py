@@ -276,3 +276,26 @@ def test_lean_two_field_launch_bitwise(cpw):
         outs.append(state.cpu().numpy())
     assert np.all(np.isfinite(outs[0]))
     assert np.array_equal(outs[0], outs[1])
+
+
+def test_vortex_fields_written_as_split_planes_bitwise():
+    # BF16x3: the six velocity / vorticity fields written straight into their split
+    # planes give the same nonlinear term, bit for bit, as FP64 fields split by
+    # k_split_spec; and an advance agrees as well
+    g, ctx = pair(48, 32, 16, 1.0, lz=8.6, policy="twothirds", precision=B.BF16X3)
+    ctx.vortex_setup()
+    ctx.implicit_setup(1e-3, 5e-3, nu_h=1e-5, p=8)
+    psi, chi = _smooth_state(g, 51)
+    outs, advs = [], []
+    for vp in (1, 0):
+        ctx.set_tuning("vortex_planes", vp)
+        state = to_gpu_spec(np.concatenate([psi, chi]))
+        out = ctx.nonlinear(B.NONLIN_VORTEX, [0.7], state, to_gpu_spec(np.zeros(2 * len(psi), np.complex128)))
+        outs.append(out.cpu().numpy())
+        prev = to_gpu_spec(np.zeros(2 * len(psi), np.complex128))
+        ctx.advance(B.NONLIN_VORTEX, [0.7], state, prev, 4, True)
+        advs.append(state.cpu().numpy())
+    assert np.all(np.isfinite(outs[0]))
+    assert np.array_equal(outs[0], outs[1])
+    assert np.array_equal(advs[0], advs[1])
+    ctx.device_status()
