@@ -651,10 +651,11 @@ def measure_batch(B, W, torch, dev, stream, steps=100, n=64, tune_cache=None):
     """64 uneven independent 2-D/3-D diffusion and Fisher-KPP instances (seed
     20261202: Nr in {32..256}, Nphi in {16..256}, Nz in {1, 16, 64}, ell in
     [0.5, 4]), FP32 transforms (BF16x3 contraction), FP64 solves, dt = 1e-3,
-    advanced together by one CUDA graph per step pair.  Timed twice: with the
-    batch's default launch shapes, and with every member's shapes chosen by the
-    autotuner (read from tune_cache when it holds them, else timed now and
-    appended to it)."""
+    advanced together by one CUDA graph per step pair: per-phase persistent
+    queue launches (the default) and, for comparison, one graph branch per
+    member.  Timed with the batch's default launch shapes and with every
+    member's shapes chosen by the autotuner (read from tune_cache when it holds
+    them, else timed now and appended to it)."""
     import math as _m
     t0 = time.perf_counter()
     insts = W.batch_instances(n)
@@ -689,6 +690,9 @@ def measure_batch(B, W, torch, dev, stream, steps=100, n=64, tune_cache=None):
         return e0.elapsed_time(e1)
 
     ms = timed_batch()
+    batch.set_persistent(0)
+    ms_branches = timed_batch()
+    batch.set_persistent(1)
     # the same instances one after another (graph per instance), for comparison
     e0.record(stream)
     for j, ctx in enumerate(ctxs):
@@ -706,17 +710,24 @@ def measure_batch(B, W, torch, dev, stream, steps=100, n=64, tune_cache=None):
             from_cache += int(got["from_cache"])
         tune_s = time.perf_counter() - t1
         ms_tuned = timed_batch()
+        batch.set_persistent(0)
+        ms_tuned_branches = timed_batch()
+        batch.set_persistent(1)
     ok = all(bool(torch.isfinite(s.real).all().item()) for s in states)
     batch.close()
     for c in ctxs:
         c.close()
-    out = {"workload": "batch64_uneven", "instances": n, "instance_timesteps_per_s": n * steps / (ms / 1000.0),
+    out = {"workload": "batch64_uneven", "graph": "persistent per-phase queue launches", "instances": n,
+           "instance_timesteps_per_s": n * steps / (ms / 1000.0),
            "batch_step_ms": ms / steps, "sequential_instance_timesteps_per_s": n * steps / (ms_seq / 1000.0),
-           "speedup_vs_sequential": ms_seq / ms, "timed_steps": steps, "setup_s": setup_s, "finite": ok}
+           "speedup_vs_sequential": ms_seq / ms, "timed_steps": steps, "setup_s": setup_s, "finite": ok,
+           "branches": {"instance_timesteps_per_s": n * steps / (ms_branches / 1000.0),
+                        "batch_step_ms": ms_branches / steps}}
     if ms_tuned is not None:
         out["autotuned"] = {"instances": tuned, "from_cache": from_cache, "tune_s": tune_s,
                             "instance_timesteps_per_s": n * steps / (ms_tuned / 1000.0),
-                            "batch_step_ms": ms_tuned / steps}
+                            "batch_step_ms": ms_tuned / steps,
+                            "branches_instance_timesteps_per_s": n * steps / (ms_tuned_branches / 1000.0)}
     return out
 
 

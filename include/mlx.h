@@ -430,13 +430,34 @@ int mlx_batch_destroy(mlx_batch* batch);
 
 /* Advance every instance i of the batch by nsteps AB-CN steps, exactly as
  * mlx_advance(ctxs[i], kinds[i], &coeffs[i], 1, states[i], prev_As[i], nsteps,
- * start) would (same arithmetic, bitwise), but with the two-step pairs of all
- * instances captured into ONE CUDA graph whose branches (one per instance) run
- * concurrently; one graph launch per pair advances the whole batch.  The graph
- * is cached per set of (state, prev_A, kind, coefficient).  MLX_ESTATE if an
- * instance lacks mlx_implicit_setup (or mlx_vortex_setup for the vortex kind). */
+ * start) would (same arithmetic, bitwise), with the two-step pairs of all
+ * instances captured into ONE CUDA graph; one graph launch per pair advances the
+ * whole batch.  The Richardson start (start != 0) and an odd last step run per
+ * instance.  The graph takes one of two forms (mlx_batch_set_persistent):
+ *  - persistent (default, used when every instance is MLX_NONLIN_NONE or
+ *    MLX_NONLIN_FKPP, has no filter, Nphi <= 256 and Nz <= 256, and, for
+ *    MLX_BF16X3, six split products): each phase of a time step is one persistent
+ *    kernel launch whose CTAs (warps for the solve) take (instance, tile) work
+ *    items of all instances from a queue, largest first -- the BF16x3 split of the
+ *    states with the backward contraction (tensor-core launches serve up to 64
+ *    instances each), the inverse z transform, the fused phi synthesis / product /
+ *    analysis, the forward z transform, the forward contraction and the banded
+ *    solve (one launch per half width and shared-memory size class).  Instances
+ *    without a nonlinear term only solve, on a graph branch beside the transform
+ *    phases.  Each instance keeps its own launch shapes (transform tiles,
+ *    column-tile width, chains per warp), and no kernel waits on another CTA;
+ *  - branches: every instance's own kernel sequence on its own graph branch,
+ *    the branches running concurrently.
+ * The graph is cached per set of (state, prev_A, kind, coefficient) and
+ * recaptured when a member's tuning or setup changes.  MLX_ESTATE if an instance
+ * lacks mlx_implicit_setup (or mlx_vortex_setup for the vortex kind). */
 int mlx_batch_advance(mlx_batch* batch, const int* kinds, const double* coeffs, void* const* states,
                       void* const* prev_As, int nsteps, int start, mlx_stream stream);
+
+/* Select the batch's graph form: 1 (default) persistent per-phase launches
+ * whenever the instances qualify (see mlx_batch_advance), 0 one graph branch per
+ * instance.  Both give bitwise-equal results.  MLX_EINVAL for another value. */
+int mlx_batch_set_persistent(mlx_batch* batch, int on);
 
 /* Choose the launch shapes of ctx for its nonlinear `kind` by timing candidates
  * with CUDA events on the context's temporaries: the tensor-core column-tile

@@ -29,7 +29,8 @@ EXPORTS = ("mlx_strerror", "mlx_last_cuda_error", "mlx_create", "mlx_destroy", "
            "mlx_filter_setup", "mlx_filter_apply", "mlx_filter_state", "mlx_axial_energy",
            "mlx_vortex_setup", "mlx_lap_h_solve", "mlx_lap_h_solve_log", "mlx_vortex_logproxy",
            "mlx_vortex_diag",
-           "mlx_batch_create", "mlx_batch_destroy", "mlx_batch_advance", "mlx_autotune",
+           "mlx_batch_create", "mlx_batch_destroy", "mlx_batch_advance", "mlx_batch_set_persistent",
+           "mlx_autotune",
            "mlx_sur_create", "mlx_sur_destroy", "mlx_sur_param_count", "mlx_sur_get_params",
            "mlx_sur_set_params", "mlx_sur_get_grads", "mlx_sur_get_scales", "mlx_sur_set_scales",
            "mlx_sur_propagate", "mlx_sur_observe", "mlx_sur_finalize_scales", "mlx_sur_make_pair",
@@ -119,6 +120,7 @@ def load():
     lib.mlx_vortex_diag.argtypes = [vp, vp, ctypes.POINTER(VortexDiagOut), vp]
     lib.mlx_batch_create.argtypes = [ctypes.POINTER(vp), i, ctypes.POINTER(vp)]
     lib.mlx_batch_destroy.argtypes = [vp]
+    lib.mlx_batch_set_persistent.argtypes = [vp, i]
     lib.mlx_batch_advance.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(d), ctypes.POINTER(vp),
                                       ctypes.POINTER(vp), i, i, vp]
     lib.mlx_autotune.argtypes = [vp, i, ctypes.POINTER(d), i, ctypes.c_char_p, ctypes.POINTER(i), vp]
@@ -375,6 +377,11 @@ class Batch:
         if rc != 0:
             raise MlxError(rc, "libmlx: mlx_batch_create failed (code %d)" % rc)
         self._h = h
+
+    def set_persistent(self, on):
+        rc = self.lib.mlx_batch_set_persistent(self._h, int(bool(on)))
+        if rc != 0:
+            raise MlxError(rc, "libmlx: mlx_batch_set_persistent failed (code %d)" % rc)
 
     def advance(self, kinds, coeffs, states, prevs, nsteps, start, stream=None):
         n = len(self.contexts)

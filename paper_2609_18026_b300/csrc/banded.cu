@@ -18,6 +18,7 @@
 #include "mlx_internal.cuh"
 #include "bf16_split.cuh"
 
+#include <string.h>
 #include <type_traits>
 
 namespace {
@@ -387,19 +388,20 @@ struct SolveSmem {
   }
 };
 
+// The work of one warp: systems (m, |k| = k0 .. k0 + G - 1), gw = m groups_per_m
+// + group; base: the warp's shared-memory slab.
 template <int KL>
-__global__ void k_band_solve(int M, int nc, int Kz, int K, int CPW, int groups_per_m, int step, int keep_s,
-                             double dt, const long long* __restrict__ soff,
-                             const long long* __restrict__ band_off, int kz_fac, int m0_shift,
-                             const double* __restrict__ U,
-                             const double* __restrict__ Lm, const int* __restrict__ piv,
-                             const double* __restrict__ invd, const double* __restrict__ s,
-                             const double* __restrict__ A, const double* __restrict__ Ap,
-                             double* __restrict__ out) {
+__device__ __forceinline__ void band_solve_warp(int gw, unsigned char* __restrict__ base, int M, int nc, int Kz,
+                                                int K, int CPW, int groups_per_m, int step, int keep_s,
+                                                double dt, const long long* __restrict__ soff,
+                                                const long long* __restrict__ band_off, int kz_fac, int m0_shift,
+                                                const double* __restrict__ U,
+                                                const double* __restrict__ Lm, const int* __restrict__ piv,
+                                                const double* __restrict__ invd, const double* __restrict__ s,
+                                                const double* __restrict__ A, const double* __restrict__ Ap,
+                                                double* __restrict__ out, double* __restrict__ Az = nullptr) {
   constexpr int W = 2 * KL + 1;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const int gw = blockIdx.x * (blockDim.x >> 5) + wib;   // global warp = (m, group)
+  const int lane = threadIdx.x & 31;
   if (gw >= M * groups_per_m) return;
   const int m = gw / groups_per_m;
   const int G = CPW / 4;
@@ -408,7 +410,6 @@ __global__ void k_band_solve(int M, int nc, int Kz, int K, int CPW, int groups_p
   const int sh = (m == 0) ? m0_shift : 0;   // Laplacian at m = 0: unknowns n >= 1
   const int Nm = nc - m;
   const int N = Nm - sh;
-  unsigned char* base = smem_raw + (size_t)wib * SolveSmem<KL>::per_warp(nc, CPW, keep_s);
   double* Us = reinterpret_cast<double*>(base);              // [N][G][W]
   double* Ls = Us + (size_t)N * G * W;                       // [N][G][KL]
   double* Ds = Ls + (size_t)N * G * KL;                      // [N][G]
@@ -574,7 +575,49 @@ __global__ void k_band_solve(int M, int nc, int Kz, int K, int CPW, int groups_p
       }
     }
     out2[pbase + i] = v;
+    // a batched member without a nonlinear term: its A^j (zero) written where
+    // the single-context step clears it
+    if (Az) reinterpret_cast<double2*>(Az)[pbase + i] = make_double2(0.0, 0.0);
   }
+}
+
+template <int KL>
+__global__ void k_band_solve(int M, int nc, int Kz, int K, int CPW, int groups_per_m, int step, int keep_s,
+                             double dt, const long long* __restrict__ soff,
+                             const long long* __restrict__ band_off, int kz_fac, int m0_shift,
+                             const double* __restrict__ U,
+                             const double* __restrict__ Lm, const int* __restrict__ piv,
+                             const double* __restrict__ invd, const double* __restrict__ s,
+                             const double* __restrict__ A, const double* __restrict__ Ap,
+                             double* __restrict__ out) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int wib = threadIdx.x >> 5;
+  const int gw = blockIdx.x * (blockDim.x >> 5) + wib;   // global warp = (m, group)
+  unsigned char* base = smem_raw + (size_t)wib * SolveSmem<KL>::per_warp(nc, CPW, keep_s);
+  band_solve_warp<KL>(gw, base, M, nc, Kz, K, CPW, groups_per_m, step, keep_s, dt, soff, band_off, kz_fac,
+                      m0_shift, U, Lm, piv, invd, s, A, Ap, out);
+}
+
+// Batched persistent form (batch.cu): every warp takes (member, warp task) items
+// from the queue into its own slab of `slab` bytes (the largest any member needs).
+template <int KL>
+__global__ void kb_band_solve(const BSolveJob* __restrict__ jobs, const int2* __restrict__ items, int nitems,
+                              int slab, int* __restrict__ ctr) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  unsigned char* base = smem_raw + (size_t)wib * slab;
+  for (;;) {
+    int it = 0;
+    if (lane == 0) it = atomicAdd(ctr, 1);
+    it = __shfl_sync(0xffffffffu, it, 0);
+    if (it >= nitems) break;
+    const int2 w = items[it];
+    const BSolveJob j = jobs[w.x];
+    band_solve_warp<KL>(w.y, base, j.M, j.nc, j.Kz, j.K, j.CPW, j.gpm, j.step, 0, j.dt, j.soff, j.band_off,
+                        j.kz_fac, 0, j.U, j.L, j.piv, j.invd, j.s, j.A, j.Ap, j.out, j.Az);
+    __syncwarp();   // the slab is restaged by the next item
+  }
+  if (lane == 0) bq_finish(ctr, gridDim.x * (blockDim.x >> 5));
 }
 
 
@@ -710,29 +753,32 @@ __global__ void k_seg_setup(int M, int nc, int Kz, const long long* __restrict__
 // the family, so the pivoted U rows carry exact zeros beyond the KL-th upper
 // entry; the recurrences then skip the swaps and those zero terms (the same
 // products in the same order: bitwise equal results, up to the sign of zero).
+// The work of one warp (gw = m groups_per_m + group) in its shared-memory slab
+// `base`; Az (may be NULL) as in band_solve_warp.
 template <int KL, int SEG, bool NP>
-__global__ void k_band_solve_seg(int M, int nc, int Kz, int K, int groups_per_m, int step, int keep_s,
-                                 double dt, const long long* __restrict__ soff,
-                                 const long long* __restrict__ band_off, const double* __restrict__ U,
-                                 const double* __restrict__ Lm, const int* __restrict__ piv,
-                                 const double* __restrict__ invd, const double* __restrict__ PHf,
-                                 const double* __restrict__ PHb, const double* __restrict__ PSf,
-                                 const double* __restrict__ RNP,
-                                 const double* __restrict__ s, const double* __restrict__ A,
-                                 const double* __restrict__ Ap, double* __restrict__ out,
-                                 SplitPlanes sp) {
+__device__ __forceinline__ void band_solve_seg_warp(int gw, unsigned char* __restrict__ base, int M, int nc,
+                                                    int Kz, int K, int groups_per_m, int step, int keep_s,
+                                                    double dt, const long long* __restrict__ soff,
+                                                    const long long* __restrict__ band_off,
+                                                    const double* __restrict__ U,
+                                                    const double* __restrict__ Lm, const int* __restrict__ piv,
+                                                    const double* __restrict__ invd,
+                                                    const double* __restrict__ PHf,
+                                                    const double* __restrict__ PHb,
+                                                    const double* __restrict__ PSf,
+                                                    const double* __restrict__ RNP,
+                                                    const double* __restrict__ s, const double* __restrict__ A,
+                                                    const double* __restrict__ Ap, double* __restrict__ out,
+                                                    const SplitPlanes& sp, double* __restrict__ Az = nullptr) {
   using SM = SegSmem<KL, SEG>;
   constexpr int W = SM::W, CPW = SM::CPW, G = SM::G, RW = SM::RW;
   constexpr int UW = NP ? KL : 2 * KL;                      // upper entries the substitution reads
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const int gw = blockIdx.x * (blockDim.x >> 5) + wib;
+  const int lane = threadIdx.x & 31;
   if (gw >= M * groups_per_m) return;
   const int m = gw / groups_per_m;
   const int k0 = (gw % groups_per_m) * G;
   const int gcnt = min(G, Kz - k0);
   const int N = nc - m;
-  unsigned char* base = smem_raw + (size_t)wib * SM::per_warp(nc, keep_s, NP);
   // pivoting form: U [N][G][W], L [N][G][KL], 1/diag [N][G], PHf [N][G][KL],
   // PHb [N][G][2KL]; pivot-free form: the records [G][N][RW]
   double* Us = reinterpret_cast<double*>(base);
@@ -983,6 +1029,7 @@ __global__ void k_band_solve_seg(int M, int nc, int Kz, int K, int groups_per_m,
       }
     }
     out2[pbase + i] = v;
+    if (Az) reinterpret_cast<double2*>(Az)[pbase + i] = make_double2(0.0, 0.0);
     if (sp.bs) {
       unsigned short h, md, lo;
       split3_f64(v.x, h, md, lo);
@@ -992,6 +1039,51 @@ __global__ void k_band_solve_seg(int M, int nc, int Kz, int K, int groups_per_m,
       sp.bs[o + sp.Kq] = h; sp.bs[sp.part + o + sp.Kq] = md; sp.bs[2 * sp.part + o + sp.Kq] = lo;
     }
   }
+}
+
+template <int KL, int SEG, bool NP>
+__global__ void k_band_solve_seg(int M, int nc, int Kz, int K, int groups_per_m, int step, int keep_s,
+                                 double dt, const long long* __restrict__ soff,
+                                 const long long* __restrict__ band_off, const double* __restrict__ U,
+                                 const double* __restrict__ Lm, const int* __restrict__ piv,
+                                 const double* __restrict__ invd, const double* __restrict__ PHf,
+                                 const double* __restrict__ PHb, const double* __restrict__ PSf,
+                                 const double* __restrict__ RNP,
+                                 const double* __restrict__ s, const double* __restrict__ A,
+                                 const double* __restrict__ Ap, double* __restrict__ out,
+                                 SplitPlanes sp) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int wib = threadIdx.x >> 5;
+  const int gw = blockIdx.x * (blockDim.x >> 5) + wib;
+  unsigned char* base = smem_raw + (size_t)wib * SegSmem<KL, SEG>::per_warp(nc, keep_s, NP);
+  band_solve_seg_warp<KL, SEG, NP>(gw, base, M, nc, Kz, K, groups_per_m, step, keep_s, dt, soff, band_off, U, Lm,
+                                   piv, invd, PHf, PHb, PSf, RNP, s, A, Ap, out, sp);
+}
+
+// Batched persistent form (batch.cu), as kb_band_solve: warps take (member, warp
+// task) items; the member's job also names its influence data and, optionally,
+// the split planes its output is written to.
+template <int KL, int SEG, bool NP>
+__global__ void kb_band_solve_seg(const BSolveJob* __restrict__ jobs, const int2* __restrict__ items, int nitems,
+                                  int slab, int* __restrict__ ctr) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  unsigned char* base = smem_raw + (size_t)wib * slab;
+  for (;;) {
+    int it = 0;
+    if (lane == 0) it = atomicAdd(ctr, 1);
+    it = __shfl_sync(0xffffffffu, it, 0);
+    if (it >= nitems) break;
+    const int2 w = items[it];
+    const BSolveJob j = jobs[w.x];
+    SplitPlanes sp;
+    sp.bs = j.bs; sp.part = j.part; sp.Kq = j.kq; sp.K2 = j.k2;
+    band_solve_seg_warp<KL, SEG, NP>(w.y, base, j.M, j.nc, j.Kz, j.K, j.gpm, j.step, 0, j.dt, j.soff, j.band_off,
+                                     j.U, j.L, j.piv, j.invd, j.PHf, j.PHb, j.PSf, j.RNP, j.s, j.A, j.Ap, j.out, sp,
+                                     j.Az);
+    __syncwarp();
+  }
+  if (lane == 0) bq_finish(ctr, gridDim.x * (blockDim.x >> 5));
 }
 
 __global__ void k_axpby(long long n, double a, const double2* __restrict__ x, double b,
@@ -1688,4 +1780,103 @@ int mlx_spec_axpby(mlx_ctx* c, double a, const double2* x, double b, const doubl
   k_axpby<<<(unsigned)((n + tb - 1) / tb), tb, 0, st>>>(n, a, x, b, y, out);
   MLX_LAUNCH_CHECK(c);
   return MLX_OK;
+}
+
+// ---- batched persistent staged solve (batch.cu) ----
+// Job and warp items of member c (index inst) for one AB-CN solve s, A, Ap -> out
+// (A, Ap may be NULL), half width c->kl; *slab: the member's shared memory per warp.
+// Az (may be NULL): a buffer the solve fills with zeros (the A^j of a member
+// without a nonlinear term).
+// planes: the segmented variant also writes the BF16x3 split planes of out into the
+// member's backward data operand (*wrote_planes tells whether it will).
+void mlx_band_batch_member(mlx_ctx* c, int inst, const double2* s, const double2* A, const double2* Ap,
+                           double2* out, double2* Az, bool planes, BSolveJob* job, std::vector<int2>& items,
+                           std::vector<double>& cost, int* slab, bool* wrote_planes) {
+  auto per_warp = [&](int cpw) -> size_t {
+    switch (c->kl) {
+      case 2: return SolveSmem<2>::per_warp(c->nc, cpw, 0);
+      case 4: return SolveSmem<4>::per_warp(c->nc, cpw, 0);
+      case 6: return SolveSmem<6>::per_warp(c->nc, cpw, 0);
+      default: return SolveSmem<8>::per_warp(c->nc, cpw, 0);
+    }
+  };
+  // the member's own variant: segmented (half width 2, influence data built) or
+  // staged with its chains per warp, as its single-context launch would take them
+  const BandLU& f = c->lu_half;
+  const bool seg = c->kl == 2 && c->solve_seg && f.PHf && f.seg;
+  const bool np = seg && f.nopiv && f.RNP;
+  int CPW = c->solve_cpw;
+  while (CPW > 4 && per_warp(CPW) > 200 * 1024) CPW /= 2;
+  size_t pw = per_warp(CPW);
+  if (seg) {
+    CPW = 32 / f.seg;
+    pw = f.seg == 8 ? SegSmem<2, 8>::per_warp(c->nc, 0, np) : SegSmem<2, 4>::per_warp(c->nc, 0, np);
+  }
+  BSolveJob j;
+  memset(&j, 0, sizeof(j));
+  j.variant = seg ? (f.seg == 8 ? 1 : 2) + (np ? 2 : 0) : 0;
+  j.M = c->M; j.nc = c->nc; j.Kz = c->Kz; j.K = c->K; j.CPW = CPW;
+  j.gpm = (c->Kz + CPW / 4 - 1) / (CPW / 4);
+  j.step = MLX_STEP_ABCN;
+  j.kz_fac = c->Kz;
+  j.dt = c->dt;
+  j.soff = c->d_soff; j.band_off = c->d_band_off;
+  j.U = f.U; j.L = f.L; j.piv = f.piv; j.invd = f.invd;
+  j.PHf = f.PHf; j.PHb = f.PHb; j.PSf = f.PSf; j.RNP = f.RNP;
+  j.s = (const double*)s; j.A = (const double*)A; j.Ap = (const double*)Ap; j.out = (double*)out;
+  j.Az = (double*)Az;
+  *wrote_planes = false;
+  if (seg && planes && c->precision == MLX_BF16X3 && c->d_bsb) {
+    j.bs = reinterpret_cast<unsigned short*>(c->d_bsb);
+    j.kq = (int)c->tc_kq;
+    j.k2 = 2 * c->K;
+    j.part = (long long)c->M * j.k2 * j.kq;
+    *wrote_planes = true;
+  }
+  *job = j;
+  *slab = (int)pw;
+  for (int gw = 0; gw < c->M * j.gpm; ++gw) {
+    items.push_back(make_int2(inst, gw));
+    cost.push_back((double)(c->nc - gw / j.gpm));
+  }
+}
+
+// the kernel of a batched solve group: variant 0 staged (half width kl), 1 / 2
+// segmented with 8 / 4 segments, 3 / 4 the same in the pivot-free form
+const void* mlx_band_batch_kernel(int kl, int variant) {
+  switch (variant) {
+    case 1: return (const void*)kb_band_solve_seg<2, 8, false>;
+    case 2: return (const void*)kb_band_solve_seg<2, 4, false>;
+    case 3: return (const void*)kb_band_solve_seg<2, 8, true>;
+    case 4: return (const void*)kb_band_solve_seg<2, 4, true>;
+    default: break;
+  }
+  switch (kl) {
+    case 2: return (const void*)kb_band_solve<2>;
+    case 4: return (const void*)kb_band_solve<4>;
+    case 6: return (const void*)kb_band_solve<6>;
+    case 8: return (const void*)kb_band_solve<8>;
+    default: return nullptr;
+  }
+}
+
+int mlx_band_batch_launch(int kl, int variant, const BSolveJob* jobs, const int2* items, int nitems, int slab,
+                          int wpb, int* ctr, int grid, cudaStream_t st) {
+  const size_t smem = (size_t)slab * wpb;
+  switch (variant) {
+    case 1: kb_band_solve_seg<2, 8, false><<<grid, 32 * wpb, smem, st>>>(jobs, items, nitems, slab, ctr); break;
+    case 2: kb_band_solve_seg<2, 4, false><<<grid, 32 * wpb, smem, st>>>(jobs, items, nitems, slab, ctr); break;
+    case 3: kb_band_solve_seg<2, 8, true><<<grid, 32 * wpb, smem, st>>>(jobs, items, nitems, slab, ctr); break;
+    case 4: kb_band_solve_seg<2, 4, true><<<grid, 32 * wpb, smem, st>>>(jobs, items, nitems, slab, ctr); break;
+    default: break;
+  }
+  if (variant) return cudaGetLastError() == cudaSuccess ? MLX_OK : MLX_ECUDA;
+  switch (kl) {
+    case 2: kb_band_solve<2><<<grid, 32 * wpb, smem, st>>>(jobs, items, nitems, slab, ctr); break;
+    case 4: kb_band_solve<4><<<grid, 32 * wpb, smem, st>>>(jobs, items, nitems, slab, ctr); break;
+    case 6: kb_band_solve<6><<<grid, 32 * wpb, smem, st>>>(jobs, items, nitems, slab, ctr); break;
+    case 8: kb_band_solve<8><<<grid, 32 * wpb, smem, st>>>(jobs, items, nitems, slab, ctr); break;
+    default: return MLX_EINVAL;
+  }
+  return cudaGetLastError() == cudaSuccess ? MLX_OK : MLX_ECUDA;
 }

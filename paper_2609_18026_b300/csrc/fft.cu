@@ -21,6 +21,7 @@
 #include "mlx_internal.cuh"
 
 #include <cuda_bf16.h>
+#include <string.h>
 
 namespace {
 
@@ -254,20 +255,19 @@ __device__ void phi_unpack_store(const C* L, int ld, int N, int B, int M, int Nr
   }
 }
 
+// One CTA tile of the phi transform: radii bx R .. bx R + R - 1 of z-plane z.
 template <typename T, int MODE, int E>
-__global__ void __launch_bounds__(256) k_phi(int N, int logN, int M, int Nr, int R,
-                                             T* __restrict__ phys, T* __restrict__ zre,
-                                             T* __restrict__ zim,
-                                             const typename C2T<T>::type* __restrict__ tw, T gamma,
-                                             int* __restrict__ err, SplitOut so) {
+__device__ __forceinline__ void phi_tile(int N, int logN, int M, int Nr, int R, int bx, int z,
+                                         T* __restrict__ phys, T* __restrict__ zre, T* __restrict__ zim,
+                                         const typename C2T<T>::type* __restrict__ tw, T gamma,
+                                         int* __restrict__ err, const SplitOut& so,
+                                         unsigned char* __restrict__ smem_raw) {
   typedef typename C2T<T>::type C;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   C* L = reinterpret_cast<C*>(smem_raw);
   const int B = R / 2;
   const int lR = __ffs(R) - 1;          // R and B are powers of two
   const int ld = N + 1;
-  const int r0 = blockIdx.x * R;
-  const int z = blockIdx.y;
+  const int r0 = bx * R;
   const long long plane = (long long)z * N * Nr;
   C* tws = L + (size_t)B * ld;          // the twiddle tables after the tile
   stage_twiddles(tws, tw, N);
@@ -372,18 +372,27 @@ __global__ void __launch_bounds__(256) k_phi(int N, int logN, int M, int Nr, int
   }
 }
 
+template <typename T, int MODE, int E>
+__global__ void __launch_bounds__(256) k_phi(int N, int logN, int M, int Nr, int R,
+                                             T* __restrict__ phys, T* __restrict__ zre,
+                                             T* __restrict__ zim,
+                                             const typename C2T<T>::type* __restrict__ tw, T gamma,
+                                             int* __restrict__ err, SplitOut so) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  phi_tile<T, MODE, E>(N, logN, M, Nr, R, blockIdx.x, blockIdx.y, phys, zre, zim, tw, gamma, err, so, smem_raw);
+}
+
 // Axial transform for one m and a tile of R radii: lines are radii.
 template <typename T, bool INVERSE, int E>
-__global__ void __launch_bounds__(256) k_z(int Nz, int logN, int Kz, int K, int M, int Nr, int R,
-                                           T* __restrict__ zre, T* __restrict__ zim,
-                                           T* __restrict__ mre, T* __restrict__ mim,
-                                           const typename C2T<T>::type* __restrict__ tw, SplitOut so) {
+__device__ __forceinline__ void z_tile(int Nz, int logN, int Kz, int K, int M, int Nr, int R, int bx, int m,
+                                       T* __restrict__ zre, T* __restrict__ zim,
+                                       T* __restrict__ mre, T* __restrict__ mim,
+                                       const typename C2T<T>::type* __restrict__ tw, const SplitOut& so,
+                                       unsigned char* __restrict__ smem_raw) {
   typedef typename C2T<T>::type C;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   C* L = reinterpret_cast<C*>(smem_raw);
   const int ld = Nz + 1;
-  const int r0 = blockIdx.x * R;
-  const int m = blockIdx.y;
+  const int r0 = bx * R;
   const int lR = __ffs(R) - 1;          // R is a power of two
   C* tws = L + (size_t)R * ld;          // the twiddle tables after the tile
   stage_twiddles(tws, tw, Nz);
@@ -479,6 +488,85 @@ __global__ void __launch_bounds__(256) k_z(int Nz, int logN, int Kz, int K, int 
       }
     }
   }
+}
+
+template <typename T, bool INVERSE, int E>
+__global__ void __launch_bounds__(256) k_z(int Nz, int logN, int Kz, int K, int M, int Nr, int R,
+                                           T* __restrict__ zre, T* __restrict__ zim,
+                                           T* __restrict__ mre, T* __restrict__ mim,
+                                           const typename C2T<T>::type* __restrict__ tw, SplitOut so) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  z_tile<T, INVERSE, E>(Nz, logN, Kz, K, M, Nr, R, blockIdx.x, blockIdx.y, zre, zim, mre, mim, tw, so, smem_raw);
+}
+
+// Batched persistent forms of the stages (batch.cu): every CTA takes (member,
+// radius tile, plane) items from the queue until it is empty; the member's job
+// gives the sizes and buffers and E (1..8: transforms of at most 256 points) the
+// register width of its lines.  The tile
+// functions are those of the single-context kernels, so each member's values are
+// bitwise those of its own launches.
+__device__ __forceinline__ SplitOut job_split(const BFftJob& j) {
+  SplitOut so;
+  if (j.bs) { so.bs = j.bs; so.part = j.part; so.Kp = j.kp; so.K2 = j.k2; }
+  return so;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) kb_phi_fkpp(const BFftJob* __restrict__ jobs, const int4* __restrict__ items,
+                                                  int nitems, int* __restrict__ ctr) {
+  typedef typename C2T<T>::type C;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int s_it;
+  for (;;) {
+    if (threadIdx.x == 0) s_it = atomicAdd(ctr, 1);
+    __syncthreads();
+    const int it = s_it;
+    if (it >= nitems) break;
+    const int4 w = items[it];
+    const BFftJob j = jobs[w.x];
+    const SplitOut so = job_split(j);
+    T* zre = (T*)j.b;
+    T* zim = (T*)j.c;
+    const C* tw = (const C*)j.tw;
+    switch (j.E) {
+      case 1: phi_tile<T, PHI_FKPP, 1>(j.N, j.logN, j.M, j.Nr, j.R, w.y, w.z, nullptr, zre, zim, tw, (T)j.gamma, j.err, so, smem_raw); break;
+      case 2: phi_tile<T, PHI_FKPP, 2>(j.N, j.logN, j.M, j.Nr, j.R, w.y, w.z, nullptr, zre, zim, tw, (T)j.gamma, j.err, so, smem_raw); break;
+      case 4: phi_tile<T, PHI_FKPP, 4>(j.N, j.logN, j.M, j.Nr, j.R, w.y, w.z, nullptr, zre, zim, tw, (T)j.gamma, j.err, so, smem_raw); break;
+      default: phi_tile<T, PHI_FKPP, 8>(j.N, j.logN, j.M, j.Nr, j.R, w.y, w.z, nullptr, zre, zim, tw, (T)j.gamma, j.err, so, smem_raw); break;
+    }
+    __syncthreads();   // the tile's shared memory and s_it are reused by the next item
+  }
+  if (threadIdx.x == 0) bq_finish(ctr, gridDim.x);
+}
+
+template <typename T, bool INV>
+__global__ void __launch_bounds__(256) kb_z(const BFftJob* __restrict__ jobs, const int4* __restrict__ items,
+                                           int nitems, int* __restrict__ ctr) {
+  typedef typename C2T<T>::type C;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int s_it;
+  for (;;) {
+    if (threadIdx.x == 0) s_it = atomicAdd(ctr, 1);
+    __syncthreads();
+    const int it = s_it;
+    if (it >= nitems) break;
+    const int4 w = items[it];
+    const BFftJob j = jobs[w.x];
+    const SplitOut so = job_split(j);
+    T* zre = (T*)j.a;
+    T* zim = (T*)j.b;
+    T* mre = (T*)j.c;
+    T* mim = (T*)j.d;
+    const C* tw = (const C*)j.tw;
+    switch (j.E) {
+      case 1: z_tile<T, INV, 1>(j.N, j.logN, j.Kz, j.K, j.M, j.Nr, j.R, w.y, w.z, zre, zim, mre, mim, tw, so, smem_raw); break;
+      case 2: z_tile<T, INV, 2>(j.N, j.logN, j.Kz, j.K, j.M, j.Nr, j.R, w.y, w.z, zre, zim, mre, mim, tw, so, smem_raw); break;
+      case 4: z_tile<T, INV, 4>(j.N, j.logN, j.Kz, j.K, j.M, j.Nr, j.R, w.y, w.z, zre, zim, mre, mim, tw, so, smem_raw); break;
+      default: z_tile<T, INV, 8>(j.N, j.logN, j.Kz, j.K, j.M, j.Nr, j.R, w.y, w.z, zre, zim, mre, mim, tw, so, smem_raw); break;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) bq_finish(ctr, gridDim.x);
 }
 
 int ilog2(int n) { int l = 0; while ((1 << l) < n) ++l; return l; }
@@ -651,6 +739,8 @@ int attr_all(mlx_ctx* c) {
 
 }  // namespace
 
+const void* mlx_fft_batch_kernel(int stage, bool dbl);
+
 // Opt every FFT kernel into the shared memory the launch helpers may ask for
 // (each launch stays below 200 KB).
 int mlx_fft_prepare(mlx_ctx* c) {
@@ -665,6 +755,13 @@ int mlx_fft_prepare(mlx_ctx* c) {
   if (!rc) rc = attr_all<double, 4>(c);
   if (!rc) rc = attr_all<double, 8>(c);
   if (!rc) rc = attr_all<double, 16>(c);
+  for (int stage = 0; stage < 3 && !rc; ++stage)
+    for (int d = 0; d < 2 && !rc; ++d)
+      if (cudaFuncSetAttribute(mlx_fft_batch_kernel(stage, d != 0), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               kSmemLimit) != cudaSuccess) {
+        c->last_err = "cudaFuncSetAttribute (batched FFT stage)";
+        rc = MLX_ECUDA;
+      }
   return rc;
 }
 
@@ -681,4 +778,93 @@ int mlx_fft_backward(mlx_ctx* c, void* phys, cudaStream_t st) {
 int mlx_fft_fkpp(mlx_ctx* c, double gamma, cudaStream_t st) {
   if (c->precision == MLX_FP64) return fft_fkpp_t<double>(c, gamma, st, c->d_twphi64, c->d_twz64);
   return fft_fkpp_t<float>(c, gamma, st, c->d_twphi32, c->d_twz32);
+}
+
+// ---- batched persistent Fisher-KPP stages (batch.cu) ----
+// Job and work items of member c (index inst) for one stage of the fused
+// Fisher-KPP transform sequence: stage 0 the inverse z transform (mixed -> zm),
+// 1 the phi synthesis / product / analysis, 2 the forward z transform (zm ->
+// mixed or the split planes).  Stages 0 and 2 exist for Nz > 1 only (returns
+// false otherwise).  cost[i]: relative work of items[i]; *smem: the shared memory
+// one of its CTAs needs.  The tiles are the member's own (its phi_tile / z_tile).
+bool mlx_fft_batch_member(mlx_ctx* c, int stage, double gamma, int inst, BFftJob* job,
+                          std::vector<int4>& items, std::vector<double>& cost, size_t* smem) {
+  const bool dbl = c->precision == MLX_FP64;
+  const size_t es = dbl ? 8 : 4, cs = 2 * es;
+  if ((stage == 0 || stage == 2) && c->nz == 1) return false;
+  BFftJob j;
+  memset(&j, 0, sizeof(j));
+  j.M = c->M;
+  j.Nr = c->nr;
+  j.Kz = c->Kz;
+  j.K = c->K;
+  j.gamma = gamma;
+  j.err = c->d_err;
+  char* mixed = (char*)c->d_mixed;
+  const long long plm = (long long)c->K * c->M * c->nr;
+  const SplitOut so = split_out(c);
+  if (stage == 1) {
+    const int N = c->nphi;
+    int R = c->phi_tile ? c->phi_tile : auto_tile(c->nr, c->nz, 2 * 148);
+    auto need = [&](int R_) { return ((size_t)(R_ / 2) * (N + 1) + N) * cs; };
+    while (need(R) > kSmemLimit && R > 2) R /= 2;
+    *smem = need(R);
+    j.N = N; j.logN = ilog2(N); j.R = R; j.E = N >= 32 ? N / 32 : 1;
+    j.tw = dbl ? (const void*)c->d_twphi64 : (const void*)c->d_twphi32;
+    if (c->nz == 1) {
+      j.b = mixed; j.c = mixed + plm * es;
+      if (so.bs) { j.bs = so.bs; j.part = so.part; j.kp = so.Kp; j.k2 = so.K2; }
+    } else {
+      const long long pl = (long long)c->nz * c->M * c->nr;
+      j.b = c->d_zm; j.c = (char*)c->d_zm + pl * es;
+    }
+    const double w = (double)N * (j.logN + 2) * R;
+    for (int z = 0; z < c->nz; ++z)
+      for (int bx = 0; bx < (c->nr + R - 1) / R; ++bx) { items.push_back(make_int4(inst, bx, z, 0)); cost.push_back(w); }
+  } else {
+    const int N = c->nz;
+    int R = c->z_tile ? c->z_tile : auto_tile(c->nr, c->M, 4 * 148);
+    auto need = [&](int R_) { return ((size_t)R_ * (N + 1) + N) * cs; };
+    while (need(R) > kSmemLimit && R > 1) R /= 2;
+    if (!c->z_tile)
+      while (R > 8 && need(R) > 34 * 1024) R /= 2;
+    *smem = need(R);
+    j.N = N; j.logN = ilog2(N); j.R = R; j.E = N >= 32 ? N / 32 : 1;
+    j.tw = dbl ? (const void*)c->d_twz64 : (const void*)c->d_twz32;
+    const long long plz = (long long)c->nz * c->M * c->nr;
+    j.a = c->d_zm; j.b = (char*)c->d_zm + plz * es;
+    j.c = mixed; j.d = mixed + plm * es;
+    if (stage == 2 && so.bs) { j.bs = so.bs; j.part = so.part; j.kp = so.Kp; j.k2 = so.K2; }
+    const double w = (double)N * (j.logN + 2) * R;
+    for (int m = 0; m < c->M; ++m)
+      for (int bx = 0; bx < (c->nr + R - 1) / R; ++bx) { items.push_back(make_int4(inst, bx, m, 0)); cost.push_back(w); }
+  }
+  *job = j;
+  return true;
+}
+
+// The kernel of a batched stage launch (stage as above, dbl: FP64 members).
+const void* mlx_fft_batch_kernel(int stage, bool dbl) {
+  if (dbl) {
+    if (stage == 0) return (const void*)kb_z<double, true>;
+    if (stage == 1) return (const void*)kb_phi_fkpp<double>;
+    return (const void*)kb_z<double, false>;
+  }
+  if (stage == 0) return (const void*)kb_z<float, true>;
+  if (stage == 1) return (const void*)kb_phi_fkpp<float>;
+  return (const void*)kb_z<float, false>;
+}
+
+int mlx_fft_batch_launch(int stage, bool dbl, const BFftJob* jobs, const int4* items, int nitems, int* ctr,
+                         size_t smem, int grid, cudaStream_t st) {
+  if (dbl) {
+    if (stage == 0) kb_z<double, true><<<grid, 256, smem, st>>>(jobs, items, nitems, ctr);
+    else if (stage == 1) kb_phi_fkpp<double><<<grid, 256, smem, st>>>(jobs, items, nitems, ctr);
+    else kb_z<double, false><<<grid, 256, smem, st>>>(jobs, items, nitems, ctr);
+  } else {
+    if (stage == 0) kb_z<float, true><<<grid, 256, smem, st>>>(jobs, items, nitems, ctr);
+    else if (stage == 1) kb_phi_fkpp<float><<<grid, 256, smem, st>>>(jobs, items, nitems, ctr);
+    else kb_z<float, false><<<grid, 256, smem, st>>>(jobs, items, nitems, ctr);
+  }
+  return cudaGetLastError() == cudaSuccess ? MLX_OK : MLX_ECUDA;
 }

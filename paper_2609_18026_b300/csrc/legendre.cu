@@ -14,17 +14,15 @@ namespace {
 
 constexpr int BM = 64, BN = 64, BK = 16, NT = 256;
 
+// One 64 x 64 output tile.
 template <typename T, bool FWD>
-__global__ void __launch_bounds__(NT) k_legendre(const LegTile* __restrict__ tiles, int nc, int nr,
-                                                 int M, int K, const long long* __restrict__ boff,
-                                                 const long long* __restrict__ soff,
-                                                 const T* __restrict__ table,  // W (fwd) or P (bwd)
-                                                 T* __restrict__ mixed,        // planar [2][K][M][Nr]
-                                                 double2* __restrict__ spec,
-                                                 const double2* __restrict__ addsrc, double alpha) {
-  __shared__ T As[BK][BM + 1];
-  __shared__ T Bs[BK][BN + 1];
-  const LegTile tile = tiles[blockIdx.x];
+__device__ __forceinline__ void leg_tile(const LegTile tile, int nc, int nr, int M, int K,
+                                         const long long* __restrict__ boff, const long long* __restrict__ soff,
+                                         const T* __restrict__ table,  // W (fwd) or P (bwd)
+                                         T* __restrict__ mixed,        // planar [2][K][M][Nr]
+                                         double2* __restrict__ spec,
+                                         const double2* __restrict__ addsrc, double alpha,
+                                         T (&As)[BK][BM + 1], T (&Bs)[BK][BN + 1]) {
   const int m = tile.m;
   const int Nm = nc - m;
   const int rows = FWD ? Nm : nr;         // output rows
@@ -107,7 +105,83 @@ __global__ void __launch_bounds__(NT) k_legendre(const LegTile* __restrict__ til
   }
 }
 
+template <typename T, bool FWD>
+__global__ void __launch_bounds__(NT) k_legendre(const LegTile* __restrict__ tiles, int nc, int nr,
+                                                 int M, int K, const long long* __restrict__ boff,
+                                                 const long long* __restrict__ soff,
+                                                 const T* __restrict__ table, T* __restrict__ mixed,
+                                                 double2* __restrict__ spec,
+                                                 const double2* __restrict__ addsrc, double alpha) {
+  __shared__ T As[BK][BM + 1];
+  __shared__ T Bs[BK][BN + 1];
+  leg_tile<T, FWD>(tiles[blockIdx.x], nc, nr, M, K, boff, soff, table, mixed, spec, addsrc, alpha, As, Bs);
+}
+
+// Batched persistent form (batch.cu): CTAs take (member, tile) items from the
+// queue; item = {m, row0, col0, member}.
+template <typename T, bool FWD>
+__global__ void __launch_bounds__(NT) kb_legendre(const BLegJob* __restrict__ jobs, const LegTile* __restrict__ items,
+                                                  int nitems, int* __restrict__ ctr) {
+  __shared__ T As[BK][BM + 1];
+  __shared__ T Bs[BK][BN + 1];
+  __shared__ int s_it;
+  for (;;) {
+    if (threadIdx.x == 0) s_it = atomicAdd(ctr, 1);
+    __syncthreads();
+    const int it = s_it;
+    if (it >= nitems) break;
+    const LegTile t = items[it];
+    const BLegJob j = jobs[t.pad];
+    leg_tile<T, FWD>(t, j.nc, j.nr, j.M, j.K, j.boff, j.soff, (const T*)j.table, (T*)j.mixed, j.spec, nullptr,
+                     0.0, As, Bs);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) bq_finish(ctr, gridDim.x);
+}
+
 }  // namespace
+
+int mlx_legendre_tiles(mlx_ctx* c, std::vector<LegTile>& fwd, std::vector<LegTile>& bwd);
+
+// ---- batched persistent SIMT contraction (FP32 / FP64 members) ----
+// Job and items of member c (index inst): forward (mixed -> spec) or backward
+// (spec -> mixed), the member's own 64 x 64 tiles.
+void mlx_legendre_batch_member(mlx_ctx* c, bool fwd, int inst, double2* spec, BLegJob* job,
+                               std::vector<LegTile>& items, std::vector<double>& cost) {
+  BLegJob j;
+  j.nc = c->nc; j.nr = c->nr; j.M = c->M; j.K = c->K;
+  j.boff = c->d_boff; j.soff = c->d_soff;
+  const bool dbl = c->precision == MLX_FP64;
+  j.table = fwd ? (dbl ? (const void*)c->d_W64 : (const void*)c->d_W32)
+                : (dbl ? (const void*)c->d_P64 : (const void*)c->d_P32);
+  j.mixed = c->d_mixed;
+  j.spec = spec;
+  *job = j;
+  std::vector<LegTile> tf, tb;
+  mlx_legendre_tiles(c, tf, tb);
+  for (const LegTile& t : (fwd ? tf : tb)) {
+    const int kdim = fwd ? c->nr : c->nc - t.m;
+    items.push_back(LegTile{t.m, t.row0, t.col0, inst});
+    cost.push_back((double)((kdim + BK - 1) / BK));
+  }
+}
+
+int mlx_legendre_batch_launch(bool fwd, bool dbl, const BLegJob* jobs, const LegTile* items, int nitems,
+                              int* ctr, int grid, cudaStream_t st) {
+  if (dbl) {
+    if (fwd) kb_legendre<double, true><<<grid, NT, 0, st>>>(jobs, items, nitems, ctr);
+    else kb_legendre<double, false><<<grid, NT, 0, st>>>(jobs, items, nitems, ctr);
+  } else {
+    if (fwd) kb_legendre<float, true><<<grid, NT, 0, st>>>(jobs, items, nitems, ctr);
+    else kb_legendre<float, false><<<grid, NT, 0, st>>>(jobs, items, nitems, ctr);
+  }
+  return cudaGetLastError() == cudaSuccess ? MLX_OK : MLX_ECUDA;
+}
+
+const void* mlx_legendre_batch_kernel(bool fwd, bool dbl) {
+  if (dbl) return fwd ? (const void*)kb_legendre<double, true> : (const void*)kb_legendre<double, false>;
+  return fwd ? (const void*)kb_legendre<float, true> : (const void*)kb_legendre<float, false>;
+}
 
 int mlx_legendre_forward(mlx_ctx* c, double2* spec, cudaStream_t st, const double2* addsrc,
                          double alpha) {

@@ -38,6 +38,8 @@
 #include "tc_ptx.cuh"
 
 #include <cuda_bf16.h>
+#include <string.h>
+#include <algorithm>
 
 namespace {
 
@@ -65,30 +67,54 @@ __device__ __forceinline__ double f32_to_f64(float v) {
   return __hiloint2double((int)hi, (int)lo);
 }
 
+// Sizes and outputs of one member of a launch (one context, or one member of a
+// batched launch).
+struct TcArgs {
+  int nc, nr, M, K, bn, pad_;
+  const long long* soff;
+  const long long* arow;      // first A row of each m
+  double2* spec_out;          // forward output
+  float* mixed_out;           // backward output (planar [2][K][M][Nr])
+  long long pad2_;
+};
+// Launch parameters: NB members' operand maps and sizes (NB = 1 for one context;
+// a batched launch indexes them by the item's member).
+template <int NB>
+struct TcParams {
+  CUtensorMap a[NB];
+  CUtensorMap b[NB];
+  TcArgs g[NB];
+};
+
 // Walk of one CTA's work: items blockIdx.x, blockIdx.x + gridDim.x, ...; chunks of
 // 32 along the contraction within each item.  Every role walks the same sequence.
+// An item's member is its pad field (0 for a single context).
 struct Walk {
   int t, kc, nch, tl;
   __device__ __forceinline__ bool valid(int nitems) const { return t < nitems; }
 };
-template <bool FWD>
-__device__ __forceinline__ int item_chunks(const LegTile* items, int t, int nc, int nr) {
-  const int kdim = FWD ? nr : nc - items[t].m;
+template <int NB>
+__device__ __forceinline__ int item_member(const LegTile& tile) { return NB == 1 ? 0 : tile.pad; }
+template <bool FWD, int NB>
+__device__ __forceinline__ int item_chunks(const TcParams<NB>& P, const LegTile* items, int t) {
+  const LegTile tile = items[t];
+  const TcArgs& g = P.g[item_member<NB>(tile)];
+  const int kdim = FWD ? g.nr : g.nc - tile.m;
   return (kdim + TC_BK - 1) / TC_BK;
 }
-template <bool FWD>
-__device__ __forceinline__ Walk walk_begin(const LegTile* items, int nitems, int nc, int nr) {
+template <bool FWD, int NB>
+__device__ __forceinline__ Walk walk_begin(const TcParams<NB>& P, const LegTile* items, int nitems) {
   Walk w{(int)blockIdx.x, 0, 0, 0};
-  if (w.t < nitems) w.nch = item_chunks<FWD>(items, w.t, nc, nr);
+  if (w.t < nitems) w.nch = item_chunks<FWD, NB>(P, items, w.t);
   return w;
 }
-template <bool FWD>
-__device__ __forceinline__ void walk_next(Walk& w, const LegTile* items, int nitems, int nc, int nr) {
+template <bool FWD, int NB>
+__device__ __forceinline__ void walk_next(Walk& w, const TcParams<NB>& P, const LegTile* items, int nitems) {
   if (++w.kc < w.nch) return;
   w.kc = 0;
   w.t += gridDim.x;
   ++w.tl;
-  if (w.t < nitems) w.nch = item_chunks<FWD>(items, w.t, nc, nr);
+  if (w.t < nitems) w.nch = item_chunks<FWD, NB>(P, items, w.t);
 }
 
 // 1 = completed, 0 = left because another role raised the abort flag, -1 = expired
@@ -100,12 +126,12 @@ __device__ __forceinline__ int wait3(unsigned bar, unsigned parity, volatile int
   return -1;
 }
 
-template <bool FWD, int NPROD>
+// bnmax: the widest column tile of the launch's members (the ring's stage size and
+// the TMEM accumulator stride follow it; each item uses its member's width).
+template <bool FWD, int NPROD, int NB>
 __global__ void __launch_bounds__(TC_THREADS, 1)
-k_leg_tc(const __grid_constant__ CUtensorMap tmapA, const __grid_constant__ CUtensorMap tmapB,
-         const LegTile* __restrict__ items, int nitems, int nc, int nr, int M, int K, int bn, int tmem_cols,
-         int expire, const long long* __restrict__ soff, const long long* __restrict__ arow_base,
-         double2* __restrict__ spec_out, float* __restrict__ mixed_out, int* __restrict__ err) {
+k_leg_tc(const __grid_constant__ TcParams<NB> P, const LegTile* __restrict__ items, int nitems, int bnmax,
+         int tmem_cols, int expire, int* __restrict__ err) {
   extern __shared__ unsigned char smem_raw[];
   __shared__ uint64_t full_a[TC_STAGES], empty[TC_STAGES], tfull[2], tempty[2], drain;
   __shared__ unsigned tmem_slot;
@@ -113,9 +139,8 @@ k_leg_tc(const __grid_constant__ CUtensorMap tmapA, const __grid_constant__ CUte
   volatile int* abortp = &abort_flag;
   const unsigned raw = tcx::smem_u32(smem_raw);
   const unsigned pad = (1024u - (raw & 1023u)) & 1023u;
-  const unsigned sbytes = tc_stage_bytes(bn);
+  const unsigned sbytes = tc_stage_bytes(bnmax);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const long long plane = (long long)K * M * nr;
 
   if (tid == 0) {
     for (int s = 0; s < TC_STAGES; ++s) {
@@ -141,7 +166,7 @@ k_leg_tc(const __grid_constant__ CUtensorMap tmapA, const __grid_constant__ CUte
     if (lane == 0) {
       unsigned fills[TC_STAGES] = {0u, 0u, 0u, 0u};
       int g = 0;
-      for (Walk w = walk_begin<FWD>(items, nitems, nc, nr); w.valid(nitems); walk_next<FWD>(w, items, nitems, nc, nr), ++g) {
+      for (Walk w = walk_begin<FWD, NB>(P, items, nitems); w.valid(nitems); walk_next<FWD, NB>(w, P, items, nitems), ++g) {
         const int s = g % TC_STAGES, u = g / TC_STAGES;
         if (u > 0) {
           if (expire && g == TC_STAGES) { atomicOr(err, 2); *abortp = 1; break; }
@@ -150,6 +175,9 @@ k_leg_tc(const __grid_constant__ CUtensorMap tmapA, const __grid_constant__ CUte
           if (r <= 0) break;
         }
         const LegTile tile = items[w.t];
+        const int mem = item_member<NB>(tile);
+        const TcArgs& ga = P.g[mem];
+        const int bn = ga.bn;
         const unsigned sA = raw + pad + (unsigned)s * sbytes;
         const unsigned sB = sA + TC_A_BYTES;
         if (w.kc == 0 && w.t + (int)gridDim.x < nitems) {
@@ -158,11 +186,11 @@ k_leg_tc(const __grid_constant__ CUtensorMap tmapA, const __grid_constant__ CUte
         }
         const unsigned bar = tcx::smem_u32(&full_a[s]);
         tcx::mbar_expect_tx(bar, TC_A_BYTES + 3u * (unsigned)bn * 64u);
-        const int arow = (int)arow_base[tile.m] + tile.row0;
-        const int brow = tile.m * 2 * K + tile.col0;
+        const int arow = (int)ga.arow[tile.m] + tile.row0;
+        const int brow = tile.m * 2 * ga.K + tile.col0;
         for (int p = 0; p < 3; ++p) {
-          tcx::tma_load_3d(sA + (unsigned)p * TC_A_PART, &tmapA, w.kc * TC_BK, arow, p, bar);
-          tcx::tma_load_3d(sB + (unsigned)p * (unsigned)bn * 64u, &tmapB, w.kc * TC_BK, brow, p, bar);
+          tcx::tma_load_3d(sA + (unsigned)p * TC_A_PART, &P.a[mem], w.kc * TC_BK, arow, p, bar);
+          tcx::tma_load_3d(sB + (unsigned)p * (unsigned)bn * 64u, &P.b[mem], w.kc * TC_BK, brow, p, bar);
         }
         ++fills[s];
       }
@@ -173,13 +201,15 @@ k_leg_tc(const __grid_constant__ CUtensorMap tmapA, const __grid_constant__ CUte
   } else if (warp == TC_MMA_WARP) {
     // ---- tensor-core issue
     if (lane == 0) {
-      const unsigned idesc = tcx::idesc_bf16(TC_BM, bn);
       bool issued = false, ok = true;
-      int g = 0, tl_cur = -1;
-      for (Walk w = walk_begin<FWD>(items, nitems, nc, nr); w.valid(nitems) && ok;) {
+      int g = 0, tl_cur = -1, bn = 0;
+      unsigned idesc = 0u;
+      for (Walk w = walk_begin<FWD, NB>(P, items, nitems); w.valid(nitems) && ok;) {
         const int buf = w.tl & 1;
         if (w.tl != tl_cur) {
           tl_cur = w.tl;
+          bn = P.g[item_member<NB>(items[w.t])].bn;
+          idesc = tcx::idesc_bf16(TC_BM, bn);
           if (w.tl >= 2) {
             const int r = wait3(tcx::smem_u32(&tempty[buf]), (unsigned)(((w.tl >> 1) - 1) & 1), abortp);
             if (r < 0) { atomicOr(err, 4); *abortp = 1; }
@@ -194,7 +224,7 @@ k_leg_tc(const __grid_constant__ CUtensorMap tmapA, const __grid_constant__ CUte
         tcx::tc_fence_after();
         const unsigned sA = raw + pad + (unsigned)s * sbytes;
         const unsigned sB = sA + TC_A_BYTES;
-        const unsigned dhi = tmem + (unsigned)(buf * 2 * bn), dco = dhi + (unsigned)bn;
+        const unsigned dhi = tmem + (unsigned)(buf * 2 * bnmax), dco = dhi + (unsigned)bnmax;
         // descriptors of the three parts of each operand, once per chunk
         const uint64_t a0 = tcx::desc_sw64(sA), a1 = tcx::desc_sw64(sA + TC_A_PART),
                        a2 = tcx::desc_sw64(sA + 2 * TC_A_PART);
@@ -219,7 +249,7 @@ k_leg_tc(const __grid_constant__ CUtensorMap tmapA, const __grid_constant__ CUte
         issued = true;
         const bool last = w.kc + 1 == w.nch;
         if (last) tcx::mma_commit(tcx::smem_u32(&tfull[buf]));
-        walk_next<FWD>(w, items, nitems, nc, nr);
+        walk_next<FWD, NB>(w, P, items, nitems);
         ++g;
       }
       // drain: every MMA issued must complete before the TMEM is freed
@@ -230,7 +260,7 @@ k_leg_tc(const __grid_constant__ CUtensorMap tmapA, const __grid_constant__ CUte
     }
   } else if (warp < 4) {
     // ---- epilogue (warps 0-3): TMEM lanes 32 warp .. 32 warp + 31
-    for (Walk w = walk_begin<FWD>(items, nitems, nc, nr); w.valid(nitems);) {
+    for (Walk w = walk_begin<FWD, NB>(P, items, nitems); w.valid(nitems);) {
       const int buf = w.tl & 1;
       int r = 0;
       if (lane == 0) {
@@ -241,16 +271,21 @@ k_leg_tc(const __grid_constant__ CUtensorMap tmapA, const __grid_constant__ CUte
       if (r <= 0) break;
       tcx::tc_fence_after();
       const LegTile tile = items[w.t];
+      const TcArgs& ga = P.g[item_member<NB>(tile)];
+      const int nc = ga.nc, nr = ga.nr, M = ga.M, K = ga.K, bn = ga.bn;
+      const long long plane = (long long)K * M * nr;
+      double2* __restrict__ spec_out = ga.spec_out;
+      float* __restrict__ mixed_out = ga.mixed_out;
       const int m = tile.m, Nm = nc - m;
       const int rows = FWD ? Nm : nr;
       const int row = tile.row0 + warp * 32 + lane;
       const int kslot0 = tile.col0 >> 1;
-      const long long so = soff[m];
-      const unsigned tb = tmem + ((unsigned)(warp * 32) << 16) + (unsigned)(buf * 2 * bn);
+      const long long so = ga.soff[m];
+      const unsigned tb = tmem + ((unsigned)(warp * 32) << 16) + (unsigned)(buf * 2 * bnmax);
       for (int c0 = 0; c0 < bn; c0 += 16) {
         unsigned hi[16], co[16];
         tcx::tmem_ld16(tb + (unsigned)c0, hi);
-        tcx::tmem_ld16(tb + (unsigned)(bn + c0), co);
+        tcx::tmem_ld16(tb + (unsigned)(bnmax + c0), co);
         tcx::tmem_wait_ld();
         if (row < rows) {
 #pragma unroll
@@ -273,7 +308,7 @@ k_leg_tc(const __grid_constant__ CUtensorMap tmapA, const __grid_constant__ CUte
       __syncwarp();
       if (lane == 0) tcx::mbar_arrive(tcx::smem_u32(&tempty[buf]));
       // next tile of this CTA
-      do { walk_next<FWD>(w, items, nitems, nc, nr); } while (w.valid(nitems) && w.kc != 0);
+      do { walk_next<FWD, NB>(w, P, items, nitems); } while (w.valid(nitems) && w.kc != 0);
     }
   }
   tcx::tc_fence_before();
@@ -474,22 +509,53 @@ int mlx_tc_retile(mlx_ctx* c, int bn_req, cudaStream_t st) {
   // the attribute is a per-function ceiling shared by every context: the largest
   // size any tile width uses
   const int smem = (int)tc_smem(TC_MAX_BN);
-  MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_leg_tc<true, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-  MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_leg_tc<false, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-  MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_leg_tc<true, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-  MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_leg_tc<false, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_leg_tc<true, 6, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_leg_tc<false, 6, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_leg_tc<true, 8, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_leg_tc<false, 8, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_leg_tc<true, 6, kTcBatchMax>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_leg_tc<false, 6, kTcBatchMax>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   return MLX_OK;
 }
 
-int mlx_legendre_tc_forward(mlx_ctx* c, double2* spec, cudaStream_t st) {
-  TimedLaunch tl(c, KID_LEG_FWD, st);
-  const int grid = c->ntc_fwd < sm_count() ? c->ntc_fwd : sm_count();
-  auto kern = c->tc_products == 8 ? k_leg_tc<true, 8> : k_leg_tc<true, 6>;
-  kern<<<grid, TC_THREADS, tc_smem(c->tc_bn), st>>>(
-      c->tmapW, c->tmapBf, c->d_tc_fwd, c->ntc_fwd, c->nc, c->nr, c->M, c->K, c->tc_bn, c->tc_tmem_cols,
-      c->tc_expire, c->d_soff, c->d_arowW, spec, nullptr, c->d_err);
+namespace {
+
+TcParams<1> single_params(mlx_ctx* c, const CUtensorMap& a, const CUtensorMap& b, bool fwd, double2* spec,
+                          float* mixed) {
+  TcParams<1> P;
+  P.a[0] = a;
+  P.b[0] = b;
+  TcArgs& g = P.g[0];
+  memset(&g, 0, sizeof(g));
+  g.nc = c->nc; g.nr = c->nr; g.M = c->M; g.K = c->K; g.bn = c->tc_bn;
+  g.soff = c->d_soff;
+  g.arow = fwd ? c->d_arowW : c->d_arowP;
+  g.spec_out = spec;
+  g.mixed_out = mixed;
+  return P;
+}
+
+int launch_single(mlx_ctx* c, bool fwd, const TcParams<1>& P, cudaStream_t st) {
+  const int n = fwd ? c->ntc_fwd : c->ntc_bwd;
+  const LegTile* items = fwd ? c->d_tc_fwd : c->d_tc_bwd;
+  const int grid = n < sm_count() ? n : sm_count();
+  const size_t smem = tc_smem(c->tc_bn);
+  if (fwd) {
+    auto kern = c->tc_products == 8 ? k_leg_tc<true, 8, 1> : k_leg_tc<true, 6, 1>;
+    kern<<<grid, TC_THREADS, smem, st>>>(P, items, n, c->tc_bn, c->tc_tmem_cols, c->tc_expire, c->d_err);
+  } else {
+    auto kern = c->tc_products == 8 ? k_leg_tc<false, 8, 1> : k_leg_tc<false, 6, 1>;
+    kern<<<grid, TC_THREADS, smem, st>>>(P, items, n, c->tc_bn, c->tc_tmem_cols, c->tc_expire, c->d_err);
+  }
   MLX_LAUNCH_CHECK(c);
   return MLX_OK;
+}
+
+}  // namespace
+
+int mlx_legendre_tc_forward(mlx_ctx* c, double2* spec, cudaStream_t st) {
+  TimedLaunch tl(c, KID_LEG_FWD, st);
+  return launch_single(c, true, single_params(c, c->tmapW, c->tmapBf, true, spec, nullptr), st);
 }
 
 int mlx_tc_vortex_planes(mlx_ctx* c, cudaStream_t st) {
@@ -503,13 +569,7 @@ int mlx_tc_vortex_planes(mlx_ctx* c, cudaStream_t st) {
 
 int mlx_legendre_tc_backward_field(mlx_ctx* c, int f, cudaStream_t st) {
   TimedLaunch tl(c, KID_LEG_BWD, st);
-  const int grid = c->ntc_bwd < sm_count() ? c->ntc_bwd : sm_count();
-  auto kern = c->tc_products == 8 ? k_leg_tc<false, 8> : k_leg_tc<false, 6>;
-  kern<<<grid, TC_THREADS, tc_smem(c->tc_bn), st>>>(
-      c->tmapP, c->tmapBv[f], c->d_tc_bwd, c->ntc_bwd, c->nc, c->nr, c->M, c->K, c->tc_bn, c->tc_tmem_cols,
-      c->tc_expire, c->d_soff, c->d_arowP, nullptr, (float*)c->d_mixed, c->d_err);
-  MLX_LAUNCH_CHECK(c);
-  return MLX_OK;
+  return launch_single(c, false, single_params(c, c->tmapP, c->tmapBv[f], false, nullptr, (float*)c->d_mixed), st);
 }
 
 int mlx_legendre_tc_backward(mlx_ctx* c, const double2* spec, cudaStream_t st, bool planes_ready) {
@@ -522,11 +582,172 @@ int mlx_legendre_tc_backward(mlx_ctx* c, const double2* spec, cudaStream_t st, b
     MLX_LAUNCH_CHECK(c);
   }
   TimedLaunch tl(c, KID_LEG_BWD, st);
-  const int grid = c->ntc_bwd < sm_count() ? c->ntc_bwd : sm_count();
-  auto kern = c->tc_products == 8 ? k_leg_tc<false, 8> : k_leg_tc<false, 6>;
-  kern<<<grid, TC_THREADS, tc_smem(c->tc_bn), st>>>(
-      c->tmapP, c->tmapBb, c->d_tc_bwd, c->ntc_bwd, c->nc, c->nr, c->M, c->K, c->tc_bn, c->tc_tmem_cols,
-      c->tc_expire, c->d_soff, c->d_arowP, nullptr, (float*)c->d_mixed, c->d_err);
-  MLX_LAUNCH_CHECK(c);
+  return launch_single(c, false, single_params(c, c->tmapP, c->tmapBb, false, nullptr, (float*)c->d_mixed), st);
+}
+
+// ---- batched persistent contraction (batch.cu) ----
+// One launch serves up to kTcBatchMax MLX_BF16X3 members: their maps and sizes are
+// the launch parameters, the work items (m, row tile, column tile, member) of all
+// members one list sorted by decreasing length (chunks), walked round-robin by the
+// persistent CTAs as in the single-context launch.  Each item uses its member's
+// column-tile width; the ring stages and TMEM accumulators are sized for the
+// widest.  A bounded wait that expires is reported in the first member's status
+// word.
+struct TcBatchPlan {
+  TcParams<kTcBatchMax> P;
+  LegTile* d_items = nullptr;
+  int nitems = 0, bnmax = 16, tmem_cols = 32, grid = 0;
+  bool fwd = true;
+  int* err = nullptr;
+  // backward split of the members' spectral states into their planes
+  SplitJob* d_split = nullptr;
+  int4* d_split_items = nullptr;
+  int nsplit = 0, split_grid = 0;
+  int* d_ctr = nullptr;
+};
+
+namespace {
+
+// Batched split (backward direction): items (member, m, k slot); a CTA of 128
+// threads splits the Nc - m coefficients of that column, as k_split_spec does.
+__global__ void __launch_bounds__(128) kb_split_spec(const SplitJob* __restrict__ jobs, const int4* __restrict__ items,
+                                                    int nitems, int* __restrict__ ctr) {
+  __shared__ int s_it;
+  for (;;) {
+    if (threadIdx.x == 0) s_it = atomicAdd(ctr, 1);
+    __syncthreads();
+    const int it = s_it;
+    if (it >= nitems) break;
+    const int4 w = items[it];
+    const SplitJob j = jobs[w.x];
+    const int m = w.y, kidx = w.z;
+    const int Nm = j.nc - m;
+    for (int a = threadIdx.x; a < Nm; a += blockDim.x) {
+      const long long idx = j.soff[m] + (long long)kidx * Nm + a;
+      const uint4 wv = __ldg(reinterpret_cast<const uint4*>(j.spec) + idx);
+      const float v[2] = {f64w_to_f32(wv.y, wv.x), f64w_to_f32(wv.w, wv.z)};
+#pragma unroll
+      for (int p = 0; p < 2; ++p) {
+        __nv_bfloat16 h, md, l;
+        split3<float>(v[p], h, md, l);
+        const long long o = ((long long)m * 2 * j.K + 2 * kidx + p) * j.Kq + a;
+        j.bs[o] = __bfloat16_as_ushort(h);
+        j.bs[j.part + o] = __bfloat16_as_ushort(md);
+        j.bs[2 * j.part + o] = __bfloat16_as_ushort(l);
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) bq_finish(ctr, gridDim.x);
+}
+
+}  // namespace
+
+// Plan of one batched contraction launch over members[0..n) (n <= kTcBatchMax,
+// every one MLX_BF16X3).  Forward: mixed planes (already split) -> specs[i];
+// backward: specs[i] split into the members' planes (those with need_split[i],
+// or all when need_split is NULL; the others' planes are already written), then
+// -> their mixed buffers.
+int mlx_tc_batch_plan(mlx_ctx* const* members, int n, bool fwd, double2* const* specs, const char* need_split,
+                      TcBatchPlan** out) {
+  *out = nullptr;
+  if (n <= 0 || n > kTcBatchMax) return MLX_EINVAL;
+  TcBatchPlan* pl = new TcBatchPlan();
+  memset(&pl->P, 0, sizeof(pl->P));
+  pl->fwd = fwd;
+  pl->err = members[0]->d_err;
+  std::vector<LegTile> items;
+  std::vector<double> cost;
+  std::vector<SplitJob> sj;
+  std::vector<int4> si;
+  for (int i = 0; i < n; ++i) {
+    mlx_ctx* c = members[i];
+    if (c->precision != MLX_BF16X3) { delete pl; return MLX_EINVAL; }
+    pl->P.a[i] = fwd ? c->tmapW : c->tmapP;
+    pl->P.b[i] = fwd ? c->tmapBf : c->tmapBb;
+    TcArgs& g = pl->P.g[i];
+    g.nc = c->nc; g.nr = c->nr; g.M = c->M; g.K = c->K; g.bn = c->tc_bn;
+    g.soff = c->d_soff;
+    g.arow = fwd ? c->d_arowW : c->d_arowP;
+    g.spec_out = fwd ? specs[i] : nullptr;
+    g.mixed_out = fwd ? nullptr : (float*)c->d_mixed;
+    if (c->tc_bn > pl->bnmax) pl->bnmax = c->tc_bn;
+    const int ncol = 2 * c->K;
+    for (int m = 0; m < c->M; ++m) {
+      const int rows = fwd ? c->nc - m : c->nr;
+      const int kdim = fwd ? c->nr : c->nc - m;
+      for (int r0 = 0; r0 < rows; r0 += TC_BM)
+        for (int c0 = 0; c0 < ncol; c0 += c->tc_bn) {
+          items.push_back(LegTile{m, r0, c0, i});
+          cost.push_back((double)((kdim + TC_BK - 1) / TC_BK));
+        }
+    }
+    if (!fwd && (!need_split || need_split[i])) {
+      SplitJob j;
+      j.nc = c->nc; j.K = c->K; j.Kq = (int)c->tc_kq;
+      j.part = (long long)c->M * 2 * c->K * c->tc_kq;
+      j.soff = c->d_soff;
+      j.spec = specs[i];
+      j.bs = (unsigned short*)c->d_bsb;
+      const int js = (int)sj.size();
+      sj.push_back(j);
+      for (int m = 0; m < c->M; ++m)
+        for (int k = 0; k < c->K; ++k) si.push_back(make_int4(js, m, k, 0));
+    }
+  }
+  // decreasing length; members' items stay in their (m, row tile, column tile)
+  // order within one length, so that neighbouring CTAs share basis chunks in L2
+  std::vector<int> ord(items.size());
+  for (size_t t = 0; t < ord.size(); ++t) ord[t] = (int)t;
+  std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return cost[x] > cost[y]; });
+  std::vector<LegTile> sorted(items.size());
+  for (size_t t = 0; t < ord.size(); ++t) sorted[t] = items[ord[t]];
+  pl->nitems = (int)sorted.size();
+  pl->grid = pl->nitems < sm_count() ? pl->nitems : sm_count();
+  int cols = 32;
+  while (cols < 4 * pl->bnmax) cols <<= 1;
+  pl->tmem_cols = cols;
+  auto fail = [&](cudaError_t) { mlx_tc_batch_free(pl); return MLX_ECUDA; };
+  cudaError_t e;
+  if ((e = cudaMalloc(&pl->d_items, sizeof(LegTile) * sorted.size())) != cudaSuccess) return fail(e);
+  if ((e = cudaMemcpy(pl->d_items, sorted.data(), sizeof(LegTile) * sorted.size(), cudaMemcpyHostToDevice)) !=
+      cudaSuccess) return fail(e);
+  if (!si.empty()) {
+    pl->nsplit = (int)si.size();
+    pl->split_grid = pl->nsplit < 8 * sm_count() ? pl->nsplit : 8 * sm_count();
+    if ((e = cudaMalloc(&pl->d_split, sizeof(SplitJob) * sj.size())) != cudaSuccess) return fail(e);
+    if ((e = cudaMalloc(&pl->d_split_items, sizeof(int4) * si.size())) != cudaSuccess) return fail(e);
+    if ((e = cudaMalloc(&pl->d_ctr, 2 * sizeof(int))) != cudaSuccess) return fail(e);
+    if ((e = cudaMemcpy(pl->d_split, sj.data(), sizeof(SplitJob) * sj.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
+      return fail(e);
+    if ((e = cudaMemcpy(pl->d_split_items, si.data(), sizeof(int4) * si.size(), cudaMemcpyHostToDevice)) !=
+        cudaSuccess) return fail(e);
+    if ((e = cudaMemset(pl->d_ctr, 0, 2 * sizeof(int))) != cudaSuccess) return fail(e);
+  }
+  *out = pl;
   return MLX_OK;
+}
+
+int mlx_tc_batch_launch(TcBatchPlan* pl, cudaStream_t st) {
+  if (!pl->fwd && pl->nsplit > 0) {
+    kb_split_spec<<<pl->split_grid, 128, 0, st>>>(pl->d_split, pl->d_split_items, pl->nsplit, pl->d_ctr);
+    if (cudaGetLastError() != cudaSuccess) return MLX_ECUDA;
+  }
+  const size_t smem = tc_smem(pl->bnmax);
+  if (pl->fwd)
+    k_leg_tc<true, 6, kTcBatchMax><<<pl->grid, TC_THREADS, smem, st>>>(pl->P, pl->d_items, pl->nitems, pl->bnmax,
+                                                                      pl->tmem_cols, 0, pl->err);
+  else
+    k_leg_tc<false, 6, kTcBatchMax><<<pl->grid, TC_THREADS, smem, st>>>(pl->P, pl->d_items, pl->nitems, pl->bnmax,
+                                                                       pl->tmem_cols, 0, pl->err);
+  return cudaGetLastError() == cudaSuccess ? MLX_OK : MLX_ECUDA;
+}
+
+void mlx_tc_batch_free(TcBatchPlan* pl) {
+  if (!pl) return;
+  if (pl->d_items) cudaFree(pl->d_items);
+  if (pl->d_split) cudaFree(pl->d_split);
+  if (pl->d_split_items) cudaFree(pl->d_split_items);
+  if (pl->d_ctr) cudaFree(pl->d_ctr);
+  delete pl;
 }

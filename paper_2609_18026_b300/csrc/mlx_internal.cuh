@@ -60,6 +60,91 @@ struct SplitPlanes {
   int Kq = 0, K2 = 0;
 };
 
+// ---- batched persistent launches (batch.cu) ----
+// A batched launch runs one phase of the time step (a transform stage, the
+// contraction, the solve) for many contexts at once: its CTAs (or warps) take
+// work items from a queue, ctr[0] handing out item indices in order (items sorted
+// by decreasing cost), until the queue is empty.  ctr[1] counts the workers that
+// found it empty; the last one resets both words, so that the next launch of the
+// same queue (a graph replay) starts from zero without a memset.  No worker waits
+// on another.
+__device__ __forceinline__ void bq_finish(int* ctr, int workers) {
+  __threadfence();
+  if (atomicAdd(ctr + 1, 1) == workers - 1) {
+    atomicExch(ctr, 0);
+    atomicExch(ctr + 1, 0);
+  }
+}
+
+// One member's transform stage in a batched FFT launch.  phi: a = physical field
+// (unused by the fused Fisher-KPP stage), b / c = Re / Im planes of its Fourier
+// planes; z: a / b = Re / Im of the zm planes, c / d = Re / Im of the mixed planes.
+// bs != NULL: the stage writes the BF16x3 split planes of the contraction's data
+// operand (part elements per part plane, row length kp, 2K columns per m).
+struct BFftJob {
+  int N, logN, M, Nr, R, E;   // N: transform length (Nphi or Nz), E = max(N / 32, 1)
+  int Kz, K;
+  void* a; void* b; void* c; void* d;
+  const void* tw;
+  double gamma;
+  int* err;
+  unsigned short* bs; long long part; int kp, k2;
+};
+
+// One member's SIMT contraction (FP32 / FP64) in a batched launch.
+struct BLegJob {
+  int nc, nr, M, K;
+  const long long* boff;
+  const long long* soff;
+  const void* table;   // W (forward) or P (backward), the member's element type
+  void* mixed;
+  double2* spec;
+};
+
+// One member's AB-CN banded solve (staged form) in a batched launch.
+struct BSolveJob {
+  int variant;          // 0 staged; 1 / 2 segmented, 8 / 4 segments; 3 / 4 the same, pivot-free
+  int M, nc, Kz, K, CPW, gpm, step, kz_fac;
+  double dt;
+  const long long* soff;
+  const long long* band_off;
+  const double* U;
+  const double* L;
+  const int* piv;
+  const double* invd;
+  const double* s;
+  const double* A;
+  const double* Ap;
+  double* out;
+  double* Az;           // NULL, or A^j of a member without a nonlinear term (written as zeros)
+  const double* PHf;    // segmented variants: influence data and pivot-free records
+  const double* PHb;
+  const double* PSf;
+  const double* RNP;
+  unsigned short* bs;   // segmented variants: split planes of out (NULL: none)
+  long long part;
+  int kq, k2;
+};
+
+// One member's BF16x3 split of its spectral state (backward data operand) in a
+// batched launch: bs[part][(m 2K + 2 kidx + p) Kq + (n - m)].
+struct SplitJob {
+  int nc, K, Kq, pad_;
+  long long part;
+  const long long* soff;
+  const double2* spec;
+  unsigned short* bs;
+};
+
+// members of one batched tensor-core contraction launch (the launch parameters
+// hold two 128-byte tensor maps and the sizes of each)
+constexpr int kTcBatchMax = 64;
+struct TcBatchPlan;
+int mlx_tc_batch_plan(mlx_ctx* const* members, int n, bool fwd, double2* const* specs, const char* need_split,
+                      TcBatchPlan** out);
+int mlx_tc_batch_launch(TcBatchPlan* plan, cudaStream_t st);
+void mlx_tc_batch_free(TcBatchPlan* plan);
+
 struct BandLU {
   double* U = nullptr;     // [rows][W_u] with W_u = 1 + kl + ku
   double* L = nullptr;     // [rows][kl]

@@ -36,7 +36,11 @@ def _make(inst, seed):
     return ctx, s, u0
 
 
-def test_batched_advance_equals_individual():
+@pytest.mark.parametrize("persistent", [1, 0])
+def test_batched_advance_equals_individual(persistent):
+    # persistent: every phase one queue launch over all members (tensor-core,
+    # FP32 and FP64 SIMT contractions, 2-D and 3-D FFT stages, solves with and
+    # without a nonlinear term); 0: one graph branch per member
     ctxs, s_b, s_i, p_b, p_i = [], [], [], [], []
     for j, inst in enumerate(INST):
         ctx, s, _ = _make(inst, j)
@@ -46,6 +50,7 @@ def test_batched_advance_equals_individual():
     kinds = [inst[4] for inst in INST]
     coeffs = [1.0] * len(INST)
     batch = B.Batch(ctxs)
+    batch.set_persistent(persistent)
     batch.advance(kinds, coeffs, s_b, p_b, 7, True)
     batch.advance(kinds, coeffs, s_b, p_b, 6, False)
     for j, ctx in enumerate(ctxs):
@@ -141,4 +146,44 @@ def test_batch64_every_instance_matches_oracle(record):
         assert e <= 1e-6, (j, insts[j], e)
         assert eb <= 1e-5, (j, insts[j], eb)
     record("batch64_vs_oracle", worst_rel_err=worst, worst_block_err=worst_blk)
+    batch.close()
+
+
+def test_batch64_persistent_equals_branches():
+    # The 64-instance uneven workload: the per-phase persistent launches (one
+    # tensor-core launch over all 33 BF16x3 Fisher-KPP members, queue-fed FFT
+    # stages and solves) against one graph branch per member, bitwise, over a
+    # Richardson start and 6 AB-CN steps (3 replayed pairs).
+    import torch
+    insts = W.batch_instances(64)
+    ctxs, kinds, s0 = [], [], []
+    for inst in insts:
+        lin = inst["kind"] == "diffusion"
+        pol = B.CHOP_LINEAR if lin else B.CHOP_TWOTHIRDS
+        m_pol = inst["nphi"] // 2 if lin else (inst["nphi"] - 1) // 3 + 1
+        ctx = B.Context(inst["nr"], inst["nphi"], inst["nz"], inst["ell"], lz=inst["lz"], precision=B.BF16X3,
+                        chop_policy=pol, nphi_c=min(m_pol, inst["nr"]))
+        kind = B.NONLIN_NONE if lin else B.NONLIN_FKPP
+        ctx.implicit_setup(1e-2 if lin else 1.0, inst["dt"])
+        x, w, r = ctx.nodes()
+        phi = 2 * np.pi * np.arange(inst["nphi"]) / inst["nphi"]
+        zz = inst["lz"] * np.arange(inst["nz"]) / inst["nz"]
+        u0 = W.batch_initial(inst, r[None, None, :], phi[None, :, None], zz[:, None, None])
+        s0.append(ctx.forward(torch.as_tensor(u0, dtype=torch.float32).cuda(), ctx.new_spec()))
+        ctxs.append(ctx); kinds.append(kind)
+    batch = B.Batch(ctxs)
+    out = []
+    for mode in (1, 0):
+        batch.set_persistent(mode)
+        st = [s.clone() for s in s0]
+        pv = [c.new_spec() for c in ctxs]
+        batch.advance(kinds, [1.0] * 64, st, pv, 7, True)
+        torch.cuda.synchronize()
+        out.append(([s.cpu().numpy() for s in st], [p.cpu().numpy() for p in pv]))
+    for j in range(64):
+        assert np.isfinite(out[0][0][j]).all(), j
+        assert np.array_equal(out[0][0][j], out[1][0][j]), (j, insts[j])
+        assert np.array_equal(out[0][1][j], out[1][1][j]), (j, insts[j])
+    for c in ctxs:
+        c.device_status()   # raises on an expired bounded wait or a non-finite product
     batch.close()
