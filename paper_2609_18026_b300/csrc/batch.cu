@@ -100,8 +100,12 @@ struct mlx_batch {
   std::map<std::vector<uintptr_t>, PGraph*> pgraphs;
   std::vector<unsigned long long> gens;   // members' graph generations the cached graphs were made at
   int persistent = 1;                     // 1: per-phase persistent launches when every member qualifies
-  cudaStream_t lin = nullptr;             // the persistent graph's second branch
-  cudaEvent_t ev_fork[2] = {nullptr, nullptr}, ev_join[2] = {nullptr, nullptr};
+  // persistent capture: the transform chain on a high-priority stream, each solve
+  // group on a stream of its own (high priority for the members with a nonlinear
+  // term, whose step waits on them; low for the others, which fill the gaps)
+  cudaStream_t pcap = nullptr;
+  std::vector<cudaStream_t> hi, lo;
+  std::vector<cudaEvent_t> evs;
 };
 
 namespace {
@@ -109,11 +113,10 @@ namespace {
 void batch_free(mlx_batch* b) {
   if (!b) return;
   for (auto& kv : b->pgraphs) free_pgraph(kv.second);
-  if (b->lin) cudaStreamDestroy(b->lin);
-  for (int k = 0; k < 2; ++k) {
-    if (b->ev_fork[k]) cudaEventDestroy(b->ev_fork[k]);
-    if (b->ev_join[k]) cudaEventDestroy(b->ev_join[k]);
-  }
+  for (auto st : b->hi) cudaStreamDestroy(st);
+  for (auto st : b->lo) cudaStreamDestroy(st);
+  for (auto e : b->evs) cudaEventDestroy(e);
+  if (b->pcap) cudaStreamDestroy(b->pcap);
   for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second);
   for (auto s : b->streams) cudaStreamDestroy(s);
   for (auto e : b->joins) cudaEventDestroy(e);
@@ -401,29 +404,78 @@ int run_launch(const QLaunch& q, cudaStream_t st) {
   return MLX_EINVAL;
 }
 
-// Capture the pair: per step, the transform branch on the capture stream and the
-// solves of the members without a nonlinear term on a second branch.
+// Capture the pair.  Per step: the transform phases in order on the capture
+// stream, then the solve groups of the members with a nonlinear term side by
+// side; the solve groups of the others side by side from the start of the step.
 int capture_pgraph(mlx_batch* b, PGraph* g) {
+  int lo_prio = 0, hi_prio = 0;
+  if (cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio) != cudaSuccess) return MLX_ECUDA;
+  if (!b->pcap && cudaStreamCreateWithPriority(&b->pcap, cudaStreamNonBlocking, hi_prio) != cudaSuccess)
+    return MLX_ECUDA;
+  size_t nhi = 0, nlo = 0;
+  for (int k = 0; k < 2; ++k) {
+    size_t ns = 0;
+    for (const QLaunch& q : g->xf[k]) ns += q.kind == QLaunch::SOLVE;
+    nhi = std::max(nhi, ns);
+    nlo = std::max(nlo, g->lin[k].size());
+  }
+  while (b->hi.size() < nhi) {
+    cudaStream_t st = nullptr;
+    if (cudaStreamCreateWithPriority(&st, cudaStreamNonBlocking, hi_prio) != cudaSuccess) return MLX_ECUDA;
+    b->hi.push_back(st);
+  }
+  while (b->lo.size() < nlo) {
+    cudaStream_t st = nullptr;
+    if (cudaStreamCreateWithPriority(&st, cudaStreamNonBlocking, lo_prio) != cudaSuccess) return MLX_ECUDA;
+    b->lo.push_back(st);
+  }
+  size_t ev_i = 0;
+  auto ev = [&](cudaEvent_t* e) -> int {
+    if (ev_i == b->evs.size()) {
+      cudaEvent_t x = nullptr;
+      if (cudaEventCreateWithFlags(&x, cudaEventDisableTiming) != cudaSuccess) return MLX_ECUDA;
+      b->evs.push_back(x);
+    }
+    *e = b->evs[ev_i++];
+    return MLX_OK;
+  };
+  // run `ls` side by side on `pool`, each after an event recorded on `from`; the
+  // join events go to `joins`
+  auto fan = [&](const std::vector<const QLaunch*>& ls, std::vector<cudaStream_t>& pool,
+                 std::vector<cudaEvent_t>& joins) -> int {
+    if (ls.empty()) return MLX_OK;
+    cudaEvent_t f;
+    int r = ev(&f);
+    if (r) return r;
+    if (cudaEventRecord(f, b->pcap) != cudaSuccess) return MLX_ECUDA;
+    for (size_t j = 0; j < ls.size(); ++j) {
+      if (cudaStreamWaitEvent(pool[j], f, 0) != cudaSuccess) return MLX_ECUDA;
+      if ((r = run_launch(*ls[j], pool[j]))) return r;
+      cudaEvent_t e;
+      if ((r = ev(&e))) return r;
+      if (cudaEventRecord(e, pool[j]) != cudaSuccess) return MLX_ECUDA;
+      joins.push_back(e);
+    }
+    return MLX_OK;
+  };
   cudaGraph_t graph = nullptr;
-  if (cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return MLX_ECUDA;
+  if (cudaStreamBeginCapture(b->pcap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return MLX_ECUDA;
   int rc = MLX_OK;
   for (int k = 0; k < 2 && !rc; ++k) {
-    const bool fork = !g->lin[k].empty();
-    if (fork) {
-      if (cudaEventRecord(b->ev_fork[k], b->cap) != cudaSuccess ||
-          cudaStreamWaitEvent(b->lin, b->ev_fork[k], 0) != cudaSuccess)
-        rc = MLX_ECUDA;
-      for (const QLaunch& q : g->lin[k])
-        if (!rc) rc = run_launch(q, b->lin);
+    std::vector<cudaEvent_t> joins;
+    std::vector<const QLaunch*> lin, sol;
+    for (const QLaunch& q : g->lin[k]) lin.push_back(&q);
+    rc = fan(lin, b->lo, joins);
+    for (const QLaunch& q : g->xf[k]) {
+      if (rc) break;
+      if (q.kind == QLaunch::SOLVE) sol.push_back(&q);
+      else rc = run_launch(q, b->pcap);
     }
-    for (const QLaunch& q : g->xf[k])
-      if (!rc) rc = run_launch(q, b->cap);
-    if (fork && !rc)
-      if (cudaEventRecord(b->ev_join[k], b->lin) != cudaSuccess ||
-          cudaStreamWaitEvent(b->cap, b->ev_join[k], 0) != cudaSuccess)
-        rc = MLX_ECUDA;
+    if (!rc) rc = fan(sol, b->hi, joins);
+    for (cudaEvent_t e : joins)
+      if (!rc && cudaStreamWaitEvent(b->pcap, e, 0) != cudaSuccess) rc = MLX_ECUDA;
   }
-  cudaError_t e = cudaStreamEndCapture(b->cap, &graph);
+  cudaError_t e = cudaStreamEndCapture(b->pcap, &graph);
   if (rc || e != cudaSuccess) {
     if (graph) cudaGraphDestroy(graph);
     if (!rc) b->ctxs[0]->last_err = cudaGetErrorString(e);
@@ -461,12 +513,7 @@ int mlx_batch_create(mlx_ctx* const* ctxs, int n, mlx_batch** out) {
     b->joins.push_back(e);
   }
   if (cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&b->lin, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&b->ev_fork[0], cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&b->ev_fork[1], cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&b->ev_join[0], cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&b->ev_join[1], cudaEventDisableTiming) != cudaSuccess) {
+      cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess) {
     batch_free(b);
     return MLX_ECUDA;
   }
