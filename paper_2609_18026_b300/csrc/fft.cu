@@ -85,6 +85,14 @@ __device__ __forceinline__ void cp_async_el(T* smem_dst, const T* gsrc) {
   else
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(gsrc) : "memory");
 }
+// the same with the shared-memory address already converted
+template <typename T>
+__device__ __forceinline__ void cp_async_el_s(unsigned d, const T* gsrc) {
+  if constexpr (sizeof(T) == 4)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(gsrc) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(gsrc) : "memory");
+}
 __device__ __forceinline__ void cp_async_all() {
   asm volatile("cp.async.commit_group;\n" ::: "memory");
   asm volatile("cp.async.wait_all;\n" ::: "memory");
@@ -134,23 +142,23 @@ __device__ __forceinline__ void dif(C (&v)[E], int N, int lj, const C* __restric
 }
 
 // Decimation in time: bit-reversed order in, natural order out.  Lane-exchange
-// stage: the lower lane keeps v + w p, the upper lane p - w v, both as
-// r0 + sgn (w q) with (q, r0) = (p, v) or (v, p) chosen per lane.
+// stage: the lower lane keeps v + w p, the upper lane p - w v.  The upper lane
+// multiplies its own value by w before the exchange (the lower lane by 1), so
+// that both write a + sgn b with the received value: no select per point.
 template <typename C, int E>
 __device__ __forceinline__ void dit(C (&v)[E], int N, int lj, const C* __restrict__ tw, bool inv) {
   typedef decltype(C().x) T;
   auto stage = [&](int d) {
     const bool upper = (lj & d) != 0;
-    const C w = stw(tw, N, d, lj & (d - 1), inv);
+    C w = stw(tw, N, d, lj & (d - 1), inv);
+    if (!upper) { w.x = (T)1; w.y = (T)0; }
     const T sg = upper ? (T)-1 : (T)1;
 #pragma unroll
     for (int e = 0; e < E; ++e) {
-      const C p = shfl_xor(v[e], d);
-      const C q = upper ? v[e] : p;
-      const C r0 = upper ? p : v[e];
-      const C wq = cmul(w, q);
-      v[e].x = fmaT(sg, wq.x, r0.x);
-      v[e].y = fmaT(sg, wq.y, r0.y);
+      const C a = cmul(w, v[e]);          // lower: v; upper: w v
+      const C p = shfl_xor(a, d);         // lower: w v_upper; upper: v_lower
+      v[e].x = fmaT(sg, a.x, p.x);
+      v[e].y = fmaT(sg, a.y, p.y);
     }
   };
   if constexpr (E > 1) {
@@ -224,9 +232,12 @@ __device__ void phi_unpack_store(const C* L, int ld, int N, int B, int M, int Nr
   const T inv = (T)1 / (T)N;
   const int R = 2 * B;
   const int lR = __ffs(R) - 1;          // tiles are powers of two: shifts, not divisions
-  for (int t = threadIdx.x; t < M * R; t += blockDim.x) {
-    const int m = t >> lR, rr = t & (R - 1);
-    const int b = rr & (B - 1);
+  // blockDim.x is a multiple of R: each thread keeps one radius and steps through m
+  const int rr = threadIdx.x & (R - 1), mstep = (int)blockDim.x >> lR;
+  const int b = rr & (B - 1);
+  if (r0 + rr >= Nr) return;
+#pragma unroll 2
+  for (int m = threadIdx.x >> lR; m < M; m += mstep) {
     const int pm = m, pc = (N - m) & (N - 1);
     const C zm = L[b * ld + (brev ? bitrev(pm, logN) : pm)];
     const C zc = L[b * ld + (brev ? bitrev(pc, logN) : pc)];
@@ -242,15 +253,13 @@ __device__ void phi_unpack_store(const C* L, int ld, int N, int B, int M, int Nr
     // member takes half of the (real) bin
     if (m == (N >> 1)) re *= (T)0.5;
     const int r = r0 + rr;
-    if (r < Nr) {
-      if (so.bs) {
-        split_store<T>(so, m, 0, 0, r, re * inv);
-        split_store<T>(so, m, 0, 1, r, im * inv);
-      } else {
-        const long long o = ((long long)z * M + m) * Nr + r;
-        zre[o] = re * inv;
-        zim[o] = im * inv;
-      }
+    if (so.bs) {
+      split_store<T>(so, m, 0, 0, r, re * inv);
+      split_store<T>(so, m, 0, 1, r, im * inv);
+    } else {
+      const long long o = ((long long)z * M + m) * Nr + r;
+      zre[o] = re * inv;
+      zim[o] = im * inv;
     }
   }
 }
@@ -272,13 +281,21 @@ __device__ __forceinline__ void phi_tile(int N, int logN, int M, int Nr, int R, 
   C* tws = L + (size_t)B * ld;          // the twiddle tables after the tile
   stage_twiddles(tws, tw, N);
 
+  // blockDim.x is a multiple of R: each thread keeps one radius of the tile
+  const int rr = threadIdx.x & (R - 1), rstep = (int)blockDim.x >> lR;
   if constexpr (MODE == PHI_FWD) {
-    for (int t = threadIdx.x; t < N * R; t += blockDim.x) {
-      const int j = t >> lR, rr = t & (R - 1);
+    {
       const int r = r0 + rr;
-      T* slot = reinterpret_cast<T*>(&L[(rr & (B - 1)) * ld + j]) + (rr < B ? 0 : 1);
-      if (r < Nr) cp_async_el(slot, phys + plane + (long long)j * Nr + r);
-      else *slot = (T)0;
+      T* srow = reinterpret_cast<T*>(&L[(rr & (B - 1)) * ld]) + (rr < B ? 0 : 1);   // point j at srow[2 j]
+      if (r < Nr) {
+        const T* g = phys + plane + r;
+        const unsigned s0 = (unsigned)__cvta_generic_to_shared(srow);
+#pragma unroll 4
+        for (int j = threadIdx.x >> lR; j < N; j += rstep)
+          cp_async_el_s(s0 + (unsigned)(j * (int)sizeof(C)), g + (long long)j * Nr);
+      } else {
+        for (int j = threadIdx.x >> lR; j < N; j += rstep) srow[2 * j] = (T)0;
+      }
     }
     cp_async_all();
     __syncthreads();
@@ -299,14 +316,17 @@ __device__ __forceinline__ void phi_tile(int N, int logN, int M, int Nr, int R, 
     // Zhat[N-m] = conj(A_m) + i conj(B_m), Zhat[0] = Re A_0 + i Re B_0
     for (int t = threadIdx.x; t < B * ld; t += blockDim.x) L[t] = C{};
     __syncthreads();
-#pragma unroll 8
-    for (int t = threadIdx.x; t < M * B; t += blockDim.x) {
-      const int m = t >> (lR - 1), b = t & (B - 1);
-      const int ra = r0 + b, rb = r0 + b + B;
+    const int b = threadIdx.x & (B - 1), mstep = (int)blockDim.x >> (lR - 1);
+    const int ra = r0 + b, rb = r0 + b + B;
+    const bool va = ra < Nr, vb = rb < Nr;
+    const T* __restrict__ zr = zre + (long long)z * M * Nr;
+    const T* __restrict__ zi = zim + (long long)z * M * Nr;
+#pragma unroll 4
+    for (int m = threadIdx.x >> (lR - 1); m < M; m += mstep) {
       T ar = 0, ai = 0, br = 0, bi = 0;
-      const long long oa = ((long long)z * M + m) * Nr;
-      if (ra < Nr) { ar = zre[oa + ra]; ai = zim[oa + ra]; }
-      if (rb < Nr) { br = zre[oa + rb]; bi = zim[oa + rb]; }
+      const long long oa = (long long)m * Nr;
+      if (va) { ar = zr[oa + ra]; ai = zi[oa + ra]; }
+      if (vb) { br = zr[oa + rb]; bi = zi[oa + rb]; }
       // the synthesis-only transform takes its input bit-reversed (DIT), the fused
       // Fisher-KPP transform in natural order (DIF, product, DIT)
       const int p1 = (MODE == PHI_BWD) ? bitrev(m, logN) : m;
@@ -360,11 +380,12 @@ __device__ __forceinline__ void phi_tile(int N, int logN, int M, int Nr, int R, 
     });
     __syncthreads();
     if constexpr (MODE == PHI_BWD) {
-      for (int t = threadIdx.x; t < N * R; t += blockDim.x) {
-        const int j = t >> lR, rr = t & (R - 1);
-        const int r = r0 + rr;
-        const C v = L[(rr & (B - 1)) * ld + j];
-        if (r < Nr) phys[plane + (long long)j * Nr + r] = (rr < B) ? v.x : v.y;
+      const int r = r0 + rr;
+      if (r < Nr) {
+        const T* srow = reinterpret_cast<const T*>(&L[(rr & (B - 1)) * ld]) + (rr < B ? 0 : 1);
+        T* g = phys + plane + r;
+#pragma unroll 4
+        for (int j = threadIdx.x >> lR; j < N; j += rstep) g[(long long)j * Nr] = srow[2 * j];
       }
     } else {
       phi_unpack_store<T, C>(L, ld, N, B, M, Nr, r0, z, zre, zim, false, logN, so);
@@ -396,19 +417,28 @@ __device__ __forceinline__ void z_tile(int Nz, int logN, int Kz, int K, int M, i
   const int lR = __ffs(R) - 1;          // R is a power of two
   C* tws = L + (size_t)R * ld;          // the twiddle tables after the tile
   stage_twiddles(tws, tw, Nz);
+  // blockDim.x is a multiple of R: each thread keeps one radius (line b) of the
+  // tile in the loads and stores (recomputed per phase, so that nothing stays
+  // live across the transform)
+#define MLX_Z_LINE                                                       \
+  const int b = threadIdx.x & (R - 1), lstep = (int)blockDim.x >> lR;    \
+  const int r = r0 + b;                                                  \
+  const long long rs = (long long)M * Nr;   /* stride of a z (or k) row */ \
+  const long long mo = (long long)m * Nr + r;                            \
+  C* Lb = L + (size_t)b * ld;
   if (!INVERSE) {
-    for (int t = threadIdx.x; t < Nz * R; t += blockDim.x) {
-      const int l = t >> lR, b = t & (R - 1);
-      const int r = r0 + b;
-      C* slot = &L[b * ld + l];
-      if (r < Nr) {
-        const long long o = ((long long)l * M + m) * Nr + r;
-        cp_async_el(&slot->x, zre + o);
-        cp_async_el(&slot->y, zim + o);
-      } else {
-        slot->x = 0;
-        slot->y = 0;
+    MLX_Z_LINE
+    if (r < Nr) {
+      const unsigned s0 = (unsigned)__cvta_generic_to_shared(Lb);
+#pragma unroll 4
+      for (int l = threadIdx.x >> lR; l < Nz; l += lstep) {
+        const long long o = (long long)l * rs + mo;
+        const unsigned d = s0 + (unsigned)(l * (int)sizeof(C));
+        cp_async_el_s(d, zre + o);
+        cp_async_el_s(d + (unsigned)sizeof(T), zim + o);
       }
+    } else {
+      for (int l = threadIdx.x >> lR; l < Nz; l += lstep) Lb[l] = C{};
     }
     cp_async_all();
   } else {
@@ -417,23 +447,25 @@ __device__ __forceinline__ void z_tile(int Nz, int logN, int Kz, int K, int M, i
     // Nyquist chop (K = Nz + 1): rows k = +Nz/2 (kk = Kz - 1) and k = -Nz/2
     // (kk = Kz) feed the same bin, which receives their sum
     const bool nyq = K == Nz + 1;
-#pragma unroll 8
-    for (int t = threadIdx.x; t < K * R; t += blockDim.x) {
-      const int kk = t >> lR, b = t & (R - 1);
-      const int r = r0 + b;
-      const int pos = (kk < Kz) ? kk : Nz - (K - kk);
-      if (r < Nr && !(nyq && kk == Kz)) {
-        const long long o = ((long long)kk * M + m) * Nr + r;
-        C* slot = &L[b * ld + bitrev(pos, logN)];   // bit-reversed input of the DIT below
+    MLX_Z_LINE
+    if (r < Nr) {
+      const unsigned s0 = (unsigned)__cvta_generic_to_shared(Lb);
+#pragma unroll 2
+      for (int kk = threadIdx.x >> lR; kk < K; kk += lstep) {
+        const int pos = (kk < Kz) ? kk : Nz - (K - kk);
+        if (nyq && kk == Kz) continue;
+        const long long o = (long long)kk * rs + mo;
+        const int q = bitrev(pos, logN);            // bit-reversed input of the DIT below
         if (nyq && kk == Kz - 1) {
-          const long long o2 = ((long long)Kz * M + m) * Nr + r;
+          const long long o2 = (long long)Kz * rs + mo;
           C v;
           v.x = mre[o] + mre[o2];
           v.y = mim[o] + mim[o2];
-          *slot = v;
+          Lb[q] = v;
         } else {
-          cp_async_el(&slot->x, mre + o);
-          cp_async_el(&slot->y, mim + o);
+          const unsigned d = s0 + (unsigned)(q * (int)sizeof(C));
+          cp_async_el_s(d, mre + o);
+          cp_async_el_s(d + (unsigned)sizeof(T), mim + o);
         }
       }
     }
@@ -456,36 +488,33 @@ __device__ __forceinline__ void z_tile(int Nz, int logN, int Kz, int K, int M, i
     }
   });
   __syncthreads();
+  MLX_Z_LINE
+#undef MLX_Z_LINE
+  if (r >= Nr) return;
   if (!INVERSE) {
     const T inv = (T)1 / (T)Nz;
     const bool nyq = K == Nz + 1;     // Nyquist chop: rows k = +-Nz/2 take half the bin each
-    for (int t = threadIdx.x; t < K * R; t += blockDim.x) {
-      const int kk = t >> lR, b = t & (R - 1);
-      const int r = r0 + b;
+#pragma unroll 4
+    for (int kk = threadIdx.x >> lR; kk < K; kk += lstep) {
       const int pos = (kk < Kz) ? kk : Nz - (K - kk);
-      if (r < Nr) {
-        C v = L[b * ld + bitrev(pos, logN)];
-        if (nyq && (kk == Kz - 1 || kk == Kz)) { v.x *= (T)0.5; v.y *= (T)0.5; }
-        if (so.bs) {
-          split_store<T>(so, m, kk, 0, r, v.x * inv);
-          split_store<T>(so, m, kk, 1, r, v.y * inv);
-        } else {
-          const long long o = ((long long)kk * M + m) * Nr + r;
-          mre[o] = v.x * inv;
-          mim[o] = v.y * inv;
-        }
+      C v = Lb[bitrev(pos, logN)];
+      if (nyq && (kk == Kz - 1 || kk == Kz)) { v.x *= (T)0.5; v.y *= (T)0.5; }
+      if (so.bs) {
+        split_store<T>(so, m, kk, 0, r, v.x * inv);
+        split_store<T>(so, m, kk, 1, r, v.y * inv);
+      } else {
+        const long long o = (long long)kk * rs + mo;
+        mre[o] = v.x * inv;
+        mim[o] = v.y * inv;
       }
     }
   } else {
-    for (int t = threadIdx.x; t < Nz * R; t += blockDim.x) {
-      const int l = t >> lR, b = t & (R - 1);
-      const int r = r0 + b;
-      if (r < Nr) {
-        const C v = L[b * ld + l];
-        const long long o = ((long long)l * M + m) * Nr + r;
-        zre[o] = v.x;
-        zim[o] = v.y;
-      }
+#pragma unroll 2
+    for (int l = threadIdx.x >> lR; l < Nz; l += lstep) {
+      const C v = Lb[l];
+      const long long o = (long long)l * rs + mo;
+      zre[o] = v.x;
+      zim[o] = v.y;
     }
   }
 }
