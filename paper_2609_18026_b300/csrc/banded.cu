@@ -1051,10 +1051,19 @@ __global__ void k_band_solve_seg(int M, int nc, int Kz, int K, int groups_per_m,
                                  const double* __restrict__ RNP,
                                  const double* __restrict__ s, const double* __restrict__ A,
                                  const double* __restrict__ Ap, double* __restrict__ out,
-                                 SplitPlanes sp) {
+                                 SplitPlanes sp, int pair) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int wib = threadIdx.x >> 5;
-  const int gw = blockIdx.x * (blockDim.x >> 5) + wib;
+  int gw = blockIdx.x * (blockDim.x >> 5) + wib;
+  if (pair) {
+    // 8 warps per CTA; warps w and w + 4 share an SM sub-partition (and its FP64
+    // unit): w < 4 takes a system from the long end of the (m ascending, so
+    // N = Nc - m descending) order, w + 4 its mirror from the short end, so that
+    // every sub-partition's two chains of rows add up to about the same length
+    const int T = M * groups_per_m, H = (T + 1) / 2;
+    const int q = blockIdx.x * 4 + (wib & 3);
+    gw = (wib < 4) ? (q < H ? q : T) : (T - 1 - q >= H ? T - 1 - q : T);
+  }
   unsigned char* base = smem_raw + (size_t)wib * SegSmem<KL, SEG>::per_warp(nc, keep_s, NP);
   band_solve_seg_warp<KL, SEG, NP>(gw, base, M, nc, Kz, K, groups_per_m, step, keep_s, dt, soff, band_off, U, Lm,
                                    piv, invd, PHf, PHb, PSf, RNP, s, A, Ap, out, sp);
@@ -1524,10 +1533,12 @@ static int launch_solve(mlx_ctx* c, int step, const BandLU& f, const long long* 
         const int gpm = (c->Kz + G - 1) / G;
         const int warps = c->M * gpm;
         auto kern = np ? k_band_solve_seg<KL, S, true> : k_band_solve_seg<KL, S, false>;
-        kern<<<(warps + WPB - 1) / WPB, 32 * WPB, pw * WPB, st>>>(
+        const int pair = WPB == 8 ? 1 : 0;
+        const int blocks = pair ? ((warps + 1) / 2 + 3) / 4 : (warps + WPB - 1) / WPB;
+        kern<<<blocks, 32 * WPB, pw * WPB, st>>>(
             c->M, c->nc, c->Kz, c->K, gpm, step, keep_s, c->dt, c->d_soff, fac_off, f.U, f.L, f.piv, f.invd,
             f.PHf, f.PHb, f.PSf, f.RNP, (const double*)s, (const double*)A, (const double*)Ap, (double*)out,
-            sp ? *sp : SplitPlanes());
+            sp ? *sp : SplitPlanes(), pair);
         if (wrote && sp && sp->bs) *wrote = true;
         return true;
       };
