@@ -386,10 +386,17 @@ int mlx_advance(mlx_ctx* c, int kind, const double* coeffs, int ncoeffs, void* s
   const int pairs = nsteps / 2;
   // capture one pair (planes_in: reuse the split planes the previous pair left) into
   // an executable graph; *left: the pair leaves the split planes of its output s
-  auto capture_pair = [&](bool planes_in, cudaGraphExec_t* exec, bool* left) -> int {
+  // (npairs > 1: that many pairs in one graph, each taking the planes the one
+  // before it left)
+  auto capture_pair = [&](bool planes_in, cudaGraphExec_t* exec, bool* left, int npairs = 1) -> int {
     cudaGraph_t g = nullptr;
     MLX_CUDA_TRY(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
-    const int r = pair_steps(c, kind, c0, s, Ap, c->cap_stream, planes_in, left);
+    int r = MLX_OK;
+    bool in = planes_in;
+    for (int q = 0; q < npairs && !r; ++q) {
+      r = pair_steps(c, kind, c0, s, Ap, c->cap_stream, in, left);
+      in = *left;
+    }
     cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
     if (r) { if (g) cudaGraphDestroy(g); return r; }
     if (e != cudaSuccess) { c->last_err = cudaGetErrorString(e); return MLX_ECUDA; }
@@ -445,16 +452,20 @@ int mlx_advance(mlx_ctx* c, int kind, const double* coeffs, int ncoeffs, void* s
   } else if (pairs > 0) {
     // two steps per graph: (s, A_prev) -> (spec1, specA) -> (s, A_prev), no copies;
     // variant 0 starts from the caller's state, variant 1 (the later pairs of the
-    // call) reuses the split planes the previous pair left
-    cudaGraphExec_t ex[2] = {nullptr, nullptr};
+    // call) reuses the split planes the previous pair left, variant 2 is kChunk
+    // later pairs in one graph (fewer graph launches, each pair as in variant 1,
+    // or as in variant 0 when the steps leave no planes)
+    constexpr int kChunk = 8;
+    cudaGraphExec_t ex[3] = {nullptr, nullptr, nullptr};
     bool left = false;
-    for (int v = 0; v < 2; ++v) {
-      if (v == 1 && !(left && pairs > 1)) break;
+    for (int v = 0; v < 3; ++v) {
+      if (v == 1 && !(left && pairs > 1)) continue;
+      if (v == 2 && pairs - 1 < kChunk) break;
       mlx_ctx::GraphKey key{state, prev_A, kind, c0, v};
       auto it = c->graphs.find(key);
       if (it == c->graphs.end()) {
         bool l = false;
-        if ((rc = capture_pair(v == 1, &ex[v], &l))) return rc;
+        if ((rc = capture_pair(v >= 1 && left, &ex[v], &l, v == 2 ? kChunk : 1))) return rc;
         c->graphs[key] = ex[v];
         c->graph_left[key] = l;
         if (v == 0) left = l;
@@ -463,7 +474,10 @@ int mlx_advance(mlx_ctx* c, int kind, const double* coeffs, int ncoeffs, void* s
         if (v == 0) left = c->graph_left[key];
       }
     }
-    for (int i = 0; i < pairs; ++i) MLX_CUDA_TRY(c, cudaGraphLaunch(ex[(i > 0 && ex[1]) ? 1 : 0], st));
+    int i = 0;
+    MLX_CUDA_TRY(c, cudaGraphLaunch(ex[0], st));
+    for (i = 1; ex[2] && i + kChunk <= pairs; i += kChunk) MLX_CUDA_TRY(c, cudaGraphLaunch(ex[2], st));
+    for (; i < pairs; ++i) MLX_CUDA_TRY(c, cudaGraphLaunch(ex[1] ? ex[1] : ex[0], st));
   }
   if (nsteps % 2) {
     if ((rc = abcn_step(c, kind, c0, s, c->d_specA, Ap, c->d_spec1, st))) return rc;
