@@ -420,10 +420,10 @@ int mlx_set_tuning(mlx_ctx* ctx, const char* key, int value);
  * paper, whose runs are single problems) ----
  * A batch groups n independent contexts (any sizes, precisions and kinds; each
  * created and set up by the caller, which keeps owning them).  The batch owns
- * only streams, events and cached CUDA graphs.  Creating a batch sets the
- * tuning keys "solve_keep_s" and "solve_seg" of every member to 0 (smaller
- * shared-memory footprint per solve CTA, so that the instances' kernels
- * co-reside). */
+ * only streams, events, cached CUDA graphs and the work lists of its persistent
+ * launches.  Creating a batch sets the tuning key "solve_keep_s" of every member
+ * to 0 (smaller shared-memory footprint per solve warp, so that more warps and
+ * the instances' kernels co-reside). */
 typedef struct mlx_batch mlx_batch;
 int mlx_batch_create(mlx_ctx* const* ctxs, int n, mlx_batch** out);
 int mlx_batch_destroy(mlx_batch* batch);
