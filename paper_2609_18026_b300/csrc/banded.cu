@@ -19,6 +19,8 @@
 #include "bf16_split.cuh"
 
 #include <string.h>
+
+#include <algorithm>
 #include <type_traits>
 
 namespace {
@@ -581,6 +583,7 @@ __device__ __forceinline__ void band_solve_warp(int gw, unsigned char* __restric
   }
 }
 
+// gw0: the first warp task (m gw0 / groups_per_m onwards; 0 for a whole family)
 template <int KL>
 __global__ void k_band_solve(int M, int nc, int Kz, int K, int CPW, int groups_per_m, int step, int keep_s,
                              double dt, const long long* __restrict__ soff,
@@ -589,10 +592,10 @@ __global__ void k_band_solve(int M, int nc, int Kz, int K, int CPW, int groups_p
                              const double* __restrict__ Lm, const int* __restrict__ piv,
                              const double* __restrict__ invd, const double* __restrict__ s,
                              const double* __restrict__ A, const double* __restrict__ Ap,
-                             double* __restrict__ out) {
+                             double* __restrict__ out, int gw0) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int wib = threadIdx.x >> 5;
-  const int gw = blockIdx.x * (blockDim.x >> 5) + wib;   // global warp = (m, group)
+  const int gw = gw0 + blockIdx.x * (blockDim.x >> 5) + wib;   // global warp = (m, group)
   unsigned char* base = smem_raw + (size_t)wib * SolveSmem<KL>::per_warp(nc, CPW, keep_s);
   band_solve_warp<KL>(gw, base, M, nc, Kz, K, CPW, groups_per_m, step, keep_s, dt, soff, band_off, kz_fac,
                       m0_shift, U, Lm, piv, invd, s, A, Ap, out);
@@ -1480,6 +1483,7 @@ static int launch_solve(mlx_ctx* c, int step, const BandLU& f, const long long* 
                         int m0_shift, const double2* s, const double2* A, const double2* Ap, double2* out,
                         cudaStream_t st, int nfields = 1, const SplitPlanes* sp = nullptr, bool* wrote = nullptr) {
   if (wrote) *wrote = false;
+  int seg_done = 0;
   if (nfields == 2 && c->solve_direct != 2) return MLX_EINVAL;   // two fields per launch: lean only
   if (c->solve_direct == 2) {
     if (!c->d_solve_y || !f.FS || !f.BS) return MLX_ESTATE;
@@ -1520,8 +1524,9 @@ static int launch_solve(mlx_ctx* c, int step, const BandLU& f, const long long* 
     return go(I32(), MP());
   }
   if constexpr (KL == 2) {
-    if (c->solve_seg && f.PHf && f.seg && kz_fac == c->Kz && m0_shift == 0) {
+    if (c->solve_seg && f.PHf && f.seg && f.seg_m > 0 && kz_fac == c->Kz && m0_shift == 0) {
       const int keep_s = (step == MLX_STEP_ABCN && c->solve_keep_s) ? 1 : 0;
+      const bool whole = f.seg_m == c->M;           // else the staged solve takes m >= seg_m
       auto go = [&](auto seg_tag) -> bool {
         constexpr int S = decltype(seg_tag)::value;
         const bool np = f.nopiv && f.RNP;
@@ -1531,22 +1536,26 @@ static int launch_solve(mlx_ctx* c, int step, const BandLU& f, const long long* 
         if (pw * WPB > 200 * 1024) return false;
         const int G = SegSmem<KL, S>::G;
         const int gpm = (c->Kz + G - 1) / G;
-        const int warps = c->M * gpm;
+        const int warps = f.seg_m * gpm;
         auto kern = np ? k_band_solve_seg<KL, S, true> : k_band_solve_seg<KL, S, false>;
         const int pair = WPB == 8 ? 1 : 0;
         const int blocks = pair ? ((warps + 1) / 2 + 3) / 4 : (warps + WPB - 1) / WPB;
         kern<<<blocks, 32 * WPB, pw * WPB, st>>>(
-            c->M, c->nc, c->Kz, c->K, gpm, step, keep_s, c->dt, c->d_soff, fac_off, f.U, f.L, f.piv, f.invd,
+            f.seg_m, c->nc, c->Kz, c->K, gpm, step, keep_s, c->dt, c->d_soff, fac_off, f.U, f.L, f.piv, f.invd,
             f.PHf, f.PHb, f.PSf, f.RNP, (const double*)s, (const double*)A, (const double*)Ap, (double*)out,
-            sp ? *sp : SplitPlanes(), pair);
-        if (wrote && sp && sp->bs) *wrote = true;
+            (sp && whole) ? *sp : SplitPlanes(), pair);
+        if (wrote && sp && sp->bs && whole) *wrote = true;
         return true;
       };
-      if (f.seg == 8 ? go(std::integral_constant<int, 8>()) : go(std::integral_constant<int, 4>())) return MLX_OK;
+      if (f.seg == 8 ? go(std::integral_constant<int, 8>()) : go(std::integral_constant<int, 4>())) {
+        if (whole) return MLX_OK;
+        seg_done = f.seg_m;                         // the staged solve below takes the rest
+      }
     }
   }
   // Chains per warp and warps per CTA are launch-shape parameters (measured best
   // at the 128x128x64 workload: 8 chains per warp, 1-4 warps per CTA).
+  // seg_done > 0: the orders m < seg_done were solved by the segmented kernel.
   int CPW = c->solve_cpw;
   const int keep_s = (step == MLX_STEP_ABCN && c->solve_keep_s) ? 1 : 0;
   while (CPW > 4 && SolveSmem<KL>::per_warp(c->nc, CPW, keep_s) > 200 * 1024) CPW /= 2;
@@ -1555,11 +1564,11 @@ static int launch_solve(mlx_ctx* c, int step, const BandLU& f, const long long* 
   while (WPB > 1 && pw * WPB > 200 * 1024) WPB /= 2;
   if (pw * WPB > 200 * 1024) return MLX_EINVAL;
   const int gpm = (c->Kz + CPW / 4 - 1) / (CPW / 4);
-  const int warps = c->M * gpm;
+  const int warps = (c->M - seg_done) * gpm;
   const int blocks = (warps + WPB - 1) / WPB;
   k_band_solve<KL><<<blocks, 32 * WPB, pw * WPB, st>>>(
       c->M, c->nc, c->Kz, c->K, CPW, gpm, step, keep_s, c->dt, c->d_soff, fac_off, kz_fac, m0_shift, f.U, f.L,
-      f.piv, f.invd, (const double*)s, (const double*)A, (const double*)Ap, (double*)out);
+      f.piv, f.invd, (const double*)s, (const double*)A, (const double*)Ap, (double*)out, seg_done * gpm);
   return MLX_OK;
 }
 
@@ -1695,35 +1704,41 @@ static int set_lean_attrs(mlx_ctx* c, int lim) {
 }
 
 // Segmented-solve influence data of an implicit-step factor family for S segments
-// (S = 0 frees it).  Built only for half width 2 when every segment has at least
-// 2 kl rows (S = 8 falls back to 4 when the shortest chain is too short); otherwise
-// the family keeps none and the staged solve runs.
+// (S = 0 frees it), half width 2 only.  A system can be cut when every segment has
+// at least 2 kl rows, N = Nc - m >= 2 kl S: the data cover the orders m < seg_m
+// (the longest systems), and the staged solve takes the rest.  S = 8 falls back to
+// 4 when 4 segments reach every order and 8 do not, or when 8 reach none.
 int mlx_seg_build(mlx_ctx* c, BandLU& f, int S, cudaStream_t st) {
   cudaFree(f.PHf); cudaFree(f.PHb); cudaFree(f.PSf); cudaFree(f.RNP);
   f.PHf = f.PHb = f.PSf = f.RNP = nullptr;
   f.seg = 0;
+  f.seg_m = 0;
   const int kl = c->kl;
-  if (S == 8 && (c->nc - (c->M - 1)) / 8 < 2 * kl) S = 4;   // chains too short for 8 segments
-  if (S == 0 || kl != 2 || !f.U || (c->nc - (c->M - 1)) / S < 2 * kl) return MLX_OK;
+  auto cover = [&](int s_) { return std::max(0, std::min(c->M, c->nc - s_ * 2 * kl + 1)); };
+  if (S == 8 && cover(8) < c->M && cover(4) == c->M) S = 4;
+  if (S == 8 && cover(8) == 0) S = 4;
+  if (S == 0 || kl != 2 || !f.U || cover(S) == 0) return MLX_OK;
+  const int segm = cover(S);
   const long long rows = c->band_rows;
   MLX_CUDA_TRY(c, cudaMalloc(&f.PHf, sizeof(double) * rows * kl));
   MLX_CUDA_TRY(c, cudaMalloc(&f.PHb, sizeof(double) * rows * 2 * kl));
   MLX_CUDA_TRY(c, cudaMalloc(&f.PSf, sizeof(double) * (long long)c->M * c->Kz * S * kl * kl));
-  const long long nt = (long long)c->M * c->Kz * S * 3 * kl;
+  const long long nt = (long long)segm * c->Kz * S * 3 * kl;
   if (S == 8)
-    k_seg_setup<2, 8><<<(unsigned)((nt + 127) / 128), 128, 0, st>>>(c->M, c->nc, c->Kz, c->d_band_off, f.U,
+    k_seg_setup<2, 8><<<(unsigned)((nt + 127) / 128), 128, 0, st>>>(segm, c->nc, c->Kz, c->d_band_off, f.U,
                                                                     f.L, f.piv, f.PHf, f.PHb, f.PSf);
   else
-    k_seg_setup<2, 4><<<(unsigned)((nt + 127) / 128), 128, 0, st>>>(c->M, c->nc, c->Kz, c->d_band_off, f.U,
+    k_seg_setup<2, 4><<<(unsigned)((nt + 127) / 128), 128, 0, st>>>(segm, c->nc, c->Kz, c->d_band_off, f.U,
                                                                     f.L, f.piv, f.PHf, f.PHb, f.PSf);
   MLX_LAUNCH_CHECK(c);
   if (f.nopiv) {
     MLX_CUDA_TRY(c, cudaMalloc(&f.RNP, sizeof(double) * rows * SegSmem<2, 8>::RW));
-    dim3 grid((unsigned)(((long long)c->Kz * c->nc + 127) / 128), c->M);
+    dim3 grid((unsigned)(((long long)c->Kz * c->nc + 127) / 128), segm);
     k_pack_seg_np<2><<<grid, 128, 0, st>>>(c->nc, c->Kz, c->d_band_off, f.U, f.L, f.invd, f.PHf, f.PHb, f.RNP);
     MLX_LAUNCH_CHECK(c);
   }
   f.seg = S;
+  f.seg_m = segm;
   return MLX_OK;
 }
 
@@ -1797,12 +1812,13 @@ int mlx_spec_axpby(mlx_ctx* c, double a, const double2* x, double b, const doubl
 // Job and warp items of member c (index inst) for one AB-CN solve s, A, Ap -> out
 // (A, Ap may be NULL), half width c->kl; *slab: the member's shared memory per warp.
 // Az (may be NULL): a buffer the solve fills with zeros (the A^j of a member
-// without a nonlinear term).
-// planes: the segmented variant also writes the BF16x3 split planes of out into the
-// member's backward data operand (*wrote_planes tells whether it will).
-void mlx_band_batch_member(mlx_ctx* c, int inst, const double2* s, const double2* A, const double2* Ap,
-                           double2* out, double2* Az, bool planes, BSolveJob* job, std::vector<int2>& items,
-                           std::vector<double>& cost, int* slab, bool* wrote_planes) {
+// without a nonlinear term).  planes: the segmented variant also writes the BF16x3
+// split planes of out into the member's backward data operand when it covers every
+// order (*wrote_planes tells whether it will).  The member's solve becomes one or
+// two parts, as its single-context launch would split it: the segmented variant
+// for the orders m < seg_m, the staged one (its chains per warp) for the rest.
+void mlx_band_batch_member(mlx_ctx* c, const double2* s, const double2* A, const double2* Ap, double2* out,
+                           double2* Az, bool planes, std::vector<BSolvePart>& parts, bool* wrote_planes) {
   auto per_warp = [&](int cpw) -> size_t {
     switch (c->kl) {
       case 2: return SolveSmem<2>::per_warp(c->nc, cpw, 0);
@@ -1811,44 +1827,59 @@ void mlx_band_batch_member(mlx_ctx* c, int inst, const double2* s, const double2
       default: return SolveSmem<8>::per_warp(c->nc, cpw, 0);
     }
   };
-  // the member's own variant: segmented (half width 2, influence data built) or
-  // staged with its chains per warp, as its single-context launch would take them
   const BandLU& f = c->lu_half;
-  const bool seg = c->kl == 2 && c->solve_seg && f.PHf && f.seg;
+  const bool seg = c->kl == 2 && c->solve_seg && f.PHf && f.seg && f.seg_m > 0;
   const bool np = seg && f.nopiv && f.RNP;
-  int CPW = c->solve_cpw;
-  while (CPW > 4 && per_warp(CPW) > 200 * 1024) CPW /= 2;
-  size_t pw = per_warp(CPW);
-  if (seg) {
-    CPW = 32 / f.seg;
-    pw = f.seg == 8 ? SegSmem<2, 8>::per_warp(c->nc, 0, np) : SegSmem<2, 4>::per_warp(c->nc, 0, np);
-  }
-  BSolveJob j;
-  memset(&j, 0, sizeof(j));
-  j.variant = seg ? (f.seg == 8 ? 1 : 2) + (np ? 2 : 0) : 0;
-  j.M = c->M; j.nc = c->nc; j.Kz = c->Kz; j.K = c->K; j.CPW = CPW;
-  j.gpm = (c->Kz + CPW / 4 - 1) / (CPW / 4);
-  j.step = MLX_STEP_ABCN;
-  j.kz_fac = c->Kz;
-  j.dt = c->dt;
-  j.soff = c->d_soff; j.band_off = c->d_band_off;
-  j.U = f.U; j.L = f.L; j.piv = f.piv; j.invd = f.invd;
-  j.PHf = f.PHf; j.PHb = f.PHb; j.PSf = f.PSf; j.RNP = f.RNP;
-  j.s = (const double*)s; j.A = (const double*)A; j.Ap = (const double*)Ap; j.out = (double*)out;
-  j.Az = (double*)Az;
+  const int mseg = seg ? f.seg_m : 0;
+  BSolveJob base;
+  memset(&base, 0, sizeof(base));
+  base.M = c->M; base.nc = c->nc; base.Kz = c->Kz; base.K = c->K;
+  base.step = MLX_STEP_ABCN;
+  base.kz_fac = c->Kz;
+  base.dt = c->dt;
+  base.soff = c->d_soff; base.band_off = c->d_band_off;
+  base.U = f.U; base.L = f.L; base.piv = f.piv; base.invd = f.invd;
+  base.s = (const double*)s; base.A = (const double*)A; base.Ap = (const double*)Ap; base.out = (double*)out;
+  base.Az = (double*)Az;
   *wrote_planes = false;
-  if (seg && planes && c->precision == MLX_BF16X3 && c->d_bsb) {
-    j.bs = reinterpret_cast<unsigned short*>(c->d_bsb);
-    j.kq = (int)c->tc_kq;
-    j.k2 = 2 * c->K;
-    j.part = (long long)c->M * j.k2 * j.kq;
-    *wrote_planes = true;
+  if (seg) {
+    BSolvePart pt;
+    pt.job = base;
+    BSolveJob& j = pt.job;
+    j.variant = (f.seg == 8 ? 1 : 2) + (np ? 2 : 0);
+    j.M = mseg;                      // the segmented kernel's orders
+    j.CPW = 32 / f.seg;
+    j.gpm = (c->Kz + j.CPW / 4 - 1) / (j.CPW / 4);
+    j.PHf = f.PHf; j.PHb = f.PHb; j.PSf = f.PSf; j.RNP = f.RNP;
+    if (planes && mseg == c->M && c->precision == MLX_BF16X3 && c->d_bsb) {
+      j.bs = reinterpret_cast<unsigned short*>(c->d_bsb);
+      j.kq = (int)c->tc_kq;
+      j.k2 = 2 * c->K;
+      j.part = (long long)c->M * j.k2 * j.kq;
+      *wrote_planes = true;
+    }
+    pt.slab = (int)(f.seg == 8 ? SegSmem<2, 8>::per_warp(c->nc, 0, np) : SegSmem<2, 4>::per_warp(c->nc, 0, np));
+    for (int gw = 0; gw < mseg * j.gpm; ++gw) {
+      pt.items.push_back(make_int2(0, gw));
+      pt.cost.push_back((double)(c->nc - gw / j.gpm));
+    }
+    parts.push_back(pt);
   }
-  *job = j;
-  *slab = (int)pw;
-  for (int gw = 0; gw < c->M * j.gpm; ++gw) {
-    items.push_back(make_int2(inst, gw));
-    cost.push_back((double)(c->nc - gw / j.gpm));
+  if (mseg < c->M) {
+    BSolvePart pt;
+    pt.job = base;
+    BSolveJob& j = pt.job;
+    int CPW = c->solve_cpw;
+    while (CPW > 4 && per_warp(CPW) > 200 * 1024) CPW /= 2;
+    j.variant = 0;
+    j.CPW = CPW;
+    j.gpm = (c->Kz + CPW / 4 - 1) / (CPW / 4);
+    pt.slab = (int)per_warp(CPW);
+    for (int gw = mseg * j.gpm; gw < c->M * j.gpm; ++gw) {
+      pt.items.push_back(make_int2(0, gw));
+      pt.cost.push_back((double)(c->nc - gw / j.gpm));
+    }
+    parts.push_back(pt);
   }
 }
 

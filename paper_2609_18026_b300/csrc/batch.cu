@@ -38,9 +38,8 @@ void mlx_legendre_batch_member(mlx_ctx* c, bool fwd, int inst, double2* spec, BL
 int mlx_legendre_batch_launch(bool fwd, bool dbl, const BLegJob* jobs, const LegTile* items, int nitems,
                               int* ctr, int grid, cudaStream_t st);
 const void* mlx_legendre_batch_kernel(bool fwd, bool dbl);
-void mlx_band_batch_member(mlx_ctx* c, int inst, const double2* s, const double2* A, const double2* Ap,
-                           double2* out, double2* Az, bool planes, BSolveJob* job, std::vector<int2>& items,
-                           std::vector<double>& cost, int* slab, bool* wrote_planes);
+void mlx_band_batch_member(mlx_ctx* c, const double2* s, const double2* A, const double2* Ap, double2* out,
+                           double2* Az, bool planes, std::vector<BSolvePart>& parts, bool* wrote_planes);
 const void* mlx_band_batch_kernel(int kl, int variant);
 int mlx_band_batch_launch(int kl, int variant, const BSolveJob* jobs, const int2* items, int nitems, int slab,
                           int wpb, int* ctr, int grid, cudaStream_t st);
@@ -205,19 +204,18 @@ int solve_launches(const std::vector<int>& members, mlx_ctx* const* ctxs,
                    const std::vector<double2*>& Az, const std::vector<char>& planes, std::vector<char>& wrote,
                    std::vector<QLaunch>& L) {
   std::map<std::vector<int>, std::vector<int>> groups;
-  std::vector<int> slabs(members.size());
-  std::vector<BSolveJob> alljobs(members.size());
-  std::vector<std::vector<int2>> allitems(members.size());
-  std::vector<std::vector<double>> allcost(members.size());
+  std::vector<BSolvePart> parts;
   for (size_t q = 0; q < members.size(); ++q) {
     const int i = members[q];
     bool w = false;
-    mlx_band_batch_member(ctxs[i], 0, sin[i], A[i], Ap[i], out[i], Az[i], planes[i] != 0, &alljobs[q],
-                          allitems[q], allcost[q], &slabs[q], &w);
+    const size_t first = parts.size();
+    mlx_band_batch_member(ctxs[i], sin[i], A[i], Ap[i], out[i], Az[i], planes[i] != 0, parts, &w);
     wrote[i] = w;
-    int cls = 0;
-    while (cls < 3 && slabs[q] > (16 << 10) << cls) ++cls;
-    groups[{ctxs[i]->kl, alljobs[q].variant, cls}].push_back((int)q);
+    for (size_t pi = first; pi < parts.size(); ++pi) {
+      int cls = 0;
+      while (cls < 3 && parts[pi].slab > (16 << 10) << cls) ++cls;
+      groups[{ctxs[i]->kl, parts[pi].job.variant, cls}].push_back((int)pi);
+    }
   }
   for (auto& kv : groups) {
     QLaunch ql;
@@ -230,12 +228,12 @@ int solve_launches(const std::vector<int>& members, mlx_ctx* const* ctxs,
     int slab = 16;
     for (int q : kv.second) {
       const int j = (int)jobs.size();
-      jobs.push_back(alljobs[q]);
-      for (size_t t = 0; t < allitems[q].size(); ++t) {
-        items.push_back(make_int2(j, allitems[q][t].y));
-        cost.push_back(allcost[q][t]);
+      jobs.push_back(parts[q].job);
+      for (size_t t = 0; t < parts[q].items.size(); ++t) {
+        items.push_back(make_int2(j, parts[q].items[t].y));
+        cost.push_back(parts[q].cost[t]);
       }
-      if (slabs[q] > slab) slab = slabs[q];
+      if (parts[q].slab > slab) slab = parts[q].slab;
     }
     const std::vector<int> ord = by_cost(cost);
     items = permute(items, ord);

@@ -145,6 +145,15 @@ int mlx_tc_batch_plan(mlx_ctx* const* members, int n, bool fwd, double2* const* 
 int mlx_tc_batch_launch(TcBatchPlan* plan, cudaStream_t st);
 void mlx_tc_batch_free(TcBatchPlan* plan);
 
+// One part of a member's solve in a batched launch (host side): its job, its warp
+// items (member index 0, warp task) with their costs, and its shared memory per warp.
+struct BSolvePart {
+  BSolveJob job;
+  std::vector<int2> items;
+  std::vector<double> cost;
+  int slab = 0;
+};
+
 struct BandLU {
   double* U = nullptr;     // [rows][W_u] with W_u = 1 + kl + ku
   double* L = nullptr;     // [rows][kl]
@@ -160,6 +169,7 @@ struct BandLU {
   double* PHb = nullptr;
   double* PSf = nullptr;
   int seg = 0;             // segments the influence data were built for (0 = none)
+  int seg_m = 0;           // the data cover the orders m < seg_m (the staged solve takes the rest)
   bool nopiv = false;      // no system of the family interchanged rows (segmented solve skips pivoting)
   // pivot-free segmented solve: one contiguous record per system row, the system's
   // rows back to back ([m][|k|][row], record = {L[kl], 1/diag, U upper[kl], PHf[kl],

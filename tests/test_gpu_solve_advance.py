@@ -206,12 +206,14 @@ def test_solve_variants_agree(nu_h, p, step):
 
 @pytest.mark.parametrize("grid", [(40, 16, 8, 1.5), (96, 32, 16, 1.0), (128, 128, 64, 4.0),
                                   (33, 16, 8, 1.0),    # shortest chain 28 rows: 8 segments fall back to 4
-                                  (16, 8, 4, 1.0)])    # 14 rows: no segments, staged solve
+                                  (16, 8, 4, 1.0),     # only m = 0 (16 rows) cut in 4, m = 1, 2 staged
+                                  (48, 128, 4, 1.0)])  # M = 43: m < 17 cut in 8 segments, the rest staged
 @pytest.mark.parametrize("step", [B.STEP_FEBE_HALF, B.STEP_FEBE_FULL, B.STEP_ABCN])
 def test_segmented_solve(grid, step):
     # half width 2: the chains cut into 4 or 8 row segments solved side by side, entry
-    # states fixed by the precomputed influence data; same systems as the staged
-    # recurrence, sums in another order: within 1e-12 of the oracle and of it
+    # states fixed by the precomputed influence data (orders whose chains are too
+    # short for the segments go to the staged recurrence); same systems as the
+    # staged recurrence, sums in another order: within 1e-12 of the oracle and of it
     nr, nphi, nz, ell = grid
     g, ctx = pair(nr, nphi, nz, ell, lz=3.0, policy="twothirds")
     dt, nu = 2e-2, 0.3
