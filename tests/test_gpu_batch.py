@@ -187,3 +187,42 @@ def test_batch64_persistent_equals_branches():
     for c in ctxs:
         c.device_status()   # raises on an expired bounded wait or a non-finite product
     batch.close()
+
+
+def test_batch_tensor_core_launches_split_past_64_members():
+    # 70 small BF16x3 Fisher-KPP members: the tensor-core contraction takes at most
+    # 64 members' maps per launch, so each direction runs as two launches; the
+    # persistent graph still matches the per-member branches bitwise.
+    import torch
+    ctxs, s0 = [], []
+    rng = np.random.default_rng(70)
+    for j in range(70):
+        nr = int(rng.choice([16, 24, 32]))
+        nphi = int(rng.choice([8, 16]))
+        nz = int(rng.choice([1, 4]))
+        ell = float(rng.uniform(0.7, 2.0))
+        ctx = B.Context(nr, nphi, nz, ell, lz=2 * math.pi, precision=B.BF16X3, chop_policy=B.CHOP_TWOTHIRDS)
+        ctx.implicit_setup(1.0, 1e-3)
+        x, w, r = ctx.nodes()
+        phi = 2 * np.pi * np.arange(nphi) / nphi
+        zz = 2 * np.pi * np.arange(nz) / nz
+        par = dict(x0=0.2 * ell, y0=0.1 * ell, sigma=ell, nz=nz, lz=2 * math.pi)
+        u0 = W.batch_initial(par, r[None, None, :], phi[None, :, None], zz[:, None, None])
+        s0.append(ctx.forward(torch.as_tensor(u0, dtype=torch.float32).cuda(), ctx.new_spec()))
+        ctxs.append(ctx)
+    kinds = [B.NONLIN_FKPP] * 70
+    batch = B.Batch(ctxs)
+    out = []
+    for mode in (1, 0):
+        batch.set_persistent(mode)
+        st = [s.clone() for s in s0]
+        pv = [c.new_spec() for c in ctxs]
+        batch.advance(kinds, [1.0] * 70, st, pv, 5, True)
+        torch.cuda.synchronize()
+        out.append([s.cpu().numpy() for s in st])
+    for j in range(70):
+        assert np.isfinite(out[0][j]).all(), j
+        assert np.array_equal(out[0][j], out[1][j]), j
+    for c in ctxs:
+        c.device_status()
+    batch.close()
