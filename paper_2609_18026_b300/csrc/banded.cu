@@ -1056,6 +1056,8 @@ __global__ void k_band_solve_seg(int M, int nc, int Kz, int K, int groups_per_m,
                                  const double* __restrict__ Ap, double* __restrict__ out,
                                  SplitPlanes sp, int pair) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  pdl_wait();
+  pdl_trigger();
   const int wib = threadIdx.x >> 5;
   int gw = blockIdx.x * (blockDim.x >> 5) + wib;
   if (pair) {
@@ -1527,6 +1529,7 @@ static int launch_solve(mlx_ctx* c, int step, const BandLU& f, const long long* 
     if (c->solve_seg && f.PHf && f.seg && f.seg_m > 0 && kz_fac == c->Kz && m0_shift == 0) {
       const int keep_s = (step == MLX_STEP_ABCN && c->solve_keep_s) ? 1 : 0;
       const bool whole = f.seg_m == c->M;           // else the staged solve takes m >= seg_m
+      cudaError_t lerr = cudaSuccess;
       auto go = [&](auto seg_tag) -> bool {
         constexpr int S = decltype(seg_tag)::value;
         const bool np = f.nopiv && f.RNP;
@@ -1540,14 +1543,15 @@ static int launch_solve(mlx_ctx* c, int step, const BandLU& f, const long long* 
         auto kern = np ? k_band_solve_seg<KL, S, true> : k_band_solve_seg<KL, S, false>;
         const int pair = WPB == 8 ? 1 : 0;
         const int blocks = pair ? ((warps + 1) / 2 + 3) / 4 : (warps + WPB - 1) / WPB;
-        kern<<<blocks, 32 * WPB, pw * WPB, st>>>(
-            f.seg_m, c->nc, c->Kz, c->K, gpm, step, keep_s, c->dt, c->d_soff, fac_off, f.U, f.L, f.piv, f.invd,
-            f.PHf, f.PHb, f.PSf, f.RNP, (const double*)s, (const double*)A, (const double*)Ap, (double*)out,
-            (sp && whole) ? *sp : SplitPlanes(), pair);
+        lerr = launch_pdl(kern, dim3(blocks), dim3(32 * WPB), pw * WPB, st,
+                          f.seg_m, c->nc, c->Kz, c->K, gpm, step, keep_s, c->dt, c->d_soff, fac_off, f.U, f.L,
+                          f.piv, f.invd, f.PHf, f.PHb, f.PSf, f.RNP, (const double*)s, (const double*)A,
+                          (const double*)Ap, (double*)out, (sp && whole) ? *sp : SplitPlanes(), pair);
         if (wrote && sp && sp->bs && whole) *wrote = true;
         return true;
       };
       if (f.seg == 8 ? go(std::integral_constant<int, 8>()) : go(std::integral_constant<int, 4>())) {
+        if (lerr != cudaSuccess) { c->last_err = cudaGetErrorString(lerr); return MLX_ECUDA; }
         if (whole) return MLX_OK;
         seg_done = f.seg_m;                         // the staged solve below takes the rest
       }

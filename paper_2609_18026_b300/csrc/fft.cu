@@ -400,7 +400,9 @@ __global__ void __launch_bounds__(256) k_phi(int N, int logN, int M, int Nr, int
                                              const typename C2T<T>::type* __restrict__ tw, T gamma,
                                              int* __restrict__ err, SplitOut so) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  pdl_wait();
   phi_tile<T, MODE, E>(N, logN, M, Nr, R, blockIdx.x, blockIdx.y, phys, zre, zim, tw, gamma, err, so, smem_raw);
+  pdl_trigger();
 }
 
 // Axial transform for one m and a tile of R radii: lines are radii.
@@ -525,7 +527,9 @@ __global__ void __launch_bounds__(256) k_z(int Nz, int logN, int Kz, int K, int 
                                            T* __restrict__ mre, T* __restrict__ mim,
                                            const typename C2T<T>::type* __restrict__ tw, SplitOut so) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  pdl_wait();
   z_tile<T, INVERSE, E>(Nz, logN, Kz, K, M, Nr, R, blockIdx.x, blockIdx.y, zre, zim, mre, mim, tw, so, smem_raw);
+  pdl_trigger();
 }
 
 // Batched persistent forms of the stages (batch.cu): every CTA takes (member,
@@ -618,8 +622,8 @@ template <typename T, int MODE, int E>
 void phi_go(dim3 grid, size_t smem, cudaStream_t st, int N, int M, int Nr, int R, T* phys, T* zre,
             T* zim, const void* tw, double gamma, int* err, const SplitOut& so) {
   typedef typename C2T<T>::type C;
-  k_phi<T, MODE, E><<<grid, 256, smem, st>>>(N, ilog2(N), M, Nr, R, phys, zre, zim,
-                                             reinterpret_cast<const C*>(tw), (T)gamma, err, so);
+  launch_pdl(k_phi<T, MODE, E>, grid, dim3(256), smem, st, N, ilog2(N), M, Nr, R, phys, zre, zim,
+             reinterpret_cast<const C*>(tw), (T)gamma, err, so);
 }
 
 template <typename T, int MODE>
@@ -674,8 +678,8 @@ void z_go(dim3 grid, size_t smem, cudaStream_t st, mlx_ctx* c, int R, T* zb, T* 
   typedef typename C2T<T>::type C;
   const long long plz = (long long)c->nz * c->M * c->nr;
   const long long plm = (long long)c->K * c->M * c->nr;
-  k_z<T, INV, E><<<grid, 256, smem, st>>>(c->nz, ilog2(c->nz), c->Kz, c->K, c->M, c->nr, R, zb,
-                                          zb + plz, mb, mb + plm, reinterpret_cast<const C*>(tw), so);
+  launch_pdl(k_z<T, INV, E>, grid, dim3(256), smem, st, c->nz, ilog2(c->nz), c->Kz, c->K, c->M, c->nr, R, zb,
+             zb + plz, mb, mb + plm, reinterpret_cast<const C*>(tw), so);
 }
 
 template <typename T, bool INV>

@@ -141,6 +141,8 @@ k_leg_tc(const __grid_constant__ TcParams<NB> P, const LegTile* __restrict__ ite
   const unsigned pad = (1024u - (raw & 1023u)) & 1023u;
   const unsigned sbytes = tc_stage_bytes(bnmax);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  pdl_wait();      // (a no-op unless launched with programmatic serialisation)
+  pdl_trigger();
 
   if (tid == 0) {
     for (int s = 0; s < TC_STAGES; ++s) {
@@ -542,10 +544,12 @@ int launch_single(mlx_ctx* c, bool fwd, const TcParams<1>& P, cudaStream_t st) {
   const size_t smem = tc_smem(c->tc_bn);
   if (fwd) {
     auto kern = c->tc_products == 8 ? k_leg_tc<true, 8, 1> : k_leg_tc<true, 6, 1>;
-    kern<<<grid, TC_THREADS, smem, st>>>(P, items, n, c->tc_bn, c->tc_tmem_cols, c->tc_expire, c->d_err);
+    MLX_CUDA_TRY(c, launch_pdl(kern, dim3(grid), dim3(TC_THREADS), smem, st, P, items, n, c->tc_bn,
+                               c->tc_tmem_cols, c->tc_expire, c->d_err));
   } else {
     auto kern = c->tc_products == 8 ? k_leg_tc<false, 8, 1> : k_leg_tc<false, 6, 1>;
-    kern<<<grid, TC_THREADS, smem, st>>>(P, items, n, c->tc_bn, c->tc_tmem_cols, c->tc_expire, c->d_err);
+    MLX_CUDA_TRY(c, launch_pdl(kern, dim3(grid), dim3(TC_THREADS), smem, st, P, items, n, c->tc_bn,
+                               c->tc_tmem_cols, c->tc_expire, c->d_err));
   }
   MLX_LAUNCH_CHECK(c);
   return MLX_OK;

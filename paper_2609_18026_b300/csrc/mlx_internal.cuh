@@ -22,6 +22,33 @@
 
 #define MLX_LAUNCH_CHECK(ctx) MLX_CUDA_TRY(ctx, cudaGetLastError())
 
+// Programmatic dependent launch of the time step's kernels (phi and z transforms,
+// the single-context tensor-core contraction, the segmented solve): the kernel may
+// be launched while its predecessor in the stream is still finishing, and every
+// such kernel calls pdl_wait() -- which returns once the predecessor grid has
+// completed and its memory is visible -- before it touches global memory, so the
+// order of all memory accesses is that of plain launches.  pdl_trigger() lets the
+// successor launch: at the start of single-wave kernels (whose CTAs are all resident
+// from the start, so a waiting successor only takes what their exits free), at the
+// end of each CTA of the multi-wave transform kernels.
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // Kernel identifiers for the opt-in per-launch CUDA-event timing.
 enum KernelId {
   KID_PHI_FWD = 0, KID_PHI_BWD, KID_PHI_FKPP, KID_Z_FWD, KID_Z_BWD,
