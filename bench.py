@@ -144,6 +144,20 @@ def oracle_sample(nsteps, threads=None):
     return nsteps / sec, used, sec
 
 
+def whole_job_rate(local_ms, units_per_rank, world, device="cpu"):
+    """Whole-job throughput of `world` ranks (independent replicas), each of which
+    processed units_per_rank units in local_ms milliseconds: the units of all ranks
+    over the slowest rank's time (max over ranks).  Returns (rate per second,
+    slowest ms).  With world > 1 the process group must be initialised."""
+    import torch
+    t = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    slowest = float(t.item())
+    return units_per_rank * world / (slowest / 1000.0), slowest
+
+
 def _oracle_worker(nsteps, barrier, queue):
     """One process of the all-core oracle timing: build, warm up, wait for the
     others, then time its own sample (BLAS limited to one thread)."""
@@ -912,13 +926,7 @@ def run_gpu(args, rank, world):
     except Exception:
         pass
     clk = clocks.stop(bus)
-    total_ms = float(sum(ms))
-    tmax = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-    total_ms = float(tmax.item())
-    timesteps = args.steps * STEPS_PER_BENCH_STEP * world
-    value = timesteps / (total_ms / 1000.0)
+    value, total_ms = whole_job_rate(float(sum(ms)), args.steps * STEPS_PER_BENCH_STEP, world, dev)
 
     # ---- FP64 form, same workload and step count
     s64, a64 = fresh(ctx64, u0_64)
@@ -1089,11 +1097,7 @@ def run_gpu(args, rank, world):
     host_out.copy_(dev_phys, non_blocking=True)
     e1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1)
-    tm = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(tm, op=dist.ReduceOp.MAX)
-    e2e_value = args.steps * STEPS_PER_BENCH_STEP * world / (float(tm.item()) / 1000.0)
+    e2e_value, _ = whole_job_rate(e0.elapsed_time(e1), args.steps * STEPS_PER_BENCH_STEP, world, dev)
 
     others = {}
     if not args.no_other_workloads:
