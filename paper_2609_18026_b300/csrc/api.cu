@@ -32,7 +32,7 @@ void free_ctx(mlx_ctx* c) {
                   c->lu_helm.FS, c->lu_helm.BS, c->lu_Q.FS, c->lu_Q.BS, c->lu_H.FS, c->lu_H.BS,
                   c->lu_G.FS, c->lu_G.BS, c->lu_half.PHf, c->lu_half.PHb, c->lu_half.PSf,
                   c->lu_full.PHf, c->lu_full.PHb, c->lu_full.PSf, c->lu_half.RNP, c->lu_full.RNP, c->d_diag,
-                  c->d_bsf, c->d_bsb, c->d_filt, c->d_lp, c->d_enst, c->d_bsv};
+                  c->d_bsf, c->d_bsb, c->d_filt, c->d_lp, c->d_enst, c->d_bsv, c->d_rdr_df, c->d_lap_df};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);

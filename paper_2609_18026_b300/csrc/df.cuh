@@ -1,0 +1,98 @@
+// Double-float arithmetic: a value is an unevaluated sum hi + lo of two FP32 numbers
+// with |lo| <= ulp(hi) / 2 (hi is the FP32 rounding of the sum), about 48 significant
+// bits.  On this GPU an FP64 instruction issues once per 64 cycles per SM
+// sub-partition while FP32 instructions issue every cycle, so coefficient-space work
+// whose result is rounded to FP32 afterwards (the vortex term of the mixed-precision
+// forms) runs on the FP32 pipe in this representation.
+//
+// The error-free transformations are the classical ones: the sum of two floats with
+// its rounding error (Knuth's branch-free two-sum, and the three-operation form when
+// the larger operand is known), and a product with its rounding error from one fused
+// multiply-add.  Every operation is spelled with the _rn intrinsics so that the
+// compiler neither fuses nor reorders them.
+#pragma once
+
+#include <stdint.h>
+
+struct dfl { float hi, lo; };
+struct dfl2 { dfl re, im; };
+
+__device__ __forceinline__ dfl df_make(float hi, float lo) { dfl r; r.hi = hi; r.lo = lo; return r; }
+
+// s + e = a + b exactly, s = fl(a + b)
+__device__ __forceinline__ dfl df_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return df_make(s, e);
+}
+// the same when |a| >= |b| (or a = 0)
+__device__ __forceinline__ dfl df_fast_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  return df_make(s, __fsub_rn(b, __fsub_rn(s, a)));
+}
+__device__ __forceinline__ dfl df_add(dfl x, dfl y) {
+  dfl s = df_two_sum(x.hi, y.hi);
+  const dfl t = df_two_sum(x.lo, y.lo);
+  s.lo = __fadd_rn(s.lo, t.hi);
+  s = df_fast_sum(s.hi, s.lo);
+  s.lo = __fadd_rn(s.lo, t.lo);
+  return df_fast_sum(s.hi, s.lo);
+}
+__device__ __forceinline__ dfl df_neg(dfl x) { return df_make(-x.hi, -x.lo); }
+__device__ __forceinline__ dfl df_sub(dfl x, dfl y) { return df_add(x, df_neg(y)); }
+__device__ __forceinline__ dfl df_mul(dfl x, dfl y) {
+  const float p = __fmul_rn(x.hi, y.hi);
+  float e = __fmaf_rn(x.hi, y.hi, -p);
+  e = __fmaf_rn(x.hi, y.lo, e);
+  e = __fmaf_rn(x.lo, y.hi, e);
+  return df_fast_sum(p, e);
+}
+// a b + c
+__device__ __forceinline__ dfl df_fma(dfl a, dfl b, dfl c) { return df_add(df_mul(a, b), c); }
+
+// The FP64 value x as hi + lo by integer operations (no FP64 instruction): hi is the
+// FP32 rounding of x (to nearest even; |x| < 2^-126 gives 0, |x| >= 2^128 and
+// non-finite values give +-inf with lo = 0), lo the FP32 rounding of x - hi.
+__device__ __forceinline__ dfl df_from_double(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+  const int E = (int)((b >> 52) & 0x7ffu);
+  if (E < 897) return df_make(__uint_as_float(sign), 0.0f);             // |x| < 2^-126 (and 0)
+  if (E >= 1151) return df_make(__uint_as_float(sign | 0x7f800000u), 0.0f);
+  const unsigned long long X = (b & 0xfffffffffffffULL) | (1ULL << 52);  // 53-bit significand, x = X 2^(E - 1075)
+  unsigned long long H = X >> 29;                                        // 24 bits
+  const unsigned long long rem = X & ((1ULL << 29) - 1);
+  if (rem > (1ULL << 28) || (rem == (1ULL << 28) && (H & 1ULL))) ++H;     // to nearest, ties to even
+  int Ef = E - 896;                                                      // biased FP32 exponent of hi
+  long long R = (long long)X - (long long)(H << 29);                     // x - hi in units of 2^(E - 1075)
+  if (H == (1ULL << 24)) { H >>= 1; ++Ef; }                              // rounding carried into the next binade
+  if (Ef >= 255) return df_make(__uint_as_float(sign | 0x7f800000u), 0.0f);
+  const float hi = __uint_as_float(sign | ((unsigned)Ef << 23) | ((unsigned)H & 0x7fffffu));
+  // |R| <= 2^28: its FP32 rounding, scaled by 2^(E - 1075) (exact power-of-two scaling
+  // unless the result falls below the normal range, where it only loses low bits)
+  float lo = __ll2float_rn(R);
+  lo = ldexpf(lo, E - 1075);
+  if (sign) lo = -lo;
+  return df_make(hi, lo);
+}
+
+// hi + lo as FP64 (exact: both fit in 53 bits) -- FP64 instructions, off the hot paths
+__device__ __forceinline__ double df_to_double(dfl x) { return (double)x.hi + (double)x.lo; }
+
+// the FP32 rounding of hi + lo as the FP64 -> FP32 rounding used by the split writers
+// would give it (values below 2^-126 flush to a signed zero)
+__device__ __forceinline__ float df_round_f32(dfl x) {
+  return (fabsf(x.hi) < 1.17549435082228751e-38f) ? __uint_as_float(__float_as_uint(x.hi) & 0x80000000u) : x.hi;
+}
+
+__device__ __forceinline__ dfl2 dfc_make(dfl re, dfl im) { dfl2 r; r.re = re; r.im = im; return r; }
+__device__ __forceinline__ dfl2 dfc_from(double2 v) { return dfc_make(df_from_double(v.x), df_from_double(v.y)); }
+__device__ __forceinline__ dfl2 dfc_add(dfl2 a, dfl2 b) { return dfc_make(df_add(a.re, b.re), df_add(a.im, b.im)); }
+__device__ __forceinline__ dfl2 dfc_sub(dfl2 a, dfl2 b) { return dfc_make(df_sub(a.re, b.re), df_sub(a.im, b.im)); }
+// real a times complex v
+__device__ __forceinline__ dfl2 dfc_scale(dfl a, dfl2 v) { return dfc_make(df_mul(a, v.re), df_mul(a, v.im)); }
+// i a v
+__device__ __forceinline__ dfl2 dfc_iscale(dfl a, dfl2 v) { return dfc_make(df_neg(df_mul(a, v.im)), df_mul(a, v.re)); }
+// a v + w
+__device__ __forceinline__ dfl2 dfc_fma(dfl a, dfl2 v, dfl2 w) { return dfc_make(df_fma(a, v.re, w.re), df_fma(a, v.im, w.im)); }

@@ -288,6 +288,8 @@ struct mlx_ctx {
   // vortex term workspace
   bool vortex_ready = false;
   double* d_rdr = nullptr;             // r d/dr band, [tri][2] (offsets -1, +1)
+  void* d_rdr_df = nullptr;            // the same and the D_m band as double-float pairs (hi, lo),
+  void* d_lap_df = nullptr;            // for the mixed-precision forms' vortex term
   double* d_jac = nullptr;             // Jacobi matrix off-diagonal e_{m,i} (x Pbar_{m+i} couples i, i+1), [tri]
   double2* d_vspec = nullptr;          // 9 spectral temporaries
   void* d_vphys = nullptr;             // 6 physical temporaries

@@ -22,6 +22,7 @@
 // of the fields; the background is U = U0 e_y + Uz e_z.
 #include "mlx_internal.cuh"
 #include "bf16_split.cuh"
+#include "df.cuh"
 
 #include <cmath>
 
@@ -132,6 +133,103 @@ __global__ void k_vortex_fields(int nc, int Kz, int K, double lz, const long lon
       wz[idx] = fwz;
     }
   }
+}
+
+// The mixed-precision forms' fields kernel: the same operations in double-float
+// arithmetic (about 48 bits; the fields are rounded to FP32 for the transforms
+// afterwards), so that the band products run on the FP32 pipe.  The state and the
+// proxy terms arrive in FP64 and are split into hi + lo by integer operations; the
+// bands were converted once at setup.  Outputs as k_vortex_fields: the FP32 rounding
+// of each field into the split planes (vp.bs), or hi + lo as FP64 fields.
+__device__ __forceinline__ dfl2 apply_R_df(const dfl* rb, const dfl2* v, int a, int Nm) {
+  dfl2 r = dfc_make(df_make(0.f, 0.f), df_make(0.f, 0.f));
+  if (a - 1 >= 0) r = dfc_fma(rb[a * 2 + 0], v[a - 1], r);
+  if (a + 1 < Nm) r = dfc_fma(rb[a * 2 + 1], v[a + 1], r);
+  return r;
+}
+__device__ __forceinline__ dfl2 apply_D_df(const dfl* db, const dfl2* v, int a, int Nm) {
+  dfl2 r = dfc_make(df_make(0.f, 0.f), df_make(0.f, 0.f));
+#pragma unroll
+  for (int o = -2; o <= 2; ++o)
+    if (a + o >= 0 && a + o < Nm) r = dfc_fma(db[a * 5 + o + 2], v[a + o], r);
+  return r;
+}
+
+__global__ void k_vortex_fields_df(int nc, int Kz, int K, double lz, const long long* __restrict__ soff,
+                                   const long long* __restrict__ rows, const dfl* __restrict__ rdr,
+                                   const dfl* __restrict__ lap, const double2* __restrict__ psi,
+                                   const double2* __restrict__ chi, double2* __restrict__ rvr,
+                                   double2* __restrict__ rvp, double2* __restrict__ vz, double2* __restrict__ rwr,
+                                   double2* __restrict__ rwp, double2* __restrict__ wz,
+                                   const double* __restrict__ lpf, SplitPlanes vp) {
+  extern __shared__ dfl2 vdf[];   // [4][nc]: psi, chi, D chi, Psi
+  const int kidx = blockIdx.x, m = blockIdx.y;
+  const int Nm = nc - m;
+  const long long base = soff[m] + (long long)kidx * Nm;
+  dfl2* P = vdf;
+  dfl2* Ch = vdf + nc;
+  dfl2* Dc = vdf + 2 * nc;
+  dfl2* Ps = vdf + 3 * nc;
+  for (int a = threadIdx.x; a < Nm; a += blockDim.x) {
+    P[a] = dfc_from(psi[base + a]);
+    Ch[a] = dfc_from(chi[base + a]);
+  }
+  __syncthreads();
+  const dfl kap = df_from_double(kappa_of(kidx, Kz, K, lz));
+  const dfl kap2 = df_mul(kap, kap);
+  const dfl mm = df_make((float)m, 0.f);
+  const dfl mk = df_mul(mm, kap);
+  const dfl* rb = rdr + rows[m] * 2;
+  const dfl* db = lap + rows[m] * 5;
+  for (int a = threadIdx.x; a < Nm; a += blockDim.x) {
+    const dfl2 d = apply_D_df(db, Ch, a, Nm);
+    Dc[a] = d;
+    Ps[a] = dfc_sub(dfc_scale(kap2, Ch[a]), d);
+  }
+  __syncthreads();
+  for (int a = threadIdx.x; a < Nm; a += blockDim.x) {
+    const long long idx = base + a;
+    const dfl2 Rpsi = apply_R_df(rb, P, a, Nm);
+    const dfl2 Rchi = apply_R_df(rb, Ch, a, Nm);
+    const dfl2 RPsi = apply_R_df(rb, Ps, a, Nm);
+    const dfl2 D_psi = apply_D_df(db, P, a, Nm);
+    dfl2 fv[6];
+    fv[0] = dfc_add(dfc_iscale(mm, P[a]), dfc_iscale(kap, Rchi));                       // r v_r
+    fv[1] = dfc_sub(dfc_make(df_neg(Rpsi.re), df_neg(Rpsi.im)), dfc_scale(mk, Ch[a]));  // r v_phi
+    fv[2] = dfc_make(df_neg(Dc[a].re), df_neg(Dc[a].im));                               // v_z
+    fv[3] = dfc_add(dfc_iscale(mm, Ps[a]), dfc_iscale(kap, Rpsi));                      // r w_r
+    fv[4] = dfc_sub(dfc_make(df_neg(RPsi.re), df_neg(RPsi.im)), dfc_scale(mk, P[a]));   // r w_phi
+    fv[5] = dfc_make(df_neg(D_psi.re), df_neg(D_psi.im));                               // w_z
+    if (lpf && m == 0 && kidx == 0 && a < 4) {   // log proxies: real coefficients, n <= 3
+      fv[1].re = df_add(fv[1].re, df_from_double(lpf[a]));
+      fv[2].re = df_add(fv[2].re, df_from_double(lpf[4 + a]));
+      fv[4].re = df_add(fv[4].re, df_from_double(lpf[8 + a]));
+      fv[5].re = df_add(fv[5].re, df_from_double(lpf[12 + a]));
+    }
+    if (vp.bs) {
+      const long long o = ((long long)m * vp.K2 + 2 * kidx) * vp.Kq + a;
+#pragma unroll
+      for (int f = 0; f < 6; ++f) {
+        unsigned short* b = vp.bs + (long long)f * 3 * vp.part;
+        __nv_bfloat16 h, md, lo;
+        split3<float>(df_round_f32(fv[f].re), h, md, lo);
+        b[o] = __bfloat16_as_ushort(h); b[vp.part + o] = __bfloat16_as_ushort(md);
+        b[2 * vp.part + o] = __bfloat16_as_ushort(lo);
+        split3<float>(df_round_f32(fv[f].im), h, md, lo);
+        b[o + vp.Kq] = __bfloat16_as_ushort(h); b[vp.part + o + vp.Kq] = __bfloat16_as_ushort(md);
+        b[2 * vp.part + o + vp.Kq] = __bfloat16_as_ushort(lo);
+      }
+    } else {
+      double2* outs[6] = {rvr, rvp, vz, rwr, rwp, wz};
+#pragma unroll
+      for (int f = 0; f < 6; ++f) outs[f][idx] = make_double2(df_to_double(fv[f].re), df_to_double(fv[f].im));
+    }
+  }
+}
+
+__global__ void k_to_df(long long n, const double* __restrict__ src, dfl* __restrict__ dst) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = df_from_double(src[i]);
 }
 
 // ---- log-proxy tables -----------------------------------------------------------
@@ -550,6 +648,16 @@ int mlx_vortex_prepare(mlx_ctx* c, cudaStream_t st) {
   k_rdr_band<<<nblk(c->tri, 256), 256, 0, st>>>(c->M, c->nc, c->d_lap_off, c->d_rdr);
   MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_vortex_fields, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)(sizeof(double2) * 4 * c->nc)));
+  if (c->precision != MLX_FP64) {
+    // the double-float fields kernel's band tables (r d/dr, D_m), converted once
+    MLX_CUDA_TRY(c, cudaMalloc(&c->d_rdr_df, sizeof(dfl) * c->tri * 2));
+    MLX_CUDA_TRY(c, cudaMalloc(&c->d_lap_df, sizeof(dfl) * c->tri * 5));
+    k_to_df<<<nblk(c->tri * 2, 256), 256, 0, st>>>(c->tri * 2, c->d_rdr, (dfl*)c->d_rdr_df);
+    k_to_df<<<nblk(c->tri * 5, 256), 256, 0, st>>>(c->tri * 5, c->d_lap, (dfl*)c->d_lap_df);
+    MLX_LAUNCH_CHECK(c);
+    MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_vortex_fields_df, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(sizeof(dfl2) * 4 * c->nc)));
+  }
   MLX_CUDA_TRY(c, cudaMalloc(&c->d_jac, sizeof(double) * c->tri));
   k_jac_table<<<nblk(c->tri, 256), 256, 0, st>>>(c->M, c->nc, c->d_lap_off, c->d_jac);
   MLX_LAUNCH_CHECK(c);
@@ -587,9 +695,15 @@ static int vortex_nonlinear_t(mlx_ctx* c, double U0, const double2* state, doubl
   }
   {
     const int vt = c->nc >= 256 ? 256 : ((c->nc + 31) / 32) * 32;
-    k_vortex_fields<<<dim3(c->K, c->M), vt, sizeof(double2) * 4 * c->nc, st>>>(
-        c->nc, c->Kz, c->K, c->lz, c->d_soff, c->d_lap_off, c->d_rdr, c->d_lap, psi, chi, F[0], F[1], F[2], F[3],
-        F[4], F[5], c->lp_on ? c->d_lp + kLpFields : nullptr, planes);
+    const double* lpf = c->lp_on ? c->d_lp + kLpFields : nullptr;
+    if (c->precision == MLX_FP64)
+      k_vortex_fields<<<dim3(c->K, c->M), vt, sizeof(double2) * 4 * c->nc, st>>>(
+          c->nc, c->Kz, c->K, c->lz, c->d_soff, c->d_lap_off, c->d_rdr, c->d_lap, psi, chi, F[0], F[1], F[2],
+          F[3], F[4], F[5], lpf, planes);
+    else
+      k_vortex_fields_df<<<dim3(c->K, c->M), vt, sizeof(dfl2) * 4 * c->nc, st>>>(
+          c->nc, c->Kz, c->K, c->lz, c->d_soff, c->d_lap_off, (const dfl*)c->d_rdr_df, (const dfl*)c->d_lap_df,
+          psi, chi, F[0], F[1], F[2], F[3], F[4], F[5], lpf, planes);
   }
   MLX_LAUNCH_CHECK(c);
   int rc;
