@@ -382,6 +382,13 @@ int mlx_set_state(mlx_ctx* ctx, int kind, const void* host, long long bytes, voi
  *                solve runs);
  *                results agree with the other variants to rounding, not
  *                bitwise; 0 = off.
+ *   "solve_df": 1 (default) = in the MLX_FP32 and MLX_BF16X3 forms the pivot-free
+ *                segmented solve computes in double-float arithmetic (pairs of
+ *                FP32 numbers, about 47 significant bits per multiply-add) on the
+ *                FP32 pipe, from factor records converted at setup; the right-hand
+ *                side is formed in FP64 and the output rounded to FP64; 0 = FP64
+ *                arithmetic.  Results agree to the FP64 form's error bound with
+ *                2^-47 in place of 2^-53; the MLX_FP64 form always uses FP64.
  *   "solve_lean_cpw": real chains per warp of the lean variant, 16 or 32
  *                (default 32).
  *   "vortex_planes": 1 (default) = an MLX_BF16X3 vortex term writes its six

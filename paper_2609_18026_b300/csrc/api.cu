@@ -31,7 +31,8 @@ void free_ctx(mlx_ctx* c) {
                   c->lu_half.FS, c->lu_half.BS, c->lu_full.FS, c->lu_full.BS, c->lu_lap.FS, c->lu_lap.BS,
                   c->lu_helm.FS, c->lu_helm.BS, c->lu_Q.FS, c->lu_Q.BS, c->lu_H.FS, c->lu_H.BS,
                   c->lu_G.FS, c->lu_G.BS, c->lu_half.PHf, c->lu_half.PHb, c->lu_half.PSf,
-                  c->lu_full.PHf, c->lu_full.PHb, c->lu_full.PSf, c->lu_half.RNP, c->lu_full.RNP, c->d_diag,
+                  c->lu_full.PHf, c->lu_full.PHb, c->lu_full.PSf, c->lu_half.RNP, c->lu_full.RNP,
+                  c->lu_half.RDF, c->lu_full.RDF, c->lu_half.PSDF, c->lu_full.PSDF, c->d_diag,
                   c->d_bsf, c->d_bsb, c->d_filt, c->d_lp, c->d_enst, c->d_bsv, c->d_rdr_df, c->d_lap_df};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -529,6 +530,12 @@ int mlx_set_tuning(mlx_ctx* c, const char* key, int value) {
       }
       MLX_CUDA_TRY(c, cudaStreamSynchronize(nullptr));
     }
+    mlx_invalidate_graphs(c);
+    return MLX_OK;
+  }
+  if (strcmp(key, "solve_df") == 0) {
+    if (value != 0 && value != 1) return MLX_EINVAL;
+    c->solve_df = value;
     mlx_invalidate_graphs(c);
     return MLX_OK;
   }

@@ -16,6 +16,7 @@
 // One thread per system factorises.  The solve variants (staged, segmented, lean)
 // are described at their kernels; all use these FP64 factors.
 #include "mlx_internal.cuh"
+#include "df.cuh"
 #include "bf16_split.cuh"
 
 #include <string.h>
@@ -752,13 +753,44 @@ __global__ void k_seg_setup(int M, int nc, int Kz, const long long* __restrict__
   }
 }
 
+// Arithmetic of the segmented recurrences: FP64, or (DF) double-float on the FP32
+// pipe (df.cuh) for the FP32 and BF16x3 forms, whose factor records and entry-window
+// data were converted to hi + lo pairs at setup.  Both representations take 8 bytes,
+// so the shared-memory layout is the same.  The right-hand side is formed in FP64
+// (as in every variant) and converted once; the output is rounded back to FP64.
+template <bool DF>
+struct SegAr;
+template <>
+struct SegAr<false> {
+  using R = double;
+  __device__ static R zero() { return 0.0; }
+  __device__ static R from(double v) { return v; }
+  __device__ static R fma(R a, R b, R c) { return __fma_rn(a, b, c); }
+  __device__ static R nfma(R a, R b, R c) { return __fma_rn(-a, b, c); }   // c - a b
+  __device__ static R mul(R a, R b) { return __dmul_rn(a, b); }
+  __device__ static double sub_out(R y, double sv) { return y - sv; }
+  __device__ static double out(R y) { return y; }
+};
+template <>
+struct SegAr<true> {
+  using R = dfl;
+  __device__ static R zero() { return df_make(0.0f, 0.0f); }
+  __device__ static R from(double v) { return df_from_double(v); }
+  __device__ static R fma(R a, R b, R c) { return df_madd(a, b, c); }
+  __device__ static R nfma(R a, R b, R c) { return df_nmadd(a, b, c); }
+  __device__ static R mul(R a, R b) { return df_mul(a, b); }
+  __device__ static double sub_out(R y, double sv) { return df_to_double(df_add(y, df_neg(df_from_double(sv)))); }
+  __device__ static double out(R y) { return df_to_double(y); }
+};
+static_assert(sizeof(dfl) == sizeof(double), "double-float records keep the FP64 layout");
+
 // NP (no pivoting): the factorisation made no row interchange in any system of
 // the family, so the pivoted U rows carry exact zeros beyond the KL-th upper
 // entry; the recurrences then skip the swaps and those zero terms (the same
 // products in the same order: bitwise equal results, up to the sign of zero).
 // The work of one warp (gw = m groups_per_m + group) in its shared-memory slab
 // `base`; Az (may be NULL) as in band_solve_warp.
-template <int KL, int SEG, bool NP>
+template <int KL, int SEG, bool NP, bool DF = false>
 __device__ __forceinline__ void band_solve_seg_warp(int gw, unsigned char* __restrict__ base, int M, int nc,
                                                     int Kz, int K, int groups_per_m, int step, int keep_s,
                                                     double dt, const long long* __restrict__ soff,
@@ -774,6 +806,9 @@ __device__ __forceinline__ void band_solve_seg_warp(int gw, unsigned char* __res
                                                     const double* __restrict__ Ap, double* __restrict__ out,
                                                     const SplitPlanes& sp, double* __restrict__ Az = nullptr) {
   using SM = SegSmem<KL, SEG>;
+  using AR = SegAr<DF>;
+  using R = typename AR::R;                                  // double, or dfl when DF
+  static_assert(NP || !DF, "the double-float form is pivot-free only");
   constexpr int W = SM::W, CPW = SM::CPW, G = SM::G, RW = SM::RW;
   constexpr int UW = NP ? KL : 2 * KL;                      // upper entries the substitution reads
   const int lane = threadIdx.x & 31;
@@ -789,14 +824,14 @@ __device__ __forceinline__ void band_solve_seg_warp(int gw, unsigned char* __res
   double* Ds = Ls + (size_t)N * G * KL;
   double* Pf = Ds + (size_t)N * G;
   double* Pb = Pf + (size_t)N * G * KL;
-  double* Rs = reinterpret_cast<double*>(base);
-  double* PS = NP ? Rs + (size_t)G * N * RW : Pb + (size_t)N * G * 2 * KL;   // [G][SEG][KL][KL]
-  double* Y = PS + (size_t)G * SEG * KL * KL;                // [N][CPW]
-  double* Sv = Y + (size_t)N * CPW;                          // [N][CPW] (keep_s)
-  double* BH = Sv + (keep_s ? (size_t)N * CPW : 0);          // [SEG][KL][CPW] right-hand side heads
-  double* EP = BH + SEG * KL * CPW;                          // [SEG][KL][CPW] particular exit windows
-  double* SF = EP + SEG * KL * CPW;                          // [SEG][KL][CPW] entry windows
-  double* SB = SF + SEG * KL * CPW;                          // [SEG][2KL][CPW] back entry values
+  R* Rs = reinterpret_cast<R*>(base);
+  R* PS = NP ? Rs + (size_t)G * N * RW : reinterpret_cast<R*>(Pb + (size_t)N * G * 2 * KL);   // [G][SEG][KL][KL]
+  R* Y = PS + (size_t)G * SEG * KL * KL;                     // [N][CPW]
+  double* Sv = reinterpret_cast<double*>(Y + (size_t)N * CPW);   // [N][CPW] (keep_s)
+  R* BH = reinterpret_cast<R*>(Sv + (keep_s ? (size_t)N * CPW : 0));   // [SEG][KL][CPW] right-hand side heads
+  R* EP = BH + SEG * KL * CPW;                               // [SEG][KL][CPW] particular exit windows
+  R* SF = EP + SEG * KL * CPW;                               // [SEG][KL][CPW] entry windows
+  R* SB = SF + SEG * KL * CPW;                               // [SEG][2KL][CPW] back entry values
   int* Pi = reinterpret_cast<int*>(SB + SEG * 2 * KL * CPW); // [N][G]
   const long long fb = band_off[m];
   const long long sm = soff[m];
@@ -817,21 +852,23 @@ __device__ __forceinline__ void band_solve_seg_warp(int gw, unsigned char* __res
                gcnt * SEG * KL * KL * 8, lane);
     stage_rows(Pi, G * 4, piv + r0, (long long)Kz * 4, N, gcnt * 4, lane);
   }
-  // operand accessors: row i of system kq
-  auto Lrow = [&](int i, int kq) -> const double* {
-    return NP ? Rs + ((size_t)kq * N + i) * RW + SM::RO_L : Ls + ((size_t)i * G + kq) * KL;
+  // operand accessors: row i of system kq (R is double whenever NP is false)
+  auto Lrow = [&](int i, int kq) -> const R* {
+    return NP ? Rs + ((size_t)kq * N + i) * RW + SM::RO_L : reinterpret_cast<const R*>(Ls + ((size_t)i * G + kq) * KL);
   };
-  auto Dval = [&](int i, int kq) -> double {
-    return NP ? Rs[((size_t)kq * N + i) * RW + SM::RO_D] : Ds[(size_t)i * G + kq];
+  auto Dval = [&](int i, int kq) -> R {
+    return NP ? Rs[((size_t)kq * N + i) * RW + SM::RO_D] : reinterpret_cast<const R*>(Ds)[(size_t)i * G + kq];
   };
-  auto Uup = [&](int i, int kq, int t) -> double {     // U_{i, i+1+t}
-    return NP ? Rs[((size_t)kq * N + i) * RW + SM::RO_U + t] : Us[((size_t)i * G + kq) * W + t + 1];
+  auto Uup = [&](int i, int kq, int t) -> R {     // U_{i, i+1+t}
+    return NP ? Rs[((size_t)kq * N + i) * RW + SM::RO_U + t]
+              : reinterpret_cast<const R*>(Us)[((size_t)i * G + kq) * W + t + 1];
   };
-  auto PFrow = [&](int i, int kq) -> const double* {
-    return NP ? Rs + ((size_t)kq * N + i) * RW + SM::RO_F : Pf + ((size_t)i * G + kq) * KL;
+  auto PFrow = [&](int i, int kq) -> const R* {
+    return NP ? Rs + ((size_t)kq * N + i) * RW + SM::RO_F : reinterpret_cast<const R*>(Pf + ((size_t)i * G + kq) * KL);
   };
-  auto PBrow = [&](int i, int kq) -> const double* {
-    return NP ? Rs + ((size_t)kq * N + i) * RW + SM::RO_B : Pb + ((size_t)i * G + kq) * 2 * KL;
+  auto PBrow = [&](int i, int kq) -> const R* {
+    return NP ? Rs + ((size_t)kq * N + i) * RW + SM::RO_B
+              : reinterpret_cast<const R*>(Pb + ((size_t)i * G + kq) * 2 * KL);
   };
   cp_async_commit();
   // right-hand sides, every lane busy (as in k_band_solve)
@@ -873,8 +910,8 @@ __device__ __forceinline__ void band_solve_seg_warp(int gw, unsigned char* __res
         r = sv[u];
         if (A) r = make_double2(rhs_febe(sv[u].x, av[u].x, true, h), rhs_febe(sv[u].y, av[u].y, true, h));
       }
-      Y[(size_t)ii * CPW + cpl * 2] = r.x;
-      Y[(size_t)ii * CPW + cpl * 2 + 1] = r.y;
+      Y[(size_t)ii * CPW + cpl * 2] = AR::from(r.x);
+      Y[(size_t)ii * CPW + cpl * 2 + 1] = AR::from(r.y);
     }
   }
   cp_async_wait_all();
@@ -891,32 +928,32 @@ __device__ __forceinline__ void band_solve_seg_warp(int gw, unsigned char* __res
     const int ss = e / (KL * CPW), q = (e / CPW) % KL, cc = e % CPW;
     int a0, a1;
     seg_range<SEG>(N, ss, a0, a1);
-    BH[e] = (ss > 0) ? Y[(size_t)(a0 + q) * CPW + cc] : 0.0;
+    BH[e] = (ss > 0) ? Y[(size_t)(a0 + q) * CPW + cc] : AR::zero();
   }
   __syncwarp();
-  double* y = Y + c;
+  R* y = Y + c;
   // ---- forward, particular run of this segment ----
   if (act) {
-    double w[KL + 1];
-    w[0] = 0.0;
+    R w[KL + 1];
+    w[0] = AR::zero();
 #pragma unroll
-    for (int q = 0; q < KL; ++q) w[q + 1] = (sg == 0 && q < N) ? y[(size_t)q * CPW] : 0.0;
+    for (int q = 0; q < KL; ++q) w[q + 1] = (sg == 0 && q < N) ? y[(size_t)q * CPW] : AR::zero();
 #pragma unroll 2
     for (int j = j0; j < j1; ++j) {
 #pragma unroll
       for (int q = 0; q < KL; ++q) w[q] = w[q + 1];
       const int jn = j + KL;
-      w[KL] = (jn >= N) ? 0.0 : (jn >= j1 ? BH[((sg + 1) * KL + (jn - j1)) * CPW + c] : y[(size_t)jn * CPW]);
+      w[KL] = (jn >= N) ? AR::zero() : (jn >= j1 ? BH[((sg + 1) * KL + (jn - j1)) * CPW + c] : y[(size_t)jn * CPW]);
       if (!NP) {
         const int d = Pi[(size_t)j * G + kk] - j;
 #pragma unroll
         for (int q = 1; q <= KL; ++q)
-          if (q == d) { const double t = w[0]; w[0] = w[q]; w[q] = t; }
+          if (q == d) { const R t = w[0]; w[0] = w[q]; w[q] = t; }
       }
       y[(size_t)j * CPW] = w[0];
-      const double* l = Lrow(j, kk);
+      const R* l = Lrow(j, kk);
 #pragma unroll
-      for (int q = 1; q <= KL; ++q) w[q] = __fma_rn(-l[q - 1], w[0], w[q]);
+      for (int q = 1; q <= KL; ++q) w[q] = AR::nfma(l[q - 1], w[0], w[q]);
     }
 #pragma unroll
     for (int q = 0; q < KL; ++q) EP[(sg * KL + q) * CPW + c] = w[q + 1];
@@ -926,11 +963,11 @@ __device__ __forceinline__ void band_solve_seg_warp(int gw, unsigned char* __res
   for (int ss = 1; ss < SEG; ++ss) {
     for (int q = sg; q < KL; q += SEG) {
       if (act) {
-        double v = EP[((ss - 1) * KL + q) * CPW + c];
+        R v = EP[((ss - 1) * KL + q) * CPW + c];
         if (ss > 1) {
-          const double* ps = PS + ((size_t)(kk * SEG + ss - 1) * KL + q) * KL;
+          const R* ps = PS + ((size_t)(kk * SEG + ss - 1) * KL + q) * KL;
 #pragma unroll
-          for (int q2 = 0; q2 < KL; ++q2) v = __fma_rn(ps[q2], SF[((ss - 1) * KL + q2) * CPW + c], v);
+          for (int q2 = 0; q2 < KL; ++q2) v = AR::fma(ps[q2], SF[((ss - 1) * KL + q2) * CPW + c], v);
         }
         SF[(ss * KL + q) * CPW + c] = v;
       }
@@ -939,44 +976,44 @@ __device__ __forceinline__ void band_solve_seg_warp(int gw, unsigned char* __res
   }
   // ---- forward corrections, then y / U_rr for every row and chain ----
   if (act && sg > 0) {
-    double wv[KL];
+    R wv[KL];
 #pragma unroll
     for (int q = 0; q < KL; ++q) wv[q] = SF[(sg * KL + q) * CPW + c];
     for (int j = j0; j < j1; ++j) {
-      const double* pf = PFrow(j, kk);
-      double v = y[(size_t)j * CPW];
+      const R* pf = PFrow(j, kk);
+      R v = y[(size_t)j * CPW];
 #pragma unroll
-      for (int q = 0; q < KL; ++q) v = __fma_rn(pf[q], wv[q], v);
+      for (int q = 0; q < KL; ++q) v = AR::fma(pf[q], wv[q], v);
       y[(size_t)j * CPW] = v;
     }
   }
   __syncwarp();
   for (int i = il; i < (lane_piece ? N : 0); i += LP) {
-    const double dv = Dval(i, kql);
-    Y[(size_t)i * CPW + cpl * 2] = __dmul_rn(Y[(size_t)i * CPW + cpl * 2], dv);
-    Y[(size_t)i * CPW + cpl * 2 + 1] = __dmul_rn(Y[(size_t)i * CPW + cpl * 2 + 1], dv);
+    const R dv = Dval(i, kql);
+    Y[(size_t)i * CPW + cpl * 2] = AR::mul(Y[(size_t)i * CPW + cpl * 2], dv);
+    Y[(size_t)i * CPW + cpl * 2 + 1] = AR::mul(Y[(size_t)i * CPW + cpl * 2 + 1], dv);
   }
   __syncwarp();
   // ---- back substitution, particular run of this segment (zero x after it) ----
   if (act) {
-    double acc[UW];
+    R acc[UW];
 #pragma unroll
     for (int t = 0; t < UW; ++t) {
       const int r = j1 - 1 - t;
-      acc[t] = (r >= j0) ? y[(size_t)r * CPW] : 0.0;
+      acc[t] = (r >= j0) ? y[(size_t)r * CPW] : AR::zero();
     }
-    double xn = 0.0;
+    R xn = AR::zero();
 #pragma unroll 2
     for (int i = j1 - 1; i >= j0; --i) {
-      const double xi = __fma_rn(-Uup(i, kk, 0), xn, acc[0]);
+      const R xi = AR::nfma(Uup(i, kk, 0), xn, acc[0]);
 #pragma unroll
       for (int t = 1; t < UW; ++t)
-        if (i - t >= j0) acc[t] = __fma_rn(-Uup(i - t, kk, t), xn, acc[t]);
+        if (i - t >= j0) acc[t] = AR::nfma(Uup(i - t, kk, t), xn, acc[t]);
       y[(size_t)i * CPW] = xi;
 #pragma unroll
       for (int t = 0; t < UW - 1; ++t) acc[t] = acc[t + 1];
       const int rn = i - UW;
-      acc[UW - 1] = (rn >= j0) ? y[(size_t)rn * CPW] : 0.0;
+      acc[UW - 1] = (rn >= j0) ? y[(size_t)rn * CPW] : AR::zero();
       xn = xi;
     }
   }
@@ -989,11 +1026,11 @@ __device__ __forceinline__ void band_solve_seg_warp(int gw, unsigned char* __res
     for (int t = sg; t < UW; t += SEG) {
       if (act) {
         const int r = a0 + t;
-        double v = y[(size_t)r * CPW];
+        R v = y[(size_t)r * CPW];
         if (ss + 1 < SEG - 1) {
-          const double* pb = PBrow(r, kk);
+          const R* pb = PBrow(r, kk);
 #pragma unroll
-          for (int t2 = 0; t2 < UW; ++t2) v = __fma_rn(pb[t2], SB[((ss + 1) * 2 * KL + t2) * CPW + c], v);
+          for (int t2 = 0; t2 < UW; ++t2) v = AR::fma(pb[t2], SB[((ss + 1) * 2 * KL + t2) * CPW + c], v);
         }
         SB[(ss * 2 * KL + t) * CPW + c] = v;
       }
@@ -1002,14 +1039,14 @@ __device__ __forceinline__ void band_solve_seg_warp(int gw, unsigned char* __res
   }
   // ---- back corrections ----
   if (act && sg < SEG - 1) {
-    double vv[UW];
+    R vv[UW];
 #pragma unroll
     for (int t = 0; t < UW; ++t) vv[t] = SB[(sg * 2 * KL + t) * CPW + c];
     for (int i = j0; i < j1; ++i) {
-      const double* pb = PBrow(i, kk);
-      double v = y[(size_t)i * CPW];
+      const R* pb = PBrow(i, kk);
+      R v = y[(size_t)i * CPW];
 #pragma unroll
-      for (int t = 0; t < UW; ++t) v = __fma_rn(pb[t], vv[t], v);
+      for (int t = 0; t < UW; ++t) v = AR::fma(pb[t], vv[t], v);
       y[(size_t)i * CPW] = v;
     }
   }
@@ -1020,16 +1057,14 @@ __device__ __forceinline__ void band_solve_seg_warp(int gw, unsigned char* __res
   const long long prow = sp.bs ? ((long long)m * sp.K2 + 2 * (sgl ? K - kabsl : kabsl)) * sp.Kq : 0;
 #pragma unroll 4
   for (int i = il; i < (lane_piece ? N : 0); i += LP) {
-    double2 v = make_double2(Y[(size_t)i * CPW + cpl * 2], Y[(size_t)i * CPW + cpl * 2 + 1]);
+    const R yx = Y[(size_t)i * CPW + cpl * 2], yy = Y[(size_t)i * CPW + cpl * 2 + 1];
+    double2 v;
     if (step == MLX_STEP_ABCN) {
-      if (keep_s) {
-        v.x -= Sv[(size_t)i * CPW + cpl * 2];
-        v.y -= Sv[(size_t)i * CPW + cpl * 2 + 1];
-      } else {
-        const double2 sv = s2[pbase + i];
-        v.x -= sv.x;
-        v.y -= sv.y;
-      }
+      const double2 sv = keep_s ? make_double2(Sv[(size_t)i * CPW + cpl * 2], Sv[(size_t)i * CPW + cpl * 2 + 1])
+                                : s2[pbase + i];
+      v = make_double2(AR::sub_out(yx, sv.x), AR::sub_out(yy, sv.y));
+    } else {
+      v = make_double2(AR::out(yx), AR::out(yy));
     }
     out2[pbase + i] = v;
     if (Az) reinterpret_cast<double2*>(Az)[pbase + i] = make_double2(0.0, 0.0);
@@ -1044,7 +1079,7 @@ __device__ __forceinline__ void band_solve_seg_warp(int gw, unsigned char* __res
   }
 }
 
-template <int KL, int SEG, bool NP>
+template <int KL, int SEG, bool NP, bool DF = false>
 __global__ void k_band_solve_seg(int M, int nc, int Kz, int K, int groups_per_m, int step, int keep_s,
                                  double dt, const long long* __restrict__ soff,
                                  const long long* __restrict__ band_off, const double* __restrict__ U,
@@ -1070,14 +1105,14 @@ __global__ void k_band_solve_seg(int M, int nc, int Kz, int K, int groups_per_m,
     gw = (wib < 4) ? (q < H ? q : T) : (T - 1 - q >= H ? T - 1 - q : T);
   }
   unsigned char* base = smem_raw + (size_t)wib * SegSmem<KL, SEG>::per_warp(nc, keep_s, NP);
-  band_solve_seg_warp<KL, SEG, NP>(gw, base, M, nc, Kz, K, groups_per_m, step, keep_s, dt, soff, band_off, U, Lm,
-                                   piv, invd, PHf, PHb, PSf, RNP, s, A, Ap, out, sp);
+  band_solve_seg_warp<KL, SEG, NP, DF>(gw, base, M, nc, Kz, K, groups_per_m, step, keep_s, dt, soff, band_off, U,
+                                       Lm, piv, invd, PHf, PHb, PSf, RNP, s, A, Ap, out, sp);
 }
 
 // Batched persistent form (batch.cu), as kb_band_solve: warps take (member, warp
 // task) items; the member's job also names its influence data and, optionally,
 // the split planes its output is written to.
-template <int KL, int SEG, bool NP>
+template <int KL, int SEG, bool NP, bool DF = false>
 __global__ void kb_band_solve_seg(const BSolveJob* __restrict__ jobs, const int2* __restrict__ items, int nitems,
                                   int slab, int* __restrict__ ctr) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1092,7 +1127,7 @@ __global__ void kb_band_solve_seg(const BSolveJob* __restrict__ jobs, const int2
     const BSolveJob j = jobs[w.x];
     SplitPlanes sp;
     sp.bs = j.bs; sp.part = j.part; sp.Kq = j.kq; sp.K2 = j.k2;
-    band_solve_seg_warp<KL, SEG, NP>(w.y, base, j.M, j.nc, j.Kz, j.K, j.gpm, j.step, 0, j.dt, j.soff, j.band_off,
+    band_solve_seg_warp<KL, SEG, NP, DF>(w.y, base, j.M, j.nc, j.Kz, j.K, j.gpm, j.step, 0, j.dt, j.soff, j.band_off,
                                      j.U, j.L, j.piv, j.invd, j.PHf, j.PHb, j.PSf, j.RNP, j.s, j.A, j.Ap, j.out, sp,
                                      j.Az);
     __syncwarp();
@@ -1120,7 +1155,7 @@ int mlx_band_setup(mlx_ctx* c, cudaStream_t st) {
   cudaFree(c->lu_full.U); cudaFree(c->lu_full.L); cudaFree(c->lu_full.piv); cudaFree(c->lu_full.invd);
   for (BandLU* f : {&c->lu_half, &c->lu_full}) {
     cudaFree(f->FS); cudaFree(f->BS);
-    cudaFree(f->PHf); cudaFree(f->PHb); cudaFree(f->PSf); cudaFree(f->RNP);
+    cudaFree(f->PHf); cudaFree(f->PHb); cudaFree(f->PSf); cudaFree(f->RNP); cudaFree(f->RDF); cudaFree(f->PSDF);
   }
   c->d_Bplus = nullptr;
   c->lu_half = BandLU();
@@ -1533,6 +1568,7 @@ static int launch_solve(mlx_ctx* c, int step, const BandLU& f, const long long* 
       auto go = [&](auto seg_tag) -> bool {
         constexpr int S = decltype(seg_tag)::value;
         const bool np = f.nopiv && f.RNP;
+        const bool df = np && c->solve_df && f.RDF && c->precision != MLX_FP64;
         const size_t pw = SegSmem<KL, S>::per_warp(c->nc, keep_s, np);
         int WPB = S;                                // S warps per CTA, halved until the CTA fits 200 KB
         while (WPB > 1 && pw * WPB > 200 * 1024) WPB /= 2;
@@ -1540,12 +1576,14 @@ static int launch_solve(mlx_ctx* c, int step, const BandLU& f, const long long* 
         const int G = SegSmem<KL, S>::G;
         const int gpm = (c->Kz + G - 1) / G;
         const int warps = f.seg_m * gpm;
-        auto kern = np ? k_band_solve_seg<KL, S, true> : k_band_solve_seg<KL, S, false>;
+        auto kern = df ? k_band_solve_seg<KL, S, true, true>
+                       : (np ? k_band_solve_seg<KL, S, true> : k_band_solve_seg<KL, S, false>);
         const int pair = WPB == 8 ? 1 : 0;
         const int blocks = pair ? ((warps + 1) / 2 + 3) / 4 : (warps + WPB - 1) / WPB;
         lerr = launch_pdl(kern, dim3(blocks), dim3(32 * WPB), pw * WPB, st,
                           f.seg_m, c->nc, c->Kz, c->K, gpm, step, keep_s, c->dt, c->d_soff, fac_off, f.U, f.L,
-                          f.piv, f.invd, f.PHf, f.PHb, f.PSf, f.RNP, (const double*)s, (const double*)A,
+                          f.piv, f.invd, f.PHf, f.PHb, df ? (const double*)f.PSDF : f.PSf,
+                          df ? (const double*)f.RDF : f.RNP, (const double*)s, (const double*)A,
                           (const double*)Ap, (double*)out, (sp && whole) ? *sp : SplitPlanes(), pair);
         if (wrote && sp && sp->bs && whole) *wrote = true;
         return true;
@@ -1712,9 +1750,21 @@ static int set_lean_attrs(mlx_ctx* c, int lim) {
 // at least 2 kl rows, N = Nc - m >= 2 kl S: the data cover the orders m < seg_m
 // (the longest systems), and the staged solve takes the rest.  S = 8 falls back to
 // 4 when 4 segments reach every order and 8 do not, or when 8 reach none.
+__global__ void k_to_df(long long n, const double* __restrict__ src, dfl* __restrict__ dst) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    const double v = src[i];
+    dst[i] = df_from_double(v);
+  }
+}
+void mlx_to_df(const double* src, void* dst, long long n, cudaStream_t st) {
+  if (n > 0) k_to_df<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, src, reinterpret_cast<dfl*>(dst));
+}
+
 int mlx_seg_build(mlx_ctx* c, BandLU& f, int S, cudaStream_t st) {
-  cudaFree(f.PHf); cudaFree(f.PHb); cudaFree(f.PSf); cudaFree(f.RNP);
+  cudaFree(f.PHf); cudaFree(f.PHb); cudaFree(f.PSf); cudaFree(f.RNP); cudaFree(f.RDF); cudaFree(f.PSDF);
   f.PHf = f.PHb = f.PSf = f.RNP = nullptr;
+  f.RDF = f.PSDF = nullptr;
   f.seg = 0;
   f.seg_m = 0;
   const int kl = c->kl;
@@ -1740,6 +1790,14 @@ int mlx_seg_build(mlx_ctx* c, BandLU& f, int S, cudaStream_t st) {
     dim3 grid((unsigned)(((long long)c->Kz * c->nc + 127) / 128), segm);
     k_pack_seg_np<2><<<grid, 128, 0, st>>>(c->nc, c->Kz, c->d_band_off, f.U, f.L, f.invd, f.PHf, f.PHb, f.RNP);
     MLX_LAUNCH_CHECK(c);
+    if (c->precision != MLX_FP64) {
+      const long long nr = rows * SegSmem<2, 8>::RW, np = (long long)c->M * c->Kz * S * kl * kl;
+      MLX_CUDA_TRY(c, cudaMalloc(&f.RDF, sizeof(dfl) * nr));
+      MLX_CUDA_TRY(c, cudaMalloc(&f.PSDF, sizeof(dfl) * np));
+      mlx_to_df(f.RNP, f.RDF, nr, st);
+      mlx_to_df(f.PSf, f.PSDF, np, st);
+      MLX_LAUNCH_CHECK(c);
+    }
   }
   f.seg = S;
   f.seg_m = segm;
@@ -1786,6 +1844,8 @@ int mlx_band_prepare(mlx_ctx* c) {
   MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_band_solve_seg<2, 8, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
   MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_band_solve_seg<2, 4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
   MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_band_solve_seg<2, 8, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+  MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_band_solve_seg<2, 4, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+  MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_band_solve_seg<2, 8, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
   MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_band_solve<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
   MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_band_solve<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
   {
@@ -1834,6 +1894,7 @@ void mlx_band_batch_member(mlx_ctx* c, const double2* s, const double2* A, const
   const BandLU& f = c->lu_half;
   const bool seg = c->kl == 2 && c->solve_seg && f.PHf && f.seg && f.seg_m > 0;
   const bool np = seg && f.nopiv && f.RNP;
+  const bool df = np && c->solve_df && f.RDF && c->precision != MLX_FP64;
   const int mseg = seg ? f.seg_m : 0;
   BSolveJob base;
   memset(&base, 0, sizeof(base));
@@ -1850,11 +1911,13 @@ void mlx_band_batch_member(mlx_ctx* c, const double2* s, const double2* A, const
     BSolvePart pt;
     pt.job = base;
     BSolveJob& j = pt.job;
-    j.variant = (f.seg == 8 ? 1 : 2) + (np ? 2 : 0);
+    j.variant = (f.seg == 8 ? 1 : 2) + (df ? 4 : (np ? 2 : 0));
     j.M = mseg;                      // the segmented kernel's orders
     j.CPW = 32 / f.seg;
     j.gpm = (c->Kz + j.CPW / 4 - 1) / (j.CPW / 4);
-    j.PHf = f.PHf; j.PHb = f.PHb; j.PSf = f.PSf; j.RNP = f.RNP;
+    j.PHf = f.PHf; j.PHb = f.PHb;
+    j.PSf = df ? (const double*)f.PSDF : f.PSf;
+    j.RNP = df ? (const double*)f.RDF : f.RNP;
     if (planes && mseg == c->M && c->precision == MLX_BF16X3 && c->d_bsb) {
       j.bs = reinterpret_cast<unsigned short*>(c->d_bsb);
       j.kq = (int)c->tc_kq;
@@ -1888,13 +1951,16 @@ void mlx_band_batch_member(mlx_ctx* c, const double2* s, const double2* A, const
 }
 
 // the kernel of a batched solve group: variant 0 staged (half width kl), 1 / 2
-// segmented with 8 / 4 segments, 3 / 4 the same in the pivot-free form
+// segmented with 8 / 4 segments, 3 / 4 the same in the pivot-free form, 5 / 6
+// pivot-free in double-float arithmetic
 const void* mlx_band_batch_kernel(int kl, int variant) {
   switch (variant) {
     case 1: return (const void*)kb_band_solve_seg<2, 8, false>;
     case 2: return (const void*)kb_band_solve_seg<2, 4, false>;
     case 3: return (const void*)kb_band_solve_seg<2, 8, true>;
     case 4: return (const void*)kb_band_solve_seg<2, 4, true>;
+    case 5: return (const void*)kb_band_solve_seg<2, 8, true, true>;
+    case 6: return (const void*)kb_band_solve_seg<2, 4, true, true>;
     default: break;
   }
   switch (kl) {
@@ -1914,6 +1980,8 @@ int mlx_band_batch_launch(int kl, int variant, const BSolveJob* jobs, const int2
     case 2: kb_band_solve_seg<2, 4, false><<<grid, 32 * wpb, smem, st>>>(jobs, items, nitems, slab, ctr); break;
     case 3: kb_band_solve_seg<2, 8, true><<<grid, 32 * wpb, smem, st>>>(jobs, items, nitems, slab, ctr); break;
     case 4: kb_band_solve_seg<2, 4, true><<<grid, 32 * wpb, smem, st>>>(jobs, items, nitems, slab, ctr); break;
+    case 5: kb_band_solve_seg<2, 8, true, true><<<grid, 32 * wpb, smem, st>>>(jobs, items, nitems, slab, ctr); break;
+    case 6: kb_band_solve_seg<2, 4, true, true><<<grid, 32 * wpb, smem, st>>>(jobs, items, nitems, slab, ctr); break;
     default: break;
   }
   if (variant) return cudaGetLastError() == cudaSuccess ? MLX_OK : MLX_ECUDA;

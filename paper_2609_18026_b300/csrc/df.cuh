@@ -3,7 +3,8 @@
 // bits.  On this GPU an FP64 instruction issues once per 64 cycles per SM
 // sub-partition while FP32 instructions issue every cycle, so coefficient-space work
 // whose result is rounded to FP32 afterwards (the vortex term of the mixed-precision
-// forms) runs on the FP32 pipe in this representation.
+// forms, the half-width-2 implicit solves of the FP32 and BF16x3 forms) runs on the
+// FP32 pipe in this representation.
 //
 // The error-free transformations are the classical ones: the sum of two floats with
 // its rounding error (Knuth's branch-free two-sum, and the three-operation form when
@@ -50,6 +51,22 @@ __device__ __forceinline__ dfl df_mul(dfl x, dfl y) {
 }
 // a b + c
 __device__ __forceinline__ dfl df_fma(dfl a, dfl b, dfl c) { return df_add(df_mul(a, b), c); }
+// a b + c with a single error-free sum (Dekker's add2 after the product): about 15
+// FP32 operations against about 27 for df_fma; the error is bounded by a small
+// multiple of 2^-47 (|a b| + |c|) -- the backward-stable error model of one FP64
+// fused multiply-add with a larger unit roundoff, which is what a triangular
+// recurrence needs (its relative error can be large only where a b and c cancel).
+__device__ __forceinline__ dfl df_madd(dfl a, dfl b, dfl c) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  const dfl s = df_two_sum(p, c.hi);
+  const float t = __fadd_rn(__fadd_rn(e, c.lo), s.lo);
+  return df_fast_sum(s.hi, t);
+}
+// c - a b
+__device__ __forceinline__ dfl df_nmadd(dfl a, dfl b, dfl c) { return df_madd(df_neg(a), b, c); }
 
 // The FP64 value x as hi + lo by integer operations (no FP64 instruction): hi is the
 // FP32 rounding of x (to nearest even; |x| < 2^-126 gives 0, |x| >= 2^128 and
@@ -69,16 +86,28 @@ __device__ __forceinline__ dfl df_from_double(double x) {
   if (H == (1ULL << 24)) { H >>= 1; ++Ef; }                              // rounding carried into the next binade
   if (Ef >= 255) return df_make(__uint_as_float(sign | 0x7f800000u), 0.0f);
   const float hi = __uint_as_float(sign | ((unsigned)Ef << 23) | ((unsigned)H & 0x7fffffu));
-  // |R| <= 2^28: its FP32 rounding, scaled by 2^(E - 1075) (exact power-of-two scaling
-  // unless the result falls below the normal range, where it only loses low bits)
-  float lo = __ll2float_rn(R);
-  lo = ldexpf(lo, E - 1075);
+  // |R| <= 2^28: its FP32 rounding, scaled by 2^(E - 1075) through the exponent field
+  // (exact); a scaled value below 2^-126 (|x| below about 2^-102) becomes 0, so such
+  // x keep FP32 precision only
+  const float lr = __int2float_rn((int)R);
+  const int el = (int)((__float_as_uint(lr) >> 23) & 0xffu) + E - 1075;   // biased exponent after scaling
+  float lo = (R == 0 || el <= 0) ? 0.0f : __uint_as_float(__float_as_uint(lr) + ((unsigned)(E - 1075) << 23));
   if (sign) lo = -lo;
   return df_make(hi, lo);
 }
 
-// hi + lo as FP64 (exact: both fit in 53 bits) -- FP64 instructions, off the hot paths
-__device__ __forceinline__ double df_to_double(dfl x) { return (double)x.hi + (double)x.lo; }
+// An FP32 value as FP64 by integer operations (exact; FP32 subnormals become a signed
+// zero, inf and NaN stay inf and NaN)
+__device__ __forceinline__ double df_f32_to_f64(float v) {
+  const unsigned u = __float_as_uint(v);
+  const unsigned sg = u & 0x80000000u, e = (u >> 23) & 0xffu, mt = u & 0x7fffffu;
+  const unsigned eo = (e == 0u) ? 0u : (e == 255u ? 2047u : e + 896u);
+  const unsigned hw = sg | (eo << 20) | (e == 0u ? 0u : ((mt >> 3) | (e == 255u && mt ? 1u : 0u)));
+  const unsigned lw = (e == 0u) ? 0u : (mt << 29);
+  return __hiloint2double((int)hw, (int)lw);
+}
+// hi + lo rounded to FP64: one FP64 addition
+__device__ __forceinline__ double df_to_double(dfl x) { return __dadd_rn(df_f32_to_f64(x.hi), df_f32_to_f64(x.lo)); }
 
 // the FP32 rounding of hi + lo as the FP64 -> FP32 rounding used by the split writers
 // would give it (values below 2^-126 flush to a signed zero)

@@ -130,7 +130,9 @@ struct BLegJob {
 
 // One member's AB-CN banded solve (staged form) in a batched launch.
 struct BSolveJob {
-  int variant;          // 0 staged; 1 / 2 segmented, 8 / 4 segments; 3 / 4 the same, pivot-free
+  int variant;          // 0 staged; 1 / 2 segmented, 8 / 4 segments; 3 / 4 the same, pivot-free;
+                        // 5 / 6 pivot-free in double-float arithmetic (RNP, PSf then hold
+                        // the double-float records)
   int M, nc, Kz, K, CPW, gpm, step, kz_fac;
   double dt;
   const long long* soff;
@@ -202,6 +204,10 @@ struct BandLU {
   // rows back to back ([m][|k|][row], record = {L[kl], 1/diag, U upper[kl], PHf[kl],
   // PHb[kl], pad}), so that a warp stages its systems as one block
   double* RNP = nullptr;
+  // the same records and the per-segment entry-window data (PSf) as double-float
+  // pairs (hi, lo) for the FP32 and BF16x3 forms' double-float solve
+  void* RDF = nullptr;
+  void* PSDF = nullptr;
 };
 
 struct mlx_ctx {
@@ -315,6 +321,7 @@ struct mlx_ctx {
   int phi_tile = 0;                    // radii per CTA of the phi kernels (2..32; 0 = automatic)
   int z_tile = 0;                      // radii per CTA of the z kernels (1..32; 0 = automatic)
   int solve_seg = 8;                   // segments of the half-width-2 segmented solve (8, 4; 0 = off)
+  int solve_df = 1;                    // 1: FP32 / BF16X3 forms run the pivot-free segmented solve in double-float
   int solve_nopiv = 1;                 // 1: the segmented solve skips pivoting for families without interchanges
   int solve_fields2 = 1;               // 1: the lean solve takes both vortex fields in one launch
   int plane_reuse = 1;                 // 1: the graph-replayed FKPP steps reuse the solve's split planes
@@ -423,6 +430,8 @@ int mlx_legendre_tc_backward(mlx_ctx* c, const double2* spec, cudaStream_t st, b
 int mlx_legendre_tc_backward_field(mlx_ctx* c, int f, cudaStream_t st);
 // allocate d_bsv (zero tails) and encode its maps (BF16X3 vortex contexts)
 int mlx_tc_vortex_planes(mlx_ctx* c, cudaStream_t st);
+// n FP64 values as double-float pairs (df.cuh), elementwise; dst may equal src
+void mlx_to_df(const double* src, void* dst, long long n, cudaStream_t st);
 // nfields = 2: both fields of a vortex state (n_spec apart) in one launch (lean
 // variant only; MLX_EINVAL otherwise).  sp: where the segmented solve also writes
 // the BF16x3 split planes of its output for the backward contraction; *wrote says

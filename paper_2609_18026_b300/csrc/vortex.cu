@@ -227,11 +227,6 @@ __global__ void k_vortex_fields_df(int nc, int Kz, int K, double lz, const long 
   }
 }
 
-__global__ void k_to_df(long long n, const double* __restrict__ src, dfl* __restrict__ dst) {
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) dst[i] = df_from_double(src[i]);
-}
-
 // ---- log-proxy tables -----------------------------------------------------------
 // d_lp layout: [16] field additions (r v_phi, v_z, r w_phi, w_z; n = 0..3), [nc] lam =
 // lap_h Lambda, [nc] L Lambda, [2 nc] matvec scratch, [1] c of the last solve, then
@@ -652,8 +647,8 @@ int mlx_vortex_prepare(mlx_ctx* c, cudaStream_t st) {
     // the double-float fields kernel's band tables (r d/dr, D_m), converted once
     MLX_CUDA_TRY(c, cudaMalloc(&c->d_rdr_df, sizeof(dfl) * c->tri * 2));
     MLX_CUDA_TRY(c, cudaMalloc(&c->d_lap_df, sizeof(dfl) * c->tri * 5));
-    k_to_df<<<nblk(c->tri * 2, 256), 256, 0, st>>>(c->tri * 2, c->d_rdr, (dfl*)c->d_rdr_df);
-    k_to_df<<<nblk(c->tri * 5, 256), 256, 0, st>>>(c->tri * 5, c->d_lap, (dfl*)c->d_lap_df);
+    mlx_to_df(c->d_rdr, c->d_rdr_df, c->tri * 2, st);
+    mlx_to_df(c->d_lap, c->d_lap_df, c->tri * 5, st);
     MLX_LAUNCH_CHECK(c);
     MLX_CUDA_TRY(c, cudaFuncSetAttribute(k_vortex_fields_df, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)(sizeof(dfl2) * 4 * c->nc)));

@@ -236,6 +236,39 @@ def test_segmented_solve(grid, step):
     ctx.timing(False)
 
 
+@pytest.mark.parametrize("prec", [B.FP32, B.BF16X3])
+@pytest.mark.parametrize("grid", [(128, 128, 64, 4.0), (48, 128, 4, 1.0), (16, 8, 4, 1.0)])
+def test_segmented_solve_double_float(grid, prec, record):
+    # FP32 / BF16x3 forms: the pivot-free segmented solve runs in double-float
+    # arithmetic (hi + lo FP32 pairs, unit roundoff about 2^-47 per multiply-add against
+    # 2^-53); against the FP64 recurrence of the same context and against the oracle,
+    # the bound is the FP64 test's 2 kappa u with u = 2^-47, at least 1e-11
+    nr, nphi, nz, ell = grid
+    g, ctx = pair(nr, nphi, nz, ell, lz=3.0, policy="twothirds", precision=prec)
+    dt, nu = 2e-2, 0.3
+    ctx.implicit_setup(nu, dt)
+    s, A, Ap = (rand_spec(g, k) for k in (17, 18, 19))
+    st = O.Stepper(g, nu, dt)
+    S, AA, AP = (O.from_flat(g, v) for v in (s, A, Ap))
+    c = 0.5 * dt * nu
+    kappa = max(np.linalg.cond(np.eye(L.shape[0]) - c * L) for L in st.L.values())
+    tol = max(1e-11, 2.0 * kappa * 2.0 ** -47)
+    for step in (B.STEP_ABCN, B.STEP_FEBE_HALF):
+        outs = []
+        for dfm in (1, 0):
+            ctx.set_tuning("solve_df", dfm)
+            outs.append(ctx.implicit_solve(step, to_gpu_spec(s), to_gpu_spec(A), to_gpu_spec(Ap),
+                                           ctx.new_spec()).cpu().numpy())
+        assert np.all(np.isfinite(outs[0]))
+        assert np.linalg.norm(outs[0] - outs[1]) <= tol * np.linalg.norm(outs[1])
+        ref = st.abcn(S, AA, AP) if step == B.STEP_ABCN else st.febe(S, True, AA)
+        err = O.spec_rel_err(g, O.from_flat(g, outs[0]), ref)
+        record("segmented_solve_df", grid=grid[:3], precision={B.FP32: "fp32", B.BF16X3: "bf16x3"}[prec],
+               step=step, rel_err=err, fp64_form_err=O.spec_rel_err(g, O.from_flat(g, outs[1]), ref), tol=tol)
+        assert err <= tol
+    ctx.set_tuning("solve_df", 1)
+
+
 def test_fkpp_plane_reuse_bitwise_and_split_count():
     # BF16x3 Fisher-KPP: within one mlx_advance call the segmented solve writes the
     # split planes of its output and the next step's backward contraction takes
