@@ -881,7 +881,10 @@ __device__ __forceinline__ void band_solve_seg_warp(int gw, unsigned char* __res
   const int kql = cpl >> 1, sgl = cpl & 1, kabsl = k0 + kql;
   const bool lane_piece = cpl < 2 * gcnt && !(sgl && kabsl == 0);
   const long long pbase = sm + (long long)(sgl ? K - kabsl : kabsl) * N;
-  constexpr int RB = 8;
+  // rows per unrolled batch and unroll depths: the double-float bodies are about 15
+  // times longer, so their loops stay short to keep the code in the instruction cache
+  constexpr int RB = DF ? 2 : 8;
+  constexpr int UR = DF ? 1 : 2, UO = DF ? 1 : 4;
   for (int i = il; i < (lane_piece ? N : 0); i += RB * LP) {
     double2 sv[RB], av[RB], apv[RB];
 #pragma unroll
@@ -938,7 +941,7 @@ __device__ __forceinline__ void band_solve_seg_warp(int gw, unsigned char* __res
     w[0] = AR::zero();
 #pragma unroll
     for (int q = 0; q < KL; ++q) w[q + 1] = (sg == 0 && q < N) ? y[(size_t)q * CPW] : AR::zero();
-#pragma unroll 2
+#pragma unroll UR
     for (int j = j0; j < j1; ++j) {
 #pragma unroll
       for (int q = 0; q < KL; ++q) w[q] = w[q + 1];
@@ -1003,7 +1006,7 @@ __device__ __forceinline__ void band_solve_seg_warp(int gw, unsigned char* __res
       acc[t] = (r >= j0) ? y[(size_t)r * CPW] : AR::zero();
     }
     R xn = AR::zero();
-#pragma unroll 2
+#pragma unroll UR
     for (int i = j1 - 1; i >= j0; --i) {
       const R xi = AR::nfma(Uup(i, kk, 0), xn, acc[0]);
 #pragma unroll
@@ -1055,7 +1058,7 @@ __device__ __forceinline__ void band_solve_seg_warp(int gw, unsigned char* __res
   // the backward contraction, exactly as k_split_spec would write them) ----
   double2* out2 = reinterpret_cast<double2*>(out);
   const long long prow = sp.bs ? ((long long)m * sp.K2 + 2 * (sgl ? K - kabsl : kabsl)) * sp.Kq : 0;
-#pragma unroll 4
+#pragma unroll UO
   for (int i = il; i < (lane_piece ? N : 0); i += LP) {
     const R yx = Y[(size_t)i * CPW + cpl * 2], yy = Y[(size_t)i * CPW + cpl * 2 + 1];
     double2 v;

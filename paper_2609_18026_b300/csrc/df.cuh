@@ -68,32 +68,31 @@ __device__ __forceinline__ dfl df_madd(dfl a, dfl b, dfl c) {
 // c - a b
 __device__ __forceinline__ dfl df_nmadd(dfl a, dfl b, dfl c) { return df_madd(df_neg(a), b, c); }
 
-// The FP64 value x as hi + lo by integer operations (no FP64 instruction): hi is the
-// FP32 rounding of x (to nearest even; |x| < 2^-126 gives 0, |x| >= 2^128 and
-// non-finite values give +-inf with lo = 0), lo the FP32 rounding of x - hi.
+// The FP64 value x as hi + lo by 32-bit integer operations on its two words (no FP64
+// instruction): hi is the FP32 rounding of x (to nearest even; |x| < 2^-126 gives a
+// signed 0, |x| >= 2^128 and non-finite values give +-inf with lo = 0), lo the FP32
+// rounding of x - hi.
 __device__ __forceinline__ dfl df_from_double(double x) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
-  const int E = (int)((b >> 52) & 0x7ffu);
-  if (E < 897) return df_make(__uint_as_float(sign), 0.0f);             // |x| < 2^-126 (and 0)
+  const unsigned h = (unsigned)__double2hiint(x), l = (unsigned)__double2loint(x);
+  const unsigned sign = h & 0x80000000u, ah = h & 0x7fffffffu;
+  const int E = (int)(ah >> 20);                                        // biased FP64 exponent
+  if (E < 897) return df_make(__uint_as_float(sign), 0.0f);
   if (E >= 1151) return df_make(__uint_as_float(sign | 0x7f800000u), 0.0f);
-  const unsigned long long X = (b & 0xfffffffffffffULL) | (1ULL << 52);  // 53-bit significand, x = X 2^(E - 1075)
-  unsigned long long H = X >> 29;                                        // 24 bits
-  const unsigned long long rem = X & ((1ULL << 29) - 1);
-  if (rem > (1ULL << 28) || (rem == (1ULL << 28) && (H & 1ULL))) ++H;     // to nearest, ties to even
-  int Ef = E - 896;                                                      // biased FP32 exponent of hi
-  long long R = (long long)X - (long long)(H << 29);                     // x - hi in units of 2^(E - 1075)
-  if (H == (1ULL << 24)) { H >>= 1; ++Ef; }                              // rounding carried into the next binade
-  if (Ef >= 255) return df_make(__uint_as_float(sign | 0x7f800000u), 0.0f);
-  const float hi = __uint_as_float(sign | ((unsigned)Ef << 23) | ((unsigned)H & 0x7fffffu));
-  // |R| <= 2^28: its FP32 rounding, scaled by 2^(E - 1075) through the exponent field
-  // (exact); a scaled value below 2^-126 (|x| below about 2^-102) becomes 0, so such
-  // x keep FP32 precision only
-  const float lr = __int2float_rn((int)R);
-  const int el = (int)((__float_as_uint(lr) >> 23) & 0xffu) + E - 1075;   // biased exponent after scaling
-  float lo = (R == 0 || el <= 0) ? 0.0f : __uint_as_float(__float_as_uint(lr) + ((unsigned)(E - 1075) << 23));
-  if (sign) lo = -lo;
-  return df_make(hi, lo);
+  // exponent and the top 23 fraction bits; the increment of the rounding carries into
+  // the exponent when the fraction overflows (and into inf above FLT_MAX)
+  unsigned f = ((ah - (896u << 20)) << 3) | (l >> 29);
+  const unsigned rem = l & 0x1fffffffu;                                  // the 29 bits below hi
+  const unsigned up = (rem > 0x10000000u) | ((rem == 0x10000000u) & (f & 1u));
+  f += up;
+  const float hi = __uint_as_float(sign | f);
+  // |x| - |hi| = rem - up 2^29 in units of 2^(E - 1075), |.| <= 2^28: its FP32 rounding,
+  // scaled through the exponent field (exact); a scaled value below 2^-126 (|x| below
+  // about 2^-102) becomes 0, so such x keep FP32 precision only
+  const int R = (int)rem - (int)(up << 29);
+  const float lr = __int2float_rn(R);
+  const int el = (int)((__float_as_uint(lr) >> 23) & 0xffu) + E - 1075;  // biased exponent after scaling
+  const unsigned lb = (R == 0 || el <= 0) ? 0u : __float_as_uint(lr) + ((unsigned)(E - 1075) << 23);
+  return df_make(hi, __uint_as_float(lb ^ sign));
 }
 
 // An FP32 value as FP64 by integer operations (exact; FP32 subnormals become a signed
