@@ -278,11 +278,10 @@ FP64_PEAK_TFLOPS = 1.20
 
 # DRAM bytes (read + write) per launch of the dominant kernel at this workload, from
 # one ncu capture of the current kernel version (None = not captured for it):
-# k_band_solve_seg<2, 8, 1> (the pivot-free segmented solve, staging one contiguous
-# record per system row, long and short systems paired per SM sub-partition),
-# dram__bytes_read.sum 17,910,272 / 17,908,992 / 17,908,992 and dram__bytes_write.sum 0
-# (its output stays in L2) in three captured launches of `--profile-workload fkpp_steps`
-TRAFFIC = {"band_solve": 17909419}
+# k_band_solve_seg<2, 8, 1, 1> (the pivot-free segmented solve, recurrences in
+# double-float arithmetic): dram__bytes_read.sum 14,733,824 and dram__bytes_write.sum 0
+# (its output stays in L2) in one captured launch of `--profile-workload fkpp_steps`
+TRAFFIC = {"band_solve": 14733824}
 
 
 def band_solve_flops(ctx, kl=2):
@@ -700,7 +699,7 @@ def measure_corot(B, W, torch, dev, stream, prec=None, t_end=10.0, every=0.5):
 
 def measure_fkpp_steps(B, W, torch, dev, stream, bench_steps=2):
     """The benchmarked Fisher-KPP step alone (the headline workload's context,
-    BF16x3 contraction, FP32 FFTs, FP64 solve): bench_steps x 100 time steps from
+    BF16x3 contraction, FP32 FFTs, double-float solve): bench_steps x 100 time steps from
     t = 0, graph-replayed.  The command an ncu launch list of the step runs on."""
     ctx = B.Context(NR, NPHI, NZ, ELL, lz=LZ, precision=B.BF16X3, chop_policy=B.CHOP_TWOTHIRDS)
     ctx.implicit_setup(D_COEF, DT)
@@ -729,7 +728,8 @@ def measure_fkpp_steps(B, W, torch, dev, stream, bench_steps=2):
 def measure_batch(B, W, torch, dev, stream, steps=100, n=64, tune_cache=None):
     """64 uneven independent 2-D/3-D diffusion and Fisher-KPP instances (seed
     20261202: Nr in {32..256}, Nphi in {16..256}, Nz in {1, 16, 64}, ell in
-    [0.5, 4]), FP32 transforms (BF16x3 contraction), FP64 solves, dt = 1e-3,
+    [0.5, 4]), FP32 transforms (BF16x3 contraction), FP64 solves (a batch sets its
+    members' solves to FP64 recurrences), dt = 1e-3,
     advanced together by one CUDA graph per step pair: per-phase persistent
     queue launches (the default) and, for comparison, one graph branch per
     member.  Timed with the batch's default launch shapes and with every
@@ -1054,10 +1054,14 @@ def run_gpu(args, rank, world):
             "bytes_per_launch": bytes_full, "achieved_gbs": bytes_full / avg_s / 1e9,
             "frac": bytes_full / avg_s / 1e9 / hbm_peak,
             "note": "s, A^j, A^{j-1} in and s^{j+1} out (right-hand side fused) plus fill-free LU factors"}
-        roofline["fp64_pipe_view"] = {
-            "bound": "alu", "achieved": f64 / avg_s / 1e12, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": f64 / avg_s / 1e12 / FP64_PEAK_TFLOPS, "algorithmic_fp64_flops_per_launch": f64,
-            "peak_source": "measured FP64 FMA rate of this GPU model (independent chains), of measured"}
+        if ctx.precision == B.FP64:
+            roofline["fp64_pipe_view"] = {
+                "bound": "alu", "achieved": f64 / avg_s / 1e12, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": f64 / avg_s / 1e12 / FP64_PEAK_TFLOPS, "algorithmic_fp64_flops_per_launch": f64,
+                "peak_source": "measured FP64 FMA rate of this GPU model (independent chains), of measured"}
+        else:
+            roofline["arithmetic"] = ("pivot-free segmented recurrences in double-float (FP32 pairs) on the "
+                                      "FP32 pipe; FP64 only for the right-hand side and the output rounding")
     kernels = {k: {"launches": v[0], "avg_us": round(1000.0 * v[1] / v[0], 2), "share": round(v[1] / total_k, 4)}
                for k, v in sorted(kt_steady.items(), key=lambda kv: -kv[1][1])}
     roofline_contraction = None
@@ -1139,8 +1143,10 @@ def run_gpu(args, rank, world):
         "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None,
-        "dtype": {"bf16x3": "bf16x3 tensor-core contraction (f32 accumulate), f32 FFTs, f64 solve",
-                  "fp32": "f32 transforms, f64 solve", "fp64": "f64"}[args.precision],
+        "dtype": {"bf16x3": "bf16x3 tensor-core contraction (f32 accumulate), f32 FFTs, "
+                            "double-float (f32 pair) solve recurrences, f64 state",
+                  "fp32": "f32 transforms, double-float (f32 pair) solve recurrences, f64 state",
+                  "fp64": "f64"}[args.precision],
         "data": "synthetic (seeded analytic initial condition, PCG64 seed 2)",
         "config": {"workload": WORKLOAD, "nr": NR, "nphi": NPHI, "nz": NZ, "ell": ELL,
                    "lz": LZ, "chop": "two-thirds (M=43, K=43)", "dt": DT,

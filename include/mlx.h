@@ -430,7 +430,8 @@ int mlx_set_tuning(mlx_ctx* ctx, const char* key, int value);
  * only streams, events, cached CUDA graphs and the work lists of its persistent
  * launches.  Creating a batch sets the tuning key "solve_keep_s" of every member
  * to 0 (smaller shared-memory footprint per solve warp, so that more warps and
- * the instances' kernels co-reside). */
+ * the instances' kernels co-reside) and "solve_df" to 0 (FP64 recurrences: the
+ * persistent solve launch over many small systems runs faster with them). */
 typedef struct mlx_batch mlx_batch;
 int mlx_batch_create(mlx_ctx* const* ctxs, int n, mlx_batch** out);
 int mlx_batch_destroy(mlx_batch* batch);

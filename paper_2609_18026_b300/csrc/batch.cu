@@ -517,9 +517,14 @@ int mlx_batch_create(mlx_ctx* const* ctxs, int n, mlx_batch** out) {
   }
   // instances run side by side: the staged solve drops its shared-memory copy of s
   // (smaller CTAs co-reside with other instances' kernels; measured 2.1x -> 2.9x
-  // over sequential on the 64-instance workload)
+  // over sequential on the 64-instance workload), and the segmented solve keeps FP64
+  // recurrences (the persistent launch over the 64 instances' systems: 69.2k against
+  // 65.9k instance-steps/s with double-float ones)
   for (mlx_ctx* c : b->ctxs)
-    if (mlx_set_tuning(c, "solve_keep_s", 0) != MLX_OK) { batch_free(b); return MLX_ECUDA; }
+    if (mlx_set_tuning(c, "solve_keep_s", 0) != MLX_OK || mlx_set_tuning(c, "solve_df", 0) != MLX_OK) {
+      batch_free(b);
+      return MLX_ECUDA;
+    }
   *out = b;
   return MLX_OK;
 }
