@@ -757,7 +757,9 @@ __global__ void k_seg_setup(int M, int nc, int Kz, const long long* __restrict__
 // pipe (df.cuh) for the FP32 and BF16x3 forms, whose factor records and entry-window
 // data were converted to hi + lo pairs at setup.  Both representations take 8 bytes,
 // so the shared-memory layout is the same.  The right-hand side is formed in FP64
-// (as in every variant) and converted once; the output is rounded back to FP64.
+// (as in every variant) and converted once; the output is rounded back to FP64 and
+// the AB-CN "- s" taken there (the FP64 pipe has room; fewer instructions than the
+// double-float subtraction).
 template <bool DF>
 struct SegAr;
 template <>
@@ -779,7 +781,7 @@ struct SegAr<true> {
   __device__ static R fma(R a, R b, R c) { return df_madd(a, b, c); }
   __device__ static R nfma(R a, R b, R c) { return df_nmadd(a, b, c); }
   __device__ static R mul(R a, R b) { return df_mul(a, b); }
-  __device__ static double sub_out(R y, double sv) { return df_to_double(df_add(y, df_neg(df_from_double(sv)))); }
+  __device__ static double sub_out(R y, double sv) { return __dsub_rn(df_to_double(y), sv); }
   __device__ static double out(R y) { return df_to_double(y); }
 };
 static_assert(sizeof(dfl) == sizeof(double), "double-float records keep the FP64 layout");
@@ -883,8 +885,8 @@ __device__ __forceinline__ void band_solve_seg_warp(int gw, unsigned char* __res
   const long long pbase = sm + (long long)(sgl ? K - kabsl : kabsl) * N;
   // rows per unrolled batch and unroll depths: the double-float bodies are about 15
   // times longer, so their loops stay short to keep the code in the instruction cache
-  constexpr int RB = DF ? 2 : 8;
-  constexpr int UR = DF ? 1 : 2, UO = DF ? 1 : 4;
+  constexpr int RB = DF ? 4 : 8;
+  constexpr int UR = DF ? 1 : 2, UO = DF ? 2 : 4;
   for (int i = il; i < (lane_piece ? N : 0); i += RB * LP) {
     double2 sv[RB], av[RB], apv[RB];
 #pragma unroll
