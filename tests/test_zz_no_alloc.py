@@ -5,7 +5,8 @@ inside another framework's CUDA-graph capture or a host whose device-memory budg
 is frozen after start-up: the intermediate Fourier planes live in a fixed 16 MiB
 array built into the library instead of freshly allocated memory.  These tests
 call it through the C-ABI and check that two calls in a row give the same result
-as mlx_forward, and that grids too large for the array are refused.  This file is
+as mlx_forward, that a call captured into a CUDA graph replays correctly on fresh
+input, and that grids too large for the array are refused.  This file is
 collected last so that a failure here never hides another test's result.
 """
 
@@ -46,6 +47,38 @@ def test_noalloc_forward_matches_forward_twice(grid, prec):
         torch.cuda.synchronize()
         a, b = out.cpu().numpy(), ref.cpu().numpy()
         assert _rel(a, b) <= TOL[prec], (call, _rel(a, b))
+    ctx.device_status()
+
+
+@pytest.mark.parametrize("prec", [B.FP64, B.BF16X3])
+def test_noalloc_forward_inside_graph_capture(prec):
+    # the entry point's purpose: after one warm-up call it can be captured into a
+    # CUDA graph (no allocation, no synchronisation), and replays of that graph on
+    # fresh input agree with mlx_forward
+    import torch
+    nr, nphi, nz, ell = 128, 128, 64, 4.0
+    ctx = B.Context(nr, nphi, nz, ell, lz=2 * np.pi * 8, precision=prec, chop_policy=B.CHOP_TWOTHIRDS)
+    lib = B.load()
+    rng = np.random.default_rng(29)
+    phys = torch.as_tensor(rng.standard_normal((nz, nphi, nr)), dtype=ctx.phys_dtype).cuda()
+    out = ctx.new_spec()
+    rc = lib.mlx_forward_noalloc(ctx._h, ctypes.c_void_p(phys.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                 ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert rc == 0, lib.mlx_last_cuda_error(ctx._h)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        rc = lib.mlx_forward_noalloc(ctx._h, ctypes.c_void_p(phys.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                     ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert rc == 0, lib.mlx_last_cuda_error(ctx._h)
+    for rep in range(2):
+        fresh = torch.as_tensor(rng.standard_normal((nz, nphi, nr)), dtype=ctx.phys_dtype).cuda()
+        phys.copy_(fresh)
+        out.zero_()
+        graph.replay()
+        torch.cuda.synchronize()
+        ref = ctx.forward(fresh, ctx.new_spec())
+        assert _rel(out.cpu().numpy(), ref.cpu().numpy()) <= TOL[prec], rep
     ctx.device_status()
 
 
