@@ -806,7 +806,8 @@ __device__ __forceinline__ void band_solve_seg_warp(int gw, unsigned char* __res
                                                     const double* __restrict__ RNP,
                                                     const double* __restrict__ s, const double* __restrict__ A,
                                                     const double* __restrict__ Ap, double* __restrict__ out,
-                                                    const SplitPlanes& sp, double* __restrict__ Az = nullptr) {
+                                                    const SplitPlanes& sp, double* __restrict__ Az = nullptr,
+                                                    bool pdl = false) {
   using SM = SegSmem<KL, SEG>;
   using AR = SegAr<DF>;
   using R = typename AR::R;                                  // double, or dfl when DF
@@ -873,6 +874,13 @@ __device__ __forceinline__ void band_solve_seg_warp(int gw, unsigned char* __res
               : reinterpret_cast<const R*>(Pb + ((size_t)i * G + kq) * 2 * KL);
   };
   cp_async_commit();
+  // pdl: launched as a programmatic dependent; the staged factors and influence data
+  // were written at setup, so their copies above may overlap the predecessor's tail,
+  // and the wait comes before the first read of s, A, A_prev and the first write
+  if (pdl) {
+    pdl_wait();
+    pdl_trigger();
+  }
   // right-hand sides, every lane busy (as in k_band_solve)
   const double h = (step == MLX_STEP_FEBE_FULL) ? dt : 0.5 * dt;
   const double2* s2 = reinterpret_cast<const double2*>(s);
@@ -1096,8 +1104,6 @@ __global__ void k_band_solve_seg(int M, int nc, int Kz, int K, int groups_per_m,
                                  const double* __restrict__ Ap, double* __restrict__ out,
                                  SplitPlanes sp, int pair) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  pdl_wait();
-  pdl_trigger();
   const int wib = threadIdx.x >> 5;
   int gw = blockIdx.x * (blockDim.x >> 5) + wib;
   if (pair) {
@@ -1111,7 +1117,7 @@ __global__ void k_band_solve_seg(int M, int nc, int Kz, int K, int groups_per_m,
   }
   unsigned char* base = smem_raw + (size_t)wib * SegSmem<KL, SEG>::per_warp(nc, keep_s, NP);
   band_solve_seg_warp<KL, SEG, NP, DF>(gw, base, M, nc, Kz, K, groups_per_m, step, keep_s, dt, soff, band_off, U,
-                                       Lm, piv, invd, PHf, PHb, PSf, RNP, s, A, Ap, out, sp);
+                                       Lm, piv, invd, PHf, PHb, PSf, RNP, s, A, Ap, out, sp, nullptr, true);
 }
 
 // Batched persistent form (batch.cu), as kb_band_solve: warps take (member, warp
