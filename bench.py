@@ -279,10 +279,11 @@ FP64_PEAK_TFLOPS = 1.20
 # DRAM bytes (read + write) per launch of the dominant kernel at this workload, from
 # one ncu capture of the current kernel version (None = not captured for it):
 # k_band_solve_seg<2, 8, 1, 1> (the pivot-free segmented solve, recurrences in
-# double-float arithmetic) has not been captured since its last change (its factor
-# staging now precedes the programmatic-dependency wait); the build before it read
-# 17,908,224 / 17,912,576 / 17,907,200 bytes and wrote none in three AB-CN launches
-TRAFFIC = {"band_solve": None}
+# double-float arithmetic, factors staged before the programmatic-dependency wait):
+# dram__bytes_read.sum 17,907,712 / 17,907,712 / 17,911,552 and dram__bytes_write.sum 0
+# (its output stays in L2) in three captured AB-CN launches of
+# `--profile-workload fkpp_steps` (-s 3 -c 3)
+TRAFFIC = {"band_solve": 17908992}
 
 
 def band_solve_flops(ctx, kl=2):
