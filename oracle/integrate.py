@@ -17,8 +17,9 @@ two real right-hand sides (the matrices are real).
 Fisher-KPP (Eq. (17)): A(s) = gamma u (1 - u) with u = backward(s), formed at the
 collocation nodes and forward-transformed; the storage truncation is the
 two-thirds mask of Sec. 3.3 when the grid uses that chop policy.
-Parity of the long nonlinear FKPP evolution beyond the linear regime is
-"parity unpinned" (oracle only); its linear regime is pinned by Eq. (18).
+Its linear regime is pinned by Eq. (18). Its nonlinear evolution is pinned in one
+reduction: a uniform state follows the logistic closed form to second order in dt.
+Other nonlinear FKPP evolutions are "parity unpinned" (oracle only).
 """
 
 import numpy as np
