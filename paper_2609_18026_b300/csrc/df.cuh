@@ -1,10 +1,11 @@
 // Double-float arithmetic: a value is an unevaluated sum hi + lo of two FP32 numbers
 // with |lo| <= ulp(hi) / 2 (hi is the FP32 rounding of the sum), about 48 significant
 // bits.  On this GPU an FP64 instruction issues once per 64 cycles per SM
-// sub-partition while FP32 instructions issue every cycle, so coefficient-space work
-// whose result is rounded to FP32 afterwards (the vortex term of the mixed-precision
-// forms, the half-width-2 implicit solves of the FP32 and BF16x3 forms) runs on the
-// FP32 pipe in this representation.
+// sub-partition while FP32 instructions issue every cycle.  So coefficient-space work
+// of the mixed-precision forms that needs more than FP32 accuracy but not full FP64
+// runs on the FP32 pipe in this representation: the vortex fields (rounded to FP32 for
+// the transforms afterwards) and the recurrences of the half-width-2 implicit solve
+// (rounded back to the FP64 state, unit roundoff about 2^-47 per multiply-add).
 //
 // The error-free transformations are the classical ones: the sum of two floats with
 // its rounding error (Knuth's branch-free two-sum, and the three-operation form when
